@@ -1,0 +1,428 @@
+"""Pins that tie the FP64 oracle to the paper and to closed forms (CPU only).
+
+Each test checks the oracle against something other than itself: a brute-force
+definition, a textbook closed form, an identity of linear algebra, an
+independent physical route, or a value printed in the paper.  A dropped term,
+wrong sign, transposed operand or wrong index anywhere in ``oracle/`` should
+fail at least one of them.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import phantom as ph
+from oracle import dft, model, optics as O, tiles
+from conftest import rel_l2
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")
+
+
+# ------------------------------------------------------------------ P1 FFT
+@pytest.mark.parametrize("shape", [(8, 8, 8), (6, 10, 12)])
+def test_numpy_fft_matches_bruteforce_dft(shape):
+    x = np.random.default_rng(1).normal(size=shape) + 1j * np.random.default_rng(2).normal(size=shape)
+    ref = dft.bruteforce_dft(x)
+    assert np.abs(np.fft.fftn(x) - ref).max() <= 1e-12 * np.abs(ref).max()
+    back = dft.bruteforce_dft(ref, inverse=True)
+    assert np.abs(back - x).max() <= 1e-12
+    # Parseval: sum |x|^2 = (1/N) sum |X|^2
+    assert abs(np.sum(np.abs(x) ** 2) - np.sum(np.abs(ref) ** 2) / x.size) <= 1e-10 * np.sum(np.abs(x) ** 2)
+
+
+def test_dft_coefficient_matches_bruteforce():
+    x = np.random.default_rng(3).normal(size=(6, 10, 12))
+    ref = dft.bruteforce_dft(x)
+    for k in [(0, 0, 0), (1, 3, 5), (5, 9, 11), (3, 0, 7)]:
+        assert abs(dft.dft_coefficient(x, k) - ref[k]) <= 1e-12 * np.abs(ref).max()
+
+
+# ------------------------------------------------------------ pupils (a1)
+def test_pupil_radius_and_tilt_on_grid():
+    # pixel 0.1 um, X = Y = 40 -> grid step 1/(40*0.1) = 0.25 /um.  lambda = 0.5.
+    o = ph.optics(lambda_um=0.5, pixel_um=0.1, na_det=0.375, na_ill=0.0, tilt_x=0.25, tilt_y=0.0)
+    # Detection cutoff NA/lambda = 0.75 /um = exactly 3 grid steps (closed disk).
+    P = O.detection_pupil(o, 40, 40)
+    assert P[0, 3] == 1 and P[0, 4] == 0 and P[3, 0] == 1 and P[0, -3] == 1 and P[0, -4] == 0
+    assert P[2, 2] == 1 and P[2, 3] == 0  # 2^2+2^2 = 8 <= 9 < 13
+    # A point source tilted by tilt_x = 0.25 NA sits at nu_x = 0.25/0.5 = 0.5 /um = +2 steps.
+    S = O.source_pupil(o, 40, 40)
+    assert S.sum() == 1 and S[0, 2] == 1
+    o2 = dict(o, tilt_x=0.0, tilt_y=-0.125)  # -1 step along y
+    S2 = O.source_pupil(o2, 40, 40)
+    assert S2.sum() == 1 and S2[-1, 0] == 1
+
+
+def test_correlation_theorem_matches_direct_sum():
+    A, B = O.arms(ph.optics(na_ill=0.6, tilt_x=0.05), (3, 16, 20))
+    C = O.correlate(A, B)
+    for qy, qx in [(0, 0), (1, 3), (-2, 5), (7, -9), (8, 10)]:
+        assert np.abs(C[:, qy % 16, qx % 20] - O.correlate_direct(A, B, qy, qx)).max() <= 1e-12 * np.abs(C).max()
+
+
+def test_table1_matrix_is_the_papers():
+    g = json.load(open(GOLDEN))["table1_scalar_labelfree_matrix"]
+    m = np.array(g["re"]) + 1j * np.array(g["im"])
+    assert np.array_equal(O.TABLE1_LABELFREE, m)
+
+
+# ----------------------------------------------- P2 thin slab closed forms
+@pytest.mark.parametrize("defocus", [0.0, 0.37])
+def test_thin_slab_born_closed_form(defocus):
+    """On-axis point source, one-voxel slab: each plane's TF is
+    -2 (c/eta) sin(2 pi z (eta - k_m)) P for index and -2 (c/eta) cos(...) P for
+    absorption (textbook defocus CTF; k_m = n/lambda, c = 2 pi n dz / lambda^2)."""
+    o = ph.optics(na_ill=0.0, defocus_um=defocus)
+    shape = (8, 32, 32)
+    Hre, Him = O.labelfree_plane_tfs(o, shape)
+    lam, n, dz = o["lambda_um"], o["n_medium"], o["z_step_um"]
+    km = n / lam
+    c = 2 * np.pi * n * dz / lam ** 2
+    ky = np.fft.fftfreq(32, d=o["pixel_um"])
+    rho2 = ky[:, None] ** 2 + ky[None, :] ** 2
+    inside = rho2 <= (o["na_det"] / lam) ** 2
+    eta = np.sqrt(np.where(inside, km ** 2 - rho2, 1.0))
+    z = np.array([0, 1, 2, 3, -4, -3, -2, -1]) * dz + defocus
+    phase = 2 * np.pi * z[:, None, None] * (eta[None] - km)
+    exp_re = np.where(inside, -2 * c / eta * np.sin(phase), 0.0)
+    exp_im = np.where(inside, -2 * c / eta * np.cos(phase), 0.0)
+    assert np.abs(Hre - exp_re).max() <= 1e-12 * np.abs(exp_im).max()
+    assert np.abs(Him - exp_im).max() <= 1e-12 * np.abs(exp_im).max()
+    # Beer-Lambert at zero frequency: transmitted intensity drops by 2 k0 kappa dz.
+    k0 = 2 * np.pi / lam
+    assert np.allclose(Him[:, 0, 0], -2 * k0 * dz, rtol=1e-13)
+    # Phase of a uniform slab is invisible.
+    assert np.abs(Hre[:, 0, 0]).max() <= 1e-12
+
+
+def test_beer_lambert_oblique_partially_coherent():
+    """A uniform absorbing slab under a tilted partially coherent source dims
+    every plane by the source average of 2 k0 kappa dz / cos(theta_s), with
+    cos(theta_s) = eta(s)/k_m (oblique rays cross the slab on a longer path)."""
+    o = ph.optics(na_ill=0.7, tilt_x=0.08, tilt_y=-0.05, defocus_um=0.3)
+    shape = (6, 24, 24)
+    tfs = O.transfer_functions(o, shape, ("phase", "absorption"))
+    modes, _, _ = model.widefield_system(tfs, ("phase", "absorption"))
+    kappa = 1e-3
+    f = np.zeros((2,) + shape)
+    f[1, 2] = kappa  # one voxel-thick uniform slab in plane 2
+    d = model.forward(modes, f, [0.0])[0]
+    # closed form from the source points
+    lam, n, dz = o["lambda_um"], o["n_medium"], o["z_step_um"]
+    km, k0 = n / lam, 2 * np.pi / lam
+    nu = np.fft.fftfreq(24, d=o["pixel_um"])
+    vy, vx = nu[:, None] * np.ones((1, 24)), nu[None, :] * np.ones((24, 1))
+    S = ((vx - 0.08 / lam) ** 2 + (vy + 0.05 / lam) ** 2) <= (0.7 / lam) ** 2
+    P = (vx ** 2 + vy ** 2) <= (o["na_det"] / lam) ** 2
+    src = S & P
+    cos_t = np.sqrt(km ** 2 - vx[src] ** 2 - vy[src] ** 2) / km
+    expected = -np.mean(2 * k0 * kappa * dz / cos_t)
+    assert np.allclose(d, expected, rtol=1e-12, atol=0)
+    # a uniform index slab changes nothing
+    f2 = np.zeros((2,) + shape)
+    f2[0, 1] = 0.01
+    assert np.abs(model.forward(modes, f2, [0.0])[0]).max() <= 1e-14
+
+
+# ------------------------------------------------------------ P3 symmetry
+@pytest.mark.parametrize("tilt", [0.0, 0.07])
+def test_parity_and_hermitian(tilt):
+    """Odd Z, so that every plane j has its mirror -j: phase TF odd (purely
+    imaginary), absorption TF even (real), fluorescence TF real, even, max at
+    DC; all Hermitian (Methods, Summary of transfer functions)."""
+    o = ph.optics(na_ill=0.5, tilt_x=tilt, tilt_y=-0.03)
+    T = O.transfer_functions(o, (9, 32, 32))
+    R = lambda H: O.reflect(H, axes=(0, 1, 2))
+    for k, H in T.items():
+        s = np.abs(H).max()
+        assert np.abs(H - np.conj(R(H))).max() <= 1e-13 * s, k
+    assert np.abs(T["phase"] + R(T["phase"])).max() <= 1e-13 * np.abs(T["phase"]).max()
+    assert np.abs(T["phase"].real).max() <= 1e-13 * np.abs(T["phase"]).max()
+    assert np.abs(T["absorption"] - R(T["absorption"])).max() <= 1e-13 * np.abs(T["absorption"]).max()
+    assert np.abs(T["absorption"].imag).max() <= 1e-13 * np.abs(T["absorption"]).max()
+    Hf = T["fluor"]
+    assert np.abs(Hf.imag).max() <= 1e-13 and np.abs(Hf - R(Hf)).max() <= 1e-13
+    assert abs(Hf[0, 0, 0] - 1.0) <= 1e-13 and np.abs(Hf).max() <= 1.0 + 1e-13
+
+
+def test_hermitian_with_even_z_and_defocus():
+    o = ph.optics(na_ill=0.8, tilt_x=-0.06, defocus_um=-0.6)
+    T = O.transfer_functions(o, (8, 16, 24))
+    for k, H in T.items():
+        assert np.abs(H - np.conj(O.reflect(H, axes=(0, 1, 2)))).max() <= 1e-13 * np.abs(H).max(), k
+
+
+# ----------------------------------------------- P4 independent routes
+def _field_route(o, shape, m, dn_plane, kappa_plane):
+    """First-Born fields per source point, summed incoherently.
+
+    For each source point s (inside S and P) and data plane i the detector sees
+    the direct plane wave u0 = e^{i2pi(s.r + eta(s) z)} and the scattered field
+    us = IDFT2[P(nu) (i c / eta(nu)) e^{i2pi eta(nu) z} F(nu - s)], with z the
+    displacement between focus and the object plane m, and F the 2D spectrum of
+    dn + i kappa.  Label-free contrast is 2 Re(u0* us) summed over the source
+    (Methods, unified framework), normalised by the direct background.
+    """
+    Z, Y, X = shape
+    S = O.source_pupil(o, Y, X)
+    P = O.detection_pupil(o, Y, X)
+    eta = O.axial_frequency(o, Y, X)
+    inv_eta = np.where(P > 0, 1.0 / np.where(eta > 0, eta, 1.0), 0.0)
+    z = O.plane_displacements(Z, o["z_step_um"], o["defocus_um"])
+    c = 2 * np.pi * o["n_medium"] * o["z_step_um"] / o["lambda_um"] ** 2
+    F = np.fft.fft2(dn_plane + 1j * kappa_plane)
+    ky, kx = O.fft_indices(Y), O.fft_indices(X)
+    yy, xx = np.meshgrid(np.arange(Y), np.arange(X), indexing="ij")
+    out = np.zeros(shape)
+    count = 0
+    for sy, sx in zip(*np.nonzero(S * P)):
+        count += 1
+        Fs = np.roll(F, shift=(sy, sx), axis=(0, 1))  # F(nu - s)
+        for i in range(Z):
+            zi = z[(i - m) % Z]
+            u0 = np.exp(2j * np.pi * (ky[sy] * yy / Y + kx[sx] * xx / X + eta[sy, sx] * zi))
+            us = np.fft.ifft2(P * 1j * c * inv_eta * np.exp(2j * np.pi * eta * zi) * Fs)
+            out[i] += 2.0 * np.real(np.conj(u0) * us)
+    return out / count
+
+
+@pytest.mark.parametrize("m,na_ill,tilt_x", [(0, 0.55, 0.06), (2, 0.55, 0.06), (1, 1.15, 0.12)])
+def test_labelfree_forward_equals_source_point_field_sum(m, na_ill, tilt_x):
+    # the last case has source points outside the detection pupil (no direct light)
+    o = ph.optics(na_ill=na_ill, tilt_x=tilt_x, tilt_y=0.02, defocus_um=0.2)
+    shape = (5, 20, 24)
+    rng = np.random.default_rng(7)
+    dn = rng.normal(size=shape[1:]) * 1e-2
+    kap = rng.normal(size=shape[1:]) * 1e-3
+    tfs = O.transfer_functions(o, shape, ("phase", "absorption"))
+    modes, _, _ = model.widefield_system(tfs, ("phase", "absorption"))
+    f = np.zeros((2,) + shape)
+    f[0, m] = dn
+    f[1, m] = kap
+    d = model.forward(modes, f, [1.0])[0] - 1.0
+    ref = _field_route(o, shape, m, dn, kap)
+    assert rel_l2(d, ref) <= 1e-12
+
+
+def test_fluorescence_forward_of_point_is_psf():
+    """Forward of a point emitter = |sum_nu P_j(nu) e^{i2pi nu.r}|^2 per plane,
+    normalised to unit sum (explicit inverse-DFT matrices, no FFT)."""
+    o = ph.optics(defocus_um=0.4)
+    shape = (6, 16, 20)
+    Z, Y, X = shape
+    tfs = O.transfer_functions(o, shape, ("fluor",))
+    modes, _, _ = model.widefield_system(tfs, ("fluor",))
+    f = np.zeros((1,) + shape)
+    f[0, 0, 0, 0] = 1.0
+    d = model.forward(modes, f, [0.0])[0]
+    P = O.detection_pupil(o, Y, X)
+    eta = O.axial_frequency(o, Y, X)
+    z = O.plane_displacements(Z, o["z_step_um"], o["defocus_um"])
+    Ey = np.exp(2j * np.pi * np.outer(np.arange(Y), O.fft_indices(Y)) / Y)
+    Ex = np.exp(2j * np.pi * np.outer(np.arange(X), O.fft_indices(X)) / X)
+    psf = np.stack([np.abs(Ey @ (P * np.exp(2j * np.pi * eta * z[j])) @ Ex.T) ** 2 for j in range(Z)])
+    psf /= psf.sum()
+    assert rel_l2(d, psf) <= 1e-12
+
+
+def test_tf_at_matches_full_build():
+    o = ph.optics(na_ill=0.7, tilt_x=0.04, defocus_um=-0.3)
+    shape = (6, 16, 20)
+    T = O.transfer_functions(o, shape)
+    for kind in O.KINDS:
+        for k in [(0, 0, 0), (1, 2, 3), (5, 15, 19), (3, 8, 10), (2, 13, 4)]:
+            assert abs(O.tf_at(o, shape, kind, k) - T[kind][k]) <= 1e-12 * np.abs(T[kind]).max()
+
+
+# -------------------------------------------------- P5 linearity, adjoint
+def test_adjoint_dot_product():
+    o = ph.optics(na_ill=0.6, tilt_y=0.05)
+    shape = (6, 12, 16)
+    tfs = O.transfer_functions(o, shape)
+    modes, props, chans = model.widefield_system(tfs, O.KINDS)
+    rng = np.random.default_rng(11)
+    f = rng.normal(size=(3,) + shape)
+    d = rng.normal(size=(2,) + shape)
+    b = [0.7, -0.2]
+    Af = model.forward(modes, f, b) - np.array(b)[:, None, None, None]
+    Ahd = model.adjoint(modes, d + np.array(b)[:, None, None, None], b)
+    assert abs(np.vdot(Af, d) - np.vdot(f, Ahd)) <= 1e-12 * np.linalg.norm(Af) * np.linalg.norm(d)
+    # linearity
+    f2 = rng.normal(size=f.shape)
+    lhs = model.forward(modes, 2 * f - 3 * f2, [0, 0])
+    rhs = 2 * model.forward(modes, f, [0, 0]) - 3 * model.forward(modes, f2, [0, 0])
+    assert np.abs(lhs - rhs).max() <= 1e-12 * np.abs(lhs).max()
+
+
+# ------------------------------------------------------ P6 solver forms
+@pytest.mark.parametrize("C,P", [(1, 1), (1, 2), (2, 1), (3, 2), (2, 3), (4, 4)])
+def test_solver_identities(C, P):
+    rng = np.random.default_rng(C * 10 + P)
+    for _ in range(5):
+        H = rng.normal(size=(C, P)) + 1j * rng.normal(size=(C, P))
+        D = rng.normal(size=C) + 1j * rng.normal(size=C)
+        eta = 10 ** rng.uniform(-3, 0)
+        a = model.solve_normal(H, D, eta)
+        for other in (model.solve_pushthrough, model.solve_svd, model.solve_lstsq):
+            assert np.abs(other(H, D, eta) - a).max() <= 1e-10 * max(1.0, np.abs(a).max())
+        # the minimiser: gradient of ||D - H f||^2 + eta ||f||^2 vanishes
+        g = H.conj().T @ (H @ a - D) + eta * a
+        assert np.abs(g).max() <= 1e-10 * max(1.0, np.abs(D).max())
+
+
+def test_batched_normal_solve_matches_single_frequency_forms():
+    rng = np.random.default_rng(5)
+    C, P, n = 2, 2, 7
+    Hm = [[rng.normal(size=n) + 1j * rng.normal(size=n) for _ in range(P)] for _ in range(C)]
+    Dm = [rng.normal(size=n) + 1j * rng.normal(size=n) for _ in range(C)]
+    F = model._normal_solve(Hm, Dm, 0.3)
+    for i in range(n):
+        H = np.array([[Hm[c][p][i] for p in range(P)] for c in range(C)])
+        D = np.array([Dm[c][i] for c in range(C)])
+        assert np.abs(np.array([F[p][i] for p in range(P)]) - model.solve_svd(H, D, 0.3)).max() <= 1e-12
+
+
+# ----------------------------------------------------- P7 exact recovery
+@pytest.mark.parametrize("kind", ["phase", "fluor"])
+def test_exact_recovery_band_limited(kind):
+    o = ph.optics(na_ill=0.6)
+    shape = (8, 16, 16)
+    tfs = O.transfer_functions(o, shape, (kind,))
+    modes, _, _ = model.widefield_system(tfs, (kind,))
+    H = tfs[kind]
+    tau = 0.05
+    mask = np.abs(H) ** 2 >= tau * np.max(np.abs(H) ** 2)
+    f0 = np.random.default_rng(9).normal(size=shape)
+    f = np.real(np.fft.ifftn(np.fft.fftn(f0) * mask))[None]
+    d = model.forward(modes, f, [1.0])
+    eta = 1e-10
+    fh = model.reconstruct(modes, d, eta, background=[1.0])
+    assert rel_l2(fh, f) <= 2 * eta / tau + 1e-12
+
+
+def test_exact_recovery_2d_pooled_screen_optics():
+    """2D phase-from-defocus at the pooled-screen optics printed in Methods."""
+    g = json.load(open(GOLDEN))["pooled_screen_autotune"]
+    o = dict(ph.POOLED_SCREEN_OPTICS)
+    assert (o["lambda_um"], o["na_det"], o["na_ill"], o["n_medium"]) == (
+        g["wavelength_um"], g["na_det"], g["na_ill"], g["n_medium"])
+    shape = (7, 32, 32)
+    pt = O.plane_tfs(o, shape, ("phase",))
+    Hj = pt["phase"]
+    tot = np.sum(np.abs(Hj) ** 2, axis=0)
+    tau = 0.05
+    mask = tot >= tau * tot.max()
+    f2 = np.real(np.fft.ifft2(np.fft.fft2(np.random.default_rng(4).normal(size=shape[1:])) * mask))
+    # thin object at the reference plane -> every data plane j sees H_j
+    d = np.real(np.fft.ifft2(Hj * np.fft.fft2(f2)[None])) + 1.0
+    plane_modes = [dict(channels=[0], props=[0], H=[[Hj]])]
+    eta = 1e-10
+    fh = model.reconstruct_2d(plane_modes, d[None], eta, background=[1.0])
+    assert rel_l2(fh[0], f2) <= 2 * eta / tau + 1e-12
+
+
+# ----------------------------------------- P8 dense operator, brute force
+def _dense_operator(apply, n_in, out_size):
+    A = np.zeros((out_size, n_in))
+    e = np.zeros(n_in)
+    for i in range(n_in):
+        e[:] = 0.0
+        e[i] = 1.0
+        A[:, i] = apply(e).ravel()
+    return A
+
+
+@pytest.mark.parametrize("kinds,bg", [(("phase",), [1.3]), (("phase", "absorption"), [0.9]),
+                                      (("fluor",), None), (("phase", "absorption", "fluor"), [1.1, 0.4])])
+def test_dense_tikhonov_equals_fourier_reconstruction(kinds, bg):
+    o = ph.optics(na_ill=0.7, tilt_x=0.05, defocus_um=0.1)
+    shape = (8, 8, 8)
+    n = int(np.prod(shape))
+    tfs = O.transfer_functions(o, shape, kinds)
+    modes, props, chans = model.widefield_system(tfs, kinds)
+    rng = np.random.default_rng(21)
+    d = 1.0 + 0.05 * rng.normal(size=(len(chans),) + shape)
+    eta = 0.37
+    fh = model.reconstruct(modes, d, eta, background=bg, relative=False)
+    for m in modes:
+        P = len(m["props"])
+        sub = dict(channels=list(range(len(m["channels"]))), props=list(range(P)), H=m["H"])
+
+        def apply(x, sub=sub, P=P):
+            return model.forward([sub], x.reshape((P,) + shape), [0.0] * len(sub["channels"]))
+
+        A = _dense_operator(apply, P * n, len(m["channels"]) * n)
+        dm = np.stack([d[c] - (np.mean(d[c]) if bg is None else bg[c]) for c in m["channels"]]).ravel()
+        x = np.linalg.solve(A.T @ A + eta * np.eye(P * n), A.T @ dm)
+        got = np.stack([fh[p] for p in m["props"]]).ravel()
+        assert np.abs(got - x).max() <= 1e-9 * np.abs(x).max()
+
+
+def test_dense_tikhonov_equals_2d_reconstruction():
+    o = ph.optics(na_ill=0.5, defocus_um=-0.2)
+    shape = (5, 8, 8)
+    Z, Y, X = shape
+    pt = O.plane_tfs(o, shape, ("phase", "absorption"))
+    tf3 = {k: O.stack_to_3d(v) for k, v in pt.items()}
+    modes3, _, _ = model.widefield_system(tf3, ("phase", "absorption"))
+    plane_modes = [dict(channels=[0], props=[0, 1], H=[[pt["phase"], pt["absorption"]]])]
+
+    def apply(x):  # thin object in plane 0 of the 3D model
+        f = np.zeros((2,) + shape)
+        f[:, 0] = x.reshape(2, Y, X)
+        return model.forward(modes3, f, [0.0])
+    A = _dense_operator(apply, 2 * Y * X, Z * Y * X)
+    rng = np.random.default_rng(8)
+    d = 1.0 + 0.05 * rng.normal(size=(1,) + shape)
+    eta = 0.2
+    x = np.linalg.solve(A.T @ A + eta * np.eye(2 * Y * X), A.T @ (d[0] - np.mean(d[0])).ravel())
+    fh = model.reconstruct_2d(plane_modes, d, eta, background=None, relative=False)
+    assert np.abs(fh.ravel() - x).max() <= 1e-9 * np.abs(x).max()
+
+
+def test_relative_eta_definition():
+    o = ph.optics()
+    shape = (4, 8, 8)
+    tfs = O.transfer_functions(o, shape, ("phase", "absorption"))
+    modes, _, _ = model.widefield_system(tfs, ("phase", "absorption"))
+    d = 1.0 + 0.01 * np.random.default_rng(2).normal(size=(1,) + shape)
+    mx = np.max(np.abs(tfs["phase"]) ** 2 + np.abs(tfs["absorption"]) ** 2)
+    a = model.reconstruct(modes, d, 1e-3, relative=True)
+    b = model.reconstruct(modes, d, 1e-3 * mx, relative=False)
+    assert np.abs(a - b).max() <= 1e-14 * np.abs(a).max()
+
+
+# ------------------------------------------------------------ tiles (a8)
+def test_mirror_index():
+    assert tiles.mirror(np.arange(-2, 7), 5).tolist() == [2, 1, 0, 1, 2, 3, 4, 3, 2]
+
+
+def test_ramp_partition_of_unity():
+    E, halo, core = 192, 32, 128
+    w = tiles.ramp(E, halo)
+    assert np.allclose(w[core:] + w[: E - core], 1.0, atol=1e-15)
+    assert np.all(w[2 * halo: E - 2 * halo] == 1.0) and w.min() > 0
+
+
+@pytest.mark.parametrize("ty,tx,core,halo", [(2, 3, 16, 4), (1, 1, 8, 2), (3, 2, 12, 6)])
+def test_gather_then_blend_is_identity(ty, tx, core, halo):
+    field = np.random.default_rng(3).normal(size=(3, ty * core, tx * core))
+    t = tiles.gather(field, ty, tx, core, halo)
+    assert t.shape == (ty * tx, 3, core + 2 * halo, core + 2 * halo)
+    # a tile's core is the field's block
+    assert np.array_equal(t[ty * tx - 1][:, halo:halo + core, halo:halo + core],
+                          field[:, (ty - 1) * core:ty * core, (tx - 1) * core:tx * core])
+    back = tiles.blend(t, ty, tx, core, halo)
+    assert np.abs(back - field).max() <= 1e-14
+
+
+def test_blend_of_constant_tiles_is_convex():
+    ty, tx, core, halo = 2, 2, 16, 4
+    vals = np.array([1.0, 2.0, 3.0, 4.0])
+    t = np.broadcast_to(vals[:, None, None, None], (4, 1, core + 2 * halo, core + 2 * halo)).copy()
+    out = tiles.blend(t, ty, tx, core, halo)[0]
+    assert out[0, 0] == 1.0 and out[-1, -1] == 4.0 and out[0, -1] == 2.0
+    assert out.min() >= 1.0 and out.max() <= 4.0
+    # at the shared corner all four tiles weigh equally
+    assert abs(out[core - 1: core + 1, core - 1: core + 1].mean() - 2.5) <= 1e-12
