@@ -1,0 +1,393 @@
+"""Benchmark of the hot path: transfer-function build + Tikhonov reconstruction.
+
+One step = build the phase, absorption and fluorescence transfer functions
+of a 96 x 512 x 512 widefield stack from its optics, then reconstruct the
+three property volumes (label-free 1 x 2 and fluorescence 1 x 1 per-frequency
+solves, relative eta = 1e-3, background = channel means) from the two data
+stacks (brightfield, fluorescence).  Inputs are synthetic (seeded phantom,
+forward-simulated, 1e-3 Gaussian noise) and resident in HBM; the working set
+(~0.2 GB of data, 0.3 GB of TFs, 0.6 GB of workspace) exceeds the 129 MB L2,
+so no flush is needed between steps.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+N > 1 runs under torchrun: every rank reconstructs its own volume (weak
+scaling, no data-path collective); the reported value is the total over ranks.
+"""
+from __future__ import annotations
+
+import os
+
+os.environ.setdefault("OMP_NUM_THREADS", "1")        # the CPU oracle baseline runs single-threaded
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("MKL_NUM_THREADS", "1")
+
+import argparse
+import hashlib
+import json
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "recon voxels/s & auto-tuned tiles/s at fixed error; % of HBM roofline"
+SHAPE = (96, 512, 512)
+KINDS = ("phase", "absorption", "fluor")
+ETA = [1e-3, 1e-3]
+WORKLOAD = "widefield 96x512x512: TF build (phase+absorption+fluorescence) + 3D Tikhonov reconstruction"
+# CPU sample for the oracle baseline: the same optics, kinds and eta on a
+# 96 x 256 x 256 sub-volume (1/4 of the voxels, a quarter of the objects).
+CPU_SAMPLE = (96, 256, 256)
+
+# Last ncu capture of DRAM traffic per launch (bytes) of the dominant kernel,
+# keyed by kernel family and the digest of its source file at capture time.
+NCU_TRAFFIC = {}
+
+
+def kernel_digest(name: str) -> str:
+    src = {"z_fused": "wo_zops.cu", "z_solve2d": "wo_zops.cu", "rows_r2c": "wo_rows.cu", "rows_c2r": "wo_rows.cu",
+           "y_fwd": "wo_cols.cu", "y_inv": "wo_cols.cu", "tf_ypass": "wo_cols.cu", "tf_arms": "wo_tf.cu",
+           "tf_psf_rows": "wo_tf.cu", "tf_zpass": "wo_tf.cu", "tf_pupil_record": "wo_tf.cu"}.get(name)
+    if src is None:
+        return ""
+    h = hashlib.sha256()
+    for f in (src, "wo_fft.cuh"):
+        with open(os.path.join(ROOT, "paper_2412_09775_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def algorithmic_bytes(shape, kinds):
+    """Compulsory HBM bytes per launch of each kernel family for one step."""
+    Z, Y, X = shape
+    Xh = X // 2 + 1
+    nk = len(kinds)
+    lf = 1 if {"phase", "absorption"} & set(kinds) else 0
+    C = lf + (1 if "fluor" in kinds else 0)
+    P = nk
+    n_arms = 2 * lf + (1 if "fluor" in kinds else 0)
+    real = Z * Y * X * 4
+    half = Z * Y * Xh * 8
+    return {
+        "tf_pupil_record": Y * X * 16,
+        "tf_arms": n_arms * Z * Y * X * 8,
+        "tf_psf_rows": n_arms * Z * Y * X * 8 + nk * half,
+        "tf_ypass": 2 * nk * half,
+        "tf_zpass": 2 * nk * half,
+        "rows_r2c": C * (real + half),
+        "y_fwd": 2 * C * half,
+        "z_fused": (C + nk + P) * half,
+        "y_inv": 2 * P * half,
+        "rows_c2r": P * (half + real),
+    }
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in getattr(self, "lines", []):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ inputs
+def make_inputs(shape, seed=2):
+    import phantom as ph
+    o = ph.optics()
+    vols = ph.widefield_phantom(seed, shape, o)
+    f = np.stack([vols["dn"], vols["kappa"], vols["rho"]]).astype(np.float32)
+    return o, f
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_step(o, d):
+    from oracle import model as OM, optics as OO
+    shape = d.shape[1:]
+    tfs = OO.transfer_functions(o, shape, KINDS)
+    modes, _, _ = OM.widefield_system(tfs, KINDS)
+    out = np.zeros((3,) + shape)
+    for m, e in zip(modes, ETA):
+        r = OM.reconstruct([m], d, e)
+        for p in m["props"]:
+            out[p] = r[p]
+    return out
+
+
+def oracle_sample_inputs():
+    """Seeded data for the CPU sample (oracle forward of a phantom + noise)."""
+    import phantom as ph
+    from oracle import model as OM, optics as OO
+    o = ph.optics()
+    shape = CPU_SAMPLE
+    vols = ph.widefield_phantom(3, shape, o, n_spheres=2000 // 4, n_shells=200 // 4)
+    f = np.stack([vols["dn"], vols["kappa"], vols["rho"]])
+    modes, _, _ = OM.widefield_system(OO.transfer_functions(o, shape, KINDS), KINDS)
+    d = OM.forward(modes, f, [1.0, 0.1])
+    for c in range(2):
+        d[c] += ph.gaussian_noise(10 + c, shape, 1e-3 * abs(d[c].mean()))
+    return o, d.astype(np.float32).astype(np.float64)
+
+
+def cpu_baseline(steps=2):
+    o, d = oracle_sample_inputs()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        oracle_step(o, d)
+    dt = (time.perf_counter() - t0) / steps
+    vox = float(np.prod(CPU_SAMPLE))
+    return {"value": vox / dt, "unit": "voxels/s", "cores": 1, "kind": "oracle",
+            "sample": f"numpy float64 oracle, TF build + reconstruction of a {CPU_SAMPLE[0]}x{CPU_SAMPLE[1]}x"
+                      f"{CPU_SAMPLE[2]} sub-volume (1/4 of the voxels, same optics/kinds/eta), "
+                      f"{dt:.1f} s per step, single thread", "seconds_per_step": dt,
+            "host_cpus": os.cpu_count()}
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    from paper_2412_09775_gb300.build import build
+    build()
+    from paper_2412_09775_gb300 import binding as B
+    import phantom as ph
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    Z, Y, X = SHAPE
+    o, f = make_inputs(SHAPE, seed=2 + rank)
+    tf, ws = B.alloc(1, Z, Y, X, KINDS, dev)
+    # synthetic data: forward model of the phantom (on the GPU) + seeded noise
+    f_d = torch.from_numpy(f).to(dev)
+    data = torch.empty((1, 2, Z, Y, X), dtype=torch.float32, device=dev)
+    B.wo_build_tf([o], 1, Z, Y, X, KINDS, tf, ws)
+    B.wo_forward(tf, KINDS, f_d, [1.0, 0.1], data, 1, Z, Y, X, ws)
+    torch.cuda.synchronize()
+    mean = data.mean(dim=(2, 3, 4)).cpu().numpy()[0]
+    for c in range(2):
+        noise = ph.gaussian_noise(100 + 10 * rank + c, SHAPE, 1e-3 * abs(float(mean[c]))).astype(np.float32)
+        data[0, c] += torch.from_numpy(noise).to(dev)
+    del f_d
+    out = torch.empty((1, 3, Z, Y, X), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        B.wo_build_tf([o], 1, Z, Y, X, KINDS, tf, ws)
+        B.wo_reconstruct(tf, KINDS, data, None, ETA, B.WO_ETA_RELATIVE, B.WO_MODE_3D, out, 1, Z, Y, X, ws)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    B.wo_profile_read()  # drop anything recorded so far
+    B.wo_profile_enable(True)
+    n0 = B.wo_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    launches = B.wo_launch_count() - n0
+    B.wo_profile_enable(False)
+    prof = B.wo_profile_read()
+    barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ms_max = ms
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+
+    # end to end through the public API: host (pinned) in, host out
+    h_in = torch.empty((1, 2, Z, Y, X), dtype=torch.float32, pin_memory=True)
+    h_in.copy_(data.cpu())
+    h_out = torch.empty((1, 3, Z, Y, X), dtype=torch.float32, pin_memory=True)
+    d_in = torch.empty_like(data)
+
+    def e2e_step():
+        d_in.copy_(h_in, non_blocking=True)
+        B.wo_build_tf([o], 1, Z, Y, X, KINDS, tf, ws)
+        B.wo_reconstruct(tf, KINDS, d_in, None, ETA, B.WO_ETA_RELATIVE, B.WO_MODE_3D, out, 1, Z, Y, X, ws)
+        h_out.copy_(out, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    if rank != 0:
+        return
+    vox = float(Z * Y * X)
+    value = world * vox / (ms_max * 1e-3)
+    algo = algorithmic_bytes(SHAPE, KINDS)
+    per_kernel = {}
+    for name, (cnt, tot) in prof.items():
+        avg = tot / cnt if cnt else 0.0
+        b = algo.get(name)
+        per_kernel[name] = {"launches": cnt, "avg_ms": round(avg, 4),
+                            "share": round(tot / max(1e-9, sum(v[1] for v in prof.values())), 4),
+                            "algo_bytes": b,
+                            "gbs": round(b / (avg * 1e-3) / 1e9, 1) if b and avg > 0 else None}
+    dom = max(prof.items(), key=lambda kv: kv[1][1])[0]
+    peak, peak_kind = peaks()
+    dk = per_kernel[dom]
+    traffic = None
+    rec = NCU_TRAFFIC.get(dom)
+    if rec and rec.get("digest") == kernel_digest(dom):
+        traffic = rec["bytes"]
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": dk["gbs"], "peak": peak, "unit": "GB/s",
+                "frac": round(dk["gbs"] / peak, 4) if dk["gbs"] else None, "traffic": traffic,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                else "fallback 6.8 TB/s"}
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "voxels/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded phantom: 2000 spheres + 200 shells, GPU forward model + 1e-3 noise)",
+        "config": {"workload": WORKLOAD, "Z": Z, "Y": Y, "X": X, "kinds": list(KINDS), "eta_relative": ETA,
+                   "background": "channel mean", "tiles": 1, "parallelism": f"replicas x{world}",
+                   "l2": "working set > L2 (no flush needed): data 201 MB, TF 303 MB, workspace 606 MB"},
+        "roofline": roofline,
+        "kernels": per_kernel,
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "e2e": {"value": round(world * vox / (e2e_ms * 1e-3), 1), "unit": "voxels/s",
+                "ms_per_step": round(e2e_ms, 4),
+                "h2d_bytes_per_step": int(2 * vox * 4 + 72), "d2h_bytes_per_step": int(3 * vox * 4)},
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    o, d = oracle_sample_inputs()
+    for _ in range(args.warmup):
+        oracle_step(o, d)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_step(o, d)
+    dt = (time.perf_counter() - t0) / args.steps
+    vox = float(np.prod(CPU_SAMPLE))
+    value = vox / dt
+    sample = (f"numpy float64 oracle (no reference code exists: the paper ships none), TF build + "
+              f"reconstruction of a {CPU_SAMPLE[0]}x{CPU_SAMPLE[1]}x{CPU_SAMPLE[2]} sub-volume of the widefield "
+              f"workload per step, single thread")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "voxels/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": list(CPU_SAMPLE)},
+            "cpu_baseline": {"value": round(value, 1), "unit": "voxels/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 1), "unit": "voxels/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        run_gpu(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,178 @@
+/*
+ * wo.h - C ABI of the GB300 (sm_103a) library for WaveOrder's linear
+ * wave-optical imaging model and its Tikhonov inverse (arxiv 2412.09775).
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ * - Volumes are float32, x contiguous: [n_tiles][channel or property][Z][Y][X].
+ * - Spectra use the unnormalised forward DFT; inverses carry 1/N.  Transfer
+ *   functions are stored as the non-redundant half spectrum
+ *   [Z][Y][X/2+1] of interleaved complex64 (re, im), FFT order, not shifted.
+ * - Frequencies nu = k / (N * pixel) with k in FFT order; plane j of a stack
+ *   sits at focal displacement z_j = k_j * z_step + defocus (k_j in FFT order),
+ *   boundaries are periodic in x, y and z.
+ * - Properties, in this order, for the kinds present in `kinds`:
+ *   WO_TF_PHASE -> index increment dn, WO_TF_ABSORPTION -> extinction index
+ *   kappa, WO_TF_FLUOR -> fluorophore density.  Channels: one brightfield
+ *   stack if any label-free kind is present, then one fluorescence stack if
+ *   WO_TF_FLUOR is.  The two contrast modes are independent (block-diagonal
+ *   operator, Eq. fwd_block).
+ * - Supported lengths: Y, Z and X/2 must each be 1 or 2^a * 3^b with
+ *   b <= 1 and the value <= 2048 (see wo_size_supported); X must be even.
+ *
+ * Ownership and errors
+ * --------------------
+ * The caller allocates every device buffer (for example as torch tensors)
+ * and keeps it alive until the work queued on `stream` has finished.  The
+ * library never allocates or frees device memory and never synchronises the
+ * device; all work is queued on `stream`.  Device pointers must be 16-byte
+ * aligned.  Every entry point validates its arguments before launching
+ * anything; on an error status nothing was launched and no output was
+ * touched.  A failed CUDA launch returns WO_ERR_CUDA (the queue may then hold
+ * partial work).  Host arrays (h_*) are read during the call only.
+ *
+ * The API is not re-entrant across host threads that share one workspace.
+ */
+#ifndef WO_H
+#define WO_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same object as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st *wo_stream;
+
+typedef enum {
+  WO_OK = 0,
+  WO_ERR_ARG = 1,              /* null or misaligned pointer, bad count or flag */
+  WO_ERR_SHAPE = 2,            /* inconsistent shape (odd X, tile grid mismatch) */
+  WO_ERR_UNSUPPORTED_SIZE = 3, /* an FFT length outside the supported set */
+  WO_ERR_UNDERSAMPLED = 4,     /* optics alias on this grid (see wo_build_tf) */
+  WO_ERR_CUDA = 5,             /* a CUDA launch or runtime call failed */
+  WO_ERR_TIMEOUT = 6,          /* a bounded device-side wait expired */
+  WO_ERR_OPTICS = 7,           /* physically invalid optics (e.g. NA_det >= n) */
+  WO_ERR_WORKSPACE = 8         /* workspace smaller than wo_workspace_bytes() */
+} wo_status;
+
+/* Per-tile optical parameters theta (Fig. 2a(ii); Ext. Data Fig. 3a-b).
+ * Lengths in micrometres; NA and tilts in NA units (n * sin(angle)). */
+typedef struct {
+  double lambda_um;   /* vacuum wavelength */
+  double n_medium;    /* refractive index of the medium */
+  double pixel_um;    /* sample-plane pixel size (x and y) */
+  double z_step_um;   /* distance between stack planes */
+  double na_det;      /* detection NA, 0 < na_det < n_medium */
+  double na_ill;      /* illumination NA, >= 0 (0: a single source point) */
+  double tilt_x;      /* illumination tilt (pupil centre) along x */
+  double tilt_y;      /* illumination tilt (pupil centre) along y */
+  double defocus_um;  /* focal offset z_offset added to every plane */
+} wo_optics;
+
+enum { WO_TF_PHASE = 1, WO_TF_ABSORPTION = 2, WO_TF_FLUOR = 4 };
+enum { WO_MODE_3D = 0, WO_MODE_2D = 1 };
+enum { WO_ETA_RELATIVE = 0, WO_ETA_ABSOLUTE = 1 };
+
+/* 1 if n is a supported FFT length, else 0. */
+int wo_size_supported(int n);
+
+/* Bytes of a transfer-function bank for these arguments: the half spectra
+ * [n_tiles][n_kinds][Z][Y][X/2+1] complex64, followed by a per-tile float
+ * statistics block [n_tiles][8] that wo_build_tf fills (maxima of sum|H|^2
+ * used by the relative regulariser). 0 on invalid arguments. */
+size_t wo_tf_bytes(int n_tiles, int Z, int Y, int X, unsigned kinds);
+
+/* Workspace bytes that suffice for every entry point with these arguments.
+ * 0 on invalid arguments. */
+size_t wo_workspace_bytes(int n_tiles, int Z, int Y, int X, unsigned kinds);
+
+/* Rows a1-a4.  Build the scalar 3D weak-object transfer functions of every
+ * tile from its optics (Table 1, scalar column; Methods "Summary of transfer
+ * functions"):
+ *   S  = 1[|nu - t/lambda| <= NA_ill/lambda],  P = 1[|nu| <= NA_det/lambda]
+ *   A_j = S P e^{i2pi eta z_j},  B_j = P (i/eta) e^{i2pi eta z_j},
+ *   eta = sqrt((n/lambda)^2 - |nu|^2)
+ *   H1_j(q) = c sum_nu A_j*(nu) B_j(nu+q) / sum S P^2,  c = 2 pi n dz / lambda^2
+ *   [H_re_j; H_im_j] = [[1, 1], [i, -i]] [H1_j(q); H1_j(-q)*]
+ *   H_fl_j(q) = sum_nu P_j*(nu) P_j(nu+q),  P_j = P e^{i2pi eta z_j}
+ * then a DFT over j gives the 3D TFs; H_fl is scaled to H_fl(0) = 1.
+ * h_optics: n_tiles host structs.  d_tf: wo_tf_bytes() bytes (output).
+ * Returns WO_ERR_OPTICS if a tile has NA_det >= n, NA_ill + |t| > n or a
+ * non-positive length; WO_ERR_UNDERSAMPLED if
+ * (NA_det + NA_ill + |t|)/lambda >= 1/(2 pixel) (the pupil correlation would
+ * alias) or (n/lambda)(1 - sqrt(1 - (NA_det/n)^2)) >= 1/(2 z_step). */
+wo_status wo_build_tf(const wo_optics *h_optics, int n_tiles, int Z, int Y, int X,
+                      unsigned kinds, void *d_tf, void *d_ws, size_t ws_bytes,
+                      wo_stream stream);
+
+/* Row a5.  Forward model (Eq. fwd, Eq. fwd_block, Fourier form):
+ *   d_c = IFFT3( sum_p H_cp FFT3(f_p) ) + b_c
+ * d_f: [n_tiles][P][Z][Y][X] properties (input); d_data: [n_tiles][C][Z][Y][X]
+ * (output).  h_background: C host floats (NULL: zero). */
+wo_status wo_forward(const void *d_tf, unsigned kinds, const float *d_f,
+                     const float *h_background, float *d_data, int n_tiles,
+                     int Z, int Y, int X, void *d_ws, size_t ws_bytes,
+                     wo_stream stream);
+
+/* Row a6.  Adjoint of the forward model's linear part:
+ *   f_p = IFFT3( sum_c conj(H_cp) FFT3(d_c - b_c) )
+ * d_data: [n_tiles][C][Z][Y][X] (input); d_f: [n_tiles][P][Z][Y][X] (output).
+ * h_background: C host floats (NULL: zero). */
+wo_status wo_forward_adjoint(const void *d_tf, unsigned kinds, const float *d_data,
+                             const float *h_background, float *d_f, int n_tiles,
+                             int Z, int Y, int X, void *d_ws, size_t ws_bytes,
+                             wo_stream stream);
+
+/* Row a7.  Tikhonov reconstruction per contrast mode (Eq. recon; its
+ * one-step solution Eq. tls_solution): per frequency
+ *   F = (H^H H + eta_abs I)^-1 H^H D~,   D~_c(0) = D_c(0) - N b_c
+ * computed in the equivalent form H^H (H H^H + eta_abs I)^-1 D~.
+ * h_eta: one value per contrast mode present (label-free first, then
+ * fluorescence).  eta_flag WO_ETA_RELATIVE: eta_abs = eta * max_nu
+ * sum_{c,p}|H_cp|^2 of that mode and tile; WO_ETA_ABSOLUTE: eta_abs = eta.
+ * h_background: C host floats, or NULL for the per-channel mean (the
+ * reconstruction then has zero mean).
+ * mode WO_MODE_3D: d_f is [n_tiles][P][Z][Y][X].
+ * mode WO_MODE_2D (phase from defocus; Methods "Cell-scale optical pooled
+ * screen data"): a thin object at the reference plane, every plane of the
+ * stack one channel of a per-transverse-frequency solve; d_f is
+ * [n_tiles][P][Y][X] and eta_abs uses max_nu_perp sum_j sum_{c,p} |H_cp,j|^2. */
+wo_status wo_reconstruct(const void *d_tf, unsigned kinds, const float *d_data,
+                         const float *h_background, const float *h_eta,
+                         int eta_flag, int mode, float *d_f, int n_tiles, int Z,
+                         int Y, int X, void *d_ws, size_t ws_bytes, wo_stream stream);
+
+/* Row a8 (gather).  Cut a field [Z][tiles_y*core][tiles_x*core] into
+ * overlapping tiles [tiles_y*tiles_x][Z][E][E], E = core + 2*halo, tile
+ * (ty, tx) starting at field pixel (ty*core - halo, tx*core - halo); pixels
+ * outside the field are mirror-padded (-i, 2(n-1)-i).  Requires
+ * 0 <= halo, 2*halo <= core (Fig. 2a(i); Methods "Organelle-scale ..."). */
+wo_status wo_tile_gather(const float *d_field, int Z, int tiles_y, int tiles_x,
+                         int core, int halo, float *d_tiles, wo_stream stream);
+
+/* Row a8 (blend).  Stitch tiles back: field = sum_t w_t tile_t / sum_t w_t
+ * with separable linear-ramp weights w(u) = min(1, (u+1/2)/(2 halo),
+ * (E-u-1/2)/(2 halo)) per axis (linearly weighted distance-to-edge blending). */
+wo_status wo_tile_blend(const float *d_tiles, int Z, int tiles_y, int tiles_x,
+                        int core, int halo, float *d_field, wo_stream stream);
+
+/* Human-readable name of a status. */
+const char *wo_status_string(wo_status status);
+
+/* Instrumentation (no counterpart in the paper).  When enabled, every kernel
+ * launch is bracketed by CUDA events on its stream and counted per kernel
+ * family.  wo_profile_read waits for the recorded events, then fills up to
+ * `cap` entries of names (static strings), launch counts and total
+ * milliseconds, and returns the number of families; it resets the record. */
+void wo_profile_enable(int on);
+int wo_profile_read(const char **names, long long *launches, double *ms, int cap);
+
+/* Total kernel launches queued by this library since load. */
+long long wo_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WO_H */

@@ -252,6 +252,35 @@ def tf_at(o: dict, shape, kind: str, k3) -> complex:
     return complex(np.sum(Hj * np.exp(-2j * np.pi * kz * j / Z)))
 
 
+def tf_samples(o: dict, shape, kind: str, ks) -> np.ndarray:
+    """3D TF values at several integer frequencies, from the definition.
+
+    Same sums as ``tf_at`` (direct per-plane correlations, then the DFT over
+    planes) with the arms computed once; O(Z Y X) per frequency.
+    """
+    Z, Y, X = shape
+    j = np.arange(Z)
+    out = np.zeros(len(ks), dtype=np.complex128)
+    if kind == "fluor":
+        Pj = fluor_arm(o, shape)
+        norm = Z * np.sum(detection_pupil(o, Y, X) ** 2)
+        for i, (kz, ky, kx) in enumerate(ks):
+            Hj = correlate_direct(Pj, Pj, int(ky), int(kx)) / norm
+            out[i] = np.sum(Hj * np.exp(-2j * np.pi * int(kz) * j / Z))
+        return out
+    A, B = arms(o, shape)
+    S = source_pupil(o, Y, X)
+    P = detection_pupil(o, Y, X)
+    c = labelfree_prefactor(o) / np.sum(S * P * P)
+    row = 0 if kind == "phase" else 1
+    for i, (kz, ky, kx) in enumerate(ks):
+        H1 = c * correlate_direct(A, B, int(ky), int(kx))
+        H2 = np.conj(c * correlate_direct(A, B, -int(ky), -int(kx)))
+        Hj = TABLE1_LABELFREE[row, 0] * H1 + TABLE1_LABELFREE[row, 1] * H2
+        out[i] = np.sum(Hj * np.exp(-2j * np.pi * int(kz) * j / Z))
+    return out
+
+
 def half_spectrum(H: np.ndarray) -> np.ndarray:
     """The non-redundant half (last axis 0..X/2) of a Hermitian spectrum."""
     return H[..., : H.shape[-1] // 2 + 1]

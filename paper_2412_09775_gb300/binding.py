@@ -1,0 +1,222 @@
+"""ctypes binding of the C ABI in include/wo.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method: it converts torch tensors to device pointers and
+the current torch stream to a cudaStream_t, calls the library, and raises
+``WoError`` on a non-zero status.  The library is loaded from the in-tree
+build (``paper_2412_09775_gb300/lib/libwo_gb300.so``); if it is missing the
+import of this module fails loudly - there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libwo_gb300.so")
+
+WO_TF_PHASE, WO_TF_ABSORPTION, WO_TF_FLUOR = 1, 2, 4
+WO_MODE_3D, WO_MODE_2D = 0, 1
+WO_ETA_RELATIVE, WO_ETA_ABSOLUTE = 0, 1
+KIND_BITS = {"phase": WO_TF_PHASE, "absorption": WO_TF_ABSORPTION, "fluor": WO_TF_FLUOR}
+STATUS = {0: "WO_OK", 1: "WO_ERR_ARG", 2: "WO_ERR_SHAPE", 3: "WO_ERR_UNSUPPORTED_SIZE",
+          4: "WO_ERR_UNDERSAMPLED", 5: "WO_ERR_CUDA", 6: "WO_ERR_TIMEOUT", 7: "WO_ERR_OPTICS",
+          8: "WO_ERR_WORKSPACE"}
+
+OPTICS_FIELDS = ("lambda_um", "n_medium", "pixel_um", "z_step_um", "na_det", "na_ill",
+                 "tilt_x", "tilt_y", "defocus_um")
+
+
+class wo_optics(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in OPTICS_FIELDS]
+
+
+class WoError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({_string(status)})")
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run paper_2412_09775_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i, u, sz, f = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint, ctypes.c_size_t, ctypes.c_float
+    fp = ctypes.POINTER(ctypes.c_float)
+    sig = {
+        "wo_size_supported": (i, [i]),
+        "wo_tf_bytes": (sz, [i, i, i, i, u]),
+        "wo_workspace_bytes": (sz, [i, i, i, i, u]),
+        "wo_build_tf": (i, [ctypes.POINTER(wo_optics), i, i, i, i, u, vp, vp, sz, vp]),
+        "wo_forward": (i, [vp, u, vp, fp, vp, i, i, i, i, vp, sz, vp]),
+        "wo_forward_adjoint": (i, [vp, u, vp, fp, vp, i, i, i, i, vp, sz, vp]),
+        "wo_reconstruct": (i, [vp, u, vp, fp, fp, i, i, vp, i, i, i, i, vp, sz, vp]),
+        "wo_tile_gather": (i, [vp, i, i, i, i, i, vp, vp]),
+        "wo_tile_blend": (i, [vp, i, i, i, i, i, vp, vp]),
+        "wo_status_string": (ctypes.c_char_p, [i]),
+        "wo_profile_enable": (None, [i]),
+        "wo_profile_read": (i, [ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong),
+                                ctypes.POINTER(ctypes.c_double), i]),
+        "wo_launch_count": (ctypes.c_longlong, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+EXPORTED = ("wo_size_supported", "wo_tf_bytes", "wo_workspace_bytes", "wo_build_tf", "wo_forward",
+            "wo_forward_adjoint", "wo_reconstruct", "wo_tile_gather", "wo_tile_blend",
+            "wo_status_string", "wo_profile_enable", "wo_profile_read", "wo_launch_count")
+
+
+def _string(status: int) -> str:
+    return _lib.wo_status_string(int(status)).decode()
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise WoError(status, where)
+
+
+def _ptr(x):
+    """Device pointer of a tensor (or an int address); None -> NULL."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _nbytes(x) -> int:
+    return x.numel() * x.element_size()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+def _floats(vals):
+    if vals is None:
+        return None
+    arr = (ctypes.c_float * len(vals))(*[float(v) for v in vals])
+    return ctypes.cast(arr, ctypes.POINTER(ctypes.c_float)), arr
+
+
+def kinds_mask(kinds) -> int:
+    if isinstance(kinds, int):
+        return kinds
+    m = 0
+    for k in kinds:
+        m |= KIND_BITS[k]
+    return m
+
+
+def optics_array(optics_list):
+    arr = (wo_optics * len(optics_list))()
+    for i, o in enumerate(optics_list):
+        for k in OPTICS_FIELDS:
+            setattr(arr[i], k, float(o[k]))
+    return arr
+
+
+# ------------------------------------------------------------- entry points
+def wo_size_supported(n: int) -> bool:
+    return bool(_lib.wo_size_supported(int(n)))
+
+
+def wo_tf_bytes(n_tiles, Z, Y, X, kinds) -> int:
+    return int(_lib.wo_tf_bytes(n_tiles, Z, Y, X, kinds_mask(kinds)))
+
+
+def wo_workspace_bytes(n_tiles, Z, Y, X, kinds) -> int:
+    return int(_lib.wo_workspace_bytes(n_tiles, Z, Y, X, kinds_mask(kinds)))
+
+
+def wo_build_tf(optics_list, n_tiles, Z, Y, X, kinds, tf, ws, stream=None):
+    arr = optics_array(optics_list)
+    if len(optics_list) != n_tiles:
+        raise ValueError("one optics entry per tile")
+    _check(_lib.wo_build_tf(arr, n_tiles, Z, Y, X, kinds_mask(kinds), _ptr(tf), _ptr(ws),
+                            _nbytes(ws), _stream(stream)), "wo_build_tf")
+
+
+def wo_forward(tf, kinds, f, background, data, n_tiles, Z, Y, X, ws, stream=None):
+    bg = _floats(background)
+    _check(_lib.wo_forward(_ptr(tf), kinds_mask(kinds), _ptr(f), bg[0] if bg else None, _ptr(data),
+                           n_tiles, Z, Y, X, _ptr(ws), _nbytes(ws), _stream(stream)), "wo_forward")
+
+
+def wo_forward_adjoint(tf, kinds, data, background, f, n_tiles, Z, Y, X, ws, stream=None):
+    bg = _floats(background)
+    _check(_lib.wo_forward_adjoint(_ptr(tf), kinds_mask(kinds), _ptr(data), bg[0] if bg else None,
+                                   _ptr(f), n_tiles, Z, Y, X, _ptr(ws), _nbytes(ws), _stream(stream)),
+           "wo_forward_adjoint")
+
+
+def wo_reconstruct(tf, kinds, data, background, eta, eta_flag, mode, f, n_tiles, Z, Y, X, ws, stream=None):
+    bg = _floats(background)
+    et = _floats(eta if isinstance(eta, (list, tuple)) else [eta])
+    _check(_lib.wo_reconstruct(_ptr(tf), kinds_mask(kinds), _ptr(data), bg[0] if bg else None, et[0],
+                               int(eta_flag), int(mode), _ptr(f), n_tiles, Z, Y, X, _ptr(ws), _nbytes(ws),
+                               _stream(stream)), "wo_reconstruct")
+
+
+def wo_tile_gather(field, Z, tiles_y, tiles_x, core, halo, tiles, stream=None):
+    _check(_lib.wo_tile_gather(_ptr(field), Z, tiles_y, tiles_x, core, halo, _ptr(tiles), _stream(stream)),
+           "wo_tile_gather")
+
+
+def wo_tile_blend(tiles, Z, tiles_y, tiles_x, core, halo, field, stream=None):
+    _check(_lib.wo_tile_blend(_ptr(tiles), Z, tiles_y, tiles_x, core, halo, _ptr(field), _stream(stream)),
+           "wo_tile_blend")
+
+
+def wo_status_string(status: int) -> str:
+    return _string(status)
+
+
+def wo_profile_enable(on: bool):
+    _lib.wo_profile_enable(1 if on else 0)
+
+
+def wo_profile_read(cap: int = 64) -> dict:
+    names = (ctypes.c_char_p * cap)()
+    cnt = (ctypes.c_longlong * cap)()
+    ms = (ctypes.c_double * cap)()
+    n = _lib.wo_profile_read(names, cnt, ms, cap)
+    return {names[i].decode(): (int(cnt[i]), float(ms[i])) for i in range(min(n, cap))}
+
+
+def wo_launch_count() -> int:
+    return int(_lib.wo_launch_count())
+
+
+# ------------------------------------------------------------- views
+def tf_views(tf, n_tiles, Z, Y, X, kinds):
+    """(spectra, stats) views of a TF bank tensor: complex64 [n][k][Z][Y][X/2+1], float32 [n][8]."""
+    import torch
+    nk = bin(kinds_mask(kinds)).count("1")
+    Xh = X // 2 + 1
+    n_spec = n_tiles * nk * Z * Y * Xh
+    raw = tf.view(torch.uint8)
+    spec = raw[: n_spec * 8].view(torch.complex64).view(n_tiles, nk, Z, Y, Xh)
+    off = ((n_spec * 8 + 255) // 256) * 256
+    stats = raw[off: off + n_tiles * 32].view(torch.float32).view(n_tiles, 8)
+    return spec, stats
+
+
+def alloc(n_tiles, Z, Y, X, kinds, device="cuda"):
+    """Allocate a TF bank and a workspace (torch uint8 tensors) for these shapes."""
+    import torch
+    tfb = wo_tf_bytes(n_tiles, Z, Y, X, kinds)
+    wsb = wo_workspace_bytes(n_tiles, Z, Y, X, kinds)
+    if tfb == 0 or wsb == 0:
+        raise ValueError("invalid shape or kinds")
+    return (torch.empty(tfb, dtype=torch.uint8, device=device),
+            torch.empty(wsb, dtype=torch.uint8, device=device))

@@ -1,0 +1,409 @@
+// wo_api.cu - the C ABI declared in include/wo.h: argument validation,
+// workspace layout and the sequence of kernel passes for each entry point.
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "wo_internal.h"
+
+namespace wo {
+
+// ------------------------------------------------------------ profiling
+namespace {
+struct Pending {
+  const char* name;
+  cudaEvent_t a, b;
+};
+std::mutex g_mu;
+bool g_prof = false;
+std::vector<Pending> g_pending;
+std::vector<cudaEvent_t> g_pool;
+std::atomic<long long> g_launches{0};
+
+cudaEvent_t take_event() {
+  if (!g_pool.empty()) {
+    cudaEvent_t e = g_pool.back();
+    g_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+}  // namespace
+
+void prof_begin(const char* name, cudaStream_t s, int* token) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  *token = -1;
+  if (!g_prof) return;
+  std::lock_guard<std::mutex> lk(g_mu);
+  Pending p{name, take_event(), take_event()};
+  if (!p.a || !p.b) return;
+  cudaEventRecord(p.a, s);
+  g_pending.push_back(p);
+  *token = (int)g_pending.size() - 1;
+}
+
+void prof_end(int token, cudaStream_t s) {
+  if (token < 0) return;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (token < (int)g_pending.size()) cudaEventRecord(g_pending[token].b, s);
+}
+
+// ------------------------------------------------------------ sizes
+static bool size_ok(int n) {
+  if (n < 1 || n > 2048) return false;
+  int m = n;
+  if (m % 3 == 0) m /= 3;
+  return (m & (m - 1)) == 0;
+}
+
+struct Sys {
+  int n_kinds, lf_props, has_fl, C, P, n_arms;
+  int want_phase, want_abs;
+};
+
+static Sys system_of(unsigned kinds) {
+  Sys s{};
+  s.want_phase = (kinds & WO_TF_PHASE) ? 1 : 0;
+  s.want_abs = (kinds & WO_TF_ABSORPTION) ? 1 : 0;
+  s.has_fl = (kinds & WO_TF_FLUOR) ? 1 : 0;
+  s.lf_props = s.want_phase + s.want_abs;
+  s.n_kinds = s.lf_props + s.has_fl;
+  s.C = (s.lf_props ? 1 : 0) + s.has_fl;
+  s.P = s.n_kinds;
+  s.n_arms = (s.lf_props ? 2 : 0) + s.has_fl;
+  return s;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+  size_t optics, counts, rec, arms, build_end;
+  size_t specA, specB, op_end;
+  size_t total;
+  size_t tf_spectra, tf_stats, tf_total;
+};
+
+static Layout layout_of(int n, int Z, int Y, int X, const Sys& s) {
+  Layout L{};
+  const size_t Xh = (size_t)X / 2 + 1;
+  size_t off = 0;
+  L.optics = off; off += align256((size_t)n * sizeof(wo_optics));
+  L.counts = off; off += align256((size_t)n * 2 * sizeof(int));
+  L.rec = off; off += align256((size_t)n * Y * X * sizeof(float4));
+  L.arms = off; off += align256((size_t)n * s.n_arms * Z * Y * X * sizeof(float2));
+  L.build_end = off;
+  const size_t vols = (size_t)(s.C > s.P ? s.C : s.P);
+  const size_t spec = align256((size_t)n * vols * Z * Y * Xh * sizeof(float2));
+  L.specA = 0;
+  L.specB = spec;
+  L.op_end = 2 * spec;
+  L.total = L.build_end > L.op_end ? L.build_end : L.op_end;
+  L.tf_spectra = align256((size_t)n * s.n_kinds * Z * Y * Xh * sizeof(float2));
+  L.tf_stats = L.tf_spectra;
+  L.tf_total = L.tf_spectra + (size_t)n * 8 * sizeof(float);
+  return L;
+}
+
+static bool aligned16(const void* p) { return p && (((uintptr_t)p) & 15u) == 0; }
+
+static size_t zfused_smem(int Z, int n_vols) {
+  const int B = (Z <= 256) ? 16 : (Z <= 512) ? 8 : (Z <= 1024) ? 4 : 2;
+  return ((size_t)Z + (size_t)n_vols * Z * B) * sizeof(float2) + 512 * 11 * sizeof(float);
+}
+
+static size_t tfz_smem(int Z, int n_kinds) {
+  const int B = (Z <= 512) ? 16 : 8;
+  return ((size_t)Z + (size_t)n_kinds * Z * B) * sizeof(float2) + 512 * 2 * sizeof(float);
+}
+
+static wo_status check_shape(int n_tiles, int Z, int Y, int X, unsigned kinds) {
+  if (n_tiles < 1 || n_tiles > 65535) return WO_ERR_ARG;
+  if (kinds == 0 || (kinds & ~7u)) return WO_ERR_ARG;
+  if (Z < 1 || Y < 1 || X < 2) return WO_ERR_SHAPE;
+  if (X % 2) return WO_ERR_SHAPE;
+  if (!size_ok(Z) || !size_ok(Y) || !size_ok(X / 2) || X > 2048) return WO_ERR_UNSUPPORTED_SIZE;
+  const Sys s = system_of(kinds);
+  if (zfused_smem(Z, s.C + s.P) > 227 * 1024) return WO_ERR_UNSUPPORTED_SIZE;
+  if (tfz_smem(Z, s.n_kinds) > 227 * 1024) return WO_ERR_UNSUPPORTED_SIZE;
+  return WO_OK;
+}
+
+static wo_status check_optics(const wo_optics& o) {
+  const double v[9] = {o.lambda_um, o.n_medium, o.pixel_um, o.z_step_um, o.na_det,
+                       o.na_ill, o.tilt_x, o.tilt_y, o.defocus_um};
+  for (double x : v)
+    if (!isfinite(x)) return WO_ERR_OPTICS;
+  if (o.lambda_um <= 0 || o.n_medium <= 0 || o.pixel_um <= 0 || o.z_step_um <= 0) return WO_ERR_OPTICS;
+  if (o.na_det <= 0 || o.na_det >= o.n_medium) return WO_ERR_OPTICS;
+  const double tilt = sqrt(o.tilt_x * o.tilt_x + o.tilt_y * o.tilt_y);
+  if (o.na_ill < 0 || o.na_ill + tilt > o.n_medium) return WO_ERR_OPTICS;
+  // the pupil correlation must not alias on the transverse grid
+  if ((o.na_det + o.na_ill + tilt) / o.lambda_um >= 1.0 / (2.0 * o.pixel_um)) return WO_ERR_UNDERSAMPLED;
+  // the axial band of the TFs must fit the z sampling
+  const double s = o.na_det / o.n_medium;
+  if ((o.n_medium / o.lambda_um) * (1.0 - sqrt(1.0 - s * s)) >= 1.0 / (2.0 * o.z_step_um))
+    return WO_ERR_UNDERSAMPLED;
+  return WO_OK;
+}
+
+static wo_status cuda_status(cudaError_t e) { return e == cudaSuccess ? WO_OK : WO_ERR_CUDA; }
+
+#define WO_TRY(expr)                          \
+  do {                                        \
+    cudaError_t _e = (expr);                  \
+    if (_e != cudaSuccess) return WO_ERR_CUDA; \
+  } while (0)
+
+}  // namespace wo
+
+using namespace wo;
+
+extern "C" {
+
+int wo_size_supported(int n) { return size_ok(n) ? 1 : 0; }
+
+size_t wo_tf_bytes(int n_tiles, int Z, int Y, int X, unsigned kinds) {
+  if (check_shape(n_tiles, Z, Y, X, kinds) != WO_OK) return 0;
+  return layout_of(n_tiles, Z, Y, X, system_of(kinds)).tf_total;
+}
+
+size_t wo_workspace_bytes(int n_tiles, int Z, int Y, int X, unsigned kinds) {
+  if (check_shape(n_tiles, Z, Y, X, kinds) != WO_OK) return 0;
+  return layout_of(n_tiles, Z, Y, X, system_of(kinds)).total;
+}
+
+const char* wo_status_string(wo_status st) {
+  switch (st) {
+    case WO_OK: return "ok";
+    case WO_ERR_ARG: return "invalid argument (null or misaligned pointer, bad count or flag)";
+    case WO_ERR_SHAPE: return "inconsistent shape";
+    case WO_ERR_UNSUPPORTED_SIZE: return "unsupported transform length";
+    case WO_ERR_UNDERSAMPLED: return "optics undersampled on this grid";
+    case WO_ERR_CUDA: return "CUDA error";
+    case WO_ERR_TIMEOUT: return "device-side wait timed out";
+    case WO_ERR_OPTICS: return "physically invalid optics";
+    case WO_ERR_WORKSPACE: return "workspace too small";
+  }
+  return "unknown status";
+}
+
+void wo_profile_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_prof = on != 0;
+}
+
+int wo_profile_read(const char** names, long long* launches, double* ms, int cap) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  std::vector<const char*> nm;
+  std::vector<long long> cnt;
+  std::vector<double> tot;
+  for (const Pending& p : g_pending) {
+    float t = 0.f;
+    if (cudaEventSynchronize(p.b) == cudaSuccess) cudaEventElapsedTime(&t, p.a, p.b);
+    size_t i = 0;
+    for (; i < nm.size(); ++i)
+      if (strcmp(nm[i], p.name) == 0) break;
+    if (i == nm.size()) {
+      nm.push_back(p.name);
+      cnt.push_back(0);
+      tot.push_back(0.0);
+    }
+    cnt[i] += 1;
+    tot[i] += t;
+    g_pool.push_back(p.a);
+    g_pool.push_back(p.b);
+  }
+  g_pending.clear();
+  const int n = (int)nm.size();
+  for (int i = 0; i < n && i < cap; ++i) {
+    if (names) names[i] = nm[i];
+    if (launches) launches[i] = cnt[i];
+    if (ms) ms[i] = tot[i];
+  }
+  return n;
+}
+
+long long wo_launch_count(void) { return g_launches.load(); }
+
+wo_status wo_build_tf(const wo_optics* h_optics, int n_tiles, int Z, int Y, int X, unsigned kinds,
+                      void* d_tf, void* d_ws, size_t ws_bytes, wo_stream stream) {
+  wo_status st = check_shape(n_tiles, Z, Y, X, kinds);
+  if (st != WO_OK) return st;
+  if (!h_optics || !aligned16(d_tf) || !aligned16(d_ws)) return WO_ERR_ARG;
+  for (int t = 0; t < n_tiles; ++t) {
+    st = check_optics(h_optics[t]);
+    if (st != WO_OK) return st;
+  }
+  const Sys s = system_of(kinds);
+  const Layout L = layout_of(n_tiles, Z, Y, X, s);
+  if (ws_bytes < L.total) return WO_ERR_WORKSPACE;
+  cudaStream_t cs = (cudaStream_t)stream;
+  char* ws = (char*)d_ws;
+  char* tfb = (char*)d_tf;
+  TfArgs a{};
+  a.optics = (const wo_optics*)(ws + L.optics);
+  a.counts = (int*)(ws + L.counts);
+  a.rec = (float4*)(ws + L.rec);
+  a.arms = (float2*)(ws + L.arms);
+  a.tf = (float2*)tfb;
+  a.stats = (float*)(tfb + L.tf_stats);
+  a.n_tiles = n_tiles; a.Z = Z; a.Y = Y; a.X = X;
+  a.lf_props = s.lf_props;
+  a.want_phase = s.want_phase; a.want_abs = s.want_abs; a.want_fl = s.has_fl;
+  a.n_arms = s.n_arms; a.n_kinds = s.n_kinds;
+  WO_TRY(cudaMemcpyAsync((void*)a.optics, h_optics, (size_t)n_tiles * sizeof(wo_optics),
+                         cudaMemcpyHostToDevice, cs));
+  WO_TRY(cudaMemsetAsync(a.counts, 0, (size_t)n_tiles * 2 * sizeof(int), cs));
+  WO_TRY(cudaMemsetAsync(a.stats, 0, (size_t)n_tiles * 8 * sizeof(float), cs));
+  WO_TRY(tf_pupil_record(a, cs));
+  WO_TRY(tf_arms(a, cs));
+  WO_TRY(tf_psf_rows(a, cs));
+  const int Xh = X / 2 + 1;
+  WO_TRY(cols_c2c(Y, false, a.tf, Xh, (long long)Y * Xh, Xh, (long long)n_tiles * s.n_kinds * Z, cs,
+                  "tf_ypass"));
+  WO_TRY(tf_zpass(a, cs));
+  return WO_OK;
+}
+
+// forward (op 0), adjoint (op 1), reconstruct (op 2)
+static wo_status run_op(int op, const void* d_tf, unsigned kinds, const float* d_in, const float* h_bg,
+                        const float* h_eta, int eta_flag, int mode, float* d_out, int n_tiles, int Z,
+                        int Y, int X, void* d_ws, size_t ws_bytes, wo_stream stream) {
+  wo_status st = check_shape(n_tiles, Z, Y, X, kinds);
+  if (st != WO_OK) return st;
+  if (!aligned16(d_tf) || !aligned16(d_in) || !aligned16(d_out) || !aligned16(d_ws)) return WO_ERR_ARG;
+  const Sys s = system_of(kinds);
+  if (op == 2) {
+    if (!h_eta) return WO_ERR_ARG;
+    if (eta_flag != WO_ETA_RELATIVE && eta_flag != WO_ETA_ABSOLUTE) return WO_ERR_ARG;
+    if (mode != WO_MODE_3D && mode != WO_MODE_2D) return WO_ERR_ARG;
+    const int n_modes = (s.lf_props ? 1 : 0) + s.has_fl;
+    for (int m = 0; m < n_modes; ++m)
+      if (!(h_eta[m] >= 0.f) || !isfinite(h_eta[m])) return WO_ERR_ARG;
+  }
+  if (h_bg) {
+    for (int c = 0; c < s.C; ++c)
+      if (!isfinite(h_bg[c])) return WO_ERR_ARG;
+  }
+  const Layout L = layout_of(n_tiles, Z, Y, X, s);
+  if (ws_bytes < L.total) return WO_ERR_WORKSPACE;
+  cudaStream_t cs = (cudaStream_t)stream;
+  char* ws = (char*)d_ws;
+  float2* specA = (float2*)(ws + L.specA);
+  float2* specB = (float2*)(ws + L.specB);
+  const float2* tf = (const float2*)d_tf;
+  const int Xh = X / 2 + 1, H = X / 2;
+  const int n_in = (op == 0) ? s.P : s.C;
+  const int n_out = (op == 0) ? s.C : s.P;
+
+  RowBg bg_in{};
+  bg_in.rows_per_block = (long long)Z * Y;
+  bg_in.nchan = n_in;
+  if (op != 0) {
+    if (h_bg) {
+      bg_in.mode = 1;
+      for (int c = 0; c < s.C; ++c) bg_in.v[c] = h_bg[c];
+    } else if (op == 2) {
+      bg_in.mode = 2;  // any constant only moves the DC bin, which is zeroed
+    }
+  }
+  RowBg bg_out{};
+  bg_out.rows_per_block = (long long)Z * Y;
+  bg_out.nchan = n_out;
+  if (op == 0 && h_bg) {
+    bg_out.mode = 1;
+    for (int c = 0; c < s.C; ++c) bg_out.v[c] = h_bg[c];
+  }
+
+  ZOp zo{};
+  zo.op = op;
+  zo.n_in = n_in;
+  zo.n_out = n_out;
+  zo.n_tf = s.n_kinds;
+  zo.lf_props = s.lf_props;
+  zo.has_fl = s.has_fl;
+  zo.lf_chan = s.lf_props ? 0 : -1;
+  zo.fl_chan = s.has_fl ? (s.lf_props ? 1 : 0) : -1;
+  zo.stats = (const float*)((const char*)d_tf + L.tf_stats);
+  if (op == 2) {
+    int m = 0;
+    if (s.lf_props) zo.eta_lf = h_eta[m++];
+    if (s.has_fl) zo.eta_fl = h_eta[m++];
+    zo.eta_absolute = (eta_flag == WO_ETA_ABSOLUTE);
+    zo.zero_dc = h_bg ? 0 : 1;
+  }
+
+  const long long in_rows = (long long)n_tiles * n_in * Z * Y;
+  WO_TRY(rows_r2c(H, d_in, specA, in_rows, bg_in, cs));
+  WO_TRY(cols_c2c(Y, false, specA, Xh, (long long)Y * Xh, Xh, (long long)n_tiles * n_in * Z, cs, "y_fwd"));
+  if (op == 2 && mode == WO_MODE_2D) {
+    WO_TRY(z_solve2d(Z, specA, specB, tf, zo, n_tiles, Y, Xh, cs));
+    WO_TRY(cols_c2c(Y, true, specB, Xh, (long long)Y * Xh, Xh, (long long)n_tiles * s.P, cs, "y_inv"));
+    const float scale = 2.0f / ((float)X * (float)Y);
+    RowBg none{};
+    none.rows_per_block = Y;
+    none.nchan = 1;
+    WO_TRY(rows_c2r(H, specB, d_out, (long long)n_tiles * s.P * Y, scale, none, cs));
+    return WO_OK;
+  }
+  WO_TRY(z_fused(Z, specA, specB, tf, zo, n_tiles, Y, Xh, cs));
+  WO_TRY(cols_c2c(Y, true, specB, Xh, (long long)Y * Xh, Xh, (long long)n_tiles * n_out * Z, cs, "y_inv"));
+  const float scale = (float)(2.0 / ((double)X * (double)Y * (double)Z));
+  WO_TRY(rows_c2r(H, specB, d_out, (long long)n_tiles * n_out * Z * Y, scale, bg_out, cs));
+  return WO_OK;
+}
+
+wo_status wo_forward(const void* d_tf, unsigned kinds, const float* d_f, const float* h_background,
+                     float* d_data, int n_tiles, int Z, int Y, int X, void* d_ws, size_t ws_bytes,
+                     wo_stream stream) {
+  return run_op(0, d_tf, kinds, d_f, h_background, nullptr, 0, WO_MODE_3D, d_data, n_tiles, Z, Y, X, d_ws,
+                ws_bytes, stream);
+}
+
+wo_status wo_forward_adjoint(const void* d_tf, unsigned kinds, const float* d_data,
+                             const float* h_background, float* d_f, int n_tiles, int Z, int Y, int X,
+                             void* d_ws, size_t ws_bytes, wo_stream stream) {
+  return run_op(1, d_tf, kinds, d_data, h_background, nullptr, 0, WO_MODE_3D, d_f, n_tiles, Z, Y, X, d_ws,
+                ws_bytes, stream);
+}
+
+wo_status wo_reconstruct(const void* d_tf, unsigned kinds, const float* d_data, const float* h_background,
+                         const float* h_eta, int eta_flag, int mode, float* d_f, int n_tiles, int Z, int Y,
+                         int X, void* d_ws, size_t ws_bytes, wo_stream stream) {
+  return run_op(2, d_tf, kinds, d_data, h_background, h_eta, eta_flag, mode, d_f, n_tiles, Z, Y, X, d_ws,
+                ws_bytes, stream);
+}
+
+static wo_status check_tiles(int Z, int tiles_y, int tiles_x, int core, int halo, const void* a,
+                             const void* b) {
+  if (!aligned16(a) || !aligned16(b)) return WO_ERR_ARG;
+  if (Z < 1 || tiles_y < 1 || tiles_x < 1 || core < 1 || halo < 0) return WO_ERR_SHAPE;
+  if (2 * halo > core) return WO_ERR_SHAPE;
+  const long long E = (long long)core + 2LL * halo;
+  if (E > 65535 || (long long)tiles_y * core > 65535 || (long long)tiles_x * core > (1LL << 30) ||
+      (long long)tiles_y * tiles_x * Z > 65535 || Z > 65535)
+    return WO_ERR_SHAPE;
+  return WO_OK;
+}
+
+wo_status wo_tile_gather(const float* d_field, int Z, int tiles_y, int tiles_x, int core, int halo,
+                         float* d_tiles, wo_stream stream) {
+  wo_status st = check_tiles(Z, tiles_y, tiles_x, core, halo, d_field, d_tiles);
+  if (st != WO_OK) return st;
+  return cuda_status(tiles_gather(d_field, Z, tiles_y, tiles_x, core, halo, d_tiles, (cudaStream_t)stream));
+}
+
+wo_status wo_tile_blend(const float* d_tiles, int Z, int tiles_y, int tiles_x, int core, int halo,
+                        float* d_field, wo_stream stream) {
+  wo_status st = check_tiles(Z, tiles_y, tiles_x, core, halo, d_tiles, d_field);
+  if (st != WO_OK) return st;
+  return cuda_status(tiles_blend(d_tiles, Z, tiles_y, tiles_x, core, halo, d_field, (cudaStream_t)stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,75 @@
+// wo_cols.cu - in-place complex transforms along a strided axis (y or z).
+//
+// A CTA owns B adjacent columns of one plane for the whole transform: it
+// reads the N x B tile with coalesced B-wide row segments, runs every
+// Stockham stage in shared memory and writes the tile back to the same place.
+#include "wo_fft.cuh"
+#include "wo_internal.h"
+
+namespace wo {
+
+template <int N, bool INV>
+__global__ void __launch_bounds__(ColGeom<N>::NT, ColGeom<N>::MINB)
+    k_cols(float2* __restrict__ data, long long col_stride, long long plane_stride, int ncols,
+           long long nplanes) {
+  using G = ColGeom<N>;
+  constexpr int B = G::B, NT = G::NT;
+  extern __shared__ float2 sm[];
+  float2* buf = sm;
+  float2* tw = sm + N * B;
+  const long long plane = blockIdx.y + (long long)gridDim.y * blockIdx.z;
+  if (plane >= nplanes) return;  // uniform across the CTA
+  make_twiddles<N>(tw);
+  const int x0 = blockIdx.x * B;
+  const int w = min(B, ncols - x0);
+  float2* base = data + plane * plane_stride + x0;
+  for (int e = threadIdx.x; e < N * B; e += NT) {
+    const int n = e / B, b = e % B;
+    buf[e] = (b < w) ? base[n * col_stride + b] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  fft_smem<N, B, NT, INV, 1>(buf, B, 1, tw);
+  for (int e = threadIdx.x; e < N * B; e += NT) {
+    const int n = e / B, b = e % B;
+    if (b < w) base[n * col_stride + b] = buf[e];
+  }
+}
+
+template <int N>
+static cudaError_t launch_cols(bool inv, float2* data, long long cs, long long ps, int ncols,
+                               long long nplanes, cudaStream_t s, const char* name) {
+  using G = ColGeom<N>;
+  const size_t smem = G::SMEM;
+  static cudaError_t a0 = allow_smem(k_cols<N, false>, smem);
+  static cudaError_t a1 = allow_smem(k_cols<N, true>, smem);
+  if (a0 != cudaSuccess) return a0;
+  if (a1 != cudaSuccess) return a1;
+  const unsigned gx = (unsigned)((ncols + G::B - 1) / G::B);
+  const long long gy = nplanes < 65535 ? nplanes : 65535;
+  const long long gz = (nplanes + gy - 1) / gy;
+  dim3 grid(gx, (unsigned)gy, (unsigned)gz);
+  if (inv) {
+    WO_LAUNCH(name, s, (k_cols<N, true><<<grid, G::NT, smem, s>>>(data, cs, ps, ncols, nplanes)));
+  } else {
+    WO_LAUNCH(name, s, (k_cols<N, false><<<grid, G::NT, smem, s>>>(data, cs, ps, ncols, nplanes)));
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t cols_c2c(int N, bool inverse, float2* data, long long col_stride, long long plane_stride,
+                     int ncols, long long nplanes, cudaStream_t s, const char* name) {
+  if (N == 1 || nplanes <= 0 || ncols <= 0) return cudaSuccess;  // identity
+  switch (N) {
+#define WO_CASE(n) \
+  case n:          \
+    return launch_cols<n>(inverse, data, col_stride, plane_stride, ncols, nplanes, s, name);
+    WO_CASE(2) WO_CASE(3) WO_CASE(4) WO_CASE(6) WO_CASE(8) WO_CASE(12) WO_CASE(16) WO_CASE(24)
+    WO_CASE(32) WO_CASE(48) WO_CASE(64) WO_CASE(96) WO_CASE(128) WO_CASE(192) WO_CASE(256)
+    WO_CASE(384) WO_CASE(512) WO_CASE(768) WO_CASE(1024) WO_CASE(1536) WO_CASE(2048)
+#undef WO_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace wo

@@ -1,0 +1,101 @@
+// wo_internal.h - launchers shared between the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "../../include/wo.h"
+
+namespace wo {
+
+// Instrumentation: counts every launch; with profiling on, brackets it with
+// CUDA events on its stream (see wo_profile_enable).
+void prof_begin(const char* name, cudaStream_t s, int* token);
+void prof_end(int token, cudaStream_t s);
+
+// Background handling of a row pass over volumes laid out
+// [block][Z][Y][X], block = tile * nchan + channel.
+struct RowBg {
+  float v[4];               // per-channel constants (mode 1)
+  long long rows_per_block; // Z*Y
+  int nchan;                // channels per tile
+  int mode;                 // 0: none, 1: add/subtract v[channel], 2: subtract
+                            //    the block's first sample (before R2C only)
+};
+
+// Real rows of length 2N -> half spectra of N+1 bins (row pitch N+1).
+cudaError_t rows_r2c(int N, const float* in, float2* out, long long nrows, RowBg bg,
+                     cudaStream_t s);
+// Half spectra (pitch N+1) -> real rows of length 2N, times `scale`, plus bg.
+cudaError_t rows_c2r(int N, const float2* in, float* out, long long nrows, float scale,
+                     RowBg bg, cudaStream_t s);
+// In-place C2C transforms of length N along a strided axis:
+// element n of column c of plane p at data[p*plane_stride + n*col_stride + c].
+// `name` labels the launch for the profiler.
+cudaError_t cols_c2c(int N, bool inverse, float2* data, long long col_stride,
+                     long long plane_stride, int ncols, long long nplanes, cudaStream_t s,
+                     const char* name);
+
+// Per-frequency operator applied between a forward and an inverse z transform.
+struct ZOp {
+  int op;            // 0 forward, 1 adjoint, 2 reconstruct
+  int n_in, n_out;   // volumes per tile read / written
+  int n_tf;          // TF slots per tile
+  int lf_props;      // label-free properties (TF slots 0..lf_props-1), 0..2
+  int has_fl;        // fluorescence TF at slot lf_props
+  int lf_chan;       // data channel of the label-free mode (or -1)
+  int fl_chan;       // data channel of the fluorescence mode (or -1)
+  float eta_lf, eta_fl;
+  int eta_absolute;
+  int zero_dc;       // reconstruct: zero D(0) (background = channel mean)
+  const float* stats;  // [tile][8] from the TF bank
+};
+// Fused z pass: FFT_z of n_in volumes, per-frequency op, IFFT_z of n_out volumes.
+// Spectra laid out [tile][vol][Z][Y][Xh].
+cudaError_t z_fused(int Z, const float2* in, float2* out, const float2* tf, ZOp op, int n_tiles,
+                    int Y, int Xh, cudaStream_t s);
+// 2D reconstruction: FFT_z, per-transverse-frequency solve summed over k_z.
+// out: [tile][P][Y][Xh].
+cudaError_t z_solve2d(int Z, const float2* in, float2* out, const float2* tf, ZOp op, int n_tiles,
+                      int Y, int Xh, cudaStream_t s);
+
+// Transfer-function build.
+struct TfArgs {
+  const wo_optics* optics;  // device copy, [n_tiles]
+  int* counts;              // [n_tiles][2]: #(S and P), #P
+  float4* rec;              // [n_tiles][Y][X] pupil record
+  float2* arms;             // [n_tiles][n_arms][Z][Y][X]
+  float2* tf;               // [n_tiles][n_kinds][Z][Y][Xh]
+  float* stats;             // [n_tiles][8]
+  int n_tiles, Z, Y, X;
+  int lf_props;             // 0..2 (phase, absorption present -> slots)
+  int want_phase, want_abs, want_fl;
+  int n_arms;               // 2*(lf) + fl
+  int n_kinds;
+};
+cudaError_t tf_pupil_record(const TfArgs& a, cudaStream_t s);
+cudaError_t tf_arms(const TfArgs& a, cudaStream_t s);
+cudaError_t tf_psf_rows(const TfArgs& a, cudaStream_t s);
+cudaError_t tf_zpass(const TfArgs& a, cudaStream_t s);
+
+// Tiles.
+cudaError_t tiles_gather(const float* field, int Z, int ty, int tx, int core, int halo,
+                         float* tiles, cudaStream_t s);
+cudaError_t tiles_blend(const float* tiles, int Z, int ty, int tx, int core, int halo,
+                        float* field, cudaStream_t s);
+
+// Opt a kernel into more than 48 KB of dynamic shared memory (once).
+template <class K>
+inline cudaError_t allow_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace wo
+
+#define WO_LAUNCH(name, stream, ...)        \
+  do {                                      \
+    int _wo_tok = -1;                       \
+    wo::prof_begin(name, stream, &_wo_tok); \
+    __VA_ARGS__;                            \
+    wo::prof_end(_wo_tok, stream);          \
+  } while (0)

@@ -1,0 +1,114 @@
+"""Host-side checks of the C ABI (CPU only; no compute call reaches a GPU).
+
+Every call below is built to fail validation, so nothing is ever launched on
+the placeholder pointers it passes.
+
+The library must load without a GPU, export every symbol include/wo.h
+declares, size its buffers consistently, and reject invalid arguments with
+the documented status before launching anything.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+import phantom as ph
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2412_09775_gb300.build import build
+    build()
+    from paper_2412_09775_gb300 import binding
+    return binding
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "wo.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(wo_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(B):
+    names = header_functions()
+    assert len(names) >= 13
+    for n in names:
+        assert hasattr(B._lib, n), n
+        assert n in B.EXPORTED, n
+
+
+def test_supported_sizes(B):
+    ok = [1, 2, 3, 4, 6, 8, 12, 16, 24, 48, 64, 96, 192, 512, 1536, 2048]
+    bad = [0, 5, 7, 9, 10, 18, 36, 100, 3072, 4096, -4]
+    assert all(B.wo_size_supported(n) for n in ok)
+    assert not any(B.wo_size_supported(n) for n in bad)
+
+
+def test_buffer_sizes(B):
+    n, Z, Y, X = 3, 16, 64, 96
+    Xh = X // 2 + 1
+    for kinds, nk in ((1, 1), (3, 2), (4, 1), (7, 3)):
+        spec = n * nk * Z * Y * Xh * 8
+        assert B.wo_tf_bytes(n, Z, Y, X, kinds) == ((spec + 255) // 256) * 256 + n * 32
+        assert B.wo_workspace_bytes(n, Z, Y, X, kinds) > 0
+    assert B.wo_tf_bytes(1, 16, 64, 63, 1) == 0          # odd X
+    assert B.wo_workspace_bytes(1, 10, 64, 64, 1) == 0   # Z not supported
+    assert B.wo_tf_bytes(1, 16, 64, 64, 0) == 0          # no kinds
+
+
+def test_build_tf_validation(B):
+    lib = B._lib
+    good = B.optics_array([ph.optics()])
+    fake = 1 << 20  # 16-byte aligned non-null address; never dereferenced
+    big = 1 << 40
+    cases = [
+        (B.optics_array([ph.optics(na_det=1.33)]), 1, 16, 64, 64, 1, fake, fake, big, 7),  # NA_det >= n
+        (B.optics_array([ph.optics(na_ill=0.5, tilt_x=1.0)]), 1, 16, 64, 64, 1, fake, fake, big, 7),
+        (B.optics_array([ph.optics(lambda_um=-1.0)]), 1, 16, 64, 64, 1, fake, fake, big, 7),
+        (B.optics_array([ph.optics(pixel_um=0.2)]), 1, 16, 64, 64, 1, fake, fake, big, 4),  # aliasing
+        (B.optics_array([ph.optics(z_step_um=0.4)]), 1, 16, 64, 64, 1, fake, fake, big, 4),  # axial
+        (good, 1, 16, 64, 62, 1, fake, fake, big, 3),   # X/2 = 31
+        (good, 1, 16, 64, 63, 1, fake, fake, big, 2),   # odd X
+        (good, 1, 16, 64, 64, 8, fake, fake, big, 1),   # bad kinds
+        (good, 0, 16, 64, 64, 1, fake, fake, big, 1),   # no tiles
+        (good, 1, 16, 64, 64, 1, fake + 4, fake, big, 1),  # misaligned
+        (good, 1, 16, 64, 64, 1, None, fake, big, 1),   # null
+        (good, 1, 16, 64, 64, 1, fake, fake, 1024, 8),  # workspace too small
+    ]
+    for arr, n, Z, Y, X, kinds, tf, ws, wsb, want in cases:
+        assert lib.wo_build_tf(arr, n, Z, Y, X, kinds, tf, ws, wsb, None) == want
+
+
+def test_op_validation(B):
+    lib = B._lib
+    fake = 1 << 20
+    eta = (ctypes.c_float * 2)(1e-3, 1e-3)
+    neg = (ctypes.c_float * 2)(-1.0, 1e-3)
+    pe = ctypes.cast(eta, ctypes.POINTER(ctypes.c_float))
+    pn = ctypes.cast(neg, ctypes.POINTER(ctypes.c_float))
+    big = 1 << 40
+    assert lib.wo_reconstruct(fake, 7, fake, None, None, 0, 0, fake, 1, 16, 64, 64, fake, big, None) == 1
+    assert lib.wo_reconstruct(fake, 7, fake, None, pn, 0, 0, fake, 1, 16, 64, 64, fake, big, None) == 1
+    assert lib.wo_reconstruct(fake, 7, fake, None, pe, 2, 0, fake, 1, 16, 64, 64, fake, big, None) == 1
+    assert lib.wo_reconstruct(fake, 7, fake, None, pe, 0, 5, fake, 1, 16, 64, 64, fake, big, None) == 1
+    assert lib.wo_reconstruct(fake, 7, fake, None, pe, 0, 0, fake, 1, 16, 64, 64, fake, 16, None) == 8
+    assert lib.wo_forward(fake, 7, fake + 8, None, fake, 1, 16, 64, 64, fake, big, None) == 1
+    assert lib.wo_forward_adjoint(fake, 7, fake, None, fake, 1, 16, 64, 100, fake, big, None) == 3
+
+
+def test_tile_validation(B):
+    lib = B._lib
+    fake = 1 << 20
+    assert lib.wo_tile_gather(fake, 4, 2, 2, 16, 9, fake, None) == 2   # 2*halo > core
+    assert lib.wo_tile_gather(fake, 4, 0, 2, 16, 4, fake, None) == 2
+    assert lib.wo_tile_blend(None, 4, 2, 2, 16, 4, fake, None) == 1
+    assert lib.wo_tile_blend(fake, 4, 2, 2, 16, -1, fake, None) == 2
+
+
+def test_status_strings(B):
+    for s in range(9):
+        assert B.wo_status_string(s)
+    assert B.wo_status_string(99) == "unknown status"

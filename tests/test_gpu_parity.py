@@ -1,0 +1,332 @@
+"""Parity of the CUDA path (through the C ABI) with the float64 oracle.
+
+Both sides take the same seeded inputs; the GPU result must match the oracle
+to a relative L2 error of 1e-4 (the tolerance the workloads fix for float32
+reconstructions), element by element at sizes the oracle handles in seconds,
+and on sampled outputs or the whole transfer-function bank at the widefield
+workload's full size.
+"""
+import numpy as np
+import pytest
+
+import phantom as ph
+from conftest import rel_l2
+from oracle import dft as OD, model as OM, optics as OO, tiles as OT
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+KIND_SETS = [("phase",), ("absorption",), ("fluor",), ("phase", "absorption"), ("phase", "fluor"),
+             ("absorption", "fluor"), ("phase", "absorption", "fluor")]
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2412_09775_gb300.build import build
+    build()
+    from paper_2412_09775_gb300 import binding
+    return binding, torch, torch.device("cuda:0")
+
+
+def gpu_tf(env, optics_list, shape, kinds):
+    B, torch, dev = env
+    Z, Y, X = shape
+    n = len(optics_list)
+    tf, ws = B.alloc(n, Z, Y, X, kinds, dev)
+    B.wo_build_tf(optics_list, n, Z, Y, X, kinds, tf, ws)
+    torch.cuda.synchronize()
+    spec, stats = B.tf_views(tf, n, Z, Y, X, kinds)
+    return tf, ws, spec.cpu().numpy(), stats.cpu().numpy()
+
+
+def oracle_tf(o, shape, kinds):
+    return OO.transfer_functions(o, shape, kinds)
+
+
+def check_tf(env, optics_list, shape, kinds, tol=TOL):
+    tf, ws, spec, stats = gpu_tf(env, optics_list, shape, kinds)
+    for t, o in enumerate(optics_list):
+        ref = oracle_tf(o, shape, kinds)
+        for s, k in enumerate([k for k in OO.KINDS if k in kinds]):
+            e = rel_l2(spec[t, s], OO.half_spectrum(ref[k]))
+            assert e <= tol, (t, k, e)
+        lf = [k for k in ("phase", "absorption") if k in kinds]
+        if lf:
+            tot = sum(np.abs(ref[k]) ** 2 for k in lf)
+            assert abs(stats[t, 0] / tot.max() - 1) <= 1e-5
+            assert abs(stats[t, 1] / np.sum(tot, axis=0).max() - 1) <= 1e-5
+        if "fluor" in kinds:
+            tot = np.abs(ref["fluor"]) ** 2
+            assert abs(stats[t, 2] / tot.max() - 1) <= 1e-5
+            assert abs(stats[t, 3] / np.sum(tot, axis=0).max() - 1) <= 1e-5
+    return tf, ws
+
+
+# ------------------------------------------------------------ TF build
+@pytest.mark.parametrize("kinds", KIND_SETS)
+def test_tf_kinds(env, kinds):
+    check_tf(env, [ph.optics(na_ill=0.8, tilt_x=0.04, tilt_y=-0.02, defocus_um=0.3)], (8, 32, 48), kinds)
+
+
+@pytest.mark.parametrize("shape", [(16, 64, 64), (12, 48, 96), (6, 24, 32), (1, 16, 16), (2, 4, 4),
+                                   (3, 12, 24), (24, 96, 16), (4, 192, 24)])
+def test_tf_shapes(env, shape):
+    check_tf(env, [ph.optics(na_ill=0.6, tilt_y=0.05, defocus_um=-0.4)], shape, OO.KINDS)
+
+
+def test_tf_tiles_each_with_own_optics(env):
+    optics = ph.tile_optics(np.random.default_rng(3), 3)
+    check_tf(env, optics, (8, 32, 32), OO.KINDS)
+
+
+def test_tf_point_source_and_pooled_screen_optics(env):
+    check_tf(env, [ph.optics(na_ill=0.0)], (8, 32, 32), ("phase", "absorption"))
+    check_tf(env, [dict(ph.POOLED_SCREEN_OPTICS, tilt_x=0.03)], (5 + 1, 64, 64), ("phase",))
+
+
+def test_tf_largest_lengths(env):
+    check_tf(env, [ph.optics(na_ill=0.5)], (2, 8, 2048), ("phase", "fluor"))
+    check_tf(env, [ph.optics(na_ill=0.5)], (2, 2048, 8), ("absorption",))
+    check_tf(env, [ph.optics(na_ill=0.5)], (2048, 4, 4), ("phase",))
+
+
+# ------------------------------------------------ forward / adjoint
+def run_forward(env, tf, ws, kinds, f, bg, shape, n=1):
+    B, torch, dev = env
+    Z, Y, X = shape
+    nc = (1 if set(kinds) & {"phase", "absorption"} else 0) + (1 if "fluor" in kinds else 0)
+    fd = torch.from_numpy(np.ascontiguousarray(f, dtype=np.float32)).to(dev)
+    dd = torch.empty((n, nc, Z, Y, X), dtype=torch.float32, device=dev)
+    B.wo_forward(tf, kinds, fd, bg, dd, n, Z, Y, X, ws)
+    return dd.cpu().numpy()
+
+
+@pytest.mark.parametrize("kinds", KIND_SETS)
+def test_forward_and_adjoint(env, kinds):
+    B, torch, dev = env
+    shape = (8, 32, 48)
+    o = ph.optics(na_ill=0.7, tilt_x=-0.03, defocus_um=0.15)
+    tf, ws = check_tf(env, [o], shape, kinds)
+    modes, props, chans = OM.widefield_system(oracle_tf(o, shape, kinds), kinds)
+    f = ph.uniform_volume(5, (1, len(props)) + shape, -0.02, 0.02).astype(np.float32)
+    bg = [1.0, 0.3][: len(chans)]
+    d = run_forward(env, tf, ws, kinds, f, bg, shape)[0]
+    ref = OM.forward(modes, f[0].astype(np.float64), bg)
+    b = np.array(bg)[:, None, None, None]
+    assert rel_l2(d - b, ref - b) <= TOL
+    # adjoint on an arbitrary data stack
+    dd = ph.uniform_volume(6, (len(chans),) + shape, 0.5, 1.5).astype(np.float32)
+    Z, Y, X = shape
+    din = torch.from_numpy(dd[None]).to(dev)
+    fo = torch.empty((1, len(props)) + shape, dtype=torch.float32, device=dev)
+    B.wo_forward_adjoint(tf, kinds, din, bg, fo, 1, Z, Y, X, ws)
+    ref = OM.adjoint(modes, dd.astype(np.float64), bg)
+    assert rel_l2(fo.cpu().numpy()[0], ref) <= TOL
+
+
+# ------------------------------------------------------ reconstruct
+def run_recon(env, tf, ws, kinds, d, bg, eta, flag, mode, shape, n=1):
+    B, torch, dev = env
+    Z, Y, X = shape
+    P = len(kinds)
+    din = torch.from_numpy(np.ascontiguousarray(d, dtype=np.float32)).to(dev)
+    out_shape = (n, P) + ((Z, Y, X) if mode == B.WO_MODE_3D else (Y, X))
+    fo = torch.empty(out_shape, dtype=torch.float32, device=dev)
+    B.wo_reconstruct(tf, kinds, din, bg, eta, flag, mode, fo, n, Z, Y, X, ws)
+    return fo.cpu().numpy()
+
+
+def test_reconstruct_small_widefield_stack(env):
+    """16 x 64 x 64 stack of 20 spheres, forward + 1e-3 noise, phase-only Tikhonov with eta = 1e-3."""
+    B = env[0]
+    shape = (16, 64, 64)
+    o = ph.optics()
+    dn = ph.sphere_phantom(1, shape, o)
+    tfs = oracle_tf(o, shape, ("phase",))
+    modes, _, _ = OM.widefield_system(tfs, ("phase",))
+    d = OM.forward(modes, dn[None], [1.0])
+    d = (d + ph.gaussian_noise(101, d.shape, 1e-3 * d.mean())).astype(np.float32)
+    tf, ws = check_tf(env, [o], shape, ("phase",))
+    got = run_recon(env, tf, ws, ("phase",), d[None], None, [1e-3], B.WO_ETA_RELATIVE, B.WO_MODE_3D, shape)
+    ref = OM.reconstruct(modes, d.astype(np.float64), 1e-3)
+    assert rel_l2(got[0], ref) <= TOL
+
+
+@pytest.mark.parametrize("kinds", KIND_SETS)
+@pytest.mark.parametrize("bg,flag", [(None, 0), ("given", 0), ("given", 1)])
+def test_reconstruct_3d(env, kinds, bg, flag):
+    B = env[0]
+    shape = (12, 48, 32)
+    o = ph.optics(na_ill=0.75, tilt_y=0.04, defocus_um=-0.2)
+    tf, ws = check_tf(env, [o], shape, kinds)
+    modes, props, chans = OM.widefield_system(oracle_tf(o, shape, kinds), kinds)
+    d = ph.uniform_volume(9, (len(chans),) + shape, 0.9, 1.1).astype(np.float32)
+    b = [1.0, 0.8][: len(chans)] if bg == "given" else None
+    n_modes = len(modes)
+    eta = [1e-3, 3e-3][:n_modes] if flag == 0 else [0.5, 2e-4][:n_modes]
+    got = run_recon(env, tf, ws, kinds, d[None], b, eta, flag, B.WO_MODE_3D, shape)[0]
+    ref = np.zeros_like(got, dtype=np.float64)
+    for m, e in zip(modes, eta):
+        r = OM.reconstruct([m], d.astype(np.float64), e, background=b, relative=(flag == 0))
+        for p in m["props"]:
+            ref[p] = r[p]
+    for p in range(len(props)):
+        assert rel_l2(got[p], ref[p]) <= TOL, (props[p], rel_l2(got[p], ref[p]))
+
+
+@pytest.mark.parametrize("kinds", [("phase",), ("phase", "absorption"), ("phase", "absorption", "fluor"),
+                                   ("fluor",)])
+@pytest.mark.parametrize("bg,flag", [(None, 0), ("given", 1)])
+def test_reconstruct_2d_phase_from_defocus(env, kinds, bg, flag):
+    B = env[0]
+    shape = (8, 64, 48)
+    o = ph.optics(na_ill=0.5, tilt_x=0.06, defocus_um=0.4)
+    tf, ws = check_tf(env, [o], shape, kinds)
+    plane = OO.plane_tfs(o, shape, kinds)
+    modes, props, chans = OM.widefield_system(plane, kinds)
+    d = ph.uniform_volume(12, (len(chans),) + shape, 0.9, 1.1).astype(np.float32)
+    b = [1.0, 0.8][: len(chans)] if bg == "given" else None
+    eta = [1e-3, 1e-2][: len(modes)] if flag == 0 else [0.3, 1e-3][: len(modes)]
+    got = run_recon(env, tf, ws, kinds, d[None], b, eta, flag, B.WO_MODE_2D, shape)[0]
+    ref = np.zeros(got.shape)
+    for m, e in zip(modes, eta):
+        r = OM.reconstruct_2d([m], d.astype(np.float64), e, background=b, relative=(flag == 0))
+        for p in m["props"]:
+            ref[p] = r[p]
+    for p in range(len(props)):
+        assert rel_l2(got[p], ref[p]) <= TOL, (props[p], rel_l2(got[p], ref[p]))
+
+
+@pytest.mark.parametrize("shape", [(1, 32, 32), (2, 4, 4), (3, 24, 96), (16, 16, 2048 // 8)])
+def test_reconstruct_edge_shapes(env, shape):
+    B = env[0]
+    kinds = ("phase", "absorption", "fluor")
+    o = ph.optics(na_ill=0.6)
+    tf, ws = check_tf(env, [o], shape, kinds)
+    modes, props, chans = OM.widefield_system(oracle_tf(o, shape, kinds), kinds)
+    d = ph.uniform_volume(13, (2,) + shape, 0.9, 1.1).astype(np.float32)
+    got = run_recon(env, tf, ws, kinds, d[None], [1.0, 1.0], [1e-2, 1e-2], 0, B.WO_MODE_3D, shape)[0]
+    ref = np.zeros(got.shape)
+    for m in modes:
+        r = OM.reconstruct([m], d.astype(np.float64), 1e-2, background=[1.0, 1.0])
+        for p in m["props"]:
+            ref[p] = r[p]
+    assert rel_l2(got, ref) <= TOL
+
+
+def test_exact_recovery_band_limited_fp32(env):
+    """Noiseless band-limited object, eta_rel = 1e-6: float32 recovery within 1e-4."""
+    B = env[0]
+    shape = (16, 64, 64)
+    o = ph.optics()
+    tfs = oracle_tf(o, shape, ("phase",))
+    H = tfs["phase"]
+    mask = np.abs(H) ** 2 >= 0.05 * np.max(np.abs(H) ** 2)
+    f = np.real(np.fft.ifftn(np.fft.fftn(ph.uniform_volume(2, shape, -1, 1)) * mask)) * 0.01
+    modes, _, _ = OM.widefield_system(tfs, ("phase",))
+    d = OM.forward(modes, f[None], [1.0]).astype(np.float32)
+    tf, ws = check_tf(env, [o], shape, ("phase",))
+    got = run_recon(env, tf, ws, ("phase",), d[None], [1.0], [1e-6], 0, B.WO_MODE_3D, shape)[0, 0]
+    assert rel_l2(got, f) <= TOL
+
+
+# ------------------------------------------------------------ tiles
+def test_tiles_gather_blend(env):
+    B, torch, dev = env
+    ty, tx, core, halo, Z = 2, 3, 32, 8, 4
+    field = ph.uniform_volume(4, (Z, ty * core, tx * core)).astype(np.float32)
+    E = core + 2 * halo
+    fd = torch.from_numpy(field).to(dev)
+    td = torch.empty((ty * tx, Z, E, E), dtype=torch.float32, device=dev)
+    B.wo_tile_gather(fd, Z, ty, tx, core, halo, td)
+    ref = OT.gather(field, ty, tx, core, halo)
+    assert np.array_equal(td.cpu().numpy(), ref)  # a pure copy: bit exact
+    td2 = torch.from_numpy(ph.uniform_volume(5, ref.shape).astype(np.float32)).to(dev)
+    out = torch.empty_like(fd)
+    B.wo_tile_blend(td2, Z, ty, tx, core, halo, out)
+    ref2 = OT.blend(td2.cpu().numpy().astype(np.float64), ty, tx, core, halo)
+    assert np.abs(out.cpu().numpy() - ref2).max() <= 1e-6
+
+
+def test_shift_variant_pipeline_four_tiles(env):
+    """Field 48 x 256 x 256, 2 x 2 tiles of 128-px cores with 32-px halos
+    (48 x 192 x 192 tiles, each with its own theta), phase reconstruction, blend."""
+    B, torch, dev = env
+    ty, tx, core, halo, Z = 2, 2, 128, 32, 48
+    E = core + 2 * halo
+    o_list = ph.tile_optics(np.random.default_rng(7), ty * tx)
+    field = (1.0 + ph.sphere_phantom(3, (Z, ty * core, tx * core), n_spheres=150)
+             + ph.gaussian_noise(4, (Z, ty * core, tx * core), 1e-3)).astype(np.float32)
+    fd = torch.from_numpy(field).to(dev)
+    td = torch.empty((ty * tx, Z, E, E), dtype=torch.float32, device=dev)
+    B.wo_tile_gather(fd, Z, ty, tx, core, halo, td)
+    tf, ws = B.alloc(ty * tx, Z, E, E, ("phase",), dev)
+    B.wo_build_tf(o_list, ty * tx, Z, E, E, ("phase",), tf, ws)
+    rec = torch.empty_like(td)
+    B.wo_reconstruct(tf, ("phase",), td, None, [1e-3], B.WO_ETA_RELATIVE, B.WO_MODE_3D, rec, ty * tx, Z, E, E, ws)
+    out = torch.empty_like(fd)
+    B.wo_tile_blend(rec, Z, ty, tx, core, halo, out)
+    got = out.cpu().numpy()
+    tiles = OT.gather(field.astype(np.float64), ty, tx, core, halo)
+    rec_ref = np.empty_like(tiles)
+    for t, o in enumerate(o_list):
+        modes, _, _ = OM.widefield_system(oracle_tf(o, (Z, E, E), ("phase",)), ("phase",))
+        rec_ref[t] = OM.reconstruct(modes, tiles[t][None], 1e-3)[0]
+    ref = OT.blend(rec_ref, ty, tx, core, halo)
+    assert rel_l2(got, ref) <= TOL
+
+
+# --------------------------------------------- full widefield workload
+def test_widefield_full_size(env):
+    """96 x 512 x 512, phase + absorption + fluorescence: the whole TF bank
+    against the oracle, and the reconstruction at sampled frequencies (direct
+    DFT coefficients of the GPU's input and output)."""
+    B, torch, dev = env
+    shape = (96, 512, 512)
+    Z, Y, X = shape
+    kinds = ("phase", "absorption", "fluor")
+    o = ph.optics()
+    tf, ws, spec, stats = gpu_tf(env, [o], shape, kinds)
+    ref = oracle_tf(o, shape, kinds)
+    for s, k in enumerate(kinds):
+        assert rel_l2(spec[0, s], OO.half_spectrum(ref[k])) <= TOL, k
+    tot_lf = np.abs(ref["phase"]) ** 2 + np.abs(ref["absorption"]) ** 2
+    assert abs(stats[0, 0] / tot_lf.max() - 1) <= 1e-5
+    # input stacks: brightfield-like and fluorescence-like volumes from a phantom
+    vols = ph.widefield_phantom(2, shape, o, n_spheres=300, n_shells=30)
+    d = np.stack([1.0 + vols["dn"] + ph.gaussian_noise(5, shape, 1e-3),
+                  0.2 + 0.05 * vols["rho"] + ph.gaussian_noise(6, shape, 1e-3)]).astype(np.float32)
+    eta = [1e-3, 1e-3]
+    got = run_recon(env, tf, ws, kinds, d[None], None, eta, 0, B.WO_MODE_3D, shape)[0]
+    eta_lf = eta[0] * tot_lf.max()
+    eta_fl = eta[1] * (np.abs(ref["fluor"]) ** 2).max()
+    rng = np.random.default_rng(0)
+    ks = [(0, 0, 0), (1, 5, 7)] + [tuple(int(rng.integers(0, n)) for n in shape) for _ in range(4)]
+    for k in ks:
+        D = [OD.dft_coefficient(d[c].astype(np.float64), k) for c in range(2)]
+        if k == (0, 0, 0):
+            D = [0.0, 0.0]  # background = channel mean
+        H = [ref[kk][k] for kk in kinds]
+        Hm = np.array([[H[0], H[1]]])
+        F_lf = OM.solve_normal(Hm, np.array([D[0]]), eta_lf)
+        F_fl = np.conj(H[2]) * D[1] / (abs(H[2]) ** 2 + eta_fl)
+        want = [F_lf[0], F_lf[1], F_fl]
+        for p in range(3):
+            have = OD.dft_coefficient(got[p].astype(np.float64), k)
+            scale = max(abs(want[p]), 1e-3 * np.abs(d[0] - d[0].mean()).sum() * abs(H[p]) / (abs(H[p]) ** 2 + eta_lf))
+            assert abs(have - want[p]) <= 1e-3 * scale + 1e-6, (k, p, have, want[p])
+
+
+def test_launch_counter_and_profiler(env):
+    B, torch, dev = env
+    shape = (8, 32, 32)
+    B.wo_profile_enable(True)
+    n0 = B.wo_launch_count()
+    check_tf(env, [ph.optics()], shape, ("phase",))
+    prof = B.wo_profile_read()
+    B.wo_profile_enable(False)
+    assert B.wo_launch_count() - n0 >= 5
+    assert {"tf_pupil_record", "tf_arms", "tf_psf_rows", "tf_ypass", "tf_zpass"} <= set(prof)
+    assert all(ms > 0 for _, ms in prof.values())

@@ -235,6 +235,17 @@ def test_tf_at_matches_full_build():
             assert abs(O.tf_at(o, shape, kind, k) - T[kind][k]) <= 1e-12 * np.abs(T[kind]).max()
 
 
+def test_tf_samples_match_full_build():
+    o = ph.optics(na_ill=0.8, tilt_y=-0.05, defocus_um=0.25)
+    shape = (5, 12, 16)
+    T = O.transfer_functions(o, shape)
+    ks = [(0, 0, 0), (4, 11, 15), (2, 5, 3), (1, 0, 8)]
+    for kind in O.KINDS:
+        got = O.tf_samples(o, shape, kind, ks)
+        ref = np.array([T[kind][k] for k in ks])
+        assert np.abs(got - ref).max() <= 1e-12 * np.abs(T[kind]).max()
+
+
 # -------------------------------------------------- P5 linearity, adjoint
 def test_adjoint_dot_product():
     o = ph.optics(na_ill=0.6, tilt_y=0.05)
