@@ -50,7 +50,12 @@ def check_tf(env, optics_list, shape, kinds, tol=TOL):
     for t, o in enumerate(optics_list):
         ref = oracle_tf(o, shape, kinds)
         for s, k in enumerate([k for k in OO.KINDS if k in kinds]):
-            e = rel_l2(spec[t, s], OO.half_spectrum(ref[k]))
+            # error relative to the norm of the TFs of the same contrast mode: the
+            # phase TF alone vanishes identically in symmetric cases (one in-focus
+            # plane, or a pupil holding only the zero frequency)
+            mode = ("fluor",) if k == "fluor" else [q for q in ("phase", "absorption") if q in kinds]
+            den = np.sqrt(sum(np.linalg.norm(OO.half_spectrum(ref[q])) ** 2 for q in mode))
+            e = np.linalg.norm(spec[t, s] - OO.half_spectrum(ref[k])) / den
             assert e <= tol, (t, k, e)
         lf = [k for k in ("phase", "absorption") if k in kinds]
         if lf:
@@ -217,7 +222,11 @@ def test_reconstruct_edge_shapes(env, shape):
 
 
 def test_exact_recovery_band_limited_fp32(env):
-    """Noiseless band-limited object, eta_rel = 1e-6: float32 recovery within 1e-4."""
+    """Noiseless band-limited object, eta_rel = 1e-6: float32 recovery within 1e-4.
+
+    The data carry no background: with a background of 1 the float32 rounding
+    of the input (6e-8) is itself amplified by the near-singular inverse and
+    dominates, whatever computes the reconstruction."""
     B = env[0]
     shape = (16, 64, 64)
     o = ph.optics()
@@ -226,9 +235,9 @@ def test_exact_recovery_band_limited_fp32(env):
     mask = np.abs(H) ** 2 >= 0.05 * np.max(np.abs(H) ** 2)
     f = np.real(np.fft.ifftn(np.fft.fftn(ph.uniform_volume(2, shape, -1, 1)) * mask)) * 0.01
     modes, _, _ = OM.widefield_system(tfs, ("phase",))
-    d = OM.forward(modes, f[None], [1.0]).astype(np.float32)
+    d = OM.forward(modes, f[None], [0.0]).astype(np.float32)
     tf, ws = check_tf(env, [o], shape, ("phase",))
-    got = run_recon(env, tf, ws, ("phase",), d[None], [1.0], [1e-6], 0, B.WO_MODE_3D, shape)[0, 0]
+    got = run_recon(env, tf, ws, ("phase",), d[None], [0.0], [1e-6], 0, B.WO_MODE_3D, shape)[0, 0]
     assert rel_l2(got, f) <= TOL
 
 
@@ -315,8 +324,10 @@ def test_widefield_full_size(env):
         want = [F_lf[0], F_lf[1], F_fl]
         for p in range(3):
             have = OD.dft_coefficient(got[p].astype(np.float64), k)
-            scale = max(abs(want[p]), 1e-3 * np.abs(d[0] - d[0].mean()).sum() * abs(H[p]) / (abs(H[p]) ** 2 + eta_lf))
-            assert abs(have - want[p]) <= 1e-3 * scale + 1e-6, (k, p, have, want[p])
+            # typical coefficient magnitude sqrt(N) * rms(f): 1e-4 of it is the
+            # per-coefficient analogue of a 1e-4 relative L2 error
+            typical = np.sqrt(got[p].size) * np.sqrt(np.mean(got[p].astype(np.float64) ** 2))
+            assert abs(have - want[p]) <= 1e-4 * typical + 1e-4 * abs(want[p]), (k, p, have, want[p], typical)
 
 
 def test_launch_counter_and_profiler(env):
