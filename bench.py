@@ -96,6 +96,77 @@ def peaks():
 
 
 # ------------------------------------------------------------------ clocks
+class NvmlClockSampler:
+    """Polls SM clock and clock-event reasons through NVML (read-only queries)
+    from a background thread every ~2 ms while the timed region runs."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, torch_device):
+        import ctypes
+        import threading
+        self.ok = False
+        self.samples = []
+        self._stop = threading.Event()
+        try:
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                return
+            h = ctypes.c_void_p()
+            bus = None
+            try:
+                import torch
+                p = torch.cuda.get_device_properties(torch_device)
+                bus = f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0".encode()
+            except Exception:
+                bus = None
+            if bus is None or nv.nvmlDeviceGetHandleByPciBusId_v2(bus, ctypes.byref(h)) != 0:
+                if nv.nvmlDeviceGetHandleByIndex_v2(0, ctypes.byref(h)) != 0:
+                    return
+            self.nv, self.h, self.ct = nv, h, ctypes
+            mx = ctypes.c_uint()
+            self.max_mhz = float(mx.value) if nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0 else None
+            fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                getattr(nv, "nvmlDeviceGetCurrentClocksThrottleReasons")
+            self.reason_fn = fn
+            self.ok = True
+            self.thread = threading.Thread(target=self._run, daemon=True)
+        except OSError:
+            self.ok = False
+
+    def _run(self):
+        ct = self.ct
+        clk = ct.c_uint()
+        rs = ct.c_ulonglong()
+        while not self._stop.is_set():
+            a = self.nv.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(clk))
+            b = self.reason_fn(self.h, ct.byref(rs))
+            if a == 0:
+                self.samples.append((float(clk.value), int(rs.value) if b == 0 else 0))
+            self._stop.wait(0.002)
+
+    def __enter__(self):
+        if self.ok:
+            self.thread.start()
+        return self
+
+    def __exit__(self, *exc):
+        if self.ok:
+            self._stop.set()
+            self.thread.join()
+
+    def summary(self):
+        if not self.samples:
+            return None
+        reasons = set()
+        for _, r in self.samples:
+            for bit, name in self.REASONS.items():
+                if r & bit:
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median([c for c, _ in self.samples]), "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(reasons), "samples": len(self.samples), "source": "nvml"}
+
+
 class ClockSampler:
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -244,12 +315,14 @@ def run_gpu(args, rank, world, local_rank):
     B.wo_profile_enable(True)
     n0 = B.wo_launch_count()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local_rank) as clk:
+    nvml = NvmlClockSampler(dev)
+    with ClockSampler(local_rank) as smi, nvml:
         ev0.record(stream)
         for _ in range(args.steps):
             step()
         ev1.record(stream)
         torch.cuda.synchronize()
+    clk = nvml.summary() or smi.summary()
     launches = B.wo_launch_count() - n0
     B.wo_profile_enable(False)
     prof = B.wo_profile_read()
@@ -263,6 +336,18 @@ def run_gpu(args, rank, world, local_rank):
         ms_max = float(t.item())
 
     # end to end through the public API: host (pinned) in, host out
+    if args.no_e2e:
+        e2e_ms = float("nan")
+    else:
+        e2e_ms = run_e2e(args, B, o, data, out, tf, ws, stream, barrier, world, dev)
+    if rank != 0:
+        return
+    report(args, world, ms_max, e2e_ms, prof, launches, clk)
+
+
+def run_e2e(args, B, o, data, out, tf, ws, stream, barrier, world, dev):
+    import torch
+    Z, Y, X = SHAPE
     h_in = torch.empty((1, 2, Z, Y, X), dtype=torch.float32, pin_memory=True)
     h_in.copy_(data.cpu())
     h_out = torch.empty((1, 3, Z, Y, X), dtype=torch.float32, pin_memory=True)
@@ -290,9 +375,11 @@ def run_gpu(args, rank, world, local_rank):
         t = torch.tensor([e2e_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
+    return e2e_ms
 
-    if rank != 0:
-        return
+
+def report(args, world, ms_max, e2e_ms, prof, launches, clk):
+    Z, Y, X = SHAPE
     vox = float(Z * Y * X)
     value = world * vox / (ms_max * 1e-3)
     algo = algorithmic_bytes(SHAPE, KINDS)
@@ -320,14 +407,15 @@ def run_gpu(args, rank, world, local_rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded phantom: 2000 spheres + 200 shells, GPU forward model + 1e-3 noise)",
-        "config": {"workload": WORKLOAD, "Z": Z, "Y": Y, "X": X, "kinds": list(KINDS), "eta_relative": ETA,
+        "config": {"workload": WORKLOAD if SHAPE == (96, 512, 512) else f"profiling case {Z}x{Y}x{X}", "Z": Z, "Y": Y, "X": X, "kinds": list(KINDS), "eta_relative": ETA,
                    "background": "channel mean", "tiles": 1, "parallelism": f"replicas x{world}",
                    "l2": "working set > L2 (no flush needed): data 201 MB, TF 303 MB, workspace 606 MB"},
         "roofline": roofline,
         "kernels": per_kernel,
         "gpu_launches": int(launches),
-        "clocks": clk.summary(),
-        "e2e": {"value": round(world * vox / (e2e_ms * 1e-3), 1), "unit": "voxels/s",
+        "clocks": clk,
+        "e2e": None if e2e_ms != e2e_ms else {
+                "value": round(world * vox / (e2e_ms * 1e-3), 1), "unit": "voxels/s",
                 "ms_per_step": round(e2e_ms, 4),
                 "h2d_bytes_per_step": int(2 * vox * 4 + 72), "d2h_bytes_per_step": int(3 * vox * 4)},
     }
@@ -369,7 +457,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--shape", type=int, nargs=3, default=None,
+                    help="override Z Y X (smaller cases for profiler captures only)")
     args = ap.parse_args()
+    if args.shape:
+        global SHAPE
+        SHAPE = tuple(args.shape)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

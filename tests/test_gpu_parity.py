@@ -94,7 +94,7 @@ def test_tf_point_source_and_pooled_screen_optics(env):
 def test_tf_largest_lengths(env):
     check_tf(env, [ph.optics(na_ill=0.5)], (2, 8, 2048), ("phase", "fluor"))
     check_tf(env, [ph.optics(na_ill=0.5)], (2, 2048, 8), ("absorption",))
-    check_tf(env, [ph.optics(na_ill=0.5)], (2048, 4, 4), ("phase",))
+    check_tf(env, [ph.optics(na_ill=0.5)], (2048, 8, 8), ("phase",))
 
 
 # ------------------------------------------------ forward / adjoint
