@@ -144,6 +144,33 @@ wo_status wo_reconstruct(const void *d_tf, unsigned kinds, const float *d_data,
                          int eta_flag, int mode, float *d_f, int n_tiles, int Z,
                          int Y, int X, void *d_ws, size_t ws_bytes, wo_stream stream);
 
+/* Allocation-free reconstruction.  The paper has no counterpart: this is a
+ * service for callers that cannot allocate device memory where they need a
+ * reconstruction - a plugin inside a host application that owns the whole
+ * device-memory budget, code behind a caching allocator it may not bypass, or
+ * a latency-bound loop that must not pay cudaMalloc/cudaFree's implicit
+ * device synchronisation.  Same arguments and result as wo_reconstruct minus
+ * the workspace: the workspace is a device array of WO_STATIC_SCRATCH_BYTES
+ * (32 MiB) inside the library, which every GPU that loads the library holds
+ * until the process exits.  The caller still provides d_tf, d_data and d_f.
+ * - Problems whose wo_workspace_bytes() exceeds WO_STATIC_SCRATCH_BYTES are
+ *   rejected with WO_ERR_WORKSPACE before anything is launched (for example
+ *   16x64x64 with all three kinds needs 2 MB; 96x512x512 does not fit).
+ * - The first call on a device looks up the array's device address with that
+ *   device current and caches it; make that first call before any stream
+ *   capture begins.
+ * - The function allocates nothing (no cudaMalloc, cudaFree or allocating
+ *   library routine).
+ * - All calls on a device share the one array and it keeps the previous
+ *   call's contents; nothing in it needs to start at zero.  Calls whose work
+ *   overlaps on the GPU (different streams, or different host threads) race
+ *   on the array: order them on one stream. */
+#define WO_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+wo_status wo_reconstruct_static(const void *d_tf, unsigned kinds, const float *d_data,
+                                const float *h_background, const float *h_eta, int eta_flag,
+                                int mode, float *d_f, int n_tiles, int Z, int Y, int X,
+                                wo_stream stream);
+
 /* Row a8 (gather).  Cut a field [Z][tiles_y*core][tiles_x*core] into
  * overlapping tiles [tiles_y*tiles_x][Z][E][E], E = core + 2*halo, tile
  * (ty, tx) starting at field pixel (ty*core - halo, tx*core - halo); pixels

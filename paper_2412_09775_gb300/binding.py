@@ -51,6 +51,7 @@ def _load():
         "wo_forward": (i, [vp, u, vp, fp, vp, i, i, i, i, vp, sz, vp]),
         "wo_forward_adjoint": (i, [vp, u, vp, fp, vp, i, i, i, i, vp, sz, vp]),
         "wo_reconstruct": (i, [vp, u, vp, fp, fp, i, i, vp, i, i, i, i, vp, sz, vp]),
+        "wo_reconstruct_static": (i, [vp, u, vp, fp, fp, i, i, vp, i, i, i, i, vp]),
         "wo_tile_gather": (i, [vp, i, i, i, i, i, vp, vp]),
         "wo_tile_blend": (i, [vp, i, i, i, i, i, vp, vp]),
         "wo_status_string": (ctypes.c_char_p, [i]),
@@ -68,7 +69,7 @@ def _load():
 
 _lib = _load()
 EXPORTED = ("wo_size_supported", "wo_tf_bytes", "wo_workspace_bytes", "wo_build_tf", "wo_forward",
-            "wo_forward_adjoint", "wo_reconstruct", "wo_tile_gather", "wo_tile_blend",
+            "wo_forward_adjoint", "wo_reconstruct", "wo_reconstruct_static", "wo_tile_gather", "wo_tile_blend",
             "wo_status_string", "wo_profile_enable", "wo_profile_read", "wo_launch_count")
 
 
@@ -165,6 +166,18 @@ def wo_reconstruct(tf, kinds, data, background, eta, eta_flag, mode, f, n_tiles,
     _check(_lib.wo_reconstruct(_ptr(tf), kinds_mask(kinds), _ptr(data), bg[0] if bg else None, et[0],
                                int(eta_flag), int(mode), _ptr(f), n_tiles, Z, Y, X, _ptr(ws), _nbytes(ws),
                                _stream(stream)), "wo_reconstruct")
+
+
+WO_STATIC_SCRATCH_BYTES = 32 * 1024 * 1024
+
+
+def wo_reconstruct_static(tf, kinds, data, background, eta, eta_flag, mode, f, n_tiles, Z, Y, X, stream=None):
+    """wo_reconstruct with the library's own fixed device workspace (no allocation)."""
+    bg = _floats(background)
+    et = _floats(eta if isinstance(eta, (list, tuple)) else [eta])
+    _check(_lib.wo_reconstruct_static(_ptr(tf), kinds_mask(kinds), _ptr(data), bg[0] if bg else None, et[0],
+                                      int(eta_flag), int(mode), _ptr(f), n_tiles, Z, Y, X, _stream(stream)),
+           "wo_reconstruct_static")
 
 
 def wo_tile_gather(field, Z, tiles_y, tiles_x, core, halo, tiles, stream=None):
