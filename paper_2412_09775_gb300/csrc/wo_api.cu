@@ -94,7 +94,7 @@ static Layout layout_of(int n, int Z, int Y, int X, const Sys& s) {
   const size_t Xh = (size_t)X / 2 + 1;
   size_t off = 0;
   L.optics = off; off += align256((size_t)n * sizeof(wo_optics));
-  L.counts = off; off += align256((size_t)n * 2 * sizeof(int));
+  L.counts = off; off += align256((size_t)n * 4 * sizeof(int));
   L.rec = off; off += align256((size_t)n * Y * X * sizeof(float4));
   L.arms = off; off += align256((size_t)n * s.n_arms * Z * Y * X * sizeof(float2));
   L.build_end = off;
@@ -112,14 +112,12 @@ static Layout layout_of(int n, int Z, int Y, int X, const Sys& s) {
 
 static bool aligned16(const void* p) { return p && (((uintptr_t)p) & 15u) == 0; }
 
-static size_t zfused_smem(int Z, int n_vols) {
-  const int B = (Z <= 256) ? 16 : (Z <= 512) ? 8 : (Z <= 1024) ? 4 : 2;
-  return ((size_t)Z + (size_t)n_vols * Z * B) * sizeof(float2) + 512 * 11 * sizeof(float);
-}
-
-static size_t tfz_smem(int Z, int n_kinds) {
-  const int B = (Z <= 512) ? 16 : 8;
-  return ((size_t)Z + (size_t)n_kinds * Z * B) * sizeof(float2) + 512 * 2 * sizeof(float);
+// Shared memory of the z kernels: up to three volumes of Z x B columns.
+static size_t zpass_smem(int Z) {
+  const int NV = 3;
+  const int B = (NV * Z * 16 * 8 <= 112 * 1024) ? 16 : (NV * Z * 8 * 8 <= 112 * 1024) ? 8
+                : (NV * Z * 4 * 8 <= 112 * 1024) ? 4 : 2;
+  return ((size_t)Z + (size_t)NV * Z * B) * sizeof(float2) + 1024 * 11 * sizeof(float);
 }
 
 static wo_status check_shape(int n_tiles, int Z, int Y, int X, unsigned kinds) {
@@ -128,9 +126,7 @@ static wo_status check_shape(int n_tiles, int Z, int Y, int X, unsigned kinds) {
   if (Z < 1 || Y < 1 || X < 2) return WO_ERR_SHAPE;
   if (X % 2) return WO_ERR_SHAPE;
   if (!size_ok(Z) || !size_ok(Y) || !size_ok(X / 2) || X > 2048) return WO_ERR_UNSUPPORTED_SIZE;
-  const Sys s = system_of(kinds);
-  if (zfused_smem(Z, s.C + s.P) > 227 * 1024) return WO_ERR_UNSUPPORTED_SIZE;
-  if (tfz_smem(Z, s.n_kinds) > 227 * 1024) return WO_ERR_UNSUPPORTED_SIZE;
+  if (zpass_smem(Z) > 227 * 1024) return WO_ERR_UNSUPPORTED_SIZE;
   return WO_OK;
 }
 
@@ -259,7 +255,7 @@ wo_status wo_build_tf(const wo_optics* h_optics, int n_tiles, int Z, int Y, int 
   a.n_arms = s.n_arms; a.n_kinds = s.n_kinds;
   WO_TRY(cudaMemcpyAsync((void*)a.optics, h_optics, (size_t)n_tiles * sizeof(wo_optics),
                          cudaMemcpyHostToDevice, cs));
-  WO_TRY(cudaMemsetAsync(a.counts, 0, (size_t)n_tiles * 2 * sizeof(int), cs));
+  WO_TRY(cudaMemsetAsync(a.counts, 0, (size_t)n_tiles * 4 * sizeof(int), cs));
   WO_TRY(cudaMemsetAsync(a.stats, 0, (size_t)n_tiles * 8 * sizeof(float), cs));
   WO_TRY(tf_pupil_record(a, cs));
   WO_TRY(tf_arms(a, cs));

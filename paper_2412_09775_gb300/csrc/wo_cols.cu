@@ -25,8 +25,9 @@ __global__ void __launch_bounds__(ColGeom<N>::NT, ColGeom<N>::MINB)
   float2* base = data + plane * plane_stride + x0;
   for (int e = threadIdx.x; e < N * B; e += NT) {
     const int n = e / B, b = e % B;
-    buf[e] = (b < w) ? base[n * col_stride + b] : make_float2(0.f, 0.f);
+    cp_async8(buf + e, base + (b < w ? n * col_stride + b : 0), b < w);
   }
+  cp_async_wait_all();
   __syncthreads();
   fft_smem<N, B, NT, INV, 1>(buf, B, 1, tw);
   for (int e = threadIdx.x; e < N * B; e += NT) {

@@ -168,25 +168,48 @@ __device__ __forceinline__ void fft_smem(float2* buf, int es, int bs, const floa
   }
 }
 
+// ------------------------------------------------------------ async copies
+// cp.async (global -> shared, bypassing registers): a thread issues all of its
+// copies before waiting, so a whole tile is in flight at once.  A source size
+// of 0 zero-fills the destination without reading the source.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = valid ? 8 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Threads for a batch of B sequences of length N at about 8 elements per
+// thread (one radix-8 butterfly per stage), a multiple of 32 in [64, 1024].
+__host__ __device__ constexpr int threads_for(int elems) {
+  int t = elems / 8;
+  t = t < 64 ? 64 : (t > 1024 ? 1024 : t);
+  return (t + 31) / 32 * 32;
+}
+
 // Launch geometry shared by the column-tile kernels (transforms along a
 // strided axis, B adjacent columns per CTA).
 template <int N>
 struct ColGeom {
-  static constexpr int B = (N <= 512) ? 16 : 8;
-  static constexpr int NT0 = (N * B) / 16;
-  static constexpr int NT = NT0 < 64 ? 64 : (NT0 > 512 ? 512 : NT0);
-  static constexpr int MINB = (768 / NT) > 1 ? (768 / NT) : 1;
+  static constexpr int B = (N <= 256) ? 16 : 8;
+  static constexpr int NT = threads_for(N * B);
+  static constexpr int MINB = (1536 / NT) > 1 ? (1536 / NT) : 1;
   static constexpr size_t SMEM = (size_t)N * B * sizeof(float2) + (size_t)N * sizeof(float2);
 };
 
 // Row tiles (transforms along the contiguous axis, B rows per CTA, odd pitch).
 template <int N>
 struct RowGeom {
-  static constexpr int B = 16;
+  static constexpr int B = (N <= 256) ? 16 : 8;
   static constexpr int LD = N | 1;
-  static constexpr int NT0 = (N * B) / 16;
-  static constexpr int NT = NT0 < 64 ? 64 : (NT0 > 512 ? 512 : NT0);
-  static constexpr int MINB = (768 / NT) > 1 ? (768 / NT) : 1;
+  static constexpr int LD2 = (N + 1) | 1;  // raw half-spectrum rows (inverse)
+  static constexpr int NT = threads_for(N * B);
+  static constexpr int MINB = (1536 / NT) > 1 ? (1536 / NT) : 1;
 };
 
 }  // namespace wo

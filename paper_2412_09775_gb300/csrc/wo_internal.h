@@ -61,7 +61,7 @@ cudaError_t z_solve2d(int Z, const float2* in, float2* out, const float2* tf, ZO
 // Transfer-function build.
 struct TfArgs {
   const wo_optics* optics;  // device copy, [n_tiles]
-  int* counts;              // [n_tiles][2]: #(S and P), #P
+  int* counts;              // [n_tiles][4]: #(S and P), #P, x band limit, -
   float4* rec;              // [n_tiles][Y][X] pupil record
   float2* arms;             // [n_tiles][n_arms][Z][Y][X]
   float2* tf;               // [n_tiles][n_kinds][Z][Y][Xh]

@@ -14,6 +14,19 @@
 
 namespace wo {
 
+// Per-row background constant (mode 1: the channel's value; mode 2: the
+// first sample of the row's (tile, channel) block), one per row of the CTA.
+__device__ __forceinline__ void row_constants(float* sc, const float* in, long long row0, long long nrows,
+                                              int B, int N, const RowBg& bg) {
+  if (threadIdx.x < B) {
+    const long long row = row0 + threadIdx.x;
+    float c = 0.f;
+    if (row < nrows && bg.mode == 1) c = bg.v[(row / bg.rows_per_block) % bg.nchan];
+    if (row < nrows && bg.mode == 2) c = in[(row / bg.rows_per_block) * bg.rows_per_block * (2LL * N)];
+    sc[threadIdx.x] = c;
+  }
+}
+
 template <int N>
 __global__ void __launch_bounds__(RowGeom<N>::NT, RowGeom<N>::MINB)
     k_rows_r2c(const float* __restrict__ in, float2* __restrict__ out, long long nrows, RowBg bg) {
@@ -21,27 +34,30 @@ __global__ void __launch_bounds__(RowGeom<N>::NT, RowGeom<N>::MINB)
   constexpr int B = G::B, LD = G::LD, NT = G::NT;
   extern __shared__ float2 sm[];
   float2* buf = sm;
-  float2* tw = sm + B * LD;  // exp(-2 pi i m / 2N), m in [0, 2N)
-  make_twiddles<2 * N>(tw);
+  float2* tw = sm + B * LD;                            // exp(-2 pi i m / 2N), m in [0, 2N)
+  float* sc = reinterpret_cast<float*>(tw + 2 * N);   // [B] background per row
   const long long row0 = (long long)blockIdx.x * B;
   for (int e = threadIdx.x; e < B * N; e += NT) {
     const int b = e / N, n = e - (e / N) * N;
     const long long row = row0 + b;
-    float2 v = make_float2(0.f, 0.f);
-    if (row < nrows) {
-      v = reinterpret_cast<const float2*>(in + row * (2LL * N))[n];
-      float c = 0.f;
-      if (bg.mode == 1) {
-        c = bg.v[(row / bg.rows_per_block) % bg.nchan];
-      } else if (bg.mode == 2) {
-        c = __ldg(in + (row / bg.rows_per_block) * bg.rows_per_block * (2LL * N));
-      }
+    const bool ok = row < nrows;
+    cp_async8(buf + b * LD + n, in + (ok ? row * (2LL * N) + 2 * n : 0), ok);
+  }
+  make_twiddles<2 * N>(tw);
+  row_constants(sc, in, row0, nrows, B, N, bg);
+  cp_async_wait_all();
+  __syncthreads();
+  if (bg.mode != 0) {
+    for (int e = threadIdx.x; e < B * N; e += NT) {
+      const int b = e / N, n = e - (e / N) * N;
+      const float c = sc[b];
+      float2 v = buf[b * LD + n];
       v.x -= c;
       v.y -= c;
+      buf[b * LD + n] = v;
     }
-    buf[b * LD + n] = v;
+    __syncthreads();
   }
-  __syncthreads();
   fft_smem<N, B, NT, false, 2>(buf, 1, LD, tw);
   for (int e = threadIdx.x; e < B * (N + 1); e += NT) {
     const int b = e / (N + 1), k = e - (e / (N + 1)) * (N + 1);
@@ -60,26 +76,33 @@ __global__ void __launch_bounds__(RowGeom<N>::NT, RowGeom<N>::MINB)
     k_rows_c2r(const float2* __restrict__ in, float* __restrict__ out, long long nrows, float scale,
                RowBg bg) {
   using G = RowGeom<N>;
-  constexpr int B = G::B, LD = G::LD, NT = G::NT;
+  constexpr int B = G::B, LD = G::LD, LD2 = G::LD2, NT = G::NT;
   extern __shared__ float2 sm[];
-  float2* buf = sm;
-  float2* tw = sm + B * LD;
-  make_twiddles<2 * N>(tw);
-  __syncthreads();
+  float2* raw = sm;                                     // [B][LD2] input half spectra
+  float2* buf = sm + B * LD2;                           // [B][LD] packed complex rows
+  float2* tw = buf + B * LD;
+  float* sc = reinterpret_cast<float*>(tw + 2 * N);
   const long long row0 = (long long)blockIdx.x * B;
+  for (int e = threadIdx.x; e < B * (N + 1); e += NT) {
+    const int b = e / (N + 1), k = e - (e / (N + 1)) * (N + 1);
+    const long long row = row0 + b;
+    const bool ok = row < nrows;
+    cp_async8(raw + b * LD2 + k, in + (ok ? row * (N + 1) + k : 0), ok);
+  }
+  make_twiddles<2 * N>(tw);
+  if (threadIdx.x < B) {
+    const long long row = row0 + threadIdx.x;
+    sc[threadIdx.x] = (row < nrows && bg.mode == 1) ? bg.v[(row / bg.rows_per_block) % bg.nchan] : 0.f;
+  }
+  cp_async_wait_all();
+  __syncthreads();
   for (int e = threadIdx.x; e < B * N; e += NT) {
     const int b = e / N, k = e - (e / N) * N;
-    const long long row = row0 + b;
-    float2 z = make_float2(0.f, 0.f);
-    if (row < nrows) {
-      const float2* r = in + row * (N + 1);
-      const float2 xk = r[k];
-      const float2 xc = cconj(r[N - k]);
-      const float2 a = make_float2(0.5f * (xk.x + xc.x), 0.5f * (xk.y + xc.y));
-      const float2 bb = cmul(make_float2(0.5f * (xk.x - xc.x), 0.5f * (xk.y - xc.y)), cconj(tw[k]));
-      z = make_float2(a.x - bb.y, a.y + bb.x);
-    }
-    buf[b * LD + k] = z;
+    const float2 xk = raw[b * LD2 + k];
+    const float2 xc = cconj(raw[b * LD2 + N - k]);
+    const float2 a = make_float2(0.5f * (xk.x + xc.x), 0.5f * (xk.y + xc.y));
+    const float2 bb = cmul(make_float2(0.5f * (xk.x - xc.x), 0.5f * (xk.y - xc.y)), cconj(tw[k]));
+    buf[b * LD + k] = make_float2(a.x - bb.y, a.y + bb.x);
   }
   __syncthreads();
   fft_smem<N, B, NT, true, 2>(buf, 1, LD, tw);
@@ -87,20 +110,26 @@ __global__ void __launch_bounds__(RowGeom<N>::NT, RowGeom<N>::MINB)
     const int b = e / N, n = e - (e / N) * N;
     const long long row = row0 + b;
     if (row >= nrows) continue;
-    const float c = (bg.mode == 1) ? bg.v[(row / bg.rows_per_block) % bg.nchan] : 0.f;
+    const float c = sc[b];
     const float2 v = buf[b * LD + n];
     reinterpret_cast<float2*>(out + row * (2LL * N))[n] = make_float2(v.x * scale + c, v.y * scale + c);
   }
 }
 
 template <int N>
-static size_t rows_smem() {
-  return ((size_t)RowGeom<N>::B * RowGeom<N>::LD + 2 * (size_t)N) * sizeof(float2);
+static size_t rows_smem_r2c() {
+  return ((size_t)RowGeom<N>::B * RowGeom<N>::LD + 2 * (size_t)N) * sizeof(float2) + RowGeom<N>::B * sizeof(float);
+}
+
+template <int N>
+static size_t rows_smem_c2r() {
+  return ((size_t)RowGeom<N>::B * (RowGeom<N>::LD + RowGeom<N>::LD2) + 2 * (size_t)N) * sizeof(float2) +
+         RowGeom<N>::B * sizeof(float);
 }
 
 template <int N>
 static cudaError_t launch_r2c(const float* in, float2* out, long long nrows, RowBg bg, cudaStream_t s) {
-  const size_t smem = rows_smem<N>();
+  const size_t smem = rows_smem_r2c<N>();
   static cudaError_t attr = allow_smem(k_rows_r2c<N>, smem);
   if (attr != cudaSuccess) return attr;
   const long long blocks = (nrows + RowGeom<N>::B - 1) / RowGeom<N>::B;
@@ -111,7 +140,7 @@ static cudaError_t launch_r2c(const float* in, float2* out, long long nrows, Row
 template <int N>
 static cudaError_t launch_c2r(const float2* in, float* out, long long nrows, float scale, RowBg bg,
                               cudaStream_t s) {
-  const size_t smem = rows_smem<N>();
+  const size_t smem = rows_smem_c2r<N>();
   static cudaError_t attr = allow_smem(k_rows_c2r<N>, smem);
   if (attr != cudaSuccess) return attr;
   const long long blocks = (nrows + RowGeom<N>::B - 1) / RowGeom<N>::B;

@@ -23,6 +23,7 @@
 //                   used by the relative regulariser.
 #include "wo_fft.cuh"
 #include "wo_internal.h"
+#include "wo_zops.cuh"
 
 namespace wo {
 
@@ -58,6 +59,10 @@ __global__ void __launch_bounds__(256)
     rec[(long long)t * Y * X + idx] = make_float4(eh, el, binv, (S && P) ? 1.f : 0.f);
     n_sp = (S && P) ? 1 : 0;
     n_p = P ? 1 : 0;
+    // band limit along x: the largest |k_x| inside P on the k_y = 0 row.  P is
+    // contained in nu_x^2 <= (NA_det/lambda)^2, so every column beyond it is
+    // zero in every arm.
+    if (y == 0 && P) atomicMax(&counts[4 * t + 2], abs(fft_index(x, X)));
   }
   for (int off = 16; off > 0; off >>= 1) {
     n_sp += __shfl_down_sync(0xffffffffu, n_sp, off);
@@ -76,8 +81,8 @@ __global__ void __launch_bounds__(256)
       a += part[0][i];
       b += part[1][i];
     }
-    if (a) atomicAdd(&counts[2 * t], a);
-    if (b) atomicAdd(&counts[2 * t + 1], b);
+    if (a) atomicAdd(&counts[4 * t], a);
+    if (b) atomicAdd(&counts[4 * t + 1], b);
   }
 }
 
@@ -91,37 +96,49 @@ __device__ __forceinline__ float phase_frac(float eh, float el, float zh, float 
 }
 
 template <int N>  // N = Y
-__global__ void __launch_bounds__(ColGeom<N>::NT, ColGeom<N>::MINB) k_arms(TfArgs a) {
+__global__ void __launch_bounds__(ColGeom<N>::NT, (1024 / ColGeom<N>::NT) > 1 ? (1024 / ColGeom<N>::NT) : 1) k_arms(TfArgs a) {
   using G = ColGeom<N>;
   constexpr int B = G::B, NT = G::NT;
+  constexpr int PER = (N * B + NT - 1) / NT;
   extern __shared__ float2 sm[];
   float2* buf = sm;
   float2* tw = sm + N * B;
-  make_twiddles<N>(tw);
   const int X = a.X, Z = a.Z;
   const int t = blockIdx.z, j = blockIdx.y, x0 = blockIdx.x * B;
   const int w = min(B, X - x0);
+  // skip strips whose columns all lie outside the detection band: every arm
+  // is exactly zero there, and the row pass never reads those columns
+  const int kxmax = a.counts[4 * t + 2];
+  bool active = false;
+  for (int b = 0; b < w; ++b) active |= abs(fft_index(x0 + b, X)) <= kxmax;
+  if (!active) return;  // uniform across the CTA
+  make_twiddles<N>(tw);
   const wo_optics o = a.optics[t];
   const double zj = __dadd_rn(__dmul_rn((double)fft_index(j, Z), o.z_step_um), o.defocus_um);
   const float zh = __double2float_rn(zj);
   const float zl = __double2float_rn(__dsub_rn(zj, (double)zh));
   const float4* rec = a.rec + (long long)t * N * X + x0;
+  float4 r[PER];
+  float s_[PER], c_[PER];
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int e = threadIdx.x + i * NT;
+    const int n = e / B, b = e % B;
+    r[i] = (e < N * B && b < w) ? __ldg(rec + (long long)n * X + b) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+#pragma unroll
+  for (int i = 0; i < PER; ++i) sincospif(2.0f * phase_frac(r[i].x, r[i].y, zh, zl), &s_[i], &c_[i]);
   int arm = 0;
   for (int which = 0; which < 3; ++which) {
     if (which < 2 && a.lf_props == 0) continue;
     if (which == 2 && !a.want_fl) continue;
-    for (int e = threadIdx.x; e < N * B; e += NT) {
-      const int n = e / B, b = e % B;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int e = threadIdx.x + i * NT;
+      if (e >= N * B) continue;
+      const bool on = (which == 0) ? (r[i].w != 0.f) : (r[i].z != 0.f);
       float2 v = make_float2(0.f, 0.f);
-      if (b < w) {
-        const float4 r = rec[(long long)n * X + b];
-        const bool on = (which == 0) ? (r.w != 0.f) : (r.z != 0.f);
-        if (on) {
-          float s, c;
-          sincospif(2.0f * phase_frac(r.x, r.y, zh, zl), &s, &c);
-          v = (which == 1) ? make_float2(-r.z * s, r.z * c) : make_float2(c, s);
-        }
-      }
+      if (on) v = (which == 1) ? make_float2(-r[i].z * s_[i], r[i].z * c_[i]) : make_float2(c_[i], s_[i]);
       buf[e] = v;
     }
     __syncthreads();
@@ -138,12 +155,11 @@ __global__ void __launch_bounds__(ColGeom<N>::NT, ColGeom<N>::MINB) k_arms(TfArg
 
 template <int NX>
 struct PsfGeom {
-  static constexpr int B = (NX <= 512) ? 16 : (NX <= 1024) ? 8 : 4;
+  static constexpr int B = (NX <= 128) ? 16 : (NX <= 1024) ? 8 : 4;
   static constexpr int LD = NX + 1;
-  static constexpr int NT0 = (NX * B) / 16;
-  static constexpr int NT = NT0 < 64 ? 64 : (NT0 > 512 ? 512 : NT0);
-  static constexpr int MINB = (768 / NT) > 1 ? (768 / NT) : 1;
-  static constexpr size_t SMEM = (2 * (size_t)B * LD + NX + B) * sizeof(float2);
+  static constexpr int NT = threads_for(NX * B);
+  static constexpr int MINB = (1536 / NT) > 1 ? (1536 / NT) : 1;
+  static constexpr size_t SMEM = (2 * (size_t)B * LD + NX + 2 * B) * sizeof(float2);
 };
 
 // Real row h (given through `val`) -> half spectrum written to dst rows.
@@ -182,14 +198,14 @@ __device__ __forceinline__ void psf_r2c_rows(float2* src, float2* pack, const fl
 __device__ __forceinline__ float lf_scale(const TfArgs& a, int t) {
   // 2K = 2 c / (N_perp sum S P^2), c = 2 pi n dz / lambda^2
   const wo_optics o = a.optics[t];
-  const int n_sp = a.counts[2 * t];
+  const int n_sp = a.counts[4 * t];
   if (n_sp == 0) return 0.f;
   const double c = 2.0 * 3.14159265358979323846 * o.n_medium * o.z_step_um / (o.lambda_um * o.lambda_um);
   return (float)(2.0 * c / ((double)a.Y * (double)a.X * (double)n_sp));
 }
 
 __device__ __forceinline__ float fl_scale(const TfArgs& a, int t) {
-  const int n_p = a.counts[2 * t + 1];
+  const int n_p = a.counts[4 * t + 1];
   if (n_p == 0) return 0.f;
   return (float)(1.0 / ((double)a.Y * (double)a.X * (double)a.Z * (double)n_p));
 }
@@ -203,7 +219,7 @@ __global__ void __launch_bounds__(PsfGeom<NX>::NT, PsfGeom<NX>::MINB) k_psf_rows
   float2* bufB = sm + B * LD;
   float2* tw = sm + 2 * B * LD;  // exp(-2 pi i m / NX)
   float* sc = reinterpret_cast<float*>(tw + NX);  // per row: [B] label-free 2K, [B] fluorescence
-  make_twiddles<NX>(tw);
+  int* kxm = reinterpret_cast<int*>(sc + 2 * B);   // per row: x band limit of its tile
   const long long nrows = (long long)a.n_tiles * a.Z * a.Y;
   const long long row0 = (long long)blockIdx.x * B;
   if (threadIdx.x < B) {
@@ -211,25 +227,31 @@ __global__ void __launch_bounds__(PsfGeom<NX>::NT, PsfGeom<NX>::MINB) k_psf_rows
     const int t = (int)((row < nrows ? row : nrows - 1) / ((long long)a.Z * a.Y));
     sc[threadIdx.x] = lf_scale(a, t);
     sc[B + threadIdx.x] = fl_scale(a, t);
+    kxm[threadIdx.x] = row < nrows ? a.counts[4 * t + 2] : -1;
   }
+  __syncthreads();
   const long long plane_elems = (long long)a.Y * NX;  // elements of one arm plane
+  // columns outside the detection band are zero (and were never written)
   auto load_arm = [&](float2* dst, int arm) {
     for (int e = threadIdx.x; e < B * NX; e += NT) {
       const int b = e / NX, n = e - (e / NX) * NX;
       const long long row = row0 + b;
-      float2 v = make_float2(0.f, 0.f);
-      if (row < nrows) {
+      const bool ok = row < nrows && abs(fft_index(n, NX)) <= kxm[b];
+      const float2* src = a.arms;
+      if (ok) {
         const long long t = row / ((long long)a.Z * a.Y);
         const long long rem = row - t * a.Z * a.Y;  // j*Y + y
-        v = a.arms[((t * a.n_arms + arm) * a.Z) * plane_elems + rem * NX + n];
+        src = a.arms + ((t * a.n_arms + arm) * a.Z) * plane_elems + rem * NX + n;
       }
-      dst[b * LD + n] = v;
+      cp_async8(dst + b * LD + n, src, ok);
     }
   };
+  make_twiddles<NX>(tw);
   int arm = 0;
   if (a.lf_props > 0) {
     load_arm(bufA, 0);
     load_arm(bufB, 1);
+    cp_async_wait_all();
     __syncthreads();
     fft_smem<NX, B, NT, true, 1>(bufA, 1, LD, tw);
     fft_smem<NX, B, NT, true, 1>(bufB, 1, LD, tw);
@@ -252,6 +274,7 @@ __global__ void __launch_bounds__(PsfGeom<NX>::NT, PsfGeom<NX>::MINB) k_psf_rows
   }
   if (a.want_fl) {
     load_arm(bufA, arm);
+    cp_async_wait_all();
     __syncthreads();
     fft_smem<NX, B, NT, true, 1>(bufA, 1, LD, tw);
     psf_r2c_rows<NX, B, NT>(bufA, bufB, tw, [&](float2 p, int b) { return sc[B + b] * cabs2(p); },
@@ -259,58 +282,57 @@ __global__ void __launch_bounds__(PsfGeom<NX>::NT, PsfGeom<NX>::MINB) k_psf_rows
   }
 }
 
-template <int N>  // N = Z
-__global__ void __launch_bounds__(ColGeom<N>::NT, ColGeom<N>::MINB) k_tf_zpass(TfArgs a) {
-  using G = ColGeom<N>;
+template <int N, int NK>  // N = Z, NK transfer functions per tile
+__global__ void __launch_bounds__(ZGeom<N, NK>::NT, ZGeom<N, NK>::MINB) k_tf_zpass(TfArgs a) {
+  using G = ZGeom<N, NK>;
   constexpr int B = G::B, NT = G::NT, KK = NT / B;
   extern __shared__ float2 sm[];
   float2* tw = sm;
-  float2* buf = sm + N;  // [n_kinds][N][B]
-  float* red = reinterpret_cast<float*>(buf + a.n_kinds * N * B);  // [NT][2]
-  make_twiddles<N>(tw);
+  float2* buf = sm + N;  // [n][kind][b]
+  float* red = reinterpret_cast<float*>(buf + NK * N * B);  // [NT][2]
   const int Y = a.Y, Xh = a.X / 2 + 1;
   const int t = blockIdx.z, y = blockIdx.y, x0 = blockIdx.x * B;
   const int w = min(B, Xh - x0);
   const long long zs = (long long)Y * Xh;
   const long long vol = (long long)N * zs;
-  float2* base = a.tf + (long long)t * a.n_kinds * vol + (long long)y * Xh + x0;
-  for (int s = 0; s < a.n_kinds; ++s) {
-    for (int e = threadIdx.x; e < N * B; e += NT) {
-      const int n = e / B, b = e % B;
-      buf[s * N * B + e] = (b < w) ? base[s * vol + n * zs + b] : make_float2(0.f, 0.f);
-    }
-  }
+  float2* base = a.tf + (long long)t * NK * vol + (long long)y * Xh + x0;
+  load_zcols<N, NK, B, NT>(buf, base, NK, vol, zs, w);
+  make_twiddles<N>(tw);
+  cp_async_wait_all();
   __syncthreads();
-  for (int s = 0; s < a.n_kinds; ++s) fft_smem<N, B, NT, false, 1>(buf + s * N * B, B, 1, tw);
+  fft_smem<N, NK * B, NT, false, 1>(buf, NK * B, 1, tw);
   const int L = a.lf_props;
   float m3_lf = 0.f, m3_fl = 0.f, col_lf = 0.f, col_fl = 0.f;
-  const int b = threadIdx.x % B;  // fixed per thread since NT % B == 0
-  for (int e = threadIdx.x; e < N * B; e += NT) {
-    const int n = e / B;
-    if (b >= w) continue;
-    float lf = 0.f;
-    for (int s = 0; s < L; ++s) lf += cabs2(buf[s * N * B + e]);
-    m3_lf = fmaxf(m3_lf, lf);
-    col_lf += lf;
-    if (a.want_fl) {
-      const float fl = cabs2(buf[L * N * B + e]);
-      m3_fl = fmaxf(m3_fl, fl);
-      col_fl += fl;
+  const int b = threadIdx.x % B;  // fixed per thread: NT is a multiple of 32 and B divides 32
+  if (b < w) {
+    for (int e = threadIdx.x; e < N * B; e += NT) {
+      const int n = e / B;
+      const float2* cell = buf + n * NK * B + b;
+      float lf = 0.f;
+      for (int s = 0; s < L; ++s) lf += cabs2(cell[s * B]);
+      m3_lf = fmaxf(m3_lf, lf);
+      col_lf += lf;
+      if (a.want_fl) {
+        const float fl = cabs2(cell[L * B]);
+        m3_fl = fmaxf(m3_fl, fl);
+        col_fl += fl;
+      }
     }
-    for (int s = 0; s < a.n_kinds; ++s) base[s * vol + n * zs + b] = buf[s * N * B + e];
+  }
+  for (int e = threadIdx.x; e < NK * N * B; e += NT) {
+    const int v = e / (N * B), r = e - v * (N * B);
+    const int n = r / B, bb = r % B;
+    if (bb < w) base[v * vol + n * zs + bb] = buf[(n * NK + v) * B + bb];
   }
   red[2 * threadIdx.x] = col_lf;
   red[2 * threadIdx.x + 1] = col_fl;
   __syncthreads();
   float m2_lf = 0.f, m2_fl = 0.f;
   if (threadIdx.x < B && threadIdx.x < w) {
-    float sl = 0.f, sf = 0.f;
     for (int q = 0; q < KK; ++q) {
-      sl += red[2 * (q * B + threadIdx.x)];
-      sf += red[2 * (q * B + threadIdx.x) + 1];
+      m2_lf += red[2 * (q * B + threadIdx.x)];
+      m2_fl += red[2 * (q * B + threadIdx.x) + 1];
     }
-    m2_lf = sl;
-    m2_fl = sf;
   }
   // block maxima (values are >= 0, so integer order equals float order)
   for (int off = 16; off > 0; off >>= 1) {
@@ -380,29 +402,30 @@ cudaError_t tf_psf_rows(const TfArgs& a, cudaStream_t s) {
   }
 }
 
-template <int N>
+template <int N, int NK>
 static cudaError_t launch_zpass(const TfArgs& a, cudaStream_t s) {
-  using G = ColGeom<N>;
-  const size_t smem = ((size_t)N + (size_t)a.n_kinds * N * G::B) * sizeof(float2) + (size_t)G::NT * 2 * sizeof(float);
-  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-  cudaError_t attr = cudaFuncSetAttribute(k_tf_zpass<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  using G = ZGeom<N, NK>;
+  const size_t smem = G::SMEM + (size_t)G::NT * 2 * sizeof(float);
+  static cudaError_t attr = allow_smem(k_tf_zpass<N, NK>, smem);
   if (attr != cudaSuccess) return attr;
   const int Xh = a.X / 2 + 1;
   dim3 grid((unsigned)((Xh + G::B - 1) / G::B), (unsigned)a.Y, (unsigned)a.n_tiles);
-  WO_LAUNCH("tf_zpass", s, (k_tf_zpass<N><<<grid, G::NT, smem, s>>>(a)));
+  WO_LAUNCH("tf_zpass", s, (k_tf_zpass<N, NK><<<grid, G::NT, smem, s>>>(a)));
   return cudaGetLastError();
 }
 
+#define WO_ZP_CASE_1(n) case n: return launch_zpass<n, 1>(a, s);
+#define WO_ZP_CASE_2(n) case n: return launch_zpass<n, 2>(a, s);
+#define WO_ZP_CASE_3(n) case n: return launch_zpass<n, 3>(a, s);
+
 cudaError_t tf_zpass(const TfArgs& a, cudaStream_t s) {
-  switch (a.Z) {
-#define WO_CASE(n) \
-  case n:          \
-    return launch_zpass<n>(a, s);
-    WO_FOR_EACH_SIZE(WO_CASE)
-#undef WO_CASE
-    default:
-      return cudaErrorInvalidValue;
+  if (a.n_kinds == 1) {
+    switch (a.Z) { WO_FOR_EACH_SIZE(WO_ZP_CASE_1) default: return cudaErrorInvalidValue; }
   }
+  if (a.n_kinds == 2) {
+    switch (a.Z) { WO_FOR_EACH_SIZE(WO_ZP_CASE_2) default: return cudaErrorInvalidValue; }
+  }
+  switch (a.Z) { WO_FOR_EACH_SIZE(WO_ZP_CASE_3) default: return cudaErrorInvalidValue; }
 }
 
 }  // namespace wo
