@@ -61,7 +61,17 @@ def kernel_digest(name: str) -> str:
     return h.hexdigest()[:16]
 
 
-def algorithmic_bytes(shape, kinds):
+def band_columns(o, X):
+    """x columns inside the detection band |nu_x| <= NA_det/lambda (the arms are
+    exactly zero elsewhere and are neither stored nor read)."""
+    R = o["na_det"] / o["lambda_um"]
+    k = 0
+    while k + 1 <= X // 2 and ((k + 1) / (X * o["pixel_um"])) ** 2 <= R * R:
+        k += 1
+    return min(X, 2 * k + 1)
+
+
+def algorithmic_bytes(shape, kinds, o):
     """Compulsory HBM bytes per launch of each kernel family for one step."""
     Z, Y, X = shape
     Xh = X // 2 + 1
@@ -72,10 +82,11 @@ def algorithmic_bytes(shape, kinds):
     n_arms = 2 * lf + (1 if "fluor" in kinds else 0)
     real = Z * Y * X * 4
     half = Z * Y * Xh * 8
+    arms = n_arms * Z * Y * band_columns(o, X) * 8
     return {
         "tf_pupil_record": Y * X * 16,
-        "tf_arms": n_arms * Z * Y * X * 8,
-        "tf_psf_rows": n_arms * Z * Y * X * 8 + nk * half,
+        "tf_arms": arms,
+        "tf_psf_rows": arms + nk * half,
         "tf_ypass": 2 * nk * half,
         "tf_zpass": 2 * nk * half,
         "rows_r2c": C * (real + half),
@@ -327,13 +338,8 @@ def run_gpu(args, rank, world, local_rank):
     B.wo_profile_enable(False)
     prof = B.wo_profile_read()
     barrier()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    ms_max = ms
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    from paper_2412_09775_gb300.shard import max_over_ranks
+    ms_max = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, device=dev)
 
     # end to end through the public API: host (pinned) in, host out
     if args.no_e2e:
@@ -369,20 +375,17 @@ def run_e2e(args, B, o, data, out, tf, ws, stream, barrier, world, dev):
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    return e2e_ms
+    from paper_2412_09775_gb300.shard import max_over_ranks
+    return max_over_ranks(e0.elapsed_time(e1) / args.steps, device=dev)
 
 
 def report(args, world, ms_max, e2e_ms, prof, launches, clk):
     Z, Y, X = SHAPE
+    from paper_2412_09775_gb300.shard import job_throughput
     vox = float(Z * Y * X)
-    value = world * vox / (ms_max * 1e-3)
-    algo = algorithmic_bytes(SHAPE, KINDS)
+    value = job_throughput(vox, world, ms_max)
+    import phantom as ph
+    algo = algorithmic_bytes(SHAPE, KINDS, ph.optics())
     per_kernel = {}
     for name, (cnt, tot) in prof.items():
         avg = tot / cnt if cnt else 0.0
@@ -415,12 +418,130 @@ def report(args, world, ms_max, e2e_ms, prof, launches, clk):
         "gpu_launches": int(launches),
         "clocks": clk,
         "e2e": None if e2e_ms != e2e_ms else {
-                "value": round(world * vox / (e2e_ms * 1e-3), 1), "unit": "voxels/s",
+                "value": round(job_throughput(vox, world, e2e_ms), 1), "unit": "voxels/s",
                 "ms_per_step": round(e2e_ms, 4),
                 "h2d_bytes_per_step": int(2 * vox * 4 + 72), "d2h_bytes_per_step": int(3 * vox * 4)},
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ tiles
+TILE_GRID = (16, 16)
+TILE_CORE, TILE_HALO = 128, 32
+FIELD_Z = 48
+TILES_WORKLOAD = ("shift-variant field 48x2048x2048: 16x16 tiles of 48x192x192 (128-px cores, 32-px halos), "
+                  "per-tile optics; gather + TF build (phase) + 3D Tikhonov + blend, one CUDA graph")
+
+
+def make_field(o_list, dev, seed=4):
+    """Synthetic shift-variant field: a sphere phantom whose 16x16 regions are
+    each forward-simulated (on the GPU) with their tile's optics, then blended."""
+    import torch
+    import phantom as ph
+    from paper_2412_09775_gb300 import binding as B
+    ty, tx = TILE_GRID
+    Z, E = FIELD_Z, TILE_CORE + 2 * TILE_HALO
+    n = ty * tx
+    obj = ph.sphere_phantom(seed, (Z, ty * TILE_CORE, tx * TILE_CORE), ph.optics(), n_spheres=16000)
+    obj_d = torch.from_numpy(obj.astype(np.float32)).to(dev)
+    t_obj = torch.empty((n, Z, E, E), dtype=torch.float32, device=dev)
+    B.wo_tile_gather(obj_d, Z, ty, tx, TILE_CORE, TILE_HALO, t_obj)
+    tf, ws = B.alloc(n, Z, E, E, ("phase",), dev)
+    B.wo_build_tf(o_list, n, Z, E, E, ("phase",), tf, ws)
+    t_dat = torch.empty_like(t_obj)
+    B.wo_forward(tf, ("phase",), t_obj, [1.0], t_dat, n, Z, E, E, ws)
+    field = torch.empty_like(obj_d)
+    B.wo_tile_blend(t_dat, Z, ty, tx, TILE_CORE, TILE_HALO, field)
+    torch.cuda.synchronize()
+    noise = ph.gaussian_noise(seed + 1, field.shape, 1e-3).astype(np.float32)
+    field += torch.from_numpy(noise).to(dev)
+    del tf, ws, t_obj, t_dat, obj_d
+    torch.cuda.empty_cache()
+    return field
+
+
+def run_tiles(args, rank, world, local_rank):
+    import torch
+    import phantom as ph
+    from paper_2412_09775_gb300.build import build
+    from paper_2412_09775_gb300.shard import job_throughput, max_over_ranks
+    build()
+    from paper_2412_09775_gb300 import binding as B
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    ty, tx = TILE_GRID
+    n = ty * tx
+    Z, E = FIELD_Z, TILE_CORE + 2 * TILE_HALO
+    o_list = ph.tile_optics(np.random.default_rng(3 + rank), n)
+    field = make_field(o_list, dev, seed=4 + rank)
+    optics = B.optics_tensor(o_list, dev)
+    tiles = torch.empty((n, Z, E, E), dtype=torch.float32, device=dev)
+    rec = torch.empty_like(tiles)
+    out = torch.empty_like(field)
+    tf, ws = B.alloc(n, Z, E, E, ("phase",), dev)
+
+    def step():
+        B.wo_tile_gather(field, Z, ty, tx, TILE_CORE, TILE_HALO, tiles)
+        B.wo_build_tf_device(optics, n, Z, E, E, ("phase",), tf, ws)
+        B.wo_reconstruct(tf, ("phase",), tiles, None, [1e-3], B.WO_ETA_RELATIVE, B.WO_MODE_3D, rec, n, Z, E, E, ws)
+        B.wo_tile_blend(rec, Z, ty, tx, TILE_CORE, TILE_HALO, out)
+
+    s = torch.cuda.Stream(device=dev)
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for _ in range(max(1, args.warmup)):
+            step()
+    torch.cuda.synchronize()
+    # per-kernel times from one eager, profiled step (events do not enter the graph)
+    B.wo_profile_read()
+    B.wo_profile_enable(True)
+    with torch.cuda.stream(s):
+        step()
+    torch.cuda.synchronize()
+    B.wo_profile_enable(False)
+    prof = B.wo_profile_read()
+    n0 = B.wo_launch_count()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        step()
+    per_step_launches = B.wo_launch_count() - n0
+    for _ in range(args.warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nvml = NvmlClockSampler(dev)
+    with nvml:
+        ev0.record()
+        for _ in range(args.steps):
+            g.replay()
+        ev1.record()
+        torch.cuda.synchronize()
+    ms_max = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, device=dev)
+    if rank != 0:
+        return
+    vox = float(field.numel())
+    peak, peak_kind = peaks()
+    per_kernel = {}
+    tot = sum(v[1] for v in prof.values())
+    for name, (cnt, t) in prof.items():
+        per_kernel[name] = {"launches": cnt, "avg_ms": round(t / cnt, 4), "share": round(t / tot, 4)}
+    line = {
+        "metric": METRIC, "value": round(job_throughput(vox, world, ms_max), 1), "unit": "voxels/s",
+        "tiles_per_s": round(job_throughput(n, world, ms_max), 1), "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_max, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (sphere phantom forward-simulated per tile with its own optics + 1e-3 noise)",
+        "config": {"workload": TILES_WORKLOAD, "field": [Z, ty * TILE_CORE, tx * TILE_CORE], "tiles": n,
+                   "tile": [Z, E, E], "eta_relative": 1e-3, "parallelism": f"replicas x{world}",
+                   "l2": "working set > L2 (field 805 MB, tiles 1.8 GB, TF 1.8 GB)"},
+        "kernels": per_kernel, "gpu_launches": int(per_step_launches * args.steps),
+        "clocks": nvml.summary(), "peak_hbm_gbs": peak,
+    }
     print(json.dumps(line), flush=True)
 
 
@@ -458,6 +579,7 @@ def main():
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--workload", choices=["widefield", "tiles"], default="widefield")
     ap.add_argument("--shape", type=int, nargs=3, default=None,
                     help="override Z Y X (smaller cases for profiler captures only)")
     args = ap.parse_args()
@@ -476,7 +598,10 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     try:
-        run_gpu(args, rank, world, local_rank)
+        if args.workload == "tiles":
+            run_tiles(args, rank, world, local_rank)
+        else:
+            run_gpu(args, rank, world, local_rank)
     finally:
         if world > 1:
             import torch.distributed as dist

@@ -79,9 +79,12 @@ enum { WO_ETA_RELATIVE = 0, WO_ETA_ABSOLUTE = 1 };
 int wo_size_supported(int n);
 
 /* Bytes of a transfer-function bank for these arguments: the half spectra
- * [n_tiles][n_kinds][Z][Y][X/2+1] complex64, followed by a per-tile float
- * statistics block [n_tiles][8] that wo_build_tf fills (maxima of sum|H|^2
- * used by the relative regulariser). 0 on invalid arguments. */
+ * [n_tiles][n_kinds][Z][Y][X/2+1] complex64, followed (at the next 256-byte
+ * boundary) by a per-tile statistics block [n_tiles][8] of 32-bit words that
+ * the TF build fills: float max_nu sum_lf|H|^2, float max_nu_perp
+ * sum_kz sum_lf|H|^2, the same two for fluorescence (used by the relative
+ * regulariser), int32 optics status (see wo_build_tf_device), three reserved.
+ * 0 on invalid arguments. */
 size_t wo_tf_bytes(int n_tiles, int Z, int Y, int X, unsigned kinds);
 
 /* Workspace bytes that suffice for every entry point with these arguments.
@@ -106,6 +109,19 @@ size_t wo_workspace_bytes(int n_tiles, int Z, int Y, int X, unsigned kinds);
 wo_status wo_build_tf(const wo_optics *h_optics, int n_tiles, int Z, int Y, int X,
                       unsigned kinds, void *d_tf, void *d_ws, size_t ws_bytes,
                       wo_stream stream);
+
+/* Rows a1-a4 with the optics in device memory (n_tiles structs at d_optics,
+ * 8-byte aligned, caller-owned, read by the kernels): the form to capture in
+ * a CUDA graph or to drive from parameters updated on the device (one
+ * parameter vector theta per tile, Fig. 2a(ii)).  The optics cannot be
+ * checked on the host, so the kernels apply the same checks per tile: a tile
+ * that fails them gets all-zero transfer functions and its status
+ * (WO_ERR_OPTICS or WO_ERR_UNDERSAMPLED) as an int32 in element 4 of its row
+ * of the statistics block (0 for valid tiles); reconstructions of such a tile
+ * are zero.  Shape, pointer and workspace errors are returned as usual. */
+wo_status wo_build_tf_device(const wo_optics *d_optics, int n_tiles, int Z, int Y, int X,
+                             unsigned kinds, void *d_tf, void *d_ws, size_t ws_bytes,
+                             wo_stream stream);
 
 /* Row a5.  Forward model (Eq. fwd, Eq. fwd_block, Fourier form):
  *   d_c = IFFT3( sum_p H_cp FFT3(f_p) ) + b_c

@@ -23,6 +23,8 @@ STATUS = {0: "WO_OK", 1: "WO_ERR_ARG", 2: "WO_ERR_SHAPE", 3: "WO_ERR_UNSUPPORTED
           4: "WO_ERR_UNDERSAMPLED", 5: "WO_ERR_CUDA", 6: "WO_ERR_TIMEOUT", 7: "WO_ERR_OPTICS",
           8: "WO_ERR_WORKSPACE"}
 
+STATUS_CODES = {v: k for k, v in STATUS.items()}
+
 OPTICS_FIELDS = ("lambda_um", "n_medium", "pixel_um", "z_step_um", "na_det", "na_ill",
                  "tilt_x", "tilt_y", "defocus_um")
 
@@ -48,6 +50,7 @@ def _load():
         "wo_tf_bytes": (sz, [i, i, i, i, u]),
         "wo_workspace_bytes": (sz, [i, i, i, i, u]),
         "wo_build_tf": (i, [ctypes.POINTER(wo_optics), i, i, i, i, u, vp, vp, sz, vp]),
+        "wo_build_tf_device": (i, [vp, i, i, i, i, u, vp, vp, sz, vp]),
         "wo_forward": (i, [vp, u, vp, fp, vp, i, i, i, i, vp, sz, vp]),
         "wo_forward_adjoint": (i, [vp, u, vp, fp, vp, i, i, i, i, vp, sz, vp]),
         "wo_reconstruct": (i, [vp, u, vp, fp, fp, i, i, vp, i, i, i, i, vp, sz, vp]),
@@ -68,7 +71,8 @@ def _load():
 
 
 _lib = _load()
-EXPORTED = ("wo_size_supported", "wo_tf_bytes", "wo_workspace_bytes", "wo_build_tf", "wo_forward",
+EXPORTED = ("wo_size_supported", "wo_tf_bytes", "wo_workspace_bytes", "wo_build_tf", "wo_build_tf_device",
+            "wo_forward",
             "wo_forward_adjoint", "wo_reconstruct", "wo_reconstruct_static", "wo_tile_gather", "wo_tile_blend",
             "wo_status_string", "wo_profile_enable", "wo_profile_read", "wo_launch_count")
 
@@ -145,6 +149,19 @@ def wo_build_tf(optics_list, n_tiles, Z, Y, X, kinds, tf, ws, stream=None):
         raise ValueError("one optics entry per tile")
     _check(_lib.wo_build_tf(arr, n_tiles, Z, Y, X, kinds_mask(kinds), _ptr(tf), _ptr(ws),
                             _nbytes(ws), _stream(stream)), "wo_build_tf")
+
+
+def wo_build_tf_device(d_optics, n_tiles, Z, Y, X, kinds, tf, ws, stream=None):
+    """TF build with the optics in device memory (a float64 tensor [n_tiles, 9])."""
+    _check(_lib.wo_build_tf_device(_ptr(d_optics), n_tiles, Z, Y, X, kinds_mask(kinds), _ptr(tf), _ptr(ws),
+                                   _nbytes(ws), _stream(stream)), "wo_build_tf_device")
+
+
+def optics_tensor(optics_list, device="cuda"):
+    """Device array of optics structs (float64 [n, 9], field order of wo_optics)."""
+    import torch
+    return torch.tensor([[float(o[k]) for k in OPTICS_FIELDS] for o in optics_list], dtype=torch.float64,
+                        device=device)
 
 
 def wo_forward(tf, kinds, f, background, data, n_tiles, Z, Y, X, ws, stream=None):

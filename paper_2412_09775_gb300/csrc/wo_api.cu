@@ -115,9 +115,9 @@ static bool aligned16(const void* p) { return p && (((uintptr_t)p) & 15u) == 0; 
 // Shared memory of the z kernels: up to three volumes of Z x B columns.
 static size_t zpass_smem(int Z) {
   const int NV = 3;
-  const int B = (NV * Z * 16 * 8 <= 112 * 1024) ? 16 : (NV * Z * 8 * 8 <= 112 * 1024) ? 8
-                : (NV * Z * 4 * 8 <= 112 * 1024) ? 4 : 2;
-  return ((size_t)Z + (size_t)NV * Z * B) * sizeof(float2) + 1024 * 11 * sizeof(float);
+  int B = 16;
+  while (B > 1 && (size_t)NV * Z * B * 8 > 64 * 1024) B /= 2;
+  return ((size_t)Z + (size_t)2 * NV * Z * B) * sizeof(float2) + 1024 * 11 * sizeof(float);
 }
 
 static wo_status check_shape(int n_tiles, int Z, int Y, int X, unsigned kinds) {
@@ -227,14 +227,19 @@ int wo_profile_read(const char** names, long long* launches, double* ms, int cap
 
 long long wo_launch_count(void) { return g_launches.load(); }
 
-wo_status wo_build_tf(const wo_optics* h_optics, int n_tiles, int Z, int Y, int X, unsigned kinds,
-                      void* d_tf, void* d_ws, size_t ws_bytes, wo_stream stream) {
+// Shared body of wo_build_tf (optics copied from the host into the workspace)
+// and wo_build_tf_device (optics read in place from device memory).
+static wo_status build_tf_impl(const wo_optics* optics, bool on_host, int n_tiles, int Z, int Y, int X,
+                               unsigned kinds, void* d_tf, void* d_ws, size_t ws_bytes, wo_stream stream) {
   wo_status st = check_shape(n_tiles, Z, Y, X, kinds);
   if (st != WO_OK) return st;
-  if (!h_optics || !aligned16(d_tf) || !aligned16(d_ws)) return WO_ERR_ARG;
-  for (int t = 0; t < n_tiles; ++t) {
-    st = check_optics(h_optics[t]);
-    if (st != WO_OK) return st;
+  if (!optics || !aligned16(d_tf) || !aligned16(d_ws)) return WO_ERR_ARG;
+  if (!on_host && (((uintptr_t)optics) & 7u)) return WO_ERR_ARG;
+  if (on_host) {
+    for (int t = 0; t < n_tiles; ++t) {
+      st = check_optics(optics[t]);
+      if (st != WO_OK) return st;
+    }
   }
   const Sys s = system_of(kinds);
   const Layout L = layout_of(n_tiles, Z, Y, X, s);
@@ -243,7 +248,7 @@ wo_status wo_build_tf(const wo_optics* h_optics, int n_tiles, int Z, int Y, int 
   char* ws = (char*)d_ws;
   char* tfb = (char*)d_tf;
   TfArgs a{};
-  a.optics = (const wo_optics*)(ws + L.optics);
+  a.optics = on_host ? (const wo_optics*)(ws + L.optics) : optics;
   a.counts = (int*)(ws + L.counts);
   a.rec = (float4*)(ws + L.rec);
   a.arms = (float2*)(ws + L.arms);
@@ -253,8 +258,8 @@ wo_status wo_build_tf(const wo_optics* h_optics, int n_tiles, int Z, int Y, int 
   a.lf_props = s.lf_props;
   a.want_phase = s.want_phase; a.want_abs = s.want_abs; a.want_fl = s.has_fl;
   a.n_arms = s.n_arms; a.n_kinds = s.n_kinds;
-  WO_TRY(cudaMemcpyAsync((void*)a.optics, h_optics, (size_t)n_tiles * sizeof(wo_optics),
-                         cudaMemcpyHostToDevice, cs));
+  if (on_host)
+    WO_TRY(cudaMemcpyAsync((void*)a.optics, optics, (size_t)n_tiles * sizeof(wo_optics), cudaMemcpyHostToDevice, cs));
   WO_TRY(cudaMemsetAsync(a.counts, 0, (size_t)n_tiles * 4 * sizeof(int), cs));
   WO_TRY(cudaMemsetAsync(a.stats, 0, (size_t)n_tiles * 8 * sizeof(float), cs));
   WO_TRY(tf_pupil_record(a, cs));
@@ -265,6 +270,16 @@ wo_status wo_build_tf(const wo_optics* h_optics, int n_tiles, int Z, int Y, int 
                   "tf_ypass"));
   WO_TRY(tf_zpass(a, cs));
   return WO_OK;
+}
+
+wo_status wo_build_tf(const wo_optics* h_optics, int n_tiles, int Z, int Y, int X, unsigned kinds,
+                      void* d_tf, void* d_ws, size_t ws_bytes, wo_stream stream) {
+  return build_tf_impl(h_optics, true, n_tiles, Z, Y, X, kinds, d_tf, d_ws, ws_bytes, stream);
+}
+
+wo_status wo_build_tf_device(const wo_optics* d_optics, int n_tiles, int Z, int Y, int X, unsigned kinds,
+                             void* d_tf, void* d_ws, size_t ws_bytes, wo_stream stream) {
+  return build_tf_impl(d_optics, false, n_tiles, Z, Y, X, kinds, d_tf, d_ws, ws_bytes, stream);
 }
 
 // forward (op 0), adjoint (op 1), reconstruct (op 2)

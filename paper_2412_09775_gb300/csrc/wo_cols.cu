@@ -8,6 +8,40 @@
 
 namespace wo {
 
+// Copy an N x B column tile (element n of column b at g[n * stride + b]) to
+// shared memory [n][b], one column per thread, pointer-walked.
+template <int N, int B, int NT>
+__device__ __forceinline__ void col_tile_load(float2* buf, const float2* __restrict__ g, long long stride,
+                                              int w) {
+  constexpr int NSTEP = NT / B;
+  const int b = threadIdx.x % B, n0 = threadIdx.x / B;
+  const bool ok = b < w;
+  const float2* p = g + (long long)n0 * stride + b;
+  float2* d = buf + n0 * B + b;
+#pragma unroll 4
+  for (int n = n0; n < N; n += NSTEP) {
+    cp_async8(d, ok ? p : g, ok);
+    p += NSTEP * stride;
+    d += NSTEP * B;
+  }
+}
+
+template <int N, int B, int NT>
+__device__ __forceinline__ void col_tile_store(const float2* buf, float2* __restrict__ g, long long stride,
+                                               int w) {
+  constexpr int NSTEP = NT / B;
+  const int b = threadIdx.x % B, n0 = threadIdx.x / B;
+  if (b >= w) return;
+  float2* p = g + (long long)n0 * stride + b;
+  const float2* d = buf + n0 * B + b;
+#pragma unroll 4
+  for (int n = n0; n < N; n += NSTEP) {
+    *p = *d;
+    p += NSTEP * stride;
+    d += NSTEP * B;
+  }
+}
+
 template <int N, bool INV>
 __global__ void __launch_bounds__(ColGeom<N>::NT, ColGeom<N>::MINB)
     k_cols(float2* __restrict__ data, long long col_stride, long long plane_stride, int ncols,
@@ -23,17 +57,11 @@ __global__ void __launch_bounds__(ColGeom<N>::NT, ColGeom<N>::MINB)
   const int x0 = blockIdx.x * B;
   const int w = min(B, ncols - x0);
   float2* base = data + plane * plane_stride + x0;
-  for (int e = threadIdx.x; e < N * B; e += NT) {
-    const int n = e / B, b = e % B;
-    cp_async8(buf + e, base + (b < w ? n * col_stride + b : 0), b < w);
-  }
+  col_tile_load<N, B, NT>(buf, base, col_stride, w);
   cp_async_wait_all();
   __syncthreads();
   fft_smem<N, B, NT, INV, 1>(buf, B, 1, tw);
-  for (int e = threadIdx.x; e < N * B; e += NT) {
-    const int n = e / B, b = e % B;
-    if (b < w) base[n * col_stride + b] = buf[e];
-  }
+  col_tile_store<N, B, NT>(buf, base, col_stride, w);
 }
 
 template <int N>

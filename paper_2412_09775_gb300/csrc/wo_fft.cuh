@@ -117,9 +117,28 @@ __device__ __forceinline__ void make_twiddles(float2* tw) {
   }
 }
 
+// Shared-memory layouts: the index of element n of sequence s.
+struct LinAddr {  // n * es + s * bs
+  int es, bs;
+  __device__ __forceinline__ int operator()(int n, int s) const { return n * es + s * bs; }
+};
+// SLOTS groups of S = 2^k sequences (s = slot * S + b), each group stored
+// n-major with the sequence index XOR-swizzled by n: index
+// slot * (L * S + S) + n * S + (b ^ (n & (S - 1))).  Copies that walk n for a
+// fixed sequence and stages that walk the sequences for a fixed n both spread
+// over all banks; the extra S elements between groups shift alternate groups
+// by half the banks.
+template <int S, int L>
+struct SwzAddr {
+  __device__ __forceinline__ int operator()(int n, int s) const {
+    const int slot = s / S, b = s & (S - 1);
+    return slot * (L * S + S) + n * S + (b ^ (n & (S - 1)));
+  }
+};
+
 // One Stockham stage.  The twiddle table holds exp(-2 pi i m / (N*TWS)).
-template <int N, int R, int NS, int B, int NT, bool INV, int TWS>
-__device__ __forceinline__ void fft_stage(float2* buf, int es, int bs, const float2* tw) {
+template <int N, int R, int NS, int B, int NT, bool INV, int TWS, class A>
+__device__ __forceinline__ void fft_stage_a(float2* buf, A addr, const float2* tw) {
   constexpr int M = N / R;
   constexpr int NB = M * B;
   constexpr int PER = (NB + NT - 1) / NT;
@@ -130,7 +149,7 @@ __device__ __forceinline__ void fft_stage(float2* buf, int es, int bs, const flo
     if ((NB % NT == 0) || beta < NB) {
       const int b = beta % B, j = beta / B;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[i][r] = buf[(j + r * M) * es + b * bs];
+      for (int r = 0; r < R; ++r) v[i][r] = buf[addr(j + r * M, b)];
     }
   }
   __syncthreads();
@@ -152,20 +171,27 @@ __device__ __forceinline__ void fft_stage(float2* buf, int es, int bs, const flo
       dftR<R, INV>(v[i]);
       const int base = (j / NS) * NS * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[(base + r * NS) * es + b * bs] = v[i][r];
+      for (int r = 0; r < R; ++r) buf[addr(base + r * NS, b)] = v[i][r];
     }
   }
   __syncthreads();
 }
 
-// All stages of a length-N transform (in place, natural order in and out).
-template <int N, int B, int NT, bool INV, int TWS, int NS = 1>
-__device__ __forceinline__ void fft_smem(float2* buf, int es, int bs, const float2* tw) {
+// All stages of a length-N transform over B sequences (in place, natural
+// order in and out), any layout.
+template <int N, int B, int NT, bool INV, int TWS, class A, int NS = 1>
+__device__ __forceinline__ void fft_smem_a(float2* buf, A addr, const float2* tw) {
   if constexpr (NS < N) {
     constexpr int R = radix_for(N / NS);
-    fft_stage<N, R, NS, B, NT, INV, TWS>(buf, es, bs, tw);
-    fft_smem<N, B, NT, INV, TWS, NS * R>(buf, es, bs, tw);
+    fft_stage_a<N, R, NS, B, NT, INV, TWS>(buf, addr, tw);
+    fft_smem_a<N, B, NT, INV, TWS, A, NS * R>(buf, addr, tw);
   }
+}
+
+// Linear layout: element n of sequence b at buf[n*es + b*bs].
+template <int N, int B, int NT, bool INV, int TWS>
+__device__ __forceinline__ void fft_smem(float2* buf, int es, int bs, const float2* tw) {
+  fft_smem_a<N, B, NT, INV, TWS>(buf, LinAddr{es, bs}, tw);
 }
 
 // ------------------------------------------------------------ async copies
@@ -183,6 +209,7 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool va
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(n) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 
 // Threads for a batch of B sequences of length N at about 8 elements per
 // thread (one radix-8 butterfly per stage), a multiple of 32 in [64, 1024].
@@ -202,12 +229,14 @@ struct ColGeom {
   static constexpr size_t SMEM = (size_t)N * B * sizeof(float2) + (size_t)N * sizeof(float2);
 };
 
-// Row tiles (transforms along the contiguous axis, B rows per CTA, odd pitch).
+// Row tiles (transforms along the contiguous axis).  B rows per CTA are held
+// column-major in shared memory, element n of row b at n * P + b with the odd
+// pitch P = B + 1: the coalesced row copies (n fastest across a warp) and the
+// FFT stages (row fastest) are both free of bank conflicts.
 template <int N>
 struct RowGeom {
-  static constexpr int B = (N <= 256) ? 16 : 8;
-  static constexpr int LD = N | 1;
-  static constexpr int LD2 = (N + 1) | 1;  // raw half-spectrum rows (inverse)
+  static constexpr int B = (N <= 512) ? 16 : 8;
+  static constexpr int P = B + 1;
   static constexpr int NT = threads_for(N * B);
   static constexpr int MINB = (1536 / NT) > 1 ? (1536 / NT) : 1;
 };

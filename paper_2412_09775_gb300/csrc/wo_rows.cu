@@ -31,17 +31,17 @@ template <int N>
 __global__ void __launch_bounds__(RowGeom<N>::NT, RowGeom<N>::MINB)
     k_rows_r2c(const float* __restrict__ in, float2* __restrict__ out, long long nrows, RowBg bg) {
   using G = RowGeom<N>;
-  constexpr int B = G::B, LD = G::LD, NT = G::NT;
+  constexpr int B = G::B, P = G::P, NT = G::NT;
   extern __shared__ float2 sm[];
-  float2* buf = sm;
-  float2* tw = sm + B * LD;                            // exp(-2 pi i m / 2N), m in [0, 2N)
+  float2* buf = sm;                                   // [N][P]
+  float2* tw = sm + N * P;                            // exp(-2 pi i m / 2N), m in [0, 2N)
   float* sc = reinterpret_cast<float*>(tw + 2 * N);   // [B] background per row
   const long long row0 = (long long)blockIdx.x * B;
+  const int rows = (int)min((long long)B, nrows - row0);
+  const float2* g = reinterpret_cast<const float2*>(in + row0 * (2LL * N));
   for (int e = threadIdx.x; e < B * N; e += NT) {
     const int b = e / N, n = e - (e / N) * N;
-    const long long row = row0 + b;
-    const bool ok = row < nrows;
-    cp_async8(buf + b * LD + n, in + (ok ? row * (2LL * N) + 2 * n : 0), ok);
+    cp_async8(buf + n * P + b, b < rows ? g + b * N + n : g, b < rows);
   }
   make_twiddles<2 * N>(tw);
   row_constants(sc, in, row0, nrows, B, N, bg);
@@ -51,43 +51,45 @@ __global__ void __launch_bounds__(RowGeom<N>::NT, RowGeom<N>::MINB)
     for (int e = threadIdx.x; e < B * N; e += NT) {
       const int b = e / N, n = e - (e / N) * N;
       const float c = sc[b];
-      float2 v = buf[b * LD + n];
+      float2 v = buf[n * P + b];
       v.x -= c;
       v.y -= c;
-      buf[b * LD + n] = v;
+      buf[n * P + b] = v;
     }
     __syncthreads();
   }
-  fft_smem<N, B, NT, false, 2>(buf, 1, LD, tw);
+  fft_smem<N, B, NT, false, 2>(buf, P, 1, tw);
+  float2* o = out + row0 * (N + 1);
   for (int e = threadIdx.x; e < B * (N + 1); e += NT) {
     const int b = e / (N + 1), k = e - (e / (N + 1)) * (N + 1);
-    const long long row = row0 + b;
-    if (row >= nrows) continue;
-    const float2 zk = buf[b * LD + (k == N ? 0 : k)];
-    const float2 zc = cconj(buf[b * LD + (k == 0 ? 0 : N - k)]);
+    if (b >= rows) continue;
+    const float2 zk = buf[(k == N ? 0 : k) * P + b];
+    const float2 zc = cconj(buf[(k == 0 ? 0 : N - k) * P + b]);
     const float2 s = cadd(zk, zc);
     const float2 u = cmul(tw[k], csub(zk, zc));
-    out[row * (N + 1) + k] = make_float2(0.5f * (s.x + u.y), 0.5f * (s.y - u.x));
+    o[b * (N + 1) + k] = make_float2(0.5f * (s.x + u.y), 0.5f * (s.y - u.x));
   }
 }
 
+// The pre-processing is done in place on pairs (k, N-k): with
+// A = (X[k] + X*[N-k])/2 and B = (X[k] - X*[N-k]) e^{+i pi k/N}/2,
+// Z[k] = A + iB and Z[N-k] = A* + iB*.
 template <int N>
 __global__ void __launch_bounds__(RowGeom<N>::NT, RowGeom<N>::MINB)
     k_rows_c2r(const float2* __restrict__ in, float* __restrict__ out, long long nrows, float scale,
                RowBg bg) {
   using G = RowGeom<N>;
-  constexpr int B = G::B, LD = G::LD, LD2 = G::LD2, NT = G::NT;
+  constexpr int B = G::B, P = G::P, NT = G::NT, H = N / 2 + 1;
   extern __shared__ float2 sm[];
-  float2* raw = sm;                                     // [B][LD2] input half spectra
-  float2* buf = sm + B * LD2;                           // [B][LD] packed complex rows
-  float2* tw = buf + B * LD;
+  float2* buf = sm;                                   // [N + 1][P]
+  float2* tw = sm + (N + 1) * P;
   float* sc = reinterpret_cast<float*>(tw + 2 * N);
   const long long row0 = (long long)blockIdx.x * B;
+  const int rows = (int)min((long long)B, nrows - row0);
+  const float2* g = in + row0 * (N + 1);
   for (int e = threadIdx.x; e < B * (N + 1); e += NT) {
     const int b = e / (N + 1), k = e - (e / (N + 1)) * (N + 1);
-    const long long row = row0 + b;
-    const bool ok = row < nrows;
-    cp_async8(raw + b * LD2 + k, in + (ok ? row * (N + 1) + k : 0), ok);
+    cp_async8(buf + k * P + b, b < rows ? g + b * (N + 1) + k : g, b < rows);
   }
   make_twiddles<2 * N>(tw);
   if (threadIdx.x < B) {
@@ -96,35 +98,35 @@ __global__ void __launch_bounds__(RowGeom<N>::NT, RowGeom<N>::MINB)
   }
   cp_async_wait_all();
   __syncthreads();
-  for (int e = threadIdx.x; e < B * N; e += NT) {
-    const int b = e / N, k = e - (e / N) * N;
-    const float2 xk = raw[b * LD2 + k];
-    const float2 xc = cconj(raw[b * LD2 + N - k]);
+  for (int e = threadIdx.x; e < B * H; e += NT) {
+    const int b = e / H, k = e - (e / H) * H;
+    const float2 xk = buf[k * P + b];
+    const float2 xc = cconj(buf[(N - k) * P + b]);
     const float2 a = make_float2(0.5f * (xk.x + xc.x), 0.5f * (xk.y + xc.y));
     const float2 bb = cmul(make_float2(0.5f * (xk.x - xc.x), 0.5f * (xk.y - xc.y)), cconj(tw[k]));
-    buf[b * LD + k] = make_float2(a.x - bb.y, a.y + bb.x);
+    buf[k * P + b] = make_float2(a.x - bb.y, a.y + bb.x);
+    if (k != 0 && 2 * k != N) buf[(N - k) * P + b] = make_float2(a.x + bb.y, -a.y + bb.x);
   }
   __syncthreads();
-  fft_smem<N, B, NT, true, 2>(buf, 1, LD, tw);
+  fft_smem<N, B, NT, true, 2>(buf, P, 1, tw);
+  float2* o = reinterpret_cast<float2*>(out + row0 * (2LL * N));
   for (int e = threadIdx.x; e < B * N; e += NT) {
     const int b = e / N, n = e - (e / N) * N;
-    const long long row = row0 + b;
-    if (row >= nrows) continue;
+    if (b >= rows) continue;
     const float c = sc[b];
-    const float2 v = buf[b * LD + n];
-    reinterpret_cast<float2*>(out + row * (2LL * N))[n] = make_float2(v.x * scale + c, v.y * scale + c);
+    const float2 v = buf[n * P + b];
+    o[b * N + n] = make_float2(v.x * scale + c, v.y * scale + c);
   }
 }
 
 template <int N>
 static size_t rows_smem_r2c() {
-  return ((size_t)RowGeom<N>::B * RowGeom<N>::LD + 2 * (size_t)N) * sizeof(float2) + RowGeom<N>::B * sizeof(float);
+  return ((size_t)N * RowGeom<N>::P + 2 * (size_t)N) * sizeof(float2) + RowGeom<N>::B * sizeof(float);
 }
 
 template <int N>
 static size_t rows_smem_c2r() {
-  return ((size_t)RowGeom<N>::B * (RowGeom<N>::LD + RowGeom<N>::LD2) + 2 * (size_t)N) * sizeof(float2) +
-         RowGeom<N>::B * sizeof(float);
+  return ((size_t)(N + 1) * RowGeom<N>::P + 2 * (size_t)N) * sizeof(float2) + RowGeom<N>::B * sizeof(float);
 }
 
 template <int N>

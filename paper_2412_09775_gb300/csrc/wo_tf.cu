@@ -29,60 +29,111 @@ namespace wo {
 
 __device__ __forceinline__ int fft_index(int i, int n) { return (i < (n + 1) / 2) ? i : i - n; }
 
+// One block per RY rows of one tile.  The frequency axes are computed once per
+// block (the same IEEE divisions as the float64 reference); the mask
+// predicates are exact float64 products and sums in the reference's order.
+// eta = sqrt(k_m^2 - |nu|^2) takes a float seed and one float64 Newton
+// correction (relative error ~1e-14, far below the float phase resolution).
+constexpr int kRecRows = 8;
+
+// Device-side copy of the host validation (wo_api.cu check_optics) for optics
+// that live in device memory: 0 if valid, else the wo_status code.
+__device__ int optics_status(const wo_optics& o) {
+  const double v[9] = {o.lambda_um, o.n_medium, o.pixel_um, o.z_step_um, o.na_det,
+                       o.na_ill, o.tilt_x, o.tilt_y, o.defocus_um};
+  for (int i = 0; i < 9; ++i)
+    if (!isfinite(v[i])) return WO_ERR_OPTICS;
+  if (o.lambda_um <= 0 || o.n_medium <= 0 || o.pixel_um <= 0 || o.z_step_um <= 0) return WO_ERR_OPTICS;
+  if (o.na_det <= 0 || o.na_det >= o.n_medium) return WO_ERR_OPTICS;
+  const double tilt = sqrt(o.tilt_x * o.tilt_x + o.tilt_y * o.tilt_y);
+  if (o.na_ill < 0 || o.na_ill + tilt > o.n_medium) return WO_ERR_OPTICS;
+  if ((o.na_det + o.na_ill + tilt) / o.lambda_um >= 1.0 / (2.0 * o.pixel_um)) return WO_ERR_UNDERSAMPLED;
+  const double s = o.na_det / o.n_medium;
+  if ((o.n_medium / o.lambda_um) * (1.0 - sqrt(1.0 - s * s)) >= 1.0 / (2.0 * o.z_step_um)) return WO_ERR_UNDERSAMPLED;
+  return WO_OK;
+}
+
 __global__ void __launch_bounds__(256)
     k_pupil_record(const wo_optics* __restrict__ optics, float4* __restrict__ rec, int* __restrict__ counts,
-                   int Y, int X) {
+                   float* __restrict__ stats, int Y, int X) {
+  extern __shared__ double nu_x[];  // [X]
+  __shared__ double nu_y[kRecRows];
+  __shared__ int part[2][8];
   const int t = blockIdx.y;
-  const int idx = blockIdx.x * 256 + threadIdx.x;
-  int n_sp = 0, n_p = 0;
-  if (idx < Y * X) {
-    const wo_optics o = optics[t];
-    const int y = idx / X, x = idx - (idx / X) * X;
-    const double nu_y = __ddiv_rn((double)fft_index(y, Y), __dmul_rn((double)Y, o.pixel_um));
-    const double nu_x = __ddiv_rn((double)fft_index(x, X), __dmul_rn((double)X, o.pixel_um));
-    const double lam = o.lambda_um;
-    // detection pupil: |nu| <= NA_det / lambda
-    const double rp = __ddiv_rn(o.na_det, lam);
-    const double r2 = __dadd_rn(__dmul_rn(nu_x, nu_x), __dmul_rn(nu_y, nu_y));
-    const bool P = r2 <= __dmul_rn(rp, rp);
-    // source pupil: |nu - t/lambda| <= NA_ill / lambda
-    const double cy = __ddiv_rn(o.tilt_y, lam), cx = __ddiv_rn(o.tilt_x, lam);
-    const double dy = __dsub_rn(nu_y, cy), dx = __dsub_rn(nu_x, cx);
-    const double rs = __ddiv_rn(o.na_ill, lam);
-    const bool S = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) <= __dmul_rn(rs, rs);
-    const double km = __ddiv_rn(o.n_medium, lam);
-    const double e2 = __dsub_rn(__dmul_rn(km, km), r2);
-    const double eta = __dsqrt_rn(e2 > 0.0 ? e2 : 0.0);
-    const float eh = __double2float_rn(eta);
-    const float el = __double2float_rn(__dsub_rn(eta, (double)eh));
-    const float binv = (P && eta > 0.0) ? __double2float_rn(__drcp_rn(eta)) : 0.f;
-    rec[(long long)t * Y * X + idx] = make_float4(eh, el, binv, (S && P) ? 1.f : 0.f);
-    n_sp = (S && P) ? 1 : 0;
-    n_p = P ? 1 : 0;
+  const int y0 = blockIdx.x * kRecRows;
+  const wo_optics o = optics[t];
+  // Invalid optics (possible only when they come from device memory): the
+  // tile's record is all zero, so its transfer functions are zero, and its
+  // status is left in the statistics block.
+  const int status = optics_status(o);
+  if (status != WO_OK) {
+    for (int e = threadIdx.x; e < kRecRows * X; e += 256) {
+      const int yy = e / X;
+      if (y0 + yy < Y) rec[((long long)t * Y + y0 + yy) * X + (e - yy * X)] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) reinterpret_cast<int*>(stats)[(long long)t * 8 + 4] = status;
+    return;  // uniform across the block
+  }
+  const double px = __dmul_rn((double)X, o.pixel_um), py = __dmul_rn((double)Y, o.pixel_um);
+  for (int x = threadIdx.x; x < X; x += 256) nu_x[x] = __ddiv_rn((double)fft_index(x, X), px);
+  if (threadIdx.x < kRecRows && y0 + threadIdx.x < Y)
+    nu_y[threadIdx.x] = __ddiv_rn((double)fft_index(y0 + threadIdx.x, Y), py);
+  __syncthreads();
+  const double lam = o.lambda_um;
+  const double rp = __ddiv_rn(o.na_det, lam), rp2 = __dmul_rn(rp, rp);
+  const double cy = __ddiv_rn(o.tilt_y, lam), cx = __ddiv_rn(o.tilt_x, lam);
+  const double rs = __ddiv_rn(o.na_ill, lam), rs2 = __dmul_rn(rs, rs);
+  const double km = __ddiv_rn(o.n_medium, lam), km2 = __dmul_rn(km, km);
+  int n_sp = 0, n_p = 0, kx_band = -1;
+  const int rows = min(kRecRows, Y - y0);
+  for (int e = threadIdx.x; e < rows * X; e += 256) {
+    const int yy = e / X, x = e - (e / X) * X;
+    const double vy = nu_y[yy], vx = nu_x[x];
+    const double r2 = __dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy));
+    const bool P = r2 <= rp2;
+    const double dy = __dsub_rn(vy, cy), dx = __dsub_rn(vx, cx);
+    const bool S = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) <= rs2;
+    const double e2 = __dsub_rn(km2, r2);
+    float eh = 0.f, el = 0.f, binv = 0.f;
+    if (e2 > 0.0) {
+      const float s0 = sqrtf((float)e2);
+      const double rem = fma(-(double)s0, (double)s0, e2);
+      const double eta = (double)s0 + (double)((float)rem * (0.5f / s0));
+      eh = __double2float_rn(eta);
+      el = __double2float_rn(__dsub_rn(eta, (double)eh));
+      binv = P ? 1.0f / eh : 0.f;
+    }
+    rec[((long long)t * Y + y0 + yy) * X + x] = make_float4(eh, el, binv, (S && P) ? 1.f : 0.f);
+    n_sp += (S && P) ? 1 : 0;
+    n_p += P ? 1 : 0;
     // band limit along x: the largest |k_x| inside P on the k_y = 0 row.  P is
     // contained in nu_x^2 <= (NA_det/lambda)^2, so every column beyond it is
     // zero in every arm.
-    if (y == 0 && P) atomicMax(&counts[4 * t + 2], abs(fft_index(x, X)));
+    if (y0 + yy == 0 && P) kx_band = max(kx_band, abs(fft_index(x, X)));
   }
   for (int off = 16; off > 0; off >>= 1) {
     n_sp += __shfl_down_sync(0xffffffffu, n_sp, off);
     n_p += __shfl_down_sync(0xffffffffu, n_p, off);
+    kx_band = max(kx_band, __shfl_down_sync(0xffffffffu, kx_band, off));
   }
-  __shared__ int part[2][8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ int band[8];
   if (lane == 0) {
     part[0][warp] = n_sp;
     part[1][warp] = n_p;
+    band[warp] = kx_band;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    int a = 0, b = 0;
+    int a = 0, b = 0, k = -1;
     for (int i = 0; i < 8; ++i) {
       a += part[0][i];
       b += part[1][i];
+      k = max(k, band[i]);
     }
     if (a) atomicAdd(&counts[4 * t], a);
     if (b) atomicAdd(&counts[4 * t + 1], b);
+    if (k >= 0) atomicMax(&counts[4 * t + 2], k);
   }
 }
 
@@ -155,45 +206,13 @@ __global__ void __launch_bounds__(ColGeom<N>::NT, (1024 / ColGeom<N>::NT) > 1 ? 
 
 template <int NX>
 struct PsfGeom {
-  static constexpr int B = (NX <= 128) ? 16 : (NX <= 1024) ? 8 : 4;
-  static constexpr int LD = NX + 1;
+  static constexpr int B = (NX <= 1024) ? 8 : 4;  // rows per CTA (a power of two: the swizzle width)
   static constexpr int NT = threads_for(NX * B);
-  static constexpr int MINB = (1536 / NT) > 1 ? (1536 / NT) : 1;
-  static constexpr size_t SMEM = (2 * (size_t)B * LD + NX + 2 * B) * sizeof(float2);
+  static constexpr int MINB = (1024 / NT) > 1 ? (1024 / NT) : 1;
+  static constexpr int SLOT = NX * B + B;  // elements per arm slot
+  // three arm slots, twiddles, per-row constants
+  static constexpr size_t SMEM = ((size_t)3 * SLOT + NX + 2 * B) * sizeof(float2);
 };
-
-// Real row h (given through `val`) -> half spectrum written to dst rows.
-template <int NX, int B, int NT, class F>
-__device__ __forceinline__ void psf_r2c_rows(float2* src, float2* pack, const float2* tw, F val,
-                                             float2* __restrict__ tf, long long row0, long long nrows,
-                                             const TfArgs& a, int slot) {
-  constexpr int H = NX / 2, LD = NX + 1;
-  const int Z = a.Z, Y = a.Y, Xh = H + 1;
-  for (int e = threadIdx.x; e < B * H; e += NT) {
-    const int b = e / H, m = e - (e / H) * H;
-    const long long row = row0 + b;
-    float2 z = make_float2(0.f, 0.f);
-    if (row < nrows) z = make_float2(val(src[b * LD + 2 * m], b), val(src[b * LD + 2 * m + 1], b));
-    pack[b * LD + m] = z;
-  }
-  __syncthreads();
-  fft_smem<H, B, NT, false, 2>(pack, 1, LD, tw);
-  for (int e = threadIdx.x; e < B * (H + 1); e += NT) {
-    const int b = e / (H + 1), k = e - (e / (H + 1)) * (H + 1);
-    const long long row = row0 + b;
-    if (row >= nrows) continue;
-    const float2 zk = pack[b * LD + (k == H ? 0 : k)];
-    const float2 zc = cconj(pack[b * LD + (k == 0 ? 0 : H - k)]);
-    const float2 s = cadd(zk, zc);
-    const float2 u = cmul(tw[k], csub(zk, zc));
-    const long long plane = row / Y;  // t*Z + j
-    const int y = (int)(row - plane * Y);
-    const long long t = plane / Z, j = plane - (plane / Z) * Z;
-    tf[(((t * a.n_kinds + slot) * Z + j) * Y + y) * Xh + k] =
-        make_float2(0.5f * (s.x + u.y), 0.5f * (s.y - u.x));
-  }
-  __syncthreads();
-}
 
 __device__ __forceinline__ float lf_scale(const TfArgs& a, int t) {
   // 2K = 2 c / (N_perp sum S P^2), c = 2 pi n dz / lambda^2
@@ -210,18 +229,30 @@ __device__ __forceinline__ float fl_scale(const TfArgs& a, int t) {
   return (float)(1.0 / ((double)a.Y * (double)a.X * (double)a.Z * (double)n_p));
 }
 
+// Per row (tile t, plane j, row y) of the arms after their y transform:
+// inverse transform along x of every arm, then the PSF rows and their forward
+// transform along x.  The label-free PSFs are the real and imaginary parts of
+// g = 2K conj(a) b, so one complex transform G of g gives both rows:
+//   H_re(k) = (G(k) + G*(-k)) / 2,   H_im(k) = i (G(k) - G*(-k)) / 2.
+// The fluorescence PSF |p|^2 / (N_perp Z sum P^2) is transformed as a complex
+// row with zero imaginary part.  Each arm's B rows sit in their own slot,
+// element n of row b at n * B + (b ^ (n & (B-1))) (SwzAddr): the coalesced
+// row copies and the transform stages are both free of bank conflicts.
 template <int NX>
 __global__ void __launch_bounds__(PsfGeom<NX>::NT, PsfGeom<NX>::MINB) k_psf_rows(TfArgs a) {
   using G = PsfGeom<NX>;
-  constexpr int B = G::B, LD = G::LD, NT = G::NT;
+  constexpr int B = G::B, NT = G::NT, H = NX / 2, SLOT = G::SLOT;
+  using Addr = SwzAddr<B, NX>;
+  const Addr addr{};
   extern __shared__ float2 sm[];
-  float2* bufA = sm;
-  float2* bufB = sm + B * LD;
-  float2* tw = sm + 2 * B * LD;  // exp(-2 pi i m / NX)
-  float* sc = reinterpret_cast<float*>(tw + NX);  // per row: [B] label-free 2K, [B] fluorescence
-  int* kxm = reinterpret_cast<int*>(sc + 2 * B);   // per row: x band limit of its tile
+  float2* buf = sm;                              // [3][SLOT]
+  float2* tw = sm + 3 * SLOT;                    // exp(-2 pi i m / NX)
+  float* sc = reinterpret_cast<float*>(tw + NX); // [B] label-free 2K, [B] fluorescence scale
+  int* kxm = reinterpret_cast<int*>(sc + 2 * B); // [B] x band limit of the row's tile
   const long long nrows = (long long)a.n_tiles * a.Z * a.Y;
   const long long row0 = (long long)blockIdx.x * B;
+  const int na = a.n_arms;
+  const bool lf = a.lf_props > 0, fl = a.want_fl != 0;
   if (threadIdx.x < B) {
     const long long row = row0 + threadIdx.x;
     const int t = (int)((row < nrows ? row : nrows - 1) / ((long long)a.Z * a.Y));
@@ -230,55 +261,57 @@ __global__ void __launch_bounds__(PsfGeom<NX>::NT, PsfGeom<NX>::MINB) k_psf_rows
     kxm[threadIdx.x] = row < nrows ? a.counts[4 * t + 2] : -1;
   }
   __syncthreads();
-  const long long plane_elems = (long long)a.Y * NX;  // elements of one arm plane
+  const long long plane_elems = (long long)a.Y * NX;
   // columns outside the detection band are zero (and were never written)
-  auto load_arm = [&](float2* dst, int arm) {
-    for (int e = threadIdx.x; e < B * NX; e += NT) {
-      const int b = e / NX, n = e - (e / NX) * NX;
-      const long long row = row0 + b;
-      const bool ok = row < nrows && abs(fft_index(n, NX)) <= kxm[b];
-      const float2* src = a.arms;
-      if (ok) {
-        const long long t = row / ((long long)a.Z * a.Y);
-        const long long rem = row - t * a.Z * a.Y;  // j*Y + y
-        src = a.arms + ((t * a.n_arms + arm) * a.Z) * plane_elems + rem * NX + n;
-      }
-      cp_async8(dst + b * LD + n, src, ok);
+  for (int e = threadIdx.x; e < na * B * NX; e += NT) {
+    const int q = e / NX, n = e - (e / NX) * NX;  // q = arm * B + b
+    const int arm = q / B, b = q - (q / B) * B;
+    const long long row = row0 + b;
+    const bool ok = abs(fft_index(n, NX)) <= kxm[b];
+    const float2* src = a.arms;
+    if (ok) {
+      const long long t = row / ((long long)a.Z * a.Y);
+      const long long rem = row - t * a.Z * a.Y;  // j*Y + y
+      src = a.arms + ((t * na + arm) * a.Z) * plane_elems + rem * NX + n;
     }
-  };
-  make_twiddles<NX>(tw);
-  int arm = 0;
-  if (a.lf_props > 0) {
-    load_arm(bufA, 0);
-    load_arm(bufB, 1);
-    cp_async_wait_all();
-    __syncthreads();
-    fft_smem<NX, B, NT, true, 1>(bufA, 1, LD, tw);
-    fft_smem<NX, B, NT, true, 1>(bufB, 1, LD, tw);
-    for (int e = threadIdx.x; e < B * NX; e += NT) {
-      const int b = e / NX, n = e - (e / NX) * NX;
-      bufA[b * LD + n] = cmulc(bufA[b * LD + n], bufB[b * LD + n]);  // g = conj(a) b
-    }
-    __syncthreads();
-    int slot = 0;
-    if (a.want_phase) {
-      psf_r2c_rows<NX, B, NT>(bufA, bufB, tw, [&](float2 g, int b) { return sc[b] * g.x; },
-                              a.tf, row0, nrows, a, slot);
-      ++slot;
-    }
-    if (a.want_abs) {
-      psf_r2c_rows<NX, B, NT>(bufA, bufB, tw, [&](float2 g, int b) { return -sc[b] * g.y; },
-                              a.tf, row0, nrows, a, slot);
-    }
-    arm = 2;
+    cp_async8(buf + addr(n, q), src, ok);
   }
-  if (a.want_fl) {
-    load_arm(bufA, arm);
-    cp_async_wait_all();
-    __syncthreads();
-    fft_smem<NX, B, NT, true, 1>(bufA, 1, LD, tw);
-    psf_r2c_rows<NX, B, NT>(bufA, bufB, tw, [&](float2 p, int b) { return sc[B + b] * cabs2(p); },
-                            a.tf, row0, nrows, a, a.lf_props);
+  make_twiddles<NX>(tw);
+  cp_async_wait_all();
+  __syncthreads();
+  for (int arm = 0; arm < na; ++arm) fft_smem_a<NX, B, NT, true, 1>(buf + arm * SLOT, addr, tw);
+  // PSF rows: slot 0 <- 2K conj(a) b (label-free), slot fl_dst <- fluorescence
+  const int fl_src = lf ? 2 : 0, fl_dst = lf ? 1 : 0;
+  for (int e = threadIdx.x; e < B * NX; e += NT) {
+    const int n = e / B, b = e - (e / B) * B;
+    const int i = addr(n, b);  // same position in every slot
+    if (lf) buf[i] = cscale(cmulc(buf[i], buf[SLOT + i]), sc[b]);
+    if (fl) {
+      const float2 p = buf[fl_src * SLOT + i];
+      buf[fl_dst * SLOT + i] = make_float2(sc[B + b] * cabs2(p), 0.f);
+    }
+  }
+  __syncthreads();
+  const int nf = (lf ? 1 : 0) + (fl ? 1 : 0);
+  for (int sl = 0; sl < nf; ++sl) fft_smem_a<NX, B, NT, false, 1>(buf + sl * SLOT, addr, tw);
+  const int Z = a.Z, Y = a.Y, Xh = H + 1;
+  for (int e = threadIdx.x; e < B * Xh; e += NT) {
+    const int b = e / Xh, k = e - (e / Xh) * Xh;
+    const long long row = row0 + b;
+    if (row >= nrows) continue;
+    const long long plane = row / Y;  // t*Z + j
+    const int y = (int)(row - plane * Y);
+    const long long t = plane / Z, j = plane - (plane / Z) * Z;
+    float2* dst = a.tf + ((t * a.n_kinds * Z + j) * Y + y) * Xh + k;  // slot 0 of this row
+    const long long kstride = (long long)Z * Y * Xh;
+    int slot = 0;
+    if (lf) {
+      const float2 gk = buf[addr(k, b)];
+      const float2 gc = cconj(buf[addr(k == 0 ? 0 : NX - k, b)]);
+      if (a.want_phase) dst[(slot++) * kstride] = make_float2(0.5f * (gk.x + gc.x), 0.5f * (gk.y + gc.y));
+      if (a.want_abs) dst[(slot++) * kstride] = make_float2(-0.5f * (gk.y - gc.y), 0.5f * (gk.x - gc.x));
+    }
+    if (fl) dst[slot * kstride] = buf[fl_dst * SLOT + addr(k, b)];
   }
 }
 
@@ -319,11 +352,7 @@ __global__ void __launch_bounds__(ZGeom<N, NK>::NT, ZGeom<N, NK>::MINB) k_tf_zpa
       }
     }
   }
-  for (int e = threadIdx.x; e < NK * N * B; e += NT) {
-    const int v = e / (N * B), r = e - v * (N * B);
-    const int n = r / B, bb = r % B;
-    if (bb < w) base[v * vol + n * zs + bb] = buf[(n * NK + v) * B + bb];
-  }
+  store_zcols<N, NK, B, NT>(buf, base, NK, vol, zs, w);
   red[2 * threadIdx.x] = col_lf;
   red[2 * threadIdx.x + 1] = col_fl;
   __syncthreads();
@@ -334,25 +363,35 @@ __global__ void __launch_bounds__(ZGeom<N, NK>::NT, ZGeom<N, NK>::MINB) k_tf_zpa
       m2_fl += red[2 * (q * B + threadIdx.x) + 1];
     }
   }
-  // block maxima (values are >= 0, so integer order equals float order)
+  // block maxima (values are >= 0, so integer order equals float order):
+  // warp shuffles, then one atomic per statistic per CTA
   for (int off = 16; off > 0; off >>= 1) {
     m3_lf = fmaxf(m3_lf, __shfl_down_sync(0xffffffffu, m3_lf, off));
     m3_fl = fmaxf(m3_fl, __shfl_down_sync(0xffffffffu, m3_fl, off));
     m2_lf = fmaxf(m2_lf, __shfl_down_sync(0xffffffffu, m2_lf, off));
     m2_fl = fmaxf(m2_fl, __shfl_down_sync(0xffffffffu, m2_fl, off));
   }
-  if ((threadIdx.x & 31) == 0) {
-    int* st = reinterpret_cast<int*>(a.stats + (long long)t * 8);
-    if (m3_lf > 0.f) atomicMax(st + 0, __float_as_int(m3_lf));
-    if (m2_lf > 0.f) atomicMax(st + 1, __float_as_int(m2_lf));
-    if (m3_fl > 0.f) atomicMax(st + 2, __float_as_int(m3_fl));
-    if (m2_fl > 0.f) atomicMax(st + 3, __float_as_int(m2_fl));
+  __syncthreads();  // red[] is reused below
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[4 * warp + 0] = m3_lf;
+    red[4 * warp + 1] = m2_lf;
+    red[4 * warp + 2] = m3_fl;
+    red[4 * warp + 3] = m2_fl;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    float m = 0.f;
+    for (int q = 0; q < NT / 32; ++q) m = fmaxf(m, red[4 * q + threadIdx.x]);
+    if (m > 0.f) atomicMax(reinterpret_cast<int*>(a.stats + (long long)t * 8) + threadIdx.x, __float_as_int(m));
   }
 }
 
 cudaError_t tf_pupil_record(const TfArgs& a, cudaStream_t s) {
-  dim3 grid((unsigned)((a.Y * a.X + 255) / 256), (unsigned)a.n_tiles);
-  WO_LAUNCH("tf_pupil_record", s, (k_pupil_record<<<grid, 256, 0, s>>>(a.optics, a.rec, a.counts, a.Y, a.X)));
+  dim3 grid((unsigned)((a.Y + kRecRows - 1) / kRecRows), (unsigned)a.n_tiles);
+  const size_t smem = (size_t)a.X * sizeof(double);
+  WO_LAUNCH("tf_pupil_record", s,
+            (k_pupil_record<<<grid, 256, smem, s>>>(a.optics, a.rec, a.counts, a.stats, a.Y, a.X)));
   return cudaGetLastError();
 }
 

@@ -23,10 +23,11 @@
 namespace wo {
 
 __host__ __device__ constexpr int z_cols(int N, int NV) {
-  return (NV * N * 16 * 8 <= 112 * 1024) ? 16
-         : (NV * N * 8 * 8 <= 112 * 1024) ? 8
-         : (NV * N * 4 * 8 <= 112 * 1024) ? 4
-                                         : 2;
+  return (NV * N * 16 * 8 <= 64 * 1024) ? 16
+         : (NV * N * 8 * 8 <= 64 * 1024) ? 8
+         : (NV * N * 4 * 8 <= 64 * 1024) ? 4
+         : (NV * N * 2 * 8 <= 64 * 1024) ? 2
+                                        : 1;
 }
 
 template <int N, int NV>
@@ -35,18 +36,49 @@ struct ZGeom {
   static constexpr int NT = threads_for(NV * N * B);
   static constexpr int MINB = (1536 / NT) > 1 ? (1536 / NT) : 1;
   static constexpr size_t SMEM = ((size_t)N + (size_t)NV * N * B) * sizeof(float2);
+  // fused pass: plus up to three transfer functions of N x B prefetched
+  static constexpr size_t SMEM_TF = SMEM + (size_t)3 * N * B * sizeof(float2);
 };
 
 __device__ __forceinline__ float2 sel3(int i, float2 a, float2 b, float2 c) { return i == 0 ? a : (i == 1 ? b : c); }
 
-// Copy the z columns of `nv` volumes into slots [n][v][b] of the tile.
+// Copy the z columns of `nv` volumes into slots [n][v][b] of the tile.  Each
+// thread keeps one column b (NT is a multiple of B) and walks n with a
+// pointer increment, so a copy costs a handful of instructions.
 template <int N, int NV, int B, int NT>
 __device__ __forceinline__ void load_zcols(float2* buf, const float2* __restrict__ src, int nv,
                                            long long vol, long long zs, int w) {
-  for (int e = threadIdx.x; e < nv * N * B; e += NT) {
-    const int v = e / (N * B), r = e - v * (N * B);
-    const int n = r / B, b = r % B;
-    cp_async8(buf + (n * NV + v) * B + b, src + (b < w ? v * vol + n * zs + b : 0), b < w);
+  constexpr int NSTEP = NT / B;
+  const int b = threadIdx.x % B, n0 = threadIdx.x / B;
+  const bool ok = b < w;
+  for (int v = 0; v < nv; ++v) {
+    const float2* g = src + v * vol + (long long)n0 * zs + b;
+    float2* d = buf + (n0 * NV + v) * B + b;
+#pragma unroll 4
+    for (int n = n0; n < N; n += NSTEP) {
+      cp_async8(d, ok ? g : src, ok);
+      g += NSTEP * zs;
+      d += NSTEP * NV * B;
+    }
+  }
+}
+
+// Store slots [n][v][b] of the tile to the z columns of `nv` volumes.
+template <int N, int NV, int B, int NT>
+__device__ __forceinline__ void store_zcols(const float2* buf, float2* __restrict__ dst, int nv, long long vol,
+                                            long long zs, int w) {
+  constexpr int NSTEP = NT / B;
+  const int b = threadIdx.x % B, n0 = threadIdx.x / B;
+  if (b >= w) return;
+  for (int v = 0; v < nv; ++v) {
+    float2* g = dst + v * vol + (long long)n0 * zs + b;
+    const float2* d = buf + (n0 * NV + v) * B + b;
+#pragma unroll 4
+    for (int n = n0; n < N; n += NSTEP) {
+      *g = *d;
+      g += NSTEP * zs;
+      d += NSTEP * NV * B;
+    }
   }
 }
 
@@ -60,12 +92,15 @@ __global__ void __launch_bounds__(ZGeom<N, (NI > NO ? NI : NO)>::NT, ZGeom<N, (N
   extern __shared__ float2 sm[];
   float2* tw = sm;
   float2* buf = sm + N;
+  float2* htf = buf + NV * N * B;  // [n][kind][b] transfer functions, prefetched
   const int t = blockIdx.z, y = blockIdx.y, x0 = blockIdx.x * B;
   const int w = min(B, Xh - x0);
   const long long zs = (long long)Y * Xh;
   const long long vol = (long long)N * zs;
   const long long col = (long long)y * Xh + x0;
+  const int ntf = op.n_tf;
   load_zcols<N, NV, B, NT>(buf, in + (long long)t * NI * vol + col, NI, vol, zs, w);
+  load_zcols<N, 3, B, NT>(htf, tf + (long long)t * ntf * vol + col, ntf, vol, zs, w);
   make_twiddles<N>(tw);
   cp_async_wait_all();
   __syncthreads();
@@ -77,17 +112,17 @@ __global__ void __launch_bounds__(ZGeom<N, (NI > NO ? NI : NO)>::NT, ZGeom<N, (N
   const int L = op.lf_props;
   const float2 zero = make_float2(0.f, 0.f);
   for (int e = threadIdx.x; e < N * B; e += NT) {
-    const int k = e / B, b = e % B;
+    const int k = e / B, b = e % B;  // B is a power of two: shifts
     float2* cell = buf + k * NV * B + b;  // slot v at cell[v * B]
     float2 y0 = zero, y1 = zero, y2 = zero;
     if (b < w) {
       const float2 x0v = cell[0];
       const float2 x1v = NI > 1 ? cell[B] : zero;
       const float2 x2v = NI > 2 ? cell[2 * B] : zero;
-      const float2* h = tf + ((long long)t * op.n_tf * N + k) * zs + col + b;
+      const float2* h = htf + k * 3 * B + b;
       float2 H[3];
 #pragma unroll
-      for (int s = 0; s < 3; ++s) H[s] = (s < op.n_tf) ? __ldg(h + s * vol) : zero;
+      for (int s = 0; s < 3; ++s) H[s] = (s < ntf) ? h[s * B] : zero;
       if (op.op == 0) {  // forward: props in, channels out
         if (L > 0) {
           float2 d = cmul(H[0], x0v);
@@ -114,13 +149,14 @@ __global__ void __launch_bounds__(ZGeom<N, (NI > NO ? NI : NO)>::NT, ZGeom<N, (N
           const float2 d = dc ? zero : sel3(op.lf_chan, x0v, x1v, x2v);
           float den = lam_lf + cabs2(H[0]);
           if (L > 1) den += cabs2(H[1]);
-          const float inv = 1.0f / den;
+          const float inv = den > 0.f ? 1.0f / den : 0.f;  // zero TF and eta: minimum norm
           y0 = cscale(cmulc(H[0], d), inv);
           if (L > 1) y1 = cscale(cmulc(H[1], d), inv);
         }
         if (op.has_fl) {
           const float2 d = dc ? zero : sel3(op.fl_chan, x0v, x1v, x2v);
-          const float2 f = cscale(cmulc(H[L], d), 1.0f / (lam_fl + cabs2(H[L])));
+          const float den = lam_fl + cabs2(H[L]);
+          const float2 f = cscale(cmulc(H[L], d), den > 0.f ? 1.0f / den : 0.f);
           if (L == 0) y0 = f; else if (L == 1) y1 = f; else y2 = f;
         }
       }
@@ -131,12 +167,7 @@ __global__ void __launch_bounds__(ZGeom<N, (NI > NO ? NI : NO)>::NT, ZGeom<N, (N
   }
   __syncthreads();
   fft_smem<N, NO * B, NT, true, 1>(buf, NV * B, 1, tw);
-  float2* dst = out + (long long)t * NO * vol + col;
-  for (int e = threadIdx.x; e < NO * N * B; e += NT) {
-    const int v = e / (N * B), r = e - v * (N * B);
-    const int n = r / B, b = r % B;
-    if (b < w) dst[v * vol + n * zs + b] = buf[(n * NV + v) * B + b];
-  }
+  store_zcols<N, NV, B, NT>(buf, out + (long long)t * NO * vol + col, NO, vol, zs, w);
 }
 
 // 2D: out[t][p][y][x] = (sum_k H_k^H H_k + lam I)^-1 sum_k H_k^H D_k per mode.
@@ -211,12 +242,14 @@ __global__ void __launch_bounds__(ZGeom<N, NI>::NT, ZGeom<N, NI>::MINB)
       const float lam = op.eta_absolute ? op.eta_lf * (float)N : op.eta_lf * st[1];
       const float2 r0 = make_float2(acc[4], acc[5]);
       if (L == 1) {
-        o[0] = cscale(r0, 1.0f / (acc[0] + lam));
+        const float den = acc[0] + lam;
+        o[0] = cscale(r0, den > 0.f ? 1.0f / den : 0.f);
       } else {
         const float a = acc[0] + lam, d = acc[1] + lam;
         const float2 m = make_float2(acc[2], acc[3]);
         const float2 r1 = make_float2(acc[6], acc[7]);
-        const float inv = 1.0f / (a * d - cabs2(m));
+        const float det = a * d - cabs2(m);
+        const float inv = det > 0.f ? 1.0f / det : 0.f;
         const float2 f0 = csub(cscale(r0, d), cmul(m, r1));
         const float2 f1 = csub(cscale(r1, a), cmulc(m, r0));
         o[0] = cscale(f0, inv);
@@ -225,7 +258,8 @@ __global__ void __launch_bounds__(ZGeom<N, NI>::NT, ZGeom<N, NI>::MINB)
     }
     if (op.has_fl) {
       const float lam = op.eta_absolute ? op.eta_fl * (float)N : op.eta_fl * st[3];
-      o[L * plane] = cscale(make_float2(acc[9], acc[10]), 1.0f / (acc[8] + lam));
+      const float den = acc[8] + lam;
+      o[L * plane] = cscale(make_float2(acc[9], acc[10]), den > 0.f ? 1.0f / den : 0.f);
     }
   }
 }
@@ -235,10 +269,10 @@ cudaError_t launch_z_fused(const float2* in, float2* out, const float2* tf, ZOp 
                            cudaStream_t s) {
   constexpr int NV = NI > NO ? NI : NO;
   using G = ZGeom<N, NV>;
-  static cudaError_t attr = allow_smem(k_z_fused<N, NI, NO>, G::SMEM);
+  static cudaError_t attr = allow_smem(k_z_fused<N, NI, NO>, G::SMEM_TF);
   if (attr != cudaSuccess) return attr;
   dim3 grid((unsigned)((Xh + G::B - 1) / G::B), (unsigned)Y, (unsigned)n_tiles);
-  WO_LAUNCH("z_fused", s, (k_z_fused<N, NI, NO><<<grid, G::NT, G::SMEM, s>>>(in, out, tf, op, Y, Xh)));
+  WO_LAUNCH("z_fused", s, (k_z_fused<N, NI, NO><<<grid, G::NT, G::SMEM_TF, s>>>(in, out, tf, op, Y, Xh)));
   return cudaGetLastError();
 }
 

@@ -341,3 +341,80 @@ def test_launch_counter_and_profiler(env):
     assert B.wo_launch_count() - n0 >= 5
     assert {"tf_pupil_record", "tf_arms", "tf_psf_rows", "tf_ypass", "tf_zpass"} <= set(prof)
     assert all(ms > 0 for _, ms in prof.values())
+
+
+# ------------------------------------------- device optics, graph capture
+def test_build_tf_device_matches_host_and_flags_bad_tiles(env):
+    B, torch, dev = env
+    shape = (8, 32, 48)
+    Z, Y, X = shape
+    good = ph.tile_optics(np.random.default_rng(5), 2)
+    bad = dict(good[0], na_det=1.4)          # NA_det > n: invalid
+    under = dict(good[0], pixel_um=0.2)       # pupil correlation aliases
+    optics = [good[0], bad, good[1], under]
+    tf_h, ws = B.alloc(2, Z, Y, X, OO.KINDS, dev)
+    B.wo_build_tf(good, 2, Z, Y, X, OO.KINDS, tf_h, ws)
+    tf_d, ws4 = B.alloc(4, Z, Y, X, OO.KINDS, dev)
+    B.wo_build_tf_device(B.optics_tensor(optics, dev), 4, Z, Y, X, OO.KINDS, tf_d, ws4)
+    torch.cuda.synchronize()
+    sh, sth = B.tf_views(tf_h, 2, Z, Y, X, OO.KINDS)
+    sd, std_ = B.tf_views(tf_d, 4, Z, Y, X, OO.KINDS)
+    assert torch.equal(sd[0], sh[0]) and torch.equal(sd[2], sh[1])
+    assert torch.count_nonzero(sd[1]) == 0 and torch.count_nonzero(sd[3]) == 0
+    status = std_.view(torch.int32)[:, 4].cpu().tolist()
+    assert status == [0, B.STATUS_CODES["WO_ERR_OPTICS"], 0, B.STATUS_CODES["WO_ERR_UNDERSAMPLED"]]
+    # reconstruction of a flagged tile is zero, the others match the host bank
+    d = torch.from_numpy(ph.uniform_volume(3, (4, 2) + shape, 0.9, 1.1).astype(np.float32)).to(dev)
+    out = torch.empty((4, 3) + shape, dtype=torch.float32, device=dev)
+    B.wo_reconstruct(tf_d, OO.KINDS, d, None, [1e-3, 1e-3], 0, 0, out, 4, Z, Y, X, ws4)
+    ref = torch.empty((2, 3) + shape, dtype=torch.float32, device=dev)
+    B.wo_reconstruct(tf_h, OO.KINDS, d[[0, 2]].contiguous(), None, [1e-3, 1e-3], 0, 0, ref, 2, Z, Y, X, ws)
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(out[1]) == 0 and torch.count_nonzero(out[3]) == 0
+    assert torch.equal(out[0], ref[0]) and torch.equal(out[2], ref[1])
+
+
+def test_tile_pipeline_under_cuda_graph(env):
+    """gather -> TF build (device optics) -> reconstruct -> blend captured once
+    and replayed; the replay equals the eager calls and follows new inputs."""
+    B, torch, dev = env
+    ty, tx, core, halo, Z = 2, 2, 32, 8, 12
+    E = core + 2 * halo
+    n = ty * tx
+    optics = B.optics_tensor(ph.tile_optics(np.random.default_rng(9), n), dev)
+    field = torch.from_numpy((1.0 + ph.sphere_phantom(2, (Z, ty * core, tx * core), n_spheres=30)).astype(np.float32)).to(dev)
+    tiles = torch.empty((n, Z, E, E), dtype=torch.float32, device=dev)
+    tf, ws = B.alloc(n, Z, E, E, ("phase",), dev)
+    rec = torch.empty_like(tiles)
+    out = torch.empty_like(field)
+
+    def pipeline():
+        B.wo_tile_gather(field, Z, ty, tx, core, halo, tiles)
+        B.wo_build_tf_device(optics, n, Z, E, E, ("phase",), tf, ws)
+        B.wo_reconstruct(tf, ("phase",), tiles, None, [1e-3], 0, 0, rec, n, Z, E, E, ws)
+        B.wo_tile_blend(rec, Z, ty, tx, core, halo, out)
+
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        pipeline()  # warm-up outside capture (one-time kernel attributes)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    eager = out.clone()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        pipeline()
+    out.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, eager)
+    field.mul_(1.5).add_(0.1)
+    g.replay()
+    with torch.cuda.stream(s):
+        pipeline()
+    torch.cuda.synchronize()
+    graph_out = out.clone()
+    with torch.cuda.stream(s):
+        pipeline()
+    torch.cuda.synchronize()
+    assert torch.equal(graph_out, out) and not torch.equal(graph_out, eager)
