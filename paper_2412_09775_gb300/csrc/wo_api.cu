@@ -150,6 +150,7 @@ static wo_status check_optics(const wo_optics& o) {
 
 static wo_status cuda_status(cudaError_t e) { return e == cudaSuccess ? WO_OK : WO_ERR_CUDA; }
 
+
 #define WO_TRY(expr)                          \
   do {                                        \
     cudaError_t _e = (expr);                  \
@@ -264,6 +265,8 @@ static wo_status build_tf_impl(const wo_optics* optics, bool on_host, int n_tile
   WO_TRY(cudaMemsetAsync(a.stats, 0, (size_t)n_tiles * 8 * sizeof(float), cs));
   WO_TRY(tf_pupil_record(a, cs));
   WO_TRY(tf_arms(a, cs));
+  a.row_begin = 0;
+  a.row_end = (long long)n_tiles * Z * Y;
   WO_TRY(tf_psf_rows(a, cs));
   const int Xh = X / 2 + 1;
   WO_TRY(cols_c2c(Y, false, a.tf, Xh, (long long)Y * Xh, Xh, (long long)n_tiles * s.n_kinds * Z, cs,
@@ -397,8 +400,8 @@ static wo_status check_tiles(int Z, int tiles_y, int tiles_x, int core, int halo
   if (Z < 1 || tiles_y < 1 || tiles_x < 1 || core < 1 || halo < 0) return WO_ERR_SHAPE;
   if (2 * halo > core) return WO_ERR_SHAPE;
   const long long E = (long long)core + 2LL * halo;
-  if (E > 65535 || (long long)tiles_y * core > 65535 || (long long)tiles_x * core > (1LL << 30) ||
-      (long long)tiles_y * tiles_x * Z > 65535 || Z > 65535)
+  if (E > 65535 || (long long)tiles_x * core > (1LL << 30) || (long long)tiles_y * tiles_x * Z > 65535 ||
+      (long long)tiles_y * core * Z > (1LL << 31) - 1)
     return WO_ERR_SHAPE;
   return WO_OK;
 }

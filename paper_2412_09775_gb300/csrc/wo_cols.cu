@@ -45,18 +45,19 @@ __device__ __forceinline__ void col_tile_store(const float2* buf, float2* __rest
 template <int N, bool INV>
 __global__ void __launch_bounds__(ColGeom<N>::NT, ColGeom<N>::MINB)
     k_cols(float2* __restrict__ data, long long col_stride, long long plane_stride, int ncols,
-           long long nplanes) {
+           long long nplanes, long long total, long long group_stride) {
   using G = ColGeom<N>;
   constexpr int B = G::B, NT = G::NT;
   extern __shared__ float2 sm[];
   float2* buf = sm;
   float2* tw = sm + N * B;
-  const long long plane = blockIdx.y + (long long)gridDim.y * blockIdx.z;
-  if (plane >= nplanes) return;  // uniform across the CTA
+  const long long p = blockIdx.y + (long long)gridDim.y * blockIdx.z;
+  if (p >= total) return;  // uniform across the CTA
+  const long long g = p / nplanes, plane = p - g * nplanes;
   make_twiddles<N>(tw);
   const int x0 = blockIdx.x * B;
   const int w = min(B, ncols - x0);
-  float2* base = data + plane * plane_stride + x0;
+  float2* base = data + g * group_stride + plane * plane_stride + x0;
   col_tile_load<N, B, NT>(buf, base, col_stride, w);
   cp_async_wait_all();
   __syncthreads();
@@ -66,7 +67,8 @@ __global__ void __launch_bounds__(ColGeom<N>::NT, ColGeom<N>::MINB)
 
 template <int N>
 static cudaError_t launch_cols(bool inv, float2* data, long long cs, long long ps, int ncols,
-                               long long nplanes, cudaStream_t s, const char* name) {
+                               long long nplanes, cudaStream_t s, const char* name, long long groups,
+                               long long gs) {
   using G = ColGeom<N>;
   const size_t smem = G::SMEM;
   static cudaError_t a0 = allow_smem(k_cols<N, false>, smem);
@@ -74,24 +76,26 @@ static cudaError_t launch_cols(bool inv, float2* data, long long cs, long long p
   if (a0 != cudaSuccess) return a0;
   if (a1 != cudaSuccess) return a1;
   const unsigned gx = (unsigned)((ncols + G::B - 1) / G::B);
-  const long long gy = nplanes < 65535 ? nplanes : 65535;
-  const long long gz = (nplanes + gy - 1) / gy;
+  const long long total = nplanes * groups;
+  const long long gy = total < 65535 ? total : 65535;
+  const long long gz = (total + gy - 1) / gy;
   dim3 grid(gx, (unsigned)gy, (unsigned)gz);
   if (inv) {
-    WO_LAUNCH(name, s, (k_cols<N, true><<<grid, G::NT, smem, s>>>(data, cs, ps, ncols, nplanes)));
+    WO_LAUNCH(name, s, (k_cols<N, true><<<grid, G::NT, smem, s>>>(data, cs, ps, ncols, nplanes, total, gs)));
   } else {
-    WO_LAUNCH(name, s, (k_cols<N, false><<<grid, G::NT, smem, s>>>(data, cs, ps, ncols, nplanes)));
+    WO_LAUNCH(name, s, (k_cols<N, false><<<grid, G::NT, smem, s>>>(data, cs, ps, ncols, nplanes, total, gs)));
   }
   return cudaGetLastError();
 }
 
 cudaError_t cols_c2c(int N, bool inverse, float2* data, long long col_stride, long long plane_stride,
-                     int ncols, long long nplanes, cudaStream_t s, const char* name) {
-  if (N == 1 || nplanes <= 0 || ncols <= 0) return cudaSuccess;  // identity
+                     int ncols, long long nplanes, cudaStream_t s, const char* name, long long groups,
+                     long long group_stride) {
+  if (N == 1 || nplanes <= 0 || ncols <= 0 || groups <= 0) return cudaSuccess;  // identity
   switch (N) {
 #define WO_CASE(n) \
   case n:          \
-    return launch_cols<n>(inverse, data, col_stride, plane_stride, ncols, nplanes, s, name);
+    return launch_cols<n>(inverse, data, col_stride, plane_stride, ncols, nplanes, s, name, groups, group_stride);
     WO_CASE(2) WO_CASE(3) WO_CASE(4) WO_CASE(6) WO_CASE(8) WO_CASE(12) WO_CASE(16) WO_CASE(24)
     WO_CASE(32) WO_CASE(48) WO_CASE(64) WO_CASE(96) WO_CASE(128) WO_CASE(192) WO_CASE(256)
     WO_CASE(384) WO_CASE(512) WO_CASE(768) WO_CASE(1024) WO_CASE(1536) WO_CASE(2048)

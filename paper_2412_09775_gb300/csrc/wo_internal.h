@@ -17,6 +17,7 @@ void prof_end(int token, cudaStream_t s);
 struct RowBg {
   float v[4];               // per-channel constants (mode 1)
   long long rows_per_block; // Z*Y
+  long long row_offset;     // global index of the first row passed to the kernel
   int nchan;                // channels per tile
   int mode;                 // 0: none, 1: add/subtract v[channel], 2: subtract
                             //    the block's first sample (before R2C only)
@@ -28,12 +29,13 @@ cudaError_t rows_r2c(int N, const float* in, float2* out, long long nrows, RowBg
 // Half spectra (pitch N+1) -> real rows of length 2N, times `scale`, plus bg.
 cudaError_t rows_c2r(int N, const float2* in, float* out, long long nrows, float scale,
                      RowBg bg, cudaStream_t s);
-// In-place C2C transforms of length N along a strided axis:
-// element n of column c of plane p at data[p*plane_stride + n*col_stride + c].
+// In-place C2C transforms of length N along a strided axis over `groups`
+// groups of `nplanes` planes: element n of column c of plane i of group g at
+// data[g*group_stride + i*plane_stride + n*col_stride + c].
 // `name` labels the launch for the profiler.
 cudaError_t cols_c2c(int N, bool inverse, float2* data, long long col_stride,
                      long long plane_stride, int ncols, long long nplanes, cudaStream_t s,
-                     const char* name);
+                     const char* name, long long groups = 1, long long group_stride = 0);
 
 // Per-frequency operator applied between a forward and an inverse z transform.
 struct ZOp {
@@ -71,6 +73,7 @@ struct TfArgs {
   int want_phase, want_abs, want_fl;
   int n_arms;               // 2*(lf) + fl
   int n_kinds;
+  long long row_begin, row_end;  // PSF-row pass: rows (t*Z + j)*Y + y in [begin, end)
 };
 cudaError_t tf_pupil_record(const TfArgs& a, cudaStream_t s);
 cudaError_t tf_arms(const TfArgs& a, cudaStream_t s);

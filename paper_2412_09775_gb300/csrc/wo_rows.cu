@@ -20,9 +20,11 @@ __device__ __forceinline__ void row_constants(float* sc, const float* in, long l
                                               int B, int N, const RowBg& bg) {
   if (threadIdx.x < B) {
     const long long row = row0 + threadIdx.x;
+    const long long grow = bg.row_offset + row;  // row index in the whole volume set
     float c = 0.f;
-    if (row < nrows && bg.mode == 1) c = bg.v[(row / bg.rows_per_block) % bg.nchan];
-    if (row < nrows && bg.mode == 2) c = in[(row / bg.rows_per_block) * bg.rows_per_block * (2LL * N)];
+    if (row < nrows && bg.mode == 1) c = bg.v[(grow / bg.rows_per_block) % bg.nchan];
+    if (row < nrows && bg.mode == 2)
+      c = in[((grow / bg.rows_per_block) * bg.rows_per_block - bg.row_offset) * (2LL * N)];
     sc[threadIdx.x] = c;
   }
 }
@@ -94,7 +96,8 @@ __global__ void __launch_bounds__(RowGeom<N>::NT, RowGeom<N>::MINB)
   make_twiddles<2 * N>(tw);
   if (threadIdx.x < B) {
     const long long row = row0 + threadIdx.x;
-    sc[threadIdx.x] = (row < nrows && bg.mode == 1) ? bg.v[(row / bg.rows_per_block) % bg.nchan] : 0.f;
+    sc[threadIdx.x] =
+        (row < nrows && bg.mode == 1) ? bg.v[((bg.row_offset + row) / bg.rows_per_block) % bg.nchan] : 0.f;
   }
   cp_async_wait_all();
   __syncthreads();

@@ -249,8 +249,8 @@ __global__ void __launch_bounds__(PsfGeom<NX>::NT, PsfGeom<NX>::MINB) k_psf_rows
   float2* tw = sm + 3 * SLOT;                    // exp(-2 pi i m / NX)
   float* sc = reinterpret_cast<float*>(tw + NX); // [B] label-free 2K, [B] fluorescence scale
   int* kxm = reinterpret_cast<int*>(sc + 2 * B); // [B] x band limit of the row's tile
-  const long long nrows = (long long)a.n_tiles * a.Z * a.Y;
-  const long long row0 = (long long)blockIdx.x * B;
+  const long long nrows = a.row_end;
+  const long long row0 = a.row_begin + (long long)blockIdx.x * B;
   const int na = a.n_arms;
   const bool lf = a.lf_props > 0, fl = a.want_fl != 0;
   if (threadIdx.x < B) {
@@ -422,7 +422,7 @@ static cudaError_t launch_psf(const TfArgs& a, cudaStream_t s) {
   using G = PsfGeom<NX>;
   static cudaError_t attr = allow_smem(k_psf_rows<NX>, G::SMEM);
   if (attr != cudaSuccess) return attr;
-  const long long rows = (long long)a.n_tiles * a.Z * a.Y;
+  const long long rows = a.row_end - a.row_begin;
   WO_LAUNCH("tf_psf_rows", s, (k_psf_rows<NX><<<(unsigned)((rows + G::B - 1) / G::B), G::NT, G::SMEM, s>>>(a)));
   return cudaGetLastError();
 }

@@ -23,70 +23,107 @@ __device__ __forceinline__ float ramp(int u, int E, int halo) {
   return fminf(1.f, fminf(((float)u + 0.5f) * inv, ((float)(E - u) - 0.5f) * inv));
 }
 
-__global__ void __launch_bounds__(128)
+// Gather: one thread per 4 consecutive tile pixels of a row.  When the four
+// field pixels are in range they are contiguous and 16-byte aligned (tile
+// origins and the field width are multiples of 4 when core and halo are), so
+// the copy is one float4 load and store; mirrored edges fall back to scalars.
+__global__ void __launch_bounds__(256)
     k_gather(const float* __restrict__ field, int Z, int tiles_x, int core, int halo, int Yf, int Xf,
-             float* __restrict__ tiles) {
+             float* __restrict__ tiles, int vec) {
   const int E = core + 2 * halo;
-  const int v = blockIdx.x * 128 + threadIdx.x;
-  if (v >= E) return;
-  const int u = blockIdx.y;
-  const long long tz = blockIdx.z;
+  const int E4 = (E + 3) / 4;
+  const long long tz = blockIdx.y;  // t * Z + z
   const long long t = tz / Z, z = tz - (tz / Z) * Z;
   const int ty = (int)(t / tiles_x), tx = (int)(t - (t / tiles_x) * tiles_x);
-  const int y = mirror_idx(ty * core - halo + u, Yf);
-  const int x = mirror_idx(tx * core - halo + v, Xf);
-  tiles[((t * Z + z) * E + u) * (long long)E + v] = __ldg(field + (z * Yf + y) * (long long)Xf + x);
+  const float* src = field + z * (long long)Yf * Xf;
+  float* dst = tiles + tz * (long long)E * E;
+  for (int i = blockIdx.x * 256 + threadIdx.x; i < E * E4; i += gridDim.x * 256) {
+    const int u = i / E4, v0 = (i - (i / E4) * E4) * 4;
+    const int y = mirror_idx(ty * core - halo + u, Yf);
+    const int xs = tx * core - halo + v0;
+    const float* row = src + (long long)y * Xf;
+    if (vec && xs >= 0 && xs + 3 < Xf && v0 + 3 < E) {
+      *reinterpret_cast<float4*>(dst + (long long)u * E + v0) = __ldg(reinterpret_cast<const float4*>(row + xs));
+    } else {
+      for (int k = 0; k < 4 && v0 + k < E; ++k) dst[(long long)u * E + v0 + k] = __ldg(row + mirror_idx(xs + k, Xf));
+    }
+  }
 }
 
-__global__ void __launch_bounds__(128)
+// Blend: one thread per 4 consecutive field pixels of a row; the covering
+// tiles (at most two per axis) are the same for the four, only the x weights
+// differ.
+__global__ void __launch_bounds__(256)
     k_blend(const float* __restrict__ tiles, int Z, int tiles_y, int tiles_x, int core, int halo,
-            float* __restrict__ field) {
+            float* __restrict__ field, int vec) {
   const int E = core + 2 * halo;
   const int Yf = tiles_y * core, Xf = tiles_x * core;
-  const int x = blockIdx.x * 128 + threadIdx.x;
-  if (x >= Xf) return;
-  const int y = blockIdx.y;
-  const long long z = blockIdx.z;
-  int tys[2], us[2], txs[2], vs[2];
-  float wys[2], wxs[2];
-  int ny = 0, nx = 0;
-  const int qy = (y + halo) / core, qx = (x + halo) / core;
+  const int X4 = Xf / 4;  // Xf is a multiple of 4 when vec != 0
+  const long long zy = blockIdx.x;  // z * Yf + y
+  const long long z = zy / Yf;
+  const int y = (int)(zy - z * Yf);
+  int tys[2], us[2];
+  float wys[2];
+  int ny = 0;
+  const int qy = (y + halo) / core;
   for (int c = qy - 1; c <= qy; ++c) {
     if (c < 0 || c >= tiles_y) continue;
     const int u = y - (c * core - halo);
     if (u < 0 || u >= E) continue;
     tys[ny] = c; us[ny] = u; wys[ny] = ramp(u, E, halo); ++ny;
   }
-  for (int c = qx - 1; c <= qx; ++c) {
-    if (c < 0 || c >= tiles_x) continue;
-    const int v = x - (c * core - halo);
-    if (v < 0 || v >= E) continue;
-    txs[nx] = c; vs[nx] = v; wxs[nx] = ramp(v, E, halo); ++nx;
-  }
-  float acc = 0.f, wsum = 0.f;
-  for (int i = 0; i < ny; ++i) {
-    for (int k = 0; k < nx; ++k) {
-      const long long t = (long long)tys[i] * tiles_x + txs[k];
-      const float wgt = wys[i] * wxs[k];
-      acc += wgt * __ldg(tiles + ((t * Z + z) * E + us[i]) * (long long)E + vs[k]);
-      wsum += wgt;
+  const int nvec = vec ? X4 : Xf;
+  for (int i = threadIdx.x; i < nvec; i += 256) {
+    const int x0 = vec ? 4 * i : i;
+    const int lanes = vec ? 4 : 1;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f}, wsum[4] = {0.f, 0.f, 0.f, 0.f};
+    const int qx = (x0 + halo) / core;
+    for (int c = qx - 1; c <= qx; ++c) {
+      if (c < 0 || c >= tiles_x) continue;
+      const int v = x0 - (c * core - halo);
+      if (v < 0 || v >= E) continue;  // vec: v..v+3 lie in the same tile
+      for (int a = 0; a < ny; ++a) {
+        const long long t = (long long)tys[a] * tiles_x + c;
+        const float* src = tiles + ((t * Z + z) * E + us[a]) * (long long)E + v;
+        float val[4];
+        if (vec) {
+          const float4 q = __ldg(reinterpret_cast<const float4*>(src));
+          val[0] = q.x; val[1] = q.y; val[2] = q.z; val[3] = q.w;
+        } else {
+          val[0] = __ldg(src);
+        }
+        for (int k = 0; k < lanes; ++k) {
+          const float wgt = wys[a] * ramp(v + k, E, halo);
+          acc[k] += wgt * val[k];
+          wsum[k] += wgt;
+        }
+      }
+    }
+    float* dst = field + zy * (long long)Xf + x0;
+    if (vec) {
+      *reinterpret_cast<float4*>(dst) =
+          make_float4(acc[0] / wsum[0], acc[1] / wsum[1], acc[2] / wsum[2], acc[3] / wsum[3]);
+    } else {
+      dst[0] = acc[0] / wsum[0];
     }
   }
-  field[(z * Yf + y) * (long long)Xf + x] = acc / wsum;
 }
 
 cudaError_t tiles_gather(const float* field, int Z, int ty, int tx, int core, int halo, float* tiles,
                          cudaStream_t s) {
   const int E = core + 2 * halo;
-  dim3 grid((unsigned)((E + 127) / 128), (unsigned)E, (unsigned)((long long)ty * tx * Z));
-  WO_LAUNCH("tile_gather", s, (k_gather<<<grid, 128, 0, s>>>(field, Z, tx, core, halo, ty * core, tx * core, tiles)));
+  const int vec = (core % 4 == 0 && halo % 4 == 0) ? 1 : 0;
+  const long long work = (long long)E * ((E + 3) / 4);
+  dim3 grid((unsigned)((work + 255) / 256), (unsigned)((long long)ty * tx * Z));
+  WO_LAUNCH("tile_gather", s, (k_gather<<<grid, 256, 0, s>>>(field, Z, tx, core, halo, ty * core, tx * core, tiles, vec)));
   return cudaGetLastError();
 }
 
 cudaError_t tiles_blend(const float* tiles, int Z, int ty, int tx, int core, int halo, float* field,
                         cudaStream_t s) {
-  dim3 grid((unsigned)((tx * core + 127) / 128), (unsigned)(ty * core), (unsigned)Z);
-  WO_LAUNCH("tile_blend", s, (k_blend<<<grid, 128, 0, s>>>(tiles, Z, ty, tx, core, halo, field)));
+  const int vec = (core % 4 == 0 && halo % 4 == 0) ? 1 : 0;
+  dim3 grid((unsigned)((long long)ty * core * Z));
+  WO_LAUNCH("tile_blend", s, (k_blend<<<grid, 256, 0, s>>>(tiles, Z, ty, tx, core, halo, field, vec)));
   return cudaGetLastError();
 }
 
