@@ -72,6 +72,15 @@ typedef struct {
 } wo_optics;
 
 enum { WO_TF_PHASE = 1, WO_TF_ABSORPTION = 2, WO_TF_FLUOR = 4 };
+/* A bank of two TF slots per tile for defocus auto-tuning (used alone, never
+ * or-ed with the kinds above): slot 0 the 3D phase TF, slot 1 its derivative
+ * with respect to the tile's defocus_um, dH/dz0 (per um).  The defocus enters
+ * both pupil arms through e^{i2pi eta z_j}, so the derivative arms are
+ * A' = i2pi eta A and B' = i2pi eta B, and dH1 = c sum (A'* B + A* B') / sum S P^2
+ * goes through the same Table 1 combination and z-DFT as H1.  Supported for
+ * X <= 768.  wo_forward, wo_forward_adjoint and wo_reconstruct accept such a
+ * bank with this kinds value and use its phase slot (a phase-only system). */
+enum { WO_TF_PHASE_DZ = 8 };
 enum { WO_MODE_3D = 0, WO_MODE_2D = 1 };
 enum { WO_ETA_RELATIVE = 0, WO_ETA_ABSOLUTE = 1 };
 
@@ -200,6 +209,57 @@ wo_status wo_tile_gather(const float *d_field, int Z, int tiles_y, int tiles_x,
  * (E-u-1/2)/(2 halo)) per axis (linearly weighted distance-to-edge blending). */
 wo_status wo_tile_blend(const float *d_tiles, int Z, int tiles_y, int tiles_x,
                         int core, int halo, float *d_field, wo_stream stream);
+
+/* Defocus auto-tuning (Results, physics-guided auto-tuning of the optical
+ * parameters theta; Fig. 2a(iv); Ext. Data Fig. 3; Methods, optical pooled
+ * screen data: 2D phase from a z-stack, Adam, fixed regulariser).
+ *
+ * wo_spectrum: the 3D half spectra [n_tiles][Z][Y][X/2+1] complex64 of
+ * n_tiles brightfield stacks d_data [n_tiles][Z][Y][X] with the background
+ * removed from the DC bin: D(0) - N b, b = h_background[0], or the stack's
+ * mean when h_background is NULL (then D(0) = 0).  d_spec holds
+ * n_tiles*Z*Y*(X/2+1)*8 bytes (caller-owned, 16-byte aligned).  Same shape
+ * rules as wo_forward. */
+wo_status wo_spectrum(const float *d_data, const float *h_background, void *d_spec,
+                      int n_tiles, int Z, int Y, int X, wo_stream stream);
+
+/* wo_defocus_objective: per tile, the loss of the 2D thin-object fit (every
+ * plane j sees the object at the reference plane through the per-plane phase
+ * TF H_j) at its Tikhonov minimiser, and its derivative with respect to the
+ * tile's defocus:
+ *   L(z0) = min_f sum_j ||d_j - b - H_j(z0) f||^2 + eta ||f||^2
+ *         = (1/(N_perp Z)) sum_nu [ sum_k |D_k - H_k F|^2 + Z eta |F|^2 ],
+ *   F(nu) = sum_k H_k* D_k / (sum_k |H_k|^2 + Z eta),
+ *   dL/dz0 = (1/(N_perp Z)) sum_nu -2 Re sum_k (dH_k F)* (D_k - H_k F)
+ * (k runs over the axial bins of the 3D spectra; the derivative needs no
+ * derivative of F because F minimises the bracket).  Transverse frequencies
+ * with |nu| > nu_max (cycles/um) are left out of both sums when nu_max > 0
+ * (0 or +inf: all frequencies): the loss of the band-limited data, whose
+ * minimum in z0 is wider.  eta is absolute (>= 0).
+ * d_tf: a WO_TF_PHASE_DZ bank of the same tiles; d_optics: the device optics
+ * the bank was built from (8-byte aligned; pixel_um sets the frequency grid);
+ * d_spec: wo_spectrum of the data.  d_value, d_grad: n_tiles doubles each
+ * (8-byte aligned; either may be NULL, not both).  The workspace needs
+ * n_tiles * ceil(Y*(X/2+1)/256) * 16 bytes, which wo_workspace_bytes(...,
+ * WO_TF_PHASE_DZ) covers; the sums are reduced in a fixed order (repeatable
+ * to the bit).  No host synchronisation: the call can be captured in a CUDA
+ * graph together with wo_build_tf_device and wo_adam_defocus. */
+wo_status wo_defocus_objective(const void *d_tf, const wo_optics *d_optics, const void *d_spec,
+                               float eta, float nu_max, double *d_value, double *d_grad,
+                               int n_tiles, int Z, int Y, int X, void *d_ws, size_t ws_bytes,
+                               wo_stream stream);
+
+/* wo_adam_defocus: one Adam step (Kingma and Ba, 2015) on each tile's
+ * defocus_um in the device optics array, from the gradient d_grad:
+ *   m = b1 m + (1-b1) g,  v = b2 v + (1-b2) g^2,  s = s + 1,
+ *   z0 -= lr (m / (1 - b1^s)) / (sqrt(v / (1 - b2^s)) + eps).
+ * d_state: n_tiles x {m, v, s} doubles, zeroed by the caller before the first
+ * step and kept on the device, so a captured graph of build + objective +
+ * step replays as further Adam iterations.  lr >= 0, 0 <= b1, b2 < 1,
+ * eps > 0; all pointers 8-byte aligned. */
+wo_status wo_adam_defocus(wo_optics *d_optics, const double *d_grad, double *d_state,
+                          int n_tiles, double lr, double beta1, double beta2, double eps,
+                          wo_stream stream);
 
 /* Human-readable name of a status. */
 const char *wo_status_string(wo_status status);

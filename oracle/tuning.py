@@ -1,0 +1,84 @@
+"""Auto-tuning objective for the per-tile defocus, float64 (test infrastructure).
+
+The paper auto-tunes each tile's parameter vector theta by back-propagating a
+scalar loss through the transfer-function build and the Tikhonov
+reconstruction of a phase-from-defocus model (Results, "Physics-guided ML
+auto-tunes multi-contrast blind deconvolution"; Fig. 2a(iv); Ext. Data
+Fig. 3; Methods, "Cell-scale optical pooled screen data": 2D phase from a
+z-stack, Adam, eta fixed at 1e-2).
+
+Reading used here (a data-fidelity loss): for the 2D thin-object model (every
+plane j of the stack sees the per-plane TF H_j of the object at the reference
+plane), the Tikhonov objective at its minimiser,
+
+    L(theta) = min_f ||d - b - H_theta f||^2 + eta ||f||^2
+             = ||d - b - H_theta f_hat||^2 + eta ||f_hat||^2,
+
+with a fixed absolute eta, the channel mean as background and theta the
+tile's defocus z_offset.  (For the 3D model the same loss does not identify
+the defocus: with one free unknown per 3D frequency the fit is exact wherever
+H != 0.)  ``objective`` evaluates the definition - reconstruct, predict,
+form the residual in real space.  ``gradient_fd`` is its central finite
+difference.  ``tf_defocus_derivative`` is dH/d(defocus) of the 3D phase TF.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import model, optics
+
+
+def band_limit(o: dict, d: np.ndarray, nu_max: float) -> np.ndarray:
+    """The stack with every plane's transverse frequencies |nu| > nu_max
+    (cycles/um) removed (an ideal low-pass; the mean is kept)."""
+    Z, Y, X = d.shape
+    ky, kx = optics.transverse_grid(Y, X, o["pixel_um"])
+    keep = ky ** 2 + kx ** 2 <= float(nu_max) ** 2
+    return np.real(np.fft.ifft2(np.fft.fft2(np.asarray(d, dtype=np.float64), axes=(1, 2)) * keep, axes=(1, 2)))
+
+
+def objective(o: dict, d: np.ndarray, eta: float, nu_max: float | None = None) -> float:
+    """L(theta) for one tile; d is the (Z, Y, X) brightfield stack.  With
+    nu_max, the loss of the band-limited stack (``band_limit``)."""
+    shape = d.shape
+    Hj = optics.plane_tfs(o, shape, ("phase",))["phase"]
+    modes = [dict(channels=[0], props=[0], H=[[Hj]])]
+    dd = np.asarray(d, dtype=np.float64)[None]
+    if nu_max is not None:
+        dd = band_limit(o, dd[0], nu_max)[None]
+    f_hat = model.reconstruct_2d(modes, dd, eta, background=None, relative=False)[0]
+    b = float(np.mean(dd[0]))
+    pred = np.real(np.fft.ifft2(Hj * np.fft.fft2(f_hat)[None], axes=(1, 2))) + b
+    r = dd[0] - pred
+    return float(np.sum(r * r) + eta * np.sum(f_hat * f_hat))
+
+
+def objective_at(o: dict, d: np.ndarray, eta: float, defocus: float, nu_max: float | None = None) -> float:
+    return objective(dict(o, defocus_um=float(defocus)), d, eta, nu_max)
+
+
+def gradient_fd(o: dict, d: np.ndarray, eta: float, h: float = 1e-4, nu_max: float | None = None) -> float:
+    """dL/d(defocus) by a central difference of the objective."""
+    z = o["defocus_um"]
+    return (objective_at(o, d, eta, z + h, nu_max) - objective_at(o, d, eta, z - h, nu_max)) / (2 * h)
+
+
+def tf_defocus_derivative(o: dict, shape) -> np.ndarray:
+    """dH_phase/d(defocus) of the 3D phase TF (complex128, (Z, Y, X)).
+
+    The defocus enters both arms through e^{i2pi eta z_j}, so
+    d/dz [sum_nu A*(nu) B(nu+q)] = sum_nu A*(nu) B'(nu+q) + sum_nu A'*(nu) B(nu+q)
+    with A' = i 2 pi eta A and B' = i 2 pi eta B; the Table 1 combination and
+    the z-DFT are linear and carry over unchanged.
+    """
+    Z, Y, X = shape
+    A, B = optics.arms(o, shape)
+    eta = optics.axial_frequency(o, Y, X)[None]
+    Ad, Bd = 2j * np.pi * eta * A, 2j * np.pi * eta * B
+    S = optics.source_pupil(o, Y, X)
+    P = optics.detection_pupil(o, Y, X)
+    c = optics.labelfree_prefactor(o) / np.sum(S * P * P)
+    dH1 = c * (optics.correlate(A, Bd) + optics.correlate(Ad, B))
+    dH2 = np.conj(optics.reflect(dH1))
+    T = optics.TABLE1_LABELFREE
+    return optics.stack_to_3d(T[0, 0] * dH1 + T[0, 1] * dH2)

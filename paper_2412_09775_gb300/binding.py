@@ -16,9 +16,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "lib", "libwo_gb300.so")
 
 WO_TF_PHASE, WO_TF_ABSORPTION, WO_TF_FLUOR = 1, 2, 4
+WO_TF_PHASE_DZ = 8
 WO_MODE_3D, WO_MODE_2D = 0, 1
 WO_ETA_RELATIVE, WO_ETA_ABSOLUTE = 0, 1
-KIND_BITS = {"phase": WO_TF_PHASE, "absorption": WO_TF_ABSORPTION, "fluor": WO_TF_FLUOR}
+KIND_BITS = {"phase": WO_TF_PHASE, "absorption": WO_TF_ABSORPTION, "fluor": WO_TF_FLUOR,
+             "phase_dz": WO_TF_PHASE_DZ}
 STATUS = {0: "WO_OK", 1: "WO_ERR_ARG", 2: "WO_ERR_SHAPE", 3: "WO_ERR_UNSUPPORTED_SIZE",
           4: "WO_ERR_UNDERSAMPLED", 5: "WO_ERR_CUDA", 6: "WO_ERR_TIMEOUT", 7: "WO_ERR_OPTICS",
           8: "WO_ERR_WORKSPACE"}
@@ -55,6 +57,10 @@ def _load():
         "wo_forward_adjoint": (i, [vp, u, vp, fp, vp, i, i, i, i, vp, sz, vp]),
         "wo_reconstruct": (i, [vp, u, vp, fp, fp, i, i, vp, i, i, i, i, vp, sz, vp]),
         "wo_reconstruct_static": (i, [vp, u, vp, fp, fp, i, i, vp, i, i, i, i, vp]),
+        "wo_spectrum": (i, [vp, fp, vp, i, i, i, i, vp]),
+        "wo_defocus_objective": (i, [vp, vp, vp, f, f, vp, vp, i, i, i, i, vp, sz, vp]),
+        "wo_adam_defocus": (i, [vp, vp, vp, i, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_double, vp]),
         "wo_tile_gather": (i, [vp, i, i, i, i, i, vp, vp]),
         "wo_tile_blend": (i, [vp, i, i, i, i, i, vp, vp]),
         "wo_status_string": (ctypes.c_char_p, [i]),
@@ -73,7 +79,8 @@ def _load():
 _lib = _load()
 EXPORTED = ("wo_size_supported", "wo_tf_bytes", "wo_workspace_bytes", "wo_build_tf", "wo_build_tf_device",
             "wo_forward",
-            "wo_forward_adjoint", "wo_reconstruct", "wo_reconstruct_static", "wo_tile_gather", "wo_tile_blend",
+            "wo_forward_adjoint", "wo_reconstruct", "wo_reconstruct_static", "wo_spectrum",
+            "wo_defocus_objective", "wo_adam_defocus", "wo_tile_gather", "wo_tile_blend",
             "wo_status_string", "wo_profile_enable", "wo_profile_read", "wo_launch_count")
 
 
@@ -116,6 +123,8 @@ def _floats(vals):
 def kinds_mask(kinds) -> int:
     if isinstance(kinds, int):
         return kinds
+    if isinstance(kinds, str):
+        kinds = (kinds,)
     m = 0
     for k in kinds:
         m |= KIND_BITS[k]
@@ -197,6 +206,26 @@ def wo_reconstruct_static(tf, kinds, data, background, eta, eta_flag, mode, f, n
            "wo_reconstruct_static")
 
 
+def wo_spectrum(data, background, spec, n_tiles, Z, Y, X, stream=None):
+    """3D half spectra [n, Z, Y, X/2+1] (complex64 tensor `spec`) of brightfield stacks."""
+    bg = _floats(background)
+    _check(_lib.wo_spectrum(_ptr(data), bg[0] if bg else None, _ptr(spec), n_tiles, Z, Y, X, _stream(stream)),
+           "wo_spectrum")
+
+
+def wo_defocus_objective(tf, d_optics, spec, eta, nu_max, value, grad, n_tiles, Z, Y, X, ws, stream=None):
+    """Per-tile loss and defocus derivative (float64 tensors [n] or None) from a phase_dz bank."""
+    _check(_lib.wo_defocus_objective(_ptr(tf), _ptr(d_optics), _ptr(spec), float(eta), float(nu_max), _ptr(value),
+                                     _ptr(grad), n_tiles, Z, Y, X, _ptr(ws), _nbytes(ws), _stream(stream)),
+           "wo_defocus_objective")
+
+
+def wo_adam_defocus(d_optics, grad, state, n_tiles, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    """One on-device Adam step on each tile's defocus (state: float64 [n, 3], zeroed before the first)."""
+    _check(_lib.wo_adam_defocus(_ptr(d_optics), _ptr(grad), _ptr(state), n_tiles, float(lr), float(beta1),
+                                float(beta2), float(eps), _stream(stream)), "wo_adam_defocus")
+
+
 def wo_tile_gather(field, Z, tiles_y, tiles_x, core, halo, tiles, stream=None):
     _check(_lib.wo_tile_gather(_ptr(field), Z, tiles_y, tiles_x, core, halo, _ptr(tiles), _stream(stream)),
            "wo_tile_gather")
@@ -231,7 +260,8 @@ def wo_launch_count() -> int:
 def tf_views(tf, n_tiles, Z, Y, X, kinds):
     """(spectra, stats) views of a TF bank tensor: complex64 [n][k][Z][Y][X/2+1], float32 [n][8]."""
     import torch
-    nk = bin(kinds_mask(kinds)).count("1")
+    m = kinds_mask(kinds)
+    nk = 2 if m == WO_TF_PHASE_DZ else bin(m).count("1")
     Xh = X // 2 + 1
     n_spec = n_tiles * nk * Z * Y * Xh
     raw = tf.view(torch.uint8)

@@ -64,7 +64,7 @@ static bool size_ok(int n) {
 
 struct Sys {
   int n_kinds, lf_props, has_fl, C, P, n_arms;
-  int want_phase, want_abs;
+  int want_phase, want_abs, want_dz;
 };
 
 static Sys system_of(unsigned kinds) {
@@ -77,6 +77,15 @@ static Sys system_of(unsigned kinds) {
   s.C = (s.lf_props ? 1 : 0) + s.has_fl;
   s.P = s.n_kinds;
   s.n_arms = (s.lf_props ? 2 : 0) + s.has_fl;
+  if (kinds == WO_TF_PHASE_DZ) {  // phase TF and its defocus derivative: two TF slots, four arms
+    s.want_phase = 1;
+    s.want_dz = 1;
+    s.lf_props = 1;
+    s.n_kinds = 2;
+    s.C = 1;
+    s.P = 1;
+    s.n_arms = 4;
+  }
   return s;
 }
 
@@ -104,6 +113,7 @@ static Layout layout_of(int n, int Z, int Y, int X, const Sys& s) {
   L.specB = spec;
   L.op_end = 2 * spec;
   L.total = L.build_end > L.op_end ? L.build_end : L.op_end;
+  if (s.want_dz && tune_partials_bytes(n, Y, X) > L.total) L.total = tune_partials_bytes(n, Y, X);
   L.tf_spectra = align256((size_t)n * s.n_kinds * Z * Y * Xh * sizeof(float2));
   L.tf_stats = L.tf_spectra;
   L.tf_total = L.tf_spectra + (size_t)n * 8 * sizeof(float);
@@ -122,11 +132,14 @@ static size_t zpass_smem(int Z) {
 
 static wo_status check_shape(int n_tiles, int Z, int Y, int X, unsigned kinds) {
   if (n_tiles < 1 || n_tiles > 65535) return WO_ERR_ARG;
-  if (kinds == 0 || (kinds & ~7u)) return WO_ERR_ARG;
+  if (kinds == 0 || (kinds & ~15u)) return WO_ERR_ARG;
+  if ((kinds & WO_TF_PHASE_DZ) && kinds != WO_TF_PHASE_DZ) return WO_ERR_ARG;
   if (Z < 1 || Y < 1 || X < 2) return WO_ERR_SHAPE;
   if (X % 2) return WO_ERR_SHAPE;
   if (!size_ok(Z) || !size_ok(Y) || !size_ok(X / 2) || X > 2048) return WO_ERR_UNSUPPORTED_SIZE;
   if (zpass_smem(Z) > 227 * 1024) return WO_ERR_UNSUPPORTED_SIZE;
+  // four arm rows of X per PSF-row block must fit shared memory
+  if (kinds == WO_TF_PHASE_DZ && X > 768) return WO_ERR_UNSUPPORTED_SIZE;
   return WO_OK;
 }
 
@@ -259,6 +272,7 @@ static wo_status build_tf_impl(const wo_optics* optics, bool on_host, int n_tile
   a.lf_props = s.lf_props;
   a.want_phase = s.want_phase; a.want_abs = s.want_abs; a.want_fl = s.has_fl;
   a.n_arms = s.n_arms; a.n_kinds = s.n_kinds;
+  a.want_dz = s.want_dz;
   if (on_host)
     WO_TRY(cudaMemcpyAsync((void*)a.optics, optics, (size_t)n_tiles * sizeof(wo_optics), cudaMemcpyHostToDevice, cs));
   WO_TRY(cudaMemsetAsync(a.counts, 0, (size_t)n_tiles * 4 * sizeof(int), cs));
@@ -392,6 +406,60 @@ wo_status wo_reconstruct(const void* d_tf, unsigned kinds, const float* d_data, 
                          int X, void* d_ws, size_t ws_bytes, wo_stream stream) {
   return run_op(2, d_tf, kinds, d_data, h_background, h_eta, eta_flag, mode, d_f, n_tiles, Z, Y, X, d_ws,
                 ws_bytes, stream);
+}
+
+wo_status wo_spectrum(const float* d_data, const float* h_background, void* d_spec, int n_tiles, int Z, int Y,
+                      int X, wo_stream stream) {
+  wo_status st = check_shape(n_tiles, Z, Y, X, WO_TF_PHASE);
+  if (st != WO_OK) return st;
+  if (!aligned16(d_data) || !aligned16(d_spec)) return WO_ERR_ARG;
+  if (h_background && !isfinite(h_background[0])) return WO_ERR_ARG;
+  cudaStream_t cs = (cudaStream_t)stream;
+  float2* spec = (float2*)d_spec;
+  const int Xh = X / 2 + 1, H = X / 2;
+  const long long plane = (long long)Y * Xh;
+  RowBg bg{};
+  bg.rows_per_block = (long long)Z * Y;
+  bg.nchan = 1;
+  if (h_background) {
+    bg.mode = 1;
+    bg.v[0] = h_background[0];
+  } else {
+    bg.mode = 2;  // only moves the DC bin, which is zeroed below
+  }
+  WO_TRY(rows_r2c(H, d_data, spec, (long long)n_tiles * Z * Y, bg, cs));
+  WO_TRY(cols_c2c(Y, false, spec, Xh, plane, Xh, (long long)n_tiles * Z, cs, "y_fwd"));
+  WO_TRY(cols_c2c(Z, false, spec, plane, (long long)Z * plane, (int)plane, n_tiles, cs, "z_fwd"));
+  if (!h_background)
+    WO_TRY(zero_dc(spec, n_tiles, (long long)Z * plane, cs));
+  return WO_OK;
+}
+
+wo_status wo_defocus_objective(const void* d_tf, const wo_optics* d_optics, const void* d_spec, float eta,
+                               float nu_max, double* d_value, double* d_grad, int n_tiles, int Z, int Y, int X,
+                               void* d_ws, size_t ws_bytes, wo_stream stream) {
+  wo_status st = check_shape(n_tiles, Z, Y, X, WO_TF_PHASE_DZ);
+  if (st != WO_OK) return st;
+  if (!aligned16(d_tf) || !aligned16(d_spec) || !aligned16(d_ws)) return WO_ERR_ARG;
+  if (!d_optics || (((uintptr_t)d_optics) & 7u)) return WO_ERR_ARG;
+  if (!d_value && !d_grad) return WO_ERR_ARG;
+  if ((d_value && (((uintptr_t)d_value) & 7u)) || (d_grad && (((uintptr_t)d_grad) & 7u))) return WO_ERR_ARG;
+  if (!(eta >= 0.f) || !isfinite(eta) || !(nu_max == nu_max)) return WO_ERR_ARG;
+  if (ws_bytes < tune_partials_bytes(n_tiles, Y, X)) return WO_ERR_WORKSPACE;
+  return cuda_status(tune_reduce((const float2*)d_tf, (const float2*)d_spec, d_optics, n_tiles, Z, Y, X, eta,
+                                 isfinite(nu_max) ? nu_max : 0.f, (double*)d_ws, d_value, d_grad,
+                                 (cudaStream_t)stream));
+}
+
+wo_status wo_adam_defocus(wo_optics* d_optics, const double* d_grad, double* d_state, int n_tiles, double lr,
+                          double beta1, double beta2, double eps, wo_stream stream) {
+  if (n_tiles < 1 || n_tiles > 65535) return WO_ERR_ARG;
+  if (!d_optics || !d_grad || !d_state) return WO_ERR_ARG;
+  if ((((uintptr_t)d_optics) | ((uintptr_t)d_grad) | ((uintptr_t)d_state)) & 7u) return WO_ERR_ARG;
+  if (!(lr >= 0.0) || !isfinite(lr) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) ||
+      !(eps > 0.0) || !isfinite(eps))
+    return WO_ERR_ARG;
+  return cuda_status(adam_defocus(d_optics, d_grad, d_state, n_tiles, lr, beta1, beta2, eps, (cudaStream_t)stream));
 }
 
 static wo_status check_tiles(int Z, int tiles_y, int tiles_x, int core, int halo, const void* a,

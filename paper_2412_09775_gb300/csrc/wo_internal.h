@@ -71,14 +71,28 @@ struct TfArgs {
   int n_tiles, Z, Y, X;
   int lf_props;             // 0..2 (phase, absorption present -> slots)
   int want_phase, want_abs, want_fl;
-  int n_arms;               // 2*(lf) + fl
+  int n_arms;               // 2*(lf) + fl, or 4 with want_dz
   int n_kinds;
+  int want_dz;              // phase TF and dH/d(defocus): arms A, B, A', B'; kinds 2
   long long row_begin, row_end;  // PSF-row pass: rows (t*Z + j)*Y + y in [begin, end)
 };
 cudaError_t tf_pupil_record(const TfArgs& a, cudaStream_t s);
 cudaError_t tf_arms(const TfArgs& a, cudaStream_t s);
 cudaError_t tf_psf_rows(const TfArgs& a, cudaStream_t s);
 cudaError_t tf_zpass(const TfArgs& a, cudaStream_t s);
+
+// Auto-tuning: per-tile value and defocus derivative of the 2D thin-object
+// loss from a data spectrum [tile][Z][Y][Xh] and a TF pair bank (H, dH/dz)
+// [tile][2][Z][Y][Xh]; frequencies above nu_max (cycles/um, > 0) are left
+// out.  `partials` holds tune_partials_bytes(n_tiles, Y, X) bytes.
+cudaError_t tune_reduce(const float2* tf2, const float2* spec, const wo_optics* optics, int n_tiles, int Z,
+                        int Y, int X, float eta, float nu_max, double* partials, double* value, double* grad,
+                        cudaStream_t s);
+size_t tune_partials_bytes(int n_tiles, int Y, int X);
+// Zero element 0 of each of n_tiles volumes of vol elements (the DC bin).
+cudaError_t zero_dc(float2* spec, int n_tiles, long long vol, cudaStream_t s);
+cudaError_t adam_defocus(wo_optics* optics, const double* grad, double* state, int n_tiles, double lr,
+                         double b1, double b2, double eps, cudaStream_t s);
 
 // Tiles.
 cudaError_t tiles_gather(const float* field, int Z, int ty, int tx, int core, int halo,

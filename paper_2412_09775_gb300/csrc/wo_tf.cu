@@ -179,18 +179,29 @@ __global__ void __launch_bounds__(ColGeom<N>::NT, (1024 / ColGeom<N>::NT) > 1 ? 
   }
 #pragma unroll
   for (int i = 0; i < PER; ++i) sincospif(2.0f * phase_frac(r[i].x, r[i].y, zh, zl), &s_[i], &c_[i]);
+  // arms, in slot order: A, B (label-free), P (fluorescence), or
+  // A, B, A' = i 2 pi eta A, B' = i 2 pi eta B (phase TF and its defocus derivative)
   int arm = 0;
-  for (int which = 0; which < 3; ++which) {
+#pragma unroll 1
+  for (int which = 0; which < 5; ++which) {
     if (which < 2 && a.lf_props == 0) continue;
     if (which == 2 && !a.want_fl) continue;
+    if (which > 2 && !a.want_dz) continue;
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
       const int e = threadIdx.x + i * NT;
       if (e >= N * B) continue;
-      const bool on = (which == 0) ? (r[i].w != 0.f) : (r[i].z != 0.f);
-      float2 v = make_float2(0.f, 0.f);
-      if (on) v = (which == 1) ? make_float2(-r[i].z * s_[i], r[i].z * c_[i]) : make_float2(c_[i], s_[i]);
-      buf[e] = v;
+      // v = (al + i be) e^{i phi}: A (1, 0), B (0, 1/eta), P (1, 0),
+      // A' (0, 2 pi eta), B' (-2 pi eta / eta, 0); zero off the pupil
+      // eta is read again from the record (an L2 hit) rather than kept live
+      // across the transforms: the derivative arms are the only users
+      float tpe = 0.f;
+      if (which > 2 && (e % B) < w) tpe = 6.28318530717958648f * __ldg(&rec[(long long)(e / B) * X + e % B].x);
+      const bool on = (which == 0 || which == 3) ? (r[i].w != 0.f) : (r[i].z != 0.f);
+      float al = (which == 0 || which == 2) ? 1.f : (which == 4 ? -tpe * r[i].z : 0.f);
+      float be = which == 1 ? r[i].z : (which == 3 ? tpe : 0.f);
+      if (!on) al = be = 0.f;
+      buf[e] = make_float2(al * c_[i] - be * s_[i], al * s_[i] + be * c_[i]);
     }
     __syncthreads();
     fft_smem<N, B, NT, true, 1>(buf, B, 1, tw);
@@ -209,9 +220,7 @@ struct PsfGeom {
   static constexpr int B = (NX <= 1024) ? 8 : 4;  // rows per CTA (a power of two: the swizzle width)
   static constexpr int NT = threads_for(NX * B);
   static constexpr int MINB = (1024 / NT) > 1 ? (1024 / NT) : 1;
-  static constexpr int SLOT = NX * B + B;  // elements per arm slot
-  // three arm slots, twiddles, per-row constants
-  static constexpr size_t SMEM = ((size_t)3 * SLOT + NX + 2 * B) * sizeof(float2);
+  static constexpr int SLOT = NX * B + B;  // elements per arm slot (up to four arms)
 };
 
 __device__ __forceinline__ float lf_scale(const TfArgs& a, int t) {
@@ -245,8 +254,8 @@ __global__ void __launch_bounds__(PsfGeom<NX>::NT, PsfGeom<NX>::MINB) k_psf_rows
   using Addr = SwzAddr<B, NX>;
   const Addr addr{};
   extern __shared__ float2 sm[];
-  float2* buf = sm;                              // [3][SLOT]
-  float2* tw = sm + 3 * SLOT;                    // exp(-2 pi i m / NX)
+  float2* buf = sm;                              // [n_arms][SLOT]
+  float2* tw = sm + a.n_arms * SLOT;             // exp(-2 pi i m / NX)
   float* sc = reinterpret_cast<float*>(tw + NX); // [B] label-free 2K, [B] fluorescence scale
   int* kxm = reinterpret_cast<int*>(sc + 2 * B); // [B] x band limit of the row's tile
   const long long nrows = a.row_end;
@@ -285,6 +294,12 @@ __global__ void __launch_bounds__(PsfGeom<NX>::NT, PsfGeom<NX>::MINB) k_psf_rows
   for (int e = threadIdx.x; e < B * NX; e += NT) {
     const int n = e / B, b = e - (e / B) * B;
     const int i = addr(n, b);  // same position in every slot
+    if (a.want_dz) {  // slot 0 <- 2K conj(a) b, slot 1 <- 2K (conj(a') b + conj(a) b')
+      const float2 va = buf[i], vb = buf[SLOT + i], vad = buf[2 * SLOT + i], vbd = buf[3 * SLOT + i];
+      buf[i] = cscale(cmulc(va, vb), sc[b]);
+      buf[SLOT + i] = cscale(cadd(cmulc(vad, vb), cmulc(va, vbd)), sc[b]);
+      continue;
+    }
     if (lf) buf[i] = cscale(cmulc(buf[i], buf[SLOT + i]), sc[b]);
     if (fl) {
       const float2 p = buf[fl_src * SLOT + i];
@@ -292,7 +307,7 @@ __global__ void __launch_bounds__(PsfGeom<NX>::NT, PsfGeom<NX>::MINB) k_psf_rows
     }
   }
   __syncthreads();
-  const int nf = (lf ? 1 : 0) + (fl ? 1 : 0);
+  const int nf = a.want_dz ? 2 : (lf ? 1 : 0) + (fl ? 1 : 0);
   for (int sl = 0; sl < nf; ++sl) fft_smem_a<NX, B, NT, false, 1>(buf + sl * SLOT, addr, tw);
   const int Z = a.Z, Y = a.Y, Xh = H + 1;
   for (int e = threadIdx.x; e < B * Xh; e += NT) {
@@ -305,6 +320,14 @@ __global__ void __launch_bounds__(PsfGeom<NX>::NT, PsfGeom<NX>::MINB) k_psf_rows
     float2* dst = a.tf + ((t * a.n_kinds * Z + j) * Y + y) * Xh + k;  // slot 0 of this row
     const long long kstride = (long long)Z * Y * Xh;
     int slot = 0;
+    if (a.want_dz) {  // H_re of g and of g' (the map g -> H_re is linear)
+      for (int q = 0; q < 2; ++q) {
+        const float2 gk = buf[q * SLOT + addr(k, b)];
+        const float2 gc = cconj(buf[q * SLOT + addr(k == 0 ? 0 : NX - k, b)]);
+        dst[q * kstride] = make_float2(0.5f * (gk.x + gc.x), 0.5f * (gk.y + gc.y));
+      }
+      continue;
+    }
     if (lf) {
       const float2 gk = buf[addr(k, b)];
       const float2 gc = cconj(buf[addr(k == 0 ? 0 : NX - k, b)]);
@@ -420,10 +443,18 @@ cudaError_t tf_arms(const TfArgs& a, cudaStream_t s) {
 template <int NX>
 static cudaError_t launch_psf(const TfArgs& a, cudaStream_t s) {
   using G = PsfGeom<NX>;
-  static cudaError_t attr = allow_smem(k_psf_rows<NX>, G::SMEM);
+  // up to four arm slots where they fit (the derivative bank needs four; the
+  // API admits it only for X <= 768), else three
+  constexpr size_t kMax = 227 * 1024;
+  constexpr size_t s4 = ((size_t)4 * G::SLOT + NX + 2 * G::B) * sizeof(float2);
+  constexpr size_t s3 = ((size_t)3 * G::SLOT + NX + 2 * G::B) * sizeof(float2);
+  constexpr size_t cap = s4 <= kMax ? s4 : s3;
+  const size_t smem = ((size_t)a.n_arms * G::SLOT + NX + 2 * G::B) * sizeof(float2);
+  if (smem > cap) return cudaErrorInvalidValue;
+  static cudaError_t attr = allow_smem(k_psf_rows<NX>, cap);
   if (attr != cudaSuccess) return attr;
   const long long rows = a.row_end - a.row_begin;
-  WO_LAUNCH("tf_psf_rows", s, (k_psf_rows<NX><<<(unsigned)((rows + G::B - 1) / G::B), G::NT, G::SMEM, s>>>(a)));
+  WO_LAUNCH("tf_psf_rows", s, (k_psf_rows<NX><<<(unsigned)((rows + G::B - 1) / G::B), G::NT, smem, s>>>(a)));
   return cudaGetLastError();
 }
 

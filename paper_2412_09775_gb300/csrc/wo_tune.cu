@@ -1,0 +1,183 @@
+// wo_tune.cu - per-tile defocus auto-tuning (Results, physics-guided
+// auto-tuning; Fig. 2a(iv); Ext. Data Fig. 3; Methods, optical pooled screen
+// data): the loss of the 2D thin-object Tikhonov fit and its exact derivative
+// with respect to the tile's defocus, and an on-device Adam step.
+//
+// Per transverse frequency nu, with the data spectrum D_k and the TF pair
+// (H_k, dH_k) over the Z axial bins k (3D spectra; Parseval over z turns the
+// sum over planes into a sum over k, with a factor Z):
+//   F  = sum_k conj(H_k) D_k / (sum_k |H_k|^2 + Z eta)      (the 2D solve)
+//   R_k = D_k - H_k F                                       (residual)
+//   q  = sum_k |R_k|^2 + Z eta |F|^2                        (loss density)
+//   dq = -2 Re sum_k conj(dH_k F) R_k                       (its derivative)
+// dq is the partial derivative at fixed F: F minimises q, so dq/dF = 0 there
+// and the hand-written adjoint needs no derivative of the solve itself.  The
+// per-tile loss is sum_nu w(nu) q / (N_perp Z), w = 2 for the half-spectrum
+// bins that stand for a conjugate pair, 1 for x = 0 and x = X/2.
+#include "wo_fft.cuh"
+#include "wo_internal.h"
+
+namespace wo {
+
+namespace {
+constexpr int kTuneThreads = 256;
+
+__device__ __forceinline__ int freq_index(int i, int n) { return (i < (n + 1) / 2) ? i : i - n; }
+
+// Deterministic block sum of two doubles (fixed tree over kTuneThreads).
+__device__ __forceinline__ void block_sum2(double& a, double& b, double* red) {
+  red[threadIdx.x] = a;
+  red[kTuneThreads + threadIdx.x] = b;
+  __syncthreads();
+  for (int h = kTuneThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      red[threadIdx.x] += red[threadIdx.x + h];
+      red[kTuneThreads + threadIdx.x] += red[kTuneThreads + threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  a = red[0];
+  b = red[kTuneThreads];
+}
+}  // namespace
+
+// One thread per transverse frequency (column c = y * Xh + x of the half
+// spectrum), grid (ceil(Y*Xh / 256), n_tiles).  Consecutive threads read
+// consecutive columns of every axial plane: each pass over k is coalesced.
+__global__ void __launch_bounds__(kTuneThreads) k_tune_cols(const float2* __restrict__ tf2,
+                                                            const float2* __restrict__ spec,
+                                                            const wo_optics* __restrict__ optics, int Z, int Y,
+                                                            int Xh, int X, float eta, float nu_max,
+                                                            double* __restrict__ partials) {
+  __shared__ double red[2 * kTuneThreads];
+  const int t = blockIdx.y;
+  const long long plane = (long long)Y * Xh;
+  const long long c = (long long)blockIdx.x * kTuneThreads + threadIdx.x;
+  double val = 0.0, grad = 0.0;
+  bool on = c < plane;
+  int x = 0;
+  if (on) {
+    const int y = (int)(c / Xh);
+    x = (int)(c - (long long)y * Xh);
+    if (nu_max > 0.f) {
+      const double p = optics[t].pixel_um;
+      const double fy = (double)freq_index(y, Y) / ((double)Y * p), fx = (double)x / ((double)X * p);
+      on = fx * fx + fy * fy <= (double)nu_max * (double)nu_max;
+    }
+  }
+  if (on) {
+    const float2* D = spec + (long long)t * Z * plane + c;
+    const float2* H = tf2 + (long long)t * 2 * Z * plane + c;
+    const float2* dH = H + (long long)Z * plane;
+    float cr = 0.f, ci = 0.f, hh = 0.f;
+#pragma unroll 4
+    for (int k = 0; k < Z; ++k) {
+      const float2 d = __ldg(D + k * plane), h = __ldg(H + k * plane);
+      const float2 r = cmulc(h, d);
+      cr += r.x;
+      ci += r.y;
+      hh += cabs2(h);
+    }
+    const float den = hh + (float)Z * eta;
+    const float inv = den > 0.f ? 1.0f / den : 0.f;
+    const float2 F = make_float2(cr * inv, ci * inv);
+    float rr = 0.f, gg = 0.f;
+#pragma unroll 4
+    for (int k = 0; k < Z; ++k) {
+      const float2 d = __ldg(D + k * plane), h = __ldg(H + k * plane), dh = __ldg(dH + k * plane);
+      const float2 R = csub(d, cmul(h, F));
+      const float2 q = cmul(dh, F);
+      rr += cabs2(R);
+      gg += q.x * R.x + q.y * R.y;  // Re(conj(q) R)
+    }
+    const double w = (x == 0 || 2 * x == X) ? 1.0 : 2.0;
+    val = w * ((double)rr + (double)Z * (double)eta * (double)cabs2(F));
+    grad = w * (-2.0 * (double)gg);
+  }
+  block_sum2(val, grad, red);
+  if (threadIdx.x == 0) {
+    double* p = partials + ((long long)t * gridDim.x + blockIdx.x) * 2;
+    p[0] = val;
+    p[1] = grad;
+  }
+}
+
+// One warp per tile: the tile's partials in a fixed order, then the scale.
+__global__ void k_tune_final(const double* __restrict__ partials, int nblk, double scale,
+                             double* __restrict__ value, double* __restrict__ grad) {
+  const int t = blockIdx.x, lane = threadIdx.x;
+  double v = 0.0, g = 0.0;
+  for (int i = lane; i < nblk; i += 32) {
+    v += partials[((long long)t * nblk + i) * 2];
+    g += partials[((long long)t * nblk + i) * 2 + 1];
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    v += __shfl_down_sync(0xffffffffu, v, off);
+    g += __shfl_down_sync(0xffffffffu, g, off);
+  }
+  if (lane == 0) {
+    if (value) value[t] = v * scale;
+    if (grad) grad[t] = g * scale;
+  }
+}
+
+cudaError_t tune_reduce(const float2* tf2, const float2* spec, const wo_optics* optics, int n_tiles, int Z,
+                        int Y, int X, float eta, float nu_max, double* partials, double* value, double* grad,
+                        cudaStream_t s) {
+  const int Xh = X / 2 + 1;
+  const long long plane = (long long)Y * Xh;
+  const unsigned nblk = (unsigned)((plane + kTuneThreads - 1) / kTuneThreads);
+  dim3 grid(nblk, (unsigned)n_tiles);
+  WO_LAUNCH("tune_cols", s,
+            (k_tune_cols<<<grid, kTuneThreads, 0, s>>>(tf2, spec, optics, Z, Y, Xh, X, eta, nu_max, partials)));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const double scale = 1.0 / ((double)X * (double)Y * (double)Z);
+  WO_LAUNCH("tune_final", s, (k_tune_final<<<(unsigned)n_tiles, 32, 0, s>>>(partials, (int)nblk, scale, value, grad)));
+  return cudaGetLastError();
+}
+
+size_t tune_partials_bytes(int n_tiles, int Y, int X) {
+  const long long plane = (long long)Y * (X / 2 + 1);
+  return (size_t)n_tiles * (size_t)((plane + kTuneThreads - 1) / kTuneThreads) * 2 * sizeof(double);
+}
+
+__global__ void k_zero_dc(float2* spec, int n_tiles, long long vol) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n_tiles) spec[(long long)t * vol] = make_float2(0.f, 0.f);
+}
+
+cudaError_t zero_dc(float2* spec, int n_tiles, long long vol, cudaStream_t s) {
+  WO_LAUNCH("zero_dc", s, (k_zero_dc<<<(unsigned)((n_tiles + 127) / 128), 128, 0, s>>>(spec, n_tiles, vol)));
+  return cudaGetLastError();
+}
+
+// Adam (Kingma and Ba, 2015) on each tile's defocus, with the moments and the
+// step count kept in device memory: state[t] = {m, v, steps}.
+__global__ void k_adam_defocus(wo_optics* __restrict__ optics, const double* __restrict__ grad,
+                               double* __restrict__ state, int n_tiles, double lr, double b1, double b2,
+                               double eps) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_tiles) return;
+  double* st = state + 3LL * t;
+  const double g = grad[t];
+  const double m = b1 * st[0] + (1.0 - b1) * g;
+  const double v = b2 * st[1] + (1.0 - b2) * g * g;
+  const double n = st[2] + 1.0;
+  st[0] = m;
+  st[1] = v;
+  st[2] = n;
+  const double mh = m / (1.0 - pow(b1, n));
+  const double vh = v / (1.0 - pow(b2, n));
+  optics[t].defocus_um -= lr * mh / (sqrt(vh) + eps);
+}
+
+cudaError_t adam_defocus(wo_optics* optics, const double* grad, double* state, int n_tiles, double lr,
+                         double b1, double b2, double eps, cudaStream_t s) {
+  WO_LAUNCH("adam_defocus", s,
+            (k_adam_defocus<<<(unsigned)((n_tiles + 127) / 128), 128, 0, s>>>(optics, grad, state, n_tiles, lr, b1,
+                                                                               b2, eps)));
+  return cudaGetLastError();
+}
+
+}  // namespace wo

@@ -57,6 +57,10 @@ def test_buffer_sizes(B):
     assert B.wo_tf_bytes(1, 16, 64, 63, 1) == 0          # odd X
     assert B.wo_workspace_bytes(1, 10, 64, 64, 1) == 0   # Z not supported
     assert B.wo_tf_bytes(1, 16, 64, 64, 0) == 0          # no kinds
+    # phase_dz: two TF slots per tile (phase TF and its defocus derivative)
+    assert B.wo_tf_bytes(n, Z, Y, X, 8) == ((n * 2 * Z * Y * Xh * 8 + 255) // 256) * 256 + n * 32
+    assert B.wo_workspace_bytes(n, Z, Y, X, 8) >= n * 4 * Z * Y * X * 8  # four pupil arms
+    assert B.wo_tf_bytes(1, 16, 64, 1024, 8) == 0 and B.wo_tf_bytes(1, 16, 64, 64, 12) == 0
 
 
 def test_build_tf_validation(B):
@@ -72,7 +76,9 @@ def test_build_tf_validation(B):
         (B.optics_array([ph.optics(z_step_um=0.4)]), 1, 16, 64, 64, 1, fake, fake, big, 4),  # axial
         (good, 1, 16, 64, 62, 1, fake, fake, big, 3),   # X/2 = 31
         (good, 1, 16, 64, 63, 1, fake, fake, big, 2),   # odd X
-        (good, 1, 16, 64, 64, 8, fake, fake, big, 1),   # bad kinds
+        (good, 1, 16, 64, 64, 16, fake, fake, big, 1),  # bad kinds
+        (good, 1, 16, 64, 64, 9, fake, fake, big, 1),   # phase_dz or-ed with phase
+        (good, 1, 16, 64, 1024, 8, fake, fake, big, 3),  # phase_dz beyond X = 768
         (good, 0, 16, 64, 64, 1, fake, fake, big, 1),   # no tiles
         (good, 1, 16, 64, 64, 1, fake + 4, fake, big, 1),  # misaligned
         (good, 1, 16, 64, 64, 1, None, fake, big, 1),   # null
@@ -97,6 +103,34 @@ def test_op_validation(B):
     assert lib.wo_reconstruct(fake, 7, fake, None, pe, 0, 0, fake, 1, 16, 64, 64, fake, 16, None) == 8
     assert lib.wo_forward(fake, 7, fake + 8, None, fake, 1, 16, 64, 64, fake, big, None) == 1
     assert lib.wo_forward_adjoint(fake, 7, fake, None, fake, 1, 16, 64, 100, fake, big, None) == 3
+
+
+def test_tuning_validation(B):
+    lib = B._lib
+    fake = 1 << 20
+    big = 1 << 40
+    d = ctypes.c_double
+    obj = lib.wo_defocus_objective
+    assert obj(fake, fake, fake, 1e-3, 0.0, None, None, 1, 16, 64, 64, fake, big, None) == 1  # no output
+    assert obj(fake, fake, fake, -1.0, 0.0, fake, fake, 1, 16, 64, 64, fake, big, None) == 1  # eta < 0
+    assert obj(fake, fake + 4, fake, 1e-3, 0.0, fake, fake, 1, 16, 64, 64, fake, big, None) == 1
+    assert obj(fake, fake, fake, 1e-3, 0.0, fake, fake + 4, 1, 16, 64, 64, fake, big, None) == 1
+    assert obj(fake, fake, fake, 1e-3, float("nan"), fake, fake, 1, 16, 64, 64, fake, big, None) == 1
+    assert obj(fake, fake, fake, 1e-3, 0.0, fake, fake, 1, 16, 64, 64, fake, 16, None) == 8
+    assert obj(fake, fake, fake, 1e-3, 0.0, fake, fake, 1, 16, 64, 1024, fake, big, None) == 3
+    assert obj(fake, fake, fake, 1e-3, 0.0, fake, fake, 1, 16, 64, 63, fake, big, None) == 2
+    adam = lib.wo_adam_defocus
+    assert adam(fake, fake, fake, 0, d(0.02), d(0.9), d(0.999), d(1e-8), None) == 1
+    assert adam(fake, fake, fake, 4, d(-0.02), d(0.9), d(0.999), d(1e-8), None) == 1
+    assert adam(fake, fake, fake, 4, d(0.02), d(1.0), d(0.999), d(1e-8), None) == 1
+    assert adam(fake, fake, fake, 4, d(0.02), d(0.9), d(0.999), d(0.0), None) == 1
+    assert adam(None, fake, fake, 4, d(0.02), d(0.9), d(0.999), d(1e-8), None) == 1
+    assert adam(fake, fake, fake + 4, 4, d(0.02), d(0.9), d(0.999), d(1e-8), None) == 1
+    spec = lib.wo_spectrum
+    assert spec(fake, None, fake, 1, 16, 64, 63, None) == 2
+    assert spec(fake, None, fake, 1, 10, 64, 64, None) == 3
+    assert spec(fake + 8, None, fake, 1, 16, 64, 64, None) == 1
+    assert spec(fake, None, fake, 0, 16, 64, 64, None) == 1
 
 
 def test_tile_validation(B):

@@ -437,3 +437,76 @@ def test_blend_of_constant_tiles_is_convex():
     assert out.min() >= 1.0 and out.max() <= 4.0
     # at the shared corner all four tiles weigh equally
     assert abs(out[core - 1: core + 1, core - 1: core + 1].mean() - 2.5) <= 1e-12
+
+
+# ------------------------------------------------ auto-tuning objective
+def test_tuning_objective_equals_rank_one_closed_form():
+    """min_F sum_j |D_j - H_j F|^2 + eta |F|^2 = sum_j |D_j|^2 - |H^H D|^2 / (||H||^2 + eta)
+    per transverse frequency (Parseval over the transform); the oracle
+    evaluates the definition (reconstruct, residual in real space)."""
+    from oracle import tuning
+    o = ph.optics(na_ill=0.6, tilt_x=0.04, defocus_um=0.3)
+    shape = (8, 32, 24)
+    d = 1 + 0.01 * np.random.default_rng(1).normal(size=shape)
+    eta = 1e-2
+    Hj = O.plane_tfs(o, shape, ("phase",))["phase"]
+    Dj = np.fft.fft2(d - d.mean(), axes=(1, 2))
+    q = (np.sum(np.abs(Dj) ** 2, 0)
+         - np.abs(np.sum(np.conj(Hj) * Dj, 0)) ** 2 / (np.sum(np.abs(Hj) ** 2, 0) + eta))
+    assert abs(tuning.objective(o, d, eta) - np.sum(q) / (32 * 24)) <= 1e-12 * np.sum(q)
+
+
+def test_tf_defocus_derivative_matches_finite_difference():
+    from oracle import tuning
+    o = ph.optics(na_ill=0.7, tilt_y=-0.03, defocus_um=-0.2)
+    shape = (6, 24, 32)
+    h = 1e-5
+    Hp = O.transfer_functions(dict(o, defocus_um=-0.2 + h), shape, ("phase",))["phase"]
+    Hm = O.transfer_functions(dict(o, defocus_um=-0.2 - h), shape, ("phase",))["phase"]
+    dH = tuning.tf_defocus_derivative(o, shape)
+    assert np.abs(dH - (Hp - Hm) / (2 * h)).max() <= 1e-7 * np.abs(dH).max()
+
+
+def test_tuning_objective_is_minimal_at_the_true_defocus():
+    """A thin band-limited object imaged at defocus z0 (noiseless): the loss
+    is smallest at z0 and its derivative vanishes there."""
+    from oracle import tuning
+    o = ph.optics(na_ill=0.5)
+    shape = (12, 48, 48)
+    Z, Y, X = shape
+    rng = np.random.default_rng(3)
+    ky, kx = np.fft.fftfreq(Y)[:, None], np.fft.fftfreq(X)[None, :]
+    f2 = 0.05 * np.real(np.fft.ifft2(np.fft.fft2(rng.normal(size=(Y, X))) * np.exp(-(ky ** 2 + kx ** 2) / 0.02)))
+    z0 = 0.35
+    Hj = O.plane_tfs(dict(o, defocus_um=z0), shape, ("phase",))["phase"]
+    d = np.real(np.fft.ifft2(Hj * np.fft.fft2(f2)[None], axes=(1, 2))) + 1.0
+    eta = 1e-6
+    L0 = tuning.objective_at(o, d, eta, z0)
+    for dz in (-0.1, -0.03, 0.03, 0.1):
+        assert tuning.objective_at(o, d, eta, z0 + dz) > L0
+    g = tuning.gradient_fd(dict(o, defocus_um=z0), d, eta, h=1e-4)
+    g_off = tuning.gradient_fd(dict(o, defocus_um=z0 + 0.1), d, eta, h=1e-4)
+    assert abs(g) <= 1e-3 * abs(g_off)
+
+
+def test_band_limited_objective_is_the_closed_form_over_the_band():
+    """Restricting the data to |nu| <= nu_max restricts the per-frequency sum
+    of the closed form to those frequencies (every frequency is solved on its
+    own), and a band above every grid frequency changes nothing."""
+    from oracle import tuning
+    o = ph.optics(na_ill=0.8, defocus_um=-0.2)
+    shape = (6, 40, 32)
+    Z, Y, X = shape
+    d = 1 + 0.02 * np.random.default_rng(4).normal(size=shape)
+    eta, nu_max = 1e-2, 1.37
+    Hj = O.plane_tfs(o, shape, ("phase",))["phase"]
+    Dj = np.fft.fft2(d - d.mean(), axes=(1, 2))
+    q = (np.sum(np.abs(Dj) ** 2, 0)
+         - np.abs(np.sum(np.conj(Hj) * Dj, 0)) ** 2 / (np.sum(np.abs(Hj) ** 2, 0) + eta))
+    fy = np.fft.fftfreq(Y, o["pixel_um"])[:, None]
+    fx = np.fft.fftfreq(X, o["pixel_um"])[None, :]
+    band = fy ** 2 + fx ** 2 <= nu_max ** 2
+    assert 10 < band.sum() < Y * X // 2
+    want = np.sum(q[band]) / (Y * X)
+    assert abs(tuning.objective(o, d, eta, nu_max) - want) <= 1e-12 * want
+    assert abs(tuning.objective(o, d, eta, 1e3) - tuning.objective(o, d, eta)) <= 1e-12 * want
