@@ -57,13 +57,17 @@ NCU_TRAFFIC = {"tf_psf_rows": {"bytes": 2 * (151.068160e6 + 105.373184e6), "dige
 
 
 def kernel_digest(name: str) -> str:
-    src = {"z_fused": "wo_zops.cu", "z_solve2d": "wo_zops.cu", "rows_r2c": "wo_rows.cu", "rows_c2r": "wo_rows.cu",
-           "y_fwd": "wo_cols.cu", "y_inv": "wo_cols.cu", "tf_ypass": "wo_cols.cu", "tf_arms": "wo_tf.cu",
-           "tf_psf_rows": "wo_tf.cu", "tf_zpass": "wo_tf.cu", "tf_pupil_record": "wo_tf.cu"}.get(name)
+    """Digest of the sources a kernel family is built from."""
+    tf = ["wo_tf.cu", "wo_tf.cuh"]
+    src = {"z_fused": ["wo_zops.cuh", "wo_zops_a.cu", "wo_zops_b.cu"],
+           "z_solve2d": ["wo_zops.cuh", "wo_zops_a.cu"], "rows_r2c": ["wo_rows.cu"], "rows_c2r": ["wo_rows.cu"],
+           "y_fwd": ["wo_cols.cu"], "y_inv": ["wo_cols.cu"], "tf_ypass": ["wo_cols.cu"], "tf_arms": tf,
+           "tf_psf_rows": tf + ["wo_psf.cu", "wo_regfft.cuh"], "tf_zpass": tf + ["wo_zops.cuh"],
+           "tf_pupil_record": tf, "tune_cols": ["wo_tune.cu"]}.get(name)
     if src is None:
         return ""
     h = hashlib.sha256()
-    for f in (src, "wo_fft.cuh"):
+    for f in src + ["wo_fft.cuh"]:
         with open(os.path.join(ROOT, "paper_2412_09775_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

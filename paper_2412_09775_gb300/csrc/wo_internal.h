@@ -79,6 +79,9 @@ struct TfArgs {
 cudaError_t tf_pupil_record(const TfArgs& a, cudaStream_t s);
 cudaError_t tf_arms(const TfArgs& a, cudaStream_t s);
 cudaError_t tf_psf_rows(const TfArgs& a, cudaStream_t s);
+// Register-resident variant of the PSF-row pass for short rows (wo_psf.cu).
+bool psf_rows_reg_supported(int X, int n_arms);
+cudaError_t tf_psf_rows_reg(const TfArgs& a, cudaStream_t s);
 cudaError_t tf_zpass(const TfArgs& a, cudaStream_t s);
 
 // Auto-tuning: per-tile value and defocus derivative of the 2D thin-object

@@ -1,0 +1,183 @@
+// wo_psf.cu - PSF rows of the transfer-function build with register-resident
+// row transforms (rows of 32 to 512 points).
+//
+// Same operation as k_psf_rows (wo_tf.cu): per row (tile t, plane j, row y)
+// of the arms after their y transform, the inverse transform along x of every
+// arm, the real PSF rows, and their forward transform along x into the TF
+// bank.  Here T lanes of a warp own a row (wo_regfft.cuh): the arms are read
+// from global memory straight into registers (columns outside the detection
+// band are zero and are not read), the products are formed in registers, and
+// every transform touches shared memory once (one transpose), with warp-level
+// synchronisation only.
+//
+// All real PSF rows are transformed as complex rows two at a time where the
+// kinds allow it: with the defocus derivative the row w = 2K (Re g + i Re g')
+// gives both TF rows from one transform (g' = conj(a') b + conj(a) b'):
+//   H(k) = (W(k) + W*(-k)) / 2,   dH(k) = (W(k) - W*(-k)) / (2i).
+// Label-free rows use the complex g = 2K conj(a) b as before:
+//   H_re(k) = (G(k) + G*(-k)) / 2,   H_im(k) = i (G(k) - G*(-k)) / 2.
+// W*(-k) lives in the lane that owns N - k; it is fetched with a shuffle.
+#include "wo_fft.cuh"
+#include "wo_internal.h"
+#include "wo_regfft.cuh"
+#include "wo_tf.cuh"
+
+namespace wo {
+
+namespace {
+constexpr int kPsfThreads = 128;
+
+template <class P>
+__device__ __forceinline__ void load_arm(float2 (&v)[P::E], const TfArgs& a, long long t, long long rem, int arm,
+                                         int kxm, int lane_t) {
+  constexpr int N = P::N, N1 = P::E, T = P::T;
+  const float2* src = a.arms + ((t * a.n_arms + arm) * a.Z) * (long long)a.Y * N + rem * N + lane_t;
+#pragma unroll
+  for (int m = 0; m < N1; ++m) {
+    const int n = lane_t + T * m;
+    v[m] = (abs(fft_index(n, N)) <= kxm) ? __ldg(src + T * m) : make_float2(0.f, 0.f);
+  }
+}
+
+// Register index holding W(N - k) in the lane that owns it (see wo_regfft.cuh):
+// for lane 0, point T m pairs with T ((N1 - m) mod N1); for lane t > 0, point
+// t + T m pairs with (T - t) + T (N1 - 1 - m).
+template <int N1>
+__device__ __forceinline__ float2 mirror_value(const float2 (&v)[N1], int m, bool lane0) {
+  return lane0 ? v[(N1 - m) % N1] : v[N1 - 1 - m];
+}
+}  // namespace
+
+// P: the row transform (Row2 or Row512 of wo_regfft.cuh).  DZ: the bank of
+// the phase TF and its defocus derivative (four arms); otherwise any mix of
+// label-free and fluorescence kinds.
+template <class P, bool DZ>
+__global__ void __launch_bounds__(kPsfThreads, 4) k_psf_rows_reg(TfArgs a) {
+  constexpr int N = P::N, N1 = P::E, T = P::T, RP = P::SLICE, RPC = kPsfThreads / T;
+  __shared__ float2 tw[P::TW];
+  __shared__ float2 slices[RPC * RP];
+  P::twiddles(tw);
+  __syncthreads();
+  const int lt = threadIdx.x % T, r = threadIdx.x / T;
+  const int lane = threadIdx.x & 31;
+  const int partner = (lane - lt) + (T - lt) % T;  // lane owning N - k
+  const bool lane0 = lt == 0;
+  float2* S = slices + r * RP;
+  const long long nrows = a.row_end;
+  const long long row = a.row_begin + (long long)blockIdx.x * RPC + r;
+  const bool live = row < nrows;
+  const long long rr = live ? row : nrows - 1;  // tail lanes compute on a valid row, store nothing
+  const long long zy = (long long)a.Z * a.Y;
+  const long long t = rr / zy, rem = rr - t * zy;  // rem = j*Y + y
+  const int kxm = a.counts[4 * t + 2];
+  const bool lf = a.lf_props > 0, fl = a.want_fl != 0;
+  const int Xh = N / 2 + 1;
+  float2* dst = a.tf + (t * a.n_kinds * a.Z) * (long long)a.Y * Xh + rem * Xh;  // slot 0 of this row
+  const long long kstride = (long long)a.Z * a.Y * Xh;
+
+  float2 w[N1];
+  int slot = 0;
+  if (DZ || lf) {
+    const float sc = lf_scale(a, (int)t);
+    float2 va[N1], vb[N1];
+    if constexpr (DZ) {
+      // w = 2K (Re conj(a) b + i (Re conj(a') b + Re conj(a) b')), arms A, B, A', B'
+      load_arm<P>(vb, a, t, rem, 1, kxm, lt);
+      P::template fft<true>(vb, tw, S, lt);
+      load_arm<P>(va, a, t, rem, 2, kxm, lt);
+      P::template fft<true>(va, tw, S, lt);
+#pragma unroll
+      for (int m = 0; m < N1; ++m) w[m].y = va[m].x * vb[m].x + va[m].y * vb[m].y;
+      load_arm<P>(va, a, t, rem, 0, kxm, lt);
+      P::template fft<true>(va, tw, S, lt);
+#pragma unroll
+      for (int m = 0; m < N1; ++m) w[m].x = va[m].x * vb[m].x + va[m].y * vb[m].y;
+      load_arm<P>(vb, a, t, rem, 3, kxm, lt);
+      P::template fft<true>(vb, tw, S, lt);
+#pragma unroll
+      for (int m = 0; m < N1; ++m) {
+        w[m].y += va[m].x * vb[m].x + va[m].y * vb[m].y;
+        w[m] = cscale(w[m], sc);
+      }
+    } else {
+      load_arm<P>(va, a, t, rem, 0, kxm, lt);
+      P::template fft<true>(va, tw, S, lt);
+      load_arm<P>(vb, a, t, rem, 1, kxm, lt);
+      P::template fft<true>(vb, tw, S, lt);
+#pragma unroll
+      for (int m = 0; m < N1; ++m) w[m] = cscale(cmulc(va[m], vb[m]), sc);
+    }
+    P::template fft<false>(w, tw, S, lt);
+#pragma unroll
+    for (int m = 0; m < N1; ++m) {
+      const float2 mv = mirror_value<N1>(w, m, lane0);
+      float2 c;  // conj(W(N - k))
+      c.x = __shfl_sync(0xffffffffu, mv.x, partner);
+      c.y = -__shfl_sync(0xffffffffu, mv.y, partner);
+      const int k = lt + T * m;
+      if (!live || k > N / 2) continue;
+      const float2 s = make_float2(0.5f * (w[m].x + c.x), 0.5f * (w[m].y + c.y));  // (W + W*(-k)) / 2
+      const float2 d = make_float2(0.5f * (w[m].x - c.x), 0.5f * (w[m].y - c.y));  // (W - W*(-k)) / 2
+      if constexpr (DZ) {
+        dst[k] = s;
+        dst[kstride + k] = make_float2(d.y, -d.x);  // d / i
+      } else {
+        int q = 0;
+        if (a.want_phase) dst[(q++) * kstride + k] = s;
+        if (a.want_abs) dst[(q++) * kstride + k] = make_float2(-d.y, d.x);  // i d
+      }
+    }
+    slot = DZ ? 2 : a.lf_props;
+  }
+  if (!DZ && fl) {
+    const float scf = fl_scale(a, (int)t);
+    load_arm<P>(w, a, t, rem, lf ? 2 : 0, kxm, lt);
+    P::template fft<true>(w, tw, S, lt);
+#pragma unroll
+    for (int m = 0; m < N1; ++m) w[m] = make_float2(scf * cabs2(w[m]), 0.f);
+    P::template fft<false>(w, tw, S, lt);
+#pragma unroll
+    for (int m = 0; m < N1; ++m) {
+      const int k = lt + T * m;
+      if (live && k <= N / 2) dst[slot * kstride + k] = w[m];
+    }
+  }
+}
+
+template <class P, bool DZ>
+static cudaError_t launch_psf_reg(const TfArgs& a, cudaStream_t s) {
+  constexpr int RPC = kPsfThreads / P::T;
+  const long long rows = a.row_end - a.row_begin;
+  const unsigned grid = (unsigned)((rows + RPC - 1) / RPC);
+  WO_LAUNCH("tf_psf_rows", s, (k_psf_rows_reg<P, DZ><<<grid, kPsfThreads, 0, s>>>(a)));
+  return cudaGetLastError();
+}
+
+template <class P>
+static cudaError_t launch_psf_reg_any(const TfArgs& a, cudaStream_t s) {
+  return a.want_dz ? launch_psf_reg<P, true>(a, s) : launch_psf_reg<P, false>(a, s);
+}
+
+bool psf_rows_reg_supported(int X, int n_arms) {
+  switch (X) {
+    case 32: case 48: case 64: case 128: case 256: case 512: return true;
+    case 96: case 192: return n_arms <= 3;  // 24 points per lane: four arms would spill
+    default: return false;
+  }
+}
+
+cudaError_t tf_psf_rows_reg(const TfArgs& a, cudaStream_t s) {
+  switch (a.X) {
+    case 32: return launch_psf_reg_any<Row2<32, 8>>(a, s);
+    case 48: return launch_psf_reg_any<Row2<48, 12>>(a, s);
+    case 64: return launch_psf_reg_any<Row2<64, 8>>(a, s);
+    case 96: return a.want_dz ? cudaErrorInvalidValue : launch_psf_reg<Row2<96, 24>, false>(a, s);
+    case 128: return launch_psf_reg_any<Row2<128, 16>>(a, s);
+    case 192: return a.want_dz ? cudaErrorInvalidValue : launch_psf_reg<Row2<192, 24>, false>(a, s);
+    case 256: return launch_psf_reg_any<Row2<256, 16>>(a, s);
+    case 512: return launch_psf_reg_any<Row512>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace wo

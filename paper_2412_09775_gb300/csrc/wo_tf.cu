@@ -23,11 +23,10 @@
 //                   used by the relative regulariser.
 #include "wo_fft.cuh"
 #include "wo_internal.h"
+#include "wo_tf.cuh"
 #include "wo_zops.cuh"
 
 namespace wo {
-
-__device__ __forceinline__ int fft_index(int i, int n) { return (i < (n + 1) / 2) ? i : i - n; }
 
 // One block per RY rows of one tile.  The frequency axes are computed once per
 // block (the same IEEE divisions as the float64 reference); the mask
@@ -222,21 +221,6 @@ struct PsfGeom {
   static constexpr int MINB = (1024 / NT) > 1 ? (1024 / NT) : 1;
   static constexpr int SLOT = NX * B + B;  // elements per arm slot (up to four arms)
 };
-
-__device__ __forceinline__ float lf_scale(const TfArgs& a, int t) {
-  // 2K = 2 c / (N_perp sum S P^2), c = 2 pi n dz / lambda^2
-  const wo_optics o = a.optics[t];
-  const int n_sp = a.counts[4 * t];
-  if (n_sp == 0) return 0.f;
-  const double c = 2.0 * 3.14159265358979323846 * o.n_medium * o.z_step_um / (o.lambda_um * o.lambda_um);
-  return (float)(2.0 * c / ((double)a.Y * (double)a.X * (double)n_sp));
-}
-
-__device__ __forceinline__ float fl_scale(const TfArgs& a, int t) {
-  const int n_p = a.counts[4 * t + 1];
-  if (n_p == 0) return 0.f;
-  return (float)(1.0 / ((double)a.Y * (double)a.X * (double)a.Z * (double)n_p));
-}
 
 // Per row (tile t, plane j, row y) of the arms after their y transform:
 // inverse transform along x of every arm, then the PSF rows and their forward
@@ -459,6 +443,7 @@ static cudaError_t launch_psf(const TfArgs& a, cudaStream_t s) {
 }
 
 cudaError_t tf_psf_rows(const TfArgs& a, cudaStream_t s) {
+  if (psf_rows_reg_supported(a.X, a.n_arms)) return tf_psf_rows_reg(a, s);
   switch (a.X) {
 #define WO_CASE(n) \
   case n:          \

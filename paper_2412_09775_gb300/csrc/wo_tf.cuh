@@ -1,0 +1,24 @@
+// wo_tf.cuh - device helpers shared by the transfer-function kernels.
+#pragma once
+#include "wo_internal.h"
+
+namespace wo {
+
+__device__ __forceinline__ int fft_index(int i, int n) { return (i < (n + 1) / 2) ? i : i - n; }
+
+__device__ __forceinline__ float lf_scale(const TfArgs& a, int t) {
+  // 2K = 2 c / (N_perp sum S P^2), c = 2 pi n dz / lambda^2
+  const wo_optics o = a.optics[t];
+  const int n_sp = a.counts[4 * t];
+  if (n_sp == 0) return 0.f;
+  const double c = 2.0 * 3.14159265358979323846 * o.n_medium * o.z_step_um / (o.lambda_um * o.lambda_um);
+  return (float)(2.0 * c / ((double)a.Y * (double)a.X * (double)n_sp));
+}
+
+__device__ __forceinline__ float fl_scale(const TfArgs& a, int t) {
+  const int n_p = a.counts[4 * t + 1];
+  if (n_p == 0) return 0.f;
+  return (float)(1.0 / ((double)a.Y * (double)a.X * (double)a.Z * (double)n_p));
+}
+
+}  // namespace wo
