@@ -49,11 +49,11 @@ WORKLOAD = "widefield 96x512x512: TF build (phase+absorption+fluorescence) + 3D 
 CPU_SAMPLE = (96, 256, 256)
 
 # Last ncu capture of DRAM traffic per launch (bytes) of the dominant kernel,
-# keyed by kernel family and the digest of its source file at capture time
-# (reported as null once the source changes).  tf_psf_rows: 151.1 MB read +
-# 105.4 MB written on the 48x512x512 case (profiles/psf_rows_arms_cols_48x512x512.md),
+# keyed by kernel family and the digest of its sources at capture time
+# (reported as null once a source changes).  tf_psf_rows: 151.1 MB read +
+# 104.6 MB written on the 48x512x512 case (profiles/tf_psf_rows_widefield_48x512x512.md),
 # scaled by 2 to the 96-plane launch (traffic grows with the planes processed).
-NCU_TRAFFIC = {"tf_psf_rows": {"bytes": 2 * (151.068160e6 + 105.373184e6), "digest": "cb8f73082bf4ec25"}}
+NCU_TRAFFIC = {"tf_psf_rows": {"bytes": 2 * (151.096320e6 + 104.627456e6), "digest": "5339ec2070fd668c"}}
 
 
 def kernel_digest(name: str) -> str:
