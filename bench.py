@@ -566,19 +566,20 @@ TUNE_SHAPE = (48, 128, 128)
 TUNE_ETA = 1e-3
 TUNE_WORKLOAD = ("defocus auto-tuning, 256 tiles of 48x128x128, per-tile optics: 50 Adam steps per tile from "
                  "defocus 0 (25 on the loss band-limited to 0.12 NA_det/lambda, lr 0.08->0.02 um; 25 on the full "
-                 "loss with fresh moments, lr 0.02->0 um); each step = TF pair build (phase TF + d/d defocus) + 2D "
-                 "thin-object loss and adjoint + Adam, one CUDA graph")
+                 "loss with fresh moments, lr 0.02->0 um); each step = per-plane TF pair build (phase TF + d/d "
+                 "defocus) + 2D thin-object loss and adjoint + Adam, one CUDA graph")
 
 
 def tune_algorithmic_bytes(o, n):
     """Compulsory HBM bytes per launch of each kernel family of one Adam step
-    over n tiles (phase TF + derivative: 4 arms, 2 TF slots)."""
+    over n tiles (phase TF + derivative: 4 arms, 2 per-plane TF slots, no z
+    transform)."""
     Z, Y, X = TUNE_SHAPE
     half = Z * Y * (X // 2 + 1) * 8
     arms = 4 * Z * Y * band_columns(o, X) * 8
     return {k: n * v for k, v in {
         "tf_pupil_record": Y * X * 16, "tf_arms": arms, "tf_psf_rows": arms + 2 * half,
-        "tf_ypass": 4 * half, "tf_zpass": 4 * half, "tune_cols": 3 * half}.items()}
+        "tf_ypass": 4 * half, "tune_cols": 3 * half}.items()}
 
 
 def make_tune_data(o_list, dev, seed=5):

@@ -81,6 +81,13 @@ enum { WO_TF_PHASE = 1, WO_TF_ABSORPTION = 2, WO_TF_FLUOR = 4 };
  * X <= 768.  wo_forward, wo_forward_adjoint and wo_reconstruct accept such a
  * bank with this kinds value and use its phase slot (a phase-only system). */
 enum { WO_TF_PHASE_DZ = 8 };
+/* Or-ed with WO_TF_PHASE_DZ only: keep the per-plane 2D TFs H_j(nu_perp) and
+ * dH_j/dz0 (slot layout unchanged, index j = plane instead of axial bin; the
+ * z-DFT is not applied and the statistics block holds only the optics
+ * status).  Such a bank serves wo_defocus_objective alone, which then takes
+ * per-plane data spectra (wo_spectrum, WO_MODE_2D) and skips a z transform
+ * per step; the operators reject it (WO_ERR_ARG). */
+enum { WO_TF_PLANES = 16 };
 enum { WO_MODE_3D = 0, WO_MODE_2D = 1 };
 enum { WO_ETA_RELATIVE = 0, WO_ETA_ABSOLUTE = 1 };
 
@@ -214,13 +221,14 @@ wo_status wo_tile_blend(const float *d_tiles, int Z, int tiles_y, int tiles_x,
  * parameters theta; Fig. 2a(iv); Ext. Data Fig. 3; Methods, optical pooled
  * screen data: 2D phase from a z-stack, Adam, fixed regulariser).
  *
- * wo_spectrum: the 3D half spectra [n_tiles][Z][Y][X/2+1] complex64 of
- * n_tiles brightfield stacks d_data [n_tiles][Z][Y][X] with the background
- * removed from the DC bin: D(0) - N b, b = h_background[0], or the stack's
- * mean when h_background is NULL (then D(0) = 0).  d_spec holds
- * n_tiles*Z*Y*(X/2+1)*8 bytes (caller-owned, 16-byte aligned).  Same shape
- * rules as wo_forward. */
-wo_status wo_spectrum(const float *d_data, const float *h_background, void *d_spec,
+ * wo_spectrum: the half spectra [n_tiles][Z][Y][X/2+1] complex64 of n_tiles
+ * brightfield stacks d_data [n_tiles][Z][Y][X]: 3D spectra (WO_MODE_3D) or
+ * each plane's 2D spectrum (WO_MODE_2D), with the background b removed:
+ * b = h_background[0], or the stack's mean when h_background is NULL.  In 3D
+ * the DC bin becomes D(0) - N b (0 for the mean); in 2D every plane's DC bin
+ * becomes D_j(0) - N_perp b.  d_spec holds n_tiles*Z*Y*(X/2+1)*8 bytes
+ * (caller-owned, 16-byte aligned).  Same shape rules as wo_forward. */
+wo_status wo_spectrum(const float *d_data, const float *h_background, int mode, void *d_spec,
                       int n_tiles, int Z, int Y, int X, wo_stream stream);
 
 /* wo_defocus_objective: per tile, the loss of the 2D thin-object fit (every
@@ -228,26 +236,30 @@ wo_status wo_spectrum(const float *d_data, const float *h_background, void *d_sp
  * TF H_j) at its Tikhonov minimiser, and its derivative with respect to the
  * tile's defocus:
  *   L(z0) = min_f sum_j ||d_j - b - H_j(z0) f||^2 + eta ||f||^2
- *         = (1/(N_perp Z)) sum_nu [ sum_k |D_k - H_k F|^2 + Z eta |F|^2 ],
- *   F(nu) = sum_k H_k* D_k / (sum_k |H_k|^2 + Z eta),
- *   dL/dz0 = (1/(N_perp Z)) sum_nu -2 Re sum_k (dH_k F)* (D_k - H_k F)
- * (k runs over the axial bins of the 3D spectra; the derivative needs no
- * derivative of F because F minimises the bracket).  Transverse frequencies
+ *         = (1/N_perp) sum_nu [ sum_j |D_j - H_j F|^2 + eta |F|^2 ],
+ *   F(nu) = sum_j H_j* D_j / (sum_j |H_j|^2 + eta),
+ *   dL/dz0 = (1/N_perp) sum_nu -2 Re sum_j (dH_j F)* (D_j - H_j F)
+ * (the derivative needs no derivative of F because F minimises the
+ * bracket).  kinds = WO_TF_PHASE_DZ | WO_TF_PLANES evaluates these sums over
+ * the planes j from per-plane banks and spectra; kinds = WO_TF_PHASE_DZ
+ * evaluates the same value over the axial bins k of 3D banks and spectra
+ * (Parseval over z: sum_j = (1/Z) sum_k, so eta enters as Z eta and the
+ * normalisation as 1/(N_perp Z)).  Transverse frequencies
  * with |nu| > nu_max (cycles/um) are left out of both sums when nu_max > 0
  * (0 or +inf: all frequencies): the loss of the band-limited data, whose
  * minimum in z0 is wider.  eta is absolute (>= 0).
- * d_tf: a WO_TF_PHASE_DZ bank of the same tiles; d_optics: the device optics
+ * d_tf: a bank of these kinds for the same tiles; d_optics: the device optics
  * the bank was built from (8-byte aligned; pixel_um sets the frequency grid);
- * d_spec: wo_spectrum of the data.  d_value, d_grad: n_tiles doubles each
+ * d_spec: wo_spectrum of the data in the matching mode.  d_value, d_grad: n_tiles doubles each
  * (8-byte aligned; either may be NULL, not both).  The workspace needs
  * n_tiles * ceil(Y*(X/2+1)/256) * 16 bytes, which wo_workspace_bytes(...,
  * WO_TF_PHASE_DZ) covers; the sums are reduced in a fixed order (repeatable
  * to the bit).  No host synchronisation: the call can be captured in a CUDA
  * graph together with wo_build_tf_device and wo_adam_defocus. */
-wo_status wo_defocus_objective(const void *d_tf, const wo_optics *d_optics, const void *d_spec,
-                               float eta, float nu_max, double *d_value, double *d_grad,
-                               int n_tiles, int Z, int Y, int X, void *d_ws, size_t ws_bytes,
-                               wo_stream stream);
+wo_status wo_defocus_objective(const void *d_tf, unsigned kinds, const wo_optics *d_optics,
+                               const void *d_spec, float eta, float nu_max, double *d_value,
+                               double *d_grad, int n_tiles, int Z, int Y, int X, void *d_ws,
+                               size_t ws_bytes, wo_stream stream);
 
 /* wo_adam_defocus: one Adam step (Kingma and Ba, 2015) on each tile's
  * defocus_um in the device optics array, from the gradient d_grad:

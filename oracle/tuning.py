@@ -63,13 +63,13 @@ def gradient_fd(o: dict, d: np.ndarray, eta: float, h: float = 1e-4, nu_max: flo
     return (objective_at(o, d, eta, z + h, nu_max) - objective_at(o, d, eta, z - h, nu_max)) / (2 * h)
 
 
-def tf_defocus_derivative(o: dict, shape) -> np.ndarray:
-    """dH_phase/d(defocus) of the 3D phase TF (complex128, (Z, Y, X)).
+def plane_tf_defocus_derivative(o: dict, shape) -> np.ndarray:
+    """dH_phase,j/d(defocus) of the per-plane 2D phase TFs (complex128, (Z, Y, X)).
 
     The defocus enters both arms through e^{i2pi eta z_j}, so
     d/dz [sum_nu A*(nu) B(nu+q)] = sum_nu A*(nu) B'(nu+q) + sum_nu A'*(nu) B(nu+q)
-    with A' = i 2 pi eta A and B' = i 2 pi eta B; the Table 1 combination and
-    the z-DFT are linear and carry over unchanged.
+    with A' = i 2 pi eta A and B' = i 2 pi eta B; Table 1's combination is
+    linear and carries over unchanged.
     """
     Z, Y, X = shape
     A, B = optics.arms(o, shape)
@@ -81,4 +81,9 @@ def tf_defocus_derivative(o: dict, shape) -> np.ndarray:
     dH1 = c * (optics.correlate(A, Bd) + optics.correlate(Ad, B))
     dH2 = np.conj(optics.reflect(dH1))
     T = optics.TABLE1_LABELFREE
-    return optics.stack_to_3d(T[0, 0] * dH1 + T[0, 1] * dH2)
+    return T[0, 0] * dH1 + T[0, 1] * dH2
+
+
+def tf_defocus_derivative(o: dict, shape) -> np.ndarray:
+    """dH_phase/d(defocus) of the 3D phase TF: the z-DFT of the per-plane derivative."""
+    return optics.stack_to_3d(plane_tf_defocus_derivative(o, shape))

@@ -8,7 +8,8 @@ the arithmetic runs in the library's kernels:
 
 * ``DefocusProblem`` holds the device buffers of one batch of tiles: their
   optics (float64 [n, 9], the device array the TF build reads), the data
-  spectra (wo_spectrum, computed once), a WO_TF_PHASE_DZ bank, the workspace,
+  spectra (wo_spectrum, computed once), a WO_TF_PHASE_DZ bank (per plane by
+  default: the loss needs no z transform, by Parseval), the workspace,
   and the per-tile loss, gradient and Adam state.
 * ``DefocusLoss`` is a torch.autograd.Function over the defocus vector: its
   forward builds the TF pair and evaluates loss and derivative in one pass,
@@ -30,7 +31,11 @@ PHASE_DZ = B.WO_TF_PHASE_DZ
 
 
 class DefocusProblem:
-    def __init__(self, data: torch.Tensor, optics_list, eta: float, background=None):
+    """``planes`` (default): per-plane TF banks and 2D data spectra, so no z
+    transform runs per step; otherwise 3D banks and spectra (the same loss by
+    Parseval over z)."""
+
+    def __init__(self, data: torch.Tensor, optics_list, eta: float, background=None, planes: bool = True):
         if data.dim() != 4 or data.dtype != torch.float32 or not data.is_cuda:
             raise ValueError("data: float32 CUDA tensor [n_tiles, Z, Y, X]")
         self.n, self.Z, self.Y, self.X = (int(s) for s in data.shape)
@@ -38,9 +43,11 @@ class DefocusProblem:
             raise ValueError("one optics entry per tile")
         dev = data.device
         self.eta = float(eta)
+        self.kinds = PHASE_DZ | (B.WO_TF_PLANES if planes else 0)
+        self.mode = B.WO_MODE_2D if planes else B.WO_MODE_3D
         self.optics = B.optics_tensor(optics_list, dev)
         self.optics0 = self.optics.clone()
-        self.tf, self.ws = B.alloc(self.n, self.Z, self.Y, self.X, PHASE_DZ, dev)
+        self.tf, self.ws = B.alloc(self.n, self.Z, self.Y, self.X, self.kinds, dev)
         self.spec = torch.empty((self.n, self.Z, self.Y, self.X // 2 + 1), dtype=torch.complex64, device=dev)
         self.background = background
         self.set_data(data)
@@ -52,7 +59,7 @@ class DefocusProblem:
 
     def set_data(self, data: torch.Tensor):
         """New stacks for the same tiles (the spectra are recomputed)."""
-        B.wo_spectrum(data.contiguous(), self.background, self.spec, self.n, self.Z, self.Y, self.X)
+        B.wo_spectrum(data.contiguous(), self.background, self.mode, self.spec, self.n, self.Z, self.Y, self.X)
 
     @property
     def defocus(self) -> torch.Tensor:
@@ -66,9 +73,9 @@ class DefocusProblem:
     def evaluate(self, nu_max: float = 0.0):
         """Loss and defocus derivative of every tile at the current optics."""
         n, Z, Y, X = self.n, self.Z, self.Y, self.X
-        B.wo_build_tf_device(self.optics, n, Z, Y, X, PHASE_DZ, self.tf, self.ws)
-        B.wo_defocus_objective(self.tf, self.optics, self.spec, self.eta, nu_max, self.value, self.grad, n, Z, Y, X,
-                               self.ws)
+        B.wo_build_tf_device(self.optics, n, Z, Y, X, self.kinds, self.tf, self.ws)
+        B.wo_defocus_objective(self.tf, self.kinds, self.optics, self.spec, self.eta, nu_max, self.value, self.grad,
+                               n, Z, Y, X, self.ws)
 
     def step(self, lr: float, nu_max: float = 0.0, beta1=0.9, beta2=0.999, eps=1e-8):
         self.evaluate(nu_max)

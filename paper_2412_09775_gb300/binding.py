@@ -17,10 +17,11 @@ LIB_PATH = os.path.join(HERE, "lib", "libwo_gb300.so")
 
 WO_TF_PHASE, WO_TF_ABSORPTION, WO_TF_FLUOR = 1, 2, 4
 WO_TF_PHASE_DZ = 8
+WO_TF_PLANES = 16
 WO_MODE_3D, WO_MODE_2D = 0, 1
 WO_ETA_RELATIVE, WO_ETA_ABSOLUTE = 0, 1
 KIND_BITS = {"phase": WO_TF_PHASE, "absorption": WO_TF_ABSORPTION, "fluor": WO_TF_FLUOR,
-             "phase_dz": WO_TF_PHASE_DZ}
+             "phase_dz": WO_TF_PHASE_DZ, "planes": WO_TF_PLANES}
 STATUS = {0: "WO_OK", 1: "WO_ERR_ARG", 2: "WO_ERR_SHAPE", 3: "WO_ERR_UNSUPPORTED_SIZE",
           4: "WO_ERR_UNDERSAMPLED", 5: "WO_ERR_CUDA", 6: "WO_ERR_TIMEOUT", 7: "WO_ERR_OPTICS",
           8: "WO_ERR_WORKSPACE"}
@@ -57,8 +58,8 @@ def _load():
         "wo_forward_adjoint": (i, [vp, u, vp, fp, vp, i, i, i, i, vp, sz, vp]),
         "wo_reconstruct": (i, [vp, u, vp, fp, fp, i, i, vp, i, i, i, i, vp, sz, vp]),
         "wo_reconstruct_static": (i, [vp, u, vp, fp, fp, i, i, vp, i, i, i, i, vp]),
-        "wo_spectrum": (i, [vp, fp, vp, i, i, i, i, vp]),
-        "wo_defocus_objective": (i, [vp, vp, vp, f, f, vp, vp, i, i, i, i, vp, sz, vp]),
+        "wo_spectrum": (i, [vp, fp, i, vp, i, i, i, i, vp]),
+        "wo_defocus_objective": (i, [vp, u, vp, vp, f, f, vp, vp, i, i, i, i, vp, sz, vp]),
         "wo_adam_defocus": (i, [vp, vp, vp, i, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                 ctypes.c_double, vp]),
         "wo_tile_gather": (i, [vp, i, i, i, i, i, vp, vp]),
@@ -206,18 +207,18 @@ def wo_reconstruct_static(tf, kinds, data, background, eta, eta_flag, mode, f, n
            "wo_reconstruct_static")
 
 
-def wo_spectrum(data, background, spec, n_tiles, Z, Y, X, stream=None):
-    """3D half spectra [n, Z, Y, X/2+1] (complex64 tensor `spec`) of brightfield stacks."""
+def wo_spectrum(data, background, mode, spec, n_tiles, Z, Y, X, stream=None):
+    """Half spectra [n, Z, Y, X/2+1] (complex64 tensor `spec`) of brightfield stacks, 3D or per plane."""
     bg = _floats(background)
-    _check(_lib.wo_spectrum(_ptr(data), bg[0] if bg else None, _ptr(spec), n_tiles, Z, Y, X, _stream(stream)),
-           "wo_spectrum")
+    _check(_lib.wo_spectrum(_ptr(data), bg[0] if bg else None, int(mode), _ptr(spec), n_tiles, Z, Y, X,
+                            _stream(stream)), "wo_spectrum")
 
 
-def wo_defocus_objective(tf, d_optics, spec, eta, nu_max, value, grad, n_tiles, Z, Y, X, ws, stream=None):
+def wo_defocus_objective(tf, kinds, d_optics, spec, eta, nu_max, value, grad, n_tiles, Z, Y, X, ws, stream=None):
     """Per-tile loss and defocus derivative (float64 tensors [n] or None) from a phase_dz bank."""
-    _check(_lib.wo_defocus_objective(_ptr(tf), _ptr(d_optics), _ptr(spec), float(eta), float(nu_max), _ptr(value),
-                                     _ptr(grad), n_tiles, Z, Y, X, _ptr(ws), _nbytes(ws), _stream(stream)),
-           "wo_defocus_objective")
+    _check(_lib.wo_defocus_objective(_ptr(tf), kinds_mask(kinds), _ptr(d_optics), _ptr(spec), float(eta),
+                                     float(nu_max), _ptr(value), _ptr(grad), n_tiles, Z, Y, X, _ptr(ws),
+                                     _nbytes(ws), _stream(stream)), "wo_defocus_objective")
 
 
 def wo_adam_defocus(d_optics, grad, state, n_tiles, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
@@ -261,7 +262,7 @@ def tf_views(tf, n_tiles, Z, Y, X, kinds):
     """(spectra, stats) views of a TF bank tensor: complex64 [n][k][Z][Y][X/2+1], float32 [n][8]."""
     import torch
     m = kinds_mask(kinds)
-    nk = 2 if m == WO_TF_PHASE_DZ else bin(m).count("1")
+    nk = 2 if (m & ~WO_TF_PLANES) == WO_TF_PHASE_DZ else bin(m).count("1")
     Xh = X // 2 + 1
     n_spec = n_tiles * nk * Z * Y * Xh
     raw = tf.view(torch.uint8)

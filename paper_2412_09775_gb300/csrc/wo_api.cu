@@ -64,7 +64,7 @@ static bool size_ok(int n) {
 
 struct Sys {
   int n_kinds, lf_props, has_fl, C, P, n_arms;
-  int want_phase, want_abs, want_dz;
+  int want_phase, want_abs, want_dz, planes;
 };
 
 static Sys system_of(unsigned kinds) {
@@ -77,7 +77,8 @@ static Sys system_of(unsigned kinds) {
   s.C = (s.lf_props ? 1 : 0) + s.has_fl;
   s.P = s.n_kinds;
   s.n_arms = (s.lf_props ? 2 : 0) + s.has_fl;
-  if (kinds == WO_TF_PHASE_DZ) {  // phase TF and its defocus derivative: two TF slots, four arms
+  if ((kinds & ~(unsigned)WO_TF_PLANES) == WO_TF_PHASE_DZ) {  // phase TF and d/dz0: two slots, four arms
+    s.planes = (kinds & WO_TF_PLANES) ? 1 : 0;
     s.want_phase = 1;
     s.want_dz = 1;
     s.lf_props = 1;
@@ -132,14 +133,16 @@ static size_t zpass_smem(int Z) {
 
 static wo_status check_shape(int n_tiles, int Z, int Y, int X, unsigned kinds) {
   if (n_tiles < 1 || n_tiles > 65535) return WO_ERR_ARG;
-  if (kinds == 0 || (kinds & ~15u)) return WO_ERR_ARG;
-  if ((kinds & WO_TF_PHASE_DZ) && kinds != WO_TF_PHASE_DZ) return WO_ERR_ARG;
+  if (kinds == 0 || (kinds & ~31u)) return WO_ERR_ARG;
+  const unsigned base = kinds & ~(unsigned)WO_TF_PLANES;
+  if ((base & WO_TF_PHASE_DZ) && base != WO_TF_PHASE_DZ) return WO_ERR_ARG;
+  if ((kinds & WO_TF_PLANES) && base != WO_TF_PHASE_DZ) return WO_ERR_ARG;
   if (Z < 1 || Y < 1 || X < 2) return WO_ERR_SHAPE;
   if (X % 2) return WO_ERR_SHAPE;
   if (!size_ok(Z) || !size_ok(Y) || !size_ok(X / 2) || X > 2048) return WO_ERR_UNSUPPORTED_SIZE;
   if (zpass_smem(Z) > 227 * 1024) return WO_ERR_UNSUPPORTED_SIZE;
   // four arm rows of X per PSF-row block must fit shared memory
-  if (kinds == WO_TF_PHASE_DZ && X > 768) return WO_ERR_UNSUPPORTED_SIZE;
+  if (base == WO_TF_PHASE_DZ && X > 768) return WO_ERR_UNSUPPORTED_SIZE;
   return WO_OK;
 }
 
@@ -285,7 +288,7 @@ static wo_status build_tf_impl(const wo_optics* optics, bool on_host, int n_tile
   const int Xh = X / 2 + 1;
   WO_TRY(cols_c2c(Y, false, a.tf, Xh, (long long)Y * Xh, Xh, (long long)n_tiles * s.n_kinds * Z, cs,
                   "tf_ypass"));
-  WO_TRY(tf_zpass(a, cs));
+  if (!s.planes) WO_TRY(tf_zpass(a, cs));  // per-plane banks stop before the z transform
   return WO_OK;
 }
 
@@ -305,6 +308,7 @@ static wo_status run_op(int op, const void* d_tf, unsigned kinds, const float* d
                         int Y, int X, void* d_ws, size_t ws_bytes, wo_stream stream) {
   wo_status st = check_shape(n_tiles, Z, Y, X, kinds);
   if (st != WO_OK) return st;
+  if (kinds & WO_TF_PLANES) return WO_ERR_ARG;  // the operators need the 3D TFs
   if (!aligned16(d_tf) || !aligned16(d_in) || !aligned16(d_out) || !aligned16(d_ws)) return WO_ERR_ARG;
   const Sys s = system_of(kinds);
   if (op == 2) {
@@ -408,10 +412,11 @@ wo_status wo_reconstruct(const void* d_tf, unsigned kinds, const float* d_data, 
                 ws_bytes, stream);
 }
 
-wo_status wo_spectrum(const float* d_data, const float* h_background, void* d_spec, int n_tiles, int Z, int Y,
-                      int X, wo_stream stream) {
+wo_status wo_spectrum(const float* d_data, const float* h_background, int mode, void* d_spec, int n_tiles, int Z,
+                      int Y, int X, wo_stream stream) {
   wo_status st = check_shape(n_tiles, Z, Y, X, WO_TF_PHASE);
   if (st != WO_OK) return st;
+  if (mode != WO_MODE_3D && mode != WO_MODE_2D) return WO_ERR_ARG;
   if (!aligned16(d_data) || !aligned16(d_spec)) return WO_ERR_ARG;
   if (h_background && !isfinite(h_background[0])) return WO_ERR_ARG;
   cudaStream_t cs = (cudaStream_t)stream;
@@ -425,20 +430,24 @@ wo_status wo_spectrum(const float* d_data, const float* h_background, void* d_sp
     bg.mode = 1;
     bg.v[0] = h_background[0];
   } else {
-    bg.mode = 2;  // only moves the DC bin, which is zeroed below
+    bg.mode = 2;  // a constant per stack only moves the DC bins, fixed below
   }
   WO_TRY(rows_r2c(H, d_data, spec, (long long)n_tiles * Z * Y, bg, cs));
   WO_TRY(cols_c2c(Y, false, spec, Xh, plane, Xh, (long long)n_tiles * Z, cs, "y_fwd"));
-  WO_TRY(cols_c2c(Z, false, spec, plane, (long long)Z * plane, (int)plane, n_tiles, cs, "z_fwd"));
-  if (!h_background)
-    WO_TRY(zero_dc(spec, n_tiles, (long long)Z * plane, cs));
+  if (mode == WO_MODE_3D) {
+    WO_TRY(cols_c2c(Z, false, spec, plane, (long long)Z * plane, (int)plane, n_tiles, cs, "z_fwd"));
+    if (!h_background) WO_TRY(zero_dc(spec, n_tiles, (long long)Z * plane, cs));
+  } else if (!h_background) {
+    WO_TRY(center_dc_planes(spec, n_tiles, Z, plane, cs));
+  }
   return WO_OK;
 }
 
-wo_status wo_defocus_objective(const void* d_tf, const wo_optics* d_optics, const void* d_spec, float eta,
-                               float nu_max, double* d_value, double* d_grad, int n_tiles, int Z, int Y, int X,
-                               void* d_ws, size_t ws_bytes, wo_stream stream) {
-  wo_status st = check_shape(n_tiles, Z, Y, X, WO_TF_PHASE_DZ);
+wo_status wo_defocus_objective(const void* d_tf, unsigned kinds, const wo_optics* d_optics, const void* d_spec,
+                               float eta, float nu_max, double* d_value, double* d_grad, int n_tiles, int Z, int Y,
+                               int X, void* d_ws, size_t ws_bytes, wo_stream stream) {
+  if (kinds != WO_TF_PHASE_DZ && kinds != (WO_TF_PHASE_DZ | WO_TF_PLANES)) return WO_ERR_ARG;
+  wo_status st = check_shape(n_tiles, Z, Y, X, kinds);
   if (st != WO_OK) return st;
   if (!aligned16(d_tf) || !aligned16(d_spec) || !aligned16(d_ws)) return WO_ERR_ARG;
   if (!d_optics || (((uintptr_t)d_optics) & 7u)) return WO_ERR_ARG;
@@ -447,8 +456,8 @@ wo_status wo_defocus_objective(const void* d_tf, const wo_optics* d_optics, cons
   if (!(eta >= 0.f) || !isfinite(eta) || !(nu_max == nu_max)) return WO_ERR_ARG;
   if (ws_bytes < tune_partials_bytes(n_tiles, Y, X)) return WO_ERR_WORKSPACE;
   return cuda_status(tune_reduce((const float2*)d_tf, (const float2*)d_spec, d_optics, n_tiles, Z, Y, X, eta,
-                                 isfinite(nu_max) ? nu_max : 0.f, (double*)d_ws, d_value, d_grad,
-                                 (cudaStream_t)stream));
+                                 isfinite(nu_max) ? nu_max : 0.f, (kinds & WO_TF_PLANES) ? 1 : Z, (double*)d_ws,
+                                 d_value, d_grad, (cudaStream_t)stream));
 }
 
 wo_status wo_adam_defocus(wo_optics* d_optics, const double* d_grad, double* d_state, int n_tiles, double lr,

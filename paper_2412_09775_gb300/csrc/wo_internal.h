@@ -88,12 +88,17 @@ cudaError_t tf_zpass(const TfArgs& a, cudaStream_t s);
 // loss from a data spectrum [tile][Z][Y][Xh] and a TF pair bank (H, dH/dz)
 // [tile][2][Z][Y][Xh]; frequencies above nu_max (cycles/um, > 0) are left
 // out.  `partials` holds tune_partials_bytes(n_tiles, Y, X) bytes.
+// zf: Z for 3D spectra (Parseval over z puts a factor Z on the eta term and
+// on the normalisation), 1 for per-plane 2D spectra.
 cudaError_t tune_reduce(const float2* tf2, const float2* spec, const wo_optics* optics, int n_tiles, int Z,
-                        int Y, int X, float eta, float nu_max, double* partials, double* value, double* grad,
+                        int Y, int X, float eta, float nu_max, int zf, double* partials, double* value, double* grad,
                         cudaStream_t s);
 size_t tune_partials_bytes(int n_tiles, int Y, int X);
 // Zero element 0 of each of n_tiles volumes of vol elements (the DC bin).
 cudaError_t zero_dc(float2* spec, int n_tiles, long long vol, cudaStream_t s);
+// Per-plane 2D spectra [tile][Z][plane]: subtract from each plane's DC bin the
+// mean of the tile's DC bins (background = the stack's mean).
+cudaError_t center_dc_planes(float2* spec, int n_tiles, int Z, long long plane, cudaStream_t s);
 cudaError_t adam_defocus(wo_optics* optics, const double* grad, double* state, int n_tiles, double lr,
                          double b1, double b2, double eps, cudaStream_t s);
 

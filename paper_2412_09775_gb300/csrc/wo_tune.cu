@@ -4,15 +4,16 @@
 // with respect to the tile's defocus, and an on-device Adam step.
 //
 // Per transverse frequency nu, with the data spectrum D_k and the TF pair
-// (H_k, dH_k) over the Z axial bins k (3D spectra; Parseval over z turns the
-// sum over planes into a sum over k, with a factor Z):
-//   F  = sum_k conj(H_k) D_k / (sum_k |H_k|^2 + Z eta)      (the 2D solve)
+// (H_k, dH_k) over the Z entries k of a column - either the per-plane 2D
+// spectra (k = plane j, zf = 1) or the 3D spectra (k = axial bin; Parseval
+// over z turns the sum over planes into a sum over k with a factor zf = Z):
+//   F  = sum_k conj(H_k) D_k / (sum_k |H_k|^2 + zf eta)     (the 2D solve)
 //   R_k = D_k - H_k F                                       (residual)
-//   q  = sum_k |R_k|^2 + Z eta |F|^2                        (loss density)
+//   q  = sum_k |R_k|^2 + zf eta |F|^2                       (loss density)
 //   dq = -2 Re sum_k conj(dH_k F) R_k                       (its derivative)
 // dq is the partial derivative at fixed F: F minimises q, so dq/dF = 0 there
 // and the hand-written adjoint needs no derivative of the solve itself.  The
-// per-tile loss is sum_nu w(nu) q / (N_perp Z), w = 2 for the half-spectrum
+// per-tile loss is sum_nu w(nu) q / (N_perp zf), w = 2 for the half-spectrum
 // bins that stand for a conjugate pair, 1 for x = 0 and x = X/2.
 #include "wo_fft.cuh"
 #include "wo_internal.h"
@@ -47,7 +48,7 @@ __device__ __forceinline__ void block_sum2(double& a, double& b, double* red) {
 __global__ void __launch_bounds__(kTuneThreads) k_tune_cols(const float2* __restrict__ tf2,
                                                             const float2* __restrict__ spec,
                                                             const wo_optics* __restrict__ optics, int Z, int Y,
-                                                            int Xh, int X, float eta, float nu_max,
+                                                            int Xh, int X, float eta, float nu_max, int zf,
                                                             double* __restrict__ partials) {
   __shared__ double red[2 * kTuneThreads];
   const int t = blockIdx.y;
@@ -78,7 +79,7 @@ __global__ void __launch_bounds__(kTuneThreads) k_tune_cols(const float2* __rest
       ci += r.y;
       hh += cabs2(h);
     }
-    const float den = hh + (float)Z * eta;
+    const float den = hh + (float)zf * eta;
     const float inv = den > 0.f ? 1.0f / den : 0.f;
     const float2 F = make_float2(cr * inv, ci * inv);
     float rr = 0.f, gg = 0.f;
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(kTuneThreads) k_tune_cols(const float2* __rest
       gg += q.x * R.x + q.y * R.y;  // Re(conj(q) R)
     }
     const double w = (x == 0 || 2 * x == X) ? 1.0 : 2.0;
-    val = w * ((double)rr + (double)Z * (double)eta * (double)cabs2(F));
+    val = w * ((double)rr + (double)zf * (double)eta * (double)cabs2(F));
     grad = w * (-2.0 * (double)gg);
   }
   block_sum2(val, grad, red);
@@ -122,17 +123,17 @@ __global__ void k_tune_final(const double* __restrict__ partials, int nblk, doub
 }
 
 cudaError_t tune_reduce(const float2* tf2, const float2* spec, const wo_optics* optics, int n_tiles, int Z,
-                        int Y, int X, float eta, float nu_max, double* partials, double* value, double* grad,
+                        int Y, int X, float eta, float nu_max, int zf, double* partials, double* value, double* grad,
                         cudaStream_t s) {
   const int Xh = X / 2 + 1;
   const long long plane = (long long)Y * Xh;
   const unsigned nblk = (unsigned)((plane + kTuneThreads - 1) / kTuneThreads);
   dim3 grid(nblk, (unsigned)n_tiles);
   WO_LAUNCH("tune_cols", s,
-            (k_tune_cols<<<grid, kTuneThreads, 0, s>>>(tf2, spec, optics, Z, Y, Xh, X, eta, nu_max, partials)));
+            (k_tune_cols<<<grid, kTuneThreads, 0, s>>>(tf2, spec, optics, Z, Y, Xh, X, eta, nu_max, zf, partials)));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const double scale = 1.0 / ((double)X * (double)Y * (double)Z);
+  const double scale = 1.0 / ((double)X * (double)Y * (double)zf);
   WO_LAUNCH("tune_final", s, (k_tune_final<<<(unsigned)n_tiles, 32, 0, s>>>(partials, (int)nblk, scale, value, grad)));
   return cudaGetLastError();
 }
@@ -149,6 +150,32 @@ __global__ void k_zero_dc(float2* spec, int n_tiles, long long vol) {
 
 cudaError_t zero_dc(float2* spec, int n_tiles, long long vol, cudaStream_t s) {
   WO_LAUNCH("zero_dc", s, (k_zero_dc<<<(unsigned)((n_tiles + 127) / 128), 128, 0, s>>>(spec, n_tiles, vol)));
+  return cudaGetLastError();
+}
+
+// One warp per tile: subtract the mean of the Z per-plane DC bins from each.
+__global__ void k_center_dc_planes(float2* spec, int n_tiles, int Z, long long plane) {
+  const int t = blockIdx.x, lane = threadIdx.x;
+  float2* base = spec + (long long)t * Z * plane;
+  double sx = 0.0, sy = 0.0;
+  for (int j = lane; j < Z; j += 32) {
+    sx += base[(long long)j * plane].x;
+    sy += base[(long long)j * plane].y;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    sx += __shfl_xor_sync(0xffffffffu, sx, off);
+    sy += __shfl_xor_sync(0xffffffffu, sy, off);
+  }
+  const float mx = (float)(sx / Z), my = (float)(sy / Z);
+  __syncwarp();
+  for (int j = lane; j < Z; j += 32) {
+    float2& d = base[(long long)j * plane];
+    d = make_float2(d.x - mx, d.y - my);
+  }
+}
+
+cudaError_t center_dc_planes(float2* spec, int n_tiles, int Z, long long plane, cudaStream_t s) {
+  WO_LAUNCH("center_dc", s, (k_center_dc_planes<<<(unsigned)n_tiles, 32, 0, s>>>(spec, n_tiles, Z, plane)));
   return cudaGetLastError();
 }
 

@@ -111,14 +111,18 @@ def test_tuning_validation(B):
     big = 1 << 40
     d = ctypes.c_double
     obj = lib.wo_defocus_objective
-    assert obj(fake, fake, fake, 1e-3, 0.0, None, None, 1, 16, 64, 64, fake, big, None) == 1  # no output
-    assert obj(fake, fake, fake, -1.0, 0.0, fake, fake, 1, 16, 64, 64, fake, big, None) == 1  # eta < 0
-    assert obj(fake, fake + 4, fake, 1e-3, 0.0, fake, fake, 1, 16, 64, 64, fake, big, None) == 1
-    assert obj(fake, fake, fake, 1e-3, 0.0, fake, fake + 4, 1, 16, 64, 64, fake, big, None) == 1
-    assert obj(fake, fake, fake, 1e-3, float("nan"), fake, fake, 1, 16, 64, 64, fake, big, None) == 1
-    assert obj(fake, fake, fake, 1e-3, 0.0, fake, fake, 1, 16, 64, 64, fake, 16, None) == 8
-    assert obj(fake, fake, fake, 1e-3, 0.0, fake, fake, 1, 16, 64, 1024, fake, big, None) == 3
-    assert obj(fake, fake, fake, 1e-3, 0.0, fake, fake, 1, 16, 64, 63, fake, big, None) == 2
+    K = 8  # WO_TF_PHASE_DZ
+    assert obj(fake, K, fake, fake, 1e-3, 0.0, None, None, 1, 16, 64, 64, fake, big, None) == 1  # no output
+    assert obj(fake, K, fake, fake, -1.0, 0.0, fake, fake, 1, 16, 64, 64, fake, big, None) == 1  # eta < 0
+    assert obj(fake, K, fake + 4, fake, 1e-3, 0.0, fake, fake, 1, 16, 64, 64, fake, big, None) == 1
+    assert obj(fake, K, fake, fake, 1e-3, 0.0, fake, fake + 4, 1, 16, 64, 64, fake, big, None) == 1
+    assert obj(fake, K, fake, fake, 1e-3, float("nan"), fake, fake, 1, 16, 64, 64, fake, big, None) == 1
+    assert obj(fake, K, fake, fake, 1e-3, 0.0, fake, fake, 1, 16, 64, 64, fake, 16, None) == 8
+    assert obj(fake, K | 16, fake, fake, 1e-3, 0.0, fake, fake, 1, 16, 64, 64, fake, 16, None) == 8
+    assert obj(fake, K, fake, fake, 1e-3, 0.0, fake, fake, 1, 16, 64, 1024, fake, big, None) == 3
+    assert obj(fake, K, fake, fake, 1e-3, 0.0, fake, fake, 1, 16, 64, 63, fake, big, None) == 2
+    assert obj(fake, 1, fake, fake, 1e-3, 0.0, fake, fake, 1, 16, 64, 64, fake, big, None) == 1  # not a dz bank
+    assert obj(fake, 16, fake, fake, 1e-3, 0.0, fake, fake, 1, 16, 64, 64, fake, big, None) == 1
     adam = lib.wo_adam_defocus
     assert adam(fake, fake, fake, 0, d(0.02), d(0.9), d(0.999), d(1e-8), None) == 1
     assert adam(fake, fake, fake, 4, d(-0.02), d(0.9), d(0.999), d(1e-8), None) == 1
@@ -127,10 +131,15 @@ def test_tuning_validation(B):
     assert adam(None, fake, fake, 4, d(0.02), d(0.9), d(0.999), d(1e-8), None) == 1
     assert adam(fake, fake, fake + 4, 4, d(0.02), d(0.9), d(0.999), d(1e-8), None) == 1
     spec = lib.wo_spectrum
-    assert spec(fake, None, fake, 1, 16, 64, 63, None) == 2
-    assert spec(fake, None, fake, 1, 10, 64, 64, None) == 3
-    assert spec(fake + 8, None, fake, 1, 16, 64, 64, None) == 1
-    assert spec(fake, None, fake, 0, 16, 64, 64, None) == 1
+    assert spec(fake, None, 0, fake, 1, 16, 64, 63, None) == 2
+    assert spec(fake, None, 0, fake, 1, 10, 64, 64, None) == 3
+    assert spec(fake + 8, None, 1, fake, 1, 16, 64, 64, None) == 1
+    assert spec(fake, None, 0, fake, 0, 16, 64, 64, None) == 1
+    assert spec(fake, None, 2, fake, 1, 16, 64, 64, None) == 1  # bad mode
+    # per-plane banks: only with the derivative kinds; the operators reject them
+    assert B.wo_tf_bytes(1, 16, 64, 64, 16) == 0 and B.wo_tf_bytes(1, 16, 64, 64, 17) == 0
+    assert B.wo_tf_bytes(1, 16, 64, 64, 24) == B.wo_tf_bytes(1, 16, 64, 64, 8)
+    assert lib.wo_forward(fake, 24, fake, None, fake, 1, 16, 64, 64, fake, big, None) == 1
 
 
 def test_tile_validation(B):

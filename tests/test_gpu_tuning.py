@@ -48,24 +48,31 @@ def nominal(o):
 
 
 # ------------------------------------------------------------ TF pair
+@pytest.mark.parametrize("planes", [False, True])
 @pytest.mark.parametrize("shape", [(8, 32, 48), (12, 64, 64), (6, 24, 96)])
-def test_phase_dz_bank_matches_oracle(env, shape):
+def test_phase_dz_bank_matches_oracle(env, shape, planes):
     B, _, torch, dev = env
     Z, Y, X = shape
     ol = [ph.optics(defocus_um=0.4, na_ill=0.6), ph.optics(defocus_um=-0.7, tilt_x=0.05, tilt_y=-0.08, na_ill=0.8),
           ph.optics(defocus_um=0.0, na_ill=0.9)]
     n = len(ol)
-    tf, ws = B.alloc(n, Z, Y, X, "phase_dz", dev)
-    B.wo_build_tf(ol, n, Z, Y, X, "phase_dz", tf, ws)
+    kinds = B.WO_TF_PHASE_DZ | (B.WO_TF_PLANES if planes else 0)
+    tf, ws = B.alloc(n, Z, Y, X, kinds, dev)
+    B.wo_build_tf(ol, n, Z, Y, X, kinds, tf, ws)
     torch.cuda.synchronize()
-    spec, stats = B.tf_views(tf, n, Z, Y, X, "phase_dz")
+    spec, stats = B.tf_views(tf, n, Z, Y, X, kinds)
     spec, stats = spec.cpu().numpy(), stats.cpu().numpy()
     for t, o in enumerate(ol):
-        H = OO.transfer_functions(o, shape, ("phase",))["phase"]
-        dH = OT.tf_defocus_derivative(o, shape)
+        if planes:  # per-plane 2D TFs, no z-DFT
+            H = OO.plane_tfs(o, shape, ("phase",))["phase"]
+            dH = OT.plane_tf_defocus_derivative(o, shape)
+        else:
+            H = OO.transfer_functions(o, shape, ("phase",))["phase"]
+            dH = OT.tf_defocus_derivative(o, shape)
         assert rel_l2(spec[t, 0], OO.half_spectrum(H)) <= 1e-4, t
         assert rel_l2(spec[t, 1], OO.half_spectrum(dH)) <= 1e-4, t
-        assert abs(stats[t, 0] / np.max(np.abs(H) ** 2) - 1) <= 1e-5
+        if not planes:
+            assert abs(stats[t, 0] / np.max(np.abs(H) ** 2) - 1) <= 1e-5
 
 
 def test_phase_dz_bank_reconstructs_like_a_phase_bank(env):
@@ -89,41 +96,51 @@ def test_phase_dz_bank_reconstructs_like_a_phase_bank(env):
 
 
 # ------------------------------------------------------------ spectra
+@pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("bg", [None, 0.97])
-def test_spectrum_matches_oracle(env, bg):
+def test_spectrum_matches_oracle(env, bg, mode):
+    """3D spectra (DC: D(0) - N b) and per-plane 2D spectra (every plane's DC:
+    D_j(0) - N_perp b), b given or the stack mean."""
     B, _, torch, dev = env
     n, Z, Y, X = 2, 12, 48, 64
     d = 1.0 + 0.05 * ph.uniform_volume(7, (n, Z, Y, X))
     spec = torch.empty((n, Z, Y, X // 2 + 1), dtype=torch.complex64, device=dev)
-    B.wo_spectrum(torch.tensor(d, dtype=torch.float32, device=dev), None if bg is None else [bg], spec, n, Z, Y, X)
+    B.wo_spectrum(torch.tensor(d, dtype=torch.float32, device=dev), None if bg is None else [bg], mode, spec,
+                  n, Z, Y, X)
     got = spec.cpu().numpy()
     for t in range(n):
-        want = OM.residual_spectrum(d[t], bg, (0, 1, 2))[..., : X // 2 + 1]
-        assert rel_l2(got[t], want) <= 1e-5
+        if mode == 0:
+            want = OM.residual_spectrum(d[t], bg, (0, 1, 2))
+        else:
+            b = float(np.mean(d[t])) if bg is None else bg
+            want = OM.residual_spectrum(d[t], b, (1, 2))
+        assert rel_l2(got[t], want[..., : X // 2 + 1]) <= 1e-5
 
 
 # ------------------------------------------------------------ loss and adjoint
-def problem(env, ol_true, start, eta, seed=11):
+def problem(env, ol_true, start, eta, seed=11, planes=True):
     B, A, torch, dev = env
     d = np.stack([thin_stack(o, SHAPE, seed + 17 * t) for t, o in enumerate(ol_true)])
     data = torch.tensor(d, dtype=torch.float32, device=dev)
-    return A.DefocusProblem(data, start, eta), d
+    return A.DefocusProblem(data, start, eta, planes=planes), d
 
 
 def cutoff(o):
     return o["na_det"] / o["lambda_um"]
 
 
+@pytest.mark.parametrize("planes", [True, False])
 @pytest.mark.parametrize("band", [None, 0.3])
-def test_loss_and_gradient_match_the_oracle_on_eight_tiles(env, band):
+def test_loss_and_gradient_match_the_oracle_on_eight_tiles(env, band, planes):
     """Value within 1e-4 and adjoint gradient within 1e-3 (relative) of the
-    float64 oracle's loss and its central-difference derivative."""
+    float64 oracle's loss and its central-difference derivative, from
+    per-plane and from 3D banks."""
     B, A, torch, dev = env
     ol = tiles(8, 21)
     offs = np.array([0.2, -0.15, 0.12, -0.18, 0.1, -0.2, 0.16, -0.1])
     start = [dict(o, defocus_um=o["defocus_um"] + s) for o, s in zip(ol, offs)]
     eta = 1e-3
-    pb, d = problem(env, ol, start, eta)
+    pb, d = problem(env, ol, start, eta, planes=planes)
     nu = 0.0 if band is None else band * cutoff(ol[0]) + 1e-3  # off the frequency grid
     pb.evaluate(nu)
     torch.cuda.synchronize()
