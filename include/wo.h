@@ -88,6 +88,7 @@ enum { WO_TF_PHASE_DZ = 8 };
  * per-plane data spectra (wo_spectrum, WO_MODE_2D) and skips a z transform
  * per step; the operators reject it (WO_ERR_ARG). */
 enum { WO_TF_PLANES = 16 };
+enum { WO_LOSS_DATA = 0, WO_LOSS_MIDBAND = 1 };
 enum { WO_MODE_3D = 0, WO_MODE_2D = 1 };
 enum { WO_ETA_RELATIVE = 0, WO_ETA_ABSOLUTE = 1 };
 
@@ -203,6 +204,27 @@ wo_status wo_reconstruct_static(const void *d_tf, unsigned kinds, const float *d
                                 int mode, float *d_f, int n_tiles, int Z, int Y, int X,
                                 wo_stream stream);
 
+/* Multi-channel fusion (9-aperture fusion, Results: several illumination
+ * apertures fused into one phase estimate; Eq. recon with C channels and
+ * P = 1): per frequency
+ *   F = sum_c conj(H_c) D~_c / (sum_c |H_c|^2 + eta_abs),
+ * D~_c the spectrum of channel c with its background removed from the DC bin
+ * (h_background[c], or the channel's mean when h_background is NULL).
+ * WO_MODE_3D: per 3D frequency, d_f [n_tiles][Z][Y][X].  WO_MODE_2D: the thin
+ * object, per transverse frequency with the sums over every plane of every
+ * channel, d_f [n_tiles][Y][X].  eta_flag: WO_ETA_ABSOLUTE, or
+ * WO_ETA_RELATIVE for eta_abs = eta * max_nu sum_c |H_c(nu)|^2 (3D) or
+ * eta * max_nu_perp sum_j sum_c |H_cj|^2 (2D), per tile.
+ * d_tf: a WO_TF_PHASE bank built for n_tiles * n_channels entries, channel
+ * c of tile t at entry t * n_channels + c (each with that aperture's optics).
+ * d_data: [n_tiles][n_channels][Z][Y][X].  1 <= n_channels <= 16.  The
+ * workspace holds wo_fused_workspace_bytes() bytes (0 on invalid arguments). */
+size_t wo_fused_workspace_bytes(int n_channels, int n_tiles, int Z, int Y, int X);
+wo_status wo_reconstruct_fused(const void *d_tf, int n_channels, const float *d_data,
+                               const float *h_background, float eta, int eta_flag, int mode,
+                               float *d_f, int n_tiles, int Z, int Y, int X, void *d_ws,
+                               size_t ws_bytes, wo_stream stream);
+
 /* Row a8 (gather).  Cut a field [Z][tiles_y*core][tiles_x*core] into
  * overlapping tiles [tiles_y*tiles_x][Z][E][E], E = core + 2*halo, tile
  * (ty, tx) starting at field pixel (ty*core - halo, tx*core - halo); pixels
@@ -231,7 +253,10 @@ wo_status wo_tile_blend(const float *d_tiles, int Z, int tiles_y, int tiles_x,
 wo_status wo_spectrum(const float *d_data, const float *h_background, int mode, void *d_spec,
                       int n_tiles, int Z, int Y, int X, wo_stream stream);
 
-/* wo_defocus_objective: per tile, the loss of the 2D thin-object fit (every
+/* wo_defocus_objective: per tile, a loss of the 2D thin-object reconstruction
+ * and its derivative with respect to the tile's defocus.
+ *
+ * loss = WO_LOSS_DATA: the loss of the 2D thin-object fit (every
  * plane j sees the object at the reference plane through the per-plane phase
  * TF H_j) at its Tikhonov minimiser, and its derivative with respect to the
  * tile's defocus:
@@ -248,6 +273,15 @@ wo_status wo_spectrum(const float *d_data, const float *h_background, int mode, 
  * with |nu| > nu_max (cycles/um) are left out of both sums when nu_max > 0
  * (0 or +inf: all frequencies): the loss of the band-limited data, whose
  * minimum in z0 is wider.  eta is absolute (>= 0).
+ *
+ * loss = WO_LOSS_MIDBAND: the paper's image-quality loss, minus the power of
+ * the reconstruction F in the mid band c/8 <= |nu| <= c/4 of the transverse
+ * cutoff c = (NA_det + NA_ill)/lambda:
+ *   L(z0) = -(1/N_perp) sum_band |F|^2,
+ *   dL/dz0 = -(2/N_perp) sum_band Re(F* dF),  dF = (sum_j dH_j* D_j - F dh) / (h + eta),
+ *   h = sum_j |H_j|^2, dh = 2 Re sum_j H_j* dH_j
+ * (F is not the minimiser of this loss, so the derivative goes through the
+ * solve).  nu_max is ignored.
  * d_tf: a bank of these kinds for the same tiles; d_optics: the device optics
  * the bank was built from (8-byte aligned; pixel_um sets the frequency grid);
  * d_spec: wo_spectrum of the data in the matching mode.  d_value, d_grad: n_tiles doubles each
@@ -257,9 +291,9 @@ wo_status wo_spectrum(const float *d_data, const float *h_background, int mode, 
  * to the bit).  No host synchronisation: the call can be captured in a CUDA
  * graph together with wo_build_tf_device and wo_adam_defocus. */
 wo_status wo_defocus_objective(const void *d_tf, unsigned kinds, const wo_optics *d_optics,
-                               const void *d_spec, float eta, float nu_max, double *d_value,
-                               double *d_grad, int n_tiles, int Z, int Y, int X, void *d_ws,
-                               size_t ws_bytes, wo_stream stream);
+                               const void *d_spec, int loss, float eta, float nu_max,
+                               double *d_value, double *d_grad, int n_tiles, int Z, int Y, int X,
+                               void *d_ws, size_t ws_bytes, wo_stream stream);
 
 /* wo_adam_defocus: one Adam step (Kingma and Ba, 2015) on each tile's
  * defocus_um in the device optics array, from the gradient d_grad:

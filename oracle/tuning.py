@@ -20,6 +20,8 @@ the defocus: with one free unknown per 3D frequency the fit is exact wherever
 H != 0.)  ``objective`` evaluates the definition - reconstruct, predict,
 form the residual in real space.  ``gradient_fd`` is its central finite
 difference.  ``tf_defocus_derivative`` is dH/d(defocus) of the 3D phase TF.
+``midband_objective`` is the paper's own image-quality loss (minus the
+mid-band power of the reconstruction), for comparison.
 """
 from __future__ import annotations
 
@@ -51,6 +53,40 @@ def objective(o: dict, d: np.ndarray, eta: float, nu_max: float | None = None) -
     pred = np.real(np.fft.ifft2(Hj * np.fft.fft2(f_hat)[None], axes=(1, 2))) + b
     r = dd[0] - pred
     return float(np.sum(r * r) + eta * np.sum(f_hat * f_hat))
+
+
+def midband_mask(o: dict, Y: int, X: int) -> np.ndarray:
+    """Transverse frequencies with c/8 <= |nu| <= c/4, c = (NA_det + NA_ill)/lambda
+    (the transverse cutoff of the label-free transfer functions)."""
+    ky, kx = optics.transverse_grid(Y, X, o["pixel_um"])
+    r = np.sqrt(ky * ky + kx * kx)
+    c = (o["na_det"] + o["na_ill"]) / o["lambda_um"]
+    return (r >= c / 8) & (r <= c / 4)
+
+
+def midband_objective(o: dict, d: np.ndarray, eta: float) -> float:
+    """The paper's image-quality loss (Results, auto-tuning; Methods, optical
+    pooled screen data): minus the power of the 2D phase reconstruction in the
+    mid band of transverse frequencies, read as sum |F|^2 / N_perp over
+    c/8 <= |nu| <= c/4.  Evaluated by its definition: reconstruct (absolute
+    eta, channel-mean background), transform, sum the band."""
+    shape = d.shape
+    Hj = optics.plane_tfs(o, shape, ("phase",))["phase"]
+    modes = [dict(channels=[0], props=[0], H=[[Hj]])]
+    f_hat = model.reconstruct_2d(modes, np.asarray(d, dtype=np.float64)[None], eta, background=None,
+                                 relative=False)[0]
+    F = np.fft.fft2(f_hat)
+    m = midband_mask(o, shape[1], shape[2])
+    return float(-np.sum(np.abs(F[m]) ** 2) / (shape[1] * shape[2]))
+
+
+def midband_objective_at(o: dict, d: np.ndarray, eta: float, defocus: float) -> float:
+    return midband_objective(dict(o, defocus_um=float(defocus)), d, eta)
+
+
+def midband_gradient_fd(o: dict, d: np.ndarray, eta: float, h: float = 1e-4) -> float:
+    z = o["defocus_um"]
+    return (midband_objective_at(o, d, eta, z + h) - midband_objective_at(o, d, eta, z - h)) / (2 * h)
 
 
 def objective_at(o: dict, d: np.ndarray, eta: float, defocus: float, nu_max: float | None = None) -> float:

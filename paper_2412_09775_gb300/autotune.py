@@ -33,9 +33,11 @@ PHASE_DZ = B.WO_TF_PHASE_DZ
 class DefocusProblem:
     """``planes`` (default): per-plane TF banks and 2D data spectra, so no z
     transform runs per step; otherwise 3D banks and spectra (the same loss by
-    Parseval over z)."""
+    Parseval over z).  ``loss``: the data-fidelity loss (default) or the
+    paper's mid-band power loss (WO_LOSS_MIDBAND)."""
 
-    def __init__(self, data: torch.Tensor, optics_list, eta: float, background=None, planes: bool = True):
+    def __init__(self, data: torch.Tensor, optics_list, eta: float, background=None, planes: bool = True,
+                 loss: int = B.WO_LOSS_DATA):
         if data.dim() != 4 or data.dtype != torch.float32 or not data.is_cuda:
             raise ValueError("data: float32 CUDA tensor [n_tiles, Z, Y, X]")
         self.n, self.Z, self.Y, self.X = (int(s) for s in data.shape)
@@ -43,6 +45,7 @@ class DefocusProblem:
             raise ValueError("one optics entry per tile")
         dev = data.device
         self.eta = float(eta)
+        self.loss = int(loss)
         self.kinds = PHASE_DZ | (B.WO_TF_PLANES if planes else 0)
         self.mode = B.WO_MODE_2D if planes else B.WO_MODE_3D
         self.optics = B.optics_tensor(optics_list, dev)
@@ -74,8 +77,8 @@ class DefocusProblem:
         """Loss and defocus derivative of every tile at the current optics."""
         n, Z, Y, X = self.n, self.Z, self.Y, self.X
         B.wo_build_tf_device(self.optics, n, Z, Y, X, self.kinds, self.tf, self.ws)
-        B.wo_defocus_objective(self.tf, self.kinds, self.optics, self.spec, self.eta, nu_max, self.value, self.grad,
-                               n, Z, Y, X, self.ws)
+        B.wo_defocus_objective(self.tf, self.kinds, self.optics, self.spec, self.loss, self.eta, nu_max, self.value,
+                               self.grad, n, Z, Y, X, self.ws)
 
     def step(self, lr: float, nu_max: float = 0.0, beta1=0.9, beta2=0.999, eps=1e-8):
         self.evaluate(nu_max)

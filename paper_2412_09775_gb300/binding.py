@@ -20,6 +20,7 @@ WO_TF_PHASE_DZ = 8
 WO_TF_PLANES = 16
 WO_MODE_3D, WO_MODE_2D = 0, 1
 WO_ETA_RELATIVE, WO_ETA_ABSOLUTE = 0, 1
+WO_LOSS_DATA, WO_LOSS_MIDBAND = 0, 1
 KIND_BITS = {"phase": WO_TF_PHASE, "absorption": WO_TF_ABSORPTION, "fluor": WO_TF_FLUOR,
              "phase_dz": WO_TF_PHASE_DZ, "planes": WO_TF_PLANES}
 STATUS = {0: "WO_OK", 1: "WO_ERR_ARG", 2: "WO_ERR_SHAPE", 3: "WO_ERR_UNSUPPORTED_SIZE",
@@ -59,9 +60,11 @@ def _load():
         "wo_reconstruct": (i, [vp, u, vp, fp, fp, i, i, vp, i, i, i, i, vp, sz, vp]),
         "wo_reconstruct_static": (i, [vp, u, vp, fp, fp, i, i, vp, i, i, i, i, vp]),
         "wo_spectrum": (i, [vp, fp, i, vp, i, i, i, i, vp]),
-        "wo_defocus_objective": (i, [vp, u, vp, vp, f, f, vp, vp, i, i, i, i, vp, sz, vp]),
+        "wo_defocus_objective": (i, [vp, u, vp, vp, i, f, f, vp, vp, i, i, i, i, vp, sz, vp]),
         "wo_adam_defocus": (i, [vp, vp, vp, i, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                 ctypes.c_double, vp]),
+        "wo_fused_workspace_bytes": (sz, [i, i, i, i, i]),
+        "wo_reconstruct_fused": (i, [vp, i, vp, fp, f, i, i, vp, i, i, i, i, vp, sz, vp]),
         "wo_tile_gather": (i, [vp, i, i, i, i, i, vp, vp]),
         "wo_tile_blend": (i, [vp, i, i, i, i, i, vp, vp]),
         "wo_status_string": (ctypes.c_char_p, [i]),
@@ -81,7 +84,8 @@ _lib = _load()
 EXPORTED = ("wo_size_supported", "wo_tf_bytes", "wo_workspace_bytes", "wo_build_tf", "wo_build_tf_device",
             "wo_forward",
             "wo_forward_adjoint", "wo_reconstruct", "wo_reconstruct_static", "wo_spectrum",
-            "wo_defocus_objective", "wo_adam_defocus", "wo_tile_gather", "wo_tile_blend",
+            "wo_defocus_objective", "wo_adam_defocus", "wo_fused_workspace_bytes", "wo_reconstruct_fused",
+            "wo_tile_gather", "wo_tile_blend",
             "wo_status_string", "wo_profile_enable", "wo_profile_read", "wo_launch_count")
 
 
@@ -214,10 +218,11 @@ def wo_spectrum(data, background, mode, spec, n_tiles, Z, Y, X, stream=None):
                             _stream(stream)), "wo_spectrum")
 
 
-def wo_defocus_objective(tf, kinds, d_optics, spec, eta, nu_max, value, grad, n_tiles, Z, Y, X, ws, stream=None):
+def wo_defocus_objective(tf, kinds, d_optics, spec, loss, eta, nu_max, value, grad, n_tiles, Z, Y, X, ws,
+                         stream=None):
     """Per-tile loss and defocus derivative (float64 tensors [n] or None) from a phase_dz bank."""
-    _check(_lib.wo_defocus_objective(_ptr(tf), kinds_mask(kinds), _ptr(d_optics), _ptr(spec), float(eta),
-                                     float(nu_max), _ptr(value), _ptr(grad), n_tiles, Z, Y, X, _ptr(ws),
+    _check(_lib.wo_defocus_objective(_ptr(tf), kinds_mask(kinds), _ptr(d_optics), _ptr(spec), int(loss),
+                                     float(eta), float(nu_max), _ptr(value), _ptr(grad), n_tiles, Z, Y, X, _ptr(ws),
                                      _nbytes(ws), _stream(stream)), "wo_defocus_objective")
 
 
@@ -225,6 +230,19 @@ def wo_adam_defocus(d_optics, grad, state, n_tiles, lr, beta1=0.9, beta2=0.999, 
     """One on-device Adam step on each tile's defocus (state: float64 [n, 3], zeroed before the first)."""
     _check(_lib.wo_adam_defocus(_ptr(d_optics), _ptr(grad), _ptr(state), n_tiles, float(lr), float(beta1),
                                 float(beta2), float(eps), _stream(stream)), "wo_adam_defocus")
+
+
+def wo_fused_workspace_bytes(n_channels, n_tiles, Z, Y, X) -> int:
+    return int(_lib.wo_fused_workspace_bytes(n_channels, n_tiles, Z, Y, X))
+
+
+def wo_reconstruct_fused(tf, n_channels, data, background, eta, eta_flag, mode, f, n_tiles, Z, Y, X, ws,
+                         stream=None):
+    """One property from n_channels data channels, each through its own phase TF (bank of n_tiles*C entries)."""
+    bg = _floats(background)
+    _check(_lib.wo_reconstruct_fused(_ptr(tf), int(n_channels), _ptr(data), bg[0] if bg else None, float(eta),
+                                     int(eta_flag), int(mode), _ptr(f), n_tiles, Z, Y, X, _ptr(ws), _nbytes(ws),
+                                     _stream(stream)), "wo_reconstruct_fused")
 
 
 def wo_tile_gather(field, Z, tiles_y, tiles_x, core, halo, tiles, stream=None):

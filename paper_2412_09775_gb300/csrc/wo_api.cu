@@ -444,9 +444,10 @@ wo_status wo_spectrum(const float* d_data, const float* h_background, int mode, 
 }
 
 wo_status wo_defocus_objective(const void* d_tf, unsigned kinds, const wo_optics* d_optics, const void* d_spec,
-                               float eta, float nu_max, double* d_value, double* d_grad, int n_tiles, int Z, int Y,
-                               int X, void* d_ws, size_t ws_bytes, wo_stream stream) {
+                               int loss, float eta, float nu_max, double* d_value, double* d_grad, int n_tiles,
+                               int Z, int Y, int X, void* d_ws, size_t ws_bytes, wo_stream stream) {
   if (kinds != WO_TF_PHASE_DZ && kinds != (WO_TF_PHASE_DZ | WO_TF_PLANES)) return WO_ERR_ARG;
+  if (loss != WO_LOSS_DATA && loss != WO_LOSS_MIDBAND) return WO_ERR_ARG;
   wo_status st = check_shape(n_tiles, Z, Y, X, kinds);
   if (st != WO_OK) return st;
   if (!aligned16(d_tf) || !aligned16(d_spec) || !aligned16(d_ws)) return WO_ERR_ARG;
@@ -456,8 +457,8 @@ wo_status wo_defocus_objective(const void* d_tf, unsigned kinds, const wo_optics
   if (!(eta >= 0.f) || !isfinite(eta) || !(nu_max == nu_max)) return WO_ERR_ARG;
   if (ws_bytes < tune_partials_bytes(n_tiles, Y, X)) return WO_ERR_WORKSPACE;
   return cuda_status(tune_reduce((const float2*)d_tf, (const float2*)d_spec, d_optics, n_tiles, Z, Y, X, eta,
-                                 isfinite(nu_max) ? nu_max : 0.f, (kinds & WO_TF_PLANES) ? 1 : Z, (double*)d_ws,
-                                 d_value, d_grad, (cudaStream_t)stream));
+                                 isfinite(nu_max) ? nu_max : 0.f, (kinds & WO_TF_PLANES) ? 1 : Z, loss,
+                                 (double*)d_ws, d_value, d_grad, (cudaStream_t)stream));
 }
 
 wo_status wo_adam_defocus(wo_optics* d_optics, const double* d_grad, double* d_state, int n_tiles, double lr,
@@ -469,6 +470,75 @@ wo_status wo_adam_defocus(wo_optics* d_optics, const double* d_grad, double* d_s
       !(eps > 0.0) || !isfinite(eps))
     return WO_ERR_ARG;
   return cuda_status(adam_defocus(d_optics, d_grad, d_state, n_tiles, lr, beta1, beta2, eps, (cudaStream_t)stream));
+}
+
+wo_status wo_reconstruct_fused(const void* d_tf, int n_channels, const float* d_data, const float* h_background,
+                               float eta, int eta_flag, int mode, float* d_f, int n_tiles, int Z, int Y, int X,
+                               void* d_ws, size_t ws_bytes, wo_stream stream) {
+  if (n_channels < 1 || n_channels > kMaxFuseChannels) return WO_ERR_ARG;
+  if (n_tiles < 1 || (long long)n_tiles * n_channels > 65535) return WO_ERR_ARG;
+  wo_status st = check_shape(n_tiles * n_channels, Z, Y, X, WO_TF_PHASE);
+  if (st != WO_OK) return st;
+  if (!aligned16(d_tf) || !aligned16(d_data) || !aligned16(d_f) || !aligned16(d_ws)) return WO_ERR_ARG;
+  if (eta_flag != WO_ETA_RELATIVE && eta_flag != WO_ETA_ABSOLUTE) return WO_ERR_ARG;
+  if (mode != WO_MODE_3D && mode != WO_MODE_2D) return WO_ERR_ARG;
+  if (!(eta >= 0.f) || !isfinite(eta)) return WO_ERR_ARG;
+  if (h_background) {
+    for (int c = 0; c < n_channels; ++c)
+      if (!isfinite(h_background[c])) return WO_ERR_ARG;
+  }
+  const int C = n_channels;
+  const int Xh = X / 2 + 1, H = X / 2;
+  const size_t half = (size_t)Z * Y * Xh * sizeof(float2);
+  const size_t specA = align256((size_t)n_tiles * C * half);
+  const size_t specB = align256((size_t)n_tiles * half);
+  const size_t statsb = align256((size_t)n_tiles * 2 * sizeof(float));
+  if (ws_bytes < specA + specB + statsb) return WO_ERR_WORKSPACE;
+  cudaStream_t cs = (cudaStream_t)stream;
+  char* ws = (char*)d_ws;
+  float2* A = (float2*)ws;
+  float2* Bv = (float2*)(ws + specA);
+  float* stats = (float*)(ws + specA + specB);
+  RowBg bg{};
+  bg.rows_per_block = (long long)Z * Y;
+  bg.nchan = C;
+  bg.mode = h_background ? 0 : 2;  // a given background is removed from the DC bin in the z pass
+  FuseOp op{};
+  op.C = C;
+  op.mode = mode;
+  op.zero_dc = h_background ? 0 : 1;
+  op.eta_relative = eta_flag == WO_ETA_RELATIVE;
+  op.eta = eta;
+  op.stats = stats;
+  const double nvox = (double)Z * Y * X;
+  if (h_background)
+    for (int c = 0; c < C; ++c) op.bg_dc[c] = (float)(nvox * (double)h_background[c]);
+  const long long plane = (long long)Y * Xh;
+  WO_TRY(rows_r2c(H, d_data, A, (long long)n_tiles * C * Z * Y, bg, cs));
+  WO_TRY(cols_c2c(Y, false, A, Xh, plane, Xh, (long long)n_tiles * C * Z, cs, "y_fwd"));
+  if (op.eta_relative) WO_TRY(fuse_stats((const float2*)d_tf, n_tiles, C, Z, Y, Xh, stats, cs));
+  WO_TRY(z_fuse(Z, A, Bv, (const float2*)d_tf, op, n_tiles, Y, Xh, cs));
+  RowBg none{};
+  none.nchan = 1;
+  if (mode == WO_MODE_3D) {
+    WO_TRY(cols_c2c(Y, true, Bv, Xh, plane, Xh, (long long)n_tiles * Z, cs, "y_inv"));
+    none.rows_per_block = (long long)Z * Y;
+    WO_TRY(rows_c2r(H, Bv, d_f, (long long)n_tiles * Z * Y, (float)(2.0 / nvox), none, cs));
+  } else {
+    WO_TRY(cols_c2c(Y, true, Bv, Xh, plane, Xh, (long long)n_tiles, cs, "y_inv"));
+    none.rows_per_block = Y;
+    WO_TRY(rows_c2r(H, Bv, d_f, (long long)n_tiles * Y, 2.0f / ((float)X * (float)Y), none, cs));
+  }
+  return WO_OK;
+}
+
+size_t wo_fused_workspace_bytes(int n_channels, int n_tiles, int Z, int Y, int X) {
+  if (n_channels < 1 || n_channels > kMaxFuseChannels || n_tiles < 1 || (long long)n_tiles * n_channels > 65535)
+    return 0;
+  if (check_shape(n_tiles * n_channels, Z, Y, X, WO_TF_PHASE) != WO_OK) return 0;
+  const size_t half = (size_t)Z * Y * (X / 2 + 1) * sizeof(float2);
+  return align256((size_t)n_tiles * n_channels * half) + align256((size_t)n_tiles * half) +
+         align256((size_t)n_tiles * 2 * sizeof(float));
 }
 
 static wo_status check_tiles(int Z, int tiles_y, int tiles_x, int core, int halo, const void* a,

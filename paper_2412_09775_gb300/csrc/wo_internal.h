@@ -60,6 +60,22 @@ cudaError_t z_fused(int Z, const float2* in, float2* out, const float2* tf, ZOp 
 cudaError_t z_solve2d(int Z, const float2* in, float2* out, const float2* tf, ZOp op, int n_tiles,
                       int Y, int Xh, cudaStream_t s);
 
+// Multi-channel fusion (wo_fuse.cu): one property from C channels, each with
+// its own TF; input spectra [tile][C][Z][Y][Xh], TF bank [tile*C][Z][Y][Xh].
+constexpr int kMaxFuseChannels = 16;
+struct FuseOp {
+  int C;
+  int mode;          // WO_MODE_3D: out [tile][Z][Y][Xh]; WO_MODE_2D: out [tile][Y][Xh]
+  int zero_dc;       // background = channel means: zero the DC bin
+  int eta_relative;  // eta times the per-tile scale in stats
+  float eta;
+  float bg_dc[kMaxFuseChannels];  // N b_c, subtracted from the DC bin when !zero_dc
+  const float* stats;             // [tile][2]: max sum_c |H_c|^2 (3D), max sum_k sum_c |H_c|^2 (2D)
+};
+cudaError_t fuse_stats(const float2* tf, int n_tiles, int C, int Z, int Y, int Xh, float* stats, cudaStream_t s);
+cudaError_t z_fuse(int Z, const float2* in, float2* out, const float2* tf, const FuseOp& op, int n_tiles, int Y,
+                   int Xh, cudaStream_t s);
+
 // Transfer-function build.
 struct TfArgs {
   const wo_optics* optics;  // device copy, [n_tiles]
@@ -91,8 +107,8 @@ cudaError_t tf_zpass(const TfArgs& a, cudaStream_t s);
 // zf: Z for 3D spectra (Parseval over z puts a factor Z on the eta term and
 // on the normalisation), 1 for per-plane 2D spectra.
 cudaError_t tune_reduce(const float2* tf2, const float2* spec, const wo_optics* optics, int n_tiles, int Z,
-                        int Y, int X, float eta, float nu_max, int zf, double* partials, double* value, double* grad,
-                        cudaStream_t s);
+                        int Y, int X, float eta, float nu_max, int zf, int loss, double* partials, double* value,
+                        double* grad, cudaStream_t s);
 size_t tune_partials_bytes(int n_tiles, int Y, int X);
 // Zero element 0 of each of n_tiles volumes of vol elements (the DC bin).
 cudaError_t zero_dc(float2* spec, int n_tiles, long long vol, cudaStream_t s);

@@ -33,7 +33,9 @@ namespace wo {
 // predicates are exact float64 products and sums in the reference's order.
 // eta = sqrt(k_m^2 - |nu|^2) takes a float seed and one float64 Newton
 // correction (relative error ~1e-14, far below the float phase resolution).
-constexpr int kRecRows = 8;
+// Rows per block: between 8 and 32, as many as keep about two blocks per SM
+// busy (each block computes the x frequency axis once, with IEEE divisions).
+constexpr int kRecRowsMax = 32;
 
 // Device-side copy of the host validation (wo_api.cu check_optics) for optics
 // that live in device memory: 0 if valid, else the wo_status code.
@@ -54,9 +56,9 @@ __device__ int optics_status(const wo_optics& o) {
 
 __global__ void __launch_bounds__(256)
     k_pupil_record(const wo_optics* __restrict__ optics, float4* __restrict__ rec, int* __restrict__ counts,
-                   float* __restrict__ stats, int Y, int X) {
+                   float* __restrict__ stats, int Y, int X, int kRecRows) {
   extern __shared__ double nu_x[];  // [X]
-  __shared__ double nu_y[kRecRows];
+  __shared__ double nu_y[kRecRowsMax];
   __shared__ int part[2][8];
   const int t = blockIdx.y;
   const int y0 = blockIdx.x * kRecRows;
@@ -83,24 +85,50 @@ __global__ void __launch_bounds__(256)
   const double cy = __ddiv_rn(o.tilt_y, lam), cx = __ddiv_rn(o.tilt_x, lam);
   const double rs = __ddiv_rn(o.na_ill, lam), rs2 = __dmul_rn(rs, rs);
   const double km = __ddiv_rn(o.n_medium, lam), km2 = __dmul_rn(km, km);
+  // float images of the constants for the mask pre-test: a predicate is
+  // settled in float when the float value is clear of the threshold by a
+  // margin far above the float error; otherwise the float64 expression decides
+  const float rp2f = (float)rp2, rs2f = (float)rs2, cxf = (float)cx, cyf = (float)cy;
+  const float mp = 1e-5f * rp2f;
   int n_sp = 0, n_p = 0, kx_band = -1;
   const int rows = min(kRecRows, Y - y0);
   for (int e = threadIdx.x; e < rows * X; e += 256) {
     const int yy = e / X, x = e - (e / X) * X;
     const double vy = nu_y[yy], vx = nu_x[x];
-    const double r2 = __dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy));
-    const bool P = r2 <= rp2;
-    const double dy = __dsub_rn(vy, cy), dx = __dsub_rn(vx, cx);
-    const bool S = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) <= rs2;
-    const double e2 = __dsub_rn(km2, r2);
+    const float vyf = (float)vy, vxf = (float)vx;
+    const float r2f = vxf * vxf + vyf * vyf;
+    bool P;
+    if (r2f < rp2f - mp) P = true;
+    else if (r2f > rp2f + mp) P = false;
+    else P = __dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)) <= rp2;
+    bool S = false;
+    if (P) {
+      const float dxf = vxf - cxf, dyf = vyf - cyf;
+      const float s2f = dxf * dxf + dyf * dyf;
+      // the float error of s2f scales with (|nu| + |c|)^2, not with rs^2
+      const float ax = fabsf(vxf) + fabsf(cxf), ay = fabsf(vyf) + fabsf(cyf);
+      const float ms = 1e-5f * rs2f + 4e-6f * (ax * ax + ay * ay) + 1e-9f;
+      if (s2f < rs2f - ms) S = true;
+      else if (s2f > rs2f + ms) S = false;
+      else {
+        const double dy = __dsub_rn(vy, cy), dx = __dsub_rn(vx, cx);
+        S = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) <= rs2;
+      }
+    }
+    // eta (as a float pair) is used only inside the detection pupil, where
+    // every arm lives; elsewhere the record holds zeros
     float eh = 0.f, el = 0.f, binv = 0.f;
-    if (e2 > 0.0) {
-      const float s0 = sqrtf((float)e2);
-      const double rem = fma(-(double)s0, (double)s0, e2);
-      const double eta = (double)s0 + (double)((float)rem * (0.5f / s0));
-      eh = __double2float_rn(eta);
-      el = __double2float_rn(__dsub_rn(eta, (double)eh));
-      binv = P ? 1.0f / eh : 0.f;
+    if (P) {
+      const double r2 = __dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy));
+      const double e2 = __dsub_rn(km2, r2);
+      if (e2 > 0.0) {
+        const float s0 = sqrtf((float)e2);
+        const double rem = fma(-(double)s0, (double)s0, e2);
+        const double eta = (double)s0 + (double)((float)rem * (0.5f / s0));
+        eh = __double2float_rn(eta);
+        el = __double2float_rn(__dsub_rn(eta, (double)eh));
+        binv = 1.0f / eh;
+      }
     }
     rec[((long long)t * Y + y0 + yy) * X + x] = make_float4(eh, el, binv, (S && P) ? 1.f : 0.f);
     n_sp += (S && P) ? 1 : 0;
@@ -136,14 +164,6 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// fractional part of (eh + el) * (zh + zl), accurate to a few 1e-8
-__device__ __forceinline__ float phase_frac(float eh, float el, float zh, float zl) {
-  const float p = eh * zh;
-  float err = fmaf(eh, zh, -p);
-  err = fmaf(eh, zl, err);
-  err = fmaf(el, zh, err);
-  return (p - rintf(p)) + err;
-}
 
 template <int N>  // N = Y
 __global__ void __launch_bounds__(ColGeom<N>::NT, (1024 / ColGeom<N>::NT) > 1 ? (1024 / ColGeom<N>::NT) : 1) k_arms(TfArgs a) {
@@ -395,10 +415,12 @@ __global__ void __launch_bounds__(ZGeom<N, NK>::NT, ZGeom<N, NK>::MINB) k_tf_zpa
 }
 
 cudaError_t tf_pupil_record(const TfArgs& a, cudaStream_t s) {
+  const long long want = ((long long)a.Y * a.n_tiles + 303) / 304;
+  const int kRecRows = (int)(want < 8 ? 8 : (want > kRecRowsMax ? kRecRowsMax : want));
   dim3 grid((unsigned)((a.Y + kRecRows - 1) / kRecRows), (unsigned)a.n_tiles);
   const size_t smem = (size_t)a.X * sizeof(double);
   WO_LAUNCH("tf_pupil_record", s,
-            (k_pupil_record<<<grid, 256, smem, s>>>(a.optics, a.rec, a.counts, a.stats, a.Y, a.X)));
+            (k_pupil_record<<<grid, 256, smem, s>>>(a.optics, a.rec, a.counts, a.stats, a.Y, a.X, kRecRows)));
   return cudaGetLastError();
 }
 

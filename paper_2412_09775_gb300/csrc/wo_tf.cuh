@@ -21,4 +21,13 @@ __device__ __forceinline__ float fl_scale(const TfArgs& a, int t) {
   return (float)(1.0 / ((double)a.Y * (double)a.X * (double)a.Z * (double)n_p));
 }
 
+// fractional part of (eh + el) * (zh + zl), accurate to a few 1e-8
+__device__ __forceinline__ float phase_frac(float eh, float el, float zh, float zl) {
+  const float p = eh * zh;
+  float err = fmaf(eh, zh, -p);
+  err = fmaf(eh, zl, err);
+  err = fmaf(el, zh, err);
+  return (p - rintf(p)) + err;
+}
+
 }  // namespace wo

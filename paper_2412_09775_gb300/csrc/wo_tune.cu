@@ -15,6 +15,11 @@
 // and the hand-written adjoint needs no derivative of the solve itself.  The
 // per-tile loss is sum_nu w(nu) q / (N_perp zf), w = 2 for the half-spectrum
 // bins that stand for a conjugate pair, 1 for x = 0 and x = X/2.
+//
+// The mid-band loss (the paper's image-quality loss) is -sum_band w |F|^2 /
+// N_perp over c/8 <= |nu| <= c/4; F does not minimise it, so its derivative
+// goes through the solve: with c = sum conj(H) D, h = sum |H|^2,
+// den = h + zf eta, dF = (sum conj(dH) D - F 2 Re sum conj(H) dH) / den.
 #include "wo_fft.cuh"
 #include "wo_internal.h"
 
@@ -49,7 +54,7 @@ __global__ void __launch_bounds__(kTuneThreads) k_tune_cols(const float2* __rest
                                                             const float2* __restrict__ spec,
                                                             const wo_optics* __restrict__ optics, int Z, int Y,
                                                             int Xh, int X, float eta, float nu_max, int zf,
-                                                            double* __restrict__ partials) {
+                                                            int loss, double* __restrict__ partials) {
   __shared__ double red[2 * kTuneThreads];
   const int t = blockIdx.y;
   const long long plane = (long long)Y * Xh;
@@ -60,18 +65,48 @@ __global__ void __launch_bounds__(kTuneThreads) k_tune_cols(const float2* __rest
   if (on) {
     const int y = (int)(c / Xh);
     x = (int)(c - (long long)y * Xh);
-    if (nu_max > 0.f) {
-      const double p = optics[t].pixel_um;
-      const double fy = (double)freq_index(y, Y) / ((double)Y * p), fx = (double)x / ((double)X * p);
+    const wo_optics& o = optics[t];
+    const double p = o.pixel_um;
+    const double fy = (double)freq_index(y, Y) / ((double)Y * p), fx = (double)x / ((double)X * p);
+    if (loss == WO_LOSS_MIDBAND) {  // c/8 <= |nu| <= c/4, c = (NA_det + NA_ill)/lambda
+      const double r = sqrt(fx * fx + fy * fy), cut = (o.na_det + o.na_ill) / o.lambda_um;
+      on = r >= cut / 8.0 && r <= cut / 4.0;
+    } else if (nu_max > 0.f) {
       on = fx * fx + fy * fy <= (double)nu_max * (double)nu_max;
     }
+  }
+  if (on && loss == WO_LOSS_MIDBAND) {
+    // -|F|^2 and its derivative through the solve: dF = (dc - F dh) / den
+    const float2* D = spec + (long long)t * Z * plane + c;
+    const float2* H = tf2 + (long long)t * 2 * Z * plane + c;
+    const float2* dH = H + (long long)Z * plane;
+    float cr = 0.f, ci = 0.f, hh = 0.f, dcr = 0.f, dci = 0.f, dhr = 0.f;
+#pragma unroll 8
+    for (int k = 0; k < Z; ++k) {
+      const float2 d = __ldg(D + k * plane), h = __ldg(H + k * plane), dh = __ldg(dH + k * plane);
+      const float2 r = cmulc(h, d), q = cmulc(dh, d);
+      cr += r.x;
+      ci += r.y;
+      dcr += q.x;
+      dci += q.y;
+      hh += cabs2(h);
+      dhr += h.x * dh.x + h.y * dh.y;
+    }
+    const float den = hh + (float)zf * eta;
+    const float inv = den > 0.f ? 1.0f / den : 0.f;
+    const float2 F = make_float2(cr * inv, ci * inv);
+    const float2 dF = make_float2((dcr - 2.f * dhr * F.x) * inv, (dci - 2.f * dhr * F.y) * inv);
+    const double w = (x == 0 || 2 * x == X) ? 1.0 : 2.0;
+    val = -w * (double)cabs2(F);
+    grad = -w * 2.0 * ((double)F.x * dF.x + (double)F.y * dF.y);
+    on = false;
   }
   if (on) {
     const float2* D = spec + (long long)t * Z * plane + c;
     const float2* H = tf2 + (long long)t * 2 * Z * plane + c;
     const float2* dH = H + (long long)Z * plane;
     float cr = 0.f, ci = 0.f, hh = 0.f;
-#pragma unroll 4
+#pragma unroll 8
     for (int k = 0; k < Z; ++k) {
       const float2 d = __ldg(D + k * plane), h = __ldg(H + k * plane);
       const float2 r = cmulc(h, d);
@@ -83,7 +118,7 @@ __global__ void __launch_bounds__(kTuneThreads) k_tune_cols(const float2* __rest
     const float inv = den > 0.f ? 1.0f / den : 0.f;
     const float2 F = make_float2(cr * inv, ci * inv);
     float rr = 0.f, gg = 0.f;
-#pragma unroll 4
+#pragma unroll 8
     for (int k = 0; k < Z; ++k) {
       const float2 d = __ldg(D + k * plane), h = __ldg(H + k * plane), dh = __ldg(dH + k * plane);
       const float2 R = csub(d, cmul(h, F));
@@ -123,17 +158,19 @@ __global__ void k_tune_final(const double* __restrict__ partials, int nblk, doub
 }
 
 cudaError_t tune_reduce(const float2* tf2, const float2* spec, const wo_optics* optics, int n_tiles, int Z,
-                        int Y, int X, float eta, float nu_max, int zf, double* partials, double* value, double* grad,
-                        cudaStream_t s) {
+                        int Y, int X, float eta, float nu_max, int zf, int loss, double* partials, double* value,
+                        double* grad, cudaStream_t s) {
   const int Xh = X / 2 + 1;
   const long long plane = (long long)Y * Xh;
   const unsigned nblk = (unsigned)((plane + kTuneThreads - 1) / kTuneThreads);
   dim3 grid(nblk, (unsigned)n_tiles);
   WO_LAUNCH("tune_cols", s,
-            (k_tune_cols<<<grid, kTuneThreads, 0, s>>>(tf2, spec, optics, Z, Y, Xh, X, eta, nu_max, zf, partials)));
+            (k_tune_cols<<<grid, kTuneThreads, 0, s>>>(tf2, spec, optics, Z, Y, Xh, X, eta, nu_max, zf, loss,
+                                                         partials)));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const double scale = 1.0 / ((double)X * (double)Y * (double)zf);
+  // F is the same in both forms; the residual sums carry the Parseval factor zf
+  const double scale = 1.0 / ((double)X * (double)Y * (loss == WO_LOSS_MIDBAND ? 1.0 : (double)zf));
   WO_LAUNCH("tune_final", s, (k_tune_final<<<(unsigned)n_tiles, 32, 0, s>>>(partials, (int)nblk, scale, value, grad)));
   return cudaGetLastError();
 }

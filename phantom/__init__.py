@@ -211,3 +211,16 @@ def thin_phantom(seed: int, shape2d, o: dict | None = None, n_spheres: int = 40,
         rho2 = dy * dy + dx * dx
         out += dn * 2.0 * np.sqrt(np.maximum(r * r - rho2, 0.0)) / o["z_step_um"]
     return out
+
+
+def aperture_optics(n_apertures: int = 9, ring_na: float = 0.6, na_ill: float = 0.15,
+                    base: dict | None = None) -> list[dict]:
+    """Illumination apertures for multi-aperture fusion: one on axis and
+    n_apertures - 1 evenly spaced on a ring of radius ring_na (NA units), each
+    of numerical aperture na_ill."""
+    base = WIDEFIELD_OPTICS if base is None else base
+    out = [dict(base, na_ill=na_ill, tilt_x=0.0, tilt_y=0.0)]
+    for i in range(n_apertures - 1):
+        a = 2.0 * np.pi * i / (n_apertures - 1)
+        out.append(dict(base, na_ill=na_ill, tilt_x=ring_na * np.cos(a), tilt_y=ring_na * np.sin(a)))
+    return out

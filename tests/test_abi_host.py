@@ -112,17 +112,18 @@ def test_tuning_validation(B):
     d = ctypes.c_double
     obj = lib.wo_defocus_objective
     K = 8  # WO_TF_PHASE_DZ
-    assert obj(fake, K, fake, fake, 1e-3, 0.0, None, None, 1, 16, 64, 64, fake, big, None) == 1  # no output
-    assert obj(fake, K, fake, fake, -1.0, 0.0, fake, fake, 1, 16, 64, 64, fake, big, None) == 1  # eta < 0
-    assert obj(fake, K, fake + 4, fake, 1e-3, 0.0, fake, fake, 1, 16, 64, 64, fake, big, None) == 1
-    assert obj(fake, K, fake, fake, 1e-3, 0.0, fake, fake + 4, 1, 16, 64, 64, fake, big, None) == 1
-    assert obj(fake, K, fake, fake, 1e-3, float("nan"), fake, fake, 1, 16, 64, 64, fake, big, None) == 1
-    assert obj(fake, K, fake, fake, 1e-3, 0.0, fake, fake, 1, 16, 64, 64, fake, 16, None) == 8
-    assert obj(fake, K | 16, fake, fake, 1e-3, 0.0, fake, fake, 1, 16, 64, 64, fake, 16, None) == 8
-    assert obj(fake, K, fake, fake, 1e-3, 0.0, fake, fake, 1, 16, 64, 1024, fake, big, None) == 3
-    assert obj(fake, K, fake, fake, 1e-3, 0.0, fake, fake, 1, 16, 64, 63, fake, big, None) == 2
-    assert obj(fake, 1, fake, fake, 1e-3, 0.0, fake, fake, 1, 16, 64, 64, fake, big, None) == 1  # not a dz bank
-    assert obj(fake, 16, fake, fake, 1e-3, 0.0, fake, fake, 1, 16, 64, 64, fake, big, None) == 1
+    assert obj(fake, K, fake, fake, 0, 1e-3, 0.0, None, None, 1, 16, 64, 64, fake, big, None) == 1  # no output
+    assert obj(fake, K, fake, fake, 0, -1.0, 0.0, fake, fake, 1, 16, 64, 64, fake, big, None) == 1  # eta < 0
+    assert obj(fake, K, fake + 4, fake, 0, 1e-3, 0.0, fake, fake, 1, 16, 64, 64, fake, big, None) == 1
+    assert obj(fake, K, fake, fake, 0, 1e-3, 0.0, fake, fake + 4, 1, 16, 64, 64, fake, big, None) == 1
+    assert obj(fake, K, fake, fake, 0, 1e-3, float("nan"), fake, fake, 1, 16, 64, 64, fake, big, None) == 1
+    assert obj(fake, K, fake, fake, 0, 1e-3, 0.0, fake, fake, 1, 16, 64, 64, fake, 16, None) == 8
+    assert obj(fake, K | 16, fake, fake, 0, 1e-3, 0.0, fake, fake, 1, 16, 64, 64, fake, 16, None) == 8
+    assert obj(fake, K, fake, fake, 0, 1e-3, 0.0, fake, fake, 1, 16, 64, 1024, fake, big, None) == 3
+    assert obj(fake, K, fake, fake, 0, 1e-3, 0.0, fake, fake, 1, 16, 64, 63, fake, big, None) == 2
+    assert obj(fake, 1, fake, fake, 0, 1e-3, 0.0, fake, fake, 1, 16, 64, 64, fake, big, None) == 1  # not a dz bank
+    assert obj(fake, 16, fake, fake, 0, 1e-3, 0.0, fake, fake, 1, 16, 64, 64, fake, big, None) == 1
+    assert obj(fake, K, fake, fake, 2, 1e-3, 0.0, fake, fake, 1, 16, 64, 64, fake, big, None) == 1  # bad loss
     adam = lib.wo_adam_defocus
     assert adam(fake, fake, fake, 0, d(0.02), d(0.9), d(0.999), d(1e-8), None) == 1
     assert adam(fake, fake, fake, 4, d(-0.02), d(0.9), d(0.999), d(1e-8), None) == 1

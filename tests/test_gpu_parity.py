@@ -418,3 +418,53 @@ def test_tile_pipeline_under_cuda_graph(env):
         pipeline()
     torch.cuda.synchronize()
     assert torch.equal(graph_out, out) and not torch.equal(graph_out, eager)
+
+
+# ------------------------------------------------ multi-aperture fusion
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("bg,flag", [(None, 0), ("given", 1)])
+def test_nine_aperture_fusion(env, mode, bg, flag):
+    """C = 9 illumination apertures fused into one phase volume (3D) or one
+    thin-object phase image (2D): the GPU matches the oracle's C x 1
+    multi-channel Tikhonov solve, for 2 tiles at once."""
+    B, torch, dev = env
+    C, n = 9, 2
+    Z, Y, X = (12, 48, 64)
+    apertures = ph.aperture_optics(C, ring_na=0.6, na_ill=0.15)
+    optics = []
+    for t in range(n):
+        optics += [dict(o, defocus_um=0.2 * t) for o in apertures]
+    tf, _ = B.alloc(n * C, Z, Y, X, ("phase",), dev)
+    ws_build = B.alloc(n * C, Z, Y, X, ("phase",), dev)[1]
+    B.wo_build_tf(optics, n * C, Z, Y, X, ("phase",), tf, ws_build)
+    rng_f = ph.sphere_phantom(5, (Z, Y, X), ph.optics(), n_spheres=10)
+    d = np.zeros((n, C, Z, Y, X))
+    want = []
+    for t in range(n):
+        if mode == 0:
+            H = [OO.transfer_functions(optics[t * C + c], (Z, Y, X), ("phase",))["phase"] for c in range(C)]
+            m = [dict(channels=list(range(C)), props=[0], H=[[h] for h in H])]
+            dt = OM.forward(m, rng_f[None], [1.0] * C)
+        else:
+            Hj = [OO.plane_tfs(optics[t * C + c], (Z, Y, X), ("phase",))["phase"] for c in range(C)]
+            f2 = ph.thin_phantom(7 + t, (Y, X), ph.optics(), n_spheres=8)
+            dt = np.stack([1.0 + np.real(np.fft.ifft2(h * np.fft.fft2(f2)[None], axes=(1, 2))) for h in Hj])
+            m = [dict(channels=list(range(C)), props=[0], H=[[h] for h in Hj])]
+        dt = dt + ph.gaussian_noise(30 + t, dt.shape, 1e-3)
+        d[t] = dt.astype(np.float32)
+        b = None if bg is None else [1.0] * C
+        eta = 1e-3 if flag == 0 else 1e-2
+        if mode == 0:
+            want.append(OM.reconstruct(m, d[t], eta, background=b, relative=(flag == 0))[0])
+        else:
+            want.append(OM.reconstruct_2d(m, d[t], eta, background=b, relative=(flag == 0))[0])
+    wsb = B.wo_fused_workspace_bytes(C, n, Z, Y, X)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    out_shape = (n, Z, Y, X) if mode == 0 else (n, Y, X)
+    f = torch.empty(out_shape, dtype=torch.float32, device=dev)
+    B.wo_reconstruct_fused(tf, C, torch.tensor(d, dtype=torch.float32, device=dev),
+                           None if bg is None else [1.0] * C, 1e-3 if flag == 0 else 1e-2, flag, mode, f,
+                           n, Z, Y, X, ws)
+    got = f.cpu().numpy()
+    for t in range(n):
+        assert rel_l2(got[t], want[t]) <= TOL, t

@@ -153,6 +153,27 @@ def test_loss_and_gradient_match_the_oracle_on_eight_tiles(env, band, planes):
         assert abs(grad[t] - gwant) <= 1e-3 * abs(gwant), (t, grad[t], gwant)
 
 
+@pytest.mark.parametrize("planes", [True, False])
+def test_midband_loss_and_gradient_match_the_oracle(env, planes):
+    """The paper's mid-band power loss and its derivative through the solve."""
+    B, A, torch, dev = env
+    ol = tiles(6, 31)
+    offs = np.array([0.2, -0.15, 0.12, -0.18, 0.1, -0.2])
+    start = [dict(o, defocus_um=o["defocus_um"] + s) for o, s in zip(ol, offs)]
+    eta = 1e-3
+    _, d = problem(env, ol, start, eta, seed=90)
+    data = torch.tensor(d, dtype=torch.float32, device=dev)
+    pb = A.DefocusProblem(data, start, eta, planes=planes, loss=B.WO_LOSS_MIDBAND)
+    pb.evaluate()
+    torch.cuda.synchronize()
+    val, grad = pb.value.cpu().numpy(), pb.grad.cpu().numpy()
+    for t in range(len(ol)):
+        want = OT.midband_objective(start[t], d[t], eta)
+        gwant = OT.midband_gradient_fd(start[t], d[t], eta, h=1e-4)
+        assert abs(val[t] - want) <= 1e-4 * abs(want), (t, val[t], want)
+        assert abs(grad[t] - gwant) <= 1e-3 * abs(gwant), (t, grad[t], gwant)
+
+
 def test_gradient_matches_central_difference_of_the_gpu_loss(env):
     B, A, torch, dev = env
     ol = tiles(8, 22)

@@ -510,3 +510,27 @@ def test_band_limited_objective_is_the_closed_form_over_the_band():
     want = np.sum(q[band]) / (Y * X)
     assert abs(tuning.objective(o, d, eta, nu_max) - want) <= 1e-12 * want
     assert abs(tuning.objective(o, d, eta, 1e3) - tuning.objective(o, d, eta)) <= 1e-12 * want
+
+
+def test_midband_objective_closed_form_and_band():
+    """Minus the mid-band power equals -sum_band |sum_j H_j* D_j|^2 /
+    (sum_j |H_j|^2 + eta)^2 / N_perp (the 2D solve written out), and the band
+    is the annulus c/8 <= |nu| <= c/4 with c = (NA_det + NA_ill)/lambda."""
+    from oracle import tuning
+    o = ph.optics(na_ill=0.7, defocus_um=0.25, tilt_y=0.05)
+    shape = (6, 40, 48)
+    Z, Y, X = shape
+    d = 1 + 0.02 * np.random.default_rng(8).normal(size=shape)
+    eta = 1e-2
+    Hj = O.plane_tfs(o, shape, ("phase",))["phase"]
+    Dj = np.fft.fft2(d - d.mean(), axes=(1, 2))
+    F = np.sum(np.conj(Hj) * Dj, 0) / (np.sum(np.abs(Hj) ** 2, 0) + eta)
+    fy = np.fft.fftfreq(Y, o["pixel_um"])[:, None]
+    fx = np.fft.fftfreq(X, o["pixel_um"])[None, :]
+    c = (o["na_det"] + o["na_ill"]) / o["lambda_um"]
+    r = np.sqrt(fy ** 2 + fx ** 2)
+    band = (r >= c / 8) & (r <= c / 4)
+    assert 20 < band.sum() < Y * X // 4
+    want = -np.sum(np.abs(F[band]) ** 2) / (Y * X)
+    assert abs(tuning.midband_objective(o, d, eta) - want) <= 1e-12 * abs(want)
+    assert np.array_equal(tuning.midband_mask(o, Y, X), band)
