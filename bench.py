@@ -109,6 +109,12 @@ def algorithmic_bytes(shape, kinds, o):
     }
 
 
+def engines(*lengths):
+    from paper_2412_09775_gb300 import binding as B
+    names = {1: "smem", 2: "hybrid"}
+    return {f"cols_{n}": names.get(B.wo_schedule_get(B.WO_PASS_COLS, n), "?") for n in sorted(set(lengths))}
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -306,6 +312,7 @@ def run_gpu(args, rank, world, local_rank):
     Z, Y, X = SHAPE
     o, f = make_inputs(SHAPE, seed=2 + rank)
     tf, ws = B.alloc(1, Z, Y, X, KINDS, dev)
+    B.wo_autotune(1, Z, Y, X, KINDS, ws)  # engine per column-transform length, timed on these shapes
     # synthetic data: forward model of the phantom (on the GPU) + seeded noise
     f_d = torch.from_numpy(f).to(dev)
     data = torch.empty((1, 2, Z, Y, X), dtype=torch.float32, device=dev)
@@ -425,7 +432,8 @@ def report(args, world, ms_max, e2e_ms, prof, launches, clk, tune=None):
         "data": "synthetic (seeded phantom: 2000 spheres + 200 shells, GPU forward model + 1e-3 noise)",
         "config": {"workload": WORKLOAD if SHAPE == (96, 512, 512) else f"profiling case {Z}x{Y}x{X}", "Z": Z, "Y": Y, "X": X, "kinds": list(KINDS), "eta_relative": ETA,
                    "background": "channel mean", "tiles": 1, "parallelism": f"replicas x{world}",
-                   "l2": "working set > L2 (no flush needed): data 201 MB, TF 303 MB, workspace 606 MB"},
+                   "l2": "working set > L2 (no flush needed): data 201 MB, TF 303 MB, workspace 606 MB",
+                   "schedule": engines(Y, Z)},
         "roofline": roofline,
         "kernels": per_kernel,
         "gpu_launches": int(launches),
@@ -496,6 +504,7 @@ def run_tiles(args, rank, world, local_rank):
     rec = torch.empty_like(tiles)
     out = torch.empty_like(field)
     tf, ws = B.alloc(n, Z, E, E, ("phase",), dev)
+    B.wo_autotune(n, Z, E, E, ("phase",), ws)
 
     def step():
         B.wo_tile_gather(field, Z, ty, tx, TILE_CORE, TILE_HALO, tiles)
@@ -553,7 +562,7 @@ def run_tiles(args, rank, world, local_rank):
         "data": "synthetic (sphere phantom forward-simulated per tile with its own optics + 1e-3 noise)",
         "config": {"workload": TILES_WORKLOAD, "field": [Z, ty * TILE_CORE, tx * TILE_CORE], "tiles": n,
                    "tile": [Z, E, E], "eta_relative": 1e-3, "parallelism": f"replicas x{world}",
-                   "l2": "working set > L2 (field 805 MB, tiles 1.8 GB, TF 1.8 GB)"},
+                   "l2": "working set > L2 (field 805 MB, tiles 1.8 GB, TF 1.8 GB)", "schedule": engines(E, Z)},
         "kernels": per_kernel, "gpu_launches": int(per_step_launches * args.steps),
         "clocks": nvml.summary(), "peak_hbm_gbs": peak,
     }
@@ -646,6 +655,7 @@ def autotune_leg(args, rank, world, local_rank, with_cpu=True):
     start = [dict(o, defocus_um=0.0) for o in truth]
     data = make_tune_data(truth, dev, seed=5 + rank)
     pb = A.DefocusProblem(data, start, TUNE_ETA)
+    B.wo_autotune(n, Z, Y, X, pb.kinds, pb.ws)  # the workspace is scratch between calls
     sched = A.default_schedule(truth[0])
     n_adam = sum(p.steps for p in sched)
     # per-kernel times of one eager Adam step on the full loss
@@ -722,6 +732,7 @@ def autotune_leg(args, rank, world, local_rank, with_cpu=True):
                 "ms_per_step": round(e2e_ms, 3), "h2d_bytes_per_step": int(data.numel() * 4),
                 "d2h_bytes_per_step": int(n * 8)},
         "l2": "working set > L2: arms 6.4 GB, TF pair 1.6 GB, spectra 0.8 GB",
+        "schedule": engines(Y, Z),
     }
     if with_cpu and rank == 0 and not args.no_cpu_baseline:
         d0 = data[0].double().cpu().numpy()
@@ -746,7 +757,7 @@ def run_autotune(args, rank, world, local_rank):
             "data": "synthetic (thin sphere-projection specimens, GPU forward model at each tile's optics + "
                     "1e-3 noise)",
             "config": {"workload": r["workload"], "tiles": args.tune_tiles, "tile": list(TUNE_SHAPE), "eta": TUNE_ETA,
-                       "parallelism": f"replicas x{world}", "l2": r["l2"]}}
+                       "parallelism": f"replicas x{world}", "l2": r["l2"], "schedule": r["schedule"]}}
     for k in ("defocus_error_um", "roofline", "kernels", "gpu_launches", "clocks", "e2e", "cpu_baseline",
               "ms_per_adam_step"):
         if k in r:

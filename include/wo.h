@@ -307,6 +307,31 @@ wo_status wo_adam_defocus(wo_optics *d_optics, const double *d_grad, double *d_s
                           int n_tiles, double lr, double beta1, double beta2, double eps,
                           wo_stream stream);
 
+/* Schedules and the autotuner (no counterpart in the paper).  A pass with
+ * more than one implementation runs the engine its schedule table names.
+ * WO_PASS_COLS: the complex transforms along a strided axis (every y pass,
+ * the z transforms of wo_spectrum), per length n: WO_ENGINE_SMEM (shared-
+ * memory Stockham stages, radix 8, B columns per block) or WO_ENGINE_HYBRID
+ * (coalesced tile copies, a register-resident four-step transform per column
+ * with one shared-memory transpose; lengths 32, 48, 64, 96, 128, 192, 256,
+ * 512).  WO_ENGINE_DEFAULT restores the built-in choice.  Results do not
+ * depend on the engine beyond float32 rounding.
+ * wo_schedule_set: WO_ERR_ARG on a bad pass, length or engine,
+ * WO_ERR_UNSUPPORTED_SIZE for an engine that lacks the length.
+ * wo_schedule_get: the engine in use for (pass, n), -1 on bad arguments.
+ * wo_autotune: times every engine of the column transforms that an entry
+ * point on these shapes launches (lengths Y and Z, batches as large as the
+ * workspace allows up to three volumes per tile), on the workspace (its
+ * contents are destroyed), and keeps the fastest in the table.  It waits for
+ * the stream (it measures with events), so it is not for graph capture; run
+ * it once before capturing.  The table is process-wide. */
+enum { WO_PASS_COLS = 0 };
+enum { WO_ENGINE_DEFAULT = 0, WO_ENGINE_SMEM = 1, WO_ENGINE_HYBRID = 2 };
+wo_status wo_schedule_set(int pass, int n, int engine);
+int wo_schedule_get(int pass, int n);
+wo_status wo_autotune(int n_tiles, int Z, int Y, int X, unsigned kinds, void *d_ws,
+                      size_t ws_bytes, wo_stream stream);
+
 /* Human-readable name of a status. */
 const char *wo_status_string(wo_status status);
 

@@ -21,6 +21,8 @@ WO_TF_PLANES = 16
 WO_MODE_3D, WO_MODE_2D = 0, 1
 WO_ETA_RELATIVE, WO_ETA_ABSOLUTE = 0, 1
 WO_LOSS_DATA, WO_LOSS_MIDBAND = 0, 1
+WO_PASS_COLS = 0
+WO_ENGINE_DEFAULT, WO_ENGINE_SMEM, WO_ENGINE_HYBRID = 0, 1, 2
 KIND_BITS = {"phase": WO_TF_PHASE, "absorption": WO_TF_ABSORPTION, "fluor": WO_TF_FLUOR,
              "phase_dz": WO_TF_PHASE_DZ, "planes": WO_TF_PLANES}
 STATUS = {0: "WO_OK", 1: "WO_ERR_ARG", 2: "WO_ERR_SHAPE", 3: "WO_ERR_UNSUPPORTED_SIZE",
@@ -65,6 +67,9 @@ def _load():
                                 ctypes.c_double, vp]),
         "wo_fused_workspace_bytes": (sz, [i, i, i, i, i]),
         "wo_reconstruct_fused": (i, [vp, i, vp, fp, f, i, i, vp, i, i, i, i, vp, sz, vp]),
+        "wo_schedule_set": (i, [i, i, i]),
+        "wo_schedule_get": (i, [i, i]),
+        "wo_autotune": (i, [i, i, i, i, u, vp, sz, vp]),
         "wo_tile_gather": (i, [vp, i, i, i, i, i, vp, vp]),
         "wo_tile_blend": (i, [vp, i, i, i, i, i, vp, vp]),
         "wo_status_string": (ctypes.c_char_p, [i]),
@@ -85,7 +90,7 @@ EXPORTED = ("wo_size_supported", "wo_tf_bytes", "wo_workspace_bytes", "wo_build_
             "wo_forward",
             "wo_forward_adjoint", "wo_reconstruct", "wo_reconstruct_static", "wo_spectrum",
             "wo_defocus_objective", "wo_adam_defocus", "wo_fused_workspace_bytes", "wo_reconstruct_fused",
-            "wo_tile_gather", "wo_tile_blend",
+            "wo_schedule_set", "wo_schedule_get", "wo_autotune", "wo_tile_gather", "wo_tile_blend",
             "wo_status_string", "wo_profile_enable", "wo_profile_read", "wo_launch_count")
 
 
@@ -243,6 +248,20 @@ def wo_reconstruct_fused(tf, n_channels, data, background, eta, eta_flag, mode, 
     _check(_lib.wo_reconstruct_fused(_ptr(tf), int(n_channels), _ptr(data), bg[0] if bg else None, float(eta),
                                      int(eta_flag), int(mode), _ptr(f), n_tiles, Z, Y, X, _ptr(ws), _nbytes(ws),
                                      _stream(stream)), "wo_reconstruct_fused")
+
+
+def wo_schedule_set(pass_, n, engine):
+    _check(_lib.wo_schedule_set(int(pass_), int(n), int(engine)), "wo_schedule_set")
+
+
+def wo_schedule_get(pass_, n) -> int:
+    return int(_lib.wo_schedule_get(int(pass_), int(n)))
+
+
+def wo_autotune(n_tiles, Z, Y, X, kinds, ws, stream=None):
+    """Time the engines of the column transforms for these shapes and keep the fastest (destroys ws)."""
+    _check(_lib.wo_autotune(n_tiles, Z, Y, X, kinds_mask(kinds), _ptr(ws), _nbytes(ws), _stream(stream)),
+           "wo_autotune")
 
 
 def wo_tile_gather(field, Z, tiles_y, tiles_x, core, halo, tiles, stream=None):

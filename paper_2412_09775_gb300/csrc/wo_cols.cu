@@ -92,6 +92,8 @@ cudaError_t cols_c2c(int N, bool inverse, float2* data, long long col_stride, lo
                      int ncols, long long nplanes, cudaStream_t s, const char* name, long long groups,
                      long long group_stride) {
   if (N == 1 || nplanes <= 0 || ncols <= 0 || groups <= 0) return cudaSuccess;  // identity
+  if (cols_engine(N) == WO_ENGINE_HYBRID)
+    return cols_c2c_hyb(N, inverse, data, col_stride, plane_stride, ncols, nplanes, s, name, groups, group_stride);
   switch (N) {
 #define WO_CASE(n) \
   case n:          \

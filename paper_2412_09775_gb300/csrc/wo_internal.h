@@ -95,6 +95,12 @@ struct TfArgs {
 cudaError_t tf_pupil_record(const TfArgs& a, cudaStream_t s);
 cudaError_t tf_arms(const TfArgs& a, cudaStream_t s);
 cudaError_t tf_psf_rows(const TfArgs& a, cudaStream_t s);
+// Hybrid column engine (wo_colhyb.cu) and the schedule table (wo_sched.cu).
+bool cols_hyb_supported(int N);
+cudaError_t cols_c2c_hyb(int N, bool inverse, float2* data, long long col_stride, long long plane_stride, int ncols,
+                         long long nplanes, cudaStream_t s, const char* name, long long groups,
+                         long long group_stride);
+int cols_engine(int n);  // WO_ENGINE_SMEM or WO_ENGINE_HYBRID
 // Register-resident variant of the PSF-row pass for short rows (wo_psf.cu).
 bool psf_rows_reg_supported(int X, int n_arms);
 cudaError_t tf_psf_rows_reg(const TfArgs& a, cudaStream_t s);

@@ -143,6 +143,24 @@ def test_tuning_validation(B):
     assert lib.wo_forward(fake, 24, fake, None, fake, 1, 16, 64, 64, fake, big, None) == 1
 
 
+def test_schedule_table(B):
+    lib = B._lib
+    assert lib.wo_schedule_set(1, 128, 1) == 1        # unknown pass
+    assert lib.wo_schedule_set(0, 0, 1) == 1          # bad length
+    assert lib.wo_schedule_set(0, 128, 7) == 1        # bad engine
+    assert lib.wo_schedule_set(0, 1024, 2) == 3       # no hybrid engine for 1024
+    assert lib.wo_schedule_get(0, 5000) == -1
+    for n in (128, 512):
+        assert lib.wo_schedule_set(0, n, 2) == 0 and lib.wo_schedule_get(0, n) == 2
+        assert lib.wo_schedule_set(0, n, 1) == 0 and lib.wo_schedule_get(0, n) == 1
+        assert lib.wo_schedule_set(0, n, 0) == 0 and lib.wo_schedule_get(0, n) in (1, 2)
+    assert lib.wo_schedule_get(0, 1024) == 1
+    fake = 1 << 20
+    assert lib.wo_autotune(1, 16, 64, 64, 1, fake, 16, None) == 8       # workspace too small
+    assert lib.wo_autotune(1, 16, 64, 63, 1, fake, 1 << 40, None) == 1  # bad shape
+    assert lib.wo_autotune(1, 16, 64, 64, 1, fake + 4, 1 << 40, None) == 1
+
+
 def test_tile_validation(B):
     lib = B._lib
     fake = 1 << 20

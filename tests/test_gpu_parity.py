@@ -468,3 +468,56 @@ def test_nine_aperture_fusion(env, mode, bg, flag):
     got = f.cpu().numpy()
     for t in range(n):
         assert rel_l2(got[t], want[t]) <= TOL, t
+
+
+# ------------------------------------------------ column engines and the autotuner
+@pytest.mark.parametrize("engine", [1, 2])
+@pytest.mark.parametrize("shape", [(8, 64, 48), (6, 128, 64), (4, 192, 32), (4, 256, 32), (2, 512, 16),
+                                   (6, 96, 48), (4, 48, 64), (4, 32, 32)])
+def test_column_engines_match_oracle(env, shape, engine):
+    """Forward + reconstruction with the y transforms pinned to each engine
+    (shared-memory Stockham, hybrid register-resident) match the oracle."""
+    B, torch, dev = env
+    Z, Y, X = shape
+    try:
+        B.wo_schedule_set(B.WO_PASS_COLS, Y, engine)
+        assert B.wo_schedule_get(B.WO_PASS_COLS, Y) == engine
+        o = ph.optics(na_ill=0.6, defocus_um=0.2)
+        kinds = ("phase", "absorption")
+        tf, ws = check_tf(env, [o], shape, kinds)
+        f = ph.uniform_volume(3, (2,) + shape, -0.01, 0.01)
+        tfs = OO.transfer_functions(o, shape, kinds)
+        modes, _, _ = OM.widefield_system(tfs, kinds)
+        want = OM.forward(modes, f, [1.0])
+        d = torch.empty((1, 1) + shape, dtype=torch.float32, device=dev)
+        B.wo_forward(tf, kinds, torch.tensor(f[None], dtype=torch.float32, device=dev), [1.0], d, 1, Z, Y, X, ws)
+        got = d.cpu().numpy()[0]
+        assert rel_l2(got[0] - 1.0, want[0] - 1.0) <= TOL
+    finally:
+        B.wo_schedule_set(B.WO_PASS_COLS, Y, 0)
+
+
+def test_autotune_keeps_results(env):
+    """The autotuner times the engines on the workspace and records one per
+    length; the reconstruction afterwards matches the oracle as before."""
+    B, torch, dev = env
+    Z, Y, X = 16, 128, 64
+    o = ph.optics(na_ill=0.7)
+    kinds = ("phase",)
+    tf, ws = B.alloc(2, Z, Y, X, kinds, dev)
+    try:
+        B.wo_autotune(2, Z, Y, X, kinds, ws)
+        assert B.wo_schedule_get(B.WO_PASS_COLS, Y) in (1, 2)
+        assert B.wo_schedule_get(B.WO_PASS_COLS, Z) in (1, 2)
+        B.wo_build_tf([o, o], 2, Z, Y, X, kinds, tf, ws)
+        d = 1.0 + 0.01 * ph.uniform_volume(9, (Z, Y, X))
+        out = torch.empty((2, Z, Y, X), dtype=torch.float32, device=dev)
+        dd = torch.tensor(np.stack([d, d])[:, None], dtype=torch.float32, device=dev)
+        B.wo_reconstruct(tf, kinds, dd, None, 1e-3, 0, 0, out, 2, Z, Y, X, ws)
+        modes, _, _ = OM.widefield_system(OO.transfer_functions(o, (Z, Y, X), kinds), kinds)
+        want = OM.reconstruct(modes, d[None].astype(np.float32).astype(np.float64), 1e-3)[0]
+        got = out.cpu().numpy()
+        assert rel_l2(got[0], want) <= TOL and rel_l2(got[1], want) <= TOL
+    finally:
+        B.wo_schedule_set(B.WO_PASS_COLS, Y, 0)
+        B.wo_schedule_set(B.WO_PASS_COLS, Z, 0)
