@@ -16,7 +16,8 @@ Green's function, e^{ikr}/(4 pi r) = (i/4pi) Int d^2nu e^{i2pi(nu.r + eta|z|)}/e
 * frequencies nu = k / (N p) in FFT order; k_m = n_medium / lambda;
   eta(nu) = sqrt(k_m^2 - |nu|^2) (axial frequency on the Ewald shell);
 * source pupil S = 1[|nu - t/lambda| <= NA_ill/lambda] (closed disk, t the tilt
-  in NA units); detection pupil P = 1[|nu| <= NA_det/lambda];
+  in NA units), or with a logistic edge one frequency bin wide for tuning the
+  illumination; detection pupil P = 1[|nu| <= NA_det/lambda];
 * the scattered arm carries the scalar Green's spectrum G = i/eta;
 * plane j of a stack sits at focal displacement z_j = k_j dz + defocus with
   k_j in FFT order, and every arm is propagated by e^{+i 2 pi eta z_j};
@@ -70,14 +71,44 @@ def _disk(nu_y, nu_x, cy, cx, radius):
     return (r2 <= radius * radius).astype(np.float64)
 
 
+def source_edge_width(o: dict, Y: int, X: int) -> float:
+    """Edge width of the smooth source pupil: one frequency bin of the coarser axis."""
+    return 1.0 / (min(Y, X) * o["pixel_um"])
+
+
 def source_pupil(o: dict, Y: int, X: int) -> np.ndarray:
     """Illumination model S (Methods, "Summary of transfer functions", item 1).
 
     Binary disk of radius NA_ill/lambda centred on the tilt (tilt_x, tilt_y)/lambda.
+    With o["smooth_source"] the edge is a logistic ramp instead,
+    S = 1 / (1 + exp(-(R - |nu - t/lambda|) / w)), w = ``source_edge_width``:
+    the model in which the tilt and NA_ill have derivatives (auto-tuning of
+    the illumination parameters).
     """
     lam = o["lambda_um"]
     nu_y, nu_x = transverse_grid(Y, X, o["pixel_um"])
-    return _disk(nu_y, nu_x, o["tilt_y"] / lam, o["tilt_x"] / lam, o["na_ill"] / lam)
+    if not o.get("smooth_source", False):
+        return _disk(nu_y, nu_x, o["tilt_y"] / lam, o["tilt_x"] / lam, o["na_ill"] / lam)
+    d = np.sqrt((nu_x - o["tilt_x"] / lam) ** 2 + (nu_y - o["tilt_y"] / lam) ** 2)
+    w = source_edge_width(o, Y, X)
+    return 1.0 / (1.0 + np.exp(-(o["na_ill"] / lam - d) / w))
+
+
+def source_pupil_derivatives(o: dict, Y: int, X: int) -> dict:
+    """dS/d(tilt_x), dS/d(tilt_y), dS/d(NA_ill) of the smooth source pupil
+    (the chain rule through the logistic edge; zero at the disk centre for
+    the tilts by symmetry)."""
+    lam = o["lambda_um"]
+    nu_y, nu_x = transverse_grid(Y, X, o["pixel_um"])
+    ux, uy = nu_x - o["tilt_x"] / lam, nu_y - o["tilt_y"] / lam
+    d = np.sqrt(ux * ux + uy * uy)
+    w = source_edge_width(o, Y, X)
+    S = 1.0 / (1.0 + np.exp(-(o["na_ill"] / lam - d) / w))
+    ds = S * (1.0 - S) / w  # dS/dx times dx/d(R - d)
+    safe = np.where(d > 0, d, 1.0)
+    return {"tilt_x": np.where(d > 0, ds * ux / (safe * lam), 0.0),
+            "tilt_y": np.where(d > 0, ds * uy / (safe * lam), 0.0),
+            "na_ill": ds / lam}
 
 
 def detection_pupil(o: dict, Y: int, X: int) -> np.ndarray:

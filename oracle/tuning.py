@@ -123,3 +123,47 @@ def plane_tf_defocus_derivative(o: dict, shape) -> np.ndarray:
 def tf_defocus_derivative(o: dict, shape) -> np.ndarray:
     """dH_phase/d(defocus) of the 3D phase TF: the z-DFT of the per-plane derivative."""
     return optics.stack_to_3d(plane_tf_defocus_derivative(o, shape))
+
+
+def plane_tf_source_derivatives(o: dict, shape) -> dict:
+    """d H_phase,j / d theta of the per-plane 2D phase TFs for theta = tilt_x,
+    tilt_y, NA_ill under the smooth source pupil (complex128, (Z, Y, X) each).
+
+    Only the direct arm A = S P e^{i2pi eta z_j} and the normalisation
+    D = sum S P^2 depend on the source, so with A_theta = (dS/dtheta) P e^{...}
+    and D_theta = sum (dS/dtheta) P^2:
+    dH1/dtheta = c [sum A_theta* B(.+q)] / D - H1 D_theta / D,
+    and Table 1's combination carries over.
+    """
+    assert o.get("smooth_source", False), "the derivatives exist for the smooth source pupil"
+    Z, Y, X = shape
+    A, B = optics.arms(o, shape)
+    S = optics.source_pupil(o, Y, X)
+    P = optics.detection_pupil(o, Y, X)
+    eta = optics.axial_frequency(o, Y, X)
+    z = optics.plane_displacements(Z, o["z_step_um"], o["defocus_um"])
+    prop = np.exp(2j * np.pi * eta[None] * z[:, None, None])
+    D = np.sum(S * P * P)
+    c = optics.labelfree_prefactor(o)
+    H1 = c * optics.correlate(A, B) / D
+    T = optics.TABLE1_LABELFREE
+    out = {}
+    for k, dS in optics.source_pupil_derivatives(o, Y, X).items():
+        At = (dS * P)[None] * prop
+        Dt = np.sum(dS * P * P)
+        dH1 = c * optics.correlate(At, B) / D - H1 * Dt / D
+        out[k] = T[0, 0] * dH1 + T[0, 1] * np.conj(optics.reflect(dH1))
+    return out
+
+
+PARAMS = ("defocus_um", "tilt_x", "tilt_y", "na_ill")
+
+
+def gradient_fd_params(o: dict, d: np.ndarray, eta: float, h: float = 1e-4, loss: str = "data") -> np.ndarray:
+    """dL/d(defocus, tilt_x, tilt_y, NA_ill) by central differences of the
+    objective (data-fidelity or mid-band)."""
+    f = objective if loss == "data" else midband_objective
+    g = np.zeros(len(PARAMS))
+    for i, k in enumerate(PARAMS):
+        g[i] = (f(dict(o, **{k: o[k] + h}), d, eta) - f(dict(o, **{k: o[k] - h}), d, eta)) / (2 * h)
+    return g

@@ -48,9 +48,14 @@ TILE_HALO = 32
 
 
 def optics(**overrides) -> dict:
-    """A copy of the widefield optics with some fields replaced."""
+    """A copy of the widefield optics with some fields replaced.  The flag
+    smooth_source=True selects the smooth-edged source pupil (a model flag,
+    not an optics field)."""
     o = dict(WIDEFIELD_OPTICS)
     for k, v in overrides.items():
+        if k == "smooth_source":
+            o[k] = bool(v)
+            continue
         if k not in OPTICS_KEYS:
             raise KeyError(k)
         o[k] = float(v)

@@ -175,15 +175,16 @@ def _field_route(o, shape, m, dn_plane, kappa_plane):
     ky, kx = O.fft_indices(Y), O.fft_indices(X)
     yy, xx = np.meshgrid(np.arange(Y), np.arange(X), indexing="ij")
     out = np.zeros(shape)
-    count = 0
+    count = 0.0
     for sy, sx in zip(*np.nonzero(S * P)):
-        count += 1
+        wgt = S[sy, sx] * P[sy, sx]  # 1 for the binary source, the edge weight for the smooth one
+        count += wgt
         Fs = np.roll(F, shift=(sy, sx), axis=(0, 1))  # F(nu - s)
         for i in range(Z):
             zi = z[(i - m) % Z]
             u0 = np.exp(2j * np.pi * (ky[sy] * yy / Y + kx[sx] * xx / X + eta[sy, sx] * zi))
             us = np.fft.ifft2(P * 1j * c * inv_eta * np.exp(2j * np.pi * eta * zi) * Fs)
-            out[i] += 2.0 * np.real(np.conj(u0) * us)
+            out[i] += wgt * 2.0 * np.real(np.conj(u0) * us)
     return out / count
 
 
@@ -534,3 +535,61 @@ def test_midband_objective_closed_form_and_band():
     want = -np.sum(np.abs(F[band]) ** 2) / (Y * X)
     assert abs(tuning.midband_objective(o, d, eta) - want) <= 1e-12 * abs(want)
     assert np.array_equal(tuning.midband_mask(o, Y, X), band)
+
+
+# ------------------------------------------------ smooth source pupil (illumination tuning)
+def test_smooth_source_edge_values():
+    """The logistic edge is 1/2 on the circle, within 1e-4 of the disk five
+    edge widths inside and outside, and reduces to the disk away from it."""
+    o = ph.optics(na_ill=0.7, tilt_x=0.05, smooth_source=True)
+    Y, X = 32, 40
+    S = O.source_pupil(o, Y, X)
+    Sh = O.source_pupil(dict(o, smooth_source=False), Y, X)
+    lam = o["lambda_um"]
+    ky, kx = O.transverse_grid(Y, X, o["pixel_um"])
+    d = np.sqrt((kx - o["tilt_x"] / lam) ** 2 + ky ** 2)
+    w = O.source_edge_width(o, Y, X)
+    far = np.abs(d - o["na_ill"] / lam) > 10 * w
+    assert np.abs(S - Sh)[far].max() <= 1e-4
+    o2 = dict(o, na_ill=float(d[3, 4] * lam))  # a grid point exactly on the edge
+    assert abs(O.source_pupil(o2, Y, X)[3, 4] - 0.5) <= 1e-12
+
+
+def test_smooth_source_derivatives_match_finite_differences():
+    o = ph.optics(na_ill=0.6, tilt_x=0.07, tilt_y=-0.04, smooth_source=True)
+    Y, X = 24, 32
+    dS = O.source_pupil_derivatives(o, Y, X)
+    h = 1e-6
+    for k in ("tilt_x", "tilt_y", "na_ill"):
+        fd = (O.source_pupil(dict(o, **{k: o[k] + h}), Y, X) - O.source_pupil(dict(o, **{k: o[k] - h}), Y, X)) / (2 * h)
+        assert np.abs(dS[k] - fd).max() <= 1e-6 * np.abs(fd).max(), k
+
+
+def test_smooth_source_forward_equals_weighted_source_point_sum():
+    """The correlation route with the smooth source equals the incoherent sum
+    of source-point fields weighted by S (independent of the correlation)."""
+    o = ph.optics(na_ill=0.55, tilt_x=0.06, tilt_y=0.02, defocus_um=0.2, smooth_source=True)
+    shape = (5, 20, 24)
+    rng = np.random.default_rng(11)
+    dn = rng.normal(size=shape[1:]) * 1e-2
+    kap = rng.normal(size=shape[1:]) * 1e-3
+    tfs = O.transfer_functions(o, shape, ("phase", "absorption"))
+    modes, _, _ = model.widefield_system(tfs, ("phase", "absorption"))
+    f = np.zeros((2,) + shape)
+    f[0, 1] = dn
+    f[1, 1] = kap
+    d = model.forward(modes, f, [1.0])[0] - 1.0
+    assert rel_l2(d, _field_route(o, shape, 1, dn, kap)) <= 1e-12
+
+
+def test_source_tf_derivatives_match_finite_differences():
+    from oracle import tuning
+    o = ph.optics(na_ill=0.65, tilt_x=0.05, tilt_y=-0.03, defocus_um=0.3, smooth_source=True)
+    shape = (6, 24, 32)
+    dH = tuning.plane_tf_source_derivatives(o, shape)
+    h = 1e-5
+    for k in ("tilt_x", "tilt_y", "na_ill"):
+        Hp = O.plane_tfs(dict(o, **{k: o[k] + h}), shape, ("phase",))["phase"]
+        Hm = O.plane_tfs(dict(o, **{k: o[k] - h}), shape, ("phase",))["phase"]
+        fd = (Hp - Hm) / (2 * h)
+        assert np.abs(dH[k] - fd).max() <= 1e-6 * np.abs(fd).max(), k
