@@ -654,7 +654,7 @@ def autotune_leg(args, rank, world, local_rank, with_cpu=True):
     truth = ph.tile_optics(np.random.default_rng(7 + rank), n)
     start = [dict(o, defocus_um=0.0) for o in truth]
     data = make_tune_data(truth, dev, seed=5 + rank)
-    pb = A.DefocusProblem(data, start, TUNE_ETA)
+    pb = A.TuningProblem(data, start, TUNE_ETA)
     B.wo_autotune(n, Z, Y, X, pb.kinds, pb.ws)  # the workspace is scratch between calls
     sched = A.default_schedule(truth[0])
     n_adam = sum(p.steps for p in sched)

@@ -84,11 +84,26 @@ enum { WO_TF_PHASE_DZ = 8 };
 /* Or-ed with WO_TF_PHASE_DZ only: keep the per-plane 2D TFs H_j(nu_perp) and
  * dH_j/dz0 (slot layout unchanged, index j = plane instead of axial bin; the
  * z-DFT is not applied and the statistics block holds only the optics
- * status).  Such a bank serves wo_defocus_objective alone, which then takes
+ * status).  Such a bank serves wo_tune_objective alone, which then takes
  * per-plane data spectra (wo_spectrum, WO_MODE_2D) and skips a z transform
  * per step; the operators reject it (WO_ERR_ARG). */
 enum { WO_TF_PLANES = 16 };
 enum { WO_LOSS_DATA = 0, WO_LOSS_MIDBAND = 1 };
+/* Or-ed with label-free kinds (phase, absorption, WO_TF_PHASE_DZ): the source
+ * pupil gets a logistic edge one frequency bin of the coarser axis wide,
+ *   S = 1 / (1 + exp(-(NA_ill/lambda - |nu - t/lambda|) / w)),  w = 1/(min(Y,X) p),
+ * instead of the closed disk, and sum S P^2 becomes a float sum: the model in
+ * which the illumination tilt and NA_ill have derivatives.  The detection
+ * pupil stays binary. */
+enum { WO_TF_SMOOTH_SOURCE = 32 };
+/* A bank of five per-plane TF slots for tuning defocus and illumination
+ * (requires WO_TF_PLANES; implies WO_TF_SMOOTH_SOURCE): slot 0 the phase TF,
+ * then its derivatives in defocus_um, tilt_x, tilt_y and na_ill.  The source
+ * enters the direct arm A = S P e^{i2pi eta z_j} and the normalisation
+ * D = sum S P^2, so dH1/dtheta = c sum (A_theta* B) / D - H1 D_theta / D with
+ * A_theta = (dS/dtheta) P e^{...}, D_theta = sum (dS/dtheta) P^2, through
+ * Table 1 unchanged.  X must be 32, 48, 64, 128 or 256. */
+enum { WO_TF_PHASE_GRAD = 64 };
 enum { WO_MODE_3D = 0, WO_MODE_2D = 1 };
 enum { WO_ETA_RELATIVE = 0, WO_ETA_ABSOLUTE = 1 };
 
@@ -253,8 +268,12 @@ wo_status wo_tile_blend(const float *d_tiles, int Z, int tiles_y, int tiles_x,
 wo_status wo_spectrum(const float *d_data, const float *h_background, int mode, void *d_spec,
                       int n_tiles, int Z, int Y, int X, wo_stream stream);
 
-/* wo_defocus_objective: per tile, a loss of the 2D thin-object reconstruction
- * and its derivative with respect to the tile's defocus.
+/* wo_tune_objective: per tile, a loss of the 2D thin-object reconstruction
+ * and its derivatives with respect to the tile's tuned optics parameters: the
+ * defocus alone (kinds with WO_TF_PHASE_DZ) or defocus, tilt_x, tilt_y and
+ * NA_ill (WO_TF_PHASE_GRAD; d_grad [n_tiles][4] in that order).  The formulas
+ * below are written for the defocus; every other parameter takes its own
+ * dH slot in place of dH.
  *
  * loss = WO_LOSS_DATA: the loss of the 2D thin-object fit (every
  * plane j sees the object at the reference plane through the per-plane phase
@@ -284,28 +303,32 @@ wo_status wo_spectrum(const float *d_data, const float *h_background, int mode, 
  * solve).  nu_max is ignored.
  * d_tf: a bank of these kinds for the same tiles; d_optics: the device optics
  * the bank was built from (8-byte aligned; pixel_um sets the frequency grid);
- * d_spec: wo_spectrum of the data in the matching mode.  d_value, d_grad: n_tiles doubles each
- * (8-byte aligned; either may be NULL, not both).  The workspace needs
- * n_tiles * ceil(Y*(X/2+1)/256) * 16 bytes, which wo_workspace_bytes(...,
- * WO_TF_PHASE_DZ) covers; the sums are reduced in a fixed order (repeatable
- * to the bit).  No host synchronisation: the call can be captured in a CUDA
- * graph together with wo_build_tf_device and wo_adam_defocus. */
-wo_status wo_defocus_objective(const void *d_tf, unsigned kinds, const wo_optics *d_optics,
-                               const void *d_spec, int loss, float eta, float nu_max,
-                               double *d_value, double *d_grad, int n_tiles, int Z, int Y, int X,
-                               void *d_ws, size_t ws_bytes, wo_stream stream);
+ * d_spec: wo_spectrum of the data in the matching mode.  d_value: n_tiles
+ * doubles, d_grad: n_tiles x n_params doubles (8-byte aligned; either may be
+ * NULL, not both).  The workspace needs n_tiles * ceil(Y*(X/2+1)/256) *
+ * 8 * (1 + n_params) bytes, which wo_workspace_bytes() of the bank's kinds
+ * covers; the sums are reduced in a fixed order (repeatable to the bit).  No host synchronisation: the call can be captured in a CUDA
+ * graph together with wo_build_tf_device and wo_adam_optics. */
+wo_status wo_tune_objective(const void *d_tf, unsigned kinds, const wo_optics *d_optics,
+                            const void *d_spec, int loss, float eta, float nu_max, double *d_value,
+                            double *d_grad, int n_tiles, int Z, int Y, int X, void *d_ws,
+                            size_t ws_bytes, wo_stream stream);
 
-/* wo_adam_defocus: one Adam step (Kingma and Ba, 2015) on each tile's
- * defocus_um in the device optics array, from the gradient d_grad:
+/* wo_adam_optics: one Adam step (Kingma and Ba, 2015) on each tile's tuned
+ * optics parameters in the device optics array - defocus_um (n_params = 1),
+ * or defocus_um, tilt_x, tilt_y, na_ill (n_params = 4) - from d_grad
+ * [n_tiles][n_params]:
  *   m = b1 m + (1-b1) g,  v = b2 v + (1-b2) g^2,  s = s + 1,
- *   z0 -= lr (m / (1 - b1^s)) / (sqrt(v / (1 - b2^s)) + eps).
- * d_state: n_tiles x {m, v, s} doubles, zeroed by the caller before the first
- * step and kept on the device, so a captured graph of build + objective +
- * step replays as further Adam iterations.  lr >= 0, 0 <= b1, b2 < 1,
- * eps > 0; all pointers 8-byte aligned. */
-wo_status wo_adam_defocus(wo_optics *d_optics, const double *d_grad, double *d_state,
-                          int n_tiles, double lr, double beta1, double beta2, double eps,
-                          wo_stream stream);
+ *   theta -= lr_p (m / (1 - b1^s)) / (sqrt(v / (1 - b2^s)) + eps);
+ * with four parameters NA_ill is then kept inside [0.01, n - |tilt| - 1e-3].
+ * d_state: n_tiles x n_params x {m, v, s} doubles, zeroed by the caller
+ * before the first step and kept on the device, so a captured graph of build
+ * + objective + step replays as further Adam iterations.  h_lr: n_params
+ * host step sizes >= 0; 0 <= b1, b2 < 1, eps > 0; device pointers 8-byte
+ * aligned. */
+wo_status wo_adam_optics(wo_optics *d_optics, const double *d_grad, int n_params, double *d_state,
+                         int n_tiles, const double *h_lr, double beta1, double beta2, double eps,
+                         wo_stream stream);
 
 /* Schedules and the autotuner (no counterpart in the paper).  A pass with
  * more than one implementation runs the engine its schedule table names.

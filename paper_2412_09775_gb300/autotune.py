@@ -1,21 +1,22 @@
-"""Per-tile defocus auto-tuning through the library's hand-written adjoint.
+"""Per-tile auto-tuning of the optics through the library's hand-written adjoint.
 
 The paper tunes each tile's optical parameters by gradient descent on a scalar
 loss of the reconstruction (Results, physics-guided auto-tuning; Fig. 2a(iv);
-Ext. Data Fig. 3).  Here the loss is the 2D thin-object Tikhonov fit
-(wo_defocus_objective) and the parameter is the tile's defocus; every step of
-the arithmetic runs in the library's kernels:
+Ext. Data Fig. 3).  Here the loss is the 2D thin-object Tikhonov fit or the
+paper's mid-band power (wo_tune_objective) and the parameters are the tile's
+defocus, or defocus, illumination tilt (x, y) and NA_ill under the smooth
+source pupil; every step of the arithmetic runs in the library's kernels:
 
-* ``DefocusProblem`` holds the device buffers of one batch of tiles: their
+* ``TuningProblem`` holds the device buffers of one batch of tiles: their
   optics (float64 [n, 9], the device array the TF build reads), the data
-  spectra (wo_spectrum, computed once), a WO_TF_PHASE_DZ bank (per plane by
-  default: the loss needs no z transform, by Parseval), the workspace,
-  and the per-tile loss, gradient and Adam state.
-* ``DefocusLoss`` is a torch.autograd.Function over the defocus vector: its
-  forward builds the TF pair and evaluates loss and derivative in one pass,
-  its backward returns that derivative times the incoming gradient.
-* ``DefocusProblem.run`` applies a schedule of ``Phase``s of Adam steps
-  (wo_adam_defocus, state on the device), eagerly or replayed from one
+  spectra (wo_spectrum, computed once), a derivative bank (per plane by
+  default: the loss needs no z transform, by Parseval), the workspace, and
+  the per-tile loss, gradient and Adam state.
+* ``TuneLoss`` is a torch.autograd.Function over the tuned parameters: its
+  forward builds the TF and its derivatives and evaluates loss and gradient
+  in one pass, its backward returns that gradient times the incoming one.
+* ``TuningProblem.run`` applies a schedule of ``Phase``s of Adam steps
+  (wo_adam_optics, state on the device), eagerly or replayed from one
   captured CUDA graph.
 """
 from __future__ import annotations
@@ -27,26 +28,38 @@ import torch
 
 from . import binding as B
 
-PHASE_DZ = B.WO_TF_PHASE_DZ
+# parameter order of the gradient and of the Adam state
+PARAMS = ("defocus_um", "tilt_x", "tilt_y", "na_ill")
+_COLUMN = {"defocus_um": 8, "tilt_x": 6, "tilt_y": 7, "na_ill": 5}  # wo_optics field index
 
 
-class DefocusProblem:
-    """``planes`` (default): per-plane TF banks and 2D data spectra, so no z
-    transform runs per step; otherwise 3D banks and spectra (the same loss by
-    Parseval over z).  ``loss``: the data-fidelity loss (default) or the
-    paper's mid-band power loss (WO_LOSS_MIDBAND)."""
+class TuningProblem:
+    """``params``: "defocus" (the defocus alone) or "all" (defocus, tilt_x,
+    tilt_y, NA_ill; the smooth-edged source pupil, per-plane banks).
+    ``planes`` (defocus only; default): per-plane TF banks and 2D data
+    spectra, so no z transform runs per step; otherwise 3D banks and spectra
+    (the same loss by Parseval over z).  ``smooth``: the smooth source pupil
+    for the defocus-only bank too.  ``loss``: the data-fidelity loss (default)
+    or the paper's mid-band power loss (WO_LOSS_MIDBAND)."""
 
     def __init__(self, data: torch.Tensor, optics_list, eta: float, background=None, planes: bool = True,
-                 loss: int = B.WO_LOSS_DATA):
+                 loss: int = B.WO_LOSS_DATA, params: str = "defocus", smooth: bool = False):
         if data.dim() != 4 or data.dtype != torch.float32 or not data.is_cuda:
             raise ValueError("data: float32 CUDA tensor [n_tiles, Z, Y, X]")
+        if params not in ("defocus", "all"):
+            raise ValueError("params: 'defocus' or 'all'")
         self.n, self.Z, self.Y, self.X = (int(s) for s in data.shape)
         if len(optics_list) != self.n:
             raise ValueError("one optics entry per tile")
         dev = data.device
         self.eta = float(eta)
         self.loss = int(loss)
-        self.kinds = PHASE_DZ | (B.WO_TF_PLANES if planes else 0)
+        self.n_params = 1 if params == "defocus" else 4
+        if self.n_params == 4:
+            self.kinds = B.WO_TF_PHASE_GRAD | B.WO_TF_PLANES
+            planes = True
+        else:
+            self.kinds = B.WO_TF_PHASE_DZ | (B.WO_TF_PLANES if planes else 0) | (B.WO_TF_SMOOTH_SOURCE if smooth else 0)
         self.mode = B.WO_MODE_2D if planes else B.WO_MODE_3D
         self.optics = B.optics_tensor(optics_list, dev)
         self.optics0 = self.optics.clone()
@@ -55,8 +68,8 @@ class DefocusProblem:
         self.background = background
         self.set_data(data)
         self.value = torch.zeros(self.n, dtype=torch.float64, device=dev)
-        self.grad = torch.zeros_like(self.value)
-        self.state = torch.zeros((self.n, 3), dtype=torch.float64, device=dev)
+        self.grad = torch.zeros((self.n, self.n_params), dtype=torch.float64, device=dev)
+        self.state = torch.zeros((self.n, self.n_params, 3), dtype=torch.float64, device=dev)
         self._graph = None
         self._graph_key = None
 
@@ -68,21 +81,29 @@ class DefocusProblem:
     def defocus(self) -> torch.Tensor:
         return self.optics[:, 8]
 
+    def params(self) -> torch.Tensor:
+        """The tuned parameters [n, n_params] (a copy)."""
+        return torch.stack([self.optics[:, _COLUMN[k]] for k in PARAMS[: self.n_params]], dim=1)
+
+    def set_params(self, p: torch.Tensor):
+        for i, k in enumerate(PARAMS[: self.n_params]):
+            self.optics[:, _COLUMN[k]].copy_(p[:, i])
+
     def reset(self):
         """Back to the starting optics, Adam state cleared."""
         self.optics.copy_(self.optics0)
         self.state.zero_()
 
     def evaluate(self, nu_max: float = 0.0):
-        """Loss and defocus derivative of every tile at the current optics."""
+        """Loss and gradient of every tile at the current optics."""
         n, Z, Y, X = self.n, self.Z, self.Y, self.X
         B.wo_build_tf_device(self.optics, n, Z, Y, X, self.kinds, self.tf, self.ws)
-        B.wo_defocus_objective(self.tf, self.kinds, self.optics, self.spec, self.loss, self.eta, nu_max, self.value,
-                               self.grad, n, Z, Y, X, self.ws)
+        B.wo_tune_objective(self.tf, self.kinds, self.optics, self.spec, self.loss, self.eta, nu_max, self.value,
+                            self.grad, n, Z, Y, X, self.ws)
 
-    def step(self, lr: float, nu_max: float = 0.0, beta1=0.9, beta2=0.999, eps=1e-8):
+    def step(self, lr, nu_max: float = 0.0, beta1=0.9, beta2=0.999, eps=1e-8):
         self.evaluate(nu_max)
-        B.wo_adam_defocus(self.optics, self.grad, self.state, self.n, lr, beta1, beta2, eps)
+        B.wo_adam_optics(self.optics, self.grad, self.n_params, self.state, self.n, lr, beta1, beta2, eps)
 
     def _queue(self, schedule):
         for ph in schedule:
@@ -119,18 +140,20 @@ class DefocusProblem:
 @dataclass(frozen=True)
 class Phase:
     """``steps`` Adam steps on the loss restricted to |nu| <= nu_max (0: the
-    full loss), the step size going from lr_start to lr_end (um) along half a
-    cosine; ``reset`` clears the Adam moments first (a new loss)."""
+    full loss), the step size going from lr_start to lr_end along half a
+    cosine; a step size is one number (every parameter) or a tuple with one
+    per tuned parameter.  ``reset`` clears the Adam moments first (a new
+    loss)."""
     steps: int
-    lr_start: float
-    lr_end: float
+    lr_start: float | tuple
+    lr_end: float | tuple
     nu_max: float = 0.0
     reset: bool = False
 
-    def lr_at(self, i: int) -> float:
-        if self.steps <= 1:
-            return self.lr_start
-        w = 0.5 * (1.0 + math.cos(math.pi * i / self.steps))
+    def lr_at(self, i: int):
+        w = 1.0 if self.steps <= 1 else 0.5 * (1.0 + math.cos(math.pi * i / self.steps))
+        if isinstance(self.lr_start, tuple):
+            return [e + (s - e) * w for s, e in zip(self.lr_start, self.lr_end)]
         return self.lr_end + (self.lr_start - self.lr_end) * w
 
 
@@ -142,12 +165,13 @@ def default_schedule(o) -> tuple:
     return (Phase(25, 0.08, 0.02, nu), Phase(25, 0.02, 0.0, 0.0, reset=True))
 
 
-class DefocusLoss(torch.autograd.Function):
-    """loss[t] = L_t(defocus[t]) with dL/d(defocus) from the library's adjoint."""
+class TuneLoss(torch.autograd.Function):
+    """loss[t] = L_t(theta[t]) with dL/dtheta from the library's adjoint;
+    theta [n, n_params] in the order of PARAMS."""
 
     @staticmethod
-    def forward(ctx, defocus: torch.Tensor, problem: DefocusProblem, nu_max: float = 0.0):
-        problem.optics[:, 8].copy_(defocus.detach())
+    def forward(ctx, theta: torch.Tensor, problem: TuningProblem, nu_max: float = 0.0):
+        problem.set_params(theta.detach().reshape(problem.n, problem.n_params))
         problem.evaluate(nu_max)
         ctx.save_for_backward(problem.grad.clone())
         return problem.value.clone()
@@ -155,8 +179,8 @@ class DefocusLoss(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_out):
         (g,) = ctx.saved_tensors
-        return grad_out * g, None, None
+        return grad_out[:, None] * g, None, None
 
 
-def defocus_loss(defocus: torch.Tensor, problem: DefocusProblem, nu_max: float = 0.0) -> torch.Tensor:
-    return DefocusLoss.apply(defocus, problem, nu_max)
+def tune_loss(theta: torch.Tensor, problem: TuningProblem, nu_max: float = 0.0) -> torch.Tensor:
+    return TuneLoss.apply(theta, problem, nu_max)

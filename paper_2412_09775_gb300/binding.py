@@ -18,13 +18,16 @@ LIB_PATH = os.path.join(HERE, "lib", "libwo_gb300.so")
 WO_TF_PHASE, WO_TF_ABSORPTION, WO_TF_FLUOR = 1, 2, 4
 WO_TF_PHASE_DZ = 8
 WO_TF_PLANES = 16
+WO_TF_SMOOTH_SOURCE = 32
+WO_TF_PHASE_GRAD = 64
 WO_MODE_3D, WO_MODE_2D = 0, 1
 WO_ETA_RELATIVE, WO_ETA_ABSOLUTE = 0, 1
 WO_LOSS_DATA, WO_LOSS_MIDBAND = 0, 1
 WO_PASS_COLS = 0
 WO_ENGINE_DEFAULT, WO_ENGINE_SMEM, WO_ENGINE_HYBRID = 0, 1, 2
 KIND_BITS = {"phase": WO_TF_PHASE, "absorption": WO_TF_ABSORPTION, "fluor": WO_TF_FLUOR,
-             "phase_dz": WO_TF_PHASE_DZ, "planes": WO_TF_PLANES}
+             "phase_dz": WO_TF_PHASE_DZ, "planes": WO_TF_PLANES, "smooth_source": WO_TF_SMOOTH_SOURCE,
+             "phase_grad": WO_TF_PHASE_GRAD}
 STATUS = {0: "WO_OK", 1: "WO_ERR_ARG", 2: "WO_ERR_SHAPE", 3: "WO_ERR_UNSUPPORTED_SIZE",
           4: "WO_ERR_UNDERSAMPLED", 5: "WO_ERR_CUDA", 6: "WO_ERR_TIMEOUT", 7: "WO_ERR_OPTICS",
           8: "WO_ERR_WORKSPACE"}
@@ -62,9 +65,9 @@ def _load():
         "wo_reconstruct": (i, [vp, u, vp, fp, fp, i, i, vp, i, i, i, i, vp, sz, vp]),
         "wo_reconstruct_static": (i, [vp, u, vp, fp, fp, i, i, vp, i, i, i, i, vp]),
         "wo_spectrum": (i, [vp, fp, i, vp, i, i, i, i, vp]),
-        "wo_defocus_objective": (i, [vp, u, vp, vp, i, f, f, vp, vp, i, i, i, i, vp, sz, vp]),
-        "wo_adam_defocus": (i, [vp, vp, vp, i, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                ctypes.c_double, vp]),
+        "wo_tune_objective": (i, [vp, u, vp, vp, i, f, f, vp, vp, i, i, i, i, vp, sz, vp]),
+        "wo_adam_optics": (i, [vp, vp, i, vp, i, ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                               ctypes.c_double, ctypes.c_double, vp]),
         "wo_fused_workspace_bytes": (sz, [i, i, i, i, i]),
         "wo_reconstruct_fused": (i, [vp, i, vp, fp, f, i, i, vp, i, i, i, i, vp, sz, vp]),
         "wo_schedule_set": (i, [i, i, i]),
@@ -89,7 +92,7 @@ _lib = _load()
 EXPORTED = ("wo_size_supported", "wo_tf_bytes", "wo_workspace_bytes", "wo_build_tf", "wo_build_tf_device",
             "wo_forward",
             "wo_forward_adjoint", "wo_reconstruct", "wo_reconstruct_static", "wo_spectrum",
-            "wo_defocus_objective", "wo_adam_defocus", "wo_fused_workspace_bytes", "wo_reconstruct_fused",
+            "wo_tune_objective", "wo_adam_optics", "wo_fused_workspace_bytes", "wo_reconstruct_fused",
             "wo_schedule_set", "wo_schedule_get", "wo_autotune", "wo_tile_gather", "wo_tile_blend",
             "wo_status_string", "wo_profile_enable", "wo_profile_read", "wo_launch_count")
 
@@ -223,18 +226,20 @@ def wo_spectrum(data, background, mode, spec, n_tiles, Z, Y, X, stream=None):
                             _stream(stream)), "wo_spectrum")
 
 
-def wo_defocus_objective(tf, kinds, d_optics, spec, loss, eta, nu_max, value, grad, n_tiles, Z, Y, X, ws,
-                         stream=None):
-    """Per-tile loss and defocus derivative (float64 tensors [n] or None) from a phase_dz bank."""
-    _check(_lib.wo_defocus_objective(_ptr(tf), kinds_mask(kinds), _ptr(d_optics), _ptr(spec), int(loss),
-                                     float(eta), float(nu_max), _ptr(value), _ptr(grad), n_tiles, Z, Y, X, _ptr(ws),
-                                     _nbytes(ws), _stream(stream)), "wo_defocus_objective")
+def wo_tune_objective(tf, kinds, d_optics, spec, loss, eta, nu_max, value, grad, n_tiles, Z, Y, X, ws,
+                      stream=None):
+    """Per-tile loss [n] and derivatives [n, n_params] (float64 tensors or None) from a derivative bank."""
+    _check(_lib.wo_tune_objective(_ptr(tf), kinds_mask(kinds), _ptr(d_optics), _ptr(spec), int(loss), float(eta),
+                                  float(nu_max), _ptr(value), _ptr(grad), n_tiles, Z, Y, X, _ptr(ws), _nbytes(ws),
+                                  _stream(stream)), "wo_tune_objective")
 
 
-def wo_adam_defocus(d_optics, grad, state, n_tiles, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
-    """One on-device Adam step on each tile's defocus (state: float64 [n, 3], zeroed before the first)."""
-    _check(_lib.wo_adam_defocus(_ptr(d_optics), _ptr(grad), _ptr(state), n_tiles, float(lr), float(beta1),
-                                float(beta2), float(eps), _stream(stream)), "wo_adam_defocus")
+def wo_adam_optics(d_optics, grad, n_params, state, n_tiles, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    """One on-device Adam step on each tile's tuned parameters (state: float64 [n, n_params, 3], zeroed first)."""
+    lrs = lr if isinstance(lr, (list, tuple)) else [lr] * n_params
+    arr = (ctypes.c_double * n_params)(*[float(v) for v in lrs])
+    _check(_lib.wo_adam_optics(_ptr(d_optics), _ptr(grad), int(n_params), _ptr(state), n_tiles, arr, float(beta1),
+                               float(beta2), float(eps), _stream(stream)), "wo_adam_optics")
 
 
 def wo_fused_workspace_bytes(n_channels, n_tiles, Z, Y, X) -> int:
@@ -299,7 +304,8 @@ def tf_views(tf, n_tiles, Z, Y, X, kinds):
     """(spectra, stats) views of a TF bank tensor: complex64 [n][k][Z][Y][X/2+1], float32 [n][8]."""
     import torch
     m = kinds_mask(kinds)
-    nk = 2 if (m & ~WO_TF_PLANES) == WO_TF_PHASE_DZ else bin(m).count("1")
+    core = m & ~(WO_TF_PLANES | WO_TF_SMOOTH_SOURCE)
+    nk = 2 if core == WO_TF_PHASE_DZ else (5 if core == WO_TF_PHASE_GRAD else bin(core).count("1"))
     Xh = X // 2 + 1
     n_spec = n_tiles * nk * Z * Y * Xh
     raw = tf.view(torch.uint8)

@@ -64,7 +64,7 @@ static bool size_ok(int n) {
 
 struct Sys {
   int n_kinds, lf_props, has_fl, C, P, n_arms;
-  int want_phase, want_abs, want_dz, planes;
+  int want_phase, want_abs, want_dz, planes, want_grad, smooth;
 };
 
 static Sys system_of(unsigned kinds) {
@@ -77,7 +77,24 @@ static Sys system_of(unsigned kinds) {
   s.C = (s.lf_props ? 1 : 0) + s.has_fl;
   s.P = s.n_kinds;
   s.n_arms = (s.lf_props ? 2 : 0) + s.has_fl;
-  if ((kinds & ~(unsigned)WO_TF_PLANES) == WO_TF_PHASE_DZ) {  // phase TF and d/dz0: two slots, four arms
+  s.smooth = (kinds & WO_TF_SMOOTH_SOURCE) ? 1 : 0;
+  const unsigned core = kinds & ~(unsigned)(WO_TF_PLANES | WO_TF_SMOOTH_SOURCE);
+  if (core == WO_TF_PHASE_GRAD) {  // phase TF and d/d(z0, tilt_x, tilt_y, NA_ill): five slots, seven arms
+    s.want_phase = 1;
+    s.want_dz = 1;
+    s.want_grad = 1;
+    s.smooth = 1;
+    s.planes = 1;
+    s.lf_props = 1;
+    s.n_kinds = 5;
+    s.C = 1;
+    s.P = 1;
+    s.n_arms = 7;
+    s.want_abs = 0;
+    s.has_fl = 0;
+    return s;
+  }
+  if (core == WO_TF_PHASE_DZ) {  // phase TF and d/dz0: two slots, four arms
     s.planes = (kinds & WO_TF_PLANES) ? 1 : 0;
     s.want_phase = 1;
     s.want_dz = 1;
@@ -93,7 +110,7 @@ static Sys system_of(unsigned kinds) {
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t optics, counts, rec, arms, build_end;
+  size_t optics, counts, rec, rec2, norm_part, norms, arms, build_end;
   size_t specA, specB, op_end;
   size_t total;
   size_t tf_spectra, tf_stats, tf_total;
@@ -106,6 +123,10 @@ static Layout layout_of(int n, int Z, int Y, int X, const Sys& s) {
   L.optics = off; off += align256((size_t)n * sizeof(wo_optics));
   L.counts = off; off += align256((size_t)n * 4 * sizeof(int));
   L.rec = off; off += align256((size_t)n * Y * X * sizeof(float4));
+  L.rec2 = off; if (s.want_grad) off += align256((size_t)n * Y * X * sizeof(float4));
+  const int rb = (Y + record_rows(Y, n) - 1) / record_rows(Y, n);
+  L.norm_part = off; if (s.smooth) off += align256((size_t)n * rb * 4 * sizeof(float));
+  L.norms = off; if (s.smooth) off += align256((size_t)n * 4 * sizeof(float));
   L.arms = off; off += align256((size_t)n * s.n_arms * Z * Y * X * sizeof(float2));
   L.build_end = off;
   const size_t vols = (size_t)(s.C > s.P ? s.C : s.P);
@@ -114,7 +135,7 @@ static Layout layout_of(int n, int Z, int Y, int X, const Sys& s) {
   L.specB = spec;
   L.op_end = 2 * spec;
   L.total = L.build_end > L.op_end ? L.build_end : L.op_end;
-  if (s.want_dz && tune_partials_bytes(n, Y, X) > L.total) L.total = tune_partials_bytes(n, Y, X);
+  if (s.want_dz && tune_partials_bytes(n, Y, X, 4) > L.total) L.total = tune_partials_bytes(n, Y, X, 4);
   L.tf_spectra = align256((size_t)n * s.n_kinds * Z * Y * Xh * sizeof(float2));
   L.tf_stats = L.tf_spectra;
   L.tf_total = L.tf_spectra + (size_t)n * 8 * sizeof(float);
@@ -133,16 +154,23 @@ static size_t zpass_smem(int Z) {
 
 static wo_status check_shape(int n_tiles, int Z, int Y, int X, unsigned kinds) {
   if (n_tiles < 1 || n_tiles > 65535) return WO_ERR_ARG;
-  if (kinds == 0 || (kinds & ~31u)) return WO_ERR_ARG;
-  const unsigned base = kinds & ~(unsigned)WO_TF_PLANES;
+  if (kinds & ~127u) return WO_ERR_ARG;
+  const unsigned base = kinds & ~(unsigned)(WO_TF_PLANES | WO_TF_SMOOTH_SOURCE);
+  if (base == 0) return WO_ERR_ARG;
   if ((base & WO_TF_PHASE_DZ) && base != WO_TF_PHASE_DZ) return WO_ERR_ARG;
-  if ((kinds & WO_TF_PLANES) && base != WO_TF_PHASE_DZ) return WO_ERR_ARG;
+  if ((base & WO_TF_PHASE_GRAD) && base != WO_TF_PHASE_GRAD) return WO_ERR_ARG;
+  if ((kinds & WO_TF_PLANES) && base != WO_TF_PHASE_DZ && base != WO_TF_PHASE_GRAD) return WO_ERR_ARG;
+  if (base == WO_TF_PHASE_GRAD && !(kinds & WO_TF_PLANES)) return WO_ERR_ARG;  // per-plane banks only
+  if ((kinds & WO_TF_SMOOTH_SOURCE) && base == WO_TF_FLUOR) return WO_ERR_ARG;  // no source pupil
   if (Z < 1 || Y < 1 || X < 2) return WO_ERR_SHAPE;
   if (X % 2) return WO_ERR_SHAPE;
   if (!size_ok(Z) || !size_ok(Y) || !size_ok(X / 2) || X > 2048) return WO_ERR_UNSUPPORTED_SIZE;
   if (zpass_smem(Z) > 227 * 1024) return WO_ERR_UNSUPPORTED_SIZE;
   // four arm rows of X per PSF-row block must fit shared memory
   if (base == WO_TF_PHASE_DZ && X > 768) return WO_ERR_UNSUPPORTED_SIZE;
+  // the seven arms of the gradient bank need the register-resident row pass
+  if (base == WO_TF_PHASE_GRAD && !(X == 32 || X == 48 || X == 64 || X == 128 || X == 256))
+    return WO_ERR_UNSUPPORTED_SIZE;
   return WO_OK;
 }
 
@@ -276,6 +304,12 @@ static wo_status build_tf_impl(const wo_optics* optics, bool on_host, int n_tile
   a.want_phase = s.want_phase; a.want_abs = s.want_abs; a.want_fl = s.has_fl;
   a.n_arms = s.n_arms; a.n_kinds = s.n_kinds;
   a.want_dz = s.want_dz;
+  a.want_grad = s.want_grad;
+  a.smooth = s.smooth;
+  a.rec2 = (float4*)(ws + L.rec2);
+  a.norm_part = (float*)(ws + L.norm_part);
+  a.norms = (float*)(ws + L.norms);
+  a.rec_blocks = (Y + record_rows(Y, n_tiles) - 1) / record_rows(Y, n_tiles);
   if (on_host)
     WO_TRY(cudaMemcpyAsync((void*)a.optics, optics, (size_t)n_tiles * sizeof(wo_optics), cudaMemcpyHostToDevice, cs));
   WO_TRY(cudaMemsetAsync(a.counts, 0, (size_t)n_tiles * 4 * sizeof(int), cs));
@@ -443,10 +477,11 @@ wo_status wo_spectrum(const float* d_data, const float* h_background, int mode, 
   return WO_OK;
 }
 
-wo_status wo_defocus_objective(const void* d_tf, unsigned kinds, const wo_optics* d_optics, const void* d_spec,
-                               int loss, float eta, float nu_max, double* d_value, double* d_grad, int n_tiles,
-                               int Z, int Y, int X, void* d_ws, size_t ws_bytes, wo_stream stream) {
-  if (kinds != WO_TF_PHASE_DZ && kinds != (WO_TF_PHASE_DZ | WO_TF_PLANES)) return WO_ERR_ARG;
+wo_status wo_tune_objective(const void* d_tf, unsigned kinds, const wo_optics* d_optics, const void* d_spec,
+                            int loss, float eta, float nu_max, double* d_value, double* d_grad, int n_tiles, int Z,
+                            int Y, int X, void* d_ws, size_t ws_bytes, wo_stream stream) {
+  const unsigned base = kinds & ~(unsigned)(WO_TF_PLANES | WO_TF_SMOOTH_SOURCE);
+  if (base != WO_TF_PHASE_DZ && base != WO_TF_PHASE_GRAD) return WO_ERR_ARG;
   if (loss != WO_LOSS_DATA && loss != WO_LOSS_MIDBAND) return WO_ERR_ARG;
   wo_status st = check_shape(n_tiles, Z, Y, X, kinds);
   if (st != WO_OK) return st;
@@ -455,21 +490,28 @@ wo_status wo_defocus_objective(const void* d_tf, unsigned kinds, const wo_optics
   if (!d_value && !d_grad) return WO_ERR_ARG;
   if ((d_value && (((uintptr_t)d_value) & 7u)) || (d_grad && (((uintptr_t)d_grad) & 7u))) return WO_ERR_ARG;
   if (!(eta >= 0.f) || !isfinite(eta) || !(nu_max == nu_max)) return WO_ERR_ARG;
-  if (ws_bytes < tune_partials_bytes(n_tiles, Y, X)) return WO_ERR_WORKSPACE;
+  const int np = base == WO_TF_PHASE_GRAD ? 4 : 1;
+  if (ws_bytes < tune_partials_bytes(n_tiles, Y, X, np)) return WO_ERR_WORKSPACE;
   return cuda_status(tune_reduce((const float2*)d_tf, (const float2*)d_spec, d_optics, n_tiles, Z, Y, X, eta,
-                                 isfinite(nu_max) ? nu_max : 0.f, (kinds & WO_TF_PLANES) ? 1 : Z, loss,
+                                 isfinite(nu_max) ? nu_max : 0.f, (kinds & WO_TF_PLANES) ? 1 : Z, loss, np,
                                  (double*)d_ws, d_value, d_grad, (cudaStream_t)stream));
 }
 
-wo_status wo_adam_defocus(wo_optics* d_optics, const double* d_grad, double* d_state, int n_tiles, double lr,
-                          double beta1, double beta2, double eps, wo_stream stream) {
+wo_status wo_adam_optics(wo_optics* d_optics, const double* d_grad, int n_params, double* d_state, int n_tiles,
+                         const double* h_lr, double beta1, double beta2, double eps, wo_stream stream) {
   if (n_tiles < 1 || n_tiles > 65535) return WO_ERR_ARG;
-  if (!d_optics || !d_grad || !d_state) return WO_ERR_ARG;
+  if (n_params != 1 && n_params != 4) return WO_ERR_ARG;
+  if (!d_optics || !d_grad || !d_state || !h_lr) return WO_ERR_ARG;
   if ((((uintptr_t)d_optics) | ((uintptr_t)d_grad) | ((uintptr_t)d_state)) & 7u) return WO_ERR_ARG;
-  if (!(lr >= 0.0) || !isfinite(lr) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) ||
-      !(eps > 0.0) || !isfinite(eps))
+  AdamLr lr{};
+  for (int p = 0; p < n_params; ++p) {
+    if (!(h_lr[p] >= 0.0) || !isfinite(h_lr[p])) return WO_ERR_ARG;
+    lr.v[p] = h_lr[p];
+  }
+  if (!(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) || !(eps > 0.0) || !isfinite(eps))
     return WO_ERR_ARG;
-  return cuda_status(adam_defocus(d_optics, d_grad, d_state, n_tiles, lr, beta1, beta2, eps, (cudaStream_t)stream));
+  return cuda_status(adam_optics(d_optics, d_grad, n_params, d_state, n_tiles, lr, beta1, beta2, eps,
+                                 (cudaStream_t)stream));
 }
 
 wo_status wo_reconstruct_fused(const void* d_tf, int n_channels, const float* d_data, const float* h_background,

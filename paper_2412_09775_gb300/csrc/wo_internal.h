@@ -79,7 +79,7 @@ cudaError_t z_fuse(int Z, const float2* in, float2* out, const float2* tf, const
 // Transfer-function build.
 struct TfArgs {
   const wo_optics* optics;  // device copy, [n_tiles]
-  int* counts;              // [n_tiles][4]: #(S and P), #P, x band limit, -
+  int* counts;              // [n_tiles][4]: #(S and P) (binary source), #P, x band limit, -
   float4* rec;              // [n_tiles][Y][X] pupil record
   float2* arms;             // [n_tiles][n_arms][Z][Y][X]
   float2* tf;               // [n_tiles][n_kinds][Z][Y][Xh]
@@ -90,9 +90,16 @@ struct TfArgs {
   int n_arms;               // 2*(lf) + fl, or 4 with want_dz
   int n_kinds;
   int want_dz;              // phase TF and dH/d(defocus): arms A, B, A', B'; kinds 2
+  int want_grad;            // plus dH/d(tilt_x, tilt_y, NA_ill): arms A_tx, A_ty, A_na; kinds 5
+  int smooth;               // smooth-edged source pupil (S a float in [0, 1])
+  float4* rec2;             // [n_tiles][Y][X] (dS/dtx P, dS/dty P, dS/dNA P, 0), want_grad only
+  float* norm_part;         // [n_tiles][record blocks][4] partial sums of S P and dS P
+  float* norms;             // [n_tiles][4]: sum S P, then sum dS/dtheta P (smooth source)
+  int rec_blocks;           // record blocks per tile
   long long row_begin, row_end;  // PSF-row pass: rows (t*Z + j)*Y + y in [begin, end)
 };
 cudaError_t tf_pupil_record(const TfArgs& a, cudaStream_t s);
+int record_rows(int Y, int n_tiles);  // rows per pupil-record block
 cudaError_t tf_arms(const TfArgs& a, cudaStream_t s);
 cudaError_t tf_psf_rows(const TfArgs& a, cudaStream_t s);
 // Hybrid column engine (wo_colhyb.cu) and the schedule table (wo_sched.cu).
@@ -106,23 +113,26 @@ bool psf_rows_reg_supported(int X, int n_arms);
 cudaError_t tf_psf_rows_reg(const TfArgs& a, cudaStream_t s);
 cudaError_t tf_zpass(const TfArgs& a, cudaStream_t s);
 
-// Auto-tuning: per-tile value and defocus derivative of the 2D thin-object
-// loss from a data spectrum [tile][Z][Y][Xh] and a TF pair bank (H, dH/dz)
-// [tile][2][Z][Y][Xh]; frequencies above nu_max (cycles/um, > 0) are left
-// out.  `partials` holds tune_partials_bytes(n_tiles, Y, X) bytes.
+// Auto-tuning: per-tile value and derivatives of the 2D thin-object loss from
+// a data spectrum [tile][Z][Y][Xh] and a bank of 1 + np slots per tile (H,
+// then dH/dtheta_p); frequencies above nu_max (cycles/um, > 0) are left out.
 // zf: Z for 3D spectra (Parseval over z puts a factor Z on the eta term and
-// on the normalisation), 1 for per-plane 2D spectra.
+// on the normalisation), 1 for per-plane 2D spectra.  value [tile],
+// grad [tile][np].  `partials` holds tune_partials_bytes(n_tiles, Y, X, np).
 cudaError_t tune_reduce(const float2* tf2, const float2* spec, const wo_optics* optics, int n_tiles, int Z,
-                        int Y, int X, float eta, float nu_max, int zf, int loss, double* partials, double* value,
-                        double* grad, cudaStream_t s);
-size_t tune_partials_bytes(int n_tiles, int Y, int X);
+                        int Y, int X, float eta, float nu_max, int zf, int loss, int np, double* partials,
+                        double* value, double* grad, cudaStream_t s);
+size_t tune_partials_bytes(int n_tiles, int Y, int X, int np);
+struct AdamLr {
+  double v[4];  // step sizes for defocus_um, tilt_x, tilt_y, na_ill
+};
+cudaError_t adam_optics(wo_optics* optics, const double* grad, int np, double* state, int n_tiles, AdamLr lr,
+                        double b1, double b2, double eps, cudaStream_t s);
 // Zero element 0 of each of n_tiles volumes of vol elements (the DC bin).
 cudaError_t zero_dc(float2* spec, int n_tiles, long long vol, cudaStream_t s);
 // Per-plane 2D spectra [tile][Z][plane]: subtract from each plane's DC bin the
 // mean of the tile's DC bins (background = the stack's mean).
 cudaError_t center_dc_planes(float2* spec, int n_tiles, int Z, long long plane, cudaStream_t s);
-cudaError_t adam_defocus(wo_optics* optics, const double* grad, double* state, int n_tiles, double lr,
-                         double b1, double b2, double eps, cudaStream_t s);
 
 // Tiles.
 cudaError_t tiles_gather(const float* field, int Z, int ty, int tx, int core, int halo,

@@ -48,10 +48,12 @@ __device__ __forceinline__ float2 mirror_value(const float2 (&v)[N1], int m, boo
 }
 }  // namespace
 
-// P: the row transform (Row2 or Row512 of wo_regfft.cuh).  DZ: the bank of
-// the phase TF and its defocus derivative (four arms); otherwise any mix of
-// label-free and fluorescence kinds.
-template <class P, bool DZ>
+// P: the row transform (Row2 or Row512 of wo_regfft.cuh).  MODE 0: any mix
+// of label-free and fluorescence kinds; 1: the phase TF and its defocus
+// derivative (arms A, B, A', B'); 2: plus the derivatives in tilt_x, tilt_y
+// and NA_ill under the smooth source (arms A_tx, A_ty, A_NA; their rows
+// 2K (Re conj(a_theta) b - (D_theta / D) Re g), D = sum S P^2).
+template <class P, int MODE>
 __global__ void __launch_bounds__(kPsfThreads, 4) k_psf_rows_reg(TfArgs a) {
   constexpr int N = P::N, N1 = P::E, T = P::T, RP = P::SLICE, RPC = kPsfThreads / T;
   __shared__ float2 tw[P::TW];
@@ -75,28 +77,32 @@ __global__ void __launch_bounds__(kPsfThreads, 4) k_psf_rows_reg(TfArgs a) {
   float2* dst = a.tf + (t * a.n_kinds * a.Z) * (long long)a.Y * Xh + rem * Xh;  // slot 0 of this row
   const long long kstride = (long long)a.Z * a.Y * Xh;
 
+  constexpr bool DZ = MODE >= 1;
   float2 w[N1];
+  float gre[MODE == 2 ? N1 : 1];  // Re g (unscaled), for the normalisation terms
+  float2 vb[N1];                  // b, kept for the source-parameter arms
   int slot = 0;
   if (DZ || lf) {
     const float sc = lf_scale(a, (int)t);
-    float2 va[N1], vb[N1];
+    float2 va[N1];
     if constexpr (DZ) {
-      // w = 2K (Re conj(a) b + i (Re conj(a') b + Re conj(a) b')), arms A, B, A', B'
-      load_arm<P>(vb, a, t, rem, 1, kxm, lt);
-      P::template fft<true>(vb, tw, S, lt);
-      load_arm<P>(va, a, t, rem, 2, kxm, lt);
-      P::template fft<true>(va, tw, S, lt);
-#pragma unroll
-      for (int m = 0; m < N1; ++m) w[m].y = va[m].x * vb[m].x + va[m].y * vb[m].y;
+      // w = 2K (Re conj(a) b + i (Re conj(a) b' + Re conj(a') b)), arms A, B, A', B'
       load_arm<P>(va, a, t, rem, 0, kxm, lt);
       P::template fft<true>(va, tw, S, lt);
-#pragma unroll
-      for (int m = 0; m < N1; ++m) w[m].x = va[m].x * vb[m].x + va[m].y * vb[m].y;
       load_arm<P>(vb, a, t, rem, 3, kxm, lt);
       P::template fft<true>(vb, tw, S, lt);
 #pragma unroll
+      for (int m = 0; m < N1; ++m) w[m].y = va[m].x * vb[m].x + va[m].y * vb[m].y;
+      load_arm<P>(vb, a, t, rem, 1, kxm, lt);
+      P::template fft<true>(vb, tw, S, lt);
+#pragma unroll
+      for (int m = 0; m < N1; ++m) w[m].x = va[m].x * vb[m].x + va[m].y * vb[m].y;
+      load_arm<P>(va, a, t, rem, 2, kxm, lt);
+      P::template fft<true>(va, tw, S, lt);
+#pragma unroll
       for (int m = 0; m < N1; ++m) {
         w[m].y += va[m].x * vb[m].x + va[m].y * vb[m].y;
+        if constexpr (MODE == 2) gre[m] = w[m].x;
         w[m] = cscale(w[m], sc);
       }
     } else {
@@ -129,6 +135,44 @@ __global__ void __launch_bounds__(kPsfThreads, 4) k_psf_rows_reg(TfArgs a) {
     }
     slot = DZ ? 2 : a.lf_props;
   }
+  if constexpr (MODE == 2) {
+    // source parameters: rows 2K (Re conj(a_theta) b - r_theta Re g), tilt_x
+    // and tilt_y packed as one complex row, NA_ill as a real row
+    const float sc = lf_scale(a, (int)t);
+    const float rx = norm_dlog(a, (int)t, 0), ry = norm_dlog(a, (int)t, 1), rn = norm_dlog(a, (int)t, 2);
+    float2 va[N1];
+    load_arm<P>(va, a, t, rem, 4, kxm, lt);
+    P::template fft<true>(va, tw, S, lt);
+#pragma unroll
+    for (int m = 0; m < N1; ++m) w[m].x = sc * (va[m].x * vb[m].x + va[m].y * vb[m].y - rx * gre[m]);
+    load_arm<P>(va, a, t, rem, 5, kxm, lt);
+    P::template fft<true>(va, tw, S, lt);
+#pragma unroll
+    for (int m = 0; m < N1; ++m) w[m].y = sc * (va[m].x * vb[m].x + va[m].y * vb[m].y - ry * gre[m]);
+    P::template fft<false>(w, tw, S, lt);
+#pragma unroll
+    for (int m = 0; m < N1; ++m) {
+      const float2 mv = mirror_value<N1>(w, m, lane0);
+      float2 c;  // conj(W(N - k))
+      c.x = __shfl_sync(0xffffffffu, mv.x, partner);
+      c.y = -__shfl_sync(0xffffffffu, mv.y, partner);
+      const int k = lt + T * m;
+      if (!live || k > N / 2) continue;
+      const float2 d = make_float2(0.5f * (w[m].x - c.x), 0.5f * (w[m].y - c.y));
+      dst[2 * kstride + k] = make_float2(0.5f * (w[m].x + c.x), 0.5f * (w[m].y + c.y));
+      dst[3 * kstride + k] = make_float2(d.y, -d.x);
+    }
+    load_arm<P>(va, a, t, rem, 6, kxm, lt);
+    P::template fft<true>(va, tw, S, lt);
+#pragma unroll
+    for (int m = 0; m < N1; ++m) w[m] = make_float2(sc * (va[m].x * vb[m].x + va[m].y * vb[m].y - rn * gre[m]), 0.f);
+    P::template fft<false>(w, tw, S, lt);
+#pragma unroll
+    for (int m = 0; m < N1; ++m) {
+      const int k = lt + T * m;
+      if (live && k <= N / 2) dst[4 * kstride + k] = w[m];
+    }
+  }
   if (!DZ && fl) {
     const float scf = fl_scale(a, (int)t);
     load_arm<P>(w, a, t, rem, lf ? 2 : 0, kxm, lt);
@@ -144,23 +188,28 @@ __global__ void __launch_bounds__(kPsfThreads, 4) k_psf_rows_reg(TfArgs a) {
   }
 }
 
-template <class P, bool DZ>
+template <class P, int MODE>
 static cudaError_t launch_psf_reg(const TfArgs& a, cudaStream_t s) {
   constexpr int RPC = kPsfThreads / P::T;
   const long long rows = a.row_end - a.row_begin;
   const unsigned grid = (unsigned)((rows + RPC - 1) / RPC);
-  WO_LAUNCH("tf_psf_rows", s, (k_psf_rows_reg<P, DZ><<<grid, kPsfThreads, 0, s>>>(a)));
+  WO_LAUNCH("tf_psf_rows", s, (k_psf_rows_reg<P, MODE><<<grid, kPsfThreads, 0, s>>>(a)));
   return cudaGetLastError();
 }
 
-template <class P>
+template <class P, bool GRAD = true>
 static cudaError_t launch_psf_reg_any(const TfArgs& a, cudaStream_t s) {
-  return a.want_dz ? launch_psf_reg<P, true>(a, s) : launch_psf_reg<P, false>(a, s);
+  if (a.want_grad) {
+    if constexpr (GRAD) return launch_psf_reg<P, 2>(a, s);
+    return cudaErrorInvalidValue;
+  }
+  return a.want_dz ? launch_psf_reg<P, 1>(a, s) : launch_psf_reg<P, 0>(a, s);
 }
 
 bool psf_rows_reg_supported(int X, int n_arms) {
   switch (X) {
-    case 32: case 48: case 64: case 128: case 256: case 512: return true;
+    case 32: case 48: case 64: case 128: case 256: return true;
+    case 512: return n_arms <= 4;
     case 96: case 192: return n_arms <= 3;  // 24 points per lane: four arms would spill
     default: return false;
   }
@@ -171,11 +220,11 @@ cudaError_t tf_psf_rows_reg(const TfArgs& a, cudaStream_t s) {
     case 32: return launch_psf_reg_any<Row2<32, 8>>(a, s);
     case 48: return launch_psf_reg_any<Row2<48, 12>>(a, s);
     case 64: return launch_psf_reg_any<Row2<64, 8>>(a, s);
-    case 96: return a.want_dz ? cudaErrorInvalidValue : launch_psf_reg<Row2<96, 24>, false>(a, s);
+    case 96: return a.want_dz ? cudaErrorInvalidValue : launch_psf_reg<Row2<96, 24>, 0>(a, s);
     case 128: return launch_psf_reg_any<Row2<128, 16>>(a, s);
-    case 192: return a.want_dz ? cudaErrorInvalidValue : launch_psf_reg<Row2<192, 24>, false>(a, s);
+    case 192: return a.want_dz ? cudaErrorInvalidValue : launch_psf_reg<Row2<192, 24>, 0>(a, s);
     case 256: return launch_psf_reg_any<Row2<256, 16>>(a, s);
-    case 512: return launch_psf_reg_any<Row512>(a, s);
+    case 512: return launch_psf_reg_any<Row512, false>(a, s);
     default: return cudaErrorInvalidValue;
   }
 }

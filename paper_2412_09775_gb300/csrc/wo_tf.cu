@@ -37,6 +37,11 @@ namespace wo {
 // busy (each block computes the x frequency axis once, with IEEE divisions).
 constexpr int kRecRowsMax = 32;
 
+int record_rows(int Y, int n_tiles) {
+  const long long want = ((long long)Y * n_tiles + 303) / 304;
+  return (int)(want < 8 ? 8 : (want > kRecRowsMax ? kRecRowsMax : want));
+}
+
 // Device-side copy of the host validation (wo_api.cu check_optics) for optics
 // that live in device memory: 0 if valid, else the wo_status code.
 __device__ int optics_status(const wo_optics& o) {
@@ -54,15 +59,16 @@ __device__ int optics_status(const wo_optics& o) {
   return WO_OK;
 }
 
-__global__ void __launch_bounds__(256)
-    k_pupil_record(const wo_optics* __restrict__ optics, float4* __restrict__ rec, int* __restrict__ counts,
-                   float* __restrict__ stats, int Y, int X, int kRecRows) {
+__global__ void __launch_bounds__(256) k_pupil_record(TfArgs a, int kRecRows) {
   extern __shared__ double nu_x[];  // [X]
   __shared__ double nu_y[kRecRowsMax];
   __shared__ int part[2][8];
+  __shared__ float fpart[4][8];
+  const int Y = a.Y, X = a.X;
   const int t = blockIdx.y;
   const int y0 = blockIdx.x * kRecRows;
-  const wo_optics o = optics[t];
+  const wo_optics o = a.optics[t];
+  float4* rec = a.rec;
   // Invalid optics (possible only when they come from device memory): the
   // tile's record is all zero, so its transfer functions are zero, and its
   // status is left in the statistics block.
@@ -70,9 +76,13 @@ __global__ void __launch_bounds__(256)
   if (status != WO_OK) {
     for (int e = threadIdx.x; e < kRecRows * X; e += 256) {
       const int yy = e / X;
-      if (y0 + yy < Y) rec[((long long)t * Y + y0 + yy) * X + (e - yy * X)] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (y0 + yy >= Y) continue;
+      const long long i = ((long long)t * Y + y0 + yy) * X + (e - yy * X);
+      rec[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (a.want_grad) a.rec2[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) reinterpret_cast<int*>(stats)[(long long)t * 8 + 4] = status;
+    if (a.smooth && threadIdx.x < 4) a.norm_part[((long long)t * a.rec_blocks + blockIdx.x) * 4 + threadIdx.x] = 0.f;
+    if (blockIdx.x == 0 && threadIdx.x == 0) reinterpret_cast<int*>(a.stats)[(long long)t * 8 + 4] = status;
     return;  // uniform across the block
   }
   const double px = __dmul_rn((double)X, o.pixel_um), py = __dmul_rn((double)Y, o.pixel_um);
@@ -90,7 +100,12 @@ __global__ void __launch_bounds__(256)
   // margin far above the float error; otherwise the float64 expression decides
   const float rp2f = (float)rp2, rs2f = (float)rs2, cxf = (float)cx, cyf = (float)cy;
   const float mp = 1e-5f * rp2f;
+  // smooth source: S = 1 / (1 + exp(-(R - d) / w)), w one frequency bin of the
+  // coarser axis, and its derivatives in tilt and NA_ill
+  const float rsf = (float)rs, lamf = (float)lam;
+  const float wedge = (float)(1.0 / ((double)min(Y, X) * o.pixel_um));
   int n_sp = 0, n_p = 0, kx_band = -1;
+  float s_sp = 0.f, s_tx = 0.f, s_ty = 0.f, s_na = 0.f;
   const int rows = min(kRecRows, Y - y0);
   for (int e = threadIdx.x; e < rows * X; e += 256) {
     const int yy = e / X, x = e - (e / X) * X;
@@ -101,19 +116,31 @@ __global__ void __launch_bounds__(256)
     if (r2f < rp2f - mp) P = true;
     else if (r2f > rp2f + mp) P = false;
     else P = __dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)) <= rp2;
-    bool S = false;
-    if (P) {
+    float S = 0.f, dtx = 0.f, dty = 0.f, dna = 0.f;
+    if (P && a.smooth) {
+      const float ux = vxf - cxf, uy = vyf - cyf;
+      const float d = sqrtf(ux * ux + uy * uy);
+      S = 1.0f / (1.0f + expf(-(rsf - d) / wedge));
+      const float ds = S * (1.0f - S) / wedge;
+      dna = ds / lamf;
+      if (d > 0.f) {
+        dtx = ds * ux / (d * lamf);
+        dty = ds * uy / (d * lamf);
+      }
+    } else if (P) {
       const float dxf = vxf - cxf, dyf = vyf - cyf;
       const float s2f = dxf * dxf + dyf * dyf;
       // the float error of s2f scales with (|nu| + |c|)^2, not with rs^2
       const float ax = fabsf(vxf) + fabsf(cxf), ay = fabsf(vyf) + fabsf(cyf);
       const float ms = 1e-5f * rs2f + 4e-6f * (ax * ax + ay * ay) + 1e-9f;
-      if (s2f < rs2f - ms) S = true;
-      else if (s2f > rs2f + ms) S = false;
+      bool Sb;
+      if (s2f < rs2f - ms) Sb = true;
+      else if (s2f > rs2f + ms) Sb = false;
       else {
         const double dy = __dsub_rn(vy, cy), dx = __dsub_rn(vx, cx);
-        S = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) <= rs2;
+        Sb = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) <= rs2;
       }
+      S = Sb ? 1.f : 0.f;
     }
     // eta (as a float pair) is used only inside the detection pupil, where
     // every arm lives; elsewhere the record holds zeros
@@ -130,9 +157,15 @@ __global__ void __launch_bounds__(256)
         binv = 1.0f / eh;
       }
     }
-    rec[((long long)t * Y + y0 + yy) * X + x] = make_float4(eh, el, binv, (S && P) ? 1.f : 0.f);
-    n_sp += (S && P) ? 1 : 0;
+    const long long i = ((long long)t * Y + y0 + yy) * X + x;
+    rec[i] = make_float4(eh, el, binv, S);  // S is 0 outside P
+    if (a.want_grad) a.rec2[i] = make_float4(dtx, dty, dna, 0.f);
+    n_sp += (S != 0.f) ? 1 : 0;
     n_p += P ? 1 : 0;
+    s_sp += S;
+    s_tx += dtx;
+    s_ty += dty;
+    s_na += dna;
     // band limit along x: the largest |k_x| inside P on the k_y = 0 row.  P is
     // contained in nu_x^2 <= (NA_det/lambda)^2, so every column beyond it is
     // zero in every arm.
@@ -142,6 +175,10 @@ __global__ void __launch_bounds__(256)
     n_sp += __shfl_down_sync(0xffffffffu, n_sp, off);
     n_p += __shfl_down_sync(0xffffffffu, n_p, off);
     kx_band = max(kx_band, __shfl_down_sync(0xffffffffu, kx_band, off));
+    s_sp += __shfl_down_sync(0xffffffffu, s_sp, off);
+    s_tx += __shfl_down_sync(0xffffffffu, s_tx, off);
+    s_ty += __shfl_down_sync(0xffffffffu, s_ty, off);
+    s_na += __shfl_down_sync(0xffffffffu, s_na, off);
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __shared__ int band[8];
@@ -149,21 +186,40 @@ __global__ void __launch_bounds__(256)
     part[0][warp] = n_sp;
     part[1][warp] = n_p;
     band[warp] = kx_band;
+    fpart[0][warp] = s_sp;
+    fpart[1][warp] = s_tx;
+    fpart[2][warp] = s_ty;
+    fpart[3][warp] = s_na;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    int a = 0, b = 0, k = -1;
+    int ca = 0, cb = 0, k = -1;
     for (int i = 0; i < 8; ++i) {
-      a += part[0][i];
-      b += part[1][i];
+      ca += part[0][i];
+      cb += part[1][i];
       k = max(k, band[i]);
     }
-    if (a) atomicAdd(&counts[4 * t], a);
-    if (b) atomicAdd(&counts[4 * t + 1], b);
-    if (k >= 0) atomicMax(&counts[4 * t + 2], k);
+    if (ca) atomicAdd(&a.counts[4 * t], ca);
+    if (cb) atomicAdd(&a.counts[4 * t + 1], cb);
+    if (k >= 0) atomicMax(&a.counts[4 * t + 2], k);
+  }
+  // smooth source: per-block partial sums, reduced per tile in a fixed order
+  if (a.smooth && threadIdx.x < 4) {
+    float v = 0.f;
+    for (int i = 0; i < 8; ++i) v += fpart[threadIdx.x][i];
+    a.norm_part[((long long)t * a.rec_blocks + blockIdx.x) * 4 + threadIdx.x] = v;
   }
 }
 
+// Per tile: the four smooth-source sums from the record blocks' partials.
+__global__ void k_norms(const float* __restrict__ part, int blocks, int n_tiles, float* __restrict__ norms) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // tile * 4 + sum
+  if (i >= 4 * n_tiles) return;
+  const int t = i / 4, q = i % 4;
+  double v = 0.0;
+  for (int b = 0; b < blocks; ++b) v += part[((long long)t * blocks + b) * 4 + q];
+  norms[i] = (float)v;
+}
 
 template <int N>  // N = Y
 __global__ void __launch_bounds__(ColGeom<N>::NT, (1024 / ColGeom<N>::NT) > 1 ? (1024 / ColGeom<N>::NT) : 1) k_arms(TfArgs a) {
@@ -199,27 +255,37 @@ __global__ void __launch_bounds__(ColGeom<N>::NT, (1024 / ColGeom<N>::NT) > 1 ? 
 #pragma unroll
   for (int i = 0; i < PER; ++i) sincospif(2.0f * phase_frac(r[i].x, r[i].y, zh, zl), &s_[i], &c_[i]);
   // arms, in slot order: A, B (label-free), P (fluorescence), or
-  // A, B, A' = i 2 pi eta A, B' = i 2 pi eta B (phase TF and its defocus derivative)
+  // A, B, A' = i 2 pi eta A, B' = i 2 pi eta B (phase TF and its defocus
+  // derivative), then A_tx, A_ty, A_NA (derivatives in the source parameters)
   int arm = 0;
 #pragma unroll 1
-  for (int which = 0; which < 5; ++which) {
+  for (int which = 0; which < 8; ++which) {
     if (which < 2 && a.lf_props == 0) continue;
     if (which == 2 && !a.want_fl) continue;
-    if (which > 2 && !a.want_dz) continue;
+    if ((which == 3 || which == 4) && !a.want_dz) continue;
+    if (which > 4 && !a.want_grad) continue;
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
       const int e = threadIdx.x + i * NT;
       if (e >= N * B) continue;
-      // v = (al + i be) e^{i phi}: A (1, 0), B (0, 1/eta), P (1, 0),
-      // A' (0, 2 pi eta), B' (-2 pi eta / eta, 0); zero off the pupil
-      // eta is read again from the record (an L2 hit) rather than kept live
-      // across the transforms: the derivative arms are the only users
-      float tpe = 0.f;
-      if (which > 2 && (e % B) < w) tpe = 6.28318530717958648f * __ldg(&rec[(long long)(e / B) * X + e % B].x);
-      const bool on = (which == 0 || which == 3) ? (r[i].w != 0.f) : (r[i].z != 0.f);
-      float al = (which == 0 || which == 2) ? 1.f : (which == 4 ? -tpe * r[i].z : 0.f);
-      float be = which == 1 ? r[i].z : (which == 3 ? tpe : 0.f);
-      if (!on) al = be = 0.f;
+      // v = (al + i be) e^{i phi}: A (S, 0), B (0, 1/eta), P (1, 0),
+      // A' (0, 2 pi eta S), B' (-2 pi eta / eta, 0), and for the source
+      // parameters A_theta (dS/dtheta, 0); zero off the pupil.  S (the
+      // record's w) is 0 or 1 for the binary source.  eta and the source
+      // derivatives are read again from the records (L2 hits) rather than
+      // kept live across the transforms
+      float tpe = 0.f, dsv = 0.f;
+      const bool inb = (e % B) < w;
+      if ((which == 3 || which == 4) && inb)
+        tpe = 6.28318530717958648f * __ldg(&rec[(long long)(e / B) * X + e % B].x);
+      if (which > 4 && inb) {
+        const float* r2 = reinterpret_cast<const float*>(a.rec2 + (long long)t * N * X + x0 +
+                                                         (long long)(e / B) * X + e % B);
+        dsv = __ldg(r2 + (which - 5));
+      }
+      float al = which == 0 ? r[i].w : (which == 2 ? (r[i].z != 0.f ? 1.f : 0.f)
+                                        : (which == 4 ? -tpe * r[i].z : (which > 4 ? dsv : 0.f)));
+      float be = which == 1 ? r[i].z : (which == 3 ? tpe * r[i].w : 0.f);
       buf[e] = make_float2(al * c_[i] - be * s_[i], al * s_[i] + be * c_[i]);
     }
     __syncthreads();
@@ -415,12 +481,15 @@ __global__ void __launch_bounds__(ZGeom<N, NK>::NT, ZGeom<N, NK>::MINB) k_tf_zpa
 }
 
 cudaError_t tf_pupil_record(const TfArgs& a, cudaStream_t s) {
-  const long long want = ((long long)a.Y * a.n_tiles + 303) / 304;
-  const int kRecRows = (int)(want < 8 ? 8 : (want > kRecRowsMax ? kRecRowsMax : want));
+  const int kRecRows = record_rows(a.Y, a.n_tiles);
   dim3 grid((unsigned)((a.Y + kRecRows - 1) / kRecRows), (unsigned)a.n_tiles);
   const size_t smem = (size_t)a.X * sizeof(double);
   WO_LAUNCH("tf_pupil_record", s,
-            (k_pupil_record<<<grid, 256, smem, s>>>(a.optics, a.rec, a.counts, a.stats, a.Y, a.X, kRecRows)));
+            (k_pupil_record<<<grid, 256, smem, s>>>(a, kRecRows)));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !a.smooth) return e;
+  WO_LAUNCH("tf_norms", s, (k_norms<<<(unsigned)((4 * a.n_tiles + 127) / 128), 128, 0, s>>>(a.norm_part, a.rec_blocks,
+                                                                                          a.n_tiles, a.norms)));
   return cudaGetLastError();
 }
 

@@ -7,12 +7,20 @@ namespace wo {
 __device__ __forceinline__ int fft_index(int i, int n) { return (i < (n + 1) / 2) ? i : i - n; }
 
 __device__ __forceinline__ float lf_scale(const TfArgs& a, int t) {
-  // 2K = 2 c / (N_perp sum S P^2), c = 2 pi n dz / lambda^2
+  // 2K = 2 c / (N_perp sum S P^2), c = 2 pi n dz / lambda^2; the sum is a count
+  // for the binary source and a float sum for the smooth one
   const wo_optics o = a.optics[t];
-  const int n_sp = a.counts[4 * t];
-  if (n_sp == 0) return 0.f;
+  const double sp = a.smooth ? (double)a.norms[4 * t] : (double)a.counts[4 * t];
+  if (!(sp > 0.0)) return 0.f;
   const double c = 2.0 * 3.14159265358979323846 * o.n_medium * o.z_step_um / (o.lambda_um * o.lambda_um);
-  return (float)(2.0 * c / ((double)a.Y * (double)a.X * (double)n_sp));
+  return (float)(2.0 * c / ((double)a.Y * (double)a.X * sp));
+}
+
+// d log(sum S P^2) / d theta for the smooth source (theta = 0 tilt_x,
+// 1 tilt_y, 2 NA_ill): the normalisation's share of dH1/dtheta.
+__device__ __forceinline__ float norm_dlog(const TfArgs& a, int t, int theta) {
+  const float sp = a.norms[4 * t];
+  return sp > 0.f ? a.norms[4 * t + 1 + theta] / sp : 0.f;
 }
 
 __device__ __forceinline__ float fl_scale(const TfArgs& a, int t) {

@@ -30,36 +30,41 @@ constexpr int kTuneThreads = 256;
 
 __device__ __forceinline__ int freq_index(int i, int n) { return (i < (n + 1) / 2) ? i : i - n; }
 
-// Deterministic block sum of two doubles (fixed tree over kTuneThreads).
-__device__ __forceinline__ void block_sum2(double& a, double& b, double* red) {
-  red[threadIdx.x] = a;
-  red[kTuneThreads + threadIdx.x] = b;
+// Deterministic block sum of NV doubles per thread (fixed tree over
+// kTuneThreads); the sums land in red[v * kTuneThreads].
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* red) {
+#pragma unroll
+  for (int i = 0; i < NV; ++i) red[i * kTuneThreads + threadIdx.x] = v[i];
   __syncthreads();
   for (int h = kTuneThreads / 2; h > 0; h >>= 1) {
     if (threadIdx.x < h) {
-      red[threadIdx.x] += red[threadIdx.x + h];
-      red[kTuneThreads + threadIdx.x] += red[kTuneThreads + threadIdx.x + h];
+#pragma unroll
+      for (int i = 0; i < NV; ++i) red[i * kTuneThreads + threadIdx.x] += red[i * kTuneThreads + threadIdx.x + h];
     }
     __syncthreads();
   }
-  a = red[0];
-  b = red[kTuneThreads];
 }
 }  // namespace
 
 // One thread per transverse frequency (column c = y * Xh + x of the half
 // spectrum), grid (ceil(Y*Xh / 256), n_tiles).  Consecutive threads read
 // consecutive columns of every axial plane: each pass over k is coalesced.
+// The bank holds 1 + NP slots per tile: H, then dH/dtheta_p.
+template <int NP>
 __global__ void __launch_bounds__(kTuneThreads) k_tune_cols(const float2* __restrict__ tf2,
                                                             const float2* __restrict__ spec,
                                                             const wo_optics* __restrict__ optics, int Z, int Y,
                                                             int Xh, int X, float eta, float nu_max, int zf,
                                                             int loss, double* __restrict__ partials) {
-  __shared__ double red[2 * kTuneThreads];
+  __shared__ double red[(1 + NP) * kTuneThreads];
   const int t = blockIdx.y;
   const long long plane = (long long)Y * Xh;
+  const long long vol = (long long)Z * plane;
   const long long c = (long long)blockIdx.x * kTuneThreads + threadIdx.x;
-  double val = 0.0, grad = 0.0;
+  double acc[1 + NP];  // value, then the derivatives
+#pragma unroll
+  for (int i = 0; i <= NP; ++i) acc[i] = 0.0;
   bool on = c < plane;
   int x = 0;
   if (on) {
@@ -75,36 +80,40 @@ __global__ void __launch_bounds__(kTuneThreads) k_tune_cols(const float2* __rest
       on = fx * fx + fy * fy <= (double)nu_max * (double)nu_max;
     }
   }
+  const double w = (x == 0 || 2 * x == X) ? 1.0 : 2.0;
+  const float2* D = spec + (long long)t * vol + c;
+  const float2* H = tf2 + (long long)t * (1 + NP) * vol + c;
   if (on && loss == WO_LOSS_MIDBAND) {
-    // -|F|^2 and its derivative through the solve: dF = (dc - F dh) / den
-    const float2* D = spec + (long long)t * Z * plane + c;
-    const float2* H = tf2 + (long long)t * 2 * Z * plane + c;
-    const float2* dH = H + (long long)Z * plane;
-    float cr = 0.f, ci = 0.f, hh = 0.f, dcr = 0.f, dci = 0.f, dhr = 0.f;
-#pragma unroll 8
+    // -|F|^2 and its derivatives through the solve: dF_p = (dc_p - F dh_p) / den
+    float cr = 0.f, ci = 0.f, hh = 0.f, dcr[NP], dci[NP], dhr[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) dcr[q] = dci[q] = dhr[q] = 0.f;
+#pragma unroll 4
     for (int k = 0; k < Z; ++k) {
-      const float2 d = __ldg(D + k * plane), h = __ldg(H + k * plane), dh = __ldg(dH + k * plane);
-      const float2 r = cmulc(h, d), q = cmulc(dh, d);
+      const float2 d = __ldg(D + k * plane), h = __ldg(H + k * plane);
+      const float2 r = cmulc(h, d);
       cr += r.x;
       ci += r.y;
-      dcr += q.x;
-      dci += q.y;
       hh += cabs2(h);
-      dhr += h.x * dh.x + h.y * dh.y;
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        const float2 dh = __ldg(H + (q + 1) * vol + k * plane);
+        const float2 e = cmulc(dh, d);
+        dcr[q] += e.x;
+        dci[q] += e.y;
+        dhr[q] += h.x * dh.x + h.y * dh.y;
+      }
     }
     const float den = hh + (float)zf * eta;
     const float inv = den > 0.f ? 1.0f / den : 0.f;
     const float2 F = make_float2(cr * inv, ci * inv);
-    const float2 dF = make_float2((dcr - 2.f * dhr * F.x) * inv, (dci - 2.f * dhr * F.y) * inv);
-    const double w = (x == 0 || 2 * x == X) ? 1.0 : 2.0;
-    val = -w * (double)cabs2(F);
-    grad = -w * 2.0 * ((double)F.x * dF.x + (double)F.y * dF.y);
-    on = false;
-  }
-  if (on) {
-    const float2* D = spec + (long long)t * Z * plane + c;
-    const float2* H = tf2 + (long long)t * 2 * Z * plane + c;
-    const float2* dH = H + (long long)Z * plane;
+    acc[0] = -w * (double)cabs2(F);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const float2 dF = make_float2((dcr[q] - 2.f * dhr[q] * F.x) * inv, (dci[q] - 2.f * dhr[q] * F.y) * inv);
+      acc[1 + q] = -w * 2.0 * ((double)F.x * dF.x + (double)F.y * dF.y);
+    }
+  } else if (on) {
     float cr = 0.f, ci = 0.f, hh = 0.f;
 #pragma unroll 8
     for (int k = 0; k < Z; ++k) {
@@ -117,67 +126,70 @@ __global__ void __launch_bounds__(kTuneThreads) k_tune_cols(const float2* __rest
     const float den = hh + (float)zf * eta;
     const float inv = den > 0.f ? 1.0f / den : 0.f;
     const float2 F = make_float2(cr * inv, ci * inv);
-    float rr = 0.f, gg = 0.f;
-#pragma unroll 8
+    float rr = 0.f, gg[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) gg[q] = 0.f;
+#pragma unroll 4
     for (int k = 0; k < Z; ++k) {
-      const float2 d = __ldg(D + k * plane), h = __ldg(H + k * plane), dh = __ldg(dH + k * plane);
+      const float2 d = __ldg(D + k * plane), h = __ldg(H + k * plane);
       const float2 R = csub(d, cmul(h, F));
-      const float2 q = cmul(dh, F);
       rr += cabs2(R);
-      gg += q.x * R.x + q.y * R.y;  // Re(conj(q) R)
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        const float2 e = cmul(__ldg(H + (q + 1) * vol + k * plane), F);
+        gg[q] += e.x * R.x + e.y * R.y;  // Re(conj(dH F) R)
+      }
     }
-    const double w = (x == 0 || 2 * x == X) ? 1.0 : 2.0;
-    val = w * ((double)rr + (double)zf * (double)eta * (double)cabs2(F));
-    grad = w * (-2.0 * (double)gg);
+    acc[0] = w * ((double)rr + (double)zf * (double)eta * (double)cabs2(F));
+#pragma unroll
+    for (int q = 0; q < NP; ++q) acc[1 + q] = w * (-2.0 * (double)gg[q]);
   }
-  block_sum2(val, grad, red);
-  if (threadIdx.x == 0) {
-    double* p = partials + ((long long)t * gridDim.x + blockIdx.x) * 2;
-    p[0] = val;
-    p[1] = grad;
-  }
+  block_sum<1 + NP>(acc, red);
+  if (threadIdx.x <= NP) partials[((long long)t * gridDim.x + blockIdx.x) * (1 + NP) + threadIdx.x] =
+      red[threadIdx.x * kTuneThreads];
 }
 
 // One warp per tile: the tile's partials in a fixed order, then the scale.
-__global__ void k_tune_final(const double* __restrict__ partials, int nblk, double scale,
+__global__ void k_tune_final(const double* __restrict__ partials, int nblk, int np, double scale,
                              double* __restrict__ value, double* __restrict__ grad) {
   const int t = blockIdx.x, lane = threadIdx.x;
-  double v = 0.0, g = 0.0;
-  for (int i = lane; i < nblk; i += 32) {
-    v += partials[((long long)t * nblk + i) * 2];
-    g += partials[((long long)t * nblk + i) * 2 + 1];
-  }
-  for (int off = 16; off > 0; off >>= 1) {
-    v += __shfl_down_sync(0xffffffffu, v, off);
-    g += __shfl_down_sync(0xffffffffu, g, off);
-  }
-  if (lane == 0) {
-    if (value) value[t] = v * scale;
-    if (grad) grad[t] = g * scale;
+  for (int q = 0; q <= np; ++q) {
+    double v = 0.0;
+    for (int i = lane; i < nblk; i += 32) v += partials[((long long)t * nblk + i) * (1 + np) + q];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) {
+      if (q == 0 && value) value[t] = v * scale;
+      if (q > 0 && grad) grad[(long long)t * np + q - 1] = v * scale;
+    }
   }
 }
 
 cudaError_t tune_reduce(const float2* tf2, const float2* spec, const wo_optics* optics, int n_tiles, int Z,
-                        int Y, int X, float eta, float nu_max, int zf, int loss, double* partials, double* value,
-                        double* grad, cudaStream_t s) {
+                        int Y, int X, float eta, float nu_max, int zf, int loss, int np, double* partials,
+                        double* value, double* grad, cudaStream_t s) {
   const int Xh = X / 2 + 1;
   const long long plane = (long long)Y * Xh;
   const unsigned nblk = (unsigned)((plane + kTuneThreads - 1) / kTuneThreads);
   dim3 grid(nblk, (unsigned)n_tiles);
-  WO_LAUNCH("tune_cols", s,
-            (k_tune_cols<<<grid, kTuneThreads, 0, s>>>(tf2, spec, optics, Z, Y, Xh, X, eta, nu_max, zf, loss,
-                                                         partials)));
+  if (np == 4) {
+    WO_LAUNCH("tune_cols", s, (k_tune_cols<4><<<grid, kTuneThreads, 0, s>>>(tf2, spec, optics, Z, Y, Xh, X, eta,
+                                                                           nu_max, zf, loss, partials)));
+  } else {
+    WO_LAUNCH("tune_cols", s, (k_tune_cols<1><<<grid, kTuneThreads, 0, s>>>(tf2, spec, optics, Z, Y, Xh, X, eta,
+                                                                           nu_max, zf, loss, partials)));
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // F is the same in both forms; the residual sums carry the Parseval factor zf
   const double scale = 1.0 / ((double)X * (double)Y * (loss == WO_LOSS_MIDBAND ? 1.0 : (double)zf));
-  WO_LAUNCH("tune_final", s, (k_tune_final<<<(unsigned)n_tiles, 32, 0, s>>>(partials, (int)nblk, scale, value, grad)));
+  WO_LAUNCH("tune_final", s, (k_tune_final<<<(unsigned)n_tiles, 32, 0, s>>>(partials, (int)nblk, np, scale, value,
+                                                                             grad)));
   return cudaGetLastError();
 }
 
-size_t tune_partials_bytes(int n_tiles, int Y, int X) {
+size_t tune_partials_bytes(int n_tiles, int Y, int X, int np) {
   const long long plane = (long long)Y * (X / 2 + 1);
-  return (size_t)n_tiles * (size_t)((plane + kTuneThreads - 1) / kTuneThreads) * 2 * sizeof(double);
+  return (size_t)n_tiles * (size_t)((plane + kTuneThreads - 1) / kTuneThreads) * (1 + np) * sizeof(double);
 }
 
 __global__ void k_zero_dc(float2* spec, int n_tiles, long long vol) {
@@ -216,31 +228,43 @@ cudaError_t center_dc_planes(float2* spec, int n_tiles, int Z, long long plane, 
   return cudaGetLastError();
 }
 
-// Adam (Kingma and Ba, 2015) on each tile's defocus, with the moments and the
-// step count kept in device memory: state[t] = {m, v, steps}.
-__global__ void k_adam_defocus(wo_optics* __restrict__ optics, const double* __restrict__ grad,
-                               double* __restrict__ state, int n_tiles, double lr, double b1, double b2,
-                               double eps) {
+// Adam (Kingma and Ba, 2015) on each tile's tuned optics parameters, in the
+// order defocus_um, tilt_x, tilt_y, na_ill (the first np of them), with the
+// moments and the step count kept in device memory: state[t][p] = {m, v, s}.
+// NA_ill is kept inside [0.01, n_medium - |tilt| - 1e-3] after each step (a
+// projection onto physically valid illumination).
+__global__ void k_adam_optics(wo_optics* __restrict__ optics, const double* __restrict__ grad, int np,
+                              double* __restrict__ state, int n_tiles, AdamLr lr, double b1, double b2,
+                              double eps) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_tiles) return;
-  double* st = state + 3LL * t;
-  const double g = grad[t];
-  const double m = b1 * st[0] + (1.0 - b1) * g;
-  const double v = b2 * st[1] + (1.0 - b2) * g * g;
-  const double n = st[2] + 1.0;
-  st[0] = m;
-  st[1] = v;
-  st[2] = n;
-  const double mh = m / (1.0 - pow(b1, n));
-  const double vh = v / (1.0 - pow(b2, n));
-  optics[t].defocus_um -= lr * mh / (sqrt(vh) + eps);
+  wo_optics o = optics[t];
+  double* par[4] = {&o.defocus_um, &o.tilt_x, &o.tilt_y, &o.na_ill};
+  for (int p = 0; p < np; ++p) {
+    double* st = state + (3LL * np) * t + 3 * p;
+    const double g = grad[(long long)t * np + p];
+    const double m = b1 * st[0] + (1.0 - b1) * g;
+    const double v = b2 * st[1] + (1.0 - b2) * g * g;
+    const double n = st[2] + 1.0;
+    st[0] = m;
+    st[1] = v;
+    st[2] = n;
+    const double mh = m / (1.0 - pow(b1, n));
+    const double vh = v / (1.0 - pow(b2, n));
+    *par[p] -= lr.v[p] * mh / (sqrt(vh) + eps);
+  }
+  if (np > 3) {
+    const double tilt = sqrt(o.tilt_x * o.tilt_x + o.tilt_y * o.tilt_y);
+    o.na_ill = fmin(fmax(o.na_ill, 0.01), o.n_medium - tilt - 1e-3);
+  }
+  optics[t] = o;
 }
 
-cudaError_t adam_defocus(wo_optics* optics, const double* grad, double* state, int n_tiles, double lr,
-                         double b1, double b2, double eps, cudaStream_t s) {
-  WO_LAUNCH("adam_defocus", s,
-            (k_adam_defocus<<<(unsigned)((n_tiles + 127) / 128), 128, 0, s>>>(optics, grad, state, n_tiles, lr, b1,
-                                                                               b2, eps)));
+cudaError_t adam_optics(wo_optics* optics, const double* grad, int np, double* state, int n_tiles, AdamLr lr,
+                        double b1, double b2, double eps, cudaStream_t s) {
+  WO_LAUNCH("adam_optics", s,
+            (k_adam_optics<<<(unsigned)((n_tiles + 127) / 128), 128, 0, s>>>(optics, grad, np, state, n_tiles, lr,
+                                                                              b1, b2, eps)));
   return cudaGetLastError();
 }
 

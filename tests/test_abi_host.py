@@ -110,7 +110,7 @@ def test_tuning_validation(B):
     fake = 1 << 20
     big = 1 << 40
     d = ctypes.c_double
-    obj = lib.wo_defocus_objective
+    obj = lib.wo_tune_objective
     K = 8  # WO_TF_PHASE_DZ
     assert obj(fake, K, fake, fake, 0, 1e-3, 0.0, None, None, 1, 16, 64, 64, fake, big, None) == 1  # no output
     assert obj(fake, K, fake, fake, 0, -1.0, 0.0, fake, fake, 1, 16, 64, 64, fake, big, None) == 1  # eta < 0
@@ -124,13 +124,18 @@ def test_tuning_validation(B):
     assert obj(fake, 1, fake, fake, 0, 1e-3, 0.0, fake, fake, 1, 16, 64, 64, fake, big, None) == 1  # not a dz bank
     assert obj(fake, 16, fake, fake, 0, 1e-3, 0.0, fake, fake, 1, 16, 64, 64, fake, big, None) == 1
     assert obj(fake, K, fake, fake, 2, 1e-3, 0.0, fake, fake, 1, 16, 64, 64, fake, big, None) == 1  # bad loss
-    adam = lib.wo_adam_defocus
-    assert adam(fake, fake, fake, 0, d(0.02), d(0.9), d(0.999), d(1e-8), None) == 1
-    assert adam(fake, fake, fake, 4, d(-0.02), d(0.9), d(0.999), d(1e-8), None) == 1
-    assert adam(fake, fake, fake, 4, d(0.02), d(1.0), d(0.999), d(1e-8), None) == 1
-    assert adam(fake, fake, fake, 4, d(0.02), d(0.9), d(0.999), d(0.0), None) == 1
-    assert adam(None, fake, fake, 4, d(0.02), d(0.9), d(0.999), d(1e-8), None) == 1
-    assert adam(fake, fake, fake + 4, 4, d(0.02), d(0.9), d(0.999), d(1e-8), None) == 1
+    adam = lib.wo_adam_optics
+    lr1 = (ctypes.c_double * 1)(0.02)
+    lr4 = (ctypes.c_double * 4)(0.02, 0.005, 0.005, 0.005)
+    neg = (ctypes.c_double * 4)(0.02, -0.005, 0.005, 0.005)
+    assert adam(fake, fake, 1, fake, 0, lr1, d(0.9), d(0.999), d(1e-8), None) == 1      # no tiles
+    assert adam(fake, fake, 2, fake, 4, lr4, d(0.9), d(0.999), d(1e-8), None) == 1      # 2 parameters
+    assert adam(fake, fake, 4, fake, 4, neg, d(0.9), d(0.999), d(1e-8), None) == 1      # lr < 0
+    assert adam(fake, fake, 1, fake, 4, lr1, d(1.0), d(0.999), d(1e-8), None) == 1      # beta1 = 1
+    assert adam(fake, fake, 1, fake, 4, lr1, d(0.9), d(0.999), d(0.0), None) == 1       # eps = 0
+    assert adam(None, fake, 1, fake, 4, lr1, d(0.9), d(0.999), d(1e-8), None) == 1
+    assert adam(fake, fake, 1, fake + 4, 4, lr1, d(0.9), d(0.999), d(1e-8), None) == 1
+    assert adam(fake, fake, 4, fake, 4, None, d(0.9), d(0.999), d(1e-8), None) == 1
     spec = lib.wo_spectrum
     assert spec(fake, None, 0, fake, 1, 16, 64, 63, None) == 2
     assert spec(fake, None, 0, fake, 1, 10, 64, 64, None) == 3
@@ -141,6 +146,15 @@ def test_tuning_validation(B):
     assert B.wo_tf_bytes(1, 16, 64, 64, 16) == 0 and B.wo_tf_bytes(1, 16, 64, 64, 17) == 0
     assert B.wo_tf_bytes(1, 16, 64, 64, 24) == B.wo_tf_bytes(1, 16, 64, 64, 8)
     assert lib.wo_forward(fake, 24, fake, None, fake, 1, 16, 64, 64, fake, big, None) == 1
+    # the gradient bank: per plane only, five slots, register row pass lengths only
+    assert B.wo_tf_bytes(1, 16, 64, 64, 64) == 0                 # needs WO_TF_PLANES
+    assert B.wo_tf_bytes(1, 16, 64, 64, 64 | 16) == ((5 * 16 * 64 * 33 * 8 + 255) // 256) * 256 + 32
+    assert B.wo_tf_bytes(1, 16, 64, 64, 64 | 16 | 32) == B.wo_tf_bytes(1, 16, 64, 64, 64 | 16)
+    assert B.wo_tf_bytes(1, 16, 64, 96, 64 | 16) == 0            # 96-point rows: no gradient bank
+    assert B.wo_tf_bytes(1, 16, 64, 64, 64 | 8 | 16) == 0        # two derivative banks at once
+    assert B.wo_tf_bytes(1, 16, 64, 64, 4 | 32) == 0             # smooth source without label-free kinds
+    assert B.wo_tf_bytes(1, 16, 64, 64, 1 | 32) == B.wo_tf_bytes(1, 16, 64, 64, 1)
+    assert obj(fake, 64 | 16, fake, fake, 0, 1e-3, 0.0, fake, fake, 1, 16, 64, 64, fake, 16, None) == 8
 
 
 def test_schedule_table(B):

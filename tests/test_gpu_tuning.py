@@ -122,7 +122,7 @@ def problem(env, ol_true, start, eta, seed=11, planes=True):
     B, A, torch, dev = env
     d = np.stack([thin_stack(o, SHAPE, seed + 17 * t) for t, o in enumerate(ol_true)])
     data = torch.tensor(d, dtype=torch.float32, device=dev)
-    return A.DefocusProblem(data, start, eta, planes=planes), d
+    return A.TuningProblem(data, start, eta, planes=planes), d
 
 
 def cutoff(o):
@@ -144,7 +144,7 @@ def test_loss_and_gradient_match_the_oracle_on_eight_tiles(env, band, planes):
     nu = 0.0 if band is None else band * cutoff(ol[0]) + 1e-3  # off the frequency grid
     pb.evaluate(nu)
     torch.cuda.synchronize()
-    val, grad = pb.value.cpu().numpy(), pb.grad.cpu().numpy()
+    val, grad = pb.value.cpu().numpy(), pb.grad[:, 0].cpu().numpy()
     for t in range(8):
         nm = None if band is None else nu
         want = OT.objective(start[t], d[t], eta, nm)
@@ -163,10 +163,10 @@ def test_midband_loss_and_gradient_match_the_oracle(env, planes):
     eta = 1e-3
     _, d = problem(env, ol, start, eta, seed=90)
     data = torch.tensor(d, dtype=torch.float32, device=dev)
-    pb = A.DefocusProblem(data, start, eta, planes=planes, loss=B.WO_LOSS_MIDBAND)
+    pb = A.TuningProblem(data, start, eta, planes=planes, loss=B.WO_LOSS_MIDBAND)
     pb.evaluate()
     torch.cuda.synchronize()
-    val, grad = pb.value.cpu().numpy(), pb.grad.cpu().numpy()
+    val, grad = pb.value.cpu().numpy(), pb.grad[:, 0].cpu().numpy()
     for t in range(len(ol)):
         want = OT.midband_objective(start[t], d[t], eta)
         gwant = OT.midband_gradient_fd(start[t], d[t], eta, h=1e-4)
@@ -180,7 +180,7 @@ def test_gradient_matches_central_difference_of_the_gpu_loss(env):
     start = [dict(o, defocus_um=o["defocus_um"] + (0.2 if t % 2 else -0.25)) for t, o in enumerate(ol)]
     pb, _ = problem(env, ol, start, 1e-3, seed=40)
     pb.evaluate()
-    g = pb.grad.clone()
+    g = pb.grad[:, 0].clone()
     h = 1e-3
     z0 = pb.defocus.clone()
     vals = []
@@ -198,14 +198,14 @@ def test_autograd_function_returns_the_adjoint_gradient(env):
     ol = tiles(4, 23)
     start = [dict(o, defocus_um=o["defocus_um"] - 0.2) for o in ol]
     pb, d = problem(env, ol, start, 1e-3, seed=60)
-    z = torch.tensor([o["defocus_um"] for o in start], dtype=torch.float64, device=dev, requires_grad=True)
+    z = torch.tensor([[o["defocus_um"]] for o in start], dtype=torch.float64, device=dev, requires_grad=True)
     w = torch.tensor([1.0, -2.0, 0.5, 3.0], dtype=torch.float64, device=dev)
-    loss = (A.defocus_loss(z, pb) * w).sum()
+    loss = (A.tune_loss(z, pb) * w).sum()
     loss.backward()
     pb.evaluate()
-    assert torch.allclose(z.grad, w * pb.grad, rtol=0, atol=0)
+    assert torch.allclose(z.grad, w[:, None] * pb.grad, rtol=0, atol=0)
     want = sum(float(w[t]) * OT.objective(start[t], d[t], 1e-3) for t in range(4))
-    assert abs(float(loss) - want) <= 1e-4 * abs(want)
+    assert abs(float(loss.detach()) - want) <= 1e-4 * abs(want)
 
 
 def test_adam_reaches_the_true_defocus_under_a_cuda_graph(env):
@@ -233,3 +233,68 @@ def test_adam_reaches_the_true_defocus_under_a_cuda_graph(env):
     pb.run(schedule, graph=True)
     torch.cuda.synchronize()
     assert np.array_equal(pb.defocus.cpu().numpy(), z_graph)
+
+
+# ------------------------------------------------ smooth source, four parameters
+def smooth_tiles(n, seed):
+    return [dict(o, smooth_source=True) for o in tiles(n, seed)]
+
+
+def test_smooth_source_bank_matches_oracle(env):
+    B, _, torch, dev = env
+    shape = (8, 32, 48)
+    Z, Y, X = shape
+    ol = smooth_tiles(3, 41)
+    kinds = B.WO_TF_PHASE | B.WO_TF_ABSORPTION | B.WO_TF_SMOOTH_SOURCE
+    tf, ws = B.alloc(3, Z, Y, X, kinds, dev)
+    B.wo_build_tf(ol, 3, Z, Y, X, kinds, tf, ws)
+    spec = B.tf_views(tf, 3, Z, Y, X, kinds)[0].cpu().numpy()
+    for t, o in enumerate(ol):
+        ref = OO.transfer_functions(o, shape, ("phase", "absorption"))
+        den = np.sqrt(sum(np.linalg.norm(OO.half_spectrum(ref[k])) ** 2 for k in ref))
+        for s_, k in enumerate(("phase", "absorption")):
+            assert np.linalg.norm(spec[t, s_] - OO.half_spectrum(ref[k])) / den <= 1e-4, (t, k)
+
+
+@pytest.mark.parametrize("shape", [(8, 32, 48), (6, 64, 64), (4, 24, 128)])
+def test_gradient_bank_matches_oracle(env, shape):
+    """The five per-plane slots: H, dH/d(defocus, tilt_x, tilt_y, NA_ill)."""
+    B, _, torch, dev = env
+    Z, Y, X = shape
+    ol = smooth_tiles(3, 42)
+    kinds = B.WO_TF_PHASE_GRAD | B.WO_TF_PLANES
+    tf, ws = B.alloc(3, Z, Y, X, kinds, dev)
+    B.wo_build_tf(ol, 3, Z, Y, X, kinds, tf, ws)
+    spec = B.tf_views(tf, 3, Z, Y, X, kinds)[0].cpu().numpy()
+    for t, o in enumerate(ol):
+        refs = [OO.plane_tfs(o, shape, ("phase",))["phase"], OT.plane_tf_defocus_derivative(o, shape)]
+        src = OT.plane_tf_source_derivatives(o, shape)
+        refs += [src["tilt_x"], src["tilt_y"], src["na_ill"]]
+        for q, ref in enumerate(refs):
+            assert rel_l2(spec[t, q], OO.half_spectrum(ref)) <= 1e-4, (t, q)
+
+
+@pytest.mark.parametrize("loss", [0, 1])
+def test_four_parameter_gradient_matches_oracle(env, loss):
+    """Loss and its gradient in (defocus, tilt_x, tilt_y, NA_ill) against the
+    oracle's loss and central differences, data from the smooth-source model."""
+    B, A, torch, dev = env
+    ol = smooth_tiles(4, 43)
+    offs = [(0.15, 0.02, -0.03, 0.05), (-0.12, -0.04, 0.02, -0.06), (0.1, 0.03, 0.03, 0.04),
+            (-0.18, -0.02, -0.04, -0.05)]
+    start = [dict(o, defocus_um=o["defocus_um"] + a, tilt_x=o["tilt_x"] + b, tilt_y=o["tilt_y"] + c,
+                  na_ill=o["na_ill"] + e) for o, (a, b, c, e) in zip(ol, offs)]
+    eta = 1e-3
+    d = np.stack([thin_stack(o, SHAPE, 70 + 17 * t) for t, o in enumerate(ol)])
+    data = torch.tensor(d, dtype=torch.float32, device=dev)
+    pb = A.TuningProblem(data, start, eta, params="all", loss=loss)
+    pb.evaluate()
+    torch.cuda.synchronize()
+    val, grad = pb.value.cpu().numpy(), pb.grad.cpu().numpy()
+    name = "data" if loss == 0 else "midband"
+    for t in range(len(ol)):
+        want = (OT.objective if loss == 0 else OT.midband_objective)(start[t], d[t], eta)
+        gwant = OT.gradient_fd_params(start[t], d[t], eta, h=1e-4, loss=name)
+        assert abs(val[t] - want) <= 1e-4 * abs(want), (t, val[t], want)
+        scale = np.linalg.norm(gwant)
+        assert np.all(np.abs(grad[t] - gwant) <= 1e-3 * np.abs(gwant) + 1e-4 * scale), (t, grad[t], gwant)
