@@ -573,25 +573,33 @@ def run_tiles(args, rank, world, local_rank):
 TUNE_TILES = 256
 TUNE_SHAPE = (48, 128, 128)
 TUNE_ETA = 1e-3
-TUNE_WORKLOAD = ("defocus auto-tuning, 256 tiles of 48x128x128, per-tile optics: 50 Adam steps per tile from "
-                 "defocus 0 (25 on the loss band-limited to 0.12 NA_det/lambda, lr 0.08->0.02 um; 25 on the full "
-                 "loss with fresh moments, lr 0.02->0 um); each step = per-plane TF pair build (phase TF + d/d "
-                 "defocus) + 2D thin-object loss and adjoint + Adam, one CUDA graph")
+TUNE_WORKLOAD = {
+    "all": ("auto-tuning of (defocus, tilt_x, tilt_y, NA_ill), 256 tiles of 48x128x128 with their own optics, "
+            "smooth-edged source pupil: 50 Adam steps per tile from nominal (defocus 0, no tilt, NA_ill 0.825; 25 "
+            "on the loss band-limited to 0.12 NA_det/lambda, 25 on the full loss with fresh moments); each step = "
+            "per-plane build of the phase TF and its 4 derivatives + 2D thin-object loss and adjoint + Adam, one "
+            "CUDA graph"),
+    "defocus": ("defocus auto-tuning, 256 tiles of 48x128x128, per-tile optics: 50 Adam steps per tile from "
+                "defocus 0 (25 on the loss band-limited to 0.12 NA_det/lambda, lr 0.08->0.02 um; 25 on the full "
+                "loss with fresh moments, lr 0.02->0 um); each step = per-plane TF pair build (phase TF + d/d "
+                "defocus) + 2D thin-object loss and adjoint + Adam, one CUDA graph")}
 
 
-def tune_algorithmic_bytes(o, n):
+def tune_algorithmic_bytes(o, n, n_params):
     """Compulsory HBM bytes per launch of each kernel family of one Adam step
-    over n tiles (phase TF + derivative: 4 arms, 2 per-plane TF slots, no z
-    transform)."""
+    over n tiles: 4 arms and 2 per-plane TF slots for the defocus alone, 7
+    arms and 5 slots for the four parameters (no z transform)."""
     Z, Y, X = TUNE_SHAPE
     half = Z * Y * (X // 2 + 1) * 8
-    arms = 4 * Z * Y * band_columns(o, X) * 8
+    n_arms, n_slots = (4, 2) if n_params == 1 else (7, 5)
+    arms = n_arms * Z * Y * band_columns(o, X) * 8
     return {k: n * v for k, v in {
-        "tf_pupil_record": Y * X * 16, "tf_arms": arms, "tf_psf_rows": arms + 2 * half,
-        "tf_ypass": 4 * half, "tune_cols": 3 * half}.items()}
+        "tf_pupil_record": Y * X * (16 if n_params == 1 else 32), "tf_arms": arms,
+        "tf_psf_rows": arms + n_slots * half, "tf_ypass": 2 * n_slots * half,
+        "tune_cols": (1 + n_slots) * half}.items()}
 
 
-def make_tune_data(o_list, dev, seed=5):
+def make_tune_data(o_list, dev, seed=5, smooth=False):
     """Thin specimens (projected spheres) imaged at each tile's true optics by
     the 2D model: the 3D forward model of an object held in plane 0 alone
     (its z-DFT is flat, so plane j sees H_j of that plane), + 1e-3 noise."""
@@ -604,10 +612,11 @@ def make_tune_data(o_list, dev, seed=5):
     for t in range(n):
         f[t, 0] = torch.from_numpy(ph.thin_phantom(seed * 100003 + t, (Y, X), o_list[t], n_spheres=20)
                                    .astype(np.float32)).to(dev)
-    tf, ws = B.alloc(n, Z, Y, X, ("phase",), dev)
-    B.wo_build_tf(o_list, n, Z, Y, X, ("phase",), tf, ws)
+    kinds = B.WO_TF_PHASE | (B.WO_TF_SMOOTH_SOURCE if smooth else 0)
+    tf, ws = B.alloc(n, Z, Y, X, kinds, dev)
+    B.wo_build_tf(o_list, n, Z, Y, X, kinds, tf, ws)
     data = torch.empty_like(f)
-    B.wo_forward(tf, ("phase",), f, [1.0], data, n, Z, Y, X, ws)
+    B.wo_forward(tf, kinds, f, [1.0], data, n, Z, Y, X, ws)
     g = torch.Generator(device=dev)
     g.manual_seed(seed)
     data += 1e-3 * torch.randn(data.shape, generator=g, device=dev, dtype=torch.float32)
@@ -617,29 +626,44 @@ def make_tune_data(o_list, dev, seed=5):
     return data
 
 
-def tune_cpu_baseline(o, d, schedule):
-    """The oracle tuning one tile: the same 50 Adam steps, each with the
-    oracle's loss at z +/- 1e-4 (a central difference: the oracle has no
-    adjoint)."""
+def tune_cpu_baseline(o, start, d, schedule, params, max_steps=8):
+    """The oracle tuning one tile: the first `max_steps` of the same Adam
+    schedule, each with the oracle's loss at theta +/- 1e-4 per parameter
+    (central differences: the oracle has no adjoint); the time is scaled to
+    the whole schedule."""
     from oracle import tuning as OT
+    keys = OT.PARAMS[: len(params)]
+    total = sum(ph_.steps for ph_ in schedule)
+    done = 0
     t0 = time.perf_counter()
-    z, m, v, k = 0.0, 0.0, 0.0, 0
+    th = np.array([start[k] for k in keys])
+    m = np.zeros_like(th)
+    v = np.zeros_like(th)
+    k = 0
     for ph_ in schedule:
         if ph_.reset:
-            m, v, k = 0.0, 0.0, 0
+            m[:], v[:], k = 0.0, 0.0, 0
         for i in range(ph_.steps):
-            lr = ph_.lr_at(i)
-            nu = ph_.nu_max
-            g = OT.gradient_fd(dict(o, defocus_um=z), d, TUNE_ETA, h=1e-4, nu_max=nu if nu > 0 else None)
+            if done >= max_steps:
+                break
+            done += 1
+            lr = np.array(ph_.lr_at(i), dtype=float).reshape(-1)
+            nu = ph_.nu_max if ph_.nu_max > 0 else None
+            cur = dict(start, **dict(zip(keys, th)))
+            g = np.zeros_like(th)
+            for q, key in enumerate(keys):
+                g[q] = (OT.objective(dict(cur, **{key: cur[key] + 1e-4}), d, TUNE_ETA, nu)
+                        - OT.objective(dict(cur, **{key: cur[key] - 1e-4}), d, TUNE_ETA, nu)) / 2e-4
             k += 1
             m = 0.9 * m + 0.1 * g
             v = 0.999 * v + 0.001 * g * g
-            z -= lr * (m / (1 - 0.9 ** k)) / (np.sqrt(v / (1 - 0.999 ** k)) + 1e-8)
-    dt = time.perf_counter() - t0
+            th = th - lr * (m / (1 - 0.9 ** k)) / (np.sqrt(v / (1 - 0.999 ** k)) + 1e-8)
+    dt = (time.perf_counter() - t0) * total / max(done, 1)
     return {"value": 1.0 / dt, "unit": "tiles/s", "cores": 1, "kind": "oracle",
-            "sample": f"numpy float64 oracle tuning 1 of the 256 tiles (48x128x128), the same 50-step Adam "
-                      f"schedule with central-difference gradients, {dt:.1f} s, single thread",
-            "defocus_error_um": abs(z - o["defocus_um"])}
+            "sample": f"numpy float64 oracle tuning 1 of the 256 tiles (48x128x128): the first {done} of the "
+                      f"{total} Adam steps of the same schedule with central-difference gradients "
+                      f"({2 * len(keys)} loss evaluations per step), timed and scaled to {total} steps "
+                      f"({dt:.1f} s per tile), single thread"}
 
 
 def autotune_leg(args, rank, world, local_rank, with_cpu=True):
@@ -651,12 +675,17 @@ def autotune_leg(args, rank, world, local_rank, with_cpu=True):
     dev = torch.device("cuda", local_rank)
     n = args.tune_tiles
     Z, Y, X = TUNE_SHAPE
+    four = args.tune_params == "all"
     truth = ph.tile_optics(np.random.default_rng(7 + rank), n)
-    start = [dict(o, defocus_um=0.0) for o in truth]
-    data = make_tune_data(truth, dev, seed=5 + rank)
-    pb = A.TuningProblem(data, start, TUNE_ETA)
+    if four:
+        truth = [dict(o, smooth_source=True) for o in truth]
+        start = [dict(o, defocus_um=0.0, tilt_x=0.0, tilt_y=0.0, na_ill=0.825) for o in truth]
+    else:
+        start = [dict(o, defocus_um=0.0) for o in truth]
+    data = make_tune_data(truth, dev, seed=5 + rank, smooth=four)
+    pb = A.TuningProblem(data, start, TUNE_ETA, params=args.tune_params)
     B.wo_autotune(n, Z, Y, X, pb.kinds, pb.ws)  # the workspace is scratch between calls
-    sched = A.default_schedule(truth[0])
+    sched = A.default_schedule4(truth[0]) if four else A.default_schedule(truth[0])
     n_adam = sum(p.steps for p in sched)
     # per-kernel times of one eager Adam step on the full loss
     B.wo_profile_read()
@@ -686,7 +715,9 @@ def autotune_leg(args, rank, world, local_rank, with_cpu=True):
         ev1.record(stream)
         torch.cuda.synchronize()
     ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, device=dev)
-    err = np.abs(pb.defocus.cpu().numpy() - np.array([o["defocus_um"] for o in truth]))
+    keys = ("defocus_um", "tilt_x", "tilt_y", "na_ill")[: pb.n_params]
+    errs = np.abs(pb.params().cpu().numpy() - np.array([[o[k] for k in keys] for o in truth]))
+    err = errs[:, 0]
     # end to end: host stacks in (pinned), tuned defocus out
     h_in = torch.empty(data.shape, dtype=torch.float32, pin_memory=True)
     h_in.copy_(data.cpu())
@@ -709,7 +740,7 @@ def autotune_leg(args, rank, world, local_rank, with_cpu=True):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, device=dev)
-    algo = tune_algorithmic_bytes(truth[0], n)
+    algo = tune_algorithmic_bytes(truth[0], n, pb.n_params)
     tot = sum(v[1] for v in prof.values())
     kern = {}
     for name, (cnt, t) in prof.items():
@@ -720,10 +751,11 @@ def autotune_leg(args, rank, world, local_rank, with_cpu=True):
     peak, peak_kind = peaks()
     out = {
         "value": round(job_throughput(n, world, ms), 2), "unit": "tiles/s", "ms_per_step": round(ms, 3),
-        "workload": TUNE_WORKLOAD if n == TUNE_TILES else f"profiling case: {n} tiles",
+        "workload": TUNE_WORKLOAD[args.tune_params] if n == TUNE_TILES else f"profiling case: {n} tiles",
         "adam_steps": n_adam, "ms_per_adam_step": round(ms / n_adam, 4),
         "defocus_error_um": {"max": round(float(err.max()), 4), "median": round(float(np.median(err)), 4),
                              "frac_within_0.05": round(float(np.mean(err <= 0.05)), 4)},
+        "param_error_max": {k: round(float(errs[:, i].max()), 5) for i, k in enumerate(keys)},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["gbs"], "peak": peak, "unit": "GB/s",
                      "frac": round(kern[dom]["gbs"] / peak, 4) if kern[dom]["gbs"] else None, "traffic": None,
                      "peak_source": peak_kind},
@@ -736,7 +768,7 @@ def autotune_leg(args, rank, world, local_rank, with_cpu=True):
     }
     if with_cpu and rank == 0 and not args.no_cpu_baseline:
         d0 = data[0].double().cpu().numpy()
-        out["cpu_baseline"] = tune_cpu_baseline(truth[0], d0, sched)
+        out["cpu_baseline"] = tune_cpu_baseline(truth[0], start[0], d0, sched, keys)
     del pb, data, d_in
     torch.cuda.empty_cache()
     return out
@@ -758,8 +790,8 @@ def run_autotune(args, rank, world, local_rank):
                     "1e-3 noise)",
             "config": {"workload": r["workload"], "tiles": args.tune_tiles, "tile": list(TUNE_SHAPE), "eta": TUNE_ETA,
                        "parallelism": f"replicas x{world}", "l2": r["l2"], "schedule": r["schedule"]}}
-    for k in ("defocus_error_um", "roofline", "kernels", "gpu_launches", "clocks", "e2e", "cpu_baseline",
-              "ms_per_adam_step"):
+    for k in ("defocus_error_um", "param_error_max", "roofline", "kernels", "gpu_launches", "clocks", "e2e",
+              "cpu_baseline", "ms_per_adam_step"):
         if k in r:
             line[k] = r[k]
     print(json.dumps(line), flush=True)
@@ -804,6 +836,8 @@ def main():
                     help="widefield workload: skip the auto-tuning summary leg")
     ap.add_argument("--tune-tiles", type=int, default=TUNE_TILES,
                     help="auto-tuning tiles (fewer only for profiler captures)")
+    ap.add_argument("--tune-params", choices=["all", "defocus"], default="all",
+                    help="auto-tuning of (defocus, tilt_x, tilt_y, NA_ill) or of the defocus alone")
     ap.add_argument("--shape", type=int, nargs=3, default=None,
                     help="override Z Y X (smaller cases for profiler captures only)")
     args = ap.parse_args()

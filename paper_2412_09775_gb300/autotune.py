@@ -165,6 +165,16 @@ def default_schedule(o) -> tuple:
     return (Phase(25, 0.08, 0.02, nu), Phase(25, 0.02, 0.0, 0.0, reset=True))
 
 
+def default_schedule4(o) -> tuple:
+    """50 Adam steps on (defocus, tilt_x, tilt_y, NA_ill) from nominal: 25 on
+    the band-limited loss (lr 0.08 -> 0.02 um for the defocus, 0.01 -> 0.003
+    NA for the illumination), then 25 on the full loss with fresh moments
+    (0.02 -> 0 um, 0.005 -> 0 NA)."""
+    nu = 0.12 * o["na_det"] / o["lambda_um"]
+    return (Phase(25, (0.08, 0.01, 0.01, 0.01), (0.02, 0.003, 0.003, 0.003), nu),
+            Phase(25, (0.02, 0.005, 0.005, 0.005), (0.0, 0.0, 0.0, 0.0), 0.0, reset=True))
+
+
 class TuneLoss(torch.autograd.Function):
     """loss[t] = L_t(theta[t]) with dL/dtheta from the library's adjoint;
     theta [n, n_params] in the order of PARAMS."""

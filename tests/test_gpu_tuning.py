@@ -298,3 +298,19 @@ def test_four_parameter_gradient_matches_oracle(env, loss):
         assert abs(val[t] - want) <= 1e-4 * abs(want), (t, val[t], want)
         scale = np.linalg.norm(gwant)
         assert np.all(np.abs(grad[t] - gwant) <= 1e-3 * np.abs(gwant) + 1e-4 * scale), (t, grad[t], gwant)
+
+
+def test_four_parameter_adam_from_nominal_under_a_cuda_graph(env):
+    """50 Adam steps on (defocus, tilt_x, tilt_y, NA_ill) from defocus 0, no
+    tilt and NA_ill 0.825: every tile within 0.05 um in defocus and 0.01 NA in
+    tilt and NA_ill of its true optics (smooth-source data)."""
+    B, A, torch, dev = env
+    ol = smooth_tiles(8, 24)
+    d = np.stack([thin_stack(o, SHAPE, 80 + 17 * t) for t, o in enumerate(ol)])
+    data = torch.tensor(d, dtype=torch.float32, device=dev)
+    truth = np.array([[o["defocus_um"], o["tilt_x"], o["tilt_y"], o["na_ill"]] for o in ol])
+    start = [dict(o, defocus_um=0.0, tilt_x=0.0, tilt_y=0.0, na_ill=0.825) for o in ol]
+    pb = A.TuningProblem(data, start, 1e-3, params="all")
+    pb.run(A.default_schedule4(ol[0]), graph=True)
+    err = np.abs(pb.params().cpu().numpy() - truth)
+    assert np.all(err[:, 0] <= 0.05) and np.all(err[:, 1:] <= 0.01), err
