@@ -69,10 +69,11 @@ static int tune_cols(int n, int ncols, long long planes, float2* scratch, cudaSt
     if (engine == WO_ENGINE_HYBRID && !cols_hyb_supported(n)) continue;
     g_cols_engine[n].store(engine);
     const long long ps = (long long)n * ncols;
-    // one launch to set up the kernel, then three timed
+    // one launch to set up the kernel, then kReps timed
+    constexpr int kReps = 8;
     if (cols_c2c(n, false, scratch, ncols, ps, ncols, planes, s, "autotune") != cudaSuccess) break;
     cudaEventRecord(e0, s);
-    for (int r = 0; r < 3; ++r) cols_c2c(n, r & 1, scratch, ncols, ps, ncols, planes, s, "autotune");
+    for (int r = 0; r < kReps; ++r) cols_c2c(n, r & 1, scratch, ncols, ps, ncols, planes, s, "autotune");
     cudaEventRecord(e1, s);
     if (cudaEventSynchronize(e1) != cudaSuccess) break;
     float ms = 0.f;
@@ -85,7 +86,7 @@ static int tune_cols(int n, int ncols, long long planes, float2* scratch, cudaSt
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   g_cols_engine[n].store(best < 0 ? saved : best);
-  if (best_ms) *best_ms = best_t / 3.f;
+  if (best_ms) *best_ms = best_t / 8.f;
   return best;
 }
 
