@@ -593,3 +593,86 @@ def test_source_tf_derivatives_match_finite_differences():
         Hm = O.plane_tfs(dict(o, **{k: o[k] - h}), shape, ("phase",))["phase"]
         fd = (Hp - Hm) / (2 * h)
         assert np.abs(dH[k] - fd).max() <= 1e-6 * np.abs(fd).max(), k
+
+
+# ------------------------------------------------ learned estimator (reference network and features)
+def test_estimator_conv_equals_scipy_correlation():
+    """The network's 3x3 zero-padded strided convolution equals a sum of
+    scipy.signal.correlate2d results, subsampled."""
+    from scipy.signal import correlate2d
+    from oracle import estimator as E
+    rng = np.random.default_rng(0)
+    x = rng.normal(size=(2, 3, 10, 12))
+    w = rng.normal(size=(4, 3, 3, 3))
+    b = rng.normal(size=4)
+    for s in (1, 2):
+        y = E._conv(x, w, b, s)
+        for bi in range(2):
+            for co in range(4):
+                full = sum(correlate2d(x[bi, ci], w[co, ci], mode="same", boundary="fill") for ci in range(3))
+                assert np.allclose(y[bi, co], full[::s, ::s] + b[co], atol=1e-12)
+
+
+def test_estimator_bf16_rounding_matches_torch():
+    import torch
+    from oracle import estimator as E
+    vals = np.array([1.0, 1 + 2 ** -8, 1 + 3 * 2 ** -9, -2.7182817, 3.1415927e-5, 65504.0, 1e-40], dtype=np.float32)
+    want = torch.tensor(vals).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(E.bf16(vals), want)
+
+
+def test_estimator_backward_matches_finite_differences(monkeypatch):
+    """The hand-derived backward pass equals central differences of the loss
+    for weights and biases of every layer.  The bfloat16 rounding of the
+    weights makes the loss piecewise constant in them, so the check runs
+    with the rounding replaced by the identity (the backward pass is the
+    gradient with respect to the rounded values)."""
+    from oracle import estimator as E
+    monkeypatch.setattr(E, "bf16", lambda v: np.asarray(v, dtype=np.float64))
+    rng = np.random.default_rng(1)
+    flat = rng.normal(size=E.n_params()) * 0.05
+    x = rng.normal(size=(2, 3, 16, 16))
+    t = rng.normal(size=(2, 4))
+    L, g = E.backward(flat, x, t)
+    assert abs(L - E.loss(flat, x, t)) <= 1e-14 * abs(L)
+    offs = np.cumsum([0] + [int(np.prod(sh)) for sh in E.param_shapes()])
+    h = 1e-6
+    for k in range(len(offs) - 1):  # a few entries of every parameter array
+        for i in rng.integers(offs[k], offs[k + 1], size=3):
+            fp, fm = flat.copy(), flat.copy()
+            fp[i] += h
+            fm[i] -= h
+            fd = (E.loss(fp, x, t) - E.loss(fm, x, t)) / (2 * h)
+            assert abs(g[i] - fd) <= 1e-6 * (abs(fd) + 1e-4), (k, i, g[i], fd)
+
+
+def test_estimator_features_properties():
+    """Plane-to-plane drift shows in the cross channels with its sign and
+    axis; reversing the plane order mirrors the rows and flips the drift;
+    the power channel does not see the data's scale."""
+    from oracle import estimator as E
+    o = ph.optics()
+    rng = np.random.default_rng(2)
+    Z, Y, X = 8, 32, 32
+    base = rng.normal(size=(Y, X))
+    same = np.stack([base] * Z)
+    f = E.tile_features(same, o)
+    assert np.abs(f[1:]).max() <= 1e-12
+    xs = np.stack([np.roll(base, r, axis=1) for r in range(Z)])  # +1 pixel in x per plane
+    f = E.tile_features(xs, o)
+    band = f[0, 0] > 0
+    assert np.all(f[1, : Z - 1][:, band] < 0) and np.abs(f[2]).max() <= 1e-12
+    ys = np.stack([np.roll(base, r, axis=0) for r in range(Z)])
+    f = E.tile_features(ys, o)
+    assert np.all(f[2, : Z - 1][:, band] < 0) and np.abs(f[1]).max() <= 1e-12
+    # plane order reversed (row r <-> Z-1-r in natural order): drift flips sign
+    stack = rng.normal(size=(Z, Y, X))
+    nat = np.stack([stack[E.natural_plane(r, Z)] for r in range(Z)])
+    rev = nat[::-1]
+    back = np.zeros_like(stack)
+    for r in range(Z):
+        back[E.natural_plane(r, Z)] = rev[r]
+    fa, fb = E.tile_features(stack, o), E.tile_features(back, o)
+    assert np.allclose(fb[0, :Z], fa[0, :Z][::-1], atol=1e-12)
+    assert np.allclose(fb[1, : Z - 1], -fa[1, : Z - 1][::-1], atol=1e-12)
+    assert np.allclose(E.tile_features(1 + 3.0 * (stack - 1), o)[0], fa[0], atol=1e-12)
