@@ -658,11 +658,21 @@ def test_estimator_features_properties():
     same = np.stack([base] * Z)
     f = E.tile_features(same, o)
     assert np.abs(f[1:]).max() <= 1e-12
-    xs = np.stack([np.roll(base, r, axis=1) for r in range(Z)])  # +1 pixel in x per plane
+    # +1 pixel in x per plane; an image even in y has no drift signal along y
+    def stack_drift(img, axis):  # natural plane r shifted by r pixels, stored in FFT order
+        out = np.zeros((Z,) + img.shape)
+        for r in range(Z):
+            out[E.natural_plane(r, Z)] = np.roll(img, r, axis=axis)
+        return out
+
+    sym_y = base + np.roll(base[::-1], 1, axis=0)
+    xs = stack_drift(sym_y, 1)
     f = E.tile_features(xs, o)
     band = f[0, 0] > 0
+    band[0] = False  # bin 0 holds only the zero frequency, which has no direction
     assert np.all(f[1, : Z - 1][:, band] < 0) and np.abs(f[2]).max() <= 1e-12
-    ys = np.stack([np.roll(base, r, axis=0) for r in range(Z)])
+    sym_x = base + np.roll(base[:, ::-1], 1, axis=1)
+    ys = stack_drift(sym_x, 0)
     f = E.tile_features(ys, o)
     assert np.all(f[2, : Z - 1][:, band] < 0) and np.abs(f[1]).max() <= 1e-12
     # plane order reversed (row r <-> Z-1-r in natural order): drift flips sign
