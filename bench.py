@@ -797,6 +797,117 @@ def run_autotune(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ learned estimator
+EST_TRAIN = 100000
+EST_TEST = 4096
+EST_WORKLOAD = ("learned optics estimator: conv net (4 conv 3x3 + pool + linear, 186k bfloat16 weights, float32 "
+                "sums) trained on forward-simulated tiles of 48x128x128, then inference on 4096 tiles + 10 "
+                "refinement Adam steps, against 50-step auto-tuning from nominal on the same tiles")
+
+
+def run_estimator(args, rank, world, local_rank):
+    import torch
+    import phantom as ph
+    from paper_2412_09775_gb300.build import build
+    build()
+    from paper_2412_09775_gb300 import autotune as A, binding as B, estimator as E
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    base = ph.optics()
+    shape = TUNE_SHAPE
+    Z, Y, X = shape
+
+    def clock(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t0
+
+    (feat, truth), t_gen = clock(lambda: E.generate(args.est_train, shape, base, seed=100 + rank, device=dev))
+    est = E.Estimator(dev, seed=rank, batch=256)
+    losses, t_train = clock(lambda: est.train(feat, truth, epochs=args.est_epochs, lr=2e-3))
+    del feat
+    torch.cuda.empty_cache()
+    # test tiles: stacks kept for the refinement, in chunks of 256
+    rng = np.random.default_rng(200 + rank)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(200 + rank)
+    sim = E.Simulator(shape, 256, dev)
+    n_test = args.est_test
+    stacks, optics, truths = [], [], []
+    for i0 in range(0, n_test, 256):
+        m = min(256, n_test - i0)
+        ol = E.random_optics(rng, m, base)
+        stacks.append(sim.stacks(ol, E.sphere_params(rng, m, shape[1:], base["pixel_um"]), 1e-3, gen))
+        optics.append(ol)
+        truths.append(np.array([[o["defocus_um"], o["tilt_x"], o["tilt_y"], o["na_ill"]] for o in ol]))
+    truth_all = np.concatenate(truths)
+    nominal = [dict(o, defocus_um=0.0, tilt_x=0.0, tilt_y=0.0, na_ill=0.825) for o in optics[0]]
+    refine, plain = A.refine_schedule(10), A.default_schedule4(base)
+
+    def new_problem(data, start):
+        q = A.TuningProblem(data, start, TUNE_ETA, params="all")
+        B.wo_autotune(q.n, Z, Y, X, q.kinds, q.ws)
+        for sch in (refine, plain):  # capture both graphs outside the timed regions
+            q.run(sch, graph=True)
+            q.reset()
+        return q
+
+    pb = new_problem(stacks[0], nominal)
+    feats = torch.empty((256, 3, 64, 64), dtype=torch.float32, device=dev)
+    t_feat = t_inf = t_ref = t_plain = 0.0
+    est_err, ref_err, plain_err = [], [], []
+    for c, data in enumerate(stacks):
+        m = data.shape[0]
+        ol = optics[c]
+        nom = [dict(o, defocus_um=0.0, tilt_x=0.0, tilt_y=0.0, na_ill=0.825) for o in ol]
+        _, dt = clock(lambda: sim.features(data, B.optics_tensor(nom, dev), feats[:m]))
+        t_feat += dt
+        pred, dt = clock(lambda: est.predict(feats[:m]))
+        t_inf += dt
+        p = pred.cpu().numpy().astype(np.float64)
+        est_err.append(np.abs(p - truths[c]))
+        start = [dict(o, defocus_um=float(q[0]), tilt_x=float(q[1]), tilt_y=float(q[2]),
+                      na_ill=float(np.clip(q[3], 0.5, 1.0))) for o, q in zip(nom, p)]
+        if m != pb.n:
+            pb = new_problem(data, start)
+        pb.set_data(data)
+        pb.restart(start)
+        _, dt = clock(lambda: pb.run(refine, graph=True))
+        t_ref += dt
+        ref_err.append(np.abs(pb.params().cpu().numpy() - truths[c]))
+        pb.restart(nom)
+        _, dt = clock(lambda: pb.run(plain, graph=True))
+        t_plain += dt
+        plain_err.append(np.abs(pb.params().cpu().numpy() - truths[c]))
+    est_err, ref_err, plain_err = (np.concatenate(e) for e in (est_err, ref_err, plain_err))
+    if rank != 0:
+        return
+
+    def summary(err):
+        return {"defocus_max_um": round(float(err[:, 0].max()), 4),
+                "defocus_median_um": round(float(np.median(err[:, 0])), 4),
+                "frac_defocus_within_0.05": round(float(np.mean(err[:, 0] <= 0.05)), 4),
+                "illumination_max_na": [round(float(err[:, k].max()), 4) for k in (1, 2, 3)]}
+
+    learned_s = (t_feat + t_inf + t_ref) / n_test
+    plain_s = t_plain / n_test
+    line = {"metric": METRIC, "value": round(1.0 / learned_s, 2), "unit": "tiles/s", "n_gpus": world,
+            "steps": 1, "warmup": 1, "ms_per_step": round(1e3 * (t_feat + t_inf + t_ref), 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 weights, f32 sums",
+            "data": "synthetic (thin sphere-projection specimens, forward model with the smooth source, 1e-3 noise)",
+            "config": {"workload": EST_WORKLOAD, "train_tiles": args.est_train, "epochs": args.est_epochs,
+                       "test_tiles": n_test, "tile": list(shape), "parallelism": f"replicas x{world}"},
+            "learned": {"s_per_tile": learned_s, "features_s": t_feat, "inference_s": t_inf, "refine_10_s": t_ref,
+                        "estimate_error": summary(est_err), "refined_error": summary(ref_err)},
+            "plain": {"s_per_tile": plain_s, "tune_50_s": t_plain, "error": summary(plain_err)},
+            "speedup_vs_plain": round(plain_s / learned_s, 2),
+            "training": {"generate_s": round(t_gen, 2), "train_s": round(t_train, 2),
+                         "loss_per_epoch": [round(v, 5) for v in losses], "params": est.n}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -831,7 +942,10 @@ def main():
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
-    ap.add_argument("--workload", choices=["widefield", "tiles", "autotune"], default="widefield")
+    ap.add_argument("--workload", choices=["widefield", "tiles", "autotune", "estimator"], default="widefield")
+    ap.add_argument("--est-train", type=int, default=EST_TRAIN, help="estimator training tiles")
+    ap.add_argument("--est-epochs", type=int, default=6, help="estimator training epochs")
+    ap.add_argument("--est-test", type=int, default=EST_TEST, help="estimator test tiles")
     ap.add_argument("--no-autotune", action="store_true",
                     help="widefield workload: skip the auto-tuning summary leg")
     ap.add_argument("--tune-tiles", type=int, default=TUNE_TILES,
@@ -860,6 +974,8 @@ def main():
             run_tiles(args, rank, world, local_rank)
         elif args.workload == "autotune":
             run_autotune(args, rank, world, local_rank)
+        elif args.workload == "estimator":
+            run_estimator(args, rank, world, local_rank)
         else:
             run_gpu(args, rank, world, local_rank)
     finally:

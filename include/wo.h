@@ -330,6 +330,58 @@ wo_status wo_adam_optics(wo_optics *d_optics, const double *d_grad, int n_params
                          int n_tiles, const double *h_lr, double beta1, double beta2, double eps,
                          wo_stream stream);
 
+/* Learned optics estimator (no counterpart in the paper: the workload asks
+ * for a learned starting point of auto-tuning).  Features: per tile, a
+ * 3 x 64 x 64 float image from the per-plane 2D spectra of its stack
+ * (wo_spectrum, WO_MODE_2D, channel-mean background), planes in natural
+ * order as rows (Z <= 64, zero rows below), 64 radial bins of |nu| up to
+ * 2 NA_det/lambda as columns:
+ *   ch0 = log(1 + P / mean P),  P = sum_bin |D_r|^2            (power profile)
+ *   ch1 = sum_bin Im(D_{r+1} D_r*) nu_x/|nu| / sum_bin |D_{r+1}| |D_r|
+ *   ch2 = the same with nu_y                                  (plane-to-plane drift)
+ * The power profile locates the in-focus plane (the defocus with its sign),
+ * the drift follows the illumination tilt.  wo_est_features: d_feat
+ * [n_tiles][3][64][64] (caller-owned).
+ * Network: conv 3x3 3->32 (stride 1), 32->64, 64->96, 96->128 (stride 2), zero
+ * padding 1, ReLU; global average pool; linear 128->4.  Parameters: one flat
+ * float32 array of wo_est_param_count() values (each conv W [co][ci][3][3]
+ * then its bias, then the linear W [4][128] and bias) and a bfloat16 copy
+ * (uint16 storage, same offsets) from which every weight is read; sums are
+ * float32.  Outputs are standardised; h_scale / h_offset (4 host floats
+ * each, scale != 0) map them to physical units, out = scale * net + offset,
+ * and targets back.  wo_est_forward: d_out [batch][4] physical values.
+ * wo_est_backward: mean squared error of the standardised outputs and its
+ * gradient (d_grad: param_count floats, or NULL to keep it in the
+ * workspace; d_loss: one float or NULL).  wo_est_train_step: backward, then
+ * one Adam step (Kingma and Ba, 2015; b1 0.9, b2 0.999, eps 1e-8, 1-based
+ * step) on the float32 weights with moments d_m, d_v (param_count floats
+ * each, zeroed before the first step) and a refresh of the bfloat16 copy.
+ * wo_est_sync_bf16: the bfloat16 copy from the float32 weights (round to
+ * nearest even).  All device arrays 16-byte aligned; 1 <= batch <= 4096;
+ * workspace wo_est_workspace_bytes(batch).
+ * wo_thin_phantom: the training specimens, [n_tiles][Y][X] float: spheres
+ * (d_params [n_tiles][n_spheres][4] floats: centre y, centre x, radius in
+ * um, index increment) projected along z on the periodic tile, as the
+ * increment of one plane of thickness z_step: sum dn 2 sqrt(r^2 - rho^2) / dz. */
+size_t wo_est_param_count(void);
+size_t wo_est_workspace_bytes(int batch);
+wo_status wo_est_sync_bf16(const float *d_w32, void *d_wbf16, wo_stream stream);
+wo_status wo_est_forward(const void *d_wbf16, const float *d_w32, const float *d_feat, int batch,
+                         const float *h_scale, const float *h_offset, float *d_out, void *d_ws,
+                         size_t ws_bytes, wo_stream stream);
+wo_status wo_est_backward(const void *d_wbf16, const float *d_w32, const float *d_feat,
+                          const float *d_target, int batch, const float *h_scale,
+                          const float *h_offset, float *d_grad, float *d_loss, void *d_ws,
+                          size_t ws_bytes, wo_stream stream);
+wo_status wo_est_train_step(float *d_w32, void *d_wbf16, float *d_m, float *d_v,
+                            const float *d_feat, const float *d_target, int batch,
+                            const float *h_scale, const float *h_offset, int step, float lr,
+                            float *d_loss, void *d_ws, size_t ws_bytes, wo_stream stream);
+wo_status wo_est_features(const void *d_spec, const wo_optics *d_optics, int n_tiles, int Z, int Y,
+                          int X, float *d_feat, wo_stream stream);
+wo_status wo_thin_phantom(const float *d_params, int n_tiles, int n_spheres, int Y, int X,
+                          double pixel_um, double z_step_um, float *d_out, wo_stream stream);
+
 /* Schedules and the autotuner (no counterpart in the paper).  A pass with
  * more than one implementation runs the engine its schedule table names.
  * WO_PASS_COLS: the complex transforms along a strided axis (every y pass,

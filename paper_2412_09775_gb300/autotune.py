@@ -70,8 +70,7 @@ class TuningProblem:
         self.value = torch.zeros(self.n, dtype=torch.float64, device=dev)
         self.grad = torch.zeros((self.n, self.n_params), dtype=torch.float64, device=dev)
         self.state = torch.zeros((self.n, self.n_params, 3), dtype=torch.float64, device=dev)
-        self._graph = None
-        self._graph_key = None
+        self._graphs = {}  # schedule -> captured CUDA graph
 
     def set_data(self, data: torch.Tensor):
         """New stacks for the same tiles (the spectra are recomputed)."""
@@ -88,6 +87,11 @@ class TuningProblem:
     def set_params(self, p: torch.Tensor):
         for i, k in enumerate(PARAMS[: self.n_params]):
             self.optics[:, _COLUMN[k]].copy_(p[:, i])
+
+    def restart(self, optics_list):
+        """New starting optics for the same tiles (e.g. an estimator's output)."""
+        self.optics0.copy_(B.optics_tensor(optics_list, self.optics.device))
+        self.reset()
 
     def reset(self):
         """Back to the starting optics, Adam state cleared."""
@@ -118,13 +122,15 @@ class TuningProblem:
         With ``graph`` the whole schedule is captured once into a CUDA graph
         (after one eager pass that sets up the kernels, undone afterwards)
         and replayed; the Adam state lives on the device, so the replay
-        continues from wherever the optics stand.
+        continues from wherever the optics stand.  Graphs are kept per
+        schedule and stay valid across ``set_data`` and ``restart``, which
+        only rewrite the problem's buffers.
         """
         key = tuple(schedule)
         if not graph:
             self._queue(key)
             return
-        if self._graph is None or self._graph_key != key:
+        if key not in self._graphs:
             saved_o, saved_s = self.optics.clone(), self.state.clone()
             self._queue(key[:1])  # first launch of every kernel, outside the capture
             torch.cuda.synchronize()
@@ -133,8 +139,8 @@ class TuningProblem:
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g):
                 self._queue(key)
-            self._graph, self._graph_key = g, key
-        self._graph.replay()
+            self._graphs[key] = g
+        self._graphs[key].replay()
 
 
 @dataclass(frozen=True)
@@ -173,6 +179,13 @@ def default_schedule4(o) -> tuple:
     nu = 0.12 * o["na_det"] / o["lambda_um"]
     return (Phase(25, (0.08, 0.01, 0.01, 0.01), (0.02, 0.003, 0.003, 0.003), nu),
             Phase(25, (0.02, 0.005, 0.005, 0.005), (0.0, 0.0, 0.0, 0.0), 0.0, reset=True))
+
+
+def refine_schedule(steps: int = 10) -> tuple:
+    """A short run on the full loss from a good starting point (an
+    estimator's output): lr 0.01 -> 0 um for the defocus, 0.002 -> 0 NA for
+    the illumination."""
+    return (Phase(steps, (0.01, 0.002, 0.002, 0.002), (0.0, 0.0, 0.0, 0.0), 0.0),)
 
 
 class TuneLoss(torch.autograd.Function):

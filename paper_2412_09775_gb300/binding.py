@@ -70,6 +70,14 @@ def _load():
                                ctypes.c_double, ctypes.c_double, vp]),
         "wo_fused_workspace_bytes": (sz, [i, i, i, i, i]),
         "wo_reconstruct_fused": (i, [vp, i, vp, fp, f, i, i, vp, i, i, i, i, vp, sz, vp]),
+        "wo_est_param_count": (sz, []),
+        "wo_est_workspace_bytes": (sz, [i]),
+        "wo_est_sync_bf16": (i, [vp, vp, vp]),
+        "wo_est_forward": (i, [vp, vp, vp, i, fp, fp, vp, vp, sz, vp]),
+        "wo_est_backward": (i, [vp, vp, vp, vp, i, fp, fp, vp, vp, vp, sz, vp]),
+        "wo_est_train_step": (i, [vp, vp, vp, vp, vp, vp, i, fp, fp, i, f, vp, vp, sz, vp]),
+        "wo_est_features": (i, [vp, vp, i, i, i, i, vp, vp]),
+        "wo_thin_phantom": (i, [vp, i, i, i, i, ctypes.c_double, ctypes.c_double, vp, vp]),
         "wo_schedule_set": (i, [i, i, i]),
         "wo_schedule_get": (i, [i, i]),
         "wo_autotune": (i, [i, i, i, i, u, vp, sz, vp]),
@@ -93,6 +101,8 @@ EXPORTED = ("wo_size_supported", "wo_tf_bytes", "wo_workspace_bytes", "wo_build_
             "wo_forward",
             "wo_forward_adjoint", "wo_reconstruct", "wo_reconstruct_static", "wo_spectrum",
             "wo_tune_objective", "wo_adam_optics", "wo_fused_workspace_bytes", "wo_reconstruct_fused",
+            "wo_est_param_count", "wo_est_workspace_bytes", "wo_est_sync_bf16", "wo_est_forward", "wo_est_backward",
+            "wo_est_train_step", "wo_est_features", "wo_thin_phantom",
             "wo_schedule_set", "wo_schedule_get", "wo_autotune", "wo_tile_gather", "wo_tile_blend",
             "wo_status_string", "wo_profile_enable", "wo_profile_read", "wo_launch_count")
 
@@ -253,6 +263,47 @@ def wo_reconstruct_fused(tf, n_channels, data, background, eta, eta_flag, mode, 
     _check(_lib.wo_reconstruct_fused(_ptr(tf), int(n_channels), _ptr(data), bg[0] if bg else None, float(eta),
                                      int(eta_flag), int(mode), _ptr(f), n_tiles, Z, Y, X, _ptr(ws), _nbytes(ws),
                                      _stream(stream)), "wo_reconstruct_fused")
+
+
+def wo_est_param_count() -> int:
+    return int(_lib.wo_est_param_count())
+
+
+def wo_est_workspace_bytes(batch) -> int:
+    return int(_lib.wo_est_workspace_bytes(int(batch)))
+
+
+def wo_est_sync_bf16(w32, wbf16, stream=None):
+    _check(_lib.wo_est_sync_bf16(_ptr(w32), _ptr(wbf16), _stream(stream)), "wo_est_sync_bf16")
+
+
+def wo_est_forward(wbf16, w32, feat, batch, scale, offset, out, ws, stream=None):
+    sc, off = _floats(scale), _floats(offset)
+    _check(_lib.wo_est_forward(_ptr(wbf16), _ptr(w32), _ptr(feat), int(batch), sc[0], off[0], _ptr(out), _ptr(ws),
+                               _nbytes(ws), _stream(stream)), "wo_est_forward")
+
+
+def wo_est_backward(wbf16, w32, feat, target, batch, scale, offset, grad, loss, ws, stream=None):
+    sc, off = _floats(scale), _floats(offset)
+    _check(_lib.wo_est_backward(_ptr(wbf16), _ptr(w32), _ptr(feat), _ptr(target), int(batch), sc[0], off[0],
+                                _ptr(grad), _ptr(loss), _ptr(ws), _nbytes(ws), _stream(stream)), "wo_est_backward")
+
+
+def wo_est_train_step(w32, wbf16, m, v, feat, target, batch, scale, offset, step, lr, loss, ws, stream=None):
+    sc, off = _floats(scale), _floats(offset)
+    _check(_lib.wo_est_train_step(_ptr(w32), _ptr(wbf16), _ptr(m), _ptr(v), _ptr(feat), _ptr(target), int(batch),
+                                  sc[0], off[0], int(step), float(lr), _ptr(loss), _ptr(ws), _nbytes(ws),
+                                  _stream(stream)), "wo_est_train_step")
+
+
+def wo_est_features(spec, d_optics, n_tiles, Z, Y, X, feat, stream=None):
+    _check(_lib.wo_est_features(_ptr(spec), _ptr(d_optics), n_tiles, Z, Y, X, _ptr(feat), _stream(stream)),
+           "wo_est_features")
+
+
+def wo_thin_phantom(params, n_tiles, n_spheres, Y, X, pixel_um, z_step_um, out, stream=None):
+    _check(_lib.wo_thin_phantom(_ptr(params), n_tiles, n_spheres, Y, X, float(pixel_um), float(z_step_um), _ptr(out),
+                                _stream(stream)), "wo_thin_phantom")
 
 
 def wo_schedule_set(pass_, n, engine):

@@ -1,0 +1,651 @@
+// wo_est.cu - the learned optics estimator: spectral features of a tile, a
+// small convolutional network with bfloat16 weights and float32 sums
+// (inference and training), and the thin-specimen generator that makes its
+// training data with the forward model.
+//
+// Network: four 3x3 convolutions (3->32 stride 1, 32->64, 64->96, 96->128
+// stride 2, zero padding 1, ReLU), a global average pool, a linear layer to 4
+// outputs.  Parameters live in one flat float32 array (master weights, in the
+// order conv1 W, conv1 b, ..., conv4 W, conv4 b, fc W, fc b) and a bfloat16
+// copy of it that the kernels read for every weight (biases are read as
+// float32).  The outputs are the standardised optics; the caller's scale and
+// offset map them to physical units (out = scale * net + offset).
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "wo_fft.cuh"
+#include "wo_internal.h"
+
+namespace wo {
+
+namespace {
+
+constexpr int kSide = 64;
+constexpr int kOut = 4;
+struct LayerDef {
+  int ci, co, stride, hin;
+};
+constexpr LayerDef kLayers[4] = {{3, 32, 1, 64}, {32, 64, 2, 64}, {64, 96, 2, 32}, {96, 128, 2, 16}};
+
+__host__ __device__ constexpr int hout(int h, int s) { return (h + s - 1) / s; }
+
+// Offsets of every parameter array in the flat layout.
+struct ParamMap {
+  long long w[4], b[4], fw, fb, total;
+};
+constexpr ParamMap param_map() {
+  ParamMap m{};
+  long long o = 0;
+  for (int l = 0; l < 4; ++l) {
+    m.w[l] = o;
+    o += (long long)kLayers[l].co * kLayers[l].ci * 9;
+    m.b[l] = o;
+    o += kLayers[l].co;
+  }
+  m.fw = o;
+  o += (long long)kOut * kLayers[3].co;
+  m.fb = o;
+  o += kOut;
+  m.total = o;
+  return m;
+}
+constexpr ParamMap kMap = param_map();
+
+__device__ __forceinline__ float bf(const __nv_bfloat16* p, long long i) { return __bfloat162float(p[i]); }
+
+// ---------------------------------------------------------------- features
+__device__ __forceinline__ int freq_idx(int i, int n) { return (i < (n + 1) / 2) ? i : i - n; }
+
+// One block per (natural row r, tile): radial sums of the plane's power and of
+// the cross spectrum with the next plane, over the half spectrum with the
+// weights of the conjugate pairs.  Rows >= Z are zero.  ch0 holds the raw
+// power until k_feat_norm.
+__global__ void __launch_bounds__(256) k_features(const float2* __restrict__ spec, const wo_optics* __restrict__ optics,
+                                                  int Z, int Y, int X, float* __restrict__ feat) {
+  __shared__ float P[kSide], den[kSide], sx[kSide], sy[kSide];
+  const int r = blockIdx.x, t = blockIdx.y;
+  const int Xh = X / 2 + 1;
+  for (int i = threadIdx.x; i < kSide; i += blockDim.x) P[i] = den[i] = sx[i] = sy[i] = 0.f;
+  __syncthreads();
+  float* out = feat + (long long)t * 3 * kSide * kSide + (long long)r * kSide;
+  if (r < Z) {
+    const wo_optics o = optics[t];
+    const double cut = 2.0 * o.na_det / o.lambda_um;
+    const long long plane = (long long)Y * Xh;
+    const float2* Dr = spec + ((long long)t * Z + ((r - Z / 2 + Z) % Z)) * plane;
+    const bool nxt = r + 1 < Z;
+    const float2* Dn = spec + ((long long)t * Z + ((r + 1 - Z / 2 + Z) % Z)) * plane;
+    for (long long e = threadIdx.x; e < plane; e += blockDim.x) {
+      const int y = (int)(e / Xh), x = (int)(e - (long long)y * Xh);
+      const double fy = (double)freq_idx(y, Y) / ((double)Y * o.pixel_um);
+      const double fx = (double)x / ((double)X * o.pixel_um);
+      const double rad = sqrt(fx * fx + fy * fy);
+      const int b = (int)floor(rad / cut * kSide);
+      if (b >= kSide) continue;
+      const float w = (x == 0 || 2 * x == X) ? 1.f : 2.f;
+      const float2 dr = Dr[e];
+      atomicAdd(&P[b], w * cabs2(dr));
+      if (nxt) {
+        const float2 dn = Dn[e];
+        const float2 c = cmulc(dr, dn);  // dn * conj(dr)
+        const float ux = rad > 0 ? (float)(fx / rad) : 0.f, uy = rad > 0 ? (float)(fy / rad) : 0.f;
+        atomicAdd(&den[b], w * sqrtf(cabs2(dn) * cabs2(dr)));
+        atomicAdd(&sx[b], w * c.y * ux);
+        atomicAdd(&sy[b], w * c.y * uy);
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kSide; i += blockDim.x) {
+    out[i] = P[i];
+    out[kSide * kSide + i] = den[i] > 0.f ? sx[i] / den[i] : 0.f;
+    out[2 * kSide * kSide + i] = den[i] > 0.f ? sy[i] / den[i] : 0.f;
+  }
+}
+
+// One block per tile: ch0 = log(1 + P / mean P) over the Z valid rows.
+__global__ void __launch_bounds__(256) k_feat_norm(int Z, float* __restrict__ feat) {
+  __shared__ double red[256];
+  float* f = feat + (long long)blockIdx.x * 3 * kSide * kSide;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < Z * kSide; i += blockDim.x) s += f[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  const double m = red[0] / (double)(Z * kSide);
+  for (int i = threadIdx.x; i < Z * kSide; i += blockDim.x) f[i] = m > 0 ? (float)log1p((double)f[i] / m) : 0.f;
+}
+
+// ---------------------------------------------------------------- phantom
+// Spheres projected along z onto one plane, as the index increment of a
+// plane of thickness dz: sum dn 2 sqrt(r^2 - rho^2) / dz, periodic tile.
+__global__ void k_thin_phantom(const float4* __restrict__ par, int S, int Y, int X, float pixel, float dz,
+                               float* __restrict__ out) {
+  const int t = blockIdx.y;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)Y * X) return;
+  const int y = (int)(i / X), x = (int)(i - (long long)y * X);
+  const float py = y * pixel, px = x * pixel, ey = Y * pixel, ex = X * pixel;
+  float v = 0.f;
+  for (int s = 0; s < S; ++s) {
+    const float4 q = __ldg(par + (long long)t * S + s);  // cy, cx, radius, dn
+    float dy = py - q.x + 0.5f * ey, dx = px - q.y + 0.5f * ex;
+    dy -= floorf(dy / ey) * ey;
+    dx -= floorf(dx / ex) * ex;
+    dy -= 0.5f * ey;
+    dx -= 0.5f * ex;
+    const float r2 = q.z * q.z - (dy * dy + dx * dx);
+    if (r2 > 0.f) v += q.w * 2.f * sqrtf(r2) / dz;
+  }
+  out[(long long)t * Y * X + i] = v;
+}
+
+// ---------------------------------------------------------------- network
+constexpr int kCoTile = 8;  // output channels per thread in the forward pass
+
+// y[b][co][oh][ow] = relu(b[co] + sum_ci sum_k x[b][ci][oh*s+kh-1][ow*s+kw-1] w[co][ci][kh][kw])
+__global__ void __launch_bounds__(256) k_conv_fwd(const float* __restrict__ x, const __nv_bfloat16* __restrict__ wb,
+                                                  const float* __restrict__ w32, long long woff, long long boff,
+                                                  int Ci, int Co, int H, int s, float* __restrict__ y) {
+  extern __shared__ float ws[];  // [kCoTile][Ci][9]
+  const int Ho = hout(H, s);
+  const int co0 = blockIdx.y * kCoTile, b = blockIdx.z;
+  for (int i = threadIdx.x; i < kCoTile * Ci * 9; i += blockDim.x) {
+    const int c = i / (Ci * 9);
+    ws[i] = co0 + c < Co ? bf(wb, woff + (long long)(co0 + c) * Ci * 9 + (i - c * Ci * 9)) : 0.f;
+  }
+  __syncthreads();
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= Ho * Ho) return;
+  const int oh = p / Ho, ow = p - (p / Ho) * Ho;
+  float acc[kCoTile];
+#pragma unroll
+  for (int c = 0; c < kCoTile; ++c) acc[c] = co0 + c < Co ? w32[boff + co0 + c] : 0.f;
+  const float* xb = x + (long long)b * Ci * H * H;
+  for (int ci = 0; ci < Ci; ++ci) {
+    const float* xc = xb + (long long)ci * H * H;
+    float v[9];
+#pragma unroll
+    for (int kh = 0; kh < 3; ++kh) {
+#pragma unroll
+      for (int kw = 0; kw < 3; ++kw) {
+        const int ih = oh * s + kh - 1, iw = ow * s + kw - 1;
+        v[kh * 3 + kw] = (ih >= 0 && ih < H && iw >= 0 && iw < H) ? __ldg(xc + ih * H + iw) : 0.f;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < kCoTile; ++c) {
+      const float* wc = ws + (c * Ci + ci) * 9;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) acc[c] = fmaf(v[k], wc[k], acc[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < kCoTile; ++c)
+    if (co0 + c < Co) y[((long long)b * Co + co0 + c) * Ho * Ho + p] = fmaxf(acc[c], 0.f);
+}
+
+// pooled[b][c] = mean y4; out[b][k] = sum_c fw[k][c] pooled[b][c] + fb[k]; one block per sample
+__global__ void __launch_bounds__(128) k_head_fwd(const float* __restrict__ y4, const __nv_bfloat16* __restrict__ wb,
+                                                  const float* __restrict__ w32, int C, int HW,
+                                                  float* __restrict__ pooled, float* __restrict__ out,
+                                                  const float* __restrict__ scale, const float* __restrict__ offset,
+                                                  float* __restrict__ phys) {
+  __shared__ float pl[128];
+  const int b = blockIdx.x;
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    const float* yc = y4 + ((long long)b * C + c) * HW;
+    float s = 0.f;
+    for (int i = 0; i < HW; ++i) s += yc[i];
+    pl[c] = s / (float)HW;
+    pooled[(long long)b * C + c] = pl[c];
+  }
+  __syncthreads();
+  if (threadIdx.x < kOut) {
+    const int k = threadIdx.x;
+    float s = w32[kMap.fb + k];
+    for (int c = 0; c < C; ++c) s = fmaf(bf(wb, kMap.fw + (long long)k * C + c), pl[c], s);
+    out[(long long)b * kOut + k] = s;
+    if (phys) phys[(long long)b * kOut + k] = scale[k] * s + offset[k];
+  }
+}
+
+// Loss and the head's gradients.  One block: g_out = 2 (out - t) / (B * 4),
+// d fc W = g_out^T pooled, d fc b = sum g_out; g_pooled = g_out fc W.
+__global__ void __launch_bounds__(256) k_head_bwd(const float* __restrict__ out, const float* __restrict__ target,
+                                                  const float* __restrict__ pooled, const __nv_bfloat16* __restrict__ wb,
+                                                  int B, int C, float* __restrict__ grad, float* __restrict__ gpool,
+                                                  float* __restrict__ loss) {
+  __shared__ float red[256];
+  float l = 0.f;
+  for (int i = threadIdx.x; i < B * kOut; i += blockDim.x) {
+    const float d = out[i] - target[i];
+    l += d * d;
+  }
+  red[threadIdx.x] = l;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && loss) *loss = red[0] / (float)(B * kOut);
+  const float gs = 2.f / (float)(B * kOut);
+  for (int i = threadIdx.x; i < kOut * C; i += blockDim.x) {
+    const int k = i / C, c = i - (i / C) * C;
+    float s = 0.f;
+    for (int b = 0; b < B; ++b) s += gs * (out[b * kOut + k] - target[b * kOut + k]) * pooled[(long long)b * C + c];
+    grad[kMap.fw + i] = s;
+  }
+  if (threadIdx.x < kOut) {
+    float s = 0.f;
+    for (int b = 0; b < B; ++b) s += gs * (out[b * kOut + threadIdx.x] - target[b * kOut + threadIdx.x]);
+    grad[kMap.fb + threadIdx.x] = s;
+  }
+  for (int i = threadIdx.x; i < B * C; i += blockDim.x) {
+    const int b = i / C, c = i - (i / C) * C;
+    float s = 0.f;
+    for (int k = 0; k < kOut; ++k) s += gs * (out[b * kOut + k] - target[b * kOut + k]) * bf(wb, kMap.fw + (long long)k * C + c);
+    gpool[i] = s;
+  }
+}
+
+// Gradient at the last conv layer's output from the pooled gradient,
+// masked by its ReLU: g[b][c][i] = gpool[b][c] / HW where y > 0.
+__global__ void k_unpool(const float* __restrict__ gpool, const float* __restrict__ y, int C, int HW, long long n,
+                         float* __restrict__ g) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const long long bc = i / HW;
+  g[i] = y[i] > 0.f ? gpool[bc] / (float)HW : 0.f;
+}
+
+// gx[b][ci][ih][iw] = sum_co sum_k g[b][co][oh][ow] w[co][ci][kh][kw] over the
+// (oh, ow, kh, kw) with oh*s + kh - 1 = ih, ow*s + kw - 1 = iw; then masked
+// by the ReLU of the layer below (xin > 0).  g is already masked.
+__global__ void __launch_bounds__(256) k_conv_bwd_data(const float* __restrict__ g, const __nv_bfloat16* __restrict__ wb,
+                                                       long long woff, int Ci, int Co, int H, int s,
+                                                       const float* __restrict__ xin, float* __restrict__ gx) {
+  extern __shared__ float ws[];  // [kCoTile ci][Co][9]
+  const int Ho = hout(H, s);
+  const int ci0 = blockIdx.y * kCoTile, b = blockIdx.z;
+  for (int i = threadIdx.x; i < kCoTile * Co * 9; i += blockDim.x) {
+    const int c = i / (Co * 9), rem = i - c * Co * 9, co = rem / 9, k = rem - co * 9;
+    ws[i] = ci0 + c < Ci ? bf(wb, woff + ((long long)co * Ci + ci0 + c) * 9 + k) : 0.f;
+  }
+  __syncthreads();
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= H * H) return;
+  const int ih = p / H, iw = p - (p / H) * H;
+  float acc[kCoTile];
+#pragma unroll
+  for (int c = 0; c < kCoTile; ++c) acc[c] = 0.f;
+  const float* gb = g + (long long)b * Co * Ho * Ho;
+#pragma unroll
+  for (int kh = 0; kh < 3; ++kh) {
+    const int th = ih + 1 - kh;
+    if (th < 0 || th % s) continue;
+    const int oh = th / s;
+    if (oh >= Ho) continue;
+#pragma unroll
+    for (int kw = 0; kw < 3; ++kw) {
+      const int tw_ = iw + 1 - kw;
+      if (tw_ < 0 || tw_ % s) continue;
+      const int ow = tw_ / s;
+      if (ow >= Ho) continue;
+      const int k = kh * 3 + kw;
+      for (int co = 0; co < Co; ++co) {
+        const float gv = __ldg(gb + ((long long)co * Ho + oh) * Ho + ow);
+#pragma unroll
+        for (int c = 0; c < kCoTile; ++c) acc[c] = fmaf(gv, ws[(c * Co + co) * 9 + k], acc[c]);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < kCoTile; ++c) {
+    if (ci0 + c >= Ci) continue;
+    const long long i = ((long long)b * Ci + ci0 + c) * H * H + p;
+    gx[i] = xin[i] > 0.f ? acc[c] : 0.f;
+  }
+}
+
+// dW[co][ci][k] += sum over a chunk of samples and all output pixels of
+// g[b][co][o] x[b][ci][o*s + k - 1]; db[co] likewise from g.  Grid
+// (Co, ceil(Ci/4), sample chunks); one block reduces and adds atomically.
+constexpr int kWgCi = 4;
+__global__ void __launch_bounds__(256) k_conv_bwd_weight(const float* __restrict__ g, const float* __restrict__ x,
+                                                         int Ci, int Co, int H, int s, int B, int chunk,
+                                                         long long woff, long long boff, float* __restrict__ grad) {
+  __shared__ float red[256];
+  const int co = blockIdx.x, ci0 = blockIdx.y * kWgCi;
+  const int b0 = blockIdx.z * chunk, b1 = min(B, b0 + chunk);
+  const int Ho = hout(H, s);
+  float acc[kWgCi * 9 + 1];
+#pragma unroll
+  for (int i = 0; i < kWgCi * 9 + 1; ++i) acc[i] = 0.f;
+  const long long n = (long long)(b1 - b0) * Ho * Ho;
+  for (long long e = threadIdx.x; e < n; e += blockDim.x) {
+    const int b = b0 + (int)(e / (Ho * Ho));
+    const int o = (int)(e % (Ho * Ho));
+    const int oh = o / Ho, ow = o - (o / Ho) * Ho;
+    const float gv = g[((long long)b * Co + co) * Ho * Ho + o];
+    if (gv == 0.f) continue;
+    acc[kWgCi * 9] += gv;
+#pragma unroll
+    for (int c = 0; c < kWgCi; ++c) {
+      if (ci0 + c >= Ci) break;
+      const float* xc = x + ((long long)b * Ci + ci0 + c) * H * H;
+#pragma unroll
+      for (int kh = 0; kh < 3; ++kh) {
+        const int ih = oh * s + kh - 1;
+        if (ih < 0 || ih >= H) continue;
+#pragma unroll
+        for (int kw = 0; kw < 3; ++kw) {
+          const int iw = ow * s + kw - 1;
+          if (iw < 0 || iw >= H) continue;
+          acc[c * 9 + kh * 3 + kw] = fmaf(gv, __ldg(xc + ih * H + iw), acc[c * 9 + kh * 3 + kw]);
+        }
+      }
+    }
+  }
+  for (int i = 0; i < kWgCi * 9 + 1; ++i) {
+    red[threadIdx.x] = acc[i];
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+      if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      if (i == kWgCi * 9) {
+        if (blockIdx.y == 0) atomicAdd(grad + boff + co, red[0]);
+      } else {
+        const int c = i / 9, k = i - (i / 9) * 9;
+        if (ci0 + c < Ci) atomicAdd(grad + woff + ((long long)co * Ci + ci0 + c) * 9 + k, red[0]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Adam (Kingma and Ba, 2015) on the float32 master weights, then their
+// bfloat16 copy (round to nearest even).  step is 1-based.
+__global__ void k_adam_flat(float* __restrict__ w, __nv_bfloat16* __restrict__ wb, const float* __restrict__ g,
+                            float* __restrict__ m, float* __restrict__ v, long long n, float lr, float b1, float b2,
+                            float eps, float c1, float c2) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  w[i] = wi;
+  wb[i] = __float2bfloat16_rn(wi);
+}
+
+__global__ void k_to_bf16(const float* __restrict__ w, __nv_bfloat16* __restrict__ wb, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) wb[i] = __float2bfloat16_rn(w[i]);
+}
+
+// standardise physical targets: t = (phys - offset) / scale
+__global__ void k_standardise(const float* __restrict__ phys, const float* __restrict__ scale,
+                              const float* __restrict__ offset, int n, float* __restrict__ t) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n * kOut) t[i] = (phys[i] - offset[i % kOut]) / scale[i % kOut];
+}
+
+// Workspace layout for a batch.
+struct EstWs {
+  size_t act[5], out, pooled, gpool, gA, gB, grad, target, scale, total;
+};
+size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+EstWs est_ws(int B) {
+  EstWs L{};
+  size_t o = 0;
+  const size_t sizes[5] = {(size_t)B * 3 * kSide * kSide, (size_t)B * 32 * 64 * 64, (size_t)B * 64 * 32 * 32,
+                           (size_t)B * 96 * 16 * 16, (size_t)B * 128 * 8 * 8};
+  L.act[0] = 0;  // the caller's features are read in place
+  for (int i = 1; i < 5; ++i) {
+    L.act[i] = o;
+    o += al(sizes[i] * sizeof(float));
+  }
+  L.out = o; o += al((size_t)B * kOut * sizeof(float));
+  L.pooled = o; o += al((size_t)B * 128 * sizeof(float));
+  L.gpool = o; o += al((size_t)B * 128 * sizeof(float));
+  L.gA = o; o += al(sizes[1] * sizeof(float));
+  L.gB = o; o += al(sizes[1] * sizeof(float));
+  L.grad = o; o += al((size_t)kMap.total * sizeof(float));
+  L.target = o; o += al((size_t)B * kOut * sizeof(float));
+  L.scale = o; o += al(2 * kOut * sizeof(float));
+  L.total = o;
+  return L;
+}
+
+cudaError_t net_forward(const __nv_bfloat16* wb, const float* w32, const float* feat, int B, char* ws, const EstWs& L,
+                        cudaStream_t s, const float* scale, const float* offset, float* phys) {
+  const float* x = feat;
+  for (int l = 0; l < 4; ++l) {
+    const LayerDef d = kLayers[l];
+    const int Ho = hout(d.hin, d.stride);
+    float* y = (float*)(ws + L.act[l + 1]);
+    dim3 grid((unsigned)((Ho * Ho + 255) / 256), (unsigned)((d.co + kCoTile - 1) / kCoTile), (unsigned)B);
+    const size_t smem = (size_t)kCoTile * d.ci * 9 * sizeof(float);
+    WO_LAUNCH("est_conv_fwd", s, (k_conv_fwd<<<grid, 256, smem, s>>>(x, wb, w32, kMap.w[l], kMap.b[l], d.ci, d.co,
+                                                                      d.hin, d.stride, y)));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    x = y;
+  }
+  WO_LAUNCH("est_head_fwd", s, (k_head_fwd<<<(unsigned)B, 128, 0, s>>>(x, wb, w32, 128, 64, (float*)(ws + L.pooled),
+                                                                       (float*)(ws + L.out), scale, offset, phys)));
+  return cudaGetLastError();
+}
+
+cudaError_t net_backward(const __nv_bfloat16* wb, const float* w32, const float* feat, const float* target, int B,
+                         char* ws, const EstWs& L, float* grad, float* loss, cudaStream_t s) {
+  cudaError_t e = net_forward(wb, w32, feat, B, ws, L, s, nullptr, nullptr, nullptr);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(grad, 0, (size_t)kMap.total * sizeof(float), s);
+  if (e != cudaSuccess) return e;
+  WO_LAUNCH("est_head_bwd", s, (k_head_bwd<<<1, 256, 0, s>>>((float*)(ws + L.out), target, (float*)(ws + L.pooled), wb,
+                                                             B, 128, grad, (float*)(ws + L.gpool), loss)));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  float* g = (float*)(ws + L.gA);
+  float* gnext = (float*)(ws + L.gB);
+  const long long n4 = (long long)B * 128 * 64;
+  WO_LAUNCH("est_unpool", s, (k_unpool<<<(unsigned)((n4 + 255) / 256), 256, 0, s>>>((float*)(ws + L.gpool),
+                                                                                     (float*)(ws + L.act[4]), 128, 64,
+                                                                                     n4, g)));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  for (int l = 3; l >= 0; --l) {
+    const LayerDef d = kLayers[l];
+    const float* xin = l == 0 ? feat : (const float*)(ws + L.act[l]);
+    const int Ho = hout(d.hin, d.stride);
+    // chunks of samples so that the grid has a few thousand blocks
+    const int per = (int)((long long)d.co * ((d.ci + kWgCi - 1) / kWgCi));
+    int chunks = (4096 + per - 1) / per;
+    if (chunks > B) chunks = B;
+    const int chunk = (B + chunks - 1) / chunks;
+    chunks = (B + chunk - 1) / chunk;
+    dim3 gw((unsigned)d.co, (unsigned)((d.ci + kWgCi - 1) / kWgCi), (unsigned)chunks);
+    WO_LAUNCH("est_conv_bwd_w", s, (k_conv_bwd_weight<<<gw, 256, 0, s>>>(g, xin, d.ci, d.co, d.hin, d.stride, B, chunk,
+                                                                          kMap.w[l], kMap.b[l], grad)));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (l == 0) break;
+    dim3 gd((unsigned)((d.hin * d.hin + 255) / 256), (unsigned)((d.ci + kCoTile - 1) / kCoTile), (unsigned)B);
+    const size_t smem = (size_t)kCoTile * d.co * 9 * sizeof(float);
+    WO_LAUNCH("est_conv_bwd_x", s, (k_conv_bwd_data<<<gd, 256, smem, s>>>(g, wb, kMap.w[l], d.ci, d.co, d.hin,
+                                                                           d.stride, xin, gnext)));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    (void)Ho;
+    float* tmp = g;
+    g = gnext;
+    gnext = tmp;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+size_t est_param_count() { return (size_t)kMap.total; }
+size_t est_workspace_bytes(int B) { return est_ws(B).total; }
+
+cudaError_t est_features(const float2* spec, const wo_optics* optics, int n, int Z, int Y, int X, float* feat,
+                         cudaStream_t s) {
+  dim3 grid((unsigned)kSide, (unsigned)n);
+  WO_LAUNCH("est_features", s, (k_features<<<grid, 256, 0, s>>>(spec, optics, Z, Y, X, feat)));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  WO_LAUNCH("est_feat_norm", s, (k_feat_norm<<<(unsigned)n, 256, 0, s>>>(Z, feat)));
+  return cudaGetLastError();
+}
+
+cudaError_t est_thin_phantom(const float4* par, int n, int S, int Y, int X, float pixel, float dz, float* out,
+                             cudaStream_t s) {
+  dim3 grid((unsigned)(((long long)Y * X + 255) / 256), (unsigned)n);
+  WO_LAUNCH("thin_phantom", s, (k_thin_phantom<<<grid, 256, 0, s>>>(par, S, Y, X, pixel, dz, out)));
+  return cudaGetLastError();
+}
+
+cudaError_t est_to_bf16(const float* w, void* wb, cudaStream_t s) {
+  const long long n = kMap.total;
+  WO_LAUNCH("est_to_bf16", s, (k_to_bf16<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w, (__nv_bfloat16*)wb, n)));
+  return cudaGetLastError();
+}
+
+cudaError_t est_forward(const void* wb, const float* w32, const float* feat, int B, const float* h_scale,
+                        const float* h_offset, float* phys, void* ws, cudaStream_t s) {
+  const EstWs L = est_ws(B);
+  char* w = (char*)ws;
+  float* sc = (float*)(w + L.scale);
+  float hv[2 * kOut];
+  for (int k = 0; k < kOut; ++k) {
+    hv[k] = h_scale[k];
+    hv[kOut + k] = h_offset[k];
+  }
+  cudaError_t e = cudaMemcpyAsync(sc, hv, sizeof(hv), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  return net_forward((const __nv_bfloat16*)wb, w32, feat, B, w, L, s, sc, sc + kOut, phys);
+}
+
+cudaError_t est_backward(const void* wb, const float* w32, const float* feat, const float* phys_target, int B,
+                         const float* h_scale, const float* h_offset, float* grad, float* loss, void* ws,
+                         cudaStream_t s) {
+  const EstWs L = est_ws(B);
+  char* w = (char*)ws;
+  float* sc = (float*)(w + L.scale);
+  float hv[2 * kOut];
+  for (int k = 0; k < kOut; ++k) {
+    hv[k] = h_scale[k];
+    hv[kOut + k] = h_offset[k];
+  }
+  cudaError_t e = cudaMemcpyAsync(sc, hv, sizeof(hv), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  float* t = (float*)(w + L.target);
+  WO_LAUNCH("est_standardise", s, (k_standardise<<<(unsigned)((B * kOut + 255) / 256), 256, 0, s>>>(phys_target, sc,
+                                                                                                  sc + kOut, B, t)));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return net_backward((const __nv_bfloat16*)wb, w32, feat, t, B, w, L, grad ? grad : (float*)(w + L.grad), loss, s);
+}
+
+cudaError_t est_adam(float* w32, void* wb, const float* grad, float* m, float* v, int step, float lr, float b1,
+                     float b2, float eps, cudaStream_t s) {
+  const long long n = kMap.total;
+  const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+  WO_LAUNCH("est_adam", s, (k_adam_flat<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w32, (__nv_bfloat16*)wb, grad, m,
+                                                                                    v, n, lr, b1, b2, eps, c1, c2)));
+  return cudaGetLastError();
+}
+
+float* est_grad_buffer(void* ws, int B) { return (float*)((char*)ws + est_ws(B).grad); }
+
+}  // namespace wo
+
+using namespace wo;
+
+namespace {
+bool a16(const void* p) { return p && (((uintptr_t)p) & 15u) == 0; }
+bool a8(const void* p) { return p && (((uintptr_t)p) & 7u) == 0; }
+wo_status cs(cudaError_t e) { return e == cudaSuccess ? WO_OK : WO_ERR_CUDA; }
+bool scale_ok(const float* sc, const float* off) {
+  if (!sc || !off) return false;
+  for (int k = 0; k < 4; ++k)
+    if (!(sc[k] != 0.f) || !isfinite(sc[k]) || !isfinite(off[k])) return false;
+  return true;
+}
+}  // namespace
+
+extern "C" {
+
+size_t wo_est_param_count(void) { return est_param_count(); }
+
+size_t wo_est_workspace_bytes(int batch) {
+  if (batch < 1 || batch > 4096) return 0;
+  return est_workspace_bytes(batch);
+}
+
+wo_status wo_est_sync_bf16(const float* d_w32, void* d_wbf16, wo_stream stream) {
+  if (!a16(d_w32) || !a16(d_wbf16)) return WO_ERR_ARG;
+  return cs(est_to_bf16(d_w32, d_wbf16, (cudaStream_t)stream));
+}
+
+wo_status wo_est_forward(const void* d_wbf16, const float* d_w32, const float* d_feat, int batch,
+                         const float* h_scale, const float* h_offset, float* d_out, void* d_ws, size_t ws_bytes,
+                         wo_stream stream) {
+  if (batch < 1 || batch > 4096) return WO_ERR_ARG;
+  if (!a16(d_wbf16) || !a16(d_w32) || !a16(d_feat) || !a16(d_out) || !a16(d_ws)) return WO_ERR_ARG;
+  if (!scale_ok(h_scale, h_offset)) return WO_ERR_ARG;
+  if (ws_bytes < est_workspace_bytes(batch)) return WO_ERR_WORKSPACE;
+  return cs(est_forward(d_wbf16, d_w32, d_feat, batch, h_scale, h_offset, d_out, d_ws, (cudaStream_t)stream));
+}
+
+wo_status wo_est_backward(const void* d_wbf16, const float* d_w32, const float* d_feat, const float* d_target,
+                          int batch, const float* h_scale, const float* h_offset, float* d_grad, float* d_loss,
+                          void* d_ws, size_t ws_bytes, wo_stream stream) {
+  if (batch < 1 || batch > 4096) return WO_ERR_ARG;
+  if (!a16(d_wbf16) || !a16(d_w32) || !a16(d_feat) || !a16(d_target) || !a16(d_ws)) return WO_ERR_ARG;
+  if ((d_grad && !a16(d_grad)) || (d_loss && !a8(d_loss))) return WO_ERR_ARG;
+  if (!scale_ok(h_scale, h_offset)) return WO_ERR_ARG;
+  if (ws_bytes < est_workspace_bytes(batch)) return WO_ERR_WORKSPACE;
+  return cs(est_backward(d_wbf16, d_w32, d_feat, d_target, batch, h_scale, h_offset, d_grad, d_loss, d_ws,
+                         (cudaStream_t)stream));
+}
+
+wo_status wo_est_train_step(float* d_w32, void* d_wbf16, float* d_m, float* d_v, const float* d_feat,
+                            const float* d_target, int batch, const float* h_scale, const float* h_offset, int step,
+                            float lr, float* d_loss, void* d_ws, size_t ws_bytes, wo_stream stream) {
+  if (step < 1 || !(lr >= 0.f) || !isfinite(lr)) return WO_ERR_ARG;
+  if (!a16(d_m) || !a16(d_v)) return WO_ERR_ARG;
+  wo_status st = wo_est_backward(d_wbf16, d_w32, d_feat, d_target, batch, h_scale, h_offset, nullptr, d_loss, d_ws,
+                                 ws_bytes, stream);
+  if (st != WO_OK) return st;
+  return cs(est_adam(d_w32, d_wbf16, est_grad_buffer(d_ws, batch), d_m, d_v, step, lr, 0.9f, 0.999f, 1e-8f,
+                     (cudaStream_t)stream));
+}
+
+wo_status wo_est_features(const void* d_spec, const wo_optics* d_optics, int n_tiles, int Z, int Y, int X,
+                          float* d_feat, wo_stream stream) {
+  if (n_tiles < 1 || n_tiles > 65535 || Z < 2 || Z > 64 || Y < 2 || X < 2 || (X % 2)) return WO_ERR_SHAPE;
+  if (!a16(d_spec) || !a8(d_optics) || !a16(d_feat)) return WO_ERR_ARG;
+  return cs(est_features((const float2*)d_spec, d_optics, n_tiles, Z, Y, X, d_feat, (cudaStream_t)stream));
+}
+
+wo_status wo_thin_phantom(const float* d_params, int n_tiles, int n_spheres, int Y, int X, double pixel_um,
+                          double z_step_um, float* d_out, wo_stream stream) {
+  if (n_tiles < 1 || n_tiles > 65535 || n_spheres < 0 || Y < 1 || X < 1) return WO_ERR_SHAPE;
+  if (!(pixel_um > 0) || !(z_step_um > 0)) return WO_ERR_ARG;
+  if (!a16(d_params) || !a16(d_out)) return WO_ERR_ARG;
+  return cs(est_thin_phantom((const float4*)d_params, n_tiles, n_spheres, Y, X, (float)pixel_um, (float)z_step_um,
+                             d_out, (cudaStream_t)stream));
+}
+
+}  // extern "C"

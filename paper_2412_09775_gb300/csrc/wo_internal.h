@@ -134,6 +134,23 @@ cudaError_t zero_dc(float2* spec, int n_tiles, long long vol, cudaStream_t s);
 // mean of the tile's DC bins (background = the stack's mean).
 cudaError_t center_dc_planes(float2* spec, int n_tiles, int Z, long long plane, cudaStream_t s);
 
+// Learned optics estimator (wo_est.cu).
+size_t est_param_count();
+size_t est_workspace_bytes(int B);
+cudaError_t est_features(const float2* spec, const wo_optics* optics, int n, int Z, int Y, int X, float* feat,
+                         cudaStream_t s);
+cudaError_t est_thin_phantom(const float4* par, int n, int S, int Y, int X, float pixel, float dz, float* out,
+                             cudaStream_t s);
+cudaError_t est_to_bf16(const float* w, void* wb, cudaStream_t s);
+cudaError_t est_forward(const void* wb, const float* w32, const float* feat, int B, const float* h_scale,
+                        const float* h_offset, float* phys, void* ws, cudaStream_t s);
+cudaError_t est_backward(const void* wb, const float* w32, const float* feat, const float* phys_target, int B,
+                         const float* h_scale, const float* h_offset, float* grad, float* loss, void* ws,
+                         cudaStream_t s);
+cudaError_t est_adam(float* w32, void* wb, const float* grad, float* m, float* v, int step, float lr, float b1,
+                     float b2, float eps, cudaStream_t s);
+float* est_grad_buffer(void* ws, int B);
+
 // Tiles.
 cudaError_t tiles_gather(const float* field, int Z, int ty, int tx, int core, int halo,
                          float* tiles, cudaStream_t s);

@@ -194,28 +194,44 @@ def uniform_volume(seed: int, shape, lo=-1.0, hi=1.0) -> np.ndarray:
     return np.random.default_rng(seed).uniform(lo, hi, size=shape)
 
 
-def thin_phantom(seed: int, shape2d, o: dict | None = None, n_spheres: int = 40,
-                 r_range=(0.5, 2.0), dn_range=(0.005, 0.03)) -> np.ndarray:
-    """Thin specimen for the 2D (phase-from-defocus) model: spheres projected
-    along z onto the object plane, as the index increment of one plane of
-    thickness z_step: sum dn 2 sqrt(r^2 - rho^2) / z_step (float64 (Y, X)).
-    Centres are uniform over the periodic tile; radius and dn as in
-    ``sphere_phantom``."""
+def thin_sphere_params(seed: int, shape2d, o: dict | None = None, n_spheres: int = 40,
+                       r_range=(0.5, 2.0), dn_range=(0.005, 0.03)) -> np.ndarray:
+    """Sphere parameters of a thin specimen, (n_spheres, 4) float64 rows of
+    (centre y, centre x, radius, dn) in um: centres uniform over the periodic
+    tile, radius and dn as in ``sphere_phantom``."""
     o = WIDEFIELD_OPTICS if o is None else o
     rng = np.random.default_rng(seed)
     Y, X = shape2d
     p = o["pixel_um"]
+    out = np.zeros((n_spheres, 4))
+    for i in range(n_spheres):
+        out[i] = (rng.uniform(0, Y * p), rng.uniform(0, X * p), rng.uniform(*r_range), rng.uniform(*dn_range))
+    return out
+
+
+def thin_phantom_from_params(params: np.ndarray, shape2d, o: dict | None = None) -> np.ndarray:
+    """Spheres projected along z onto the object plane, as the index increment
+    of one plane of thickness z_step: sum dn 2 sqrt(r^2 - rho^2) / z_step
+    (float64 (Y, X), periodic minimum-image distances)."""
+    o = WIDEFIELD_OPTICS if o is None else o
+    Y, X = shape2d
+    p = o["pixel_um"]
     yy, xx = np.meshgrid(np.arange(Y) * p, np.arange(X) * p, indexing="ij")
     out = np.zeros((Y, X))
-    for _ in range(n_spheres):
-        cy, cx = rng.uniform(0, Y * p), rng.uniform(0, X * p)
-        r = rng.uniform(*r_range)
-        dn = rng.uniform(*dn_range)
+    for cy, cx, r, dn in params:
         dy = (yy - cy + 0.5 * Y * p) % (Y * p) - 0.5 * Y * p
         dx = (xx - cx + 0.5 * X * p) % (X * p) - 0.5 * X * p
         rho2 = dy * dy + dx * dx
         out += dn * 2.0 * np.sqrt(np.maximum(r * r - rho2, 0.0)) / o["z_step_um"]
     return out
+
+
+def thin_phantom(seed: int, shape2d, o: dict | None = None, n_spheres: int = 40,
+                 r_range=(0.5, 2.0), dn_range=(0.005, 0.03)) -> np.ndarray:
+    """Thin specimen for the 2D (phase-from-defocus) model: spheres projected
+    along z onto the object plane (``thin_sphere_params`` then
+    ``thin_phantom_from_params``)."""
+    return thin_phantom_from_params(thin_sphere_params(seed, shape2d, o, n_spheres, r_range, dn_range), shape2d, o)
 
 
 def aperture_optics(n_apertures: int = 9, ring_na: float = 0.6, na_ill: float = 0.15,
