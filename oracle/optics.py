@@ -17,7 +17,10 @@ Green's function, e^{ikr}/(4 pi r) = (i/4pi) Int d^2nu e^{i2pi(nu.r + eta|z|)}/e
   eta(nu) = sqrt(k_m^2 - |nu|^2) (axial frequency on the Ewald shell);
 * source pupil S = 1[|nu - t/lambda| <= NA_ill/lambda] (closed disk, t the tilt
   in NA units), or with a logistic edge one frequency bin wide for tuning the
-  illumination; detection pupil P = 1[|nu| <= NA_det/lambda];
+  illumination; detection pupil P = 1[|nu| <= NA_det/lambda], times
+  e^{i 2 pi W} for an aberrated detection pupil (Ext. Data Fig. 3b), W the sum
+  of Zernike polynomials in Noll's order and normalisation over the unit
+  pupil rho = |nu| lambda / NA_det, coefficients in waves;
 * the scattered arm carries the scalar Green's spectrum G = i/eta;
 * plane j of a stack sits at focal displacement z_j = k_j dz + defocus with
   k_j in FFT order, and every arm is propagated by e^{+i 2 pi eta z_j};
@@ -118,6 +121,72 @@ def detection_pupil(o: dict, Y: int, X: int) -> np.ndarray:
     return _disk(nu_y, nu_x, 0.0, 0.0, o["na_det"] / lam)
 
 
+def noll_nm(j: int):
+    """Radial order n and signed azimuthal order m of Noll's index j >= 1.
+
+    Orders are taken n = 0, 1, 2, ... and within an order |m| increasing; an
+    |m| > 0 takes two consecutive indices, the even one for cos(|m| phi)
+    (m > 0) and the odd one for sin(|m| phi) (m < 0).
+    """
+    if j < 1:
+        raise ValueError("Noll indices start at 1")
+    nxt = 1
+    n = 0
+    while True:
+        for am in range(n % 2, n + 1, 2):
+            idx = [nxt] if am == 0 else [nxt, nxt + 1]
+            nxt += len(idx)
+            for i in idx:
+                if i == j:
+                    return n, (0 if am == 0 else (am if i % 2 == 0 else -am))
+        n += 1
+
+
+def zernike_radial(n: int, am: int, rho):
+    """R_n^|m|(rho) = sum_s (-1)^s (n-s)! / (s! ((n+|m|)/2-s)! ((n-|m|)/2-s)!) rho^(n-2s)."""
+    from math import factorial
+    rho = np.asarray(rho, dtype=np.float64)
+    out = np.zeros_like(rho)
+    for s_ in range((n - am) // 2 + 1):
+        c = (-1) ** s_ * factorial(n - s_) / (factorial(s_) * factorial((n + am) // 2 - s_) *
+                                               factorial((n - am) // 2 - s_))
+        out = out + c * rho ** (n - 2 * s_)
+    return out
+
+
+def zernike(j: int, rho, phi):
+    """Noll's Z_j(rho, phi) with unit RMS over the unit disk:
+    sqrt(n+1) R_n^0 for m = 0, sqrt(2(n+1)) R_n^|m| cos(m phi) or sin(|m| phi)."""
+    n, m = noll_nm(j)
+    R = zernike_radial(n, abs(m), rho)
+    if m == 0:
+        return np.sqrt(n + 1.0) * R
+    ang = np.cos(m * phi) if m > 0 else np.sin(-m * phi)
+    return np.sqrt(2.0 * (n + 1.0)) * R * ang
+
+
+def aberration_phase(o: dict, Y: int, X: int) -> np.ndarray:
+    """W(nu) = sum_j c_j Z_j(|nu| lambda / NA_det, atan2(nu_y, nu_x)) in waves,
+    c_j = o["zernike"][j - 1]; zero without coefficients and outside P."""
+    coef = np.asarray(o.get("zernike", ()), dtype=np.float64)
+    W = np.zeros((Y, X))
+    if coef.size == 0:
+        return W
+    nu_y, nu_x = transverse_grid(Y, X, o["pixel_um"])
+    rho = np.sqrt(nu_x * nu_x + nu_y * nu_y) * o["lambda_um"] / o["na_det"]
+    phi = np.arctan2(nu_y, nu_x)
+    for j, c in enumerate(coef, start=1):
+        if c != 0.0:
+            W += c * zernike(j, rho, phi)
+    return W * detection_pupil(o, Y, X)
+
+
+def detection_pupil_complex(o: dict, Y: int, X: int) -> np.ndarray:
+    """The (possibly aberrated) detection pupil P e^{i 2 pi W} (complex128).
+    |P e^{i 2 pi W}|^2 = P^2, so the normalisations keep the binary P."""
+    return detection_pupil(o, Y, X) * np.exp(2j * np.pi * aberration_phase(o, Y, X))
+
+
 def axial_frequency(o: dict, Y: int, X: int) -> np.ndarray:
     """eta(nu) = sqrt(k_m^2 - |nu|^2); set to 0 outside the shell (never used there)."""
     km = o["n_medium"] / o["lambda_um"]
@@ -149,19 +218,20 @@ def arms(o: dict, shape):
     Z, Y, X = shape
     S = source_pupil(o, Y, X)
     P = detection_pupil(o, Y, X)
+    Pc = detection_pupil_complex(o, Y, X)
     eta = axial_frequency(o, Y, X)
     z = plane_displacements(Z, o["z_step_um"], o["defocus_um"])
     prop = np.exp(2j * np.pi * eta[None, :, :] * z[:, None, None])
     inv_eta = np.where(P > 0, 1.0 / np.where(eta > 0, eta, 1.0), 0.0)
-    A = (S * P)[None] * prop
-    B = (P * 1j * inv_eta)[None] * prop
+    A = (S * Pc)[None] * prop
+    B = (Pc * 1j * inv_eta)[None] * prop
     return A, B
 
 
 def fluor_arm(o: dict, shape):
     """Defocused detection pupil P_j = P e^{i2pi eta z_j} (complex128, (Z, Y, X))."""
     Z, Y, X = shape
-    P = detection_pupil(o, Y, X)
+    P = detection_pupil_complex(o, Y, X)
     eta = axial_frequency(o, Y, X)
     z = plane_displacements(Z, o["z_step_um"], o["defocus_um"])
     return P[None] * np.exp(2j * np.pi * eta[None, :, :] * z[:, None, None])

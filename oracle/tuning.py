@@ -149,7 +149,7 @@ def plane_tf_source_derivatives(o: dict, shape) -> dict:
     T = optics.TABLE1_LABELFREE
     out = {}
     for k, dS in optics.source_pupil_derivatives(o, Y, X).items():
-        At = (dS * P)[None] * prop
+        At = (dS * optics.detection_pupil_complex(o, Y, X))[None] * prop
         Dt = np.sum(dS * P * P)
         dH1 = c * optics.correlate(At, B) / D - H1 * Dt / D
         out[k] = T[0, 0] * dH1 + T[0, 1] * np.conj(optics.reflect(dH1))

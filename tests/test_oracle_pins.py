@@ -154,7 +154,7 @@ def test_hermitian_with_even_z_and_defocus():
 
 
 # ----------------------------------------------- P4 independent routes
-def _field_route(o, shape, m, dn_plane, kappa_plane):
+def _field_route(o, shape, m, dn_plane, kappa_plane, pupil=None):
     """First-Born fields per source point, summed incoherently.
 
     For each source point s (inside S and P) and data plane i the detector sees
@@ -163,10 +163,13 @@ def _field_route(o, shape, m, dn_plane, kappa_plane):
     displacement between focus and the object plane m, and F the 2D spectrum of
     dn + i kappa.  Label-free contrast is 2 Re(u0* us) summed over the source
     (Methods, unified framework), normalised by the direct background.
+    ``pupil``: a complex detection pupil (an aberrated one) applied to both
+    the direct wave, u0 -> pupil(s) u0, and the scattered field.
     """
     Z, Y, X = shape
     S = O.source_pupil(o, Y, X)
     P = O.detection_pupil(o, Y, X)
+    Pc = P if pupil is None else pupil
     eta = O.axial_frequency(o, Y, X)
     inv_eta = np.where(P > 0, 1.0 / np.where(eta > 0, eta, 1.0), 0.0)
     z = O.plane_displacements(Z, o["z_step_um"], o["defocus_um"])
@@ -182,8 +185,8 @@ def _field_route(o, shape, m, dn_plane, kappa_plane):
         Fs = np.roll(F, shift=(sy, sx), axis=(0, 1))  # F(nu - s)
         for i in range(Z):
             zi = z[(i - m) % Z]
-            u0 = np.exp(2j * np.pi * (ky[sy] * yy / Y + kx[sx] * xx / X + eta[sy, sx] * zi))
-            us = np.fft.ifft2(P * 1j * c * inv_eta * np.exp(2j * np.pi * eta * zi) * Fs)
+            u0 = Pc[sy, sx] * np.exp(2j * np.pi * (ky[sy] * yy / Y + kx[sx] * xx / X + eta[sy, sx] * zi))
+            us = np.fft.ifft2(Pc * 1j * c * inv_eta * np.exp(2j * np.pi * eta * zi) * Fs)
             out[i] += wgt * 2.0 * np.real(np.conj(u0) * us)
     return out / count
 
@@ -686,3 +689,132 @@ def test_estimator_features_properties():
     assert np.allclose(fb[0, :Z], fa[0, :Z][::-1], atol=1e-12)
     assert np.allclose(fb[1, : Z - 1], -fa[1, : Z - 1][::-1], atol=1e-12)
     assert np.allclose(E.tile_features(1 + 3.0 * (stack - 1), o)[0], fa[0], atol=1e-12)
+
+
+# ------------------------------------------------- aberrated detection pupils
+def _unit_pupil(o, Y, X):
+    nu_y, nu_x = O.transverse_grid(Y, X, o["pixel_um"])
+    R = o["na_det"] / o["lambda_um"]
+    return nu_x / R, nu_y / R
+
+
+def test_zernike_matches_nolls_table():
+    """Noll (1976), Table 1: the closed forms of the first polynomials."""
+    rng = np.random.default_rng(3)
+    rho = np.sqrt(rng.uniform(0, 1, 200))
+    phi = rng.uniform(-np.pi, np.pi, 200)
+    r, c, s_ = rho, np.cos, np.sin
+    table = {
+        1: np.ones_like(r), 2: 2 * r * c(phi), 3: 2 * r * s_(phi), 4: np.sqrt(3) * (2 * r**2 - 1),
+        5: np.sqrt(6) * r**2 * s_(2 * phi), 6: np.sqrt(6) * r**2 * c(2 * phi),
+        7: np.sqrt(8) * (3 * r**3 - 2 * r) * s_(phi), 8: np.sqrt(8) * (3 * r**3 - 2 * r) * c(phi),
+        9: np.sqrt(8) * r**3 * s_(3 * phi), 10: np.sqrt(8) * r**3 * c(3 * phi),
+        11: np.sqrt(5) * (6 * r**4 - 6 * r**2 + 1),
+        12: np.sqrt(10) * (4 * r**4 - 3 * r**2) * c(2 * phi), 13: np.sqrt(10) * (4 * r**4 - 3 * r**2) * s_(2 * phi),
+        14: np.sqrt(10) * r**4 * c(4 * phi), 15: np.sqrt(10) * r**4 * s_(4 * phi),
+        16: np.sqrt(12) * (10 * r**5 - 12 * r**3 + 3 * r) * c(phi),
+        17: np.sqrt(12) * (10 * r**5 - 12 * r**3 + 3 * r) * s_(phi),
+        22: np.sqrt(7) * (20 * r**6 - 30 * r**4 + 12 * r**2 - 1),
+    }
+    for j, want in table.items():
+        assert np.abs(O.zernike(j, rho, phi) - want).max() <= 1e-12, j
+
+
+def test_zernike_orthonormal_on_the_unit_disk():
+    """<Z_i, Z_j> = pi delta_ij for the first 36 (Gauss-Legendre in rho, exact
+    for these degrees; a uniform grid in phi, exact for trigonometric degree < 64)."""
+    xg, wg = np.polynomial.legendre.leggauss(16)
+    rho = 0.5 * (xg + 1.0)
+    w_r = 0.5 * wg * rho  # rho d rho
+    phi = np.arange(64) * 2 * np.pi / 64
+    R, PH = np.meshgrid(rho, phi, indexing="ij")
+    W = w_r[:, None] * (2 * np.pi / 64)
+    Zs = np.stack([O.zernike(j, R, PH) for j in range(1, 37)])
+    G = np.einsum("iab,jab,ab->ij", Zs, Zs, W) / np.pi
+    assert np.abs(G - np.eye(36)).max() <= 1e-12
+    # every (n, m) with n <= 7 and n - |m| even, exactly once
+    nm = [O.noll_nm(j) for j in range(1, 37)]
+    assert sorted(nm) == sorted((n, m) for n in range(8) for m in range(-n, n + 1, 2))
+
+
+def test_piston_leaves_every_tf_unchanged():
+    o = ph.optics(na_ill=0.6, tilt_x=0.05, defocus_um=0.3)
+    shape = (6, 24, 32)
+    ref = O.transfer_functions(o, shape)
+    got = O.transfer_functions(dict(o, zernike=[0.37]), shape)
+    for k in O.KINDS:
+        assert rel_l2(got[k], ref[k]) <= 1e-13, k
+
+
+@pytest.mark.parametrize("axis,shift", [("x", 2), ("y", -3)])
+def test_tilt_zernike_is_a_lateral_shift(axis, shift):
+    """W = c_2 Z_2 = 2 c_2 nu_x lambda / NA_det: the pupil gains e^{i 2 pi s nu_x}
+    with s = 2 c_2 lambda / NA_det, every PSF moves by -s, and every TF is
+    multiplied by e^{i 2 pi s q_x}.  With s a whole number of pixels that is
+    exact on the periodic grid (Z_3 likewise along y)."""
+    o = ph.optics(na_ill=0.5, tilt_x=0.04, tilt_y=-0.03, defocus_um=-0.2)
+    shape = (6, 24, 32)
+    Z, Y, X = shape
+    c = shift * o["pixel_um"] * o["na_det"] / (2.0 * o["lambda_um"])
+    coef = [0.0, c, 0.0] if axis == "x" else [0.0, 0.0, c]
+    ref = O.transfer_functions(o, shape)
+    got = O.transfer_functions(dict(o, zernike=coef), shape)
+    k = O.fft_indices(X)[None, None, :] if axis == "x" else O.fft_indices(Y)[None, :, None]
+    n = X if axis == "x" else Y
+    ramp = np.exp(2j * np.pi * shift * k / n)
+    for kind in O.KINDS:
+        assert rel_l2(got[kind], ref[kind] * ramp) <= 1e-12, kind
+
+
+def test_aberrated_forward_equals_source_point_field_sum():
+    """Astigmatism and coma (closed forms typed here, Cartesian) through the
+    field route against the TF model with the same Noll coefficients."""
+    o = ph.optics(na_ill=0.55, tilt_x=0.06, tilt_y=0.02, defocus_um=0.2)
+    shape = (5, 20, 24)
+    Z, Y, X = shape
+    c6, c8 = 0.21, -0.13
+    ux, uy = _unit_pupil(o, Y, X)
+    W = c6 * np.sqrt(6) * (ux * ux - uy * uy) + c8 * np.sqrt(8) * (3 * (ux * ux + uy * uy) - 2) * ux
+    P = O.detection_pupil(o, Y, X)
+    pupil = P * np.exp(2j * np.pi * W)
+    rng = np.random.default_rng(11)
+    dn = rng.normal(size=shape[1:]) * 1e-2
+    kap = rng.normal(size=shape[1:]) * 1e-3
+    oa = dict(o, zernike=[0, 0, 0, 0, 0, c6, 0, c8])
+    tfs = O.transfer_functions(oa, shape, ("phase", "absorption"))
+    modes, _, _ = model.widefield_system(tfs, ("phase", "absorption"))
+    f = np.zeros((2,) + shape)
+    f[0, 1] = dn
+    f[1, 1] = kap
+    d = model.forward(modes, f, [1.0])[0] - 1.0
+    assert rel_l2(d, _field_route(o, shape, 1, dn, kap, pupil)) <= 1e-12
+    # and the aberration matters: the unaberrated model is far from it
+    tf0 = O.transfer_functions(o, shape, ("phase", "absorption"))
+    d0 = model.forward(model.widefield_system(tf0, ("phase", "absorption"))[0], f, [1.0])[0] - 1.0
+    assert rel_l2(d0, d) >= 0.05
+
+
+def test_aberrated_fluorescence_point_is_psf():
+    """Spherical aberration (Z_11, typed here): the image of a point emitter is
+    |IDFT2(P e^{i 2 pi W} e^{i 2 pi eta z_j})|^2 per plane, unit sum."""
+    o = ph.optics(defocus_um=0.3)
+    shape = (6, 16, 20)
+    Z, Y, X = shape
+    c11 = 0.3
+    ux, uy = _unit_pupil(o, Y, X)
+    r2 = ux * ux + uy * uy
+    W = c11 * np.sqrt(5) * (6 * r2 * r2 - 6 * r2 + 1)
+    tfs = O.transfer_functions(dict(o, zernike=[0] * 10 + [c11]), shape, ("fluor",))
+    modes, _, _ = model.widefield_system(tfs, ("fluor",))
+    f = np.zeros((1,) + shape)
+    f[0, 0, 0, 0] = 1.0
+    d = model.forward(modes, f, [0.0])[0]
+    P = O.detection_pupil(o, Y, X) * np.exp(2j * np.pi * W)
+    eta = O.axial_frequency(o, Y, X)
+    z = O.plane_displacements(Z, o["z_step_um"], o["defocus_um"])
+    Ey = np.exp(2j * np.pi * np.outer(np.arange(Y), O.fft_indices(Y)) / Y)
+    Ex = np.exp(2j * np.pi * np.outer(np.arange(X), O.fft_indices(X)) / X)
+    psf = np.stack([np.abs(Ey @ (P * np.exp(2j * np.pi * eta * z[j])) @ Ex.T) ** 2 for j in range(Z)])
+    psf /= psf.sum()
+    assert rel_l2(d, psf) <= 1e-12
+    assert abs(np.sum(tfs["fluor"][0, 0, 0]) - 1.0) <= 1e-12  # H_fl(0) = 1 still
