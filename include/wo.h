@@ -155,6 +155,32 @@ wo_status wo_build_tf_device(const wo_optics *d_optics, int n_tiles, int Z, int 
                              unsigned kinds, void *d_tf, void *d_ws, size_t ws_bytes,
                              wo_stream stream);
 
+/* Rows a1-a4 with an aberrated detection pupil (row f4; Ext. Data Fig. 3b:
+ * the detection branch takes N_z Zernike coefficients besides NA_det and the
+ * defocus).  The detection pupil becomes
+ *   P = 1[|nu| <= NA_det/lambda] exp(i 2 pi W(nu)),  W = sum_j c_j Z_j(rho, phi),
+ *   rho = |nu| lambda / NA_det,  phi = atan2(nu_y, nu_x),
+ * Z_j Noll's Zernike polynomials (j = 1 piston, 2/3 tilt along x/y, 4
+ * defocus, 5/6 astigmatism, 7/8 coma, 11 primary spherical, ...; unit RMS
+ * over the pupil), c_j in waves.  The paper does not fix the ordering,
+ * normalisation or unit; this is the convention of this library.  P enters
+ * every arm (A = S P e^{...}, B = P (i/eta) e^{...}, P_j = P e^{...}), so
+ * every kind, including the derivative banks, takes the aberration; the
+ * normalisations use |P|^2, which it leaves unchanged.  The TFs lose the
+ * parity of the unaberrated ones and stay Hermitian (real PSFs).  A tilt
+ * c_2 = s NA_det / (2 lambda) shifts every PSF by -s along x.
+ * h_zernike: [n_tiles][n_zernike] host doubles (c_1 .. c_n_zernike per tile),
+ * read during the call; 0 <= n_zernike <= WO_MAX_ZERNIKE (radial orders up
+ * to 7); n_zernike = 0 is wo_build_tf.  Non-finite coefficients: WO_ERR_ARG.
+ * The workspace must hold wo_aberrated_workspace_bytes() bytes; the bank
+ * has the layout of wo_tf_bytes() and serves every operator as usual. */
+#define WO_MAX_ZERNIKE 36
+size_t wo_aberrated_workspace_bytes(int n_tiles, int Z, int Y, int X, unsigned kinds);
+wo_status wo_build_tf_aberrated(const wo_optics *h_optics, const double *h_zernike,
+                                int n_zernike, int n_tiles, int Z, int Y, int X,
+                                unsigned kinds, void *d_tf, void *d_ws, size_t ws_bytes,
+                                wo_stream stream);
+
 /* Row a5.  Forward model (Eq. fwd, Eq. fwd_block, Fourier form):
  *   d_c = IFFT3( sum_p H_cp FFT3(f_p) ) + b_c
  * d_f: [n_tiles][P][Z][Y][X] properties (input); d_data: [n_tiles][C][Z][Y][X]

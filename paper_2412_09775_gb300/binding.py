@@ -25,6 +25,7 @@ WO_ETA_RELATIVE, WO_ETA_ABSOLUTE = 0, 1
 WO_LOSS_DATA, WO_LOSS_MIDBAND = 0, 1
 WO_PASS_COLS = 0
 WO_ENGINE_DEFAULT, WO_ENGINE_SMEM, WO_ENGINE_HYBRID = 0, 1, 2
+WO_MAX_ZERNIKE = 36
 KIND_BITS = {"phase": WO_TF_PHASE, "absorption": WO_TF_ABSORPTION, "fluor": WO_TF_FLUOR,
              "phase_dz": WO_TF_PHASE_DZ, "planes": WO_TF_PLANES, "smooth_source": WO_TF_SMOOTH_SOURCE,
              "phase_grad": WO_TF_PHASE_GRAD}
@@ -60,6 +61,9 @@ def _load():
         "wo_workspace_bytes": (sz, [i, i, i, i, u]),
         "wo_build_tf": (i, [ctypes.POINTER(wo_optics), i, i, i, i, u, vp, vp, sz, vp]),
         "wo_build_tf_device": (i, [vp, i, i, i, i, u, vp, vp, sz, vp]),
+        "wo_aberrated_workspace_bytes": (sz, [i, i, i, i, u]),
+        "wo_build_tf_aberrated": (i, [ctypes.POINTER(wo_optics), ctypes.POINTER(ctypes.c_double), i, i, i, i, i, u,
+                                      vp, vp, sz, vp]),
         "wo_forward": (i, [vp, u, vp, fp, vp, i, i, i, i, vp, sz, vp]),
         "wo_forward_adjoint": (i, [vp, u, vp, fp, vp, i, i, i, i, vp, sz, vp]),
         "wo_reconstruct": (i, [vp, u, vp, fp, fp, i, i, vp, i, i, i, i, vp, sz, vp]),
@@ -98,6 +102,7 @@ def _load():
 
 _lib = _load()
 EXPORTED = ("wo_size_supported", "wo_tf_bytes", "wo_workspace_bytes", "wo_build_tf", "wo_build_tf_device",
+            "wo_aberrated_workspace_bytes", "wo_build_tf_aberrated",
             "wo_forward",
             "wo_forward_adjoint", "wo_reconstruct", "wo_reconstruct_static", "wo_spectrum",
             "wo_tune_objective", "wo_adam_optics", "wo_fused_workspace_bytes", "wo_reconstruct_fused",
@@ -187,6 +192,24 @@ def wo_build_tf_device(d_optics, n_tiles, Z, Y, X, kinds, tf, ws, stream=None):
     """TF build with the optics in device memory (a float64 tensor [n_tiles, 9])."""
     _check(_lib.wo_build_tf_device(_ptr(d_optics), n_tiles, Z, Y, X, kinds_mask(kinds), _ptr(tf), _ptr(ws),
                                    _nbytes(ws), _stream(stream)), "wo_build_tf_device")
+
+
+def wo_aberrated_workspace_bytes(n_tiles, Z, Y, X, kinds) -> int:
+    return int(_lib.wo_aberrated_workspace_bytes(n_tiles, Z, Y, X, kinds_mask(kinds)))
+
+
+def wo_build_tf_aberrated(optics_list, zernike, n_tiles, Z, Y, X, kinds, tf, ws, stream=None):
+    """TF build with aberrated detection pupils: ``zernike`` [n_tiles, n_zernike]
+    Noll coefficients in waves (c_1 first)."""
+    if len(optics_list) != n_tiles:
+        raise ValueError("one optics entry per tile")
+    arr = optics_array(optics_list)
+    nz = len(zernike[0]) if n_tiles > 0 and len(zernike) > 0 else 0
+    if len(zernike) != n_tiles or any(len(row) != nz for row in zernike):
+        raise ValueError("zernike: one row of equal length per tile")
+    flat = (ctypes.c_double * max(n_tiles * nz, 1))(*[float(v) for row in zernike for v in row])
+    _check(_lib.wo_build_tf_aberrated(arr, flat, nz, n_tiles, Z, Y, X, kinds_mask(kinds), _ptr(tf), _ptr(ws),
+                                      _nbytes(ws), _stream(stream)), "wo_build_tf_aberrated")
 
 
 def optics_tensor(optics_list, device="cuda"):

@@ -65,6 +65,7 @@ static bool size_ok(int n) {
 struct Sys {
   int n_kinds, lf_props, has_fl, C, P, n_arms;
   int want_phase, want_abs, want_dz, planes, want_grad, smooth;
+  int aberr;  // aberrated detection pupil (wo_build_tf_aberrated): set by the caller, not by kinds
 };
 
 static Sys system_of(unsigned kinds) {
@@ -110,7 +111,7 @@ static Sys system_of(unsigned kinds) {
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t optics, counts, rec, rec2, norm_part, norms, arms, build_end;
+  size_t optics, zern, counts, rec, rec2, norm_part, norms, arms, build_end;
   size_t specA, specB, op_end;
   size_t total;
   size_t tf_spectra, tf_stats, tf_total;
@@ -121,9 +122,10 @@ static Layout layout_of(int n, int Z, int Y, int X, const Sys& s) {
   const size_t Xh = (size_t)X / 2 + 1;
   size_t off = 0;
   L.optics = off; off += align256((size_t)n * sizeof(wo_optics));
+  L.zern = off; if (s.aberr) off += align256((size_t)n * WO_MAX_ZERNIKE * sizeof(double));
   L.counts = off; off += align256((size_t)n * 4 * sizeof(int));
   L.rec = off; off += align256((size_t)n * Y * X * sizeof(float4));
-  L.rec2 = off; if (s.want_grad) off += align256((size_t)n * Y * X * sizeof(float4));
+  L.rec2 = off; if (s.want_grad || s.aberr) off += align256((size_t)n * Y * X * sizeof(float4));
   const int rb = (Y + record_rows(Y, n) - 1) / record_rows(Y, n);
   L.norm_part = off; if (s.smooth) off += align256((size_t)n * rb * 4 * sizeof(float));
   L.norms = off; if (s.smooth) off += align256((size_t)n * 4 * sizeof(float));
@@ -214,6 +216,13 @@ size_t wo_tf_bytes(int n_tiles, int Z, int Y, int X, unsigned kinds) {
   return layout_of(n_tiles, Z, Y, X, system_of(kinds)).tf_total;
 }
 
+size_t wo_aberrated_workspace_bytes(int n_tiles, int Z, int Y, int X, unsigned kinds) {
+  if (check_shape(n_tiles, Z, Y, X, kinds) != WO_OK) return 0;
+  Sys s = system_of(kinds);
+  s.aberr = 1;
+  return layout_of(n_tiles, Z, Y, X, s).total;
+}
+
 size_t wo_workspace_bytes(int n_tiles, int Z, int Y, int X, unsigned kinds) {
   if (check_shape(n_tiles, Z, Y, X, kinds) != WO_OK) return 0;
   return layout_of(n_tiles, Z, Y, X, system_of(kinds)).total;
@@ -275,10 +284,14 @@ long long wo_launch_count(void) { return g_launches.load(); }
 // Shared body of wo_build_tf (optics copied from the host into the workspace)
 // and wo_build_tf_device (optics read in place from device memory).
 static wo_status build_tf_impl(const wo_optics* optics, bool on_host, int n_tiles, int Z, int Y, int X,
-                               unsigned kinds, void* d_tf, void* d_ws, size_t ws_bytes, wo_stream stream) {
+                               unsigned kinds, void* d_tf, void* d_ws, size_t ws_bytes, wo_stream stream,
+                               const double* h_zern = nullptr, int n_zern = 0) {
   wo_status st = check_shape(n_tiles, Z, Y, X, kinds);
   if (st != WO_OK) return st;
   if (!optics || !aligned16(d_tf) || !aligned16(d_ws)) return WO_ERR_ARG;
+  if (n_zern < 0 || n_zern > WO_MAX_ZERNIKE || (n_zern > 0 && !h_zern)) return WO_ERR_ARG;
+  for (long long i = 0; i < (long long)n_tiles * n_zern; ++i)
+    if (!isfinite(h_zern[i])) return WO_ERR_ARG;
   if (!on_host && (((uintptr_t)optics) & 7u)) return WO_ERR_ARG;
   if (on_host) {
     for (int t = 0; t < n_tiles; ++t) {
@@ -286,13 +299,16 @@ static wo_status build_tf_impl(const wo_optics* optics, bool on_host, int n_tile
       if (st != WO_OK) return st;
     }
   }
-  const Sys s = system_of(kinds);
+  Sys s = system_of(kinds);
+  s.aberr = n_zern > 0 ? 1 : 0;
   const Layout L = layout_of(n_tiles, Z, Y, X, s);
   if (ws_bytes < L.total) return WO_ERR_WORKSPACE;
   cudaStream_t cs = (cudaStream_t)stream;
   char* ws = (char*)d_ws;
   char* tfb = (char*)d_tf;
   TfArgs a{};
+  a.zern = s.aberr ? (const double*)(ws + L.zern) : nullptr;
+  a.n_zern = n_zern;
   a.optics = on_host ? (const wo_optics*)(ws + L.optics) : optics;
   a.counts = (int*)(ws + L.counts);
   a.rec = (float4*)(ws + L.rec);
@@ -312,6 +328,9 @@ static wo_status build_tf_impl(const wo_optics* optics, bool on_host, int n_tile
   a.rec_blocks = (Y + record_rows(Y, n_tiles) - 1) / record_rows(Y, n_tiles);
   if (on_host)
     WO_TRY(cudaMemcpyAsync((void*)a.optics, optics, (size_t)n_tiles * sizeof(wo_optics), cudaMemcpyHostToDevice, cs));
+  if (s.aberr)
+    WO_TRY(cudaMemcpyAsync((void*)a.zern, h_zern, (size_t)n_tiles * n_zern * sizeof(double), cudaMemcpyHostToDevice,
+                           cs));
   WO_TRY(cudaMemsetAsync(a.counts, 0, (size_t)n_tiles * 4 * sizeof(int), cs));
   WO_TRY(cudaMemsetAsync(a.stats, 0, (size_t)n_tiles * 8 * sizeof(float), cs));
   WO_TRY(tf_pupil_record(a, cs));
@@ -334,6 +353,12 @@ wo_status wo_build_tf(const wo_optics* h_optics, int n_tiles, int Z, int Y, int 
 wo_status wo_build_tf_device(const wo_optics* d_optics, int n_tiles, int Z, int Y, int X, unsigned kinds,
                              void* d_tf, void* d_ws, size_t ws_bytes, wo_stream stream) {
   return build_tf_impl(d_optics, false, n_tiles, Z, Y, X, kinds, d_tf, d_ws, ws_bytes, stream);
+}
+
+wo_status wo_build_tf_aberrated(const wo_optics* h_optics, const double* h_zernike, int n_zernike, int n_tiles,
+                                int Z, int Y, int X, unsigned kinds, void* d_tf, void* d_ws, size_t ws_bytes,
+                                wo_stream stream) {
+  return build_tf_impl(h_optics, true, n_tiles, Z, Y, X, kinds, d_tf, d_ws, ws_bytes, stream, h_zernike, n_zernike);
 }
 
 // forward (op 0), adjoint (op 1), reconstruct (op 2)

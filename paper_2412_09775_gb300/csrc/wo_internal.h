@@ -92,7 +92,9 @@ struct TfArgs {
   int want_dz;              // phase TF and dH/d(defocus): arms A, B, A', B'; kinds 2
   int want_grad;            // plus dH/d(tilt_x, tilt_y, NA_ill): arms A_tx, A_ty, A_na; kinds 5
   int smooth;               // smooth-edged source pupil (S a float in [0, 1])
-  float4* rec2;             // [n_tiles][Y][X] (dS/dtx P, dS/dty P, dS/dNA P, 0), want_grad only
+  float4* rec2;             // [n_tiles][Y][X] (dS/dtx P, dS/dty P, dS/dNA P, W - rint(W)), want_grad or aberrated
+  const double* zern;       // [n_tiles][n_zern] Zernike coefficients (waves, Noll order), device copy
+  int n_zern;               // 0: unaberrated detection pupil
   float* norm_part;         // [n_tiles][record blocks][4] partial sums of S P and dS P
   float* norms;             // [n_tiles][4]: sum S P, then sum dS/dtheta P (smooth source)
   int rec_blocks;           // record blocks per tile

@@ -59,11 +59,64 @@ __device__ int optics_status(const wo_optics& o) {
   return WO_OK;
 }
 
+// Noll's index j >= 1 -> radial order n and |m|; cos(|m| phi) for even j,
+// sin(|m| phi) for odd j (m != 0).  Within order n (indices n(n+1)/2 + 1 ..
+// n(n+1)/2 + n + 1) |m| runs 0 or 1, then pairs of 2, 4, ... or 3, 5, ...
+__device__ __forceinline__ void noll_index(int j, int& n, int& am) {
+  n = 0;
+  while ((n + 1) * (n + 2) / 2 < j) ++n;
+  const int p = j - n * (n + 1) / 2 - 1;
+  am = 2 * ((p + 1 - (n & 1)) / 2) + (n & 1);
+}
+
+// Aberration phase W = sum_j c_j Z_j at the unit-pupil point (ux, uy),
+// |u| <= 1, in waves.  Z_j = N_j R_n^|m|(rho) {cos, sin}(|m| phi) with
+// rho^|m| {cos, sin}(|m| phi) = {Re, Im} (ux + i uy)^|m| and
+// R_n^|m|(rho) = rho^|m| P_k^(0,|m|)(2 rho^2 - 1), k = (n - |m|)/2, the Jacobi
+// polynomial by its three-term recurrence (stable in float on [-1, 1]).
+// zc: the tile's coefficients pre-multiplied by N_j; zn, zm: n and signed m.
+__device__ float aberration_waves(float ux, float uy, const float* zc, const signed char* zn,
+                                  const signed char* zm, int nz) {
+  const float x = 2.f * (ux * ux + uy * uy) - 1.f;
+  float W = 0.f;
+  for (int q = 0; q < nz; ++q) {
+    const float c = zc[q];
+    if (c == 0.f) continue;
+    const int m = zm[q], am = m < 0 ? -m : m, k = (zn[q] - am) / 2;
+    float re = 1.f, im = 0.f;
+    for (int i = 0; i < am; ++i) {
+      const float t = re * ux - im * uy;
+      im = fmaf(re, uy, im * ux);
+      re = t;
+    }
+    const float ang = m > 0 ? re : (m < 0 ? im : 1.f);
+    const float b = (float)am;
+    float p0 = 1.f, p1 = 0.5f * ((b + 2.f) * x - b);
+    float pk = k == 0 ? p0 : p1;
+    for (int i = 1; i < k; ++i) {  // P_{i+1} from P_i and P_{i-1}
+      const float s2 = 2.f * i + b;
+      const float a1 = 2.f * (i + 1) * (i + b + 1.f) * s2;
+      const float a2 = -(s2 + 1.f) * b * b;
+      const float a3 = s2 * (s2 + 1.f) * (s2 + 2.f);
+      const float a4 = 2.f * i * (i + b) * (s2 + 2.f);
+      const float p2 = ((a2 + a3 * x) * p1 - a4 * p0) / a1;
+      p0 = p1;
+      p1 = p2;
+      pk = p2;
+    }
+    W = fmaf(c * ang, pk, W);
+  }
+  return W;
+}
+
 __global__ void __launch_bounds__(256) k_pupil_record(TfArgs a, int kRecRows) {
   extern __shared__ double nu_x[];  // [X]
   __shared__ double nu_y[kRecRowsMax];
   __shared__ int part[2][8];
   __shared__ float fpart[4][8];
+  __shared__ float zc[WO_MAX_ZERNIKE];
+  __shared__ signed char zn[WO_MAX_ZERNIKE], zm[WO_MAX_ZERNIKE];
+  const bool want_rec2 = a.want_grad || a.n_zern > 0;
   const int Y = a.Y, X = a.X;
   const int t = blockIdx.y;
   const int y0 = blockIdx.x * kRecRows;
@@ -79,7 +132,7 @@ __global__ void __launch_bounds__(256) k_pupil_record(TfArgs a, int kRecRows) {
       if (y0 + yy >= Y) continue;
       const long long i = ((long long)t * Y + y0 + yy) * X + (e - yy * X);
       rec[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (a.want_grad) a.rec2[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (want_rec2) a.rec2[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     if (a.smooth && threadIdx.x < 4) a.norm_part[((long long)t * a.rec_blocks + blockIdx.x) * 4 + threadIdx.x] = 0.f;
     if (blockIdx.x == 0 && threadIdx.x == 0) reinterpret_cast<int*>(a.stats)[(long long)t * 8 + 4] = status;
@@ -89,6 +142,15 @@ __global__ void __launch_bounds__(256) k_pupil_record(TfArgs a, int kRecRows) {
   for (int x = threadIdx.x; x < X; x += 256) nu_x[x] = __ddiv_rn((double)fft_index(x, X), px);
   if (threadIdx.x < kRecRows && y0 + threadIdx.x < Y)
     nu_y[threadIdx.x] = __ddiv_rn((double)fft_index(y0 + threadIdx.x, Y), py);
+  if (threadIdx.x < a.n_zern) {
+    int n, am;
+    noll_index(threadIdx.x + 1, n, am);
+    const int m = am == 0 ? 0 : (((threadIdx.x + 1) & 1) ? -am : am);
+    const double norm = sqrt(am == 0 ? (double)(n + 1) : 2.0 * (n + 1));
+    zc[threadIdx.x] = (float)(a.zern[(long long)t * a.n_zern + threadIdx.x] * norm);
+    zn[threadIdx.x] = (signed char)n;
+    zm[threadIdx.x] = (signed char)m;
+  }
   __syncthreads();
   const double lam = o.lambda_um;
   const double rp = __ddiv_rn(o.na_det, lam), rp2 = __dmul_rn(rp, rp);
@@ -103,6 +165,7 @@ __global__ void __launch_bounds__(256) k_pupil_record(TfArgs a, int kRecRows) {
   // smooth source: S = 1 / (1 + exp(-(R - d) / w)), w one frequency bin of the
   // coarser axis, and its derivatives in tilt and NA_ill
   const float rsf = (float)rs, lamf = (float)lam;
+  const float inv_rp = (float)(1.0 / rp);  // unit-pupil coordinates of the aberration
   const float wedge = (float)(1.0 / ((double)min(Y, X) * o.pixel_um));
   int n_sp = 0, n_p = 0, kx_band = -1;
   float s_sp = 0.f, s_tx = 0.f, s_ty = 0.f, s_na = 0.f;
@@ -157,9 +220,14 @@ __global__ void __launch_bounds__(256) k_pupil_record(TfArgs a, int kRecRows) {
         binv = 1.0f / eh;
       }
     }
+    float wfrac = 0.f;
+    if (P && a.n_zern > 0) {
+      const float W = aberration_waves(vxf * inv_rp, vyf * inv_rp, zc, zn, zm, a.n_zern);
+      wfrac = W - rintf(W);
+    }
     const long long i = ((long long)t * Y + y0 + yy) * X + x;
     rec[i] = make_float4(eh, el, binv, S);  // S is 0 outside P
-    if (a.want_grad) a.rec2[i] = make_float4(dtx, dty, dna, 0.f);
+    if (want_rec2) a.rec2[i] = make_float4(dtx, dty, dna, wfrac);
     n_sp += (S != 0.f) ? 1 : 0;
     n_p += P ? 1 : 0;
     s_sp += S;
@@ -252,8 +320,15 @@ __global__ void __launch_bounds__(ColGeom<N>::NT, (1024 / ColGeom<N>::NT) > 1 ? 
     const int n = e / B, b = e % B;
     r[i] = (e < N * B && b < w) ? __ldg(rec + (long long)n * X + b) : make_float4(0.f, 0.f, 0.f, 0.f);
   }
+  // an aberrated detection pupil adds W (waves, reduced to [-1/2, 1/2]) to every arm's phase
+  const float* wrec = a.n_zern > 0 ? reinterpret_cast<const float*>(a.rec2 + (long long)t * N * X + x0) + 3 : nullptr;
 #pragma unroll
-  for (int i = 0; i < PER; ++i) sincospif(2.0f * phase_frac(r[i].x, r[i].y, zh, zl), &s_[i], &c_[i]);
+  for (int i = 0; i < PER; ++i) {
+    const int e = threadIdx.x + i * NT;
+    float ph = phase_frac(r[i].x, r[i].y, zh, zl);
+    if (wrec && e < N * B && (e % B) < w) ph += __ldg(wrec + 4 * ((long long)(e / B) * X + e % B));
+    sincospif(2.0f * ph, &s_[i], &c_[i]);
+  }
   // arms, in slot order: A, B (label-free), P (fluorescence), or
   // A, B, A' = i 2 pi eta A, B' = i 2 pi eta B (phase TF and its defocus
   // derivative), then A_tx, A_ty, A_NA (derivatives in the source parameters)

@@ -88,6 +88,28 @@ def test_build_tf_validation(B):
         assert lib.wo_build_tf(arr, n, Z, Y, X, kinds, tf, ws, wsb, None) == want
 
 
+def test_aberrated_build_validation(B):
+    lib = B._lib
+    good = B.optics_array([ph.optics(), ph.optics()])
+    fake = 1 << 20
+    big = 1 << 40
+    D = ctypes.c_double
+    z = (D * 8)(0.0, 0.0, 0.0, 0.1, 0.0, 0.05, 0.0, 0.0)
+    nan = (D * 8)(0.0, 0.0, 0.0, float("nan"), 0.0, 0.0, 0.0, 0.0)
+    ws_plain = B.wo_workspace_bytes(2, 16, 64, 64, 1)
+    ws_ab = B.wo_aberrated_workspace_bytes(2, 16, 64, 64, 1)
+    assert ws_ab > ws_plain > 0  # the aberration record and the coefficients
+    assert B.wo_aberrated_workspace_bytes(2, 16, 64, 64, 0) == 0
+    f = lib.wo_build_tf_aberrated
+    assert f(good, z, 37, 2, 16, 64, 64, 1, fake, fake, big, None) == 1     # more than WO_MAX_ZERNIKE
+    assert f(good, z, -1, 2, 16, 64, 64, 1, fake, fake, big, None) == 1
+    assert f(good, None, 4, 2, 16, 64, 64, 1, fake, fake, big, None) == 1   # coefficients missing
+    assert f(good, nan, 4, 2, 16, 64, 64, 1, fake, fake, big, None) == 1    # non-finite coefficient
+    assert f(good, z, 4, 2, 16, 64, 64, 1, fake, fake, ws_ab - 1, None) == 8  # workspace too small
+    assert f(good, z, 4, 2, 16, 64, 40, 1, fake, fake, big, None) == 3      # X/2 = 20 unsupported
+    assert B.WO_MAX_ZERNIKE == 36
+
+
 def test_op_validation(B):
     lib = B._lib
     fake = 1 << 20
