@@ -71,3 +71,47 @@ def blend(tiles: np.ndarray, tiles_y: int, tiles_x: int, core: int, halo: int) -
             acc[:, ya:yb, xa:xb] += wt[None] * tiles[ty * tiles_x + tx][:, ya - y0: yb - y0, xa - x0: xb - x0]
             wsum[ya:yb, xa:xb] += wt
     return acc / wsum[None]
+
+
+# ------------------------------------------------------------------ padding
+PAD_MODES = ("zero", "mirror", "edge")
+
+
+def pad_index(i: np.ndarray, n: int, mode: str) -> np.ndarray:
+    """Source index of position i of an axis of length n padded on both sides
+    (-1: a zero).  mirror: reflection about the edge samples, -i and
+    2(n-1) - i, repeated with period 2(n-1); edge: the nearest sample."""
+    i = np.asarray(i)
+    inside = (i >= 0) & (i < n)
+    if mode == "zero":
+        return np.where(inside, i, -1)
+    if mode == "edge":
+        return np.clip(i, 0, n - 1)
+    if n == 1:
+        return np.zeros_like(i)
+    p = 2 * (n - 1)
+    r = np.mod(i, p)
+    return np.where(r < n, r, p - r)
+
+
+def pad(vol: np.ndarray, shape_p, mode: str) -> np.ndarray:
+    """(..., Z, Y, X) -> (..., Zp, Yp, Xp): the input at offset ((Zp-Z)//2,
+    (Yp-Y)//2, (Xp-X)//2), the margin filled per ``mode`` (padding in place
+    of circular boundaries)."""
+    out = np.asarray(vol)
+    for ax, n_p in zip((-3, -2, -1), shape_p):
+        n = out.shape[ax]
+        idx = pad_index(np.arange(n_p) - (n_p - n) // 2, n, mode)
+        taken = np.take(out, np.maximum(idx, 0), axis=ax)
+        mask_shape = [1] * out.ndim
+        mask_shape[ax] = n_p
+        out = np.where((idx >= 0).reshape(mask_shape), taken, 0.0)
+    return out
+
+
+def crop(vol: np.ndarray, shape) -> np.ndarray:
+    """The window of ``shape`` at the offset ``pad`` uses."""
+    Zp, Yp, Xp = vol.shape[-3:]
+    Z, Y, X = shape
+    oz, oy, ox = (Zp - Z) // 2, (Yp - Y) // 2, (Xp - X) // 2
+    return vol[..., oz:oz + Z, oy:oy + Y, ox:ox + X]
