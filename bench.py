@@ -50,10 +50,10 @@ CPU_SAMPLE = (96, 256, 256)
 
 # Last ncu capture of DRAM traffic per launch (bytes) of the dominant kernel,
 # keyed by kernel family and the digest of its sources at capture time
-# (reported as null once a source changes).  tf_psf_rows: 151.1 MB read +
-# 104.6 MB written on the 48x512x512 case (profiles/tf_psf_rows_widefield_48x512x512.md),
-# scaled by 2 to the 96-plane launch (traffic grows with the planes processed).
-NCU_TRAFFIC = {"tf_psf_rows": {"bytes": 2 * (151.096320e6 + 104.627456e6), "digest": "5339ec2070fd668c"}}
+# (reported as null once a source changes).  tf_psf_rows: 302.1 MB read +
+# 255.0 MB written per launch on the 96x512x512 widefield step itself
+# (profiles/tf_psf_rows_dram_widefield_96x512x512.md).
+NCU_TRAFFIC = {"tf_psf_rows": {"bytes": 302073088 + 254975232, "digest": "41a8fd8ba9aec533"}}
 
 
 def kernel_digest(name: str) -> str:

@@ -280,6 +280,26 @@ wo_status wo_tile_gather(const float *d_field, int Z, int tiles_y, int tiles_x,
 wo_status wo_tile_blend(const float *d_tiles, int Z, int tiles_y, int tiles_x,
                         int core, int halo, float *d_field, wo_stream stream);
 
+/* Row f4, padding in place of circular boundaries.  The operators above are
+ * periodic in x, y and z (the Fourier form of Eq. fwd); to get other
+ * boundaries, pad the stacks to a larger supported grid, build the TFs and
+ * run the operator there, and crop the result back.
+ * wo_pad: d_in [n_vol][Z][Y][X] -> d_out [n_vol][Zp][Yp][Xp], the input at
+ * offset (oz, oy, ox) = ((Zp-Z)/2, (Yp-Y)/2, (Xp-X)/2) (integer halves), the
+ * margin filled per `mode`: WO_PAD_ZERO zeros, WO_PAD_EDGE the nearest edge
+ * sample, WO_PAD_MIRROR the mirror image about the edge samples (index -i
+ * and 2(n-1) - i, periodic with period 2(n-1) for margins wider than the
+ * volume; a length-1 axis repeats its sample).  wo_crop: the window of shape
+ * (Z, Y, X) at the same offset, d_in [n_vol][Zp][Yp][Xp] -> d_out
+ * [n_vol][Z][Y][X].  Out of place (WO_ERR_ARG if d_in == d_out; other
+ * overlaps are undefined); Zp >= Z >= 1 etc., else WO_ERR_SHAPE; any sizes
+ * (the FFT-length rules apply to the padded grid's operators, not here). */
+enum { WO_PAD_ZERO = 0, WO_PAD_MIRROR = 1, WO_PAD_EDGE = 2 };
+wo_status wo_pad(const float *d_in, int n_vol, int Z, int Y, int X, int Zp, int Yp, int Xp,
+                 int mode, float *d_out, wo_stream stream);
+wo_status wo_crop(const float *d_in, int n_vol, int Zp, int Yp, int Xp, int Z, int Y, int X,
+                  float *d_out, wo_stream stream);
+
 /* Defocus auto-tuning (Results, physics-guided auto-tuning of the optical
  * parameters theta; Fig. 2a(iv); Ext. Data Fig. 3; Methods, optical pooled
  * screen data: 2D phase from a z-stack, Adam, fixed regulariser).

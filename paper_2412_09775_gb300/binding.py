@@ -26,6 +26,7 @@ WO_LOSS_DATA, WO_LOSS_MIDBAND = 0, 1
 WO_PASS_COLS = 0
 WO_ENGINE_DEFAULT, WO_ENGINE_SMEM, WO_ENGINE_HYBRID = 0, 1, 2
 WO_MAX_ZERNIKE = 36
+WO_PAD_ZERO, WO_PAD_MIRROR, WO_PAD_EDGE = 0, 1, 2
 KIND_BITS = {"phase": WO_TF_PHASE, "absorption": WO_TF_ABSORPTION, "fluor": WO_TF_FLUOR,
              "phase_dz": WO_TF_PHASE_DZ, "planes": WO_TF_PLANES, "smooth_source": WO_TF_SMOOTH_SOURCE,
              "phase_grad": WO_TF_PHASE_GRAD}
@@ -87,6 +88,8 @@ def _load():
         "wo_autotune": (i, [i, i, i, i, u, vp, sz, vp]),
         "wo_tile_gather": (i, [vp, i, i, i, i, i, vp, vp]),
         "wo_tile_blend": (i, [vp, i, i, i, i, i, vp, vp]),
+        "wo_pad": (i, [vp, i, i, i, i, i, i, i, i, vp, vp]),
+        "wo_crop": (i, [vp, i, i, i, i, i, i, i, vp, vp]),
         "wo_status_string": (ctypes.c_char_p, [i]),
         "wo_profile_enable": (None, [i]),
         "wo_profile_read": (i, [ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong),
@@ -109,6 +112,7 @@ EXPORTED = ("wo_size_supported", "wo_tf_bytes", "wo_workspace_bytes", "wo_build_
             "wo_est_param_count", "wo_est_workspace_bytes", "wo_est_sync_bf16", "wo_est_forward", "wo_est_backward",
             "wo_est_train_step", "wo_est_features", "wo_thin_phantom",
             "wo_schedule_set", "wo_schedule_get", "wo_autotune", "wo_tile_gather", "wo_tile_blend",
+            "wo_pad", "wo_crop",
             "wo_status_string", "wo_profile_enable", "wo_profile_read", "wo_launch_count")
 
 
@@ -351,6 +355,14 @@ def wo_tile_gather(field, Z, tiles_y, tiles_x, core, halo, tiles, stream=None):
 def wo_tile_blend(tiles, Z, tiles_y, tiles_x, core, halo, field, stream=None):
     _check(_lib.wo_tile_blend(_ptr(tiles), Z, tiles_y, tiles_x, core, halo, _ptr(field), _stream(stream)),
            "wo_tile_blend")
+
+
+def wo_pad(vol, n_vol, Z, Y, X, Zp, Yp, Xp, mode, out, stream=None):
+    _check(_lib.wo_pad(_ptr(vol), n_vol, Z, Y, X, Zp, Yp, Xp, int(mode), _ptr(out), _stream(stream)), "wo_pad")
+
+
+def wo_crop(vol, n_vol, Zp, Yp, Xp, Z, Y, X, out, stream=None):
+    _check(_lib.wo_crop(_ptr(vol), n_vol, Zp, Yp, Xp, Z, Y, X, _ptr(out), _stream(stream)), "wo_crop")
 
 
 def wo_status_string(status: int) -> str:

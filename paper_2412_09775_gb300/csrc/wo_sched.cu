@@ -57,37 +57,51 @@ int wo_schedule_get(int pass, int n) {
 
 // Time every engine for the column transforms of length n over `planes`
 // planes of `ncols` columns (pitch ncols) in the scratch buffer; keep the
-// fastest.  Returns the engine kept, or -1 on a CUDA error.
+// fastest.  The engines are timed in alternating rounds (kReps launches per
+// round, after one untimed launch each) and each keeps its best round, so a
+// clock ramp or a cold cache early on does not decide the choice.  Returns
+// the engine kept, or -1 on a CUDA error.
 static int tune_cols(int n, int ncols, long long planes, float2* scratch, cudaStream_t s, float* best_ms) {
-  const int engines[2] = {WO_ENGINE_SMEM, WO_ENGINE_HYBRID};
+  constexpr int kEngines = 2, kRounds = 3, kReps = 8;
+  const int engines[kEngines] = {WO_ENGINE_SMEM, WO_ENGINE_HYBRID};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return -1;
-  int best = -1;
-  float best_t = 0.f;
+  float t_best[kEngines];
+  bool ok[kEngines];
   const int saved = g_cols_engine[n].load();
-  for (int engine : engines) {
-    if (engine == WO_ENGINE_HYBRID && !cols_hyb_supported(n)) continue;
-    g_cols_engine[n].store(engine);
-    const long long ps = (long long)n * ncols;
-    // one launch to set up the kernel, then kReps timed
-    constexpr int kReps = 8;
-    if (cols_c2c(n, false, scratch, ncols, ps, ncols, planes, s, "autotune") != cudaSuccess) break;
-    cudaEventRecord(e0, s);
-    for (int r = 0; r < kReps; ++r) cols_c2c(n, r & 1, scratch, ncols, ps, ncols, planes, s, "autotune");
-    cudaEventRecord(e1, s);
-    if (cudaEventSynchronize(e1) != cudaSuccess) break;
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (best < 0 || ms < best_t) {
-      best = engine;
-      best_t = ms;
+  const long long ps = (long long)n * ncols;
+  bool failed = false;
+  for (int k = 0; k < kEngines; ++k) {
+    t_best[k] = 0.f;
+    ok[k] = engines[k] != WO_ENGINE_HYBRID || cols_hyb_supported(n);
+    if (!ok[k]) continue;
+    g_cols_engine[n].store(engines[k]);
+    if (cols_c2c(n, false, scratch, ncols, ps, ncols, planes, s, "autotune") != cudaSuccess) failed = true;
+  }
+  for (int r = 0; r < kRounds && !failed; ++r) {
+    for (int k = 0; k < kEngines && !failed; ++k) {
+      if (!ok[k]) continue;
+      g_cols_engine[n].store(engines[k]);
+      cudaEventRecord(e0, s);
+      for (int q = 0; q < kReps; ++q) cols_c2c(n, q & 1, scratch, ncols, ps, ncols, planes, s, "autotune");
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        failed = true;
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (r == 0 || ms < t_best[k]) t_best[k] = ms;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  g_cols_engine[n].store(best < 0 ? saved : best);
-  if (best_ms) *best_ms = best_t / 8.f;
-  return best;
+  int best = -1;
+  for (int k = 0; k < kEngines && !failed; ++k)
+    if (ok[k] && (best < 0 || t_best[k] < t_best[best])) best = k;
+  g_cols_engine[n].store(best < 0 ? saved : engines[best]);
+  if (best_ms) *best_ms = best < 0 ? 0.f : t_best[best] / kReps;
+  return best < 0 ? -1 : engines[best];
 }
 
 wo_status wo_autotune(int n_tiles, int Z, int Y, int X, unsigned kinds, void* d_ws, size_t ws_bytes,

@@ -206,6 +206,18 @@ def test_tile_validation(B):
     assert lib.wo_tile_blend(fake, 4, 2, 2, 16, -1, fake, None) == 2
 
 
+def test_pad_validation(B):
+    lib = B._lib
+    fake, other = 1 << 20, 1 << 21
+    assert lib.wo_pad(fake, 1, 4, 4, 4, 8, 8, 8, 3, other, None) == 1     # unknown mode
+    assert lib.wo_pad(fake, 1, 4, 4, 4, 8, 8, 8, 0, fake, None) == 1      # in place
+    assert lib.wo_pad(None, 1, 4, 4, 4, 8, 8, 8, 0, other, None) == 1
+    assert lib.wo_pad(fake, 1, 4, 4, 4, 8, 3, 8, 1, other, None) == 2     # padded axis shorter
+    assert lib.wo_pad(fake, 0, 4, 4, 4, 8, 8, 8, 1, other, None) == 2
+    assert lib.wo_crop(fake, 1, 8, 8, 8, 4, 9, 4, other, None) == 2       # window larger than the volume
+    assert lib.wo_crop(fake, 1, 8, 8, 8, 4, 4, 4, fake, None) == 1
+
+
 def test_status_strings(B):
     for s in range(9):
         assert B.wo_status_string(s)
