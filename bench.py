@@ -83,6 +83,25 @@ def band_columns(o, X):
     return min(X, 2 * k + 1)
 
 
+def support_columns(o, kinds, Y, X):
+    """(k_y, k_x) columns of the half spectrum inside the TFs' support disk,
+    (k_y/Y)^2 + (k_x/X)^2 <= r^2 with r = R p + 2/min(Y, X) (cycles per pixel;
+    R = (NA_det + min(NA_det, NA_ill + |t|))/lambda label-free, 2 NA_det/lambda
+    fluorescence): the z passes read and transform only these, the others are
+    written as zeros."""
+    lam = o["lambda_um"]
+    tilt = float(np.hypot(o["tilt_x"], o["tilt_y"]))
+    R = 0.0
+    if {"phase", "absorption"} & set(kinds):
+        R = o["na_det"] + min(o["na_det"], o["na_ill"] + tilt)
+    if "fluor" in kinds:
+        R = max(R, 2 * o["na_det"])
+    r = R / lam * o["pixel_um"] + 2.0 / min(Y, X)
+    ky = np.where(np.arange(Y) < (Y + 1) // 2, np.arange(Y), np.arange(Y) - Y) / Y
+    kx = np.arange(X // 2 + 1) / X
+    return int(np.sum(ky[:, None] ** 2 + kx[None, :] ** 2 <= r * r))
+
+
 def algorithmic_bytes(shape, kinds, o):
     """Compulsory HBM bytes per launch of each kernel family for one step."""
     Z, Y, X = shape
@@ -94,16 +113,17 @@ def algorithmic_bytes(shape, kinds, o):
     n_arms = 2 * lf + (1 if "fluor" in kinds else 0)
     real = Z * Y * X * 4
     half = Z * Y * Xh * 8
+    inside = Z * support_columns(o, kinds, Y, X) * 8  # bytes of one volume inside the support
     arms = n_arms * Z * Y * band_columns(o, X) * 8
     return {
         "tf_pupil_record": Y * X * 16,
         "tf_arms": arms,
         "tf_psf_rows": arms + nk * half,
         "tf_ypass": 2 * nk * half,
-        "tf_zpass": 2 * nk * half,
+        "tf_zpass": nk * (half + inside),  # read inside the support, write everything
         "rows_r2c": C * (real + half),
         "y_fwd": 2 * C * half,
-        "z_fused": (C + nk + P) * half,
+        "z_fused": (C + nk) * inside + P * half,
         "y_inv": 2 * P * half,
         "rows_c2r": P * (half + real),
     }

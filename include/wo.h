@@ -115,7 +115,13 @@ int wo_size_supported(int n);
  * boundary) by a per-tile statistics block [n_tiles][8] of 32-bit words that
  * the TF build fills: float max_nu sum_lf|H|^2, float max_nu_perp
  * sum_kz sum_lf|H|^2, the same two for fluorescence (used by the relative
- * regulariser), int32 optics status (see wo_build_tf_device), three reserved.
+ * regulariser), int32 optics status (see wo_build_tf_device), float support
+ * radius r in cycles per pixel (every TF of the tile is zero where
+ * (k_y/Y)^2 + (k_x/X)^2 > r^2: r = (R p + 2/min(Y, X)), R = (NA_det +
+ * min(NA_det, NA_ill + |t|))/lambda for label-free kinds, 2 NA_det/lambda for
+ * fluorescence or the smooth source, the largest over the kinds present,
+ * two bins of margin), two reserved.  The z passes of the operators skip
+ * the frequencies outside that disk (their outputs are zero there).
  * 0 on invalid arguments. */
 size_t wo_tf_bytes(int n_tiles, int Z, int Y, int X, unsigned kinds);
 

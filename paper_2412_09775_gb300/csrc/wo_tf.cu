@@ -138,6 +138,16 @@ __global__ void __launch_bounds__(256) k_pupil_record(TfArgs a, int kRecRows) {
     if (blockIdx.x == 0 && threadIdx.x == 0) reinterpret_cast<int*>(a.stats)[(long long)t * 8 + 4] = status;
     return;  // uniform across the block
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    // support radius of the tile's TFs (cycles per pixel, two bins of margin):
+    // H1(q) needs nu in S and P and nu + q in P; the fluorescence TF and the
+    // smooth source (nonzero wherever P is) reach 2 NA_det / lambda
+    const double tilt = sqrt(o.tilt_x * o.tilt_x + o.tilt_y * o.tilt_y);
+    double r = 0.0;
+    if (a.lf_props > 0) r = a.smooth ? 2.0 * o.na_det : o.na_det + fmin(o.na_det, o.na_ill + tilt);
+    if (a.want_fl) r = fmax(r, 2.0 * o.na_det);
+    a.stats[(long long)t * 8 + 5] = (float)(r / o.lambda_um * o.pixel_um + 2.0 / (double)min(Y, X));
+  }
   const double px = __dmul_rn((double)X, o.pixel_um), py = __dmul_rn((double)Y, o.pixel_um);
   for (int x = threadIdx.x; x < X; x += 256) nu_x[x] = __ddiv_rn((double)fft_index(x, X), px);
   if (threadIdx.x < kRecRows && y0 + threadIdx.x < Y)
@@ -497,6 +507,10 @@ __global__ void __launch_bounds__(ZGeom<N, NK>::NT, ZGeom<N, NK>::MINB) k_tf_zpa
   const long long zs = (long long)Y * Xh;
   const long long vol = (long long)N * zs;
   float2* base = a.tf + (long long)t * NK * vol + (long long)y * Xh + x0;
+  if (outside_support(a.stats + (long long)t * 8, y, Y, x0, a.X)) {
+    zero_zcols<N, B, NT>(base, NK, vol, zs, w);  // the TFs vanish there: no transform
+    return;  // uniform across the CTA
+  }
   load_zcols<N, NK, B, NT>(buf, base, NK, vol, zs, w);
   make_twiddles<N>(tw);
   cp_async_wait_all();

@@ -22,8 +22,11 @@
 
 namespace wo {
 
+// Columns per CTA of the z kernels: 16 while the tile stays within 32 KB,
+// else the widest that fits 64 KB.  At 96 planes and three volumes 8 columns
+// (more CTAs resident per SM) measured faster than 16 and 4.
 __host__ __device__ constexpr int z_cols(int N, int NV) {
-  return (NV * N * 16 * 8 <= 64 * 1024) ? 16
+  return (NV * N * 16 * 8 <= 32 * 1024) ? 16
          : (NV * N * 8 * 8 <= 64 * 1024) ? 8
          : (NV * N * 4 * 8 <= 64 * 1024) ? 4
          : (NV * N * 2 * 8 <= 64 * 1024) ? 2
@@ -82,6 +85,32 @@ __device__ __forceinline__ void store_zcols(const float2* buf, float2* __restric
   }
 }
 
+// Zero the z columns of `nv` volumes (frequencies outside the TF support).
+template <int N, int B, int NT>
+__device__ __forceinline__ void zero_zcols(float2* __restrict__ dst, int nv, long long vol, long long zs, int w) {
+  constexpr int NSTEP = NT / B;
+  const int b = threadIdx.x % B, n0 = threadIdx.x / B;
+  if (b >= w) return;
+  for (int v = 0; v < nv; ++v) {
+    float2* g = dst + v * vol + (long long)n0 * zs + b;
+#pragma unroll 4
+    for (int n = n0; n < N; n += NSTEP) {
+      *g = make_float2(0.f, 0.f);
+      g += NSTEP * zs;
+    }
+  }
+}
+
+// True when the strip of columns k_x >= x0 of row y lies outside the tile's
+// TF support disk (k_y/Y)^2 + (k_x/X)^2 <= r^2 (r: statistics word 5, cycles
+// per pixel).  The nearest column of the strip is x0 (k_x >= 0 in the half
+// spectrum), so the whole strip is outside when x0 is.
+__device__ __forceinline__ bool outside_support(const float* stats, int y, int Y, int x0, int X) {
+  const float r = stats[5];
+  const float fy = (float)(y < (Y + 1) / 2 ? y : y - Y) / (float)Y, fx = (float)x0 / (float)X;
+  return fy * fy + fx * fx > r * r;
+}
+
 template <int N, int NI, int NO>
 __global__ void __launch_bounds__(ZGeom<N, (NI > NO ? NI : NO)>::NT, ZGeom<N, (NI > NO ? NI : NO)>::MINB)
     k_z_fused(const float2* __restrict__ in, float2* __restrict__ out, const float2* __restrict__ tf, ZOp op,
@@ -99,6 +128,11 @@ __global__ void __launch_bounds__(ZGeom<N, (NI > NO ? NI : NO)>::NT, ZGeom<N, (N
   const long long vol = (long long)N * zs;
   const long long col = (long long)y * Xh + x0;
   const int ntf = op.n_tf;
+  if (outside_support(op.stats + (long long)t * 8, y, Y, x0, 2 * (Xh - 1))) {
+    // every TF is zero here, so is every operator's output
+    zero_zcols<N, B, NT>(out + (long long)t * NO * vol + col, NO, vol, zs, w);
+    return;  // uniform across the CTA
+  }
   load_zcols<N, NV, B, NT>(buf, in + (long long)t * NI * vol + col, NI, vol, zs, w);
   load_zcols<N, 3, B, NT>(htf, tf + (long long)t * ntf * vol + col, ntf, vol, zs, w);
   make_twiddles<N>(tw);
@@ -187,13 +221,20 @@ __global__ void __launch_bounds__(ZGeom<N, NI>::NT, ZGeom<N, NI>::MINB)
   const long long zs = (long long)Y * Xh;
   const long long vol = (long long)N * zs;
   const long long col = (long long)y * Xh + x0;
+  const int L = op.lf_props;
+  if (outside_support(op.stats + (long long)t * 8, y, Y, x0, 2 * (Xh - 1))) {
+    if (threadIdx.x < w) {
+      float2* o = out + (long long)t * (L + op.has_fl) * Y * Xh + col + threadIdx.x;
+      for (int p = 0; p < L + op.has_fl; ++p) o[(long long)p * Y * Xh] = make_float2(0.f, 0.f);
+    }
+    return;  // uniform across the CTA
+  }
   load_zcols<N, NI, B, NT>(buf, in + (long long)t * NI * vol + col, NI, vol, zs, w);
   make_twiddles<N>(tw);
   cp_async_wait_all();
   __syncthreads();
   fft_smem<N, NI * B, NT, false, 1>(buf, NI * B, 1, tw);
 
-  const int L = op.lf_props;
   const int b = threadIdx.x % B, kk = threadIdx.x / B;
   float acc[NACC];
 #pragma unroll
