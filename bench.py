@@ -53,7 +53,7 @@ CPU_SAMPLE = (96, 256, 256)
 # (reported as null once a source changes).  tf_psf_rows: 302.1 MB read +
 # 255.2 MB written per launch on the 96x512x512 widefield step itself
 # (profiles/tf_psf_rows_dram_widefield_96x512x512.md).
-NCU_TRAFFIC = {"tf_psf_rows": {"bytes": 302074880 + 255188224, "digest": "d3d5616be234d1b0"}}
+NCU_TRAFFIC = {"tf_psf_rows": {"bytes": 302074880 + 255188224, "digest": "99d949fd1880d2f9"}}
 
 
 def kernel_digest(name: str) -> str:
@@ -62,7 +62,10 @@ def kernel_digest(name: str) -> str:
     src = {"z_fused": ["wo_zops.cuh", "wo_zops_a.cu", "wo_zops_b.cu"],
            "z_solve2d": ["wo_zops.cuh", "wo_zops_a.cu"], "rows_r2c": ["wo_rows.cu"], "rows_c2r": ["wo_rows.cu"],
            "y_fwd": ["wo_cols.cu"], "y_inv": ["wo_cols.cu"], "tf_ypass": ["wo_cols.cu"], "tf_arms": tf,
-           "tf_psf_rows": tf + ["wo_psf.cu", "wo_regfft.cuh"], "tf_zpass": tf + ["wo_zops.cuh"],
+           # the register-resident row kernel (rows of 32..512 points; wo_tf.cu holds only the
+           # shared-memory fallback for other lengths)
+           "tf_psf_rows": ["wo_psf.cu", "wo_regfft.cuh", "wo_tf.cuh", "wo_internal.h"],
+           "tf_zpass": tf + ["wo_zops.cuh"],
            "tf_pupil_record": tf, "tune_cols": ["wo_tune.cu"]}.get(name)
     if src is None:
         return ""
@@ -120,7 +123,7 @@ def algorithmic_bytes(shape, kinds, o):
         "tf_arms": arms,
         "tf_psf_rows": arms + nk * half,
         "tf_ypass": 2 * nk * half,
-        "tf_zpass": nk * (half + inside),  # read inside the support, write everything
+        "tf_zpass": 2 * nk * half,
         "rows_r2c": C * (real + half),
         "y_fwd": 2 * C * half,
         "z_fused": (C + nk) * inside + P * half,

@@ -507,10 +507,6 @@ __global__ void __launch_bounds__(ZGeom<N, NK>::NT, ZGeom<N, NK>::MINB) k_tf_zpa
   const long long zs = (long long)Y * Xh;
   const long long vol = (long long)N * zs;
   float2* base = a.tf + (long long)t * NK * vol + (long long)y * Xh + x0;
-  if (outside_support(a.stats + (long long)t * 8, y, Y, x0, a.X)) {
-    zero_zcols<N, B, NT>(base, NK, vol, zs, w);  // the TFs vanish there: no transform
-    return;  // uniform across the CTA
-  }
   load_zcols<N, NK, B, NT>(buf, base, NK, vol, zs, w);
   make_twiddles<N>(tw);
   cp_async_wait_all();
