@@ -16,8 +16,58 @@
 
 namespace wo {
 
-// In-register Stockham stages over L points (natural order in and out).  The
-// table tw holds w_N^m = exp(-2 pi i m / N) with N = L * STEP.
+// Twiddles of the in-register stages as compile-time constants.  Their
+// lengths NS * R (12, 16 or 24 for the row lengths here) divide 48, so every
+// one is a power of w_48 = exp(-2 pi i / 48); the table is evaluated at
+// compile time from the Taylor series of cos and sin on [-pi, pi] (30 terms,
+// far below double rounding there) and rounded to float.
+namespace twc {
+constexpr double kPi = 3.14159265358979323846264338327950288;
+constexpr double taylor_cos(double x) {
+  double t = 1.0, s = 1.0;
+  for (int n = 1; n < 30; ++n) {
+    t *= -x * x / ((2.0 * n - 1.0) * (2.0 * n));
+    s += t;
+  }
+  return s;
+}
+constexpr double taylor_sin(double x) {
+  double t = x, s = x;
+  for (int n = 1; n < 30; ++n) {
+    t *= -x * x / ((2.0 * n) * (2.0 * n + 1.0));
+    s += t;
+  }
+  return s;
+}
+struct W48 {
+  float re[48], im[48];  // exp(-2 pi i m / 48)
+};
+constexpr W48 make_w48() {
+  W48 w{};
+  for (int m = 0; m < 48; ++m) {
+    const double x = (m <= 24 ? m : m - 48) * (2.0 * kPi / 48.0);
+    w.re[m] = (float)taylor_cos(x);
+    w.im[m] = (float)(-taylor_sin(x));
+  }
+  return w;
+}
+}  // namespace twc
+__device__ constexpr twc::W48 kW48 = twc::make_w48();
+
+// a * w_DEN^e (forward) or a * w_DEN^-e (inverse); e and DEN are constants
+// once the stage loops are unrolled, so the trivial powers cost nothing.
+template <bool INV, int DEN>
+__device__ __forceinline__ float2 twiddle_mul(float2 a, int e) {
+  static_assert(48 % DEN == 0, "stage length must divide 48");
+  const int m = (e % DEN) * (48 / DEN);
+  if (m == 0) return a;
+  if (m == 24) return make_float2(-a.x, -a.y);
+  if (m == 12) return mul_mi<INV>(a);
+  if (m == 36) return mul_mi<!INV>(a);
+  return cmul(a, make_float2(kW48.re[m], INV ? -kW48.im[m] : kW48.im[m]));
+}
+
+// In-register Stockham stages over L points (natural order in and out).
 template <int L, int NS, bool INV, int STEP>
 __device__ __forceinline__ void reg_stages(float2 (&v)[L], const float2* tw) {
   if constexpr (NS < L) {
@@ -32,11 +82,7 @@ __device__ __forceinline__ void reg_stages(float2 (&v)[L], const float2* tw) {
       for (int r = 0; r < R; ++r) w[r] = v[j + r * M];
       if constexpr (NS > 1) {
 #pragma unroll
-        for (int r = 1; r < R; ++r) {
-          float2 t = tw[r * k * (L / (NS * R)) * STEP];
-          if (INV) t.y = -t.y;
-          w[r] = cmul(w[r], t);
-        }
+        for (int r = 1; r < R; ++r) w[r] = twiddle_mul<INV, NS * R>(w[r], r * k);
       }
       dftR<R, INV>(w);
       const int base = (j / NS) * NS * R + k;
