@@ -521,3 +521,54 @@ def test_autotune_keeps_results(env):
     finally:
         B.wo_schedule_set(B.WO_PASS_COLS, Y, 0)
         B.wo_schedule_set(B.WO_PASS_COLS, Z, 0)
+
+
+def test_shift_variant_field_full_size(env):
+    """The shift-variant workload at its full size, in the calls the bench
+    times: a 48 x 2048 x 2048 field cut into 256 tiles of 48 x 192 x 192
+    (128-px cores, 32-px halos), each tile's TF built from its own optics on
+    the device, reconstructed, and blended back.  Checked on samples the
+    oracle computes one by one: three whole tiles (gather bit for bit, the
+    reconstruction within 1e-4), and blended field values at pixels on tile
+    cores, overlaps and the field's edges."""
+    B, torch, dev = env
+    ty = tx = 16
+    core, halo = 128, 32
+    Z, E = 48, core + 2 * halo
+    n = ty * tx
+    o_list = ph.tile_optics(np.random.default_rng(3), n)
+    field_np = (1.0 + ph.uniform_volume(21, (Z, ty * core, tx * core), -0.01, 0.01)).astype(np.float32)
+    field = torch.from_numpy(field_np).to(dev)
+    optics = B.optics_tensor(o_list, dev)
+    tiles = torch.empty((n, Z, E, E), dtype=torch.float32, device=dev)
+    rec = torch.empty_like(tiles)
+    out = torch.empty_like(field)
+    tf, ws = B.alloc(n, Z, E, E, ("phase",), dev)
+    B.wo_tile_gather(field, Z, ty, tx, core, halo, tiles)
+    B.wo_build_tf_device(optics, n, Z, E, E, ("phase",), tf, ws)
+    B.wo_reconstruct(tf, ("phase",), tiles, None, [1e-3], B.WO_ETA_RELATIVE, B.WO_MODE_3D, rec, n, Z, E, E, ws)
+    B.wo_tile_blend(rec, Z, ty, tx, core, halo, out)
+    torch.cuda.synchronize()
+    for t in (0, 17, 255):  # a corner, an interior tile, the opposite corner
+        y0, x0 = OT.tile_origin(t // tx, t % tx, core, halo)
+        ys = OT.mirror(np.arange(y0, y0 + E), ty * core)
+        xs = OT.mirror(np.arange(x0, x0 + E), tx * core)
+        want_tile = field_np[:, ys][:, :, xs]
+        got_tile = tiles[t].cpu().numpy()
+        assert np.array_equal(got_tile, want_tile), t
+        modes, _, _ = OM.widefield_system(OO.transfer_functions(o_list[t], (Z, E, E), ("phase",)), ("phase",))
+        want = OM.reconstruct(modes, want_tile[None].astype(np.float64), 1e-3)[0]
+        assert rel_l2(rec[t].cpu().numpy(), want) <= TOL, t
+    w1 = OT.ramp(E, halo)
+    for z, y, x in ((0, 0, 0), (5, 64, 1000), (17, 127, 128), (31, 160, 96), (47, 2047, 2047), (23, 1024, 900),
+                    (40, 96, 2040)):
+        acc = wsum = 0.0
+        for a in range(ty):
+            for b in range(tx):
+                y0, x0 = OT.tile_origin(a, b, core, halo)
+                if y0 <= y < y0 + E and x0 <= x < x0 + E:
+                    wgt = w1[y - y0] * w1[x - x0]
+                    acc += wgt * float(rec[a * tx + b, z, y - y0, x - x0].item())
+                    wsum += wgt
+        got = float(out[z, y, x].item())
+        assert abs(got - acc / wsum) <= 1e-6 * max(1.0, abs(acc / wsum)), (z, y, x, got, acc / wsum)

@@ -314,3 +314,32 @@ def test_four_parameter_adam_from_nominal_under_a_cuda_graph(env):
     pb.run(A.default_schedule4(ol[0]), graph=True)
     err = np.abs(pb.params().cpu().numpy() - truth)
     assert np.all(err[:, 0] <= 0.05) and np.all(err[:, 1:] <= 0.01), err
+
+
+def test_four_parameter_gradient_full_batch(env):
+    """The auto-tuning workload's launch configuration: 256 tiles of
+    48 x 128 x 128 with their own optics in one batch (per-plane gradient
+    bank, smooth source, data-fidelity loss).  Loss and gradient of two
+    sampled tiles (the first and the last) against the oracle's loss and its
+    central differences."""
+    B, A, torch, dev = env
+    shape = (48, 128, 128)
+    n = 256
+    ol = [dict(o, smooth_source=True) for o in tiles(n, 77)]
+    start = [dict(o, defocus_um=0.0, tilt_x=0.0, tilt_y=0.0, na_ill=0.825) for o in ol]
+    eta = 1e-3
+    d = (1.0 + ph.uniform_volume(78, (n,) + shape, -0.01, 0.01)).astype(np.float32)
+    for t in (0, n - 1):  # physically consistent stacks where the oracle checks
+        d[t] = thin_stack(ol[t], shape, 79 + t).astype(np.float32)
+    pb = A.TuningProblem(torch.from_numpy(d).to(dev), start, eta, params="all")
+    pb.evaluate()
+    torch.cuda.synchronize()
+    val, grad = pb.value.cpu().numpy(), pb.grad.cpu().numpy()
+    assert np.all(np.isfinite(val)) and np.all(np.isfinite(grad))
+    for t in (0, n - 1):
+        dt = d[t].astype(np.float64)
+        want = OT.objective(start[t], dt, eta)
+        gwant = OT.gradient_fd_params(start[t], dt, eta, h=1e-4, loss="data")
+        assert abs(val[t] - want) <= 1e-4 * abs(want), (t, val[t], want)
+        scale = np.linalg.norm(gwant)
+        assert np.all(np.abs(grad[t] - gwant) <= 1e-3 * np.abs(gwant) + 1e-4 * scale), (t, grad[t], gwant)
