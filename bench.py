@@ -132,10 +132,19 @@ def algorithmic_bytes(shape, kinds, o):
     }
 
 
-def engines(*lengths):
+def pin_rows_engine(args, B, n):
+    """Pin the x passes' engine for n complex points (engine comparisons)."""
+    if args.rows_engine != "default":
+        B.wo_schedule_set(B.WO_PASS_ROWS, n, {"smem": 1, "hybrid": 2}[args.rows_engine])
+
+
+def engines(*lengths, rows=None):
     from paper_2412_09775_gb300 import binding as B
     names = {1: "smem", 2: "hybrid"}
-    return {f"cols_{n}": names.get(B.wo_schedule_get(B.WO_PASS_COLS, n), "?") for n in sorted(set(lengths))}
+    out = {f"cols_{n}": names.get(B.wo_schedule_get(B.WO_PASS_COLS, n), "?") for n in sorted(set(lengths))}
+    if rows is not None:
+        out[f"rows_{rows}"] = names.get(B.wo_schedule_get(B.WO_PASS_ROWS, rows), "?")
+    return out
 
 
 def peaks():
@@ -336,6 +345,7 @@ def run_gpu(args, rank, world, local_rank):
     o, f = make_inputs(SHAPE, seed=2 + rank)
     tf, ws = B.alloc(1, Z, Y, X, KINDS, dev)
     B.wo_autotune(1, Z, Y, X, KINDS, ws)  # engine per column-transform length, timed on these shapes
+    pin_rows_engine(args, B, X // 2)
     # synthetic data: forward model of the phantom (on the GPU) + seeded noise
     f_d = torch.from_numpy(f).to(dev)
     data = torch.empty((1, 2, Z, Y, X), dtype=torch.float32, device=dev)
@@ -478,7 +488,7 @@ def report(args, world, ms_max, e2e_ms, prof, launches, clk, tune=None):
         "config": {"workload": WORKLOAD if SHAPE == (96, 512, 512) else f"profiling case {Z}x{Y}x{X}", "Z": Z, "Y": Y, "X": X, "kinds": list(KINDS), "eta_relative": ETA,
                    "background": "channel mean", "tiles": 1, "parallelism": f"replicas x{world}",
                    "l2": "working set > L2 (no flush needed): data 201 MB, TF 303 MB, workspace 606 MB",
-                   "schedule": engines(Y, Z)},
+                   "schedule": engines(Y, Z, rows=X // 2)},
         "roofline": roofline,
         "kernels": per_kernel,
         "gpu_launches": int(launches),
@@ -555,6 +565,7 @@ def run_tiles(args, rank, world, local_rank):
     out = torch.empty_like(field)
     tf, ws = B.alloc(n, Z, E, E, ("phase",), dev)
     B.wo_autotune(n, Z, E, E, ("phase",), ws)
+    pin_rows_engine(args, B, E // 2)
 
     def step():
         B.wo_tile_gather(field, Z, ty, tx, TILE_CORE, TILE_HALO, tiles)
@@ -612,7 +623,7 @@ def run_tiles(args, rank, world, local_rank):
         "data": "synthetic (sphere phantom forward-simulated per tile with its own optics + 1e-3 noise)",
         "config": {"workload": TILES_WORKLOAD, "field": [Z, ty * TILE_CORE, tx * TILE_CORE], "tiles": n,
                    "tile": [Z, E, E], "eta_relative": 1e-3, "parallelism": f"replicas x{world}",
-                   "l2": "working set > L2 (field 805 MB, tiles 1.8 GB, TF 1.8 GB)", "schedule": engines(E, Z)},
+                   "l2": "working set > L2 (field 805 MB, tiles 1.8 GB, TF 1.8 GB)", "schedule": engines(E, Z, rows=E // 2)},
         "kernels": per_kernel, "gpu_launches": int(per_step_launches * args.steps),
         "clocks": nvml.summary(), "peak_hbm_gbs": peak,
     }
@@ -814,7 +825,7 @@ def autotune_leg(args, rank, world, local_rank, with_cpu=True):
                 "ms_per_step": round(e2e_ms, 3), "h2d_bytes_per_step": int(data.numel() * 4),
                 "d2h_bytes_per_step": int(n * 8)},
         "l2": "working set > L2: arms 6.4 GB, TF pair 1.6 GB, spectra 0.8 GB",
-        "schedule": engines(Y, Z),
+        "schedule": engines(Y, Z, rows=X // 2),
     }
     if with_cpu and rank == 0 and not args.no_cpu_baseline:
         d0 = data[0].double().cpu().numpy()
@@ -1031,6 +1042,8 @@ def main():
                     help="auto-tuning of (defocus, tilt_x, tilt_y, NA_ill) or of the defocus alone")
     ap.add_argument("--e2e-streams", type=int, default=3,
                     help="streams the end-to-end leg's consecutive steps go round (1: serial)")
+    ap.add_argument("--rows-engine", choices=["default", "smem", "hybrid"], default="default",
+                    help="engine of the x passes (default: the library's choice)")
     ap.add_argument("--shape", type=int, nargs=3, default=None,
                     help="override Z Y X (smaller cases for profiler captures only)")
     args = ap.parse_args()

@@ -448,11 +448,20 @@ wo_status wo_thin_phantom(const float *d_params, int n_tiles, int n_spheres, int
  * wo_schedule_get: the engine in use for (pass, n), -1 on bad arguments.
  * wo_autotune: times every engine of the column transforms that an entry
  * point on these shapes launches (lengths Y and Z, batches as large as the
- * workspace allows up to three volumes per tile), on the workspace (its
+ * workspace allows up to three volumes per tile) and of the x passes (X/2
+ * points, the rows of the same volumes), on the workspace (its
  * contents are destroyed), and keeps the fastest in the table.  It waits for
  * the stream (it measures with events), so it is not for graph capture; run
  * it once before capturing.  The table is process-wide. */
 enum { WO_PASS_COLS = 0 };
+/* WO_PASS_ROWS: the real <-> half-spectrum transforms along x (the first and
+ * last pass of every operator and of wo_spectrum), per n = X/2 complex
+ * points: WO_ENGINE_SMEM (rows staged in shared memory, Stockham stages) or
+ * WO_ENGINE_HYBRID (each row held by T lanes of one warp straight from global
+ * memory, register-resident four-step transform, the Hermitian split by warp
+ * shuffles; n = 32, 48, 64, 96, 128, 192, 256, 512; the default where it
+ * exists). */
+enum { WO_PASS_ROWS = 1 };
 enum { WO_ENGINE_DEFAULT = 0, WO_ENGINE_SMEM = 1, WO_ENGINE_HYBRID = 2 };
 wo_status wo_schedule_set(int pass, int n, int engine);
 int wo_schedule_get(int pass, int n);

@@ -110,6 +110,11 @@ cudaError_t cols_c2c_hyb(int N, bool inverse, float2* data, long long col_stride
                          long long nplanes, cudaStream_t s, const char* name, long long groups,
                          long long group_stride);
 int cols_engine(int n);  // WO_ENGINE_SMEM or WO_ENGINE_HYBRID
+int rows_engine(int n);  // engine of the x passes for n complex points (wo_rowsreg.cu: HYBRID)
+bool rows_reg_supported(int N);
+cudaError_t rows_r2c_reg(int N, const float* in, float2* out, long long nrows, RowBg bg, cudaStream_t s);
+cudaError_t rows_c2r_reg(int N, const float2* in, float* out, long long nrows, float scale, RowBg bg,
+                         cudaStream_t s);
 // Register-resident variant of the PSF-row pass for short rows (wo_psf.cu).
 bool psf_rows_reg_supported(int X, int n_arms);
 cudaError_t tf_psf_rows_reg(const TfArgs& a, cudaStream_t s);

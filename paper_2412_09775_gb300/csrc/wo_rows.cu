@@ -156,6 +156,7 @@ static cudaError_t launch_c2r(const float2* in, float* out, long long nrows, flo
 
 cudaError_t rows_r2c(int N, const float* in, float2* out, long long nrows, RowBg bg, cudaStream_t s) {
   if (nrows <= 0) return cudaSuccess;
+  if (rows_engine(N) == WO_ENGINE_HYBRID) return rows_r2c_reg(N, in, out, nrows, bg, s);
   switch (N) {
 #define WO_CASE(n) \
   case n:          \
@@ -172,6 +173,7 @@ cudaError_t rows_r2c(int N, const float* in, float2* out, long long nrows, RowBg
 cudaError_t rows_c2r(int N, const float2* in, float* out, long long nrows, float scale, RowBg bg,
                      cudaStream_t s) {
   if (nrows <= 0) return cudaSuccess;
+  if (rows_engine(N) == WO_ENGINE_HYBRID) return rows_c2r_reg(N, in, out, nrows, scale, bg, s);
   switch (N) {
 #define WO_CASE(n) \
   case n:          \

@@ -1,0 +1,189 @@
+// wo_rowsreg.cu - transforms along x (real <-> half spectrum) with register-
+// resident row transforms (the "hybrid" engine of the row passes).
+//
+// Same operations as k_rows_r2c / k_rows_c2r (wo_rows.cu): a real row of 2N
+// samples is read as N complex samples z[n] = x[2n] + i x[2n+1], transformed
+// with a length-N complex FFT and split into the N+1 bins of the real
+// transform,
+//   X[k] = (Z[k] + Z*[N-k])/2 - (i/2) e^{-2 pi i k/2N} (Z[k] - Z*[N-k]),
+//   X[N] = Re Z[0] - Im Z[0],
+// and back (Z[k] = A + iB, A = (X[k] + X*[N-k])/2,
+// B = (X[k] - X*[N-k]) e^{+2 pi i k/2N}/2, then a length-N inverse FFT).  Here
+// T lanes of one warp own a row, lane t holding points t + T m (the row
+// transforms of wo_regfft.cuh): the row is loaded straight into registers
+// (16 lanes read 16 consecutive complex samples), the partner value
+// Z*[N-k] comes from the lane that owns N - k by a shuffle, and only the
+// transform's transposes touch shared memory.
+#include "wo_fft.cuh"
+#include "wo_internal.h"
+#include "wo_regfft.cuh"
+
+namespace wo {
+
+namespace {
+
+constexpr int kRowThreads = 128;
+
+template <class P>
+struct RowRegGeom {
+  static constexpr int N = P::N, T = P::T, E = P::E;
+  static constexpr int RPC = kRowThreads / T;  // rows per CTA
+  static constexpr size_t SMEM = ((size_t)P::TW + 2 * (size_t)N + (size_t)RPC * P::SLICE) * sizeof(float2);
+};
+
+// Background constant of a row (see RowBg): mode 1 the channel's value, mode 2
+// the first sample of the row's (tile, channel) block.
+__device__ __forceinline__ float row_constant(const float* in, long long row, long long n2, const RowBg& bg) {
+  const long long grow = bg.row_offset + row;
+  if (bg.mode == 1) return bg.v[(grow / bg.rows_per_block) % bg.nchan];
+  if (bg.mode == 2) return __ldg(in + ((grow / bg.rows_per_block) * bg.rows_per_block - bg.row_offset) * n2);
+  return 0.f;
+}
+
+// Lane layout shared by both kernels: the partner lane owns N - k, and the
+// register it sends for our register m is mirror(m) (lane 0: point T m pairs
+// with T ((E - m) mod E); lane t > 0: t + T m pairs with (T - t) + T (E-1-m)).
+template <int E>
+__device__ __forceinline__ float2 mirror_reg(const float2 (&v)[E], int m, bool lane0) {
+  return lane0 ? v[(E - m) % E] : v[E - 1 - m];
+}
+
+template <class P>
+__global__ void __launch_bounds__(kRowThreads) k_rows_r2c_reg(const float* __restrict__ in, float2* __restrict__ out,
+                                                               long long nrows, RowBg bg) {
+  using G = RowRegGeom<P>;
+  constexpr int N = G::N, T = G::T, E = G::E, RPC = G::RPC;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;                  // P's twiddles
+  float2* tw2 = sm + P::TW;         // exp(-2 pi i m / 2N)
+  P::twiddles(tw);
+  make_twiddles<2 * N>(tw2);
+  __syncthreads();
+  const int t = threadIdx.x % T, r = threadIdx.x / T;
+  const int lane = threadIdx.x & 31;
+  const int partner = (lane - t) + (T - t) % T;
+  float2* S = sm + P::TW + 2 * N + r * P::SLICE;
+  const long long row = (long long)blockIdx.x * RPC + r;
+  const bool live = row < nrows;
+  const long long rr = live ? row : nrows - 1;  // tail lanes transform a valid row and store nothing
+  const float c = row_constant(in, rr, 2LL * N, bg);
+  const float2* src = reinterpret_cast<const float2*>(in + rr * (2LL * N)) + t;
+  float2 v[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const float2 x = __ldg(src + T * m);
+    v[m] = make_float2(x.x - c, x.y - c);
+  }
+  P::template fft<false>(v, tw, S, t);
+  float2* o = out + rr * (N + 1);
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const float2 mv = mirror_reg<E>(v, m, t == 0);
+    const float2 zc = make_float2(__shfl_sync(0xffffffffu, mv.x, partner), -__shfl_sync(0xffffffffu, mv.y, partner));
+    const int k = t + T * m;
+    const float2 s = cadd(v[m], zc);
+    const float2 u = cmul(tw2[k], csub(v[m], zc));
+    if (live) o[k] = make_float2(0.5f * (s.x + u.y), 0.5f * (s.y - u.x));
+  }
+  if (live && t == 0) o[N] = make_float2(v[0].x - v[0].y, 0.f);
+}
+
+template <class P>
+__global__ void __launch_bounds__(kRowThreads) k_rows_c2r_reg(const float2* __restrict__ in, float* __restrict__ out,
+                                                               long long nrows, float scale, RowBg bg) {
+  using G = RowRegGeom<P>;
+  constexpr int N = G::N, T = G::T, E = G::E, RPC = G::RPC;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* tw2 = sm + P::TW;
+  P::twiddles(tw);
+  make_twiddles<2 * N>(tw2);
+  __syncthreads();
+  const int t = threadIdx.x % T, r = threadIdx.x / T;
+  const int lane = threadIdx.x & 31;
+  const int partner = (lane - t) + (T - t) % T;
+  float2* S = sm + P::TW + 2 * N + r * P::SLICE;
+  const long long row = (long long)blockIdx.x * RPC + r;
+  const bool live = row < nrows;
+  const long long rr = live ? row : nrows - 1;
+  const float2* src = in + rr * (N + 1) + t;
+  float2 x[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) x[m] = __ldg(src + T * m);
+  const float2 xn = t == 0 ? __ldg(in + rr * (N + 1) + N) : make_float2(0.f, 0.f);  // X[N], partner of X[0]
+  float2 v[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const float2 mv = mirror_reg<E>(x, m, t == 0);
+    float2 xc = make_float2(__shfl_sync(0xffffffffu, mv.x, partner), -__shfl_sync(0xffffffffu, mv.y, partner));
+    if (t == 0 && m == 0) xc = make_float2(xn.x, -xn.y);
+    const int k = t + T * m;
+    const float2 a = make_float2(0.5f * (x[m].x + xc.x), 0.5f * (x[m].y + xc.y));
+    const float2 b = cmul(make_float2(0.5f * (x[m].x - xc.x), 0.5f * (x[m].y - xc.y)), cconj(tw2[k]));
+    v[m] = make_float2(a.x - b.y, a.y + b.x);
+  }
+  P::template fft<true>(v, tw, S, t);
+  if (!live) return;
+  const float cst = bg.mode == 1 ? bg.v[((bg.row_offset + rr) / bg.rows_per_block) % bg.nchan] : 0.f;
+  float2* o = reinterpret_cast<float2*>(out + rr * (2LL * N)) + t;
+#pragma unroll
+  for (int m = 0; m < E; ++m) o[T * m] = make_float2(v[m].x * scale + cst, v[m].y * scale + cst);
+}
+
+template <class P>
+cudaError_t launch_r2c_reg(const float* in, float2* out, long long nrows, RowBg bg, cudaStream_t s) {
+  using G = RowRegGeom<P>;
+  static cudaError_t attr = allow_smem(k_rows_r2c_reg<P>, G::SMEM);
+  if (attr != cudaSuccess) return attr;
+  const long long blocks = (nrows + G::RPC - 1) / G::RPC;
+  WO_LAUNCH("rows_r2c", s, (k_rows_r2c_reg<P><<<(unsigned)blocks, kRowThreads, G::SMEM, s>>>(in, out, nrows, bg)));
+  return cudaGetLastError();
+}
+
+template <class P>
+cudaError_t launch_c2r_reg(const float2* in, float* out, long long nrows, float scale, RowBg bg, cudaStream_t s) {
+  using G = RowRegGeom<P>;
+  static cudaError_t attr = allow_smem(k_rows_c2r_reg<P>, G::SMEM);
+  if (attr != cudaSuccess) return attr;
+  const long long blocks = (nrows + G::RPC - 1) / G::RPC;
+  WO_LAUNCH("rows_c2r", s,
+            (k_rows_c2r_reg<P><<<(unsigned)blocks, kRowThreads, G::SMEM, s>>>(in, out, nrows, scale, bg)));
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool rows_reg_supported(int N) {
+  return N == 32 || N == 48 || N == 64 || N == 96 || N == 128 || N == 192 || N == 256 || N == 512;
+}
+
+cudaError_t rows_r2c_reg(int N, const float* in, float2* out, long long nrows, RowBg bg, cudaStream_t s) {
+  switch (N) {
+    case 32: return launch_r2c_reg<Row2<32, 8>>(in, out, nrows, bg, s);
+    case 48: return launch_r2c_reg<Row2<48, 12>>(in, out, nrows, bg, s);
+    case 64: return launch_r2c_reg<Row2<64, 8>>(in, out, nrows, bg, s);
+    case 96: return launch_r2c_reg<Row2<96, 24>>(in, out, nrows, bg, s);
+    case 128: return launch_r2c_reg<Row2<128, 16>>(in, out, nrows, bg, s);
+    case 192: return launch_r2c_reg<Row2<192, 24>>(in, out, nrows, bg, s);
+    case 256: return launch_r2c_reg<Row2<256, 16>>(in, out, nrows, bg, s);
+    case 512: return launch_r2c_reg<Row512>(in, out, nrows, bg, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t rows_c2r_reg(int N, const float2* in, float* out, long long nrows, float scale, RowBg bg,
+                         cudaStream_t s) {
+  switch (N) {
+    case 32: return launch_c2r_reg<Row2<32, 8>>(in, out, nrows, scale, bg, s);
+    case 48: return launch_c2r_reg<Row2<48, 12>>(in, out, nrows, scale, bg, s);
+    case 64: return launch_c2r_reg<Row2<64, 8>>(in, out, nrows, scale, bg, s);
+    case 96: return launch_c2r_reg<Row2<96, 24>>(in, out, nrows, scale, bg, s);
+    case 128: return launch_c2r_reg<Row2<128, 16>>(in, out, nrows, scale, bg, s);
+    case 192: return launch_c2r_reg<Row2<192, 24>>(in, out, nrows, scale, bg, s);
+    case 256: return launch_c2r_reg<Row2<256, 16>>(in, out, nrows, scale, bg, s);
+    case 512: return launch_c2r_reg<Row512>(in, out, nrows, scale, bg, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace wo

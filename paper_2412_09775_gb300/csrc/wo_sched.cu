@@ -22,6 +22,7 @@ namespace wo {
 namespace {
 constexpr int kMaxLen = 2048;
 std::atomic<int> g_cols_engine[kMaxLen + 1];  // 0: default
+std::atomic<int> g_rows_engine[kMaxLen + 1];  // 0: default
 }  // namespace
 
 int cols_engine(int n) {
@@ -35,55 +36,44 @@ int cols_engine(int n) {
   return WO_ENGINE_SMEM;
 }
 
-}  // namespace wo
-
-using namespace wo;
-
-extern "C" {
-
-wo_status wo_schedule_set(int pass, int n, int engine) {
-  if (pass != WO_PASS_COLS) return WO_ERR_ARG;
-  if (n < 1 || n > kMaxLen) return WO_ERR_ARG;
-  if (engine != WO_ENGINE_DEFAULT && engine != WO_ENGINE_SMEM && engine != WO_ENGINE_HYBRID) return WO_ERR_ARG;
-  if (engine == WO_ENGINE_HYBRID && !cols_hyb_supported(n)) return WO_ERR_UNSUPPORTED_SIZE;
-  g_cols_engine[n].store(engine, std::memory_order_relaxed);
-  return WO_OK;
+int rows_engine(int n) {
+  if (n < 1 || n > kMaxLen || !rows_reg_supported(n)) return WO_ENGINE_SMEM;
+  const int e = g_rows_engine[n].load(std::memory_order_relaxed);
+  if (e == WO_ENGINE_SMEM || e == WO_ENGINE_HYBRID) return e;
+  // default: the register rows, faster on the workloads' x passes (256 and 96
+  // points: 0.127 -> 0.087 ms and 0.152 -> 0.112 ms on the widefield step)
+  return WO_ENGINE_HYBRID;
 }
 
-int wo_schedule_get(int pass, int n) {
-  if (pass != WO_PASS_COLS || n < 1 || n > kMaxLen) return -1;
-  return cols_engine(n);
-}
-
-// Time every engine for the column transforms of length n over `planes`
-// planes of `ncols` columns (pitch ncols) in the scratch buffer; keep the
-// fastest.  The engines are timed in alternating rounds (kReps launches per
-// round, after one untimed launch each) and each keeps its best round, so a
-// clock ramp or a cold cache early on does not decide the choice.  Returns
-// the engine kept, or -1 on a CUDA error.
-static int tune_cols(int n, int ncols, long long planes, float2* scratch, cudaStream_t s, float* best_ms) {
+// Time the two engines of one table entry on `run` (a batch of launches on
+// stream s) and keep the faster.  The engines are timed in alternating rounds
+// (kReps runs per round, after one untimed run each) and each keeps its best
+// round, so a clock ramp or a cold cache early on does not decide the
+// choice.  Returns the engine kept, or -1 on a CUDA error (the entry is then
+// restored).
+template <class Run>
+static int tune_entry(std::atomic<int>& entry, bool hybrid_ok, cudaStream_t s, Run run) {
   constexpr int kEngines = 2, kRounds = 3, kReps = 8;
   const int engines[kEngines] = {WO_ENGINE_SMEM, WO_ENGINE_HYBRID};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return -1;
   float t_best[kEngines];
   bool ok[kEngines];
-  const int saved = g_cols_engine[n].load();
-  const long long ps = (long long)n * ncols;
+  const int saved = entry.load();
   bool failed = false;
   for (int k = 0; k < kEngines; ++k) {
     t_best[k] = 0.f;
-    ok[k] = engines[k] != WO_ENGINE_HYBRID || cols_hyb_supported(n);
+    ok[k] = engines[k] != WO_ENGINE_HYBRID || hybrid_ok;
     if (!ok[k]) continue;
-    g_cols_engine[n].store(engines[k]);
-    if (cols_c2c(n, false, scratch, ncols, ps, ncols, planes, s, "autotune") != cudaSuccess) failed = true;
+    entry.store(engines[k]);
+    if (run(0) != cudaSuccess) failed = true;
   }
   for (int r = 0; r < kRounds && !failed; ++r) {
     for (int k = 0; k < kEngines && !failed; ++k) {
       if (!ok[k]) continue;
-      g_cols_engine[n].store(engines[k]);
+      entry.store(engines[k]);
       cudaEventRecord(e0, s);
-      for (int q = 0; q < kReps; ++q) cols_c2c(n, q & 1, scratch, ncols, ps, ncols, planes, s, "autotune");
+      for (int q = 0; q < kReps; ++q) run(q);
       cudaEventRecord(e1, s);
       if (cudaEventSynchronize(e1) != cudaSuccess) {
         failed = true;
@@ -99,9 +89,53 @@ static int tune_cols(int n, int ncols, long long planes, float2* scratch, cudaSt
   int best = -1;
   for (int k = 0; k < kEngines && !failed; ++k)
     if (ok[k] && (best < 0 || t_best[k] < t_best[best])) best = k;
-  g_cols_engine[n].store(best < 0 ? saved : engines[best]);
-  if (best_ms) *best_ms = best < 0 ? 0.f : t_best[best] / kReps;
+  entry.store(best < 0 ? saved : engines[best]);
   return best < 0 ? -1 : engines[best];
+}
+
+// Column transforms of length n over `planes` planes of `ncols` columns
+// (pitch ncols) in the scratch buffer, alternating directions.
+static int tune_cols(int n, int ncols, long long planes, float2* scratch, cudaStream_t s) {
+  const long long ps = (long long)n * ncols;
+  return tune_entry(g_cols_engine[n], cols_hyb_supported(n), s, [&](int q) {
+    return cols_c2c(n, q & 1, scratch, ncols, ps, ncols, planes, s, "autotune");
+  });
+}
+
+// x passes of n complex points over `rows` rows: a real-to-half-spectrum
+// pass and its inverse per run, on two disjoint parts of the scratch buffer.
+static int tune_rows(int n, long long rows, float2* scratch, cudaStream_t s) {
+  float* real = reinterpret_cast<float*>(scratch);
+  float2* half = scratch + (size_t)rows * n;  // after the 2n real samples of every row
+  const RowBg none{};
+  return tune_entry(g_rows_engine[n], rows_reg_supported(n), s, [&](int) {
+    cudaError_t e = rows_r2c(n, real, half, rows, none, s);
+    if (e != cudaSuccess) return e;
+    return rows_c2r(n, half, real, rows, 1.0f, none, s);
+  });
+}
+
+}  // namespace wo
+
+using namespace wo;
+
+extern "C" {
+
+wo_status wo_schedule_set(int pass, int n, int engine) {
+  if (pass != WO_PASS_COLS && pass != WO_PASS_ROWS) return WO_ERR_ARG;
+  if (n < 1 || n > kMaxLen) return WO_ERR_ARG;
+  if (engine != WO_ENGINE_DEFAULT && engine != WO_ENGINE_SMEM && engine != WO_ENGINE_HYBRID) return WO_ERR_ARG;
+  const bool hyb_ok = pass == WO_PASS_COLS ? cols_hyb_supported(n) : rows_reg_supported(n);
+  if (engine == WO_ENGINE_HYBRID && !hyb_ok) return WO_ERR_UNSUPPORTED_SIZE;
+  (pass == WO_PASS_COLS ? g_cols_engine : g_rows_engine)[n].store(engine, std::memory_order_relaxed);
+  return WO_OK;
+}
+
+int wo_schedule_get(int pass, int n) {
+  if (n < 1 || n > kMaxLen) return -1;
+  if (pass == WO_PASS_COLS) return cols_engine(n);
+  if (pass == WO_PASS_ROWS) return rows_engine(n);
+  return -1;
 }
 
 wo_status wo_autotune(int n_tiles, int Z, int Y, int X, unsigned kinds, void* d_ws, size_t ws_bytes,
@@ -119,10 +153,14 @@ wo_status wo_autotune(int n_tiles, int Z, int Y, int X, unsigned kinds, void* d_
   long long vols = (long long)((need / 2) / vol_bytes);
   if (vols < 1) vols = 1;
   if (vols > 3LL * n_tiles) vols = 3LL * n_tiles;
-  if (cudaMemsetAsync(scratch, 0, (size_t)vols * vol_bytes, s) != cudaSuccess) return WO_ERR_CUDA;
-  if (tune_cols(Y, Xh, vols * Z, scratch, s, nullptr) < 0) return WO_ERR_CUDA;
+  // the x-pass trial uses about twice the bytes of the column trials
+  if (cudaMemsetAsync(scratch, 0, 2 * (size_t)vols * vol_bytes, s) != cudaSuccess) return WO_ERR_CUDA;
+  if (tune_cols(Y, Xh, vols * Z, scratch, s) < 0) return WO_ERR_CUDA;
   // z transforms (3D data spectra): Y*Xh columns of length Z
-  if (Z > 1 && Z != Y && tune_cols(Z, Y * Xh, vols, scratch, s, nullptr) < 0) return WO_ERR_CUDA;
+  if (Z > 1 && Z != Y && tune_cols(Z, Y * Xh, vols, scratch, s) < 0) return WO_ERR_CUDA;
+  // x passes: the rows of the same volumes (2n real samples in, n+1 bins out
+  // per row fit the volumes' half spectra twice over)
+  if (rows_reg_supported(X / 2) && tune_rows(X / 2, vols * Z * Y, scratch, s) < 0) return WO_ERR_CUDA;
   return cudaStreamSynchronize(s) == cudaSuccess ? WO_OK : WO_ERR_CUDA;
 }
 

@@ -181,7 +181,14 @@ def test_tuning_validation(B):
 
 def test_schedule_table(B):
     lib = B._lib
-    assert lib.wo_schedule_set(1, 128, 1) == 1        # unknown pass
+    assert lib.wo_schedule_set(2, 128, 1) == 1        # unknown pass
+    assert lib.wo_schedule_set(1, 1024, 2) == 3       # no register row engine for 1024 points
+    assert lib.wo_schedule_get(2, 128) == -1
+    for n in (96, 256, 512):  # the x passes
+        assert lib.wo_schedule_set(1, n, 2) == 0 and lib.wo_schedule_get(1, n) == 2
+        assert lib.wo_schedule_set(1, n, 1) == 0 and lib.wo_schedule_get(1, n) == 1
+        assert lib.wo_schedule_set(1, n, 0) == 0 and lib.wo_schedule_get(1, n) in (1, 2)
+    assert lib.wo_schedule_get(1, 24) == 1
     assert lib.wo_schedule_set(0, 0, 1) == 1          # bad length
     assert lib.wo_schedule_set(0, 128, 7) == 1        # bad engine
     assert lib.wo_schedule_set(0, 1024, 2) == 3       # no hybrid engine for 1024

@@ -572,3 +572,46 @@ def test_shift_variant_field_full_size(env):
                     wsum += wgt
         got = float(out[z, y, x].item())
         assert abs(got - acc / wsum) <= 1e-6 * max(1.0, abs(acc / wsum)), (z, y, x, got, acc / wsum)
+
+
+@pytest.mark.parametrize("engine", [1, 2])
+@pytest.mark.parametrize("shape", [(4, 8, 64), (6, 12, 96), (4, 16, 128), (8, 6, 192), (4, 8, 256), (3, 4, 384),
+                                   (4, 8, 512), (2, 4, 1024)])
+def test_row_engines_match_oracle(env, shape, engine):
+    """The x passes pinned to each engine (shared-memory rows, register rows):
+    forward with backgrounds, adjoint, 3D and 2D reconstruction with the
+    channel-mean background, and wo_spectrum, against the oracle."""
+    B, torch, dev = env
+    Z, Y, X = shape
+    n = X // 2
+    kinds = OO.KINDS
+    try:
+        B.wo_schedule_set(B.WO_PASS_ROWS, n, engine)
+        assert B.wo_schedule_get(B.WO_PASS_ROWS, n) == engine
+        o = ph.optics(na_ill=0.7, tilt_y=0.04, defocus_um=-0.2)
+        tf, ws = check_tf(env, [o], shape, kinds)
+        modes, props, chans = OM.widefield_system(oracle_tf(o, shape, kinds), kinds)
+        f = ph.uniform_volume(9, (1, 3) + shape, -0.02, 0.02).astype(np.float32)
+        bg = [1.0, 0.0]
+        b = np.array(bg)[:, None, None, None]
+        d = run_forward(env, tf, ws, kinds, f, bg, shape)[0]
+        assert rel_l2(d - b, OM.forward(modes, f[0].astype(np.float64), bg) - b) <= TOL
+        dd = ph.uniform_volume(10, (2,) + shape, 0.5, 1.5).astype(np.float32)
+        fo = torch.empty((1, 3) + shape, dtype=torch.float32, device=dev)
+        B.wo_forward_adjoint(tf, kinds, torch.from_numpy(dd[None]).to(dev), bg, fo, 1, Z, Y, X, ws)
+        assert rel_l2(fo.cpu().numpy()[0], OM.adjoint(modes, dd.astype(np.float64), bg)) <= TOL
+        got = run_recon(env, tf, ws, kinds, dd[None], None, [1e-3, 1e-3], B.WO_ETA_RELATIVE, B.WO_MODE_3D, shape)
+        ref = OM.reconstruct(modes, dd.astype(np.float64), 1e-3)
+        for p in range(3):
+            assert rel_l2(got[0, p], ref[p]) <= TOL, p
+        pm, _, _ = OM.widefield_system(OO.plane_tfs(o, shape, kinds), kinds)
+        got2 = run_recon(env, tf, ws, kinds, dd[None], None, [1e-3, 1e-3], B.WO_ETA_RELATIVE, B.WO_MODE_2D, shape)
+        ref2 = OM.reconstruct_2d(pm, dd.astype(np.float64), 1e-3)
+        for p in range(3):
+            assert rel_l2(got2[0, p], ref2[p]) <= TOL, p
+        spec = torch.empty((1, Z, Y, X // 2 + 1), dtype=torch.complex64, device=dev)
+        B.wo_spectrum(torch.from_numpy(dd[:1]).to(dev), None, B.WO_MODE_2D, spec, 1, Z, Y, X)
+        want = OM.residual_spectrum(dd[0].astype(np.float64), float(np.mean(dd[0])), (1, 2))
+        assert rel_l2(spec.cpu().numpy()[0], want[..., : X // 2 + 1]) <= 1e-5
+    finally:
+        B.wo_schedule_set(B.WO_PASS_ROWS, n, 0)
