@@ -78,12 +78,21 @@ __global__ void __launch_bounds__(kPsfThreads, 4) k_psf_rows_reg(TfArgs a) {
   const long long kstride = (long long)a.Z * a.Y * Xh;
 
   constexpr bool DZ = MODE >= 1;
+  // the row's scale factors (float64 arithmetic, slow on this part) are
+  // formed once per row, by its first lane, and broadcast
+  float sc_row = 0.f, scf_row = 0.f;
+  if (lt == 0) {
+    if (DZ || lf) sc_row = lf_scale(a, (int)t);
+    if (!DZ && fl) scf_row = fl_scale(a, (int)t);
+  }
+  sc_row = __shfl_sync(0xffffffffu, sc_row, lane - lt);
+  scf_row = __shfl_sync(0xffffffffu, scf_row, lane - lt);
   float2 w[N1];
   float gre[MODE == 2 ? N1 : 1];  // Re g (unscaled), for the normalisation terms
   float2 vb[N1];                  // b, kept for the source-parameter arms
   int slot = 0;
   if (DZ || lf) {
-    const float sc = lf_scale(a, (int)t);
+    const float sc = sc_row;
     float2 va[N1];
     if constexpr (DZ) {
       // w = 2K (Re conj(a) b + i (Re conj(a) b' + Re conj(a') b)), arms A, B, A', B'
@@ -138,7 +147,7 @@ __global__ void __launch_bounds__(kPsfThreads, 4) k_psf_rows_reg(TfArgs a) {
   if constexpr (MODE == 2) {
     // source parameters: rows 2K (Re conj(a_theta) b - r_theta Re g), tilt_x
     // and tilt_y packed as one complex row, NA_ill as a real row
-    const float sc = lf_scale(a, (int)t);
+    const float sc = sc_row;
     const float rx = norm_dlog(a, (int)t, 0), ry = norm_dlog(a, (int)t, 1), rn = norm_dlog(a, (int)t, 2);
     float2 va[N1];
     load_arm<P>(va, a, t, rem, 4, kxm, lt);
@@ -174,7 +183,7 @@ __global__ void __launch_bounds__(kPsfThreads, 4) k_psf_rows_reg(TfArgs a) {
     }
   }
   if (!DZ && fl) {
-    const float scf = fl_scale(a, (int)t);
+    const float scf = scf_row;
     load_arm<P>(w, a, t, rem, lf ? 2 : 0, kxm, lt);
     P::template fft<true>(w, tw, S, lt);
 #pragma unroll
