@@ -70,14 +70,18 @@ __global__ void __launch_bounds__(kTuneThreads) k_tune_cols(const float2* __rest
   if (on) {
     const int y = (int)(c / Xh);
     x = (int)(c - (long long)y * Xh);
-    const wo_optics& o = optics[t];
-    const double p = o.pixel_um;
-    const double fy = (double)freq_index(y, Y) / ((double)Y * p), fx = (double)x / ((double)X * p);
-    if (loss == WO_LOSS_MIDBAND) {  // c/8 <= |nu| <= c/4, c = (NA_det + NA_ill)/lambda
-      const double r = sqrt(fx * fx + fy * fy), cut = (o.na_det + o.na_ill) / o.lambda_um;
-      on = r >= cut / 8.0 && r <= cut / 4.0;
-    } else if (nu_max > 0.f) {
-      on = fx * fx + fy * fy <= (double)nu_max * (double)nu_max;
+    // the band tests take the frequencies in float64, as the oracle does;
+    // the full loss needs none (float64 is slow on this part)
+    if (loss == WO_LOSS_MIDBAND || nu_max > 0.f) {
+      const wo_optics& o = optics[t];
+      const double p = o.pixel_um;
+      const double fy = (double)freq_index(y, Y) / ((double)Y * p), fx = (double)x / ((double)X * p);
+      if (loss == WO_LOSS_MIDBAND) {  // c/8 <= |nu| <= c/4, c = (NA_det + NA_ill)/lambda
+        const double r = sqrt(fx * fx + fy * fy), cut = (o.na_det + o.na_ill) / o.lambda_um;
+        on = r >= cut / 8.0 && r <= cut / 4.0;
+      } else {
+        on = fx * fx + fy * fy <= (double)nu_max * (double)nu_max;
+      }
     }
   }
   const double w = (x == 0 || 2 * x == X) ? 1.0 : 2.0;
