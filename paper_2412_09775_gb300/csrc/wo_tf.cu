@@ -317,10 +317,16 @@ __global__ void __launch_bounds__(ColGeom<N>::NT, (1024 / ColGeom<N>::NT) > 1 ? 
   for (int b = 0; b < w; ++b) active |= abs(fft_index(x0 + b, X)) <= kxmax;
   if (!active) return;  // uniform across the CTA
   make_twiddles<N>(tw);
-  const wo_optics o = a.optics[t];
-  const double zj = __dadd_rn(__dmul_rn((double)fft_index(j, Z), o.z_step_um), o.defocus_um);
-  const float zh = __double2float_rn(zj);
-  const float zl = __double2float_rn(__dsub_rn(zj, (double)zh));
+  // the plane's focal displacement as a float pair, formed in float64 by one
+  // lane of each warp (float64 is slow on this part) and broadcast
+  float zh = 0.f, zl = 0.f;
+  if ((threadIdx.x & 31) == 0) {
+    const double zj = __dadd_rn(__dmul_rn((double)fft_index(j, Z), a.optics[t].z_step_um), a.optics[t].defocus_um);
+    zh = __double2float_rn(zj);
+    zl = __double2float_rn(__dsub_rn(zj, (double)zh));
+  }
+  zh = __shfl_sync(0xffffffffu, zh, 0);
+  zl = __shfl_sync(0xffffffffu, zl, 0);
   const float4* rec = a.rec + (long long)t * N * X + x0;
   float4 r[PER];
   float s_[PER], c_[PER];
