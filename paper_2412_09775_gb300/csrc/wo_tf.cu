@@ -122,10 +122,29 @@ __global__ void __launch_bounds__(256) k_pupil_record(TfArgs a, int kRecRows) {
   const int y0 = blockIdx.x * kRecRows;
   const wo_optics o = a.optics[t];
   float4* rec = a.rec;
+  // The tile's status and float64 constants are formed once per block
+  // (float64 is slow on this part) and shared.
+  __shared__ int status_sh;
+  __shared__ double cst[8];  // rp2, cy, cx, rs, rs2, km2, 1/rp, wedge
+  if (threadIdx.x == 0) {
+    status_sh = optics_status(o);
+    const double lam = o.lambda_um;
+    const double rp = __ddiv_rn(o.na_det, lam);
+    cst[0] = __dmul_rn(rp, rp);
+    cst[1] = __ddiv_rn(o.tilt_y, lam);
+    cst[2] = __ddiv_rn(o.tilt_x, lam);
+    cst[3] = __ddiv_rn(o.na_ill, lam);
+    cst[4] = __dmul_rn(cst[3], cst[3]);
+    const double km = __ddiv_rn(o.n_medium, lam);
+    cst[5] = __dmul_rn(km, km);
+    cst[6] = 1.0 / rp;
+    cst[7] = 1.0 / ((double)min(Y, X) * o.pixel_um);
+  }
+  __syncthreads();
   // Invalid optics (possible only when they come from device memory): the
   // tile's record is all zero, so its transfer functions are zero, and its
   // status is left in the statistics block.
-  const int status = optics_status(o);
+  const int status = status_sh;
   if (status != WO_OK) {
     for (int e = threadIdx.x; e < kRecRows * X; e += 256) {
       const int yy = e / X;
@@ -163,10 +182,7 @@ __global__ void __launch_bounds__(256) k_pupil_record(TfArgs a, int kRecRows) {
   }
   __syncthreads();
   const double lam = o.lambda_um;
-  const double rp = __ddiv_rn(o.na_det, lam), rp2 = __dmul_rn(rp, rp);
-  const double cy = __ddiv_rn(o.tilt_y, lam), cx = __ddiv_rn(o.tilt_x, lam);
-  const double rs = __ddiv_rn(o.na_ill, lam), rs2 = __dmul_rn(rs, rs);
-  const double km = __ddiv_rn(o.n_medium, lam), km2 = __dmul_rn(km, km);
+  const double rp2 = cst[0], cy = cst[1], cx = cst[2], rs = cst[3], rs2 = cst[4], km2 = cst[5];
   // float images of the constants for the mask pre-test: a predicate is
   // settled in float when the float value is clear of the threshold by a
   // margin far above the float error; otherwise the float64 expression decides
@@ -175,8 +191,8 @@ __global__ void __launch_bounds__(256) k_pupil_record(TfArgs a, int kRecRows) {
   // smooth source: S = 1 / (1 + exp(-(R - d) / w)), w one frequency bin of the
   // coarser axis, and its derivatives in tilt and NA_ill
   const float rsf = (float)rs, lamf = (float)lam;
-  const float inv_rp = (float)(1.0 / rp);  // unit-pupil coordinates of the aberration
-  const float wedge = (float)(1.0 / ((double)min(Y, X) * o.pixel_um));
+  const float inv_rp = (float)cst[6];  // unit-pupil coordinates of the aberration
+  const float wedge = (float)cst[7];
   int n_sp = 0, n_p = 0, kx_band = -1;
   float s_sp = 0.f, s_tx = 0.f, s_ty = 0.f, s_na = 0.f;
   const int rows = min(kRecRows, Y - y0);
