@@ -95,6 +95,7 @@ struct TfArgs {
   float4* rec2;             // [n_tiles][Y][X] (dS/dtx P, dS/dty P, dS/dNA P, W - rint(W)), want_grad or aberrated
   const double* zern;       // [n_tiles][n_zern] Zernike coefficients (waves, Noll order), device copy
   int n_zern;               // 0: unaberrated detection pupil
+  int arms_stage;           // arm pass: eta / source derivatives staged in shared memory (set at launch)
   float* norm_part;         // [n_tiles][record blocks][4] partial sums of S P and dS P
   float* norms;             // [n_tiles][4]: sum S P, then sum dS/dtheta P (smooth source)
   int rec_blocks;           // record blocks per tile

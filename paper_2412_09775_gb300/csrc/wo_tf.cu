@@ -315,7 +315,7 @@ __global__ void k_norms(const float* __restrict__ part, int blocks, int n_tiles,
   norms[i] = (float)v;
 }
 
-template <int N>  // N = Y
+template <int N, bool DER>  // N = Y; DER: a derivative bank (arms A', B' and the source ones)
 __global__ void __launch_bounds__(ColGeom<N>::NT, (1024 / ColGeom<N>::NT) > 1 ? (1024 / ColGeom<N>::NT) : 1) k_arms(TfArgs a) {
   using G = ColGeom<N>;
   constexpr int B = G::B, NT = G::NT;
@@ -323,6 +323,10 @@ __global__ void __launch_bounds__(ColGeom<N>::NT, (1024 / ColGeom<N>::NT) > 1 ? 
   extern __shared__ float2 sm[];
   float2* buf = sm;
   float2* tw = sm + N * B;
+  // derivative banks: eta and the source derivatives of the strip, staged
+  // once (each arm that needs them reads them from here)
+  float* eta_s = reinterpret_cast<float*>(tw + N);  // [N*B]
+  float* ds_s = eta_s + N * B;                       // [3][N*B]
   const int X = a.X, Z = a.Z;
   const int t = blockIdx.z, j = blockIdx.y, x0 = blockIdx.x * B;
   const int w = min(B, X - x0);
@@ -352,6 +356,27 @@ __global__ void __launch_bounds__(ColGeom<N>::NT, (1024 / ColGeom<N>::NT) > 1 ? 
     const int n = e / B, b = e % B;
     r[i] = (e < N * B && b < w) ? __ldg(rec + (long long)n * X + b) : make_float4(0.f, 0.f, 0.f, 0.f);
   }
+  const bool stage = DER && a.arms_stage != 0;
+  if (stage && a.want_dz) {
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int e = threadIdx.x + i * NT;
+      if (e < N * B) eta_s[e] = r[i].x;  // zero outside the strip's width (r is zero there)
+    }
+  }
+  if (stage && a.want_grad) {
+    const float4* rec2 = a.rec2 + (long long)t * N * X + x0;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int e = threadIdx.x + i * NT;
+      if (e >= N * B) continue;
+      const float4 d = (e % B) < w ? __ldg(rec2 + (long long)(e / B) * X + e % B) : make_float4(0.f, 0.f, 0.f, 0.f);
+      ds_s[e] = d.x;
+      ds_s[N * B + e] = d.y;
+      ds_s[2 * N * B + e] = d.z;
+    }
+  }
+  // (read after the first arm's barrier)
   // an aberrated detection pupil adds W (waves, reduced to [-1/2, 1/2]) to every arm's phase
   const float* wrec = a.n_zern > 0 ? reinterpret_cast<const float*>(a.rec2 + (long long)t * N * X + x0) + 3 : nullptr;
 #pragma unroll
@@ -366,7 +391,7 @@ __global__ void __launch_bounds__(ColGeom<N>::NT, (1024 / ColGeom<N>::NT) > 1 ? 
   // derivative), then A_tx, A_ty, A_NA (derivatives in the source parameters)
   int arm = 0;
 #pragma unroll 1
-  for (int which = 0; which < 8; ++which) {
+  for (int which = 0; which < (DER ? 8 : 3); ++which) {
     if (which < 2 && a.lf_props == 0) continue;
     if (which == 2 && !a.want_fl) continue;
     if ((which == 3 || which == 4) && !a.want_dz) continue;
@@ -379,16 +404,20 @@ __global__ void __launch_bounds__(ColGeom<N>::NT, (1024 / ColGeom<N>::NT) > 1 ? 
       // A' (0, 2 pi eta S), B' (-2 pi eta / eta, 0), and for the source
       // parameters A_theta (dS/dtheta, 0); zero off the pupil.  S (the
       // record's w) is 0 or 1 for the binary source.  eta and the source
-      // derivatives are read again from the records (L2 hits) rather than
-      // kept live across the transforms
+      // derivatives come from the strip's staged copies (or, where they do
+      // not fit shared memory, from the records again: L2 hits)
       float tpe = 0.f, dsv = 0.f;
       const bool inb = (e % B) < w;
-      if ((which == 3 || which == 4) && inb)
-        tpe = 6.28318530717958648f * __ldg(&rec[(long long)(e / B) * X + e % B].x);
-      if (which > 4 && inb) {
-        const float* r2 = reinterpret_cast<const float*>(a.rec2 + (long long)t * N * X + x0 +
-                                                         (long long)(e / B) * X + e % B);
-        dsv = __ldg(r2 + (which - 5));
+      if (which == 3 || which == 4)
+        tpe = 6.28318530717958648f * (stage ? eta_s[e] : (inb ? __ldg(&rec[(long long)(e / B) * X + e % B].x) : 0.f));
+      if (which > 4) {
+        if (stage) {
+          dsv = ds_s[(which - 5) * N * B + e];
+        } else if (inb) {
+          const float* r2 = reinterpret_cast<const float*>(a.rec2 + (long long)t * N * X + x0 +
+                                                           (long long)(e / B) * X + e % B);
+          dsv = __ldg(r2 + (which - 5));
+        }
       }
       float al = which == 0 ? r[i].w : (which == 2 ? (r[i].z != 0.f ? 1.f : 0.f)
                                         : (which == 4 ? -tpe * r[i].z : (which > 4 ? dsv : 0.f)));
@@ -603,10 +632,24 @@ cudaError_t tf_pupil_record(const TfArgs& a, cudaStream_t s) {
 template <int N>
 static cudaError_t launch_arms(const TfArgs& a, cudaStream_t s) {
   using G = ColGeom<N>;
-  static cudaError_t attr = allow_smem(k_arms<N>, G::SMEM);
-  if (attr != cudaSuccess) return attr;
+  // plus eta (derivative banks) and three source derivatives (gradient bank)
+  constexpr size_t kStage = (size_t)N * G::B * sizeof(float);
+  constexpr size_t kMax = 227 * 1024;
+  constexpr size_t kCap = G::SMEM + 4 * kStage <= kMax ? G::SMEM + 4 * kStage : kMax;
+  static cudaError_t attr0 = allow_smem(k_arms<N, false>, G::SMEM);
+  static cudaError_t attr1 = allow_smem(k_arms<N, true>, kCap);
+  if (attr0 != cudaSuccess) return attr0;
+  if (attr1 != cudaSuccess) return attr1;
+  TfArgs b = a;
+  size_t smem = G::SMEM + (a.want_dz ? kStage : 0) + (a.want_grad ? 3 * kStage : 0);
+  b.arms_stage = smem <= kCap ? 1 : 0;
+  if (!b.arms_stage) smem = G::SMEM;
   dim3 grid((unsigned)((a.X + G::B - 1) / G::B), (unsigned)a.Z, (unsigned)a.n_tiles);
-  WO_LAUNCH("tf_arms", s, (k_arms<N><<<grid, G::NT, G::SMEM, s>>>(a)));
+  if (a.want_dz) {
+    WO_LAUNCH("tf_arms", s, (k_arms<N, true><<<grid, G::NT, smem, s>>>(b)));
+  } else {
+    WO_LAUNCH("tf_arms", s, (k_arms<N, false><<<grid, G::NT, smem, s>>>(b)));
+  }
   return cudaGetLastError();
 }
 
