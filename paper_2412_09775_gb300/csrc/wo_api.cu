@@ -326,6 +326,24 @@ static wo_status build_tf_impl(const wo_optics* optics, bool on_host, int n_tile
   a.norm_part = (float*)(ws + L.norm_part);
   a.norms = (float*)(ws + L.norms);
   a.rec_blocks = (Y + record_rows(Y, n_tiles) - 1) / record_rows(Y, n_tiles);
+  // Columns k_x beyond the largest TF support radius of the batch hold only
+  // the PSF rows' rounding noise: the y and z passes leave them out.  The
+  // radius: H1(q) needs nu in S and P and nu + q in P; the fluorescence TF and
+  // the smooth source reach 2 NA_det / lambda; plus two bins of margin.
+  a.x_cols = X / 2 + 1;
+  if (on_host) {
+    int kmax = 0;
+    for (int q = 0; q < n_tiles; ++q) {
+      const wo_optics& o = optics[q];
+      const double tilt = sqrt(o.tilt_x * o.tilt_x + o.tilt_y * o.tilt_y);
+      double r = 0.0;
+      if (s.lf_props > 0) r = s.smooth ? 2.0 * o.na_det : o.na_det + fmin(o.na_det, o.na_ill + tilt);
+      if (s.has_fl) r = fmax(r, 2.0 * o.na_det);
+      const int k = (int)ceil(r / o.lambda_um * (double)X * o.pixel_um) + 2;
+      kmax = k > kmax ? k : kmax;
+    }
+    if (kmax + 1 < a.x_cols) a.x_cols = kmax + 1;
+  }
   if (on_host)
     WO_TRY(cudaMemcpyAsync((void*)a.optics, optics, (size_t)n_tiles * sizeof(wo_optics), cudaMemcpyHostToDevice, cs));
   if (s.aberr)
@@ -339,7 +357,7 @@ static wo_status build_tf_impl(const wo_optics* optics, bool on_host, int n_tile
   a.row_end = (long long)n_tiles * Z * Y;
   WO_TRY(tf_psf_rows(a, cs));
   const int Xh = X / 2 + 1;
-  WO_TRY(cols_c2c(Y, false, a.tf, Xh, (long long)Y * Xh, Xh, (long long)n_tiles * s.n_kinds * Z, cs,
+  WO_TRY(cols_c2c(Y, false, a.tf, Xh, (long long)Y * Xh, a.x_cols, (long long)n_tiles * s.n_kinds * Z, cs,
                   "tf_ypass"));
   if (!s.planes) WO_TRY(tf_zpass(a, cs));  // per-plane banks stop before the z transform
   return WO_OK;

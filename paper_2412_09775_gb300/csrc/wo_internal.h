@@ -96,6 +96,8 @@ struct TfArgs {
   const double* zern;       // [n_tiles][n_zern] Zernike coefficients (waves, Noll order), device copy
   int n_zern;               // 0: unaberrated detection pupil
   int arms_stage;           // arm pass: eta / source derivatives staged in shared memory (set at launch)
+  int x_cols;               // half-spectrum columns the y and z passes transform; beyond them every
+                            // tile's TFs vanish (Xh when the optics are not known on the host)
   float* norm_part;         // [n_tiles][record blocks][4] partial sums of S P and dS P
   float* norms;             // [n_tiles][4]: sum S P, then sum dS/dtheta P (smooth source)
   int rec_blocks;           // record blocks per tile

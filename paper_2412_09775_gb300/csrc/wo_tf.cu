@@ -704,8 +704,7 @@ static cudaError_t launch_zpass(const TfArgs& a, cudaStream_t s) {
   const size_t smem = G::SMEM + (size_t)G::NT * 2 * sizeof(float);
   static cudaError_t attr = allow_smem(k_tf_zpass<N, NK>, smem);
   if (attr != cudaSuccess) return attr;
-  const int Xh = a.X / 2 + 1;
-  dim3 grid((unsigned)((Xh + G::B - 1) / G::B), (unsigned)a.Y, (unsigned)a.n_tiles);
+  dim3 grid((unsigned)((a.x_cols + G::B - 1) / G::B), (unsigned)a.Y, (unsigned)a.n_tiles);
   WO_LAUNCH("tf_zpass", s, (k_tf_zpass<N, NK><<<grid, G::NT, smem, s>>>(a)));
   return cudaGetLastError();
 }
