@@ -450,7 +450,8 @@ wo_status wo_thin_phantom(const float *d_params, int n_tiles, int n_spheres, int
  * point on these shapes launches (lengths Y and Z, batches as large as the
  * workspace allows up to three volumes per tile) and of the x passes (X/2
  * points, the rows of the same volumes), on the workspace (its
- * contents are destroyed), and keeps the fastest in the table.  It waits for
+ * contents are destroyed), and keeps the fastest in the table (the non-default
+ * engine only when at least 2 % faster).  It waits for
  * the stream (it measures with events), so it is not for graph capture; run
  * it once before capturing.  The table is process-wide. */
 enum { WO_PASS_COLS = 0 };

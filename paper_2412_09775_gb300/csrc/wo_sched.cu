@@ -49,10 +49,12 @@ int rows_engine(int n) {
 // stream s) and keep the faster.  The engines are timed in alternating rounds
 // (kReps runs per round, after one untimed run each) and each keeps its best
 // round, so a clock ramp or a cold cache early on does not decide the
-// choice.  Returns the engine kept, or -1 on a CUDA error (the entry is then
+// choice.  The other engine replaces the built-in default only when it is at
+// least 2 % faster, so near-ties do not flip from one process to the next.
+// Returns the engine kept, or -1 on a CUDA error (the entry is then
 // restored).
 template <class Run>
-static int tune_entry(std::atomic<int>& entry, bool hybrid_ok, cudaStream_t s, Run run) {
+static int tune_entry(std::atomic<int>& entry, int default_engine, bool hybrid_ok, cudaStream_t s, Run run) {
   constexpr int kEngines = 2, kRounds = 3, kReps = 8;
   const int engines[kEngines] = {WO_ENGINE_SMEM, WO_ENGINE_HYBRID};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -88,7 +90,9 @@ static int tune_entry(std::atomic<int>& entry, bool hybrid_ok, cudaStream_t s, R
   cudaEventDestroy(e1);
   int best = -1;
   for (int k = 0; k < kEngines && !failed; ++k)
-    if (ok[k] && (best < 0 || t_best[k] < t_best[best])) best = k;
+    if (ok[k] && engines[k] == default_engine) best = k;
+  for (int k = 0; k < kEngines && !failed; ++k)
+    if (ok[k] && (best < 0 || t_best[k] < 0.98f * t_best[best])) best = k;
   entry.store(best < 0 ? saved : engines[best]);
   return best < 0 ? -1 : engines[best];
 }
@@ -97,7 +101,7 @@ static int tune_entry(std::atomic<int>& entry, bool hybrid_ok, cudaStream_t s, R
 // (pitch ncols) in the scratch buffer, alternating directions.
 static int tune_cols(int n, int ncols, long long planes, float2* scratch, cudaStream_t s) {
   const long long ps = (long long)n * ncols;
-  return tune_entry(g_cols_engine[n], cols_hyb_supported(n), s, [&](int q) {
+  return tune_entry(g_cols_engine[n], WO_ENGINE_SMEM, cols_hyb_supported(n), s, [&](int q) {
     return cols_c2c(n, q & 1, scratch, ncols, ps, ncols, planes, s, "autotune");
   });
 }
@@ -108,7 +112,7 @@ static int tune_rows(int n, long long rows, float2* scratch, cudaStream_t s) {
   float* real = reinterpret_cast<float*>(scratch);
   float2* half = scratch + (size_t)rows * n;  // after the 2n real samples of every row
   const RowBg none{};
-  return tune_entry(g_rows_engine[n], rows_reg_supported(n), s, [&](int) {
+  return tune_entry(g_rows_engine[n], WO_ENGINE_HYBRID, rows_reg_supported(n), s, [&](int) {
     cudaError_t e = rows_r2c(n, real, half, rows, none, s);
     if (e != cudaSuccess) return e;
     return rows_c2r(n, half, real, rows, 1.0f, none, s);
