@@ -105,6 +105,19 @@ def support_columns(o, kinds, Y, X):
     return int(np.sum(ky[:, None] ** 2 + kx[None, :] ** 2 <= r * r))
 
 
+def support_xcols(o, kinds, X):
+    """Half-spectrum columns the TF build's y and z passes transform (the
+    support radius in x plus two bins, as the library computes it)."""
+    import math
+    tilt = float(np.hypot(o["tilt_x"], o["tilt_y"]))
+    R = 0.0
+    if {"phase", "absorption"} & set(kinds):
+        R = o["na_det"] + min(o["na_det"], o["na_ill"] + tilt)
+    if "fluor" in kinds:
+        R = max(R, 2 * o["na_det"])
+    return min(X // 2 + 1, math.ceil(R / o["lambda_um"] * X * o["pixel_um"]) + 3)
+
+
 def algorithmic_bytes(shape, kinds, o):
     """Compulsory HBM bytes per launch of each kernel family for one step."""
     Z, Y, X = shape
@@ -117,13 +130,14 @@ def algorithmic_bytes(shape, kinds, o):
     real = Z * Y * X * 4
     half = Z * Y * Xh * 8
     inside = Z * support_columns(o, kinds, Y, X) * 8  # bytes of one volume inside the support
+    tf_cols = Z * Y * support_xcols(o, kinds, X) * 8  # bytes of one TF slot the build's y/z passes touch
     arms = n_arms * Z * Y * band_columns(o, X) * 8
     return {
         "tf_pupil_record": Y * X * 16,
         "tf_arms": arms,
         "tf_psf_rows": arms + nk * half,
-        "tf_ypass": 2 * nk * half,
-        "tf_zpass": 2 * nk * half,
+        "tf_ypass": 2 * nk * tf_cols,
+        "tf_zpass": 2 * nk * tf_cols,
         "rows_r2c": C * (real + half),
         "y_fwd": 2 * C * half,
         "z_fused": (C + nk) * inside + P * half,
