@@ -615,3 +615,35 @@ def test_row_engines_match_oracle(env, shape, engine):
         assert rel_l2(spec.cpu().numpy()[0], want[..., : X // 2 + 1]) <= 1e-5
     finally:
         B.wo_schedule_set(B.WO_PASS_ROWS, n, 0)
+
+
+@pytest.mark.parametrize("shape", [(1, 16, 16), (2, 2048, 8), (2, 8, 2048), (3, 4, 6), (1, 1, 2), (2048, 2, 4)])
+def test_operators_at_degenerate_and_largest_lengths(env, shape):
+    """Forward, adjoint and 3D reconstruction at a single plane, a single
+    row, the smallest transform and the largest lengths of each axis."""
+    B, torch, dev = env
+    Z, Y, X = shape
+    kinds = ("phase", "absorption", "fluor")
+    o = ph.optics(na_ill=0.6, tilt_x=0.02, defocus_um=0.1)
+    tf, ws = check_tf(env, [o], shape, kinds)
+    modes, props, chans = OM.widefield_system(oracle_tf(o, shape, kinds), kinds)
+    f = ph.uniform_volume(31, (1, 3) + shape, -0.02, 0.02).astype(np.float32)
+    bg = [1.0, 0.0]
+    b = np.array(bg)[:, None, None, None]
+    d = run_forward(env, tf, ws, kinds, f, bg, shape)[0]
+    ref = OM.forward(modes, f[0].astype(np.float64), bg)
+    assert rel_l2(d - b, ref - b) <= TOL
+    dd = ph.uniform_volume(32, (2,) + shape, 0.5, 1.5).astype(np.float32)
+    fo = torch.empty((1, 3) + shape, dtype=torch.float32, device=dev)
+    B.wo_forward_adjoint(tf, kinds, torch.from_numpy(dd[None]).to(dev), bg, fo, 1, Z, Y, X, ws)
+    assert rel_l2(fo.cpu().numpy()[0], OM.adjoint(modes, dd.astype(np.float64), bg)) <= TOL
+    got = run_recon(env, tf, ws, kinds, dd[None], None, [1e-3, 1e-3], B.WO_ETA_RELATIVE, B.WO_MODE_3D, shape)[0]
+    want = OM.reconstruct(modes, dd.astype(np.float64), 1e-3)
+    # per contrast mode, relative to the mode's norm, plus float32 rounding of
+    # data-sized values where the mode's TFs vanish off the zero frequency (a
+    # grid holding only the DC inside the pupil, whose data term the channel
+    # mean removes, so the exact answer is zero)
+    for ps in ((0, 1), (2,)):
+        err = np.linalg.norm((got[list(ps)] - want[list(ps)]).ravel())
+        tol = TOL * np.linalg.norm(want[list(ps)].ravel()) + 1e-6 * np.linalg.norm(dd.ravel())
+        assert err <= tol, (ps, err, tol)
