@@ -58,8 +58,6 @@ __global__ void __launch_bounds__(kPsfThreads, 4) k_psf_rows_reg(TfArgs a) {
   constexpr int N = P::N, N1 = P::E, T = P::T, RP = P::SLICE, RPC = kPsfThreads / T;
   __shared__ float2 tw[P::TW];
   __shared__ float2 slices[RPC * RP];
-  P::twiddles(tw);
-  __syncthreads();
   const int lt = threadIdx.x % T, r = threadIdx.x / T;
   const int lane = threadIdx.x & 31;
   const int partner = (lane - lt) + (T - lt) % T;  // lane owning N - k
@@ -78,6 +76,13 @@ __global__ void __launch_bounds__(kPsfThreads, 4) k_psf_rows_reg(TfArgs a) {
   const long long kstride = (long long)a.Z * a.Y * Xh;
 
   constexpr bool DZ = MODE >= 1;
+  float2 w[N1];
+  float gre[MODE == 2 ? N1 : 1];  // Re g (unscaled), for the normalisation terms
+  float2 vb[N1];                  // b, kept for the source-parameter arms
+  float2 va[N1];
+  // the row's first arm is on its way while the block forms its twiddles
+  if (DZ || lf) load_arm<P>(va, a, t, rem, 0, kxm, lt);
+  else load_arm<P>(w, a, t, rem, 0, kxm, lt);
   // the row's scale factors (float64 arithmetic, slow on this part) are
   // formed once per row, by its first lane, and broadcast
   float sc_row = 0.f, scf_row = 0.f;
@@ -87,16 +92,13 @@ __global__ void __launch_bounds__(kPsfThreads, 4) k_psf_rows_reg(TfArgs a) {
   }
   sc_row = __shfl_sync(0xffffffffu, sc_row, lane - lt);
   scf_row = __shfl_sync(0xffffffffu, scf_row, lane - lt);
-  float2 w[N1];
-  float gre[MODE == 2 ? N1 : 1];  // Re g (unscaled), for the normalisation terms
-  float2 vb[N1];                  // b, kept for the source-parameter arms
+  P::twiddles(tw);
+  __syncthreads();
   int slot = 0;
   if (DZ || lf) {
     const float sc = sc_row;
-    float2 va[N1];
     if constexpr (DZ) {
       // w = 2K (Re conj(a) b + i (Re conj(a) b' + Re conj(a') b)), arms A, B, A', B'
-      load_arm<P>(va, a, t, rem, 0, kxm, lt);
       P::template fft<true>(va, tw, S, lt);
       load_arm<P>(vb, a, t, rem, 3, kxm, lt);
       P::template fft<true>(vb, tw, S, lt);
@@ -115,7 +117,6 @@ __global__ void __launch_bounds__(kPsfThreads, 4) k_psf_rows_reg(TfArgs a) {
         w[m] = cscale(w[m], sc);
       }
     } else {
-      load_arm<P>(va, a, t, rem, 0, kxm, lt);
       P::template fft<true>(va, tw, S, lt);
       load_arm<P>(vb, a, t, rem, 1, kxm, lt);
       P::template fft<true>(vb, tw, S, lt);
@@ -149,15 +150,15 @@ __global__ void __launch_bounds__(kPsfThreads, 4) k_psf_rows_reg(TfArgs a) {
     // and tilt_y packed as one complex row, NA_ill as a real row
     const float sc = sc_row;
     const float rx = norm_dlog(a, (int)t, 0), ry = norm_dlog(a, (int)t, 1), rn = norm_dlog(a, (int)t, 2);
-    float2 va[N1];
-    load_arm<P>(va, a, t, rem, 4, kxm, lt);
-    P::template fft<true>(va, tw, S, lt);
+    float2 vs[N1];
+    load_arm<P>(vs, a, t, rem, 4, kxm, lt);
+    P::template fft<true>(vs, tw, S, lt);
 #pragma unroll
-    for (int m = 0; m < N1; ++m) w[m].x = sc * (va[m].x * vb[m].x + va[m].y * vb[m].y - rx * gre[m]);
-    load_arm<P>(va, a, t, rem, 5, kxm, lt);
-    P::template fft<true>(va, tw, S, lt);
+    for (int m = 0; m < N1; ++m) w[m].x = sc * (vs[m].x * vb[m].x + vs[m].y * vb[m].y - rx * gre[m]);
+    load_arm<P>(vs, a, t, rem, 5, kxm, lt);
+    P::template fft<true>(vs, tw, S, lt);
 #pragma unroll
-    for (int m = 0; m < N1; ++m) w[m].y = sc * (va[m].x * vb[m].x + va[m].y * vb[m].y - ry * gre[m]);
+    for (int m = 0; m < N1; ++m) w[m].y = sc * (vs[m].x * vb[m].x + vs[m].y * vb[m].y - ry * gre[m]);
     P::template fft<false>(w, tw, S, lt);
 #pragma unroll
     for (int m = 0; m < N1; ++m) {
@@ -171,10 +172,10 @@ __global__ void __launch_bounds__(kPsfThreads, 4) k_psf_rows_reg(TfArgs a) {
       dst[2 * kstride + k] = make_float2(0.5f * (w[m].x + c.x), 0.5f * (w[m].y + c.y));
       dst[3 * kstride + k] = make_float2(d.y, -d.x);
     }
-    load_arm<P>(va, a, t, rem, 6, kxm, lt);
-    P::template fft<true>(va, tw, S, lt);
+    load_arm<P>(vs, a, t, rem, 6, kxm, lt);
+    P::template fft<true>(vs, tw, S, lt);
 #pragma unroll
-    for (int m = 0; m < N1; ++m) w[m] = make_float2(sc * (va[m].x * vb[m].x + va[m].y * vb[m].y - rn * gre[m]), 0.f);
+    for (int m = 0; m < N1; ++m) w[m] = make_float2(sc * (vs[m].x * vb[m].x + vs[m].y * vb[m].y - rn * gre[m]), 0.f);
     P::template fft<false>(w, tw, S, lt);
 #pragma unroll
     for (int m = 0; m < N1; ++m) {
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(kPsfThreads, 4) k_psf_rows_reg(TfArgs a) {
   }
   if (!DZ && fl) {
     const float scf = scf_row;
-    load_arm<P>(w, a, t, rem, lf ? 2 : 0, kxm, lt);
+    if (lf) load_arm<P>(w, a, t, rem, 2, kxm, lt);  // without label-free kinds it is arm 0, loaded above
     P::template fft<true>(w, tw, S, lt);
 #pragma unroll
     for (int m = 0; m < N1; ++m) w[m] = make_float2(scf * cabs2(w[m]), 0.f);
