@@ -54,11 +54,11 @@ __global__ void __launch_bounds__(ColGeom<N>::NT, ColGeom<N>::MINB)
   const long long p = blockIdx.y + (long long)gridDim.y * blockIdx.z;
   if (p >= total) return;  // uniform across the CTA
   const long long g = p / nplanes, plane = p - g * nplanes;
-  make_twiddles<N>(tw);
   const int x0 = blockIdx.x * B;
   const int w = min(B, ncols - x0);
   float2* base = data + g * group_stride + plane * plane_stride + x0;
   col_tile_load<N, B, NT>(buf, base, col_stride, w);
+  make_twiddles<N>(tw);  // while the tile's copies are in flight
   cp_async_wait_all();
   __syncthreads();
   fft_smem<N, B, NT, INV, 1>(buf, B, 1, tw);

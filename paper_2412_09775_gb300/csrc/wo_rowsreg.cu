@@ -56,9 +56,6 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_r2c_reg(const float* __res
   extern __shared__ float2 sm[];
   float2* tw = sm;                  // P's twiddles
   float2* tw2 = sm + P::TW;         // exp(-2 pi i m / 2N)
-  P::twiddles(tw);
-  make_twiddles<2 * N>(tw2);
-  __syncthreads();
   const int t = threadIdx.x % T, r = threadIdx.x / T;
   const int lane = threadIdx.x & 31;
   const int partner = (lane - t) + (T - t) % T;
@@ -70,10 +67,12 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_r2c_reg(const float* __res
   const float2* src = reinterpret_cast<const float2*>(in + rr * (2LL * N)) + t;
   float2 v[E];
 #pragma unroll
-  for (int m = 0; m < E; ++m) {
-    const float2 x = __ldg(src + T * m);
-    v[m] = make_float2(x.x - c, x.y - c);
-  }
+  for (int m = 0; m < E; ++m) v[m] = __ldg(src + T * m);
+  P::twiddles(tw);  // while the row's loads are in flight
+  make_twiddles<2 * N>(tw2);
+  __syncthreads();
+#pragma unroll
+  for (int m = 0; m < E; ++m) v[m] = make_float2(v[m].x - c, v[m].y - c);
   P::template fft<false>(v, tw, S, t);
   float2* o = out + rr * (N + 1);
 #pragma unroll
@@ -96,9 +95,6 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_c2r_reg(const float2* __re
   extern __shared__ float2 sm[];
   float2* tw = sm;
   float2* tw2 = sm + P::TW;
-  P::twiddles(tw);
-  make_twiddles<2 * N>(tw2);
-  __syncthreads();
   const int t = threadIdx.x % T, r = threadIdx.x / T;
   const int lane = threadIdx.x & 31;
   const int partner = (lane - t) + (T - t) % T;
@@ -111,6 +107,9 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_c2r_reg(const float2* __re
 #pragma unroll
   for (int m = 0; m < E; ++m) x[m] = __ldg(src + T * m);
   const float2 xn = t == 0 ? __ldg(in + rr * (N + 1) + N) : make_float2(0.f, 0.f);  // X[N], partner of X[0]
+  P::twiddles(tw);  // while the row's loads are in flight
+  make_twiddles<2 * N>(tw2);
+  __syncthreads();
   float2 v[E];
 #pragma unroll
   for (int m = 0; m < E; ++m) {
