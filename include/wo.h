@@ -143,7 +143,11 @@ size_t wo_workspace_bytes(int n_tiles, int Z, int Y, int X, unsigned kinds);
  * Returns WO_ERR_OPTICS if a tile has NA_det >= n, NA_ill + |t| > n or a
  * non-positive length; WO_ERR_UNDERSAMPLED if
  * (NA_det + NA_ill + |t|)/lambda >= 1/(2 pixel) (the pupil correlation would
- * alias) or (n/lambda)(1 - sqrt(1 - (NA_det/n)^2)) >= 1/(2 z_step). */
+ * alias) or (n/lambda)(1 - sqrt(1 - (NA_det/n)^2)) >= 1/(2 z_step).
+ * With the optics on the host the y and z transforms of the build cover the
+ * half-spectrum columns k_x up to the batch's largest TF support radius plus
+ * two bins; the columns beyond hold the PSF rows' rounding noise (of the
+ * order of 1e-7 of the largest TF value) instead of exact zeros. */
 wo_status wo_build_tf(const wo_optics *h_optics, int n_tiles, int Z, int Y, int X,
                       unsigned kinds, void *d_tf, void *d_ws, size_t ws_bytes,
                       wo_stream stream);
