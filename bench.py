@@ -412,10 +412,11 @@ def run_gpu(args, rank, world, local_rank):
         e2e_ms = (float("nan"), float("nan"))
     else:
         e2e_ms = run_e2e(args, B, o, data, out, tf, ws, stream, barrier, world, dev)
+    lib = None if args.no_library_fft else library_leg(args, B, tf, ws, data, out, stream, dev)
     tune = None if args.no_autotune else autotune_leg(args, rank, world, local_rank)
     if rank != 0:
         return
-    report(args, world, ms_max, e2e_ms, prof, launches, clk, tune)
+    report(args, world, ms_max, e2e_ms, prof, launches, clk, tune, lib)
 
 
 def run_e2e(args, B, o, data, out, tf, ws, stream, barrier, world, dev):
@@ -468,7 +469,74 @@ def run_e2e(args, B, o, data, out, tf, ws, stream, barrier, world, dev):
     return timed(len(lanes)), serial
 
 
-def report(args, world, ms_max, e2e_ms, prof, launches, clk, tune=None):
+def library_leg(args, B, tf, ws, data, out, stream, dev):
+    """The same forward model and reconstruction written with torch.fft (cuFFT)
+    and torch elementwise ops on the same TF bank and shapes - the style of a
+    PyTorch implementation of the method - timed beside the library's calls.
+    Timed only, for context: nothing here is on the library's path.  Returns
+    ms per call for both and the relative L2 difference of their outputs."""
+    import torch
+    Z, Y, X = SHAPE
+    Xh = X // 2 + 1
+    spectra = tf[: 3 * Z * Y * Xh * 8]  # the bank's spectra; its per-tile statistics block follows them
+    H = torch.view_as_complex(spectra.view(torch.float32).view(3, Z, Y, Xh, 2))  # phase, absorption, fluorescence
+    dims = (-3, -2, -1)
+    bg = [1.0, 0.1]
+    f_vol = torch.empty((1, 3, Z, Y, X), dtype=torch.float32, device=dev)
+    f_vol.copy_(out)
+    d_lib = torch.empty((1, 2, Z, Y, X), dtype=torch.float32, device=dev)
+    w_re = float(ETA[0]) * float(((H[0].abs() ** 2) + (H[1].abs() ** 2)).max())
+    w_fl = float(ETA[1]) * float((H[2].abs() ** 2).max())
+
+    def torch_forward():
+        F = torch.fft.rfftn(f_vol[0], dim=dims)
+        D = torch.stack((H[0] * F[0] + H[1] * F[1], H[2] * F[2]))
+        d = torch.fft.irfftn(D, s=(Z, Y, X), dim=dims)
+        d[0] += bg[0]
+        d[1] += bg[1]
+        return d
+
+    def torch_reconstruct():
+        r = data[0] - data[0].mean(dim=dims, keepdim=True)
+        D = torch.fft.rfftn(r, dim=dims)
+        g = D[0] / ((H[0].abs() ** 2) + (H[1].abs() ** 2) + w_re)  # push-through form, C = 1 < P = 2
+        F = torch.stack((H[0].conj() * g, H[1].conj() * g, H[2].conj() * D[1] / ((H[2].abs() ** 2) + w_fl)))
+        return torch.fft.irfftn(F, s=(Z, Y, X), dim=dims)
+
+    def lib_forward():
+        B.wo_forward(tf, KINDS, f_vol, bg, d_lib, 1, Z, Y, X, ws)
+
+    def lib_reconstruct():
+        B.wo_reconstruct(tf, KINDS, data, None, ETA, B.WO_ETA_RELATIVE, B.WO_MODE_3D, out, 1, Z, Y, X, ws)
+
+    def timed(fn):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    def rel(a, b):
+        return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+
+    t_fwd, l_fwd = timed(torch_forward), timed(lib_forward)
+    diff_fwd = rel(torch_forward(), d_lib[0])
+    t_rec, l_rec = timed(torch_reconstruct), timed(lib_reconstruct)
+    diff_rec = rel(torch_reconstruct(), out[0])
+    return {"forward": {"torch_fft_ms": round(t_fwd, 4), "library_ms": round(l_fwd, 4),
+                        "speedup": round(t_fwd / l_fwd, 2), "rel_l2_diff": float(f"{diff_fwd:.3g}")},
+            "reconstruct": {"torch_fft_ms": round(t_rec, 4), "library_ms": round(l_rec, 4),
+                            "speedup": round(t_rec / l_rec, 2), "rel_l2_diff": float(f"{diff_rec:.3g}")},
+            "note": "torch.fft (cuFFT) + torch elementwise ops on the same TF bank, 96x512x512, three "
+                    "properties / two stacks, CUDA events; timed only, not on the library's path"}
+
+
+def report(args, world, ms_max, e2e_ms, prof, launches, clk, tune=None, lib=None):
     Z, Y, X = SHAPE
     from paper_2412_09775_gb300.shard import job_throughput
     vox = float(Z * Y * X)
@@ -519,6 +587,8 @@ def report(args, world, ms_max, e2e_ms, prof, launches, clk, tune=None):
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+    if lib is not None:
+        line["library_fft"] = lib  # cuFFT-based composition of the same calls, timed beside them
     if tune is not None:
         line["autotune"] = tune  # the metric's second half: auto-tuned tiles/s at fixed error
     print(json.dumps(line), flush=True)
@@ -1044,6 +1114,8 @@ def main():
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-library-fft", action="store_true",
+                    help="skip timing the torch.fft composition of the forward model and reconstruction")
     ap.add_argument("--workload", choices=["widefield", "tiles", "autotune", "estimator"], default="widefield")
     ap.add_argument("--est-train", type=int, default=EST_TRAIN, help="estimator training tiles")
     ap.add_argument("--est-epochs", type=int, default=12, help="estimator training epochs")
