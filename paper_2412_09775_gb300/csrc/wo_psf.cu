@@ -198,6 +198,120 @@ __global__ void __launch_bounds__(kPsfThreads, 4) k_psf_rows_reg(TfArgs a) {
   }
 }
 
+// Banks with the fluorescence kind and no derivatives: each lane group takes
+// two consecutive rows.  Their label-free rows are transformed one row at a
+// time as above; their fluorescence rows h0 = scf |p0|^2 and h1 = scf |p1|^2
+// are real, so they go through one forward transform as w = h0 + i h1:
+//   H0(k) = (W(k) + W*(-k)) / 2,   H1(k) = (W(k) - W*(-k)) / (2i),
+// one forward transform fewer per pair of rows.  (The two rows may belong to
+// different tiles when Z*Y is odd; everything per row is formed per row.)
+template <class P>
+__global__ void __launch_bounds__(kPsfThreads, 4) k_psf_rows_pair(TfArgs a) {
+  constexpr int N = P::N, N1 = P::E, T = P::T, RP = P::SLICE, RPC = kPsfThreads / T;
+  __shared__ float2 tw[P::TW];
+  __shared__ float2 slices[RPC * RP];
+  const int lt = threadIdx.x % T, r = threadIdx.x / T;
+  const int lane = threadIdx.x & 31;
+  const int partner = (lane - lt) + (T - lt) % T;  // lane owning N - k
+  const bool lane0 = lt == 0;
+  float2* S = slices + r * RP;
+  const long long nrows = a.row_end;
+  const long long row0 = a.row_begin + 2 * ((long long)blockIdx.x * RPC + r);
+  const bool live0 = row0 < nrows, live1 = row0 + 1 < nrows;
+  const long long r0 = live0 ? row0 : nrows - 1, r1 = live1 ? row0 + 1 : nrows - 1;  // tails compute, store nothing
+  const long long zy = (long long)a.Z * a.Y;
+  const long long t0 = r0 / zy, rem0 = r0 - t0 * zy, t1 = r1 / zy, rem1 = r1 - t1 * zy;
+  const int kxm0 = a.counts[4 * t0 + 2], kxm1 = a.counts[4 * t1 + 2];
+  const bool lf = a.lf_props > 0;
+  const int Xh = N / 2 + 1;
+  const long long kstride = (long long)a.Z * a.Y * Xh;
+  float2* dst0 = a.tf + (t0 * a.n_kinds * a.Z) * (long long)a.Y * Xh + rem0 * Xh;
+  float2* dst1 = a.tf + (t1 * a.n_kinds * a.Z) * (long long)a.Y * Xh + rem1 * Xh;
+  const int fl_arm = lf ? 2 : 0;
+
+  float2 w[N1];
+  float2 va[N1];
+  // the first row's first arm is on its way while the block forms its twiddles
+  if (lf) load_arm<P>(va, a, t0, rem0, 0, kxm0, lt);
+  else load_arm<P>(w, a, t0, rem0, fl_arm, kxm0, lt);
+  float sc0 = 0.f, sc1 = 0.f, scf0 = 0.f, scf1 = 0.f;  // float64 set-up: the group's first lane, broadcast
+  if (lt == 0) {
+    if (lf) {
+      sc0 = lf_scale(a, (int)t0);
+      sc1 = t1 == t0 ? sc0 : lf_scale(a, (int)t1);
+    }
+    scf0 = fl_scale(a, (int)t0);
+    scf1 = t1 == t0 ? scf0 : fl_scale(a, (int)t1);
+  }
+  sc0 = __shfl_sync(0xffffffffu, sc0, lane - lt);
+  sc1 = __shfl_sync(0xffffffffu, sc1, lane - lt);
+  scf0 = __shfl_sync(0xffffffffu, scf0, lane - lt);
+  scf1 = __shfl_sync(0xffffffffu, scf1, lane - lt);
+  P::twiddles(tw);
+  __syncthreads();
+  if (lf) {
+#pragma unroll 1
+    for (int q = 0; q < 2; ++q) {
+      const long long tq = q ? t1 : t0, remq = q ? rem1 : rem0;
+      const int kxq = q ? kxm1 : kxm0;
+      const bool liveq = q ? live1 : live0;
+      float2* dq = q ? dst1 : dst0;
+      const float sc = q ? sc1 : sc0;
+      if (q) load_arm<P>(va, a, tq, remq, 0, kxq, lt);
+      float2 vb[N1];
+      P::template fft<true>(va, tw, S, lt);
+      load_arm<P>(vb, a, tq, remq, 1, kxq, lt);
+      P::template fft<true>(vb, tw, S, lt);
+#pragma unroll
+      for (int m = 0; m < N1; ++m) w[m] = cscale(cmulc(va[m], vb[m]), sc);
+      P::template fft<false>(w, tw, S, lt);
+#pragma unroll
+      for (int m = 0; m < N1; ++m) {
+        const float2 mv = mirror_value<N1>(w, m, lane0);
+        float2 c;  // conj(W(N - k))
+        c.x = __shfl_sync(0xffffffffu, mv.x, partner);
+        c.y = -__shfl_sync(0xffffffffu, mv.y, partner);
+        const int k = lt + T * m;
+        if (!liveq || k > N / 2) continue;
+        int s = 0;
+        if (a.want_phase) dq[(s++) * kstride + k] = make_float2(0.5f * (w[m].x + c.x), 0.5f * (w[m].y + c.y));
+        if (a.want_abs) dq[(s++) * kstride + k] = make_float2(-0.5f * (w[m].y - c.y), 0.5f * (w[m].x - c.x));
+      }
+    }
+    load_arm<P>(w, a, t0, rem0, fl_arm, kxm0, lt);
+  }
+  P::template fft<true>(w, tw, S, lt);
+  float h0[N1];
+#pragma unroll
+  for (int m = 0; m < N1; ++m) h0[m] = scf0 * cabs2(w[m]);
+  load_arm<P>(w, a, t1, rem1, fl_arm, kxm1, lt);
+  P::template fft<true>(w, tw, S, lt);
+#pragma unroll
+  for (int m = 0; m < N1; ++m) w[m] = make_float2(h0[m], scf1 * cabs2(w[m]));
+  P::template fft<false>(w, tw, S, lt);
+  const int slot = a.lf_props;
+#pragma unroll
+  for (int m = 0; m < N1; ++m) {
+    const float2 mv = mirror_value<N1>(w, m, lane0);
+    float2 c;  // conj(W(N - k))
+    c.x = __shfl_sync(0xffffffffu, mv.x, partner);
+    c.y = -__shfl_sync(0xffffffffu, mv.y, partner);
+    const int k = lt + T * m;
+    if (k > N / 2) continue;
+    if (live0) dst0[slot * kstride + k] = make_float2(0.5f * (w[m].x + c.x), 0.5f * (w[m].y + c.y));
+    if (live1) dst1[slot * kstride + k] = make_float2(0.5f * (w[m].y - c.y), -0.5f * (w[m].x - c.x));
+  }
+}
+
+template <class P>
+static cudaError_t launch_psf_pair(const TfArgs& a, cudaStream_t s) {
+  constexpr int RPC = kPsfThreads / P::T;
+  const long long pairs = (a.row_end - a.row_begin + 1) / 2;
+  const unsigned grid = (unsigned)((pairs + RPC - 1) / RPC);
+  WO_LAUNCH("tf_psf_rows", s, (k_psf_rows_pair<P><<<grid, kPsfThreads, 0, s>>>(a)));
+  return cudaGetLastError();
+}
+
 template <class P, int MODE>
 static cudaError_t launch_psf_reg(const TfArgs& a, cudaStream_t s) {
   constexpr int RPC = kPsfThreads / P::T;
@@ -213,7 +327,8 @@ static cudaError_t launch_psf_reg_any(const TfArgs& a, cudaStream_t s) {
     if constexpr (GRAD) return launch_psf_reg<P, 2>(a, s);
     return cudaErrorInvalidValue;
   }
-  return a.want_dz ? launch_psf_reg<P, 1>(a, s) : launch_psf_reg<P, 0>(a, s);
+  if (a.want_dz) return launch_psf_reg<P, 1>(a, s);
+  return a.want_fl ? launch_psf_pair<P>(a, s) : launch_psf_reg<P, 0>(a, s);
 }
 
 bool psf_rows_reg_supported(int X, int n_arms) {

@@ -86,6 +86,15 @@ def test_tf_tiles_each_with_own_optics(env):
     check_tf(env, optics, (8, 32, 32), OO.KINDS)
 
 
+@pytest.mark.parametrize("shape", [(3, 3, 32), (3, 3, 64), (1, 3, 128), (3, 3, 512), (1, 3, 256)])
+@pytest.mark.parametrize("kinds", [("fluor",), ("phase", "absorption", "fluor")])
+def test_tf_odd_rows_per_tile(env, shape, kinds):
+    # Z*Y odd with three tiles: consecutive rows that share a transform belong
+    # to different tiles, and the batch ends on a row without a partner
+    optics = ph.tile_optics(np.random.default_rng(11), 3)
+    check_tf(env, optics, shape, kinds)
+
+
 def test_tf_point_source_and_pooled_screen_optics(env):
     check_tf(env, [ph.optics(na_ill=0.0)], (8, 32, 32), ("phase", "absorption"))
     check_tf(env, [dict(ph.POOLED_SCREEN_OPTICS, tilt_x=0.03)], (5 + 1, 64, 64), ("phase",))
