@@ -198,23 +198,31 @@ __global__ void __launch_bounds__(kPsfThreads, 4) k_psf_rows_reg(TfArgs a) {
   }
 }
 
-// Banks with the fluorescence kind and no derivatives: each lane group takes
-// two consecutive rows.  Their label-free rows are transformed one row at a
-// time as above; their fluorescence rows h0 = scf |p0|^2 and h1 = scf |p1|^2
-// are real, so they go through one forward transform as w = h0 + i h1:
-//   H0(k) = (W(k) + W*(-k)) / 2,   H1(k) = (W(k) - W*(-k)) / (2i),
-// one forward transform fewer per pair of rows.  (The two rows may belong to
-// different tiles when Z*Y is odd; everything per row is formed per row.)
-template <class P>
-__global__ void __launch_bounds__(kPsfThreads, 4) k_psf_rows_pair(TfArgs a) {
+// Banks without derivatives whose real PSF rows can share transforms: each
+// lane group takes two consecutive rows.  A real row pair h0, h1 goes through
+// one forward transform as w = h0 + i h1:
+//   H0(k) = (W(k) + W*(-k)) / 2,   H1(k) = (W(k) - W*(-k)) / (2i).
+// The fluorescence rows h = scf |p|^2 always pair this way; the label-free
+// rows pair when one label-free kind is wanted (h = 2K Re g for the phase TF,
+// -2K Im g for the absorption TF); with both, each row's complex g gives both
+// TF rows from one transform as in k_psf_rows_reg.  The first row's real PSF
+// row waits in shared memory (each lane reads back only what it wrote) while
+// the second is formed.  The two rows may belong to different tiles when Z*Y
+// is odd; everything per row is formed per row.
+template <class P, int LF>  // LF: label-free kinds wanted (0, 1 or 2)
+__global__ void __launch_bounds__(kPsfThreads, P::E > 16 ? 3 : 4) k_psf_rows_pair(TfArgs a) {
   constexpr int N = P::N, N1 = P::E, T = P::T, RP = P::SLICE, RPC = kPsfThreads / T;
+  // held-row pitch = T mod 32: the rows of one warp start on distinct banks
+  constexpr int HP = N + (((T - N) % 32) + 32) % 32;
   __shared__ float2 tw[P::TW];
   __shared__ float2 slices[RPC * RP];
+  __shared__ float held[RPC * HP];
   const int lt = threadIdx.x % T, r = threadIdx.x / T;
   const int lane = threadIdx.x & 31;
   const int partner = (lane - lt) + (T - lt) % T;  // lane owning N - k
   const bool lane0 = lt == 0;
   float2* S = slices + r * RP;
+  float* Hs = held + r * HP + lt;  // this lane's points lt + T m at Hs[T m]
   const long long nrows = a.row_end;
   const long long row0 = a.row_begin + 2 * ((long long)blockIdx.x * RPC + r);
   const bool live0 = row0 < nrows, live1 = row0 + 1 < nrows;
@@ -222,7 +230,8 @@ __global__ void __launch_bounds__(kPsfThreads, 4) k_psf_rows_pair(TfArgs a) {
   const long long zy = (long long)a.Z * a.Y;
   const long long t0 = r0 / zy, rem0 = r0 - t0 * zy, t1 = r1 / zy, rem1 = r1 - t1 * zy;
   const int kxm0 = a.counts[4 * t0 + 2], kxm1 = a.counts[4 * t1 + 2];
-  const bool lf = a.lf_props > 0;
+  constexpr bool lf = LF > 0, lf1 = LF == 1;
+  const bool fl = a.want_fl != 0;
   const int Xh = N / 2 + 1;
   const long long kstride = (long long)a.Z * a.Y * Xh;
   float2* dst0 = a.tf + (t0 * a.n_kinds * a.Z) * (long long)a.Y * Xh + rem0 * Xh;
@@ -240,8 +249,10 @@ __global__ void __launch_bounds__(kPsfThreads, 4) k_psf_rows_pair(TfArgs a) {
       sc0 = lf_scale(a, (int)t0);
       sc1 = t1 == t0 ? sc0 : lf_scale(a, (int)t1);
     }
-    scf0 = fl_scale(a, (int)t0);
-    scf1 = t1 == t0 ? scf0 : fl_scale(a, (int)t1);
+    if (fl) {
+      scf0 = fl_scale(a, (int)t0);
+      scf1 = t1 == t0 ? scf0 : fl_scale(a, (int)t1);
+    }
   }
   sc0 = __shfl_sync(0xffffffffu, sc0, lane - lt);
   sc1 = __shfl_sync(0xffffffffu, sc1, lane - lt);
@@ -249,8 +260,24 @@ __global__ void __launch_bounds__(kPsfThreads, 4) k_psf_rows_pair(TfArgs a) {
   scf1 = __shfl_sync(0xffffffffu, scf1, lane - lt);
   P::twiddles(tw);
   __syncthreads();
-  if (lf) {
-#pragma unroll 1
+  // one forward transform of w = h0 + i h1 into TF slot `slot` of both rows
+  auto store_pair = [&](int slot) {
+    P::template fft<false>(w, tw, S, lt);
+#pragma unroll
+    for (int m = 0; m < N1; ++m) {
+      const float2 mv = mirror_value<N1>(w, m, lane0);
+      float2 c;  // conj(W(N - k))
+      c.x = __shfl_sync(0xffffffffu, mv.x, partner);
+      c.y = -__shfl_sync(0xffffffffu, mv.y, partner);
+      const int k = lt + T * m;
+      if (k > N / 2) continue;
+      if (live0) dst0[slot * kstride + k] = make_float2(0.5f * (w[m].x + c.x), 0.5f * (w[m].y + c.y));
+      if (live1) dst1[slot * kstride + k] = make_float2(0.5f * (w[m].y - c.y), -0.5f * (w[m].x - c.x));
+    }
+  };
+  if constexpr (lf) {
+    // one kind: straight-line code, so w is live only from the second row's product
+#pragma unroll(LF == 1 ? 2 : 1)
     for (int q = 0; q < 2; ++q) {
       const long long tq = q ? t1 : t0, remq = q ? rem1 : rem0;
       const int kxq = q ? kxm1 : kxm0;
@@ -262,6 +289,16 @@ __global__ void __launch_bounds__(kPsfThreads, 4) k_psf_rows_pair(TfArgs a) {
       P::template fft<true>(va, tw, S, lt);
       load_arm<P>(vb, a, tq, remq, 1, kxq, lt);
       P::template fft<true>(vb, tw, S, lt);
+      if constexpr (lf1) {
+#pragma unroll
+        for (int m = 0; m < N1; ++m) {
+          const float2 g = cmulc(va[m], vb[m]);
+          const float h = sc * (a.want_phase ? g.x : -g.y);  // one kind: Re g (phase) or -Im g (absorption)
+          if (q == 0) Hs[T * m] = h;
+          else w[m] = make_float2(Hs[T * m], h);
+        }
+        continue;
+      } else {
 #pragma unroll
       for (int m = 0; m < N1; ++m) w[m] = cscale(cmulc(va[m], vb[m]), sc);
       P::template fft<false>(w, tw, S, lt);
@@ -273,34 +310,23 @@ __global__ void __launch_bounds__(kPsfThreads, 4) k_psf_rows_pair(TfArgs a) {
         c.y = -__shfl_sync(0xffffffffu, mv.y, partner);
         const int k = lt + T * m;
         if (!liveq || k > N / 2) continue;
-        int s = 0;
-        if (a.want_phase) dq[(s++) * kstride + k] = make_float2(0.5f * (w[m].x + c.x), 0.5f * (w[m].y + c.y));
-        if (a.want_abs) dq[(s++) * kstride + k] = make_float2(-0.5f * (w[m].y - c.y), 0.5f * (w[m].x - c.x));
+        dq[k] = make_float2(0.5f * (w[m].x + c.x), 0.5f * (w[m].y + c.y));
+        dq[kstride + k] = make_float2(-0.5f * (w[m].y - c.y), 0.5f * (w[m].x - c.x));
+      }
       }
     }
+    if constexpr (lf1) store_pair(0);
+    if (!fl) return;
     load_arm<P>(w, a, t0, rem0, fl_arm, kxm0, lt);
   }
   P::template fft<true>(w, tw, S, lt);
-  float h0[N1];
 #pragma unroll
-  for (int m = 0; m < N1; ++m) h0[m] = scf0 * cabs2(w[m]);
+  for (int m = 0; m < N1; ++m) Hs[T * m] = scf0 * cabs2(w[m]);
   load_arm<P>(w, a, t1, rem1, fl_arm, kxm1, lt);
   P::template fft<true>(w, tw, S, lt);
 #pragma unroll
-  for (int m = 0; m < N1; ++m) w[m] = make_float2(h0[m], scf1 * cabs2(w[m]));
-  P::template fft<false>(w, tw, S, lt);
-  const int slot = a.lf_props;
-#pragma unroll
-  for (int m = 0; m < N1; ++m) {
-    const float2 mv = mirror_value<N1>(w, m, lane0);
-    float2 c;  // conj(W(N - k))
-    c.x = __shfl_sync(0xffffffffu, mv.x, partner);
-    c.y = -__shfl_sync(0xffffffffu, mv.y, partner);
-    const int k = lt + T * m;
-    if (k > N / 2) continue;
-    if (live0) dst0[slot * kstride + k] = make_float2(0.5f * (w[m].x + c.x), 0.5f * (w[m].y + c.y));
-    if (live1) dst1[slot * kstride + k] = make_float2(0.5f * (w[m].y - c.y), -0.5f * (w[m].x - c.x));
-  }
+  for (int m = 0; m < N1; ++m) w[m] = make_float2(Hs[T * m], scf1 * cabs2(w[m]));
+  store_pair(LF);
 }
 
 template <class P>
@@ -308,7 +334,11 @@ static cudaError_t launch_psf_pair(const TfArgs& a, cudaStream_t s) {
   constexpr int RPC = kPsfThreads / P::T;
   const long long pairs = (a.row_end - a.row_begin + 1) / 2;
   const unsigned grid = (unsigned)((pairs + RPC - 1) / RPC);
-  WO_LAUNCH("tf_psf_rows", s, (k_psf_rows_pair<P><<<grid, kPsfThreads, 0, s>>>(a)));
+  switch (a.lf_props) {
+    case 0: WO_LAUNCH("tf_psf_rows", s, (k_psf_rows_pair<P, 0><<<grid, kPsfThreads, 0, s>>>(a))); break;
+    case 1: WO_LAUNCH("tf_psf_rows", s, (k_psf_rows_pair<P, 1><<<grid, kPsfThreads, 0, s>>>(a))); break;
+    default: WO_LAUNCH("tf_psf_rows", s, (k_psf_rows_pair<P, 2><<<grid, kPsfThreads, 0, s>>>(a))); break;
+  }
   return cudaGetLastError();
 }
 
@@ -321,6 +351,9 @@ static cudaError_t launch_psf_reg(const TfArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Banks whose real PSF rows pair up across rows (k_psf_rows_pair).
+static bool psf_pairs(const TfArgs& a) { return !a.want_dz && !a.want_grad && (a.want_fl || a.lf_props == 1); }
+
 template <class P, bool GRAD = true>
 static cudaError_t launch_psf_reg_any(const TfArgs& a, cudaStream_t s) {
   if (a.want_grad) {
@@ -328,7 +361,7 @@ static cudaError_t launch_psf_reg_any(const TfArgs& a, cudaStream_t s) {
     return cudaErrorInvalidValue;
   }
   if (a.want_dz) return launch_psf_reg<P, 1>(a, s);
-  return a.want_fl ? launch_psf_pair<P>(a, s) : launch_psf_reg<P, 0>(a, s);
+  return psf_pairs(a) ? launch_psf_pair<P>(a, s) : launch_psf_reg<P, 0>(a, s);
 }
 
 bool psf_rows_reg_supported(int X, int n_arms) {
@@ -345,9 +378,13 @@ cudaError_t tf_psf_rows_reg(const TfArgs& a, cudaStream_t s) {
     case 32: return launch_psf_reg_any<Row2<32, 8>>(a, s);
     case 48: return launch_psf_reg_any<Row2<48, 12>>(a, s);
     case 64: return launch_psf_reg_any<Row2<64, 8>>(a, s);
-    case 96: return a.want_dz ? cudaErrorInvalidValue : launch_psf_reg<Row2<96, 24>, 0>(a, s);
+    case 96:
+      if (a.want_dz) return cudaErrorInvalidValue;
+      return psf_pairs(a) ? launch_psf_pair<Row2<96, 24>>(a, s) : launch_psf_reg<Row2<96, 24>, 0>(a, s);
     case 128: return launch_psf_reg_any<Row2<128, 16>>(a, s);
-    case 192: return a.want_dz ? cudaErrorInvalidValue : launch_psf_reg<Row2<192, 24>, 0>(a, s);
+    case 192:
+      if (a.want_dz) return cudaErrorInvalidValue;
+      return psf_pairs(a) ? launch_psf_pair<Row2<192, 24>>(a, s) : launch_psf_reg<Row2<192, 24>, 0>(a, s);
     case 256: return launch_psf_reg_any<Row2<256, 16>>(a, s);
     case 512: return launch_psf_reg_any<Row512, false>(a, s);
     default: return cudaErrorInvalidValue;

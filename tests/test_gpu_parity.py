@@ -87,12 +87,36 @@ def test_tf_tiles_each_with_own_optics(env):
 
 
 @pytest.mark.parametrize("shape", [(3, 3, 32), (3, 3, 64), (1, 3, 128), (3, 3, 512), (1, 3, 256)])
-@pytest.mark.parametrize("kinds", [("fluor",), ("phase", "absorption", "fluor")])
+@pytest.mark.parametrize("kinds", [("fluor",), ("absorption",), ("phase", "fluor"), ("phase", "absorption", "fluor")])
 def test_tf_odd_rows_per_tile(env, shape, kinds):
     # Z*Y odd with three tiles: consecutive rows that share a transform belong
     # to different tiles, and the batch ends on a row without a partner
     optics = ph.tile_optics(np.random.default_rng(11), 3)
     check_tf(env, optics, shape, kinds)
+
+
+@pytest.mark.parametrize("shape,kinds", [((3, 3, 64), OO.KINDS), ((2, 16, 128), ("phase",)),
+                                         ((1, 3, 512), ("fluor",))])
+def test_tf_tiles_with_different_sampling_host_and_device_optics(env, shape, kinds):
+    # tiles with their own pixel size (the middle one samples the pupils more
+    # coarsely) in batches whose blocks hold rows of several tiles; host and
+    # device optics must give the same bank
+    B, torch, dev = env
+    Z, Y, X = shape
+    optics = [ph.optics(na_ill=0.5), ph.optics(na_ill=0.5, pixel_um=0.13, defocus_um=0.2),
+              ph.optics(na_ill=0.5, tilt_x=0.05)]
+    tf_h, _ = check_tf(env, optics, shape, kinds)
+    tf_d, ws_d = B.alloc(3, Z, Y, X, kinds, dev)
+    B.wo_build_tf_device(B.optics_tensor(optics, dev), 3, Z, Y, X, kinds, tf_d, ws_d)
+    torch.cuda.synchronize()
+    # with host optics the y and z passes stop at the batch's largest support
+    # radius (+2 bins); compare the columns both paths transform
+    r = max((2 * o["na_det"] if "fluor" in kinds else o["na_det"] + min(o["na_det"], o["na_ill"] + np.hypot(
+        o["tilt_x"], o["tilt_y"]))) / o["lambda_um"] * X * o["pixel_um"] for o in optics)
+    xc = min(X // 2 + 1, int(np.ceil(r)) + 3)
+    sh, _ = B.tf_views(tf_h, 3, Z, Y, X, kinds)
+    sd, _ = B.tf_views(tf_d, 3, Z, Y, X, kinds)
+    assert torch.equal(sd[..., :xc], sh[..., :xc])
 
 
 def test_tf_point_source_and_pooled_screen_optics(env):
