@@ -14,8 +14,10 @@
 // kinds allow it: with the defocus derivative the row w = 2K (Re g + i Re g')
 // gives both TF rows from one transform (g' = conj(a') b + conj(a) b'):
 //   H(k) = (W(k) + W*(-k)) / 2,   dH(k) = (W(k) - W*(-k)) / (2i).
-// Label-free rows use the complex g = 2K conj(a) b as before:
+// Label-free rows use the complex g = 2K conj(a) b:
 //   H_re(k) = (G(k) + G*(-k)) / 2,   H_im(k) = i (G(k) - G*(-k)) / 2.
+// Single real rows (fluorescence, or one label-free kind) pair up across two
+// rows of the bank instead (k_psf_rows_pair).
 // W*(-k) lives in the lane that owns N - k; it is fetched with a shuffle.
 #include "wo_fft.cuh"
 #include "wo_internal.h"
