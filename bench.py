@@ -469,6 +469,35 @@ def run_e2e(args, B, o, data, out, tf, ws, stream, barrier, world, dev):
     return timed(len(lanes)), serial
 
 
+def torch_fft_forward(H, f, bg):
+    """The widefield forward model written with torch.fft and torch elementwise
+    ops: H the (phase, absorption, fluorescence) half-spectrum TFs (3, Z, Y, Xh),
+    f the three property volumes (3, Z, Y, X); returns the brightfield and
+    fluorescence stacks (2, Z, Y, X) with backgrounds bg added."""
+    import torch
+    dims = (-3, -2, -1)
+    F = torch.fft.rfftn(f, dim=dims)
+    D = torch.stack((H[0] * F[0] + H[1] * F[1], H[2] * F[2]))
+    d = torch.fft.irfftn(D, s=tuple(f.shape[-3:]), dim=dims)
+    d[0] += bg[0]
+    d[1] += bg[1]
+    return d
+
+
+def torch_fft_reconstruct(H, d, eta):
+    """The widefield 3D Tikhonov reconstruction written the same way: channel
+    means as backgrounds, relative eta per contrast mode, the label-free 1 x 2
+    block by its push-through form and the fluorescence 1 x 1 block."""
+    import torch
+    dims = (-3, -2, -1)
+    w_re = float(eta[0]) * float(((H[0].abs() ** 2) + (H[1].abs() ** 2)).max())
+    w_fl = float(eta[1]) * float((H[2].abs() ** 2).max())
+    D = torch.fft.rfftn(d - d.mean(dim=dims, keepdim=True), dim=dims)
+    g = D[0] / ((H[0].abs() ** 2) + (H[1].abs() ** 2) + w_re)
+    F = torch.stack((H[0].conj() * g, H[1].conj() * g, H[2].conj() * D[1] / ((H[2].abs() ** 2) + w_fl)))
+    return torch.fft.irfftn(F, s=tuple(d.shape[-3:]), dim=dims)
+
+
 def library_leg(args, B, tf, ws, data, out, stream, dev):
     """The same forward model and reconstruction written with torch.fft (cuFFT)
     and torch elementwise ops on the same TF bank and shapes - the style of a
@@ -480,28 +509,16 @@ def library_leg(args, B, tf, ws, data, out, stream, dev):
     Xh = X // 2 + 1
     spectra = tf[: 3 * Z * Y * Xh * 8]  # the bank's spectra; its per-tile statistics block follows them
     H = torch.view_as_complex(spectra.view(torch.float32).view(3, Z, Y, Xh, 2))  # phase, absorption, fluorescence
-    dims = (-3, -2, -1)
     bg = [1.0, 0.1]
     f_vol = torch.empty((1, 3, Z, Y, X), dtype=torch.float32, device=dev)
     f_vol.copy_(out)
     d_lib = torch.empty((1, 2, Z, Y, X), dtype=torch.float32, device=dev)
-    w_re = float(ETA[0]) * float(((H[0].abs() ** 2) + (H[1].abs() ** 2)).max())
-    w_fl = float(ETA[1]) * float((H[2].abs() ** 2).max())
 
     def torch_forward():
-        F = torch.fft.rfftn(f_vol[0], dim=dims)
-        D = torch.stack((H[0] * F[0] + H[1] * F[1], H[2] * F[2]))
-        d = torch.fft.irfftn(D, s=(Z, Y, X), dim=dims)
-        d[0] += bg[0]
-        d[1] += bg[1]
-        return d
+        return torch_fft_forward(H, f_vol[0], bg)
 
     def torch_reconstruct():
-        r = data[0] - data[0].mean(dim=dims, keepdim=True)
-        D = torch.fft.rfftn(r, dim=dims)
-        g = D[0] / ((H[0].abs() ** 2) + (H[1].abs() ** 2) + w_re)  # push-through form, C = 1 < P = 2
-        F = torch.stack((H[0].conj() * g, H[1].conj() * g, H[2].conj() * D[1] / ((H[2].abs() ** 2) + w_fl)))
-        return torch.fft.irfftn(F, s=(Z, Y, X), dim=dims)
+        return torch_fft_reconstruct(H, data[0], ETA)
 
     def lib_forward():
         B.wo_forward(tf, KINDS, f_vol, bg, d_lib, 1, Z, Y, X, ws)
