@@ -484,14 +484,21 @@ def torch_fft_forward(H, f, bg):
     return d
 
 
-def torch_fft_reconstruct(H, d, eta):
+def torch_fft_eta(H, eta):
+    """Absolute eta per contrast mode (relative eta times the mode's largest
+    sum of |H|^2), as device scalars: formed once per TF bank, as the library
+    forms its regulariser maxima in the TF build."""
+    return (float(eta[0]) * ((H[0].abs() ** 2) + (H[1].abs() ** 2)).max(), float(eta[1]) * (H[2].abs() ** 2).max())
+
+
+def torch_fft_reconstruct(H, d, w):
     """The widefield 3D Tikhonov reconstruction written the same way: channel
-    means as backgrounds, relative eta per contrast mode, the label-free 1 x 2
-    block by its push-through form and the fluorescence 1 x 1 block."""
+    means as backgrounds, absolute eta w = (label-free, fluorescence) from
+    torch_fft_eta, the label-free 1 x 2 block by its push-through form and the
+    fluorescence 1 x 1 block."""
     import torch
     dims = (-3, -2, -1)
-    w_re = float(eta[0]) * float(((H[0].abs() ** 2) + (H[1].abs() ** 2)).max())
-    w_fl = float(eta[1]) * float((H[2].abs() ** 2).max())
+    w_re, w_fl = w
     D = torch.fft.rfftn(d - d.mean(dim=dims, keepdim=True), dim=dims)
     g = D[0] / ((H[0].abs() ** 2) + (H[1].abs() ** 2) + w_re)
     F = torch.stack((H[0].conj() * g, H[1].conj() * g, H[2].conj() * D[1] / ((H[2].abs() ** 2) + w_fl)))
@@ -517,8 +524,10 @@ def library_leg(args, B, tf, ws, data, out, stream, dev):
     def torch_forward():
         return torch_fft_forward(H, f_vol[0], bg)
 
+    w_abs = torch_fft_eta(H, ETA)
+
     def torch_reconstruct():
-        return torch_fft_reconstruct(H, data[0], ETA)
+        return torch_fft_reconstruct(H, data[0], w_abs)
 
     def lib_forward():
         B.wo_forward(tf, KINDS, f_vol, bg, d_lib, 1, Z, Y, X, ws)

@@ -73,7 +73,7 @@ def test_torch_fft_composition_matches_the_oracle():
     want = OM.forward(modes, f, [1.0, 0.1])
     assert np.linalg.norm(d - want) <= 1e-12 * np.linalg.norm(want)
     data = want + rng.normal(0.0, 1e-3, want.shape)
-    got = bench.torch_fft_reconstruct(H, torch.from_numpy(data), [1e-3, 1e-3]).numpy()
+    got = bench.torch_fft_reconstruct(H, torch.from_numpy(data), bench.torch_fft_eta(H, [1e-3, 1e-3])).numpy()
     ref = OM.reconstruct(modes, data, 1e-3)
     assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
 
