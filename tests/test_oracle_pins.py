@@ -408,6 +408,23 @@ def test_relative_eta_definition():
     assert np.abs(a - b).max() <= 1e-14 * np.abs(a).max()
 
 
+def test_relative_eta_2d_is_the_3d_plane_sum_by_parseval():
+    # 2D mode: eta_abs = eta * max over nu_perp of sum_j |H_j|^2 over the
+    # planes; by Parseval over z that is (1/Z) sum over k_z of the 3D TF's
+    # |H|^2, an independent route through the z-DFT
+    o = ph.optics(na_ill=0.6, defocus_um=0.3)
+    shape = (6, 16, 16)
+    Z = shape[0]
+    Hj = O.plane_tfs(o, shape, ("phase",))["phase"]
+    H3 = O.transfer_functions(o, shape, ("phase",))["phase"]
+    mx = float(np.max(np.sum(np.abs(H3) ** 2, axis=0) / Z))
+    modes = [dict(channels=[0], props=[0], H=[[Hj]])]
+    d = 1.0 + 0.01 * np.random.default_rng(4).normal(size=(1,) + shape)
+    a = model.reconstruct_2d(modes, d, 1e-2, relative=True)
+    b = model.reconstruct_2d(modes, d, 1e-2 * mx, relative=False)
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
+
+
 # ------------------------------------------------------------ tiles (a8)
 def test_mirror_index():
     assert tiles.mirror(np.arange(-2, 7), 5).tolist() == [2, 1, 0, 1, 2, 3, 4, 3, 2]
@@ -556,6 +573,11 @@ def test_smooth_source_edge_values():
     assert np.abs(S - Sh)[far].max() <= 1e-4
     o2 = dict(o, na_ill=float(d[3, 4] * lam))  # a grid point exactly on the edge
     assert abs(O.source_pupil(o2, Y, X)[3, 4] - 0.5) <= 1e-12
+    # the edge width is one frequency bin of the coarser axis: 1 / (32 * 0.1 um)
+    # = 0.3125 /um here, so a grid point that far outside the circle has
+    # S = 1 / (1 + e)
+    o3 = dict(o, na_ill=float((d[3, 4] - 0.3125) * lam))
+    assert abs(O.source_pupil(o3, Y, X)[3, 4] - 1.0 / (1.0 + np.e)) <= 1e-12
 
 
 def test_smooth_source_derivatives_match_finite_differences():
@@ -689,6 +711,42 @@ def test_estimator_features_properties():
     assert np.allclose(fb[0, :Z], fa[0, :Z][::-1], atol=1e-12)
     assert np.allclose(fb[1, : Z - 1], -fa[1, : Z - 1][::-1], atol=1e-12)
     assert np.allclose(E.tile_features(1 + 3.0 * (stack - 1), o)[0], fa[0], atol=1e-12)
+
+
+def test_adam_first_steps_move_by_the_learning_rate():
+    # Kingma and Ba (2015): with bias correction the first step is lr * sign(g)
+    # for |g| >> eps, and so is every step of a constant gradient
+    from oracle import estimator as E
+    g = np.array([3.0, -0.5, 1e-3, -200.0])
+    w, m, v = np.zeros(4), np.zeros(4), np.zeros(4)
+    for step in (1, 2, 3):
+        w1, m, v = E.adam(w, g, m, v, step, 0.01)
+        assert np.allclose(w1 - w, -0.01 * np.sign(g), rtol=1e-4, atol=0)
+        w = w1
+
+
+def test_estimator_feature_bins_floor():
+    # a plane wave at k_x = 7 on a 64-pixel, 0.1 um grid: |nu| = 7 / 6.4 um^-1,
+    # which is 15.52 in units of (2 NA / lambda) / 64 at NA 1.2, lambda
+    # 0.532 um, so all its power sits in radial bin 15
+    from oracle import estimator as E
+    o = ph.optics()
+    Z, Y, X = 4, 64, 64
+    x = np.arange(X)
+    d = np.stack([np.cos(2 * np.pi * 7 * x / X + 0.3 * j)[None, :] * np.ones((Y, 1)) for j in range(Z)])
+    f = E.tile_features(d, o)
+    p = np.expm1(f[0, :Z])  # power per bin over the mean power per bin
+    assert np.all(p[:, 15] > 0) and np.abs(np.delete(p, 15, axis=1)).max() <= 1e-12
+
+
+@pytest.mark.parametrize("Z", [1, 3, 4, 6, 8])
+def test_estimator_rows_are_the_planes_in_axial_order(Z):
+    # natural row r holds the plane displaced by (r - Z//2) steps: the storage
+    # index (FFT order) whose signed index is r - Z//2
+    from oracle import estimator as E
+    k = O.fft_indices(Z)
+    for r in range(Z):
+        assert k[E.natural_plane(r, Z)] == r - Z // 2
 
 
 # ------------------------------------------------- aberrated detection pupils
