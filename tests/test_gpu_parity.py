@@ -86,7 +86,8 @@ def test_tf_tiles_each_with_own_optics(env):
     check_tf(env, optics, (8, 32, 32), OO.KINDS)
 
 
-@pytest.mark.parametrize("shape", [(3, 3, 32), (3, 3, 64), (1, 3, 128), (3, 3, 512), (1, 3, 256)])
+@pytest.mark.parametrize("shape", [(3, 3, 32), (3, 3, 64), (3, 3, 96), (1, 3, 128), (1, 3, 192), (3, 3, 512),
+                                   (1, 3, 256)])
 @pytest.mark.parametrize("kinds", [("fluor",), ("absorption",), ("phase", "fluor"), ("phase", "absorption", "fluor")])
 def test_tf_odd_rows_per_tile(env, shape, kinds):
     # Z*Y odd with three tiles: consecutive rows that share a transform belong
