@@ -229,3 +229,104 @@ def test_status_strings(B):
     for s in range(9):
         assert B.wo_status_string(s)
     assert B.wo_status_string(99) == "unknown status"
+
+
+def test_device_optics_build_validation(B):
+    lib = B._lib
+    fake = 1 << 20
+    big = 1 << 40
+    f = lib.wo_build_tf_device
+    assert f(fake + 4, 1, 16, 64, 64, 1, fake, fake, big, None) == 1   # optics not 8-byte aligned
+    assert f(None, 1, 16, 64, 64, 1, fake, fake, big, None) == 1
+    assert f(fake, 1, 16, 64, 64, 1, fake + 8, fake, big, None) == 1   # TF bank not 16-byte aligned
+    assert f(fake, 1, 16, 64, 63, 1, fake, fake, big, None) == 2       # odd X
+    assert f(fake, 1, 16, 64, 62, 1, fake, fake, big, None) == 3       # X/2 = 31
+    assert f(fake, 1, 16, 64, 64, 1, fake, fake, 1024, None) == 8      # workspace too small
+
+
+def test_fusion_validation(B):
+    lib = B._lib
+    fake = 1 << 20
+    big = 1 << 40
+    Z, Y, X = 16, 64, 64
+    half = Z * Y * (X // 2 + 1) * 8
+
+    def a256(n):
+        return (n + 255) // 256 * 256
+
+    # nine apertures of two tiles: all channel spectra, one fused spectrum per tile, two floats per tile
+    assert B.wo_fused_workspace_bytes(9, 2, Z, Y, X) == a256(18 * half) + a256(2 * half) + a256(2 * 2 * 4)
+    assert B.wo_fused_workspace_bytes(17, 1, Z, Y, X) == 0     # more than 16 channels
+    assert B.wo_fused_workspace_bytes(9, 7282, Z, Y, X) == 0   # more than 65535 TF entries
+    assert B.wo_fused_workspace_bytes(9, 1, Z, Y, 63) == 0     # odd X
+    g = lib.wo_reconstruct_fused
+    F = ctypes.c_float
+    nan_bg = (F * 9)(*([1.0] * 8 + [float("nan")]))
+    pb = ctypes.cast(nan_bg, ctypes.POINTER(F))
+    ok = (fake, 9, fake, None, 1e-3, 0, 0, fake, 1, Z, Y, X, fake, big, None)
+
+    def call(**kw):
+        names = ("tf", "C", "d", "bg", "eta", "flag", "mode", "f", "n", "Z", "Y", "X", "ws", "wsb", "s")
+        args = dict(zip(names, ok))
+        args.update(kw)
+        return g(*[args[n] for n in names])
+
+    assert call(C=0) == 1 and call(C=17) == 1
+    assert call(flag=2) == 1 and call(mode=5) == 1
+    assert call(eta=-1.0) == 1 and call(eta=float("nan")) == 1 and call(eta=float("inf")) == 1
+    assert call(bg=pb) == 1                       # a non-finite background
+    assert call(d=fake + 4) == 1 and call(f=None) == 1
+    assert call(X=63) == 2 and call(X=62) == 3
+    assert call(wsb=1024) == 8
+
+
+def test_estimator_validation(B):
+    lib = B._lib
+    from oracle import estimator as E
+    # conv 3->32->64->96->128 (3x3, with biases), linear 128->4: the header's
+    # network, counted by hand, and the oracle's parameter list agree
+    n = sum(ci * co * 9 + co for ci, co in ((3, 32), (32, 64), (64, 96), (96, 128))) + 128 * 4 + 4
+    assert B._lib.wo_est_param_count() == n == E.n_params() == 186020
+    ws1, ws64 = lib.wo_est_workspace_bytes(1), lib.wo_est_workspace_bytes(64)
+    assert 0 < ws1 < ws64 and lib.wo_est_workspace_bytes(4096) > ws64
+    assert lib.wo_est_workspace_bytes(0) == 0 and lib.wo_est_workspace_bytes(4097) == 0
+    fake = 1 << 20
+    big = 1 << 40
+    F = ctypes.c_float
+    sc = (F * 4)(1.0, 1.0, 1.0, 1.0)
+    off = (F * 4)(0.0, 0.0, 0.0, 0.0)
+    zero = (F * 4)(1.0, 0.0, 1.0, 1.0)
+    ps, po, pz = (ctypes.cast(a, ctypes.POINTER(F)) for a in (sc, off, zero))
+    fwd = lib.wo_est_forward
+    assert fwd(fake, fake, fake, 0, ps, po, fake, fake, big, None) == 1       # batch 0
+    assert fwd(fake, fake, fake, 4097, ps, po, fake, fake, big, None) == 1    # batch above 4096
+    assert fwd(fake, fake, fake + 8, 4, ps, po, fake, fake, big, None) == 1   # misaligned features
+    assert fwd(fake, fake, fake, 4, pz, po, fake, fake, big, None) == 1       # a zero scale
+    assert fwd(fake, fake, fake, 4, None, po, fake, fake, big, None) == 1
+    assert fwd(fake, fake, fake, 4, ps, po, fake, fake, ws1, None) == 8       # workspace for one tile
+    bwd = lib.wo_est_backward
+    assert bwd(fake, fake, fake, fake + 4, 4, ps, po, None, None, fake, big, None) == 1  # misaligned targets
+    assert bwd(fake, fake, fake, fake, 4, ps, po, fake + 4, None, fake, big, None) == 1  # misaligned gradient
+    step = lib.wo_est_train_step
+    assert step(fake, fake, fake, fake, fake, fake, 4, ps, po, 0, 1e-3, None, fake, big, None) == 1  # step 0
+    assert step(fake, fake, fake, fake, fake, fake, 4, ps, po, 1, -1e-3, None, fake, big, None) == 1
+    assert step(fake, fake, fake, fake, fake, fake, 4, ps, po, 1, float("nan"), None, fake, big, None) == 1
+    assert step(fake, fake, fake + 8, fake, fake, fake, 4, ps, po, 1, 1e-3, None, fake, big, None) == 1
+    assert lib.wo_est_sync_bf16(fake + 8, fake, None) == 1
+    feat = lib.wo_est_features
+    assert feat(fake, fake, 4, 1, 64, 64, fake, None) == 2     # one plane
+    assert feat(fake, fake, 4, 65, 64, 64, fake, None) == 2    # more than 64 planes
+    assert feat(fake, fake, 4, 16, 64, 63, fake, None) == 2    # odd X
+    assert feat(fake, fake + 4, 4, 16, 64, 64, fake, None) == 1
+    ph_ = lib.wo_thin_phantom
+    assert ph_(fake, 4, -1, 64, 64, 0.1, 0.25, fake, None) == 2
+    assert ph_(fake, 4, 8, 64, 64, 0.0, 0.25, fake, None) == 1
+    assert ph_(fake, 4, 8, 64, 64, 0.1, float("nan"), fake, None) == 1
+    assert ph_(fake + 4, 4, 8, 64, 64, 0.1, 0.25, fake, None) == 1
+
+
+def test_launch_counter_is_host_side(B):
+    # counting needs no device: failed validations launch nothing
+    n0 = B._lib.wo_launch_count()
+    assert B._lib.wo_forward(1 << 20, 7, (1 << 20) + 8, None, 1 << 20, 1, 16, 64, 64, 1 << 20, 1 << 40, None) == 1
+    assert B._lib.wo_launch_count() == n0
