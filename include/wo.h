@@ -52,7 +52,8 @@ typedef enum {
   WO_ERR_UNSUPPORTED_SIZE = 3, /* an FFT length outside the supported set */
   WO_ERR_UNDERSAMPLED = 4,     /* optics alias on this grid (see wo_build_tf) */
   WO_ERR_CUDA = 5,             /* a CUDA launch or runtime call failed */
-  WO_ERR_TIMEOUT = 6,          /* a bounded device-side wait expired */
+  WO_ERR_TIMEOUT = 6,          /* a bounded device-side wait expired (reserved: no kernel of
+                                  this version waits on another, so none returns it) */
   WO_ERR_OPTICS = 7,           /* physically invalid optics (e.g. NA_det >= n) */
   WO_ERR_WORKSPACE = 8         /* workspace smaller than wo_workspace_bytes() */
 } wo_status;
