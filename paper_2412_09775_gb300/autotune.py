@@ -17,7 +17,8 @@ source pupil; every step of the arithmetic runs in the library's kernels:
   in one pass, its backward returns that gradient times the incoming one.
 * ``TuningProblem.run`` applies a schedule of ``Phase``s of Adam steps
   (wo_adam_optics, state on the device), eagerly or replayed from one
-  captured CUDA graph.
+  captured CUDA graph; ``state_dict`` / ``load_state_dict`` checkpoint and
+  resume the optics and the Adam state.
 """
 from __future__ import annotations
 
@@ -97,6 +98,24 @@ class TuningProblem:
         """Back to the starting optics, Adam state cleared."""
         self.optics.copy_(self.optics0)
         self.state.zero_()
+
+    def state_dict(self) -> dict:
+        """Checkpoint of the tuning state as host arrays: the current and the
+        starting optics (float64 [n, 9], wo_optics field order) and the Adam
+        state (float64 [n, n_params, 3]: m, v and the step count per
+        parameter)."""
+        return {"optics": self.optics.cpu().numpy().copy(), "optics0": self.optics0.cpu().numpy().copy(),
+                "adam": self.state.cpu().numpy().copy()}
+
+    def load_state_dict(self, sd: dict):
+        """Resume from a ``state_dict`` of a problem over the same tiles and
+        parameters.  The arrays are copied into the existing device buffers,
+        so graphs captured by ``run`` stay valid and continue from there."""
+        for name, t in (("optics", self.optics), ("optics0", self.optics0), ("adam", self.state)):
+            a = torch.as_tensor(sd[name], dtype=t.dtype)
+            if tuple(a.shape) != tuple(t.shape):
+                raise ValueError(f"{name}: shape {tuple(a.shape)}, expected {tuple(t.shape)}")
+            t.copy_(a)
 
     def evaluate(self, nu_max: float = 0.0):
         """Loss and gradient of every tile at the current optics."""

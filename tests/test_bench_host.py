@@ -1,6 +1,7 @@
-"""Host-side logic of bench.py (CPU only): the column limits and algorithmic
-byte counts behind its roofline figures, the torch.fft composition it times
-beside the library, and the reference arm's JSON line.
+"""Host-side logic of bench.py and the auto-tuning driver (CPU only): the
+column limits and algorithmic byte counts behind the roofline figures, the
+torch.fft composition timed beside the library, the reference arm's JSON
+line, and the tuning state's checkpoint round trip.
 """
 import json
 import os
@@ -87,3 +88,24 @@ def test_reference_arm_prints_its_line():
     assert line["metric"] == bench.METRIC and line["higher_is_better"] is True
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_tuning_state_checkpoint_round_trip():
+    # host logic of TuningProblem.state_dict / load_state_dict on CPU tensors
+    torch = pytest.importorskip("torch")
+    from paper_2412_09775_gb300.autotune import TuningProblem
+    p = TuningProblem.__new__(TuningProblem)
+    rng = np.random.default_rng(3)
+    p.optics = torch.from_numpy(rng.normal(size=(5, 9)))
+    p.optics0 = torch.from_numpy(rng.normal(size=(5, 9)))
+    p.state = torch.from_numpy(rng.normal(size=(5, 4, 3)))
+    sd = p.state_dict()
+    want = {k: v.copy() for k, v in sd.items()}
+    p.optics.zero_(), p.optics0.zero_(), p.state.zero_()
+    # the checkpoint holds copies: clearing the buffers left it unchanged
+    assert all(np.array_equal(sd[k], want[k]) for k in want)
+    p.load_state_dict(sd)
+    assert np.array_equal(p.optics.numpy(), want["optics"]) and np.array_equal(p.state.numpy(), want["adam"])
+    assert np.array_equal(p.optics0.numpy(), want["optics0"])
+    with pytest.raises(ValueError):
+        p.load_state_dict(dict(want, adam=np.zeros((5, 1, 3))))
