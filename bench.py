@@ -1,22 +1,29 @@
 """Benchmark of the hot path: transfer-function build + Tikhonov reconstruction.
 
-One step = build the phase, absorption and fluorescence transfer functions
-of a 96 x 512 x 512 widefield stack from its optics, then reconstruct the
-three property volumes (label-free 1 x 2 and fluorescence 1 x 1 per-frequency
-solves, relative eta = 1e-3, background = channel means) from the two data
-stacks (brightfield, fluorescence).  Inputs are synthetic (seeded phantom,
-forward-simulated, 1e-3 Gaussian noise) and resident in HBM; the working set
-(~0.2 GB of data, 0.3 GB of TFs, 0.6 GB of workspace) exceeds the 129 MB L2,
-so no flush is needed between steps.
+Default line (``--workload field``): the shift-variant field, 48 x 2048 x 2048,
+cut into 256 overlapping tiles of 48 x 192 x 192, each with its own optics
+(defocus, illumination tilt, NA_ill).  One step = gather the tiles, build
+every tile's phase transfer function from its device-side optics, reconstruct
+every tile (3D Tikhonov, relative eta 1e-3, channel-mean background) and blend
+the tiles back into the field: 12 launches in one CUDA graph.  The value is
+field voxels/s (tiles/s beside it).  Inputs are synthetic (seeded sphere
+phantom forward-simulated per tile with its tile's optics, 1e-3 Gaussian
+noise) and resident in HBM; the working set (field 805 MB, tiles 1.8 GB, TFs
+1.8 GB) exceeds the 129 MB L2, so no flush is needed between steps.
 
-The same line carries, under "autotune", the second half of the metric: the
-per-tile defocus auto-tuning of 256 tiles of 48 x 128 x 128 (50 Adam steps
-each through the library's adjoint, one CUDA graph), as tiles/s with the
-defocus error reached (``--workload autotune`` prints it as its own line).
+The same line carries the metric's other parts as legs:
+* "autotune": auto-tuning of (defocus, tilt_x, tilt_y, NA_ill) of the same 256
+  tiles of 48 x 192 x 192, 50 Adam steps each through the library's adjoint
+  in one CUDA graph, as tiles/s with the parameter errors reached;
+* "widefield": the 96 x 512 x 512 widefield step (phase + absorption +
+  fluorescence TF build and 3D reconstruction);
+* "small_stacks": one 16 x 64 x 64 reconstruction call (latency) and a batch
+  of 4096 such stacks sharing one TF bank.
+``--workload tiles|widefield|autotune|estimator`` prints one of them alone.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-N > 1 runs under torchrun: every rank reconstructs its own volume (weak
-scaling, no data-path collective); the reported value is the total over ranks.
+N > 1 runs under torchrun: every rank restores its own field (weak scaling,
+no data-path collective); the reported value is the total over ranks.
 """
 from __future__ import annotations
 
@@ -144,6 +151,11 @@ def algorithmic_bytes(shape, kinds, o):
         "y_inv": 2 * P * half,
         "rows_c2r": P * (half + real),
     }
+
+
+def engines_recon(Y):
+    from paper_2412_09775_gb300 import binding as B
+    return {1: "five passes", 2: "tile pipeline"}.get(B.wo_schedule_get(B.WO_PASS_RECON, Y), "?")
 
 
 def pin_rows_engine(args, B, n):
@@ -347,6 +359,15 @@ def cpu_baseline(steps=2):
 
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args, rank, world, local_rank):
+    """The widefield workload as its own line (``--workload widefield``)."""
+    line = widefield_leg(args, rank, world, local_rank, with_tune=not args.no_autotune)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def widefield_leg(args, rank, world, local_rank, with_tune=False):
+    """The widefield 96x512x512 step (TF build + reconstruction) with its
+    e2e, torch.fft comparison and CPU baseline; returns the line (rank 0)."""
     import torch
     from paper_2412_09775_gb300.build import build
     build()
@@ -388,8 +409,8 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
-    B.wo_profile_read()  # drop anything recorded so far
-    B.wo_profile_enable(True)
+    # the timed steps run with the library's profiler off; per-kernel times
+    # come from a separate profiled pass over the same number of steps
     n0 = B.wo_launch_count()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     nvml = NvmlClockSampler(dev)
@@ -401,11 +422,10 @@ def run_gpu(args, rank, world, local_rank):
         torch.cuda.synchronize()
     clk = nvml.summary() or smi.summary()
     launches = B.wo_launch_count() - n0
-    B.wo_profile_enable(False)
-    prof = B.wo_profile_read()
     barrier()
     from paper_2412_09775_gb300.shard import max_over_ranks
     ms_max = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, device=dev)
+    prof = profiled_pass(B, step, args.steps)
 
     # end to end through the public API: host (pinned) in, host out
     if args.no_e2e:
@@ -413,10 +433,26 @@ def run_gpu(args, rank, world, local_rank):
     else:
         e2e_ms = run_e2e(args, B, o, data, out, tf, ws, stream, barrier, world, dev)
     lib = None if args.no_library_fft else library_leg(args, B, tf, ws, data, out, stream, dev)
-    tune = None if args.no_autotune else autotune_leg(args, rank, world, local_rank)
+    del tf, ws, data, out
+    torch.cuda.empty_cache()
+    tune = autotune_leg(args, rank, world, local_rank) if with_tune else None
     if rank != 0:
-        return
-    report(args, world, ms_max, e2e_ms, prof, launches, clk, tune, lib)
+        return None
+    return report(args, world, ms_max, e2e_ms, prof, launches, clk, tune, lib)
+
+
+def profiled_pass(B, step, n):
+    """Per-kernel launches and milliseconds over n eager steps with the
+    library's event profiler on (a pass of its own, outside the timed one)."""
+    import torch
+    torch.cuda.synchronize()
+    B.wo_profile_read()  # drop anything recorded so far
+    B.wo_profile_enable(True)
+    for _ in range(n):
+        step()
+    torch.cuda.synchronize()
+    B.wo_profile_enable(False)
+    return B.wo_profile_read()
 
 
 def run_e2e(args, B, o, data, out, tf, ws, stream, barrier, world, dev):
@@ -617,7 +653,7 @@ def report(args, world, ms_max, e2e_ms, prof, launches, clk, tune=None, lib=None
         line["library_fft"] = lib  # cuFFT-based composition of the same calls, timed beside them
     if tune is not None:
         line["autotune"] = tune  # the metric's second half: auto-tuned tiles/s at fixed error
-    print(json.dumps(line), flush=True)
+    return line
 
 
 # ------------------------------------------------------------------ tiles
@@ -655,7 +691,85 @@ def make_field(o_list, dev, seed=4):
     return field
 
 
+def field_algorithmic_bytes(o_list, Z, E, field_vox):
+    """Compulsory HBM bytes per launch of each kernel family of one field step:
+    gather, the phase TF build from device optics (every half-spectrum column),
+    the 3D reconstruction, blend; summed over the tiles, each with its own
+    detection band and TF support."""
+    Xh = E // 2 + 1
+    real, half = Z * E * E * 4, Z * E * Xh * 8
+    out = {k: 0 for k in ("tf_pupil_record", "tf_arms", "tf_psf_rows", "tf_ypass", "tf_zpass", "rows_r2c", "y_fwd",
+                          "z_fused", "y_inv", "rows_c2r")}
+    for o in o_list:
+        arms = 2 * Z * E * band_columns(o, E) * 8
+        inside = Z * support_columns(o, ("phase",), E, E) * 8
+        out["tf_pupil_record"] += E * E * 16
+        out["tf_arms"] += arms
+        out["tf_psf_rows"] += arms + half
+        out["tf_ypass"] += 2 * half
+        out["tf_zpass"] += 2 * half
+        out["rows_r2c"] += real + half
+        out["y_fwd"] += 2 * half
+        out["z_fused"] += 2 * inside + half
+        out["y_inv"] += 2 * half
+        out["rows_c2r"] += half + real
+    tiles = len(o_list) * Z * E * E * 4
+    # the tile pipeline: every tile's data in, its phase TF in, its result out
+    # (the spectra between its items stay in L2)
+    out["tile_pipeline"] = len(o_list) * (2 * real + half)
+    out["tile_gather"] = 4 * field_vox + tiles
+    out["tile_blend"] = tiles + 4 * field_vox
+    return out
+
+
+def kernel_table(prof, algo, per):
+    """Per kernel family: launches, average ms, share of the profiled time,
+    algorithmic bytes per launch and the GB/s they give."""
+    tot = sum(v[1] for v in prof.values()) or 1e-9
+    out = {}
+    for name, (cnt, t) in prof.items():
+        avg = t / cnt if cnt else 0.0
+        b = algo.get(name)
+        out[name] = {per: cnt, "avg_ms": round(avg, 4), "share": round(t / tot, 4), "algo_bytes": b,
+                     "gbs": round(b / (avg * 1e-3) / 1e9, 1) if b and avg > 0 else None}
+    return out
+
+
+def roofline_of(kern, prof):
+    """The roofline entry of the kernel family with the largest share."""
+    dom = max(prof.items(), key=lambda kv: kv[1][1])[0]
+    peak, peak_kind = peaks()
+    gbs = kern[dom]["gbs"]
+    traffic = None
+    rec = NCU_TRAFFIC.get(dom)
+    if rec and rec.get("digest") == kernel_digest(dom) and rec.get("workload") == "field":
+        traffic = rec["bytes"]
+    return {"bound": "hbm", "kernel": dom, "achieved": gbs, "peak": peak, "unit": "GB/s",
+            "frac": round(gbs / peak, 4) if gbs else None, "traffic": traffic,
+            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+            else "fallback 6.8 TB/s"}
+
+
 def run_tiles(args, rank, world, local_rank):
+    """The shift-variant field as the headline line, with the auto-tuning,
+    widefield and small-stack legs unless --field-only."""
+    import torch
+    line = field_leg(args, rank, world, local_rank)
+    if not args.field_only:
+        tune = None if args.no_autotune else autotune_leg(args, rank, world, local_rank)
+        wide = widefield_leg(args, rank, world, local_rank)
+        small = small_stack_leg(args, rank, world, local_rank)
+        if rank == 0:
+            if tune is not None:
+                line["autotune"] = tune  # the metric's second half: auto-tuned tiles/s at fixed error
+            line["widefield"] = wide
+            line["small_stacks"] = small
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    torch.cuda.synchronize()
+
+
+def field_leg(args, rank, world, local_rank):
     import torch
     import phantom as ph
     from paper_2412_09775_gb300.build import build
@@ -677,11 +791,14 @@ def run_tiles(args, rank, world, local_rank):
     B.wo_autotune(n, Z, E, E, ("phase",), ws)
     pin_rows_engine(args, B, E // 2)
 
+    def step_on(fld, dst, tl, rc, tfb, wsb, opt):
+        B.wo_tile_gather(fld, Z, ty, tx, TILE_CORE, TILE_HALO, tl)
+        B.wo_build_tf_device(opt, n, Z, E, E, ("phase",), tfb, wsb)
+        B.wo_reconstruct(tfb, ("phase",), tl, None, [1e-3], B.WO_ETA_RELATIVE, B.WO_MODE_3D, rc, n, Z, E, E, wsb)
+        B.wo_tile_blend(rc, Z, ty, tx, TILE_CORE, TILE_HALO, dst)
+
     def step():
-        B.wo_tile_gather(field, Z, ty, tx, TILE_CORE, TILE_HALO, tiles)
-        B.wo_build_tf_device(optics, n, Z, E, E, ("phase",), tf, ws)
-        B.wo_reconstruct(tf, ("phase",), tiles, None, [1e-3], B.WO_ETA_RELATIVE, B.WO_MODE_3D, rec, n, Z, E, E, ws)
-        B.wo_tile_blend(rec, Z, ty, tx, TILE_CORE, TILE_HALO, out)
+        step_on(field, out, tiles, rec, tf, ws, optics)
 
     s = torch.cuda.Stream(device=dev)
     s.wait_stream(torch.cuda.current_stream())
@@ -689,14 +806,6 @@ def run_tiles(args, rank, world, local_rank):
         for _ in range(max(1, args.warmup)):
             step()
     torch.cuda.synchronize()
-    # per-kernel times from one eager, profiled step (events do not enter the graph)
-    B.wo_profile_read()
-    B.wo_profile_enable(True)
-    with torch.cuda.stream(s):
-        step()
-    torch.cuda.synchronize()
-    B.wo_profile_enable(False)
-    prof = B.wo_profile_read()
     n0 = B.wo_launch_count()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=s):
@@ -710,21 +819,43 @@ def run_tiles(args, rank, world, local_rank):
         dist.barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     nvml = NvmlClockSampler(dev)
-    with nvml:
+    with ClockSampler(local_rank) as smi, nvml:
         ev0.record()
         for _ in range(args.steps):
             g.replay()
         ev1.record()
         torch.cuda.synchronize()
+    clk = nvml.summary() or smi.summary()
     ms_max = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, device=dev)
-    if rank != 0:
-        return
+    # per-kernel times from eager profiled steps (the events do not enter a graph)
+    with torch.cuda.stream(s):
+        prof = profiled_pass(B, step, args.steps)
+    # the same step with the reconstruction on its five-pass engine instead of
+    # the tile pipeline (context for the engine choice)
+    B.wo_schedule_set(B.WO_PASS_RECON, E, B.WO_ENGINE_SMEM)
+    g5 = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        step()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g5, stream=s):
+        step()
+    B.wo_schedule_set(B.WO_PASS_RECON, E, B.WO_ENGINE_DEFAULT)
+    for _ in range(args.warmup):
+        g5.replay()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        g5.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    passes_ms = e0.elapsed_time(e1) / args.steps
+    del g5
+    code = B.wo_sync_status(ws)
     vox = float(field.numel())
-    peak, peak_kind = peaks()
-    per_kernel = {}
-    tot = sum(v[1] for v in prof.values())
-    for name, (cnt, t) in prof.items():
-        per_kernel[name] = {"launches": cnt, "avg_ms": round(t / cnt, 4), "share": round(t / tot, 4)}
+    kern = kernel_table(prof, field_algorithmic_bytes(o_list, Z, E, vox), "launches")
+    e2e = None if args.no_e2e else field_e2e(args, B, step_on, field, o_list, n, Z, E, world, dev)
+    if rank != 0:
+        return None
     line = {
         "metric": METRIC, "value": round(job_throughput(vox, world, ms_max), 1), "unit": "voxels/s",
         "tiles_per_s": round(job_throughput(n, world, ms_max), 1), "n_gpus": world, "steps": args.steps,
@@ -733,24 +864,236 @@ def run_tiles(args, rank, world, local_rank):
         "data": "synthetic (sphere phantom forward-simulated per tile with its own optics + 1e-3 noise)",
         "config": {"workload": TILES_WORKLOAD, "field": [Z, ty * TILE_CORE, tx * TILE_CORE], "tiles": n,
                    "tile": [Z, E, E], "eta_relative": 1e-3, "parallelism": f"replicas x{world}",
-                   "l2": "working set > L2 (field 805 MB, tiles 1.8 GB, TF 1.8 GB)", "schedule": engines(E, Z, rows=E // 2)},
-        "kernels": per_kernel, "gpu_launches": int(per_step_launches * args.steps),
-        "clocks": nvml.summary(), "peak_hbm_gbs": peak,
+                   "l2": "working set > L2, no flush needed (field 805 MB, tiles 1.8 GB, TF 1.8 GB)",
+                   "schedule": engines(E, Z, rows=E // 2)},
+        "roofline": roofline_of(kern, prof), "kernels": kern,
+        "gpu_launches": int(per_step_launches * args.steps), "clocks": clk,
+        "e2e": e2e,
+        "recon_engine": {"engine": engines_recon(E), "step_ms_with_five_passes": round(passes_ms, 4),
+                         "device_status": list(code)},
     }
-    print(json.dumps(line), flush=True)
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = field_cpu_baseline(field, o_list)
+    del tiles, rec, tf, ws, field, out
+    torch.cuda.empty_cache()
+    return line
+
+
+def field_e2e(args, B, step_on, field, o_list, n, Z, E, world, dev):
+    """The field step through the public API from pinned host memory: the
+    48x2048x2048 field copied in, gather + TF build + reconstruction + blend,
+    the restored field copied out, every step.  Consecutive steps go round
+    ``args.e2e_streams`` streams, each with its own device buffers, so one
+    step's copies overlap the others' kernels; also timed serially."""
+    import torch
+    from paper_2412_09775_gb300.shard import job_throughput, max_over_ranks
+    stream = torch.cuda.current_stream()
+    h_in = torch.empty(field.shape, dtype=torch.float32, pin_memory=True)
+    h_in.copy_(field.cpu())
+    lanes = []
+    for i in range(max(1, args.e2e_streams)):
+        tfb, wsb = B.alloc(n, Z, E, E, ("phase",), dev)
+        lanes.append(dict(s=torch.cuda.Stream(device=dev), d_in=torch.empty_like(field), d_out=torch.empty_like(field),
+                          tl=torch.empty((n, Z, E, E), dtype=torch.float32, device=dev),
+                          rc=torch.empty((n, Z, E, E), dtype=torch.float32, device=dev), tf=tfb, ws=wsb,
+                          opt=B.optics_tensor(o_list, dev),
+                          h_out=torch.empty(field.shape, dtype=torch.float32, pin_memory=True)))
+
+    def e2e_step(ln):
+        with torch.cuda.stream(ln["s"]):
+            ln["d_in"].copy_(h_in, non_blocking=True)
+            step_on(ln["d_in"], ln["d_out"], ln["tl"], ln["rc"], ln["tf"], ln["ws"], ln["opt"])
+            ln["h_out"].copy_(ln["d_out"], non_blocking=True)
+
+    def timed(n_lanes):
+        for i in range(max(1, args.warmup)):
+            e2e_step(lanes[i % n_lanes])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for ln in lanes[:n_lanes]:
+            ln["s"].wait_stream(stream)  # the timed region starts before any lane's first copy
+        for i in range(args.steps):
+            e2e_step(lanes[i % n_lanes])
+        for ln in lanes[:n_lanes]:
+            stream.wait_stream(ln["s"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(e0.elapsed_time(e1) / args.steps, device=dev)
+
+    serial = timed(1)
+    piped = timed(len(lanes))
+    vox = float(field.numel())
+    ok = bool(torch.equal(lanes[0]["h_out"], lanes[-1]["h_out"]))
+    del lanes
+    torch.cuda.empty_cache()
+    return {"value": round(job_throughput(vox, world, piped), 1), "unit": "voxels/s", "ms_per_step": round(piped, 4),
+            "h2d_bytes_per_step": int(vox * 4), "d2h_bytes_per_step": int(vox * 4), "streams": args.e2e_streams,
+            "serial_ms_per_step": round(serial, 4), "serial_value": round(job_throughput(vox, world, serial), 1),
+            "lanes_agree": ok,
+            "note": "pinned host field in, pinned host field out, every step, through the binding's calls "
+                    "(gather, TF build from device optics, reconstruction, blend); consecutive steps go round "
+                    "the streams, each with its own device buffers; serial_*: one stream"}
+
+
+def _oracle_tile(job):
+    """Worker of the CPU baseline: the float64 oracle's phase TF build and 3D
+    Tikhonov reconstruction of one tile (relative eta 1e-3, channel mean)."""
+    from oracle import model as OM, optics as OO
+    o, d = job
+    tfs = OO.transfer_functions(o, d.shape, ("phase",))
+    modes, _, _ = OM.widefield_system(tfs, ("phase",))
+    return OM.reconstruct(modes, d[None].astype(np.float64), 1e-3)[0].astype(np.float32)
+
+
+def _pool_map(jobs, workers):
+    """The oracle over `jobs` in a pool of `workers` processes (spawned, so no
+    worker inherits the CUDA context); returns the results and the seconds."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers) as pool:
+        pool.map(_oracle_tile, jobs[:workers], chunksize=1)  # start-up and imports outside the clock
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_tile, jobs, chunksize=1)
+        dt = time.perf_counter() - t0
+    return res, dt
+
+
+def field_cpu_baseline(field, o_list):
+    """The float64 oracle on the host cores for the field workload: gather,
+    per-tile TF build + reconstruction, blend.  One core over 8 tiles, and a
+    pool of one worker per host core over the tiles (all 256 with 16 or more
+    cores, else 16 per core), both scaled to the whole field."""
+    from oracle import tiles as OTl
+    ty, tx = TILE_GRID
+    n = ty * tx
+    fld = field.cpu().numpy()
+    t0 = time.perf_counter()
+    tl = OTl.gather(fld, ty, tx, TILE_CORE, TILE_HALO)
+    t_gather = time.perf_counter() - t0
+    jobs = [(o_list[t], tl[t]) for t in range(n)]
+    t0 = time.perf_counter()
+    for j in jobs[:8]:
+        _oracle_tile(j)
+    t_one = (time.perf_counter() - t0) / 8
+    cores = os.cpu_count() or 1
+    m = n if cores >= 16 else min(n, 16 * cores)
+    res, t_pool = _pool_map(jobs[:m], cores)
+    out_tiles = tl.copy()
+    for t in range(m):
+        out_tiles[t] = res[t]
+    t0 = time.perf_counter()
+    OTl.blend(out_tiles, ty, tx, TILE_CORE, TILE_HALO)
+    t_blend = time.perf_counter() - t0
+    vox = float(fld.size)
+    pool_s = t_gather + t_pool * n / m + t_blend
+    one_s = t_gather + t_one * n + t_blend
+    return {"value": round(vox / pool_s, 1), "unit": "voxels/s", "cores": cores, "kind": "oracle",
+            "sample": f"numpy float64 oracle on the field workload: gather and blend of the whole "
+                      f"48x2048x2048 field in the main process ({t_gather:.1f} s, {t_blend:.1f} s), TF build + "
+                      f"3D Tikhonov of {m} of the 256 tiles in a pool of {cores} processes ({t_pool:.1f} s), "
+                      f"scaled to 256 tiles: {pool_s:.1f} s per field",
+            "single_core": {"value": round(vox / one_s, 1), "unit": "voxels/s", "cores": 1,
+                            "s_per_tile": round(t_one, 3),
+                            "sample": "the same oracle on one core over 8 tiles, scaled to 256 tiles plus gather "
+                                      f"and blend: {one_s:.1f} s per field"}}
+
+
+# ------------------------------------------------------------------ small stacks
+SMALL_SHAPE = (16, 64, 64)
+SMALL_BATCH = 4096
+SMALL_WORKLOAD = ("small stacks 16x64x64 (20 spheres, phase-only, relative eta 1e-3): one wo_reconstruct call "
+                  "(single-call latency, TF prebuilt) and a batch of 4096 stacks sharing one TF bank "
+                  "(wo_reconstruct_shared_tf)")
+
+
+def small_stack_leg(args, rank, world, local_rank):
+    """Config of the 16x64x64 stack: the latency of one reconstruction call
+    (its 0.8 MB sit in L2) and the throughput of 4096 stacks sharing one TF
+    bank (compulsory 8 B per voxel: data in, volume out; the 0.27 MB bank
+    stays in L2)."""
+    import torch
+    import phantom as ph
+    from paper_2412_09775_gb300 import binding as B
+    from paper_2412_09775_gb300.shard import job_throughput, max_over_ranks
+    dev = torch.device("cuda", local_rank)
+    Z, Y, X = SMALL_SHAPE
+    o = ph.optics()
+    dn = ph.sphere_phantom(1 + rank, SMALL_SHAPE, o, n_spheres=20)
+    tf1, ws1 = B.alloc(1, Z, Y, X, ("phase",), dev)
+    B.wo_build_tf([o], 1, Z, Y, X, ("phase",), tf1, ws1)
+    f = torch.from_numpy(dn.astype(np.float32)).to(dev).view(1, 1, Z, Y, X)
+    d1 = torch.empty_like(f)
+    B.wo_forward(tf1, ("phase",), f, [1.0], d1, 1, Z, Y, X, ws1)
+    g = torch.Generator(device=dev)
+    g.manual_seed(11 + rank)
+    d1 += 1e-3 * torch.randn(d1.shape, generator=g, device=dev)
+    o1 = torch.empty_like(d1)
+    stream = torch.cuda.current_stream()
+
+    def one():
+        B.wo_reconstruct(tf1, ("phase",), d1, None, [1e-3], B.WO_ETA_RELATIVE, B.WO_MODE_3D, o1, 1, Z, Y, X, ws1)
+
+    def timed(fn, k):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(e0.elapsed_time(e1) / k, device=dev)
+
+    lat = timed(one, max(50, args.steps))
+    nb = SMALL_BATCH
+    data = d1.expand(nb, 1, Z, Y, X).contiguous()
+    data += 1e-3 * torch.randn(data.shape, generator=g, device=dev)  # every stack its own noise
+    outb = torch.empty_like(data)
+    wsb = torch.empty(B.wo_workspace_bytes(nb, Z, Y, X, ("phase",)), dtype=torch.uint8, device=dev)
+
+    def batch():
+        B.wo_reconstruct_shared_tf(tf1, ("phase",), data, None, [1e-3], B.WO_ETA_RELATIVE, B.WO_MODE_3D, outb, nb, Z,
+                                   Y, X, wsb)
+
+    ms = timed(batch, args.steps)
+    prof = profiled_pass(B, batch, args.steps)
+    vox = float(nb * Z * Y * X)
+    half = Z * Y * (X // 2 + 1) * 8
+    inside = Z * support_columns(o, ("phase",), Y, X) * 8
+    real = Z * Y * X * 4
+    algo = {"tile_pipeline": nb * 2 * real + half,
+            "rows_r2c": nb * (real + half), "y_fwd": 2 * nb * half, "z_fused": nb * (inside + half),
+            "y_inv": 2 * nb * half, "rows_c2r": nb * (half + real)}
+    kern = kernel_table(prof, algo, "launches")
+    peak, _ = peaks()
+    compulsory = 8.0 * vox
+    out = {"workload": SMALL_WORKLOAD, "single_call_ms": round(lat, 4),
+           "single_call_voxels_per_s": round(job_throughput(Z * Y * X, world, lat), 1),
+           "batch": nb, "value": round(job_throughput(vox, world, ms), 1), "unit": "voxels/s",
+           "ms_per_batch": round(ms, 4),
+           "compulsory_gbs": round(compulsory / (ms * 1e-3) / 1e9, 1),
+           "compulsory_frac": round(compulsory / (ms * 1e-3) / 1e9 / peak, 4),
+           "roofline": roofline_of(kern, prof), "kernels": kern,
+           "l2": "batch data 268 MB in, 268 MB out (> L2); the shared TF bank 0.27 MB stays in L2"}
+    del data, outb, wsb
+    torch.cuda.empty_cache()
+    return out if rank == 0 else None
 
 
 # ------------------------------------------------------------------ auto-tuning
 TUNE_TILES = 256
-TUNE_SHAPE = (48, 128, 128)
+TUNE_SHAPE = (48, 192, 192)  # the shift-variant field's tiles
+EST_SHAPE = (48, 128, 128)   # the learned estimator's tiles
 TUNE_ETA = 1e-3
 TUNE_WORKLOAD = {
-    "all": ("auto-tuning of (defocus, tilt_x, tilt_y, NA_ill), 256 tiles of 48x128x128 with their own optics, "
+    "all": ("auto-tuning of (defocus, tilt_x, tilt_y, NA_ill), 256 tiles of 48x192x192 with their own optics, "
             "smooth-edged source pupil: 50 Adam steps per tile from nominal (defocus 0, no tilt, NA_ill 0.825; 25 "
             "on the loss band-limited to 0.12 NA_det/lambda, 25 on the full loss with fresh moments); each step = "
             "per-plane build of the phase TF and its 4 derivatives + 2D thin-object loss and adjoint + Adam, one "
             "CUDA graph"),
-    "defocus": ("defocus auto-tuning, 256 tiles of 48x128x128, per-tile optics: 50 Adam steps per tile from "
+    "defocus": ("defocus auto-tuning, 256 tiles of 48x192x192, per-tile optics: 50 Adam steps per tile from "
                 "defocus 0 (25 on the loss band-limited to 0.12 NA_det/lambda, lr 0.08->0.02 um; 25 on the full "
                 "loss with fresh moments, lr 0.02->0 um); each step = per-plane TF pair build (phase TF + d/d "
                 "defocus) + 2D thin-object loss and adjoint + Adam, one CUDA graph")}
@@ -797,7 +1140,7 @@ def make_tune_data(o_list, dev, seed=5, smooth=False):
     return data
 
 
-def tune_cpu_baseline(o, start, d, schedule, params, max_steps=8):
+def tune_cpu_baseline(o, start, d, schedule, params, max_steps=4):
     """The oracle tuning one tile: the first `max_steps` of the same Adam
     schedule, each with the oracle's loss at theta +/- 1e-4 per parameter
     (central differences: the oracle has no adjoint); the time is scaled to
@@ -831,7 +1174,7 @@ def tune_cpu_baseline(o, start, d, schedule, params, max_steps=8):
             th = th - lr * (m / (1 - 0.9 ** k)) / (np.sqrt(v / (1 - 0.999 ** k)) + 1e-8)
     dt = (time.perf_counter() - t0) * total / max(done, 1)
     return {"value": 1.0 / dt, "unit": "tiles/s", "cores": 1, "kind": "oracle",
-            "sample": f"numpy float64 oracle tuning 1 of the 256 tiles (48x128x128): the first {done} of the "
+            "sample": f"numpy float64 oracle tuning 1 of the 256 tiles ({'x'.join(map(str, TUNE_SHAPE))}): the first {done} of the "
                       f"{total} Adam steps of the same schedule with central-difference gradients "
                       f"({2 * len(keys)} loss evaluations per step), timed and scaled to {total} steps "
                       f"({dt:.1f} s per tile), single thread"}
@@ -987,7 +1330,7 @@ def run_estimator(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     base = ph.optics()
-    shape = TUNE_SHAPE
+    shape = EST_SHAPE
     Z, Y, X = shape
 
     def clock(fn):
@@ -1106,26 +1449,54 @@ def run_estimator(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def _oracle_field_tile(job):
+    """Worker: one tile of the field workload made on the host - a sphere
+    phantom region (the field's sphere density, 140 spheres per 48x192x192
+    tile) imaged by the oracle's forward model with the tile's optics, plus
+    1e-3 Gaussian noise."""
+    import phantom as ph
+    from oracle import model as OM, optics as OO
+    o, seed = job
+    shape = (FIELD_Z, TILE_CORE + 2 * TILE_HALO, TILE_CORE + 2 * TILE_HALO)
+    dn = ph.sphere_phantom(seed, shape, o, n_spheres=140)
+    modes, _, _ = OM.widefield_system(OO.transfer_functions(o, shape, ("phase",)), ("phase",))
+    d = OM.forward(modes, dn[None], [1.0])[0] + ph.gaussian_noise(seed + 1, shape, 1e-3)
+    return d.astype(np.float32)
+
+
 def run_reference(args, rank, world):
+    """The float64 oracle timed on the host cores on the field workload: each
+    step reconstructs (TF build + 3D Tikhonov) one tile per host core in a pool
+    of spawned processes; the value is field voxels/s scaled from the tiles
+    done (256 tiles per field; gather and blend left out, a few % of the
+    oracle's time)."""
     if rank != 0:
         return
-    o, d = oracle_sample_inputs()
-    for _ in range(args.warmup):
-        oracle_step(o, d)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle_step(o, d)
-    dt = (time.perf_counter() - t0) / args.steps
-    vox = float(np.prod(CPU_SAMPLE))
-    value = vox / dt
-    sample = (f"numpy float64 oracle (no reference code exists: the paper ships none), TF build + "
-              f"reconstruction of a {CPU_SAMPLE[0]}x{CPU_SAMPLE[1]}x{CPU_SAMPLE[2]} sub-volume of the widefield "
-              f"workload per step, single thread")
+    import multiprocessing as mp
+    import phantom as ph
+    cores = os.cpu_count() or 1
+    n = TILE_GRID[0] * TILE_GRID[1]
+    o_list = ph.tile_optics(np.random.default_rng(3), n)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        tiles = pool.map(_oracle_field_tile, [(o_list[t], 1000 + t) for t in range(cores)], chunksize=1)
+        jobs = [(o_list[t], tiles[t]) for t in range(cores)]
+        for _ in range(args.warmup):
+            pool.map(_oracle_tile, jobs, chunksize=1)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            pool.map(_oracle_tile, jobs, chunksize=1)
+        dt = (time.perf_counter() - t0) / max(1, args.steps)
+    field_vox = float(FIELD_Z * (TILE_GRID[0] * TILE_CORE) * (TILE_GRID[1] * TILE_CORE))
+    value = field_vox * (cores / n) / dt
+    sample = (f"numpy float64 oracle (no reference code exists: the paper ships none) on the field workload: "
+              f"per step, TF build + 3D Tikhonov of {cores} of the 256 tiles of 48x192x192 (one per process, "
+              f"{cores} spawned processes), {dt:.2f} s per step, scaled to field voxels/s")
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "voxels/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": list(CPU_SAMPLE)},
-            "cpu_baseline": {"value": round(value, 1), "unit": "voxels/s", "cores": 1, "kind": "oracle",
+            "data": "synthetic", "config": {"workload": TILES_WORKLOAD, "tiles_per_step": cores},
+            "cpu_baseline": {"value": round(value, 1), "unit": "voxels/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 1), "unit": "voxels/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -1142,7 +1513,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-library-fft", action="store_true",
                     help="skip timing the torch.fft composition of the forward model and reconstruction")
-    ap.add_argument("--workload", choices=["widefield", "tiles", "autotune", "estimator"], default="widefield")
+    ap.add_argument("--workload", choices=["field", "tiles", "widefield", "autotune", "estimator"], default="field",
+                    help="field (default): the shift-variant field as the headline with the auto-tuning, widefield "
+                         "and small-stack legs; tiles: the field line alone")
+    ap.add_argument("--field-only", action="store_true", help="field workload without the other legs")
     ap.add_argument("--est-train", type=int, default=EST_TRAIN, help="estimator training tiles")
     ap.add_argument("--est-epochs", type=int, default=12, help="estimator training epochs")
     ap.add_argument("--est-test", type=int, default=EST_TEST, help="estimator test tiles")
@@ -1174,7 +1548,9 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     try:
-        if args.workload == "tiles":
+        if args.workload in ("field", "tiles"):
+            if args.workload == "tiles":
+                args.field_only = True
             run_tiles(args, rank, world, local_rank)
         elif args.workload == "autotune":
             run_autotune(args, rank, world, local_rank)

@@ -25,7 +25,8 @@
  * The caller allocates every device buffer (for example as torch tensors)
  * and keeps it alive until the work queued on `stream` has finished.  The
  * library never allocates or frees device memory and never synchronises the
- * device; all work is queued on `stream`.  Device pointers must be 16-byte
+ * device (except wo_sync_status and wo_autotune, which say so); all work is
+ * queued on `stream`.  Device pointers must be 16-byte
  * aligned.  Every entry point validates its arguments before launching
  * anything; on an error status nothing was launched and no output was
  * touched.  A failed CUDA launch returns WO_ERR_CUDA (the queue may then hold
@@ -52,10 +53,13 @@ typedef enum {
   WO_ERR_UNSUPPORTED_SIZE = 3, /* an FFT length outside the supported set */
   WO_ERR_UNDERSAMPLED = 4,     /* optics alias on this grid (see wo_build_tf) */
   WO_ERR_CUDA = 5,             /* a CUDA launch or runtime call failed */
-  WO_ERR_TIMEOUT = 6,          /* a bounded device-side wait expired (reserved: no kernel of
-                                  this version waits on another, so none returns it) */
+  WO_ERR_TIMEOUT = 6,          /* a bounded device-side wait expired (the tile pipeline of
+                                  WO_PASS_RECON; reported through wo_sync_status) */
   WO_ERR_OPTICS = 7,           /* physically invalid optics (e.g. NA_det >= n) */
-  WO_ERR_WORKSPACE = 8         /* workspace smaller than wo_workspace_bytes() */
+  WO_ERR_WORKSPACE = 8,        /* workspace smaller than wo_workspace_bytes() */
+  WO_ERR_BOUNDS = 9            /* a kernel of a WO_CHECK build found an index outside its
+                                  buffer and skipped the access (reported through
+                                  wo_sync_status) */
 } wo_status;
 
 /* Per-tile optical parameters theta (Fig. 2a(ii); Ext. Data Fig. 3a-b).
@@ -103,7 +107,7 @@ enum { WO_TF_SMOOTH_SOURCE = 32 };
  * enters the direct arm A = S P e^{i2pi eta z_j} and the normalisation
  * D = sum S P^2, so dH1/dtheta = c sum (A_theta* B) / D - H1 D_theta / D with
  * A_theta = (dS/dtheta) P e^{...}, D_theta = sum (dS/dtheta) P^2, through
- * Table 1 unchanged.  X must be 32, 48, 64, 128 or 256. */
+ * Table 1 unchanged.  X must be 32, 48, 64, 96, 128, 192 or 256. */
 enum { WO_TF_PHASE_GRAD = 64 };
 enum { WO_MODE_3D = 0, WO_MODE_2D = 1 };
 enum { WO_ETA_RELATIVE = 0, WO_ETA_ABSOLUTE = 1 };
@@ -229,6 +233,19 @@ wo_status wo_reconstruct(const void *d_tf, unsigned kinds, const float *d_data,
                          int eta_flag, int mode, float *d_f, int n_tiles, int Z,
                          int Y, int X, void *d_ws, size_t ws_bytes, wo_stream stream);
 
+/* Row a7 for a batch of independent stacks imaged with the same optics (the
+ * many small z-stacks of a pooled screen, Methods "Cell-scale optical pooled
+ * screen data"): wo_reconstruct with one transfer-function bank for the whole
+ * batch.  d_tf: a bank built for ONE tile (wo_tf_bytes(1, Z, Y, X, kinds)
+ * bytes), read by every stack; d_data [n_tiles][C][Z][Y][X], d_f as in
+ * wo_reconstruct; the relative regulariser uses that bank's statistics.  The
+ * workspace holds wo_workspace_bytes(n_tiles, ...) bytes.  Same errors as
+ * wo_reconstruct. */
+wo_status wo_reconstruct_shared_tf(const void *d_tf, unsigned kinds, const float *d_data,
+                                   const float *h_background, const float *h_eta, int eta_flag, int mode,
+                                   float *d_f, int n_tiles, int Z, int Y, int X, void *d_ws, size_t ws_bytes,
+                                   wo_stream stream);
+
 /* Allocation-free reconstruction.  The paper has no counterpart: this is a
  * service for callers that cannot allocate device memory where they need a
  * reconstruction - a plugin inside a host application that owns the whole
@@ -242,8 +259,10 @@ wo_status wo_reconstruct(const void *d_tf, unsigned kinds, const float *d_data,
  *   rejected with WO_ERR_WORKSPACE before anything is launched (for example
  *   16x64x64 with all three kinds needs 2 MB; 96x512x512 does not fit).
  * - The first call on a device looks up the array's device address with that
- *   device current and caches it; make that first call before any stream
- *   capture begins.
+ *   device current (and loads the array there); make that first call before
+ *   any stream capture begins.  Later calls outside capture look the address
+ *   up again (a reset or replaced context is followed); calls made while the
+ *   stream is captured use the address of the last call on that device.
  * - The function allocates nothing (no cudaMalloc, cudaFree or allocating
  *   library routine).
  * - All calls on a device share the one array and it keeps the previous
@@ -371,6 +390,34 @@ wo_status wo_tune_objective(const void *d_tf, unsigned kinds, const wo_optics *d
                             double *d_grad, int n_tiles, int Z, int Y, int X, void *d_ws,
                             size_t ws_bytes, wo_stream stream);
 
+/* wo_reconstruct_vjp: the hand-written adjoint of the phase reconstruction
+ * with respect to the tuned optics (Ext. Data Fig. 3: the paper
+ * back-propagates a loss of the reconstruction to each tile's parameters).
+ * Given the upstream gradient g = dL/df of a loss L of the reconstruction f,
+ * it returns dL/dtheta_p = <g, df/dtheta_p> per tile, the reconstruction
+ * taken with an absolute regulariser eta (>= 0) and the background removed as
+ * d_spec was made:
+ *   WO_MODE_3D (kinds WO_TF_PHASE_DZ, a 3D bank; theta = defocus_um): f the 3D
+ *     reconstruction of wo_reconstruct, F = conj(H) D / (|H|^2 + eta) per 3D
+ *     frequency; d_spec the 3D spectra (wo_spectrum, WO_MODE_3D); d_gout
+ *     [n_tiles][Z][Y][X].
+ *   WO_MODE_2D (kinds WO_TF_PHASE_DZ | WO_TF_PLANES, theta = defocus_um, or
+ *     WO_TF_PHASE_GRAD | WO_TF_PLANES, theta = (defocus_um, tilt_x, tilt_y,
+ *     na_ill)): f the thin-object reconstruction of wo_reconstruct's 2D mode,
+ *     F = sum_j conj(H_j) D_j / (sum_j |H_j|^2 + eta) per transverse
+ *     frequency (Parseval over z: the same f as WO_MODE_2D with a 3D bank of
+ *     the same optics and absolute eta); d_spec the per-plane spectra
+ *     (wo_spectrum, WO_MODE_2D); d_gout [n_tiles][Y][X].
+ * In both: dF_p = (conj(dH_p) D - 2 Re(conj(H) dH_p) F) / den with the sums
+ * over planes in 2D, and dL/dtheta_p = (1/N) Re sum_nu conj(G) dF_p (G the
+ * unnormalised spectrum of g, N its number of samples).  d_grad: n_tiles x
+ * n_params doubles (8-byte aligned).  The workspace holds the upstream
+ * spectra and the partial sums: wo_workspace_bytes() of the bank's kinds
+ * suffices.  The sums are reduced in a fixed order; no host synchronisation. */
+wo_status wo_reconstruct_vjp(const void *d_tf, unsigned kinds, const void *d_spec, const float *d_gout, float eta,
+                             int mode, double *d_grad, int n_tiles, int Z, int Y, int X, void *d_ws, size_t ws_bytes,
+                             wo_stream stream);
+
 /* wo_adam_optics: one Adam step (Kingma and Ba, 2015) on each tile's tuned
  * optics parameters in the device optics array - defocus_um (n_params = 1),
  * or defocus_um, tilt_x, tilt_y, na_ill (n_params = 4) - from d_grad
@@ -468,11 +515,55 @@ enum { WO_PASS_COLS = 0 };
  * shuffles; n = 32, 48, 64, 96, 128, 192, 256, 512; the default where it
  * exists). */
 enum { WO_PASS_ROWS = 1 };
+/* WO_PASS_RECON: the phase-only 3D reconstruction (wo_reconstruct,
+ * wo_reconstruct_shared_tf with kinds WO_TF_PHASE, optionally with
+ * WO_TF_SMOOTH_SOURCE, or a WO_TF_PHASE_DZ bank, WO_MODE_3D) of tiles whose
+ * planes fit one SM's shared memory, keyed by n = Y: WO_ENGINE_SMEM (the five
+ * passes, each a kernel over the whole batch) or WO_ENGINE_HYBRID (one
+ * persistent kernel: CTAs take per-plane x/y work, per-row z-solve work and
+ * per-plane inverse x/y work from one queue, so a tile's spectra stay in L2
+ * between them; the default where it exists: (Z, Y, X) = (48, 192, 192),
+ * (48, 128, 128), (16, 64, 64)).  Every wait of that kernel on another CTA's
+ * work is bounded (one second): when it runs out, the kernel records
+ * WO_ERR_TIMEOUT in the workspace's status block (wo_sync_status) and stops.
+ * Results agree with the passes to float32 rounding. */
+enum { WO_PASS_RECON = 2 };
 enum { WO_ENGINE_DEFAULT = 0, WO_ENGINE_SMEM = 1, WO_ENGINE_HYBRID = 2 };
 wo_status wo_schedule_set(int pass, int n, int engine);
 int wo_schedule_get(int pass, int n);
 wo_status wo_autotune(int n_tiles, int Z, int Y, int X, unsigned kinds, void *d_ws,
                       size_t ws_bytes, wo_stream stream);
+
+/* Device-side errors.  Errors found on the device - a bounded wait of the
+ * tile pipeline that ran out (WO_ERR_TIMEOUT), an index check of a WO_CHECK
+ * build (WO_ERR_BOUNDS) - cannot be returned by the call that queued the
+ * kernel.  They are recorded in the status block: the first 256 bytes of the
+ * workspace (int32 code, site, detail; the first error since the block was
+ * last cleared is kept).  Workspaces sized by wo_workspace_bytes and
+ * wo_fused_workspace_bytes begin with it.
+ * wo_clear_status: zero the block (stream-ordered); do it once on a new
+ *   workspace before its first use.
+ * wo_sync_status: wait for `stream`, read the block, clear it, and return the
+ *   recorded code (WO_OK if none); h_info (2 ints, or NULL) receives the site
+ *   (1: a z-solve item waited for its tile's plane items, 2: an inverse plane
+ *   item waited for the z-solve items, 3: a TMA copy into shared memory, 4+: a
+ *   WO_CHECK kernel family) and the detail (tile index, or the offending
+ *   index).  Unlike every other entry point it synchronises the stream.
+ *   WO_ERR_CUDA if the block holds no status code (never cleared).
+ * wo_pipeline_probe: a diagnostic of the tile pipeline's bounded waits.  It
+ *   runs the pipeline of the phase-only 3D reconstruction (eta 1e-3
+ *   absolute, channel-mean background) on a WO_TF_PHASE bank exactly as
+ *   wo_reconstruct does, except that every wait gives up after budget_ns
+ *   (1e3 .. 1e10) and, when 0 <= withhold < n_tiles, the plane items of tile
+ *   `withhold` are never posted: the items waiting for them then run out of
+ *   time, record WO_ERR_TIMEOUT (site 1, detail withhold) and the kernel
+ *   returns instead of hanging.  withhold = -1 runs the pipeline whole.
+ *   Shapes: those of WO_PASS_RECON's pipeline; the workspace of
+ *   wo_workspace_bytes(n_tiles, Z, Y, X, WO_TF_PHASE). */
+wo_status wo_clear_status(void *d_ws, wo_stream stream);
+wo_status wo_sync_status(void *d_ws, int *h_info, wo_stream stream);
+wo_status wo_pipeline_probe(const void *d_tf, const float *d_data, float *d_f, int n_tiles, int Z, int Y, int X,
+                            int withhold, long long budget_ns, void *d_ws, size_t ws_bytes, wo_stream stream);
 
 /* Human-readable name of a status. */
 const char *wo_status_string(wo_status status);

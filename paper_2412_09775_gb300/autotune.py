@@ -226,3 +226,92 @@ class TuneLoss(torch.autograd.Function):
 
 def tune_loss(theta: torch.Tensor, problem: TuningProblem, nu_max: float = 0.0) -> torch.Tensor:
     return TuneLoss.apply(theta, problem, nu_max)
+
+
+class Reconstruction:
+    """The phase reconstruction of a batch of stacks as a differentiable
+    function of each tile's tuned optics (Ext. Data Fig. 3: a loss of the
+    reconstruction is back-propagated to the parameters).
+
+    ``mode``: B.WO_MODE_3D (the 3D reconstruction; ``params="defocus"``) or
+    B.WO_MODE_2D (the thin-object reconstruction from the z-stack;
+    ``params="defocus"`` or ``"all"`` = defocus, tilt_x, tilt_y, NA_ill under
+    the smooth source pupil).  The regulariser ``eta`` is absolute; the
+    background is each stack's mean.  ``forward(theta)`` builds the phase
+    transfer function from the device optics and reconstructs (wo_reconstruct);
+    ``vjp(grad_out)`` builds the derivative bank at the same optics and returns
+    dL/dtheta for the upstream gradient dL/df (wo_reconstruct_vjp).
+    ``ReconstructFn`` wraps both for autograd."""
+
+    def __init__(self, data: torch.Tensor, optics_list, eta: float, mode: int = B.WO_MODE_3D,
+                 params: str = "defocus"):
+        if data.dim() != 4 or data.dtype != torch.float32 or not data.is_cuda:
+            raise ValueError("data: float32 CUDA tensor [n_tiles, Z, Y, X]")
+        if params not in ("defocus", "all") or (mode == B.WO_MODE_3D and params != "defocus"):
+            raise ValueError("params: 'defocus' (3D or 2D) or 'all' (2D)")
+        self.n, self.Z, self.Y, self.X = (int(s) for s in data.shape)
+        if len(optics_list) != self.n:
+            raise ValueError("one optics entry per tile")
+        dev = data.device
+        self.data = data.contiguous()
+        self.eta, self.mode = float(eta), int(mode)
+        self.n_params = 1 if params == "defocus" else 4
+        smooth = B.WO_TF_SMOOTH_SOURCE if self.n_params == 4 else 0
+        self.kinds_fwd = (B.WO_TF_PHASE_DZ if mode == B.WO_MODE_3D else B.WO_TF_PHASE) | smooth
+        if mode == B.WO_MODE_3D:
+            self.kinds_vjp = B.WO_TF_PHASE_DZ
+        else:
+            self.kinds_vjp = (B.WO_TF_PHASE_GRAD if self.n_params == 4 else B.WO_TF_PHASE_DZ) | B.WO_TF_PLANES
+        self.optics = B.optics_tensor(optics_list, dev)
+        n, Z, Y, X = self.n, self.Z, self.Y, self.X
+        self.tf_fwd, ws1 = B.alloc(n, Z, Y, X, self.kinds_fwd, dev)
+        self.tf_vjp, ws2 = B.alloc(n, Z, Y, X, self.kinds_vjp, dev)
+        self.ws = ws1 if ws1.numel() >= ws2.numel() else ws2
+        self.spec = torch.empty((n, Z, Y, X // 2 + 1), dtype=torch.complex64, device=dev)
+        B.wo_spectrum(self.data, None, self.mode, self.spec, n, Z, Y, X)
+        shape = (n, Z, Y, X) if mode == B.WO_MODE_3D else (n, Y, X)
+        self.out = torch.empty(shape, dtype=torch.float32, device=dev)
+        self.grad = torch.zeros((n, self.n_params), dtype=torch.float64, device=dev)
+
+    def set_params(self, theta: torch.Tensor):
+        for i, k in enumerate(PARAMS[: self.n_params]):
+            self.optics[:, _COLUMN[k]].copy_(theta[:, i])
+
+    def forward(self, theta: torch.Tensor) -> torch.Tensor:
+        n, Z, Y, X = self.n, self.Z, self.Y, self.X
+        self.set_params(theta.detach().reshape(n, self.n_params).to(torch.float64))
+        B.wo_build_tf_device(self.optics, n, Z, Y, X, self.kinds_fwd, self.tf_fwd, self.ws)
+        B.wo_reconstruct(self.tf_fwd, self.kinds_fwd, self.data, None, [self.eta], B.WO_ETA_ABSOLUTE, self.mode,
+                         self.out, n, Z, Y, X, self.ws)
+        return self.out.clone()
+
+    def vjp(self, grad_out: torch.Tensor) -> torch.Tensor:
+        n, Z, Y, X = self.n, self.Z, self.Y, self.X
+        g = grad_out.detach().to(torch.float32).contiguous()
+        B.wo_build_tf_device(self.optics, n, Z, Y, X, self.kinds_vjp, self.tf_vjp, self.ws)
+        B.wo_reconstruct_vjp(self.tf_vjp, self.kinds_vjp, self.spec, g, self.eta, self.mode, self.grad, n, Z, Y, X,
+                             self.ws)
+        return self.grad.clone()
+
+
+class ReconstructFn(torch.autograd.Function):
+    """f = R(theta) for a ``Reconstruction``: theta [n, n_params] (float64, in
+    the order of PARAMS) -> the reconstructed phase [n, Z, Y, X] (3D) or
+    [n, Y, X] (2D); backward returns the library's vector-Jacobian product."""
+
+    @staticmethod
+    def forward(ctx, theta: torch.Tensor, problem: Reconstruction):
+        ctx.problem = problem
+        ctx.save_for_backward(theta.detach().clone())
+        return problem.forward(theta)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (theta,) = ctx.saved_tensors
+        p = ctx.problem
+        p.set_params(theta.reshape(p.n, p.n_params).to(torch.float64))  # the optics this output was made at
+        return p.vjp(grad_out).to(theta.dtype), None
+
+
+def reconstruct(theta: torch.Tensor, problem: Reconstruction) -> torch.Tensor:
+    return ReconstructFn.apply(theta, problem)

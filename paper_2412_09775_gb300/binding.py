@@ -23,7 +23,7 @@ WO_TF_PHASE_GRAD = 64
 WO_MODE_3D, WO_MODE_2D = 0, 1
 WO_ETA_RELATIVE, WO_ETA_ABSOLUTE = 0, 1
 WO_LOSS_DATA, WO_LOSS_MIDBAND = 0, 1
-WO_PASS_COLS, WO_PASS_ROWS = 0, 1
+WO_PASS_COLS, WO_PASS_ROWS, WO_PASS_RECON = 0, 1, 2
 WO_ENGINE_DEFAULT, WO_ENGINE_SMEM, WO_ENGINE_HYBRID = 0, 1, 2
 WO_MAX_ZERNIKE = 36
 WO_PAD_ZERO, WO_PAD_MIRROR, WO_PAD_EDGE = 0, 1, 2
@@ -32,7 +32,7 @@ KIND_BITS = {"phase": WO_TF_PHASE, "absorption": WO_TF_ABSORPTION, "fluor": WO_T
              "phase_grad": WO_TF_PHASE_GRAD}
 STATUS = {0: "WO_OK", 1: "WO_ERR_ARG", 2: "WO_ERR_SHAPE", 3: "WO_ERR_UNSUPPORTED_SIZE",
           4: "WO_ERR_UNDERSAMPLED", 5: "WO_ERR_CUDA", 6: "WO_ERR_TIMEOUT", 7: "WO_ERR_OPTICS",
-          8: "WO_ERR_WORKSPACE"}
+          8: "WO_ERR_WORKSPACE", 9: "WO_ERR_BOUNDS"}
 
 STATUS_CODES = {v: k for k, v in STATUS.items()}
 
@@ -69,8 +69,13 @@ def _load():
         "wo_forward_adjoint": (i, [vp, u, vp, fp, vp, i, i, i, i, vp, sz, vp]),
         "wo_reconstruct": (i, [vp, u, vp, fp, fp, i, i, vp, i, i, i, i, vp, sz, vp]),
         "wo_reconstruct_static": (i, [vp, u, vp, fp, fp, i, i, vp, i, i, i, i, vp]),
+        "wo_reconstruct_shared_tf": (i, [vp, u, vp, fp, fp, i, i, vp, i, i, i, i, vp, sz, vp]),
+        "wo_clear_status": (i, [vp, vp]),
+        "wo_sync_status": (i, [vp, ctypes.POINTER(ctypes.c_int), vp]),
+        "wo_pipeline_probe": (i, [vp, vp, vp, i, i, i, i, i, ctypes.c_longlong, vp, sz, vp]),
         "wo_spectrum": (i, [vp, fp, i, vp, i, i, i, i, vp]),
         "wo_tune_objective": (i, [vp, u, vp, vp, i, f, f, vp, vp, i, i, i, i, vp, sz, vp]),
+        "wo_reconstruct_vjp": (i, [vp, u, vp, vp, f, i, vp, i, i, i, i, vp, sz, vp]),
         "wo_adam_optics": (i, [vp, vp, i, vp, i, ctypes.POINTER(ctypes.c_double), ctypes.c_double,
                                ctypes.c_double, ctypes.c_double, vp]),
         "wo_fused_workspace_bytes": (sz, [i, i, i, i, i]),
@@ -107,8 +112,9 @@ _lib = _load()
 EXPORTED = ("wo_size_supported", "wo_tf_bytes", "wo_workspace_bytes", "wo_build_tf", "wo_build_tf_device",
             "wo_aberrated_workspace_bytes", "wo_build_tf_aberrated",
             "wo_forward",
-            "wo_forward_adjoint", "wo_reconstruct", "wo_reconstruct_static", "wo_spectrum",
-            "wo_tune_objective", "wo_adam_optics", "wo_fused_workspace_bytes", "wo_reconstruct_fused",
+            "wo_forward_adjoint", "wo_reconstruct", "wo_reconstruct_static", "wo_reconstruct_shared_tf",
+            "wo_clear_status", "wo_sync_status", "wo_pipeline_probe", "wo_spectrum",
+            "wo_tune_objective", "wo_reconstruct_vjp", "wo_adam_optics", "wo_fused_workspace_bytes", "wo_reconstruct_fused",
             "wo_est_param_count", "wo_est_workspace_bytes", "wo_est_sync_bf16", "wo_est_forward", "wo_est_backward",
             "wo_est_train_step", "wo_est_features", "wo_thin_phantom",
             "wo_schedule_set", "wo_schedule_get", "wo_autotune", "wo_tile_gather", "wo_tile_blend",
@@ -244,6 +250,16 @@ def wo_reconstruct(tf, kinds, data, background, eta, eta_flag, mode, f, n_tiles,
                                _stream(stream)), "wo_reconstruct")
 
 
+def wo_reconstruct_shared_tf(tf, kinds, data, background, eta, eta_flag, mode, f, n_tiles, Z, Y, X, ws,
+                             stream=None):
+    """wo_reconstruct of n_tiles stacks with one TF bank (built for one tile) shared by all of them."""
+    bg = _floats(background)
+    et = _floats(eta if isinstance(eta, (list, tuple)) else [eta])
+    _check(_lib.wo_reconstruct_shared_tf(_ptr(tf), kinds_mask(kinds), _ptr(data), bg[0] if bg else None, et[0],
+                                         int(eta_flag), int(mode), _ptr(f), n_tiles, Z, Y, X, _ptr(ws), _nbytes(ws),
+                                         _stream(stream)), "wo_reconstruct_shared_tf")
+
+
 WO_STATIC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 
@@ -254,6 +270,25 @@ def wo_reconstruct_static(tf, kinds, data, background, eta, eta_flag, mode, f, n
     _check(_lib.wo_reconstruct_static(_ptr(tf), kinds_mask(kinds), _ptr(data), bg[0] if bg else None, et[0],
                                       int(eta_flag), int(mode), _ptr(f), n_tiles, Z, Y, X, _stream(stream)),
            "wo_reconstruct_static")
+
+
+def wo_clear_status(ws, stream=None):
+    """Zero the status block at the start of a workspace (once, before its first use)."""
+    _check(_lib.wo_clear_status(_ptr(ws), _stream(stream)), "wo_clear_status")
+
+
+def wo_sync_status(ws, stream=None):
+    """Wait for the stream, read and clear the workspace's status block:
+    (status code, site, detail); code 0 when no device-side error was recorded."""
+    info = (ctypes.c_int * 2)()
+    code = int(_lib.wo_sync_status(_ptr(ws), info, _stream(stream)))
+    return code, int(info[0]), int(info[1])
+
+
+def wo_pipeline_probe(tf, data, f, n_tiles, Z, Y, X, withhold, budget_ns, ws, stream=None):
+    """The tile pipeline with one tile's plane items withheld and a wait budget (diagnostic)."""
+    _check(_lib.wo_pipeline_probe(_ptr(tf), _ptr(data), _ptr(f), n_tiles, Z, Y, X, int(withhold), int(budget_ns),
+                                  _ptr(ws), _nbytes(ws), _stream(stream)), "wo_pipeline_probe")
 
 
 def wo_spectrum(data, background, mode, spec, n_tiles, Z, Y, X, stream=None):
@@ -269,6 +304,13 @@ def wo_tune_objective(tf, kinds, d_optics, spec, loss, eta, nu_max, value, grad,
     _check(_lib.wo_tune_objective(_ptr(tf), kinds_mask(kinds), _ptr(d_optics), _ptr(spec), int(loss), float(eta),
                                   float(nu_max), _ptr(value), _ptr(grad), n_tiles, Z, Y, X, _ptr(ws), _nbytes(ws),
                                   _stream(stream)), "wo_tune_objective")
+
+
+def wo_reconstruct_vjp(tf, kinds, spec, gout, eta, mode, grad, n_tiles, Z, Y, X, ws, stream=None):
+    """dL/dtheta [n, n_params] (float64 tensor `grad`) of the phase reconstruction for an upstream gradient gout."""
+    _check(_lib.wo_reconstruct_vjp(_ptr(tf), kinds_mask(kinds), _ptr(spec), _ptr(gout), float(eta), int(mode),
+                                   _ptr(grad), n_tiles, Z, Y, X, _ptr(ws), _nbytes(ws), _stream(stream)),
+           "wo_reconstruct_vjp")
 
 
 def wo_adam_optics(d_optics, grad, n_params, state, n_tiles, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
@@ -408,5 +450,6 @@ def alloc(n_tiles, Z, Y, X, kinds, device="cuda"):
     wsb = wo_workspace_bytes(n_tiles, Z, Y, X, kinds)
     if tfb == 0 or wsb == 0:
         raise ValueError("invalid shape or kinds")
-    return (torch.empty(tfb, dtype=torch.uint8, device=device),
-            torch.empty(wsb, dtype=torch.uint8, device=device))
+    ws = torch.empty(wsb, dtype=torch.uint8, device=device)
+    ws[:256].zero_()  # the status block starts cleared
+    return torch.empty(tfb, dtype=torch.uint8, device=device), ws

@@ -111,16 +111,24 @@ static Sys system_of(unsigned kinds) {
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
+  size_t status, pipe, head;
   size_t optics, zern, counts, rec, rec2, norm_part, norms, arms, build_end;
   size_t specA, specB, op_end;
   size_t total;
   size_t tf_spectra, tf_stats, tf_total;
 };
 
+// Every workspace starts with the device status block (kStatusBytes) and the
+// tile pipeline's counters; the entry points' regions follow.
+static size_t ws_head(int n) { return kStatusBytes + align256(pipe_counter_bytes(n)); }
+
 static Layout layout_of(int n, int Z, int Y, int X, const Sys& s) {
   Layout L{};
   const size_t Xh = (size_t)X / 2 + 1;
-  size_t off = 0;
+  L.status = 0;
+  L.pipe = kStatusBytes;
+  L.head = ws_head(n);
+  size_t off = L.head;
   L.optics = off; off += align256((size_t)n * sizeof(wo_optics));
   L.zern = off; if (s.aberr) off += align256((size_t)n * WO_MAX_ZERNIKE * sizeof(double));
   L.counts = off; off += align256((size_t)n * 4 * sizeof(int));
@@ -133,11 +141,12 @@ static Layout layout_of(int n, int Z, int Y, int X, const Sys& s) {
   L.build_end = off;
   const size_t vols = (size_t)(s.C > s.P ? s.C : s.P);
   const size_t spec = align256((size_t)n * vols * Z * Y * Xh * sizeof(float2));
-  L.specA = 0;
-  L.specB = spec;
-  L.op_end = 2 * spec;
+  L.specA = L.head;
+  L.specB = L.head + spec;
+  L.op_end = L.head + 2 * spec;
   L.total = L.build_end > L.op_end ? L.build_end : L.op_end;
-  if (s.want_dz && tune_partials_bytes(n, Y, X, 4) > L.total) L.total = tune_partials_bytes(n, Y, X, 4);
+  const size_t tune_end = kStatusBytes + tune_partials_bytes(n, Y, X, 4);
+  if (s.want_dz && tune_end > L.total) L.total = tune_end;
   L.tf_spectra = align256((size_t)n * s.n_kinds * Z * Y * Xh * sizeof(float2));
   L.tf_stats = L.tf_spectra;
   L.tf_total = L.tf_spectra + (size_t)n * 8 * sizeof(float);
@@ -171,7 +180,7 @@ static wo_status check_shape(int n_tiles, int Z, int Y, int X, unsigned kinds) {
   // four arm rows of X per PSF-row block must fit shared memory
   if (base == WO_TF_PHASE_DZ && X > 768) return WO_ERR_UNSUPPORTED_SIZE;
   // the seven arms of the gradient bank need the register-resident row pass
-  if (base == WO_TF_PHASE_GRAD && !(X == 32 || X == 48 || X == 64 || X == 128 || X == 256))
+  if (base == WO_TF_PHASE_GRAD && !(X == 32 || X == 48 || X == 64 || X == 96 || X == 128 || X == 192 || X == 256))
     return WO_ERR_UNSUPPORTED_SIZE;
   return WO_OK;
 }
@@ -239,6 +248,7 @@ const char* wo_status_string(wo_status st) {
     case WO_ERR_TIMEOUT: return "device-side wait timed out";
     case WO_ERR_OPTICS: return "physically invalid optics";
     case WO_ERR_WORKSPACE: return "workspace too small";
+    case WO_ERR_BOUNDS: return "a device-side index check failed (WO_CHECK build)";
   }
   return "unknown status";
 }
@@ -380,9 +390,43 @@ wo_status wo_build_tf_aberrated(const wo_optics* h_optics, const double* h_zerni
 }
 
 // forward (op 0), adjoint (op 1), reconstruct (op 2)
+// Kinds whose reconstruction the tile pipeline covers: the phase TF alone
+// (also from a defocus-derivative bank, whose slot 0 it is).
+static bool pipe_system(const Sys& s) { return s.lf_props == 1 && s.want_phase && !s.has_fl && !s.planes; }
+
+// Arguments of the tile pipeline for a reconstruction with this layout.
+static PipeLaunch pipe_launch(const Layout& L, const Sys& s, const void* d_tf, const float* d_in, float* d_out,
+                              int n_tiles, int Z, int Y, int X, char* ws, int tf_shared, float eta, int eta_absolute,
+                              const float* h_bg) {
+  const int Xh = X / 2 + 1;
+  PipeLaunch p{};
+  p.in = d_in;
+  p.out = d_out;
+  p.spec = (float2*)(ws + L.specA);
+  p.tf = (const float2*)d_tf;  // the phase TF is slot 0 of every bank that has one
+  p.tf_stride = (long long)s.n_kinds * Z * Y * Xh;
+  p.stats = (const float*)((const char*)d_tf + (tf_shared ? layout_of(1, Z, Y, X, s).tf_stats : L.tf_stats));
+  p.counters = (int*)(ws + L.pipe);
+  p.status = (int*)(ws + L.status);
+  p.n_tiles = n_tiles;
+  p.Z = Z;
+  p.Y = Y;
+  p.X = X;
+  p.tf_shared = tf_shared;
+  p.eta_absolute = eta_absolute;
+  p.zero_dc = h_bg ? 0 : 1;
+  p.withhold = -1;
+  p.eta = eta;
+  p.bg_plane = h_bg ? (float)((double)Y * X * h_bg[0]) : 0.f;
+  p.scale = (float)(2.0 / ((double)X * (double)Y * (double)Z));
+  p.budget_ns = kPipeBudgetNs;
+  return p;
+}
+
+// tf_shared: d_tf holds one tile's bank, used for every tile of the batch.
 static wo_status run_op(int op, const void* d_tf, unsigned kinds, const float* d_in, const float* h_bg,
                         const float* h_eta, int eta_flag, int mode, float* d_out, int n_tiles, int Z,
-                        int Y, int X, void* d_ws, size_t ws_bytes, wo_stream stream) {
+                        int Y, int X, void* d_ws, size_t ws_bytes, wo_stream stream, int tf_shared = 0) {
   wo_status st = check_shape(n_tiles, Z, Y, X, kinds);
   if (st != WO_OK) return st;
   if (kinds & WO_TF_PLANES) return WO_ERR_ARG;  // the operators need the 3D TFs
@@ -439,7 +483,9 @@ static wo_status run_op(int op, const void* d_tf, unsigned kinds, const float* d
   zo.has_fl = s.has_fl;
   zo.lf_chan = s.lf_props ? 0 : -1;
   zo.fl_chan = s.has_fl ? (s.lf_props ? 1 : 0) : -1;
-  zo.stats = (const float*)((const char*)d_tf + L.tf_stats);
+  zo.tf_shared = tf_shared;
+  // the statistics block follows the spectra of the tiles the bank was built for
+  zo.stats = (const float*)((const char*)d_tf + (tf_shared ? layout_of(1, Z, Y, X, s).tf_stats : L.tf_stats));
   if (op == 2) {
     int m = 0;
     if (s.lf_props) zo.eta_lf = h_eta[m++];
@@ -448,6 +494,14 @@ static wo_status run_op(int op, const void* d_tf, unsigned kinds, const float* d
     zo.zero_dc = h_bg ? 0 : 1;
   }
 
+  // The phase-only 3D reconstruction of tile-sized planes runs as one
+  // persistent pipeline (wo_pipe.cu) unless the schedule table says otherwise.
+  if (op == 2 && mode == WO_MODE_3D && pipe_system(s) && pipe_supported(Z, Y, X) &&
+      recon_engine(Z, Y, X) == WO_ENGINE_HYBRID) {
+    PipeLaunch p = pipe_launch(L, s, d_tf, d_in, d_out, n_tiles, Z, Y, X, ws, tf_shared, zo.eta_lf,
+                               zo.eta_absolute, h_bg);
+    return cuda_status(tile_pipeline(p, cs));
+  }
   const long long in_rows = (long long)n_tiles * n_in * Z * Y;
   WO_TRY(rows_r2c(H, d_in, specA, in_rows, bg_in, cs));
   WO_TRY(cols_c2c(Y, false, specA, Xh, (long long)Y * Xh, Xh, (long long)n_tiles * n_in * Z, cs, "y_fwd"));
@@ -487,6 +541,50 @@ wo_status wo_reconstruct(const void* d_tf, unsigned kinds, const float* d_data, 
                          int X, void* d_ws, size_t ws_bytes, wo_stream stream) {
   return run_op(2, d_tf, kinds, d_data, h_background, h_eta, eta_flag, mode, d_f, n_tiles, Z, Y, X, d_ws,
                 ws_bytes, stream);
+}
+
+wo_status wo_reconstruct_shared_tf(const void* d_tf, unsigned kinds, const float* d_data,
+                                   const float* h_background, const float* h_eta, int eta_flag, int mode, float* d_f,
+                                   int n_tiles, int Z, int Y, int X, void* d_ws, size_t ws_bytes, wo_stream stream) {
+  return run_op(2, d_tf, kinds, d_data, h_background, h_eta, eta_flag, mode, d_f, n_tiles, Z, Y, X, d_ws, ws_bytes,
+                stream, 1);
+}
+
+wo_status wo_pipeline_probe(const void* d_tf, const float* d_data, float* d_f, int n_tiles, int Z, int Y, int X,
+                            int withhold, long long budget_ns, void* d_ws, size_t ws_bytes, wo_stream stream) {
+  wo_status st = check_shape(n_tiles, Z, Y, X, WO_TF_PHASE);
+  if (st != WO_OK) return st;
+  if (!pipe_supported(Z, Y, X)) return WO_ERR_UNSUPPORTED_SIZE;
+  if (!aligned16(d_tf) || !aligned16(d_data) || !aligned16(d_f) || !aligned16(d_ws)) return WO_ERR_ARG;
+  if (withhold < -1 || withhold >= n_tiles || budget_ns < 1000 || budget_ns > 10LL * kPipeBudgetNs) return WO_ERR_ARG;
+  const Sys s = system_of(WO_TF_PHASE);
+  const Layout L = layout_of(n_tiles, Z, Y, X, s);
+  if (ws_bytes < L.total) return WO_ERR_WORKSPACE;
+  PipeLaunch p = pipe_launch(L, s, d_tf, d_data, d_f, n_tiles, Z, Y, X, (char*)d_ws, 0, 1e-3f, 1, nullptr);
+  p.withhold = withhold;
+  p.budget_ns = budget_ns;
+  return cuda_status(tile_pipeline(p, (cudaStream_t)stream));
+}
+
+wo_status wo_sync_status(void* d_ws, int* h_info, wo_stream stream) {
+  if (!aligned16(d_ws)) return WO_ERR_ARG;
+  cudaStream_t cs = (cudaStream_t)stream;
+  int blk[4] = {0, 0, 0, 0};
+  // pageable destination: the copy has landed when the call returns
+  WO_TRY(cudaMemcpyAsync(blk, d_ws, sizeof(blk), cudaMemcpyDeviceToHost, cs));
+  WO_TRY(cudaMemsetAsync(d_ws, 0, kStatusBytes, cs));
+  WO_TRY(cudaStreamSynchronize(cs));
+  if (h_info) {
+    h_info[0] = blk[1];
+    h_info[1] = blk[2];
+  }
+  if (blk[0] < 0 || blk[0] > (int)WO_ERR_BOUNDS) return WO_ERR_CUDA;  // not a status: the block was never cleared
+  return (wo_status)blk[0];
+}
+
+wo_status wo_clear_status(void* d_ws, wo_stream stream) {
+  if (!aligned16(d_ws)) return WO_ERR_ARG;
+  return cuda_status(cudaMemsetAsync(d_ws, 0, kStatusBytes, (cudaStream_t)stream));
 }
 
 wo_status wo_spectrum(const float* d_data, const float* h_background, int mode, void* d_spec, int n_tiles, int Z,
@@ -534,10 +632,42 @@ wo_status wo_tune_objective(const void* d_tf, unsigned kinds, const wo_optics* d
   if ((d_value && (((uintptr_t)d_value) & 7u)) || (d_grad && (((uintptr_t)d_grad) & 7u))) return WO_ERR_ARG;
   if (!(eta >= 0.f) || !isfinite(eta) || !(nu_max == nu_max)) return WO_ERR_ARG;
   const int np = base == WO_TF_PHASE_GRAD ? 4 : 1;
-  if (ws_bytes < tune_partials_bytes(n_tiles, Y, X, np)) return WO_ERR_WORKSPACE;
+  if (ws_bytes < kStatusBytes + tune_partials_bytes(n_tiles, Y, X, np)) return WO_ERR_WORKSPACE;
   return cuda_status(tune_reduce((const float2*)d_tf, (const float2*)d_spec, d_optics, n_tiles, Z, Y, X, eta,
                                  isfinite(nu_max) ? nu_max : 0.f, (kinds & WO_TF_PLANES) ? 1 : Z, loss, np,
-                                 (double*)d_ws, d_value, d_grad, (cudaStream_t)stream));
+                                 (double*)((char*)d_ws + kStatusBytes), d_value, d_grad, (cudaStream_t)stream));
+}
+
+wo_status wo_reconstruct_vjp(const void* d_tf, unsigned kinds, const void* d_spec, const float* d_gout, float eta,
+                             int mode, double* d_grad, int n_tiles, int Z, int Y, int X, void* d_ws, size_t ws_bytes,
+                             wo_stream stream) {
+  const unsigned base = kinds & ~(unsigned)(WO_TF_PLANES | WO_TF_SMOOTH_SOURCE);
+  if (base != WO_TF_PHASE_DZ && base != WO_TF_PHASE_GRAD) return WO_ERR_ARG;
+  if (mode != WO_MODE_3D && mode != WO_MODE_2D) return WO_ERR_ARG;
+  wo_status st = check_shape(n_tiles, Z, Y, X, kinds);
+  if (st != WO_OK) return st;
+  const bool planes = (kinds & WO_TF_PLANES) != 0;
+  if ((mode == WO_MODE_3D) == planes) return WO_ERR_ARG;  // 3D needs a 3D bank, 2D a per-plane bank
+  if (!aligned16(d_tf) || !aligned16(d_spec) || !aligned16(d_gout) || !aligned16(d_ws)) return WO_ERR_ARG;
+  if (!d_grad || (((uintptr_t)d_grad) & 7u)) return WO_ERR_ARG;
+  if (!(eta >= 0.f) || !isfinite(eta)) return WO_ERR_ARG;
+  const int np = base == WO_TF_PHASE_GRAD ? 4 : 1;
+  const int Xh = X / 2 + 1, H = X / 2;
+  const long long plane = (long long)Y * Xh;
+  const int gz = mode == WO_MODE_3D ? Z : 1;  // planes of the upstream gradient
+  const size_t gbytes = align256((size_t)n_tiles * gz * plane * sizeof(float2));
+  if (ws_bytes < kStatusBytes + gbytes + tune_partials_bytes(n_tiles, Y, X, np)) return WO_ERR_WORKSPACE;
+  cudaStream_t cs = (cudaStream_t)stream;
+  float2* G = (float2*)((char*)d_ws + kStatusBytes);
+  double* partials = (double*)((char*)d_ws + kStatusBytes + gbytes);
+  RowBg none{};
+  none.rows_per_block = (long long)gz * Y;
+  none.nchan = 1;
+  WO_TRY(rows_r2c(H, d_gout, G, (long long)n_tiles * gz * Y, none, cs));
+  WO_TRY(cols_c2c(Y, false, G, Xh, plane, Xh, (long long)n_tiles * gz, cs, "y_fwd"));
+  if (mode == WO_MODE_3D) WO_TRY(cols_c2c(Z, false, G, plane, (long long)Z * plane, (int)plane, n_tiles, cs, "z_fwd"));
+  return cuda_status(vjp_reduce((const float2*)d_tf, (const float2*)d_spec, G, n_tiles, Z, Y, X, eta,
+                                mode == WO_MODE_3D ? 1 : 0, np, partials, d_grad, cs));
 }
 
 wo_status wo_adam_optics(wo_optics* d_optics, const double* d_grad, int n_params, double* d_state, int n_tiles,
@@ -578,9 +708,9 @@ wo_status wo_reconstruct_fused(const void* d_tf, int n_channels, const float* d_
   const size_t specA = align256((size_t)n_tiles * C * half);
   const size_t specB = align256((size_t)n_tiles * half);
   const size_t statsb = align256((size_t)n_tiles * 2 * sizeof(float));
-  if (ws_bytes < specA + specB + statsb) return WO_ERR_WORKSPACE;
+  if (ws_bytes < kStatusBytes + specA + specB + statsb) return WO_ERR_WORKSPACE;
   cudaStream_t cs = (cudaStream_t)stream;
-  char* ws = (char*)d_ws;
+  char* ws = (char*)d_ws + kStatusBytes;
   float2* A = (float2*)ws;
   float2* Bv = (float2*)(ws + specA);
   float* stats = (float*)(ws + specA + specB);
@@ -622,7 +752,7 @@ size_t wo_fused_workspace_bytes(int n_channels, int n_tiles, int Z, int Y, int X
     return 0;
   if (check_shape(n_tiles * n_channels, Z, Y, X, WO_TF_PHASE) != WO_OK) return 0;
   const size_t half = (size_t)Z * Y * (X / 2 + 1) * sizeof(float2);
-  return align256((size_t)n_tiles * n_channels * half) + align256((size_t)n_tiles * half) +
+  return kStatusBytes + align256((size_t)n_tiles * n_channels * half) + align256((size_t)n_tiles * half) +
          align256((size_t)n_tiles * 2 * sizeof(float));
 }
 

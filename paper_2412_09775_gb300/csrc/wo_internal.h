@@ -49,6 +49,7 @@ struct ZOp {
   float eta_lf, eta_fl;
   int eta_absolute;
   int zero_dc;       // reconstruct: zero D(0) (background = channel mean)
+  int tf_shared;     // 1: every tile uses tile 0's TFs and statistics (one bank for a batch of stacks)
   const float* stats;  // [tile][8] from the TF bank
 };
 // Fused z pass: FFT_z of n_in volumes, per-frequency op, IFFT_z of n_out volumes.
@@ -59,6 +60,35 @@ cudaError_t z_fused(int Z, const float2* in, float2* out, const float2* tf, ZOp 
 // out: [tile][P][Y][Xh].
 cudaError_t z_solve2d(int Z, const float2* in, float2* out, const float2* tf, ZOp op, int n_tiles,
                       int Y, int Xh, cudaStream_t s);
+
+// The device status block at the start of every workspace: int32 code (a
+// wo_status, 0 while nothing went wrong), site, detail; the rest reserved.
+constexpr size_t kStatusBytes = 256;
+
+// Persistent tile pipeline of the phase-only 3D reconstruction (wo_pipe.cu).
+struct PipeLaunch {
+  const float* in;       // [T][Z][Y][X] data
+  float* out;            // [T][Z][Y][X] result
+  float2* spec;          // [T][Z][Y][X/2+1] workspace spectra
+  const float2* tf;      // phase TF slot of tile 0; tiles tf_stride float2 apart (0: shared bank)
+  long long tf_stride;
+  const float* stats;    // [T or 1][8]
+  int* counters;         // pipe_counter_bytes(T), zeroed by the launcher
+  int* status;           // the workspace's status block
+  int n_tiles, Z, Y, X;
+  int tf_shared, eta_absolute, zero_dc, withhold;
+  float eta, bg_plane, scale;
+  long long budget_ns;
+};
+bool pipe_supported(int Z, int Y, int X);
+// Engine of the phase-only 3D reconstruction for these shapes: WO_ENGINE_SMEM
+// (the five passes) or WO_ENGINE_HYBRID (the persistent pipeline).
+int recon_engine(int Z, int Y, int X);
+// Bound of every wait of the pipeline (ns): far above any legitimate wait
+// (an item takes microseconds), far below a hang.
+constexpr long long kPipeBudgetNs = 1000000000LL;
+size_t pipe_counter_bytes(int n_tiles);
+cudaError_t tile_pipeline(const PipeLaunch& p, cudaStream_t s);
 
 // Multi-channel fusion (wo_fuse.cu): one property from C channels, each with
 // its own TF; input spectra [tile][C][Z][Y][Xh], TF bank [tile*C][Z][Y][Xh].
@@ -133,6 +163,12 @@ cudaError_t tune_reduce(const float2* tf2, const float2* spec, const wo_optics* 
                         int Y, int X, float eta, float nu_max, int zf, int loss, int np, double* partials,
                         double* value, double* grad, cudaStream_t s);
 size_t tune_partials_bytes(int n_tiles, int Y, int X, int np);
+// Vector-Jacobian product of the phase reconstruction in the tuned optics:
+// spectra D [tile][Z][Y][Xh] (3D or per plane), upstream spectra G
+// [tile][Z][Y][Xh] (3D) or [tile][Y][Xh] (2D), bank of 1 + np slots per tile;
+// grad [tile][np].
+cudaError_t vjp_reduce(const float2* tf2, const float2* spec, const float2* gspec, int n_tiles, int Z, int Y, int X,
+                       float eta, int mode3d, int np, double* partials, double* grad, cudaStream_t s);
 struct AdamLr {
   double v[4];  // step sizes for defocus_um, tilt_x, tilt_y, na_ill
 };

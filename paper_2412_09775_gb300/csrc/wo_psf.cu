@@ -56,7 +56,7 @@ __device__ __forceinline__ float2 mirror_value(const float2 (&v)[N1], int m, boo
 // and NA_ill under the smooth source (arms A_tx, A_ty, A_NA; their rows
 // 2K (Re conj(a_theta) b - (D_theta / D) Re g), D = sum S P^2).
 template <class P, int MODE>
-__global__ void __launch_bounds__(kPsfThreads, 4) k_psf_rows_reg(TfArgs a) {
+__global__ void __launch_bounds__(kPsfThreads, (P::E > 16 && MODE == 2) ? 2 : 4) k_psf_rows_reg(TfArgs a) {
   constexpr int N = P::N, N1 = P::E, T = P::T, RP = P::SLICE, RPC = kPsfThreads / T;
   __shared__ float2 tw[P::TW];
   __shared__ float2 slices[RPC * RP];
@@ -370,7 +370,7 @@ bool psf_rows_reg_supported(int X, int n_arms) {
   switch (X) {
     case 32: case 48: case 64: case 128: case 256: return true;
     case 512: return n_arms <= 4;
-    case 96: case 192: return n_arms <= 3;  // 24 points per lane: four arms would spill
+    case 96: case 192: return n_arms <= 3 || n_arms == 7;  // 24 points per lane: the derivative bank would spill
     default: return false;
   }
 }
@@ -381,10 +381,12 @@ cudaError_t tf_psf_rows_reg(const TfArgs& a, cudaStream_t s) {
     case 48: return launch_psf_reg_any<Row2<48, 12>>(a, s);
     case 64: return launch_psf_reg_any<Row2<64, 8>>(a, s);
     case 96:
+      if (a.want_grad) return launch_psf_reg<Row2<96, 24>, 2>(a, s);
       if (a.want_dz) return cudaErrorInvalidValue;
       return psf_pairs(a) ? launch_psf_pair<Row2<96, 24>>(a, s) : launch_psf_reg<Row2<96, 24>, 0>(a, s);
     case 128: return launch_psf_reg_any<Row2<128, 16>>(a, s);
     case 192:
+      if (a.want_grad) return launch_psf_reg<Row2<192, 24>, 2>(a, s);
       if (a.want_dz) return cudaErrorInvalidValue;
       return psf_pairs(a) ? launch_psf_pair<Row2<192, 24>>(a, s) : launch_psf_reg<Row2<192, 24>, 0>(a, s);
     case 256: return launch_psf_reg_any<Row2<256, 16>>(a, s);

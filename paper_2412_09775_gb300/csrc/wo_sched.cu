@@ -23,7 +23,19 @@ namespace {
 constexpr int kMaxLen = 2048;
 std::atomic<int> g_cols_engine[kMaxLen + 1];  // 0: default
 std::atomic<int> g_rows_engine[kMaxLen + 1];  // 0: default
+std::atomic<int> g_recon_engine[kMaxLen + 1];  // 0: default, keyed by Y
 }  // namespace
+
+int recon_engine(int Z, int Y, int X) {
+  if (!pipe_supported(Z, Y, X)) return WO_ENGINE_SMEM;
+  const int e = g_recon_engine[Y].load(std::memory_order_relaxed);
+  if (e == WO_ENGINE_SMEM || e == WO_ENGINE_HYBRID) return e;
+  // default: the persistent pipeline, which keeps a tile's spectra in L2
+  // between its passes
+  return WO_ENGINE_HYBRID;
+}
+
+static bool recon_pipe_length(int n) { return n == 64 || n == 128 || n == 192; }
 
 int cols_engine(int n) {
   if (n < 1 || n > kMaxLen) return WO_ENGINE_SMEM;
@@ -126,9 +138,14 @@ using namespace wo;
 extern "C" {
 
 wo_status wo_schedule_set(int pass, int n, int engine) {
-  if (pass != WO_PASS_COLS && pass != WO_PASS_ROWS) return WO_ERR_ARG;
+  if (pass != WO_PASS_COLS && pass != WO_PASS_ROWS && pass != WO_PASS_RECON) return WO_ERR_ARG;
   if (n < 1 || n > kMaxLen) return WO_ERR_ARG;
   if (engine != WO_ENGINE_DEFAULT && engine != WO_ENGINE_SMEM && engine != WO_ENGINE_HYBRID) return WO_ERR_ARG;
+  if (pass == WO_PASS_RECON) {
+    if (engine == WO_ENGINE_HYBRID && !recon_pipe_length(n)) return WO_ERR_UNSUPPORTED_SIZE;
+    g_recon_engine[n].store(engine, std::memory_order_relaxed);
+    return WO_OK;
+  }
   const bool hyb_ok = pass == WO_PASS_COLS ? cols_hyb_supported(n) : rows_reg_supported(n);
   if (engine == WO_ENGINE_HYBRID && !hyb_ok) return WO_ERR_UNSUPPORTED_SIZE;
   (pass == WO_PASS_COLS ? g_cols_engine : g_rows_engine)[n].store(engine, std::memory_order_relaxed);
@@ -139,6 +156,11 @@ int wo_schedule_get(int pass, int n) {
   if (n < 1 || n > kMaxLen) return -1;
   if (pass == WO_PASS_COLS) return cols_engine(n);
   if (pass == WO_PASS_ROWS) return rows_engine(n);
+  if (pass == WO_PASS_RECON) {
+    if (!recon_pipe_length(n)) return WO_ENGINE_SMEM;
+    const int e = g_recon_engine[n].load(std::memory_order_relaxed);
+    return e == WO_ENGINE_SMEM ? WO_ENGINE_SMEM : WO_ENGINE_HYBRID;
+  }
   return -1;
 }
 
@@ -149,12 +171,13 @@ wo_status wo_autotune(int n_tiles, int Z, int Y, int X, unsigned kinds, void* d_
   if (!d_ws || (((uintptr_t)d_ws) & 15u)) return WO_ERR_ARG;
   if (ws_bytes < need) return WO_ERR_WORKSPACE;
   cudaStream_t s = (cudaStream_t)stream;
-  float2* scratch = (float2*)d_ws;
+  // the trials use the workspace past its status block
+  float2* scratch = (float2*)((char*)d_ws + kStatusBytes);
   const int Xh = X / 2 + 1;
   // y passes: Z planes per volume of Y x Xh; the largest batch of the entry
   // points (three volumes per tile) stays inside the workspace's first half
   const size_t vol_bytes = (size_t)Z * Y * Xh * sizeof(float2);
-  long long vols = (long long)((need / 2) / vol_bytes);
+  long long vols = (long long)(((need - kStatusBytes) / 2) / vol_bytes);
   if (vols < 1) vols = 1;
   if (vols > 3LL * n_tiles) vols = 3LL * n_tiles;
   // the x-pass trial uses about twice the bytes of the column trials

@@ -191,6 +191,119 @@ cudaError_t tune_reduce(const float2* tf2, const float2* spec, const wo_optics* 
   return cudaGetLastError();
 }
 
+// Vector-Jacobian product of the phase reconstruction with respect to the
+// tuned optics: dL/dtheta_p = <g, d f/d theta_p> for an upstream gradient g
+// of the reconstruction f (Parseval: (1/N) Re sum_nu conj(G) dF_p, the half
+// spectrum weighted by w as above).  With the regulariser eta absolute:
+//   3D (per 3D frequency):   F = conj(H) D / (|H|^2 + eta),
+//     dF_p = (conj(dH_p) D - 2 Re(conj(H) dH_p) F) / (|H|^2 + eta);
+//   2D (per transverse frequency, sums over the planes j):
+//     F = sum_j conj(H_j) D_j / (sum_j |H_j|^2 + eta),
+//     dF_p = (sum_j conj(dH_pj) D_j - 2 Re(sum_j conj(H_j) dH_pj) F) / (sum_j |H_j|^2 + eta).
+// Partials hold 1 + NP doubles per block (slot 0 unused) so that k_tune_final
+// reduces them.
+template <int NP, bool MODE3D>
+__global__ void __launch_bounds__(kTuneThreads) k_vjp_cols(const float2* __restrict__ tf2,
+                                                           const float2* __restrict__ spec,
+                                                           const float2* __restrict__ gspec, int Z, int Y, int Xh,
+                                                           int X, float eta, double* __restrict__ partials) {
+  __shared__ double red[(1 + NP) * kTuneThreads];
+  const int t = blockIdx.y;
+  const long long plane = (long long)Y * Xh;
+  const long long vol = (long long)Z * plane;
+  const long long c = (long long)blockIdx.x * kTuneThreads + threadIdx.x;
+  double acc[1 + NP];
+#pragma unroll
+  for (int i = 0; i <= NP; ++i) acc[i] = 0.0;
+  if (c < plane) {
+    const int y = (int)(c / Xh), x = (int)(c - (long long)y * Xh);
+    const double w = (x == 0 || 2 * x == X) ? 1.0 : 2.0;
+    const float2* D = spec + (long long)t * vol + c;
+    const float2* H = tf2 + (long long)t * (1 + NP) * vol + c;
+    if constexpr (MODE3D) {
+      const float2* G = gspec + (long long)t * vol + c;
+      float gs[NP];
+#pragma unroll
+      for (int q = 0; q < NP; ++q) gs[q] = 0.f;
+#pragma unroll 4
+      for (int k = 0; k < Z; ++k) {
+        const float2 d = __ldg(D + k * plane), h = __ldg(H + k * plane), g = __ldg(G + k * plane);
+        const float den = cabs2(h) + eta;
+        const float inv = den > 0.f ? 1.0f / den : 0.f;
+        const float2 F = cscale(cmulc(h, d), inv);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+          const float2 dh = __ldg(H + (q + 1) * vol + k * plane);
+          const float2 e = cmulc(dh, d);
+          const float dhr = h.x * dh.x + h.y * dh.y;
+          const float2 dF = make_float2((e.x - 2.f * dhr * F.x) * inv, (e.y - 2.f * dhr * F.y) * inv);
+          gs[q] += g.x * dF.x + g.y * dF.y;  // Re(conj(G) dF)
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < NP; ++q) acc[1 + q] = w * (double)gs[q];
+    } else {
+      float cr = 0.f, ci = 0.f, hh = 0.f, dcr[NP], dci[NP], dhr[NP];
+#pragma unroll
+      for (int q = 0; q < NP; ++q) dcr[q] = dci[q] = dhr[q] = 0.f;
+#pragma unroll 4
+      for (int k = 0; k < Z; ++k) {
+        const float2 d = __ldg(D + k * plane), h = __ldg(H + k * plane);
+        const float2 r = cmulc(h, d);
+        cr += r.x;
+        ci += r.y;
+        hh += cabs2(h);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+          const float2 dh = __ldg(H + (q + 1) * vol + k * plane);
+          const float2 e = cmulc(dh, d);
+          dcr[q] += e.x;
+          dci[q] += e.y;
+          dhr[q] += h.x * dh.x + h.y * dh.y;
+        }
+      }
+      const float den = hh + eta;
+      const float inv = den > 0.f ? 1.0f / den : 0.f;
+      const float2 F = make_float2(cr * inv, ci * inv);
+      const float2 g = __ldg(gspec + (long long)t * plane + c);
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        const float2 dF = make_float2((dcr[q] - 2.f * dhr[q] * F.x) * inv, (dci[q] - 2.f * dhr[q] * F.y) * inv);
+        acc[1 + q] = w * ((double)g.x * dF.x + (double)g.y * dF.y);
+      }
+    }
+  }
+  block_sum<1 + NP>(acc, red);
+  if (threadIdx.x <= NP) partials[((long long)t * gridDim.x + blockIdx.x) * (1 + NP) + threadIdx.x] =
+      red[threadIdx.x * kTuneThreads];
+}
+
+cudaError_t vjp_reduce(const float2* tf2, const float2* spec, const float2* gspec, int n_tiles, int Z, int Y, int X,
+                       float eta, int mode3d, int np, double* partials, double* grad, cudaStream_t s) {
+  const int Xh = X / 2 + 1;
+  const long long plane = (long long)Y * Xh;
+  const unsigned nblk = (unsigned)((plane + kTuneThreads - 1) / kTuneThreads);
+  dim3 grid(nblk, (unsigned)n_tiles);
+  if (np == 4 && !mode3d) {
+    WO_LAUNCH("vjp_cols", s, (k_vjp_cols<4, false><<<grid, kTuneThreads, 0, s>>>(tf2, spec, gspec, Z, Y, Xh, X, eta,
+                                                                                partials)));
+  } else if (np == 1 && !mode3d) {
+    WO_LAUNCH("vjp_cols", s, (k_vjp_cols<1, false><<<grid, kTuneThreads, 0, s>>>(tf2, spec, gspec, Z, Y, Xh, X, eta,
+                                                                                partials)));
+  } else if (np == 1) {
+    WO_LAUNCH("vjp_cols", s, (k_vjp_cols<1, true><<<grid, kTuneThreads, 0, s>>>(tf2, spec, gspec, Z, Y, Xh, X, eta,
+                                                                               partials)));
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const double scale = 1.0 / ((double)X * (double)Y * (mode3d ? (double)Z : 1.0));
+  WO_LAUNCH("tune_final", s, (k_tune_final<<<(unsigned)n_tiles, 32, 0, s>>>(partials, (int)nblk, np, scale, nullptr,
+                                                                             grad)));
+  return cudaGetLastError();
+}
+
 size_t tune_partials_bytes(int n_tiles, int Y, int X, int np) {
   const long long plane = (long long)Y * (X / 2 + 1);
   return (size_t)n_tiles * (size_t)((plane + kTuneThreads - 1) / kTuneThreads) * (1 + np) * sizeof(double);

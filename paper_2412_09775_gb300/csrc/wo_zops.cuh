@@ -128,19 +128,20 @@ __global__ void __launch_bounds__(ZGeom<N, (NI > NO ? NI : NO)>::NT, ZGeom<N, (N
   const long long vol = (long long)N * zs;
   const long long col = (long long)y * Xh + x0;
   const int ntf = op.n_tf;
-  if (outside_support(op.stats + (long long)t * 8, y, Y, x0, 2 * (Xh - 1))) {
+  const int tt = op.tf_shared ? 0 : t;  // the tile whose TFs and statistics apply
+  if (outside_support(op.stats + (long long)tt * 8, y, Y, x0, 2 * (Xh - 1))) {
     // every TF is zero here, so is every operator's output
     zero_zcols<N, B, NT>(out + (long long)t * NO * vol + col, NO, vol, zs, w);
     return;  // uniform across the CTA
   }
   load_zcols<N, NV, B, NT>(buf, in + (long long)t * NI * vol + col, NI, vol, zs, w);
-  load_zcols<N, 3, B, NT>(htf, tf + (long long)t * ntf * vol + col, ntf, vol, zs, w);
+  load_zcols<N, 3, B, NT>(htf, tf + (long long)tt * ntf * vol + col, ntf, vol, zs, w);
   make_twiddles<N>(tw);
   cp_async_wait_all();
   __syncthreads();
   fft_smem<N, NI * B, NT, false, 1>(buf, NV * B, 1, tw);
 
-  const float* st = op.stats + (long long)t * 8;
+  const float* st = op.stats + (long long)tt * 8;
   const float lam_lf = op.eta_absolute ? op.eta_lf : op.eta_lf * st[0];
   const float lam_fl = op.eta_absolute ? op.eta_fl : op.eta_fl * st[2];
   const int L = op.lf_props;
@@ -222,7 +223,8 @@ __global__ void __launch_bounds__(ZGeom<N, NI>::NT, ZGeom<N, NI>::MINB)
   const long long vol = (long long)N * zs;
   const long long col = (long long)y * Xh + x0;
   const int L = op.lf_props;
-  if (outside_support(op.stats + (long long)t * 8, y, Y, x0, 2 * (Xh - 1))) {
+  const int tt = op.tf_shared ? 0 : t;  // the tile whose TFs and statistics apply
+  if (outside_support(op.stats + (long long)tt * 8, y, Y, x0, 2 * (Xh - 1))) {
     if (threadIdx.x < w) {
       float2* o = out + (long long)t * (L + op.has_fl) * Y * Xh + col + threadIdx.x;
       for (int p = 0; p < L + op.has_fl; ++p) o[(long long)p * Y * Xh] = make_float2(0.f, 0.f);
@@ -243,7 +245,7 @@ __global__ void __launch_bounds__(ZGeom<N, NI>::NT, ZGeom<N, NI>::MINB)
     for (int k = kk; k < N; k += KK) {
       const float2* cell = buf + k * NI * B + b;
       const bool dc = op.zero_dc && k == 0 && y == 0 && (x0 + b) == 0;
-      const float2* h = tf + ((long long)t * op.n_tf * N + k) * zs + col + b;
+      const float2* h = tf + ((long long)tt * op.n_tf * N + k) * zs + col + b;
       if (L > 0) {
         const float2 d = dc ? make_float2(0.f, 0.f) : cell[op.lf_chan * B];
         const float2 h0 = __ldg(h);
@@ -276,7 +278,7 @@ __global__ void __launch_bounds__(ZGeom<N, NI>::NT, ZGeom<N, NI>::MINB)
 #pragma unroll
       for (int i = 0; i < NACC; ++i) acc[i] += red[(q * B + b) * NACC + i];
     }
-    const float* st = op.stats + (long long)t * 8;
+    const float* st = op.stats + (long long)tt * 8;
     float2* o = out + (long long)t * (L + op.has_fl) * Y * Xh + (long long)y * Xh + x0 + b;
     const long long plane = (long long)Y * Xh;
     if (L > 0) {

@@ -123,6 +123,9 @@ def test_op_validation(B):
     assert lib.wo_reconstruct(fake, 7, fake, None, pe, 2, 0, fake, 1, 16, 64, 64, fake, big, None) == 1
     assert lib.wo_reconstruct(fake, 7, fake, None, pe, 0, 5, fake, 1, 16, 64, 64, fake, big, None) == 1
     assert lib.wo_reconstruct(fake, 7, fake, None, pe, 0, 0, fake, 1, 16, 64, 64, fake, 16, None) == 8
+    assert lib.wo_reconstruct_shared_tf(fake, 7, fake, None, None, 0, 0, fake, 4, 16, 64, 64, fake, big, None) == 1
+    assert lib.wo_reconstruct_shared_tf(fake, 7, fake, None, pe, 0, 0, fake, 4, 16, 64, 64, fake, 16, None) == 8
+    assert lib.wo_reconstruct_shared_tf(fake, 7, fake, None, pe, 0, 0, fake, 4, 16, 64, 60, fake, big, None) == 3
     assert lib.wo_forward(fake, 7, fake + 8, None, fake, 1, 16, 64, 64, fake, big, None) == 1
     assert lib.wo_forward_adjoint(fake, 7, fake, None, fake, 1, 16, 64, 100, fake, big, None) == 3
 
@@ -172,7 +175,9 @@ def test_tuning_validation(B):
     assert B.wo_tf_bytes(1, 16, 64, 64, 64) == 0                 # needs WO_TF_PLANES
     assert B.wo_tf_bytes(1, 16, 64, 64, 64 | 16) == ((5 * 16 * 64 * 33 * 8 + 255) // 256) * 256 + 32
     assert B.wo_tf_bytes(1, 16, 64, 64, 64 | 16 | 32) == B.wo_tf_bytes(1, 16, 64, 64, 64 | 16)
-    assert B.wo_tf_bytes(1, 16, 64, 96, 64 | 16) == 0            # 96-point rows: no gradient bank
+    assert B.wo_tf_bytes(1, 16, 64, 96, 64 | 16) > 0             # 96- and 192-point rows (the field's tiles)
+    assert B.wo_tf_bytes(1, 16, 192, 192, 64 | 16) > 0
+    assert B.wo_tf_bytes(1, 16, 64, 384, 64 | 16) == 0           # 384-point rows: no gradient bank
     assert B.wo_tf_bytes(1, 16, 64, 64, 64 | 8 | 16) == 0        # two derivative banks at once
     assert B.wo_tf_bytes(1, 16, 64, 64, 4 | 32) == 0             # smooth source without label-free kinds
     assert B.wo_tf_bytes(1, 16, 64, 64, 1 | 32) == B.wo_tf_bytes(1, 16, 64, 64, 1)
@@ -181,9 +186,15 @@ def test_tuning_validation(B):
 
 def test_schedule_table(B):
     lib = B._lib
-    assert lib.wo_schedule_set(2, 128, 1) == 1        # unknown pass
+    assert lib.wo_schedule_set(3, 128, 1) == 1        # unknown pass
     assert lib.wo_schedule_set(1, 1024, 2) == 3       # no register row engine for 1024 points
-    assert lib.wo_schedule_get(2, 128) == -1
+    assert lib.wo_schedule_get(3, 128) == -1
+    # the reconstruction engine, keyed by Y: the tile pipeline at 64, 128 and 192 only
+    for n in (64, 128, 192):
+        assert lib.wo_schedule_get(2, n) == 2                                     # default: the pipeline
+        assert lib.wo_schedule_set(2, n, 1) == 0 and lib.wo_schedule_get(2, n) == 1
+        assert lib.wo_schedule_set(2, n, 0) == 0 and lib.wo_schedule_get(2, n) == 2
+    assert lib.wo_schedule_set(2, 512, 2) == 3 and lib.wo_schedule_get(2, 512) == 1
     for n in (96, 256, 512):  # the x passes
         assert lib.wo_schedule_set(1, n, 2) == 0 and lib.wo_schedule_get(1, n) == 2
         assert lib.wo_schedule_set(1, n, 1) == 0 and lib.wo_schedule_get(1, n) == 1
@@ -225,6 +236,27 @@ def test_pad_validation(B):
     assert lib.wo_crop(fake, 1, 8, 8, 8, 4, 4, 4, fake, None) == 1
 
 
+def test_status_block_entry_points(B):
+    lib = B._lib
+    # the status block leads every workspace: the sizes grow by it
+    n, Z, Y, X = 2, 16, 64, 64
+    assert B.wo_workspace_bytes(n, Z, Y, X, 1) >= 256 + 2 * n * Z * Y * (X // 2 + 1) * 8
+    assert B.wo_fused_workspace_bytes(3, n, Z, Y, X) >= 256 + 4 * n * Z * Y * (X // 2 + 1) * 8
+    info = (ctypes.c_int * 2)()
+    assert lib.wo_sync_status(None, info, None) == 1
+    assert lib.wo_sync_status((1 << 20) + 8, info, None) == 1   # misaligned
+    assert lib.wo_clear_status(None, None) == 1
+    fake, big = 1 << 20, 1 << 40
+    probe = lib.wo_pipeline_probe
+    assert probe(fake, fake, fake, 2, 48, 192, 192, 2, 10 ** 6, fake, big, None) == 1      # withhold >= n_tiles
+    assert probe(fake, fake, fake, 2, 48, 192, 192, -2, 10 ** 6, fake, big, None) == 1
+    assert probe(fake, fake, fake, 2, 48, 192, 192, 0, 10, fake, big, None) == 1           # budget below 1 us
+    assert probe(fake, fake, fake, 2, 48, 96, 96, 0, 10 ** 6, fake, big, None) == 3        # no pipeline for 96
+    assert probe(fake, fake, fake, 2, 48, 192, 192, 0, 10 ** 6, fake, 1024, None) == 8     # workspace
+    assert probe(fake + 4, fake, fake, 2, 48, 192, 192, 0, 10 ** 6, fake, big, None) == 1  # misaligned
+    assert B.STATUS[9] == "WO_ERR_BOUNDS" and "WO_CHECK" in B.wo_status_string(9)
+
+
 def test_status_strings(B):
     for s in range(9):
         assert B.wo_status_string(s)
@@ -254,8 +286,9 @@ def test_fusion_validation(B):
     def a256(n):
         return (n + 255) // 256 * 256
 
-    # nine apertures of two tiles: all channel spectra, one fused spectrum per tile, two floats per tile
-    assert B.wo_fused_workspace_bytes(9, 2, Z, Y, X) == a256(18 * half) + a256(2 * half) + a256(2 * 2 * 4)
+    # nine apertures of two tiles: the status block, all channel spectra, one fused spectrum per tile, two
+    # floats per tile
+    assert B.wo_fused_workspace_bytes(9, 2, Z, Y, X) == 256 + a256(18 * half) + a256(2 * half) + a256(2 * 2 * 4)
     assert B.wo_fused_workspace_bytes(17, 1, Z, Y, X) == 0     # more than 16 channels
     assert B.wo_fused_workspace_bytes(9, 7282, Z, Y, X) == 0   # more than 65535 TF entries
     assert B.wo_fused_workspace_bytes(9, 1, Z, Y, 63) == 0     # odd X

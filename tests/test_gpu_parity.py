@@ -193,6 +193,64 @@ def test_reconstruct_small_widefield_stack(env):
     assert rel_l2(got[0], ref) <= TOL
 
 
+@pytest.mark.parametrize("kinds,mode", [(("phase",), 0), (("phase",), 1), (("phase", "absorption", "fluor"), 0),
+                                        (("phase", "absorption"), 1)])
+def test_reconstruct_batch_sharing_one_tf_bank(env, kinds, mode):
+    """A batch of independent small stacks (16 x 64 x 64) with the same optics
+    reconstructed from one TF bank (wo_reconstruct_shared_tf): every stack
+    against the oracle, and bit for bit equal to wo_reconstruct with the bank
+    replicated per stack."""
+    B, torch, dev = env
+    shape = (16, 64, 64)
+    Z, Y, X = shape
+    n = 5
+    o = ph.optics(na_ill=0.8, tilt_x=0.03, defocus_um=0.1)
+    tf1, _ = check_tf(env, [o], shape, kinds)
+    tfn, ws = B.alloc(n, Z, Y, X, kinds, dev)
+    B.wo_build_tf([o] * n, n, Z, Y, X, kinds, tfn, ws)
+    modes, props, chans = OM.widefield_system(oracle_tf(o, shape, kinds), kinds)
+    d = ph.uniform_volume(21, (n, len(chans)) + shape, 0.9, 1.1).astype(np.float32)
+    eta = [1e-3, 2e-3][: len(modes)]
+    din = torch.from_numpy(d).to(dev)
+    out_shape = (n, len(props)) + ((Z, Y, X) if mode == B.WO_MODE_3D else (Y, X))
+    got = torch.empty(out_shape, dtype=torch.float32, device=dev)
+    rep = torch.empty_like(got)
+    B.wo_reconstruct_shared_tf(tf1, kinds, din, None, eta, B.WO_ETA_RELATIVE, mode, got, n, Z, Y, X, ws)
+    B.wo_reconstruct(tfn, kinds, din, None, eta, B.WO_ETA_RELATIVE, mode, rep, n, Z, Y, X, ws)
+    got, rep = got.cpu().numpy(), rep.cpu().numpy()
+    assert np.array_equal(got, rep)
+    if mode == B.WO_MODE_2D:
+        modes = OM.widefield_system(OO.plane_tfs(o, shape, kinds), kinds)[0]
+    solve = OM.reconstruct if mode == B.WO_MODE_3D else OM.reconstruct_2d
+    for t in range(n):
+        for m, e in zip(modes, eta):
+            r = solve([m], d[t].astype(np.float64), e)
+            for p in m["props"]:
+                assert rel_l2(got[t, p], r[p]) <= TOL, (t, p)
+
+
+def test_reconstruct_shared_tf_full_batch(env):
+    """The small-stack workload's launch configuration: 4096 stacks of
+    16 x 64 x 64 sharing one phase TF bank; the first and last stacks against
+    the oracle."""
+    B, torch, dev = env
+    shape = (16, 64, 64)
+    Z, Y, X = shape
+    n = 4096
+    o = ph.optics()
+    tf1, _ = check_tf(env, [o], shape, ("phase",))
+    ws = torch.empty(B.wo_workspace_bytes(n, Z, Y, X, ("phase",)), dtype=torch.uint8, device=dev)
+    modes, _, _ = OM.widefield_system(oracle_tf(o, shape, ("phase",)), ("phase",))
+    d = ph.uniform_volume(22, (n, 1) + shape, 0.95, 1.05).astype(np.float32)
+    din = torch.from_numpy(d).to(dev)
+    got = torch.empty((n, 1) + shape, dtype=torch.float32, device=dev)
+    B.wo_reconstruct_shared_tf(tf1, ("phase",), din, None, [1e-3], B.WO_ETA_RELATIVE, B.WO_MODE_3D, got, n, Z, Y, X,
+                               ws)
+    for t in (0, n - 1):
+        ref = OM.reconstruct(modes, d[t].astype(np.float64), 1e-3)
+        assert rel_l2(got[t, 0].cpu().numpy(), ref[0]) <= TOL, t
+
+
 @pytest.mark.parametrize("kinds", KIND_SETS)
 @pytest.mark.parametrize("bg,flag", [(None, 0), ("given", 0), ("given", 1)])
 def test_reconstruct_3d(env, kinds, bg, flag):

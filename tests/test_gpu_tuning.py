@@ -16,7 +16,8 @@ from oracle import model as OM, optics as OO, tuning as OT
 
 pytestmark = pytest.mark.gpu
 
-SHAPE = (48, 128, 128)  # the shift-variant tiles (48 planes of 128 x 128)
+SHAPE = (48, 128, 128)  # tiles of 48 planes of 128 x 128
+SHAPE192 = (48, 192, 192)  # the shift-variant field's tiles (128-px cores with 32-px halos)
 
 
 @pytest.fixture(scope="module")
@@ -256,7 +257,7 @@ def test_smooth_source_bank_matches_oracle(env):
             assert np.linalg.norm(spec[t, s_] - OO.half_spectrum(ref[k])) / den <= 1e-4, (t, k)
 
 
-@pytest.mark.parametrize("shape", [(8, 32, 48), (6, 64, 64), (4, 24, 128)])
+@pytest.mark.parametrize("shape", [(8, 32, 48), (6, 64, 64), (4, 24, 128), (6, 48, 96), (4, 24, 192), (3, 192, 192)])
 def test_gradient_bank_matches_oracle(env, shape):
     """The five per-plane slots: H, dH/d(defocus, tilt_x, tilt_y, NA_ill)."""
     B, _, torch, dev = env
@@ -274,8 +275,16 @@ def test_gradient_bank_matches_oracle(env, shape):
             assert rel_l2(spec[t, q], OO.half_spectrum(ref)) <= 1e-4, (t, q)
 
 
+def assert_gradient(grad, gwant, what):
+    """Every component of the adjoint gradient within 1e-3 of the oracle's
+    central difference, relative to that component (no absolute slack)."""
+    err = np.abs(np.asarray(grad) - gwant) / np.abs(gwant)
+    assert np.all(err <= 1e-3), (what, grad, gwant, err)
+
+
+@pytest.mark.parametrize("shape", [SHAPE, SHAPE192])
 @pytest.mark.parametrize("loss", [0, 1])
-def test_four_parameter_gradient_matches_oracle(env, loss):
+def test_four_parameter_gradient_matches_oracle(env, loss, shape):
     """Loss and its gradient in (defocus, tilt_x, tilt_y, NA_ill) against the
     oracle's loss and central differences, data from the smooth-source model."""
     B, A, torch, dev = env
@@ -285,7 +294,7 @@ def test_four_parameter_gradient_matches_oracle(env, loss):
     start = [dict(o, defocus_um=o["defocus_um"] + a, tilt_x=o["tilt_x"] + b, tilt_y=o["tilt_y"] + c,
                   na_ill=o["na_ill"] + e) for o, (a, b, c, e) in zip(ol, offs)]
     eta = 1e-3
-    d = np.stack([thin_stack(o, SHAPE, 70 + 17 * t) for t, o in enumerate(ol)])
+    d = np.stack([thin_stack(o, shape, 70 + 17 * t) for t, o in enumerate(ol)])
     data = torch.tensor(d, dtype=torch.float32, device=dev)
     pb = A.TuningProblem(data, start, eta, params="all", loss=loss)
     pb.evaluate()
@@ -296,17 +305,17 @@ def test_four_parameter_gradient_matches_oracle(env, loss):
         want = (OT.objective if loss == 0 else OT.midband_objective)(start[t], d[t], eta)
         gwant = OT.gradient_fd_params(start[t], d[t], eta, h=1e-4, loss=name)
         assert abs(val[t] - want) <= 1e-4 * abs(want), (t, val[t], want)
-        scale = np.linalg.norm(gwant)
-        assert np.all(np.abs(grad[t] - gwant) <= 1e-3 * np.abs(gwant) + 1e-4 * scale), (t, grad[t], gwant)
+        assert_gradient(grad[t], gwant, t)
 
 
-def test_four_parameter_adam_from_nominal_under_a_cuda_graph(env):
+@pytest.mark.parametrize("shape", [SHAPE, SHAPE192])
+def test_four_parameter_adam_from_nominal_under_a_cuda_graph(env, shape):
     """50 Adam steps on (defocus, tilt_x, tilt_y, NA_ill) from defocus 0, no
     tilt and NA_ill 0.825: every tile within 0.05 um in defocus and 0.01 NA in
     tilt and NA_ill of its true optics (smooth-source data)."""
     B, A, torch, dev = env
     ol = smooth_tiles(8, 24)
-    d = np.stack([thin_stack(o, SHAPE, 80 + 17 * t) for t, o in enumerate(ol)])
+    d = np.stack([thin_stack(o, shape, 80 + 17 * t) for t, o in enumerate(ol)])
     data = torch.tensor(d, dtype=torch.float32, device=dev)
     truth = np.array([[o["defocus_um"], o["tilt_x"], o["tilt_y"], o["na_ill"]] for o in ol])
     start = [dict(o, defocus_um=0.0, tilt_x=0.0, tilt_y=0.0, na_ill=0.825) for o in ol]
@@ -316,14 +325,14 @@ def test_four_parameter_adam_from_nominal_under_a_cuda_graph(env):
     assert np.all(err[:, 0] <= 0.05) and np.all(err[:, 1:] <= 0.01), err
 
 
-def test_four_parameter_gradient_full_batch(env):
+@pytest.mark.parametrize("shape", [SHAPE, SHAPE192])
+def test_four_parameter_gradient_full_batch(env, shape):
     """The auto-tuning workload's launch configuration: 256 tiles of
-    48 x 128 x 128 with their own optics in one batch (per-plane gradient
-    bank, smooth source, data-fidelity loss).  Loss and gradient of two
-    sampled tiles (the first and the last) against the oracle's loss and its
-    central differences."""
+    48 x 192 x 192 (the shift-variant field's tiles; also 48 x 128 x 128) with
+    their own optics in one batch (per-plane gradient bank, smooth source,
+    data-fidelity loss).  Loss and gradient of two sampled tiles (the first
+    and the last) against the oracle's loss and its central differences."""
     B, A, torch, dev = env
-    shape = (48, 128, 128)
     n = 256
     ol = [dict(o, smooth_source=True) for o in tiles(n, 77)]
     start = [dict(o, defocus_um=0.0, tilt_x=0.0, tilt_y=0.0, na_ill=0.825) for o in ol]
@@ -341,5 +350,4 @@ def test_four_parameter_gradient_full_batch(env):
         want = OT.objective(start[t], dt, eta)
         gwant = OT.gradient_fd_params(start[t], dt, eta, h=1e-4, loss="data")
         assert abs(val[t] - want) <= 1e-4 * abs(want), (t, val[t], want)
-        scale = np.linalg.norm(gwant)
-        assert np.all(np.abs(grad[t] - gwant) <= 1e-3 * np.abs(gwant) + 1e-4 * scale), (t, grad[t], gwant)
+        assert_gradient(grad[t], gwant, t)
