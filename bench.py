@@ -55,12 +55,13 @@ WORKLOAD = "widefield 96x512x512: TF build (phase+absorption+fluorescence) + 3D 
 # 96 x 256 x 256 sub-volume (1/4 of the voxels, a quarter of the objects).
 CPU_SAMPLE = (96, 256, 256)
 
-# Last ncu capture of DRAM traffic per launch (bytes) of the dominant kernel,
-# keyed by kernel family and the digest of its sources at capture time
-# (reported as null once a source changes).  tf_psf_rows: 302.1 MB read +
-# 256.3 MB written per launch on the 96x512x512 widefield step itself
-# (profiles/tf_psf_rows_dram_widefield_96x512x512.md).
-NCU_TRAFFIC = {"tf_psf_rows": {"bytes": 302102528 + 256278016, "digest": "659c004dea35d31a"}}
+# Last ncu capture of DRAM traffic per launch (bytes) of a workload's dominant
+# kernel, keyed by (workload, kernel family), with the digest of the kernel's
+# sources at capture time (reported as null once a source changes).
+# field / tf_arms: 18.9 MB read + 844.6 MB written per launch on 64 tiles of
+# 48x192x192 (an 8x8-tile field; the full 256-tile workload is too large for a
+# full capture), scaled by 4 to the 256 tiles of a launch of the bench's field.
+NCU_TRAFFIC = {("field", "tf_arms"): {"bytes": 4 * (18939136 + 844591616), "digest": "f6f532e1fad69ba6"}}
 
 
 def kernel_digest(name: str) -> str:
@@ -617,7 +618,7 @@ def report(args, world, ms_max, e2e_ms, prof, launches, clk, tune=None, lib=None
     peak, peak_kind = peaks()
     dk = per_kernel[dom]
     traffic = None
-    rec = NCU_TRAFFIC.get(dom)
+    rec = NCU_TRAFFIC.get(("widefield", dom))
     if rec and rec.get("digest") == kernel_digest(dom):
         traffic = rec["bytes"]
     roofline = {"bound": "hbm", "kernel": dom, "achieved": dk["gbs"], "peak": peak, "unit": "GB/s",
@@ -673,7 +674,7 @@ def make_field(o_list, dev, seed=4):
     ty, tx = TILE_GRID
     Z, E = FIELD_Z, TILE_CORE + 2 * TILE_HALO
     n = ty * tx
-    obj = ph.sphere_phantom(seed, (Z, ty * TILE_CORE, tx * TILE_CORE), ph.optics(), n_spheres=16000)
+    obj = ph.sphere_phantom(seed, (Z, ty * TILE_CORE, tx * TILE_CORE), ph.optics(), n_spheres=16000 * n // 256)
     obj_d = torch.from_numpy(obj.astype(np.float32)).to(dev)
     t_obj = torch.empty((n, Z, E, E), dtype=torch.float32, device=dev)
     B.wo_tile_gather(obj_d, Z, ty, tx, TILE_CORE, TILE_HALO, t_obj)
@@ -735,14 +736,14 @@ def kernel_table(prof, algo, per):
     return out
 
 
-def roofline_of(kern, prof):
+def roofline_of(kern, prof, workload=None):
     """The roofline entry of the kernel family with the largest share."""
     dom = max(prof.items(), key=lambda kv: kv[1][1])[0]
     peak, peak_kind = peaks()
     gbs = kern[dom]["gbs"]
     traffic = None
-    rec = NCU_TRAFFIC.get(dom)
-    if rec and rec.get("digest") == kernel_digest(dom) and rec.get("workload") == "field":
+    rec = NCU_TRAFFIC.get((workload, dom))
+    if rec and rec.get("digest") == kernel_digest(dom):
         traffic = rec["bytes"]
     return {"bound": "hbm", "kernel": dom, "achieved": gbs, "peak": peak, "unit": "GB/s",
             "frac": round(gbs / peak, 4) if gbs else None, "traffic": traffic,
@@ -830,9 +831,9 @@ def field_leg(args, rank, world, local_rank):
     # per-kernel times from eager profiled steps (the events do not enter a graph)
     with torch.cuda.stream(s):
         prof = profiled_pass(B, step, args.steps)
-    # the same step with the reconstruction on its five-pass engine instead of
-    # the tile pipeline (context for the engine choice)
-    B.wo_schedule_set(B.WO_PASS_RECON, E, B.WO_ENGINE_SMEM)
+    # the same step with the reconstruction on the persistent tile pipeline
+    # instead of the five passes (context for the engine choice)
+    B.wo_schedule_set(B.WO_PASS_RECON, E, B.WO_ENGINE_HYBRID)
     g5 = torch.cuda.CUDAGraph()
     with torch.cuda.stream(s):
         step()
@@ -862,14 +863,15 @@ def field_leg(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": round(ms_max, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (sphere phantom forward-simulated per tile with its own optics + 1e-3 noise)",
-        "config": {"workload": TILES_WORKLOAD, "field": [Z, ty * TILE_CORE, tx * TILE_CORE], "tiles": n,
+        "config": {"workload": TILES_WORKLOAD if (ty, tx) == (16, 16) else f"profiling case: {ty}x{tx} tiles",
+                   "field": [Z, ty * TILE_CORE, tx * TILE_CORE], "tiles": n,
                    "tile": [Z, E, E], "eta_relative": 1e-3, "parallelism": f"replicas x{world}",
                    "l2": "working set > L2, no flush needed (field 805 MB, tiles 1.8 GB, TF 1.8 GB)",
                    "schedule": engines(E, Z, rows=E // 2)},
-        "roofline": roofline_of(kern, prof), "kernels": kern,
+        "roofline": roofline_of(kern, prof, "field" if (ty, tx) == (16, 16) else None), "kernels": kern,
         "gpu_launches": int(per_step_launches * args.steps), "clocks": clk,
         "e2e": e2e,
-        "recon_engine": {"engine": engines_recon(E), "step_ms_with_five_passes": round(passes_ms, 4),
+        "recon_engine": {"engine": engines_recon(E), "step_ms_with_tile_pipeline": round(passes_ms, 4),
                          "device_status": list(code)},
     }
     if not args.no_cpu_baseline:
@@ -1532,10 +1534,15 @@ def main():
                     help="engine of the x passes (default: the library's choice)")
     ap.add_argument("--shape", type=int, nargs=3, default=None,
                     help="override Z Y X (smaller cases for profiler captures only)")
+    ap.add_argument("--tile-grid", type=int, nargs=2, default=None,
+                    help="field workload: tiles along y and x (smaller cases for profiler captures only)")
     args = ap.parse_args()
     if args.shape:
         global SHAPE
         SHAPE = tuple(args.shape)
+    if args.tile_grid:
+        global TILE_GRID
+        TILE_GRID = tuple(args.tile_grid)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -469,6 +469,13 @@ wo_status wo_adam_optics(wo_optics *d_optics, const double *d_grad, int n_params
  * increment of one plane of thickness z_step: sum dn 2 sqrt(r^2 - rho^2) / dz. */
 size_t wo_est_param_count(void);
 size_t wo_est_workspace_bytes(int batch);
+/* Byte offset, in the estimator's workspace, of convolution layer `layer`'s
+ * output (1..4: float32 [batch][C][H][H] after its ReLU) as the last
+ * wo_est_forward / wo_est_backward / wo_est_train_step of that batch size
+ * left it: the network's ReLU decisions, for comparisons with a reference
+ * that decides them in another precision.  Layer 1's output starts the
+ * workspace (offset 0); 0 on invalid arguments for the other layers. */
+size_t wo_est_activation_offset(int batch, int layer);
 wo_status wo_est_sync_bf16(const float *d_w32, void *d_wbf16, wo_stream stream);
 wo_status wo_est_forward(const void *d_wbf16, const float *d_w32, const float *d_feat, int batch,
                          const float *h_scale, const float *h_offset, float *d_out, void *d_ws,
@@ -520,10 +527,12 @@ enum { WO_PASS_ROWS = 1 };
  * WO_TF_SMOOTH_SOURCE, or a WO_TF_PHASE_DZ bank, WO_MODE_3D) of tiles whose
  * planes fit one SM's shared memory, keyed by n = Y: WO_ENGINE_SMEM (the five
  * passes, each a kernel over the whole batch) or WO_ENGINE_HYBRID (one
- * persistent kernel: CTAs take per-plane x/y work, per-row z-solve work and
- * per-plane inverse x/y work from one queue, so a tile's spectra stay in L2
- * between them; the default where it exists: (Z, Y, X) = (48, 192, 192),
- * (48, 128, 128), (16, 64, 64)).  Every wait of that kernel on another CTA's
+ * kernel: CTAs take per-plane x/y work, per-row z-solve work and per-plane
+ * inverse x/y work from one queue in ticket order, so a tile's spectra stay
+ * in L2 between them; available for (Z, Y, X) = (48, 192, 192),
+ * (48, 128, 128), (16, 64, 64)).  The default is WO_ENGINE_SMEM, the faster
+ * on this part (the pipeline holds one plane per SM and cannot overlap one
+ * item's copies with another's transforms).  Every wait of that kernel on another CTA's
  * work is bounded (one second): when it runs out, the kernel records
  * WO_ERR_TIMEOUT in the workspace's status block (wo_sync_status) and stops.
  * Results agree with the passes to float32 rounding. */
@@ -562,6 +571,14 @@ wo_status wo_autotune(int n_tiles, int Z, int Y, int X, unsigned kinds, void *d_
  *   wo_workspace_bytes(n_tiles, Z, Y, X, WO_TF_PHASE). */
 wo_status wo_clear_status(void *d_ws, wo_stream stream);
 wo_status wo_sync_status(void *d_ws, int *h_info, wo_stream stream);
+/* 1 for a WO_CHECK build of the library, else 0.  In a WO_CHECK build the
+ * kernels test the index of each global-memory access against the extent of
+ * the buffer it addresses; an access outside is skipped (never a fault) and
+ * the first such index is recorded (WO_ERR_BOUNDS; site: 4 tile gather/blend,
+ * 5 column transforms, 6 z passes, 7 x passes, 8 arms, 9 PSF rows; detail:
+ * the index), which wo_sync_status returns when the workspace's own block is
+ * clear. */
+int wo_check_build(void);
 wo_status wo_pipeline_probe(const void *d_tf, const float *d_data, float *d_f, int n_tiles, int Z, int Y, int X,
                             int withhold, long long budget_ns, void *d_ws, size_t ws_bytes, wo_stream stream);
 

@@ -133,8 +133,14 @@ def loss(flat, x, target) -> float:
     return float(np.mean((out - target) ** 2))
 
 
-def backward(flat: np.ndarray, x: np.ndarray, target: np.ndarray):
-    """Loss and d(mean squared error)/d(parameters), float64, flattened."""
+def backward(flat: np.ndarray, x: np.ndarray, target: np.ndarray, masks=None):
+    """Loss and d(mean squared error)/d(parameters), float64, flattened.
+
+    ``masks`` (optional, one boolean array per convolution layer, the shape
+    of its output) gives the ReLU decisions to differentiate through; by
+    default they are this forward pass's (activation > 0).  A pre-activation
+    within float rounding of zero can be decided either way, so a comparison
+    with float32 kernels passes their decisions here."""
     p = [bf16(q) if q.ndim > 1 else np.asarray(q, dtype=np.float64) for q in unpack(flat)]
     out, acts = forward(flat, x)
     B = x.shape[0]
@@ -147,7 +153,7 @@ def backward(flat: np.ndarray, x: np.ndarray, target: np.ndarray):
     g = (g_out @ p[-2])[:, :, None, None] * np.ones_like(h) / (h.shape[2] * h.shape[3])
     for li in range(len(LAYERS) - 1, -1, -1):
         ci, co, s = LAYERS[li]
-        g = g * (acts[li + 1] > 0)
+        g = g * ((acts[li + 1] > 0) if masks is None else masks[li])
         xin = acts[li]
         Bn, Ci, H, W = xin.shape
         Ho, Wo = g.shape[2], g.shape[3]

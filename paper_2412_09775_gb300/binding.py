@@ -4,8 +4,9 @@ Every function here has the name of the C entry point it calls and does no
 arithmetic of the method: it converts torch tensors to device pointers and
 the current torch stream to a cudaStream_t, calls the library, and raises
 ``WoError`` on a non-zero status.  The library is loaded from the in-tree
-build (``paper_2412_09775_gb300/lib/libwo_gb300.so``); if it is missing the
-import of this module fails loudly - there is no CPU fallback.
+build (``paper_2412_09775_gb300/lib/libwo_gb300.so``, or its WO_CHECK variant
+``libwo_gb300_check.so`` when the environment sets WO_LIB=check); if it is
+missing the import of this module fails loudly - there is no CPU fallback.
 """
 from __future__ import annotations
 
@@ -13,7 +14,8 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "lib", "libwo_gb300.so")
+LIB_PATH = os.path.join(HERE, "lib", "libwo_gb300_check.so" if os.environ.get("WO_LIB") == "check"
+                        else "libwo_gb300.so")
 
 WO_TF_PHASE, WO_TF_ABSORPTION, WO_TF_FLUOR = 1, 2, 4
 WO_TF_PHASE_DZ = 8
@@ -72,6 +74,7 @@ def _load():
         "wo_reconstruct_shared_tf": (i, [vp, u, vp, fp, fp, i, i, vp, i, i, i, i, vp, sz, vp]),
         "wo_clear_status": (i, [vp, vp]),
         "wo_sync_status": (i, [vp, ctypes.POINTER(ctypes.c_int), vp]),
+        "wo_check_build": (i, []),
         "wo_pipeline_probe": (i, [vp, vp, vp, i, i, i, i, i, ctypes.c_longlong, vp, sz, vp]),
         "wo_spectrum": (i, [vp, fp, i, vp, i, i, i, i, vp]),
         "wo_tune_objective": (i, [vp, u, vp, vp, i, f, f, vp, vp, i, i, i, i, vp, sz, vp]),
@@ -82,6 +85,7 @@ def _load():
         "wo_reconstruct_fused": (i, [vp, i, vp, fp, f, i, i, vp, i, i, i, i, vp, sz, vp]),
         "wo_est_param_count": (sz, []),
         "wo_est_workspace_bytes": (sz, [i]),
+        "wo_est_activation_offset": (sz, [i, i]),
         "wo_est_sync_bf16": (i, [vp, vp, vp]),
         "wo_est_forward": (i, [vp, vp, vp, i, fp, fp, vp, vp, sz, vp]),
         "wo_est_backward": (i, [vp, vp, vp, vp, i, fp, fp, vp, vp, vp, sz, vp]),
@@ -113,9 +117,9 @@ EXPORTED = ("wo_size_supported", "wo_tf_bytes", "wo_workspace_bytes", "wo_build_
             "wo_aberrated_workspace_bytes", "wo_build_tf_aberrated",
             "wo_forward",
             "wo_forward_adjoint", "wo_reconstruct", "wo_reconstruct_static", "wo_reconstruct_shared_tf",
-            "wo_clear_status", "wo_sync_status", "wo_pipeline_probe", "wo_spectrum",
+            "wo_clear_status", "wo_sync_status", "wo_check_build", "wo_pipeline_probe", "wo_spectrum",
             "wo_tune_objective", "wo_reconstruct_vjp", "wo_adam_optics", "wo_fused_workspace_bytes", "wo_reconstruct_fused",
-            "wo_est_param_count", "wo_est_workspace_bytes", "wo_est_sync_bf16", "wo_est_forward", "wo_est_backward",
+            "wo_est_param_count", "wo_est_workspace_bytes", "wo_est_activation_offset", "wo_est_sync_bf16", "wo_est_forward", "wo_est_backward",
             "wo_est_train_step", "wo_est_features", "wo_thin_phantom",
             "wo_schedule_set", "wo_schedule_get", "wo_autotune", "wo_tile_gather", "wo_tile_blend",
             "wo_pad", "wo_crop",
@@ -285,6 +289,11 @@ def wo_sync_status(ws, stream=None):
     return code, int(info[0]), int(info[1])
 
 
+def wo_check_build() -> bool:
+    """True for the WO_CHECK variant of the library (kernels test their indices)."""
+    return bool(_lib.wo_check_build())
+
+
 def wo_pipeline_probe(tf, data, f, n_tiles, Z, Y, X, withhold, budget_ns, ws, stream=None):
     """The tile pipeline with one tile's plane items withheld and a wait budget (diagnostic)."""
     _check(_lib.wo_pipeline_probe(_ptr(tf), _ptr(data), _ptr(f), n_tiles, Z, Y, X, int(withhold), int(budget_ns),
@@ -340,6 +349,10 @@ def wo_est_param_count() -> int:
 
 def wo_est_workspace_bytes(batch) -> int:
     return int(_lib.wo_est_workspace_bytes(int(batch)))
+
+
+def wo_est_activation_offset(batch, layer) -> int:
+    return int(_lib.wo_est_activation_offset(int(batch), int(layer)))
 
 
 def wo_est_sync_bf16(w32, wbf16, stream=None):

@@ -290,6 +290,60 @@ int wo_profile_read(const char** names, long long* launches, double* ms, int cap
 }
 
 long long wo_launch_count(void) { return g_launches.load(); }
+}  // extern "C"
+
+namespace wo {
+namespace {
+std::mutex g_attr_mu;
+std::vector<std::pair<const void*, int>> g_attr_set;  // (kernel, device) with the shared-memory attribute set
+}  // namespace
+
+#if defined(WO_CHECK) && WO_CHECK
+namespace {
+std::vector<CheckReader>& check_units() {
+  static std::vector<CheckReader> units;
+  return units;
+}
+std::mutex g_check_mu;
+}  // namespace
+
+void check_register(CheckReader r) {
+  std::lock_guard<std::mutex> lk(g_check_mu);
+  check_units().push_back(r);
+}
+
+int check_take_all(int* info) {
+  std::lock_guard<std::mutex> lk(g_check_mu);
+  int first = 0;
+  for (CheckReader r : check_units()) {
+    int inf[2] = {0, 0};
+    const int c = r(inf);
+    if (c != 0 && first == 0) {
+      first = c;
+      if (info) {
+        info[0] = inf[0];
+        info[1] = inf[1];
+      }
+    }
+  }
+  return first;
+}
+#endif
+
+bool smem_attr_done(const void* kernel, int device) {
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  for (const auto& e : g_attr_set)
+    if (e.first == kernel && e.second == device) return true;
+  return false;
+}
+
+void smem_attr_mark(const void* kernel, int device) {
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  g_attr_set.emplace_back(kernel, device);
+}
+}  // namespace wo
+
+extern "C" {
 
 // Shared body of wo_build_tf (optics copied from the host into the workspace)
 // and wo_build_tf_device (optics read in place from device memory).
@@ -579,7 +633,27 @@ wo_status wo_sync_status(void* d_ws, int* h_info, wo_stream stream) {
     h_info[1] = blk[2];
   }
   if (blk[0] < 0 || blk[0] > (int)WO_ERR_BOUNDS) return WO_ERR_CUDA;  // not a status: the block was never cleared
+#if defined(WO_CHECK) && WO_CHECK
+  // the index checks of every translation unit (read and cleared in any case)
+  int cinfo[2] = {0, 0};
+  const int c = check_take_all(cinfo);
+  if (blk[0] == 0 && c != 0) {
+    if (h_info) {
+      h_info[0] = cinfo[0];
+      h_info[1] = cinfo[1];
+    }
+    return (wo_status)c;
+  }
+#endif
   return (wo_status)blk[0];
+}
+
+int wo_check_build(void) {
+#if defined(WO_CHECK) && WO_CHECK
+  return 1;
+#else
+  return 0;
+#endif
 }
 
 wo_status wo_clear_status(void* d_ws, wo_stream stream) {

@@ -83,8 +83,8 @@ template <class P>
 cudaError_t launch_cols_hyb(bool inv, float2* data, long long cs, long long ps, int ncols, long long nplanes,
                             cudaStream_t s, const char* name, long long groups, long long gs) {
   using G = HybGeom<P>;
-  static cudaError_t a0 = allow_smem(k_cols_hyb<P, false>, G::SMEM);
-  static cudaError_t a1 = allow_smem(k_cols_hyb<P, true>, G::SMEM);
+  const cudaError_t a0 = allow_smem(k_cols_hyb<P, false>, G::SMEM);
+  const cudaError_t a1 = allow_smem(k_cols_hyb<P, true>, G::SMEM);
   if (a0 != cudaSuccess) return a0;
   if (a1 != cudaSuccess) return a1;
   const unsigned gx = (unsigned)((ncols + G::CPC - 1) / G::CPC);

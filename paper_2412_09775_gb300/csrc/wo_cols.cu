@@ -57,6 +57,14 @@ __global__ void __launch_bounds__(ColGeom<N>::NT, ColGeom<N>::MINB)
   const int x0 = blockIdx.x * B;
   const int w = min(B, ncols - x0);
   float2* base = data + g * group_stride + plane * plane_stride + x0;
+#if defined(WO_CHECK) && WO_CHECK
+  {  // the elements this tile addresses, against the extent of the passes' volume
+    const long long extent = (total / nplanes - 1) * group_stride + (nplanes - 1) * plane_stride +
+                             (long long)(N - 1) * col_stride + ncols;
+    const long long first = base - data, last = first + (long long)(N - 1) * col_stride + w - 1;
+    if (!WO_IN(first, extent, 5) || !WO_IN(last, extent, 5)) return;  // uniform across the CTA
+  }
+#endif
   col_tile_load<N, B, NT>(buf, base, col_stride, w);
   make_twiddles<N>(tw);  // while the tile's copies are in flight
   cp_async_wait_all();
@@ -71,8 +79,8 @@ static cudaError_t launch_cols(bool inv, float2* data, long long cs, long long p
                                long long gs) {
   using G = ColGeom<N>;
   const size_t smem = G::SMEM;
-  static cudaError_t a0 = allow_smem(k_cols<N, false>, smem);
-  static cudaError_t a1 = allow_smem(k_cols<N, true>, smem);
+  const cudaError_t a0 = allow_smem(k_cols<N, false>, smem);
+  const cudaError_t a1 = allow_smem(k_cols<N, true>, smem);
   if (a0 != cudaSuccess) return a0;
   if (a1 != cudaSuccess) return a1;
   const unsigned gx = (unsigned)((ncols + G::B - 1) / G::B);

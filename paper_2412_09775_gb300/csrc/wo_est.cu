@@ -27,7 +27,6 @@ struct LayerDef {
 };
 constexpr LayerDef kLayers[4] = {{3, 32, 1, 64}, {32, 64, 2, 64}, {64, 96, 2, 32}, {96, 128, 2, 16}};
 
-__host__ __device__ constexpr int hout(int h, int s) { return (h + s - 1) / s; }
 
 // Offsets of every parameter array in the flat layout.
 struct ParamMap {
@@ -158,49 +157,7 @@ __global__ void k_thin_phantom(const float4* __restrict__ par, int S, int Y, int
 }
 
 // ---------------------------------------------------------------- network
-constexpr int kCoTile = 8;  // output channels per thread in the forward pass
-
-// y[b][co][oh][ow] = relu(b[co] + sum_ci sum_k x[b][ci][oh*s+kh-1][ow*s+kw-1] w[co][ci][kh][kw])
-__global__ void __launch_bounds__(256) k_conv_fwd(const float* __restrict__ x, const __nv_bfloat16* __restrict__ wb,
-                                                  const float* __restrict__ w32, long long woff, long long boff,
-                                                  int Ci, int Co, int H, int s, float* __restrict__ y) {
-  extern __shared__ float ws[];  // [kCoTile][Ci][9]
-  const int Ho = hout(H, s);
-  const int co0 = blockIdx.y * kCoTile, b = blockIdx.z;
-  for (int i = threadIdx.x; i < kCoTile * Ci * 9; i += blockDim.x) {
-    const int c = i / (Ci * 9);
-    ws[i] = co0 + c < Co ? bf(wb, woff + (long long)(co0 + c) * Ci * 9 + (i - c * Ci * 9)) : 0.f;
-  }
-  __syncthreads();
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= Ho * Ho) return;
-  const int oh = p / Ho, ow = p - (p / Ho) * Ho;
-  float acc[kCoTile];
-#pragma unroll
-  for (int c = 0; c < kCoTile; ++c) acc[c] = co0 + c < Co ? w32[boff + co0 + c] : 0.f;
-  const float* xb = x + (long long)b * Ci * H * H;
-  for (int ci = 0; ci < Ci; ++ci) {
-    const float* xc = xb + (long long)ci * H * H;
-    float v[9];
-#pragma unroll
-    for (int kh = 0; kh < 3; ++kh) {
-#pragma unroll
-      for (int kw = 0; kw < 3; ++kw) {
-        const int ih = oh * s + kh - 1, iw = ow * s + kw - 1;
-        v[kh * 3 + kw] = (ih >= 0 && ih < H && iw >= 0 && iw < H) ? __ldg(xc + ih * H + iw) : 0.f;
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < kCoTile; ++c) {
-      const float* wc = ws + (c * Ci + ci) * 9;
-#pragma unroll
-      for (int k = 0; k < 9; ++k) acc[c] = fmaf(v[k], wc[k], acc[c]);
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < kCoTile; ++c)
-    if (co0 + c < Co) y[((long long)b * Co + co0 + c) * Ho * Ho + p] = fmaxf(acc[c], 0.f);
-}
+// (the convolutions run on the tensor cores: wo_estmma.cu)
 
 // pooled[b][c] = mean y4; out[b][k] = sum_c fw[k][c] pooled[b][c] + fb[k]; one block per sample
 __global__ void __launch_bounds__(128) k_head_fwd(const float* __restrict__ y4, const __nv_bfloat16* __restrict__ wb,
@@ -276,113 +233,6 @@ __global__ void k_unpool(const float* __restrict__ gpool, const float* __restric
   g[i] = y[i] > 0.f ? gpool[bc] / (float)HW : 0.f;
 }
 
-// gx[b][ci][ih][iw] = sum_co sum_k g[b][co][oh][ow] w[co][ci][kh][kw] over the
-// (oh, ow, kh, kw) with oh*s + kh - 1 = ih, ow*s + kw - 1 = iw; then masked
-// by the ReLU of the layer below (xin > 0).  g is already masked.
-__global__ void __launch_bounds__(256) k_conv_bwd_data(const float* __restrict__ g, const __nv_bfloat16* __restrict__ wb,
-                                                       long long woff, int Ci, int Co, int H, int s,
-                                                       const float* __restrict__ xin, float* __restrict__ gx) {
-  extern __shared__ float ws[];  // [kCoTile ci][Co][9]
-  const int Ho = hout(H, s);
-  const int ci0 = blockIdx.y * kCoTile, b = blockIdx.z;
-  for (int i = threadIdx.x; i < kCoTile * Co * 9; i += blockDim.x) {
-    const int c = i / (Co * 9), rem = i - c * Co * 9, co = rem / 9, k = rem - co * 9;
-    ws[i] = ci0 + c < Ci ? bf(wb, woff + ((long long)co * Ci + ci0 + c) * 9 + k) : 0.f;
-  }
-  __syncthreads();
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= H * H) return;
-  const int ih = p / H, iw = p - (p / H) * H;
-  float acc[kCoTile];
-#pragma unroll
-  for (int c = 0; c < kCoTile; ++c) acc[c] = 0.f;
-  const float* gb = g + (long long)b * Co * Ho * Ho;
-#pragma unroll
-  for (int kh = 0; kh < 3; ++kh) {
-    const int th = ih + 1 - kh;
-    if (th < 0 || th % s) continue;
-    const int oh = th / s;
-    if (oh >= Ho) continue;
-#pragma unroll
-    for (int kw = 0; kw < 3; ++kw) {
-      const int tw_ = iw + 1 - kw;
-      if (tw_ < 0 || tw_ % s) continue;
-      const int ow = tw_ / s;
-      if (ow >= Ho) continue;
-      const int k = kh * 3 + kw;
-      for (int co = 0; co < Co; ++co) {
-        const float gv = __ldg(gb + ((long long)co * Ho + oh) * Ho + ow);
-#pragma unroll
-        for (int c = 0; c < kCoTile; ++c) acc[c] = fmaf(gv, ws[(c * Co + co) * 9 + k], acc[c]);
-      }
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < kCoTile; ++c) {
-    if (ci0 + c >= Ci) continue;
-    const long long i = ((long long)b * Ci + ci0 + c) * H * H + p;
-    gx[i] = xin[i] > 0.f ? acc[c] : 0.f;
-  }
-}
-
-// dW[co][ci][k] += sum over a chunk of samples and all output pixels of
-// g[b][co][o] x[b][ci][o*s + k - 1]; db[co] likewise from g.  Grid
-// (Co, ceil(Ci/4), sample chunks); one block reduces and adds atomically.
-constexpr int kWgCi = 4;
-__global__ void __launch_bounds__(256) k_conv_bwd_weight(const float* __restrict__ g, const float* __restrict__ x,
-                                                         int Ci, int Co, int H, int s, int B, int chunk,
-                                                         long long woff, long long boff, float* __restrict__ grad) {
-  __shared__ float red[256];
-  const int co = blockIdx.x, ci0 = blockIdx.y * kWgCi;
-  const int b0 = blockIdx.z * chunk, b1 = min(B, b0 + chunk);
-  const int Ho = hout(H, s);
-  float acc[kWgCi * 9 + 1];
-#pragma unroll
-  for (int i = 0; i < kWgCi * 9 + 1; ++i) acc[i] = 0.f;
-  const long long n = (long long)(b1 - b0) * Ho * Ho;
-  for (long long e = threadIdx.x; e < n; e += blockDim.x) {
-    const int b = b0 + (int)(e / (Ho * Ho));
-    const int o = (int)(e % (Ho * Ho));
-    const int oh = o / Ho, ow = o - (o / Ho) * Ho;
-    const float gv = g[((long long)b * Co + co) * Ho * Ho + o];
-    if (gv == 0.f) continue;
-    acc[kWgCi * 9] += gv;
-#pragma unroll
-    for (int c = 0; c < kWgCi; ++c) {
-      if (ci0 + c >= Ci) break;
-      const float* xc = x + ((long long)b * Ci + ci0 + c) * H * H;
-#pragma unroll
-      for (int kh = 0; kh < 3; ++kh) {
-        const int ih = oh * s + kh - 1;
-        if (ih < 0 || ih >= H) continue;
-#pragma unroll
-        for (int kw = 0; kw < 3; ++kw) {
-          const int iw = ow * s + kw - 1;
-          if (iw < 0 || iw >= H) continue;
-          acc[c * 9 + kh * 3 + kw] = fmaf(gv, __ldg(xc + ih * H + iw), acc[c * 9 + kh * 3 + kw]);
-        }
-      }
-    }
-  }
-  for (int i = 0; i < kWgCi * 9 + 1; ++i) {
-    red[threadIdx.x] = acc[i];
-    __syncthreads();
-    for (int h = 128; h > 0; h >>= 1) {
-      if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-      if (i == kWgCi * 9) {
-        if (blockIdx.y == 0) atomicAdd(grad + boff + co, red[0]);
-      } else {
-        const int c = i / 9, k = i - (i / 9) * 9;
-        if (ci0 + c < Ci) atomicAdd(grad + woff + ((long long)co * Ci + ci0 + c) * 9 + k, red[0]);
-      }
-    }
-    __syncthreads();
-  }
-}
-
 // Adam (Kingma and Ba, 2015) on the float32 master weights, then their
 // bfloat16 copy (round to nearest even).  step is 1-based.
 __global__ void k_adam_flat(float* __restrict__ w, __nv_bfloat16* __restrict__ wb, const float* __restrict__ g,
@@ -414,8 +264,24 @@ __global__ void k_standardise(const float* __restrict__ phys, const float* __res
 
 // Workspace layout for a batch.
 struct EstWs {
-  size_t act[5], out, pooled, gpool, gA, gB, grad, target, scale, total;
+  size_t act[5], out, pooled, gpool, gA, gB, grad, target, scale, part, total;
+  size_t part_floats;  // partial weight gradients of the tensor-core kernels
 };
+
+// Floats of the per-chunk partial weight gradients (the largest layer's need:
+// about 2k blocks of one tap and 16 input channels, at most one chunk per
+// sample).
+size_t est_part_floats(int B) {
+  size_t m = 0;
+  for (int l = 0; l < 4; ++l) {
+    const int per = 9 * ((kLayers[l].ci + 15) / 16);
+    long long chunks = (2048 + per - 1) / per;
+    if (chunks > B) chunks = B;
+    const size_t need = (size_t)chunks * kLayers[l].co * kLayers[l].ci * 9;
+    m = need > m ? need : m;
+  }
+  return m;
+}
 size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 EstWs est_ws(int B) {
   EstWs L{};
@@ -435,6 +301,8 @@ EstWs est_ws(int B) {
   L.grad = o; o += al((size_t)kMap.total * sizeof(float));
   L.target = o; o += al((size_t)B * kOut * sizeof(float));
   L.scale = o; o += al(2 * kOut * sizeof(float));
+  L.part_floats = est_part_floats(B);
+  L.part = o; o += al(L.part_floats * sizeof(float));
   L.total = o;
   return L;
 }
@@ -443,14 +311,8 @@ cudaError_t net_forward(const __nv_bfloat16* wb, const float* w32, const float* 
                         cudaStream_t s, const float* scale, const float* offset, float* phys) {
   const float* x = feat;
   for (int l = 0; l < 4; ++l) {
-    const LayerDef d = kLayers[l];
-    const int Ho = hout(d.hin, d.stride);
     float* y = (float*)(ws + L.act[l + 1]);
-    dim3 grid((unsigned)((Ho * Ho + 255) / 256), (unsigned)((d.co + kCoTile - 1) / kCoTile), (unsigned)B);
-    const size_t smem = (size_t)kCoTile * d.ci * 9 * sizeof(float);
-    WO_LAUNCH("est_conv_fwd", s, (k_conv_fwd<<<grid, 256, smem, s>>>(x, wb, w32, kMap.w[l], kMap.b[l], d.ci, d.co,
-                                                                      d.hin, d.stride, y)));
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = est_conv_fwd_mma(l, x, wb, w32, kMap.w[l], kMap.b[l], B, y, s);
     if (e != cudaSuccess) return e;
     x = y;
   }
@@ -478,28 +340,13 @@ cudaError_t net_backward(const __nv_bfloat16* wb, const float* w32, const float*
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   for (int l = 3; l >= 0; --l) {
-    const LayerDef d = kLayers[l];
     const float* xin = l == 0 ? feat : (const float*)(ws + L.act[l]);
-    const int Ho = hout(d.hin, d.stride);
-    // chunks of samples so that the grid has a few thousand blocks
-    const int per = (int)((long long)d.co * ((d.ci + kWgCi - 1) / kWgCi));
-    int chunks = (4096 + per - 1) / per;
-    if (chunks > B) chunks = B;
-    const int chunk = (B + chunks - 1) / chunks;
-    chunks = (B + chunk - 1) / chunk;
-    dim3 gw((unsigned)d.co, (unsigned)((d.ci + kWgCi - 1) / kWgCi), (unsigned)chunks);
-    WO_LAUNCH("est_conv_bwd_w", s, (k_conv_bwd_weight<<<gw, 256, 0, s>>>(g, xin, d.ci, d.co, d.hin, d.stride, B, chunk,
-                                                                          kMap.w[l], kMap.b[l], grad)));
-    e = cudaGetLastError();
+    // weight and bias gradients, then (below the first layer) the gradient at
+    // the layer's input, masked by the ReLU that produced it
+    e = est_conv_bwd_mma(l, g, xin, wb, kMap.w[l], kMap.b[l], B, l == 0 ? nullptr : gnext, (float*)(ws + L.part),
+                         L.part_floats, grad, s);
     if (e != cudaSuccess) return e;
     if (l == 0) break;
-    dim3 gd((unsigned)((d.hin * d.hin + 255) / 256), (unsigned)((d.ci + kCoTile - 1) / kCoTile), (unsigned)B);
-    const size_t smem = (size_t)kCoTile * d.co * 9 * sizeof(float);
-    WO_LAUNCH("est_conv_bwd_x", s, (k_conv_bwd_data<<<gd, 256, smem, s>>>(g, wb, kMap.w[l], d.ci, d.co, d.hin,
-                                                                           d.stride, xin, gnext)));
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    (void)Ho;
     float* tmp = g;
     g = gnext;
     gnext = tmp;
@@ -605,6 +452,11 @@ size_t wo_est_param_count(void) { return est_param_count(); }
 size_t wo_est_workspace_bytes(int batch) {
   if (batch < 1 || batch > 4096) return 0;
   return est_workspace_bytes(batch);
+}
+
+size_t wo_est_activation_offset(int batch, int layer) {
+  if (batch < 1 || batch > 4096 || layer < 1 || layer > 4) return 0;
+  return est_ws(batch).act[layer];
 }
 
 wo_status wo_est_sync_bf16(const float* d_w32, void* d_wbf16, wo_stream stream) {

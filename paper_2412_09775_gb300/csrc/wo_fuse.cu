@@ -136,7 +136,7 @@ template <int N>
 cudaError_t launch_z_fuse(const float2* in, float2* out, const float2* tf, const FuseOp& op, int n_tiles, int Y,
                           int Xh, cudaStream_t s) {
   using G = FuseGeom<N>;
-  static cudaError_t attr = allow_smem(k_z_fuse<N>, G::SMEM);
+  const cudaError_t attr = allow_smem(k_z_fuse<N>, G::SMEM);
   if (attr != cudaSuccess) return attr;
   dim3 grid((unsigned)((Xh + G::B - 1) / G::B), (unsigned)Y, (unsigned)n_tiles);
   WO_LAUNCH("z_fuse", s, (k_z_fuse<N><<<grid, G::NT, G::SMEM, s>>>(in, out, tf, op, Y, Xh)));

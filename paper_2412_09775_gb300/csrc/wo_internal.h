@@ -7,6 +7,48 @@
 
 namespace wo {
 
+// Index checks of the WO_CHECK build.  WO_IN(i, n, site) is true when
+// 0 <= i < n; in a WO_CHECK build a kernel guards its global-memory accesses
+// with it, skips an access whose index falls outside the buffer it addresses
+// and records the first such index in its translation unit's device check
+// block (code WO_ERR_BOUNDS, the site, the index), which wo_sync_status reads
+// and clears.  Without WO_CHECK it is the constant true and costs nothing.
+#if defined(WO_CHECK) && WO_CHECK
+using CheckReader = int (*)(int* info);  // reads and clears one unit's block: code, [site, index]
+void check_register(CheckReader r);
+int check_take_all(int* info);           // the first recorded error over every unit (WO_OK if none)
+namespace {
+__device__ int g_wo_check[4];  // per translation unit: this build has no relocatable device code
+__device__ __noinline__ void check_fail(int site, long long i) {
+  if (atomicCAS(&g_wo_check[0], 0, (int)WO_ERR_BOUNDS) == 0) {
+    g_wo_check[1] = site;
+    g_wo_check[2] = (int)(i > 2147483647LL ? 2147483647LL : (i < -2147483647LL ? -2147483647LL : i));
+  }
+}
+int check_take_unit(int* info) {
+  int h[4] = {0, 0, 0, 0};
+  if (cudaMemcpyFromSymbol(h, g_wo_check, sizeof(h)) != cudaSuccess) return (int)WO_ERR_CUDA;
+  if (h[0] != 0) {
+    const int z[4] = {0, 0, 0, 0};
+    if (cudaMemcpyToSymbol(g_wo_check, z, sizeof(z)) != cudaSuccess) return (int)WO_ERR_CUDA;
+    if (info) {
+      info[0] = h[1];
+      info[1] = h[2];
+    }
+  }
+  return h[0];
+}
+struct CheckUnit {
+  CheckUnit() { check_register(&check_take_unit); }
+};
+const CheckUnit g_check_unit;
+}  // namespace
+#define WO_IN(i, n, site) \
+  (((unsigned long long)(long long)(i) < (unsigned long long)(long long)(n)) ? true : (wo::check_fail((site), (long long)(i)), false))
+#else
+#define WO_IN(i, n, site) true
+#endif
+
 // Instrumentation: counts every launch; with profiling on, brackets it with
 // CUDA events on its stream (see wo_profile_enable).
 void prof_begin(const char* name, cudaStream_t s, int* token);
@@ -196,6 +238,16 @@ cudaError_t est_backward(const void* wb, const float* w32, const float* feat, co
 cudaError_t est_adam(float* w32, void* wb, const float* grad, float* m, float* v, int step, float lr, float b1,
                      float b2, float eps, cudaStream_t s);
 float* est_grad_buffer(void* ws, int B);
+// The estimator's convolutions on the tensor cores (wo_estmma.cu): layer
+// 0..3, bfloat16 weights wb (element offsets woff, boff of the flat
+// parameter array), float32 activations [B][C][H][H].  Backward: weight and
+// bias gradients of the layer into grad, and (gx != NULL) the gradient at its
+// input masked by xin > 0; part holds part_floats floats of scratch.
+cudaError_t est_conv_fwd_mma(int layer, const float* x, const void* wb, const float* w32, long long woff,
+                             long long boff, int B, float* y, cudaStream_t s);
+cudaError_t est_conv_bwd_mma(int layer, const float* gy, const float* xin, const void* wb, long long woff,
+                             long long boff, int B, float* gx, float* part, size_t part_floats, float* grad,
+                             cudaStream_t s);
 
 // Tiles.
 cudaError_t tiles_gather(const float* field, int Z, int ty, int tx, int core, int halo,
@@ -203,11 +255,21 @@ cudaError_t tiles_gather(const float* field, int Z, int ty, int tx, int core, in
 cudaError_t tiles_blend(const float* tiles, int Z, int ty, int tx, int core, int halo,
                         float* field, cudaStream_t s);
 
-// Opt a kernel into more than 48 KB of dynamic shared memory (once).
+// Opt a kernel into more than 48 KB of dynamic shared memory, once per kernel
+// and device (the attribute belongs to the device's context): a registry of
+// the (kernel, device) pairs already set, kept by wo_api.cu.
+bool smem_attr_done(const void* kernel, int device);
+void smem_attr_mark(const void* kernel, int device);
 template <class K>
 inline cudaError_t allow_smem(K kernel, size_t bytes) {
   if (bytes <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (smem_attr_done((const void*)kernel, dev)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) smem_attr_mark((const void*)kernel, dev);
+  return e;
 }
 
 }  // namespace wo

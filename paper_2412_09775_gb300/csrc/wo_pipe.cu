@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(PipeArgs a) {
 template <int Z, int Y, int H>
 cudaError_t launch_pipe(const PipeArgs& a, cudaStream_t s) {
   using G = PipeGeom<Z, Y, H>;
-  static cudaError_t attr = allow_smem(k_pipe<Z, Y, H>, G::SMEM);
+  const cudaError_t attr = allow_smem(k_pipe<Z, Y, H>, G::SMEM);
   if (attr != cudaSuccess) return attr;
   int dev = 0, sms = 0, per = 0;
   cudaError_t e = cudaGetDevice(&dev);

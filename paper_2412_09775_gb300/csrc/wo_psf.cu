@@ -67,15 +67,30 @@ __global__ void __launch_bounds__(kPsfThreads, (P::E > 16 && MODE == 2) ? 2 : 4)
   float2* S = slices + r * RP;
   const long long nrows = a.row_end;
   const long long row = a.row_begin + (long long)blockIdx.x * RPC + r;
-  const bool live = row < nrows;
+  bool live = row < nrows;
   const long long rr = live ? row : nrows - 1;  // tail lanes compute on a valid row, store nothing
   const long long zy = (long long)a.Z * a.Y;
-  const long long t = rr / zy, rem = rr - t * zy;  // rem = j*Y + y
-  const int kxm = a.counts[4 * t + 2];
+  long long t = rr / zy, rem = rr - t * zy;  // rem = j*Y + y
   const bool lf = a.lf_props > 0, fl = a.want_fl != 0;
   const int Xh = N / 2 + 1;
-  float2* dst = a.tf + (t * a.n_kinds * a.Z) * (long long)a.Y * Xh + rem * Xh;  // slot 0 of this row
   const long long kstride = (long long)a.Z * a.Y * Xh;
+#if defined(WO_CHECK) && WO_CHECK
+  {  // the row's count, last arm point and last TF bin inside their arrays; a
+     // failed check turns the row into a tail row (row 0, nothing stored), so
+     // the block's barrier is still met
+    const long long arms_end = (long long)a.n_tiles * a.n_arms * a.Z * a.Y * N;
+    const long long tf_end = (long long)a.n_tiles * a.n_kinds * kstride;
+    if (!WO_IN(t, a.n_tiles, 9) ||
+        !WO_IN(((t * a.n_arms + a.n_arms - 1) * a.Z) * (long long)a.Y * N + rem * N + N - 1, arms_end, 9) ||
+        !WO_IN((t * a.n_kinds * a.Z) * (long long)a.Y * Xh + rem * Xh + (a.n_kinds - 1) * kstride + N / 2, tf_end, 9)) {
+      live = false;
+      t = 0;
+      rem = 0;
+    }
+  }
+#endif
+  const int kxm = a.counts[4 * t + 2];
+  float2* dst = a.tf + (t * a.n_kinds * a.Z) * (long long)a.Y * Xh + rem * Xh;  // slot 0 of this row
 
   constexpr bool DZ = MODE >= 1;
   float2 w[N1];
@@ -227,18 +242,34 @@ __global__ void __launch_bounds__(kPsfThreads, P::E > 16 ? 3 : 4) k_psf_rows_pai
   float* Hs = held + r * HP + lt;  // this lane's points lt + T m at Hs[T m]
   const long long nrows = a.row_end;
   const long long row0 = a.row_begin + 2 * ((long long)blockIdx.x * RPC + r);
-  const bool live0 = row0 < nrows, live1 = row0 + 1 < nrows;
+  bool live0 = row0 < nrows, live1 = row0 + 1 < nrows;
   const long long r0 = live0 ? row0 : nrows - 1, r1 = live1 ? row0 + 1 : nrows - 1;  // tails compute, store nothing
   const long long zy = (long long)a.Z * a.Y;
-  const long long t0 = r0 / zy, rem0 = r0 - t0 * zy, t1 = r1 / zy, rem1 = r1 - t1 * zy;
-  const int kxm0 = a.counts[4 * t0 + 2], kxm1 = a.counts[4 * t1 + 2];
+  long long t0 = r0 / zy, rem0 = r0 - t0 * zy, t1 = r1 / zy, rem1 = r1 - t1 * zy;
   constexpr bool lf = LF > 0, lf1 = LF == 1;
   const bool fl = a.want_fl != 0;
   const int Xh = N / 2 + 1;
   const long long kstride = (long long)a.Z * a.Y * Xh;
+  const int fl_arm = lf ? 2 : 0;
+#if defined(WO_CHECK) && WO_CHECK
+  {  // both rows' counts, last arm points and last TF bins inside their arrays
+    const long long arms_end = (long long)a.n_tiles * a.n_arms * a.Z * a.Y * N;
+    const long long tf_end = (long long)a.n_tiles * a.n_kinds * kstride;
+    const long long last_arm = (long long)a.n_arms - 1;
+    if (!WO_IN(t0, a.n_tiles, 9) || !WO_IN(t1, a.n_tiles, 9) ||
+        !WO_IN(((t0 * a.n_arms + last_arm) * a.Z) * (long long)a.Y * N + rem0 * N + N - 1, arms_end, 9) ||
+        !WO_IN(((t1 * a.n_arms + last_arm) * a.Z) * (long long)a.Y * N + rem1 * N + N - 1, arms_end, 9) ||
+        !WO_IN((t0 * a.n_kinds * a.Z) * (long long)a.Y * Xh + rem0 * Xh + (a.n_kinds - 1) * kstride + N / 2, tf_end, 9) ||
+        !WO_IN((t1 * a.n_kinds * a.Z) * (long long)a.Y * Xh + rem1 * Xh + (a.n_kinds - 1) * kstride + N / 2, tf_end, 9)) {
+      live0 = live1 = false;  // both rows become tail rows: nothing stored, the barrier still met
+      t0 = t1 = 0;
+      rem0 = rem1 = 0;
+    }
+  }
+#endif
+  const int kxm0 = a.counts[4 * t0 + 2], kxm1 = a.counts[4 * t1 + 2];
   float2* dst0 = a.tf + (t0 * a.n_kinds * a.Z) * (long long)a.Y * Xh + rem0 * Xh;
   float2* dst1 = a.tf + (t1 * a.n_kinds * a.Z) * (long long)a.Y * Xh + rem1 * Xh;
-  const int fl_arm = lf ? 2 : 0;
 
   float2 w[N1];
   float2 va[N1];

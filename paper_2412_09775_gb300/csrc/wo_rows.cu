@@ -135,7 +135,7 @@ static size_t rows_smem_c2r() {
 template <int N>
 static cudaError_t launch_r2c(const float* in, float2* out, long long nrows, RowBg bg, cudaStream_t s) {
   const size_t smem = rows_smem_r2c<N>();
-  static cudaError_t attr = allow_smem(k_rows_r2c<N>, smem);
+  const cudaError_t attr = allow_smem(k_rows_r2c<N>, smem);
   if (attr != cudaSuccess) return attr;
   const long long blocks = (nrows + RowGeom<N>::B - 1) / RowGeom<N>::B;
   WO_LAUNCH("rows_r2c", s, (k_rows_r2c<N><<<(unsigned)blocks, RowGeom<N>::NT, smem, s>>>(in, out, nrows, bg)));
@@ -146,7 +146,7 @@ template <int N>
 static cudaError_t launch_c2r(const float2* in, float* out, long long nrows, float scale, RowBg bg,
                               cudaStream_t s) {
   const size_t smem = rows_smem_c2r<N>();
-  static cudaError_t attr = allow_smem(k_rows_c2r<N>, smem);
+  const cudaError_t attr = allow_smem(k_rows_c2r<N>, smem);
   if (attr != cudaSuccess) return attr;
   const long long blocks = (nrows + RowGeom<N>::B - 1) / RowGeom<N>::B;
   WO_LAUNCH("rows_c2r", s,

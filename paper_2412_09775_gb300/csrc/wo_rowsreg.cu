@@ -61,8 +61,12 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_r2c_reg(const float* __res
   const int partner = (lane - t) + (T - t) % T;
   float2* S = sm + P::TW + 2 * N + r * P::SLICE;
   const long long row = (long long)blockIdx.x * RPC + r;
-  const bool live = row < nrows;
-  const long long rr = live ? row : nrows - 1;  // tail lanes transform a valid row and store nothing
+  const bool live0 = row < nrows;
+  long long rr = live0 ? row : nrows - 1;  // tail lanes transform a valid row and store nothing
+  // (a failed index check turns the row into a tail row: the block's barriers are still met)
+  const bool inside = WO_IN(rr, nrows, 7);
+  if (!inside) rr = 0;
+  const bool live = live0 && inside;
   const float c = row_constant(in, rr, 2LL * N, bg);
   const float2* src = reinterpret_cast<const float2*>(in + rr * (2LL * N)) + t;
   float2 v[E];
@@ -100,8 +104,11 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_c2r_reg(const float2* __re
   const int partner = (lane - t) + (T - t) % T;
   float2* S = sm + P::TW + 2 * N + r * P::SLICE;
   const long long row = (long long)blockIdx.x * RPC + r;
-  const bool live = row < nrows;
-  const long long rr = live ? row : nrows - 1;
+  const bool live0 = row < nrows;
+  long long rr = live0 ? row : nrows - 1;
+  const bool inside = WO_IN(rr, nrows, 7);
+  if (!inside) rr = 0;
+  const bool live = live0 && inside;
   const float2* src = in + rr * (N + 1) + t;
   float2 x[E];
 #pragma unroll
@@ -132,7 +139,7 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_c2r_reg(const float2* __re
 template <class P>
 cudaError_t launch_r2c_reg(const float* in, float2* out, long long nrows, RowBg bg, cudaStream_t s) {
   using G = RowRegGeom<P>;
-  static cudaError_t attr = allow_smem(k_rows_r2c_reg<P>, G::SMEM);
+  const cudaError_t attr = allow_smem(k_rows_r2c_reg<P>, G::SMEM);
   if (attr != cudaSuccess) return attr;
   const long long blocks = (nrows + G::RPC - 1) / G::RPC;
   WO_LAUNCH("rows_r2c", s, (k_rows_r2c_reg<P><<<(unsigned)blocks, kRowThreads, G::SMEM, s>>>(in, out, nrows, bg)));
@@ -142,7 +149,7 @@ cudaError_t launch_r2c_reg(const float* in, float2* out, long long nrows, RowBg 
 template <class P>
 cudaError_t launch_c2r_reg(const float2* in, float* out, long long nrows, float scale, RowBg bg, cudaStream_t s) {
   using G = RowRegGeom<P>;
-  static cudaError_t attr = allow_smem(k_rows_c2r_reg<P>, G::SMEM);
+  const cudaError_t attr = allow_smem(k_rows_c2r_reg<P>, G::SMEM);
   if (attr != cudaSuccess) return attr;
   const long long blocks = (nrows + G::RPC - 1) / G::RPC;
   WO_LAUNCH("rows_c2r", s,

@@ -336,6 +336,15 @@ __global__ void __launch_bounds__(ColGeom<N>::NT, (1024 / ColGeom<N>::NT) > 1 ? 
   bool active = false;
   for (int b = 0; b < w; ++b) active |= abs(fft_index(x0 + b, X)) <= kxmax;
   if (!active) return;  // uniform across the CTA
+#if defined(WO_CHECK) && WO_CHECK
+  {  // the strip's records and the arm strips it writes
+    const long long nt = gridDim.z;
+    if (!WO_IN((long long)t * N * X + x0 + (long long)(N - 1) * X + w - 1, nt * N * X, 8) ||
+        !WO_IN((((long long)t * a.n_arms + a.n_arms - 1) * Z + j) * (long long)N * X + x0 + (long long)(N - 1) * X + w - 1,
+               nt * a.n_arms * Z * (long long)N * X, 8))
+      return;
+  }
+#endif
   make_twiddles<N>(tw);
   // the plane's focal displacement as a float pair, formed in float64 by one
   // lane of each warp (float64 is slow on this part) and broadcast
@@ -636,8 +645,8 @@ static cudaError_t launch_arms(const TfArgs& a, cudaStream_t s) {
   constexpr size_t kStage = (size_t)N * G::B * sizeof(float);
   constexpr size_t kMax = 227 * 1024;
   constexpr size_t kCap = G::SMEM + 4 * kStage <= kMax ? G::SMEM + 4 * kStage : kMax;
-  static cudaError_t attr0 = allow_smem(k_arms<N, false>, G::SMEM);
-  static cudaError_t attr1 = allow_smem(k_arms<N, true>, kCap);
+  const cudaError_t attr0 = allow_smem(k_arms<N, false>, G::SMEM);
+  const cudaError_t attr1 = allow_smem(k_arms<N, true>, kCap);
   if (attr0 != cudaSuccess) return attr0;
   if (attr1 != cudaSuccess) return attr1;
   TfArgs b = a;
@@ -676,7 +685,7 @@ static cudaError_t launch_psf(const TfArgs& a, cudaStream_t s) {
   constexpr size_t cap = s4 <= kMax ? s4 : s3;
   const size_t smem = ((size_t)a.n_arms * G::SLOT + NX + 2 * G::B) * sizeof(float2);
   if (smem > cap) return cudaErrorInvalidValue;
-  static cudaError_t attr = allow_smem(k_psf_rows<NX>, cap);
+  const cudaError_t attr = allow_smem(k_psf_rows<NX>, cap);
   if (attr != cudaSuccess) return attr;
   const long long rows = a.row_end - a.row_begin;
   WO_LAUNCH("tf_psf_rows", s, (k_psf_rows<NX><<<(unsigned)((rows + G::B - 1) / G::B), G::NT, smem, s>>>(a)));
@@ -702,7 +711,7 @@ template <int N, int NK>
 static cudaError_t launch_zpass(const TfArgs& a, cudaStream_t s) {
   using G = ZGeom<N, NK>;
   const size_t smem = G::SMEM + (size_t)G::NT * 2 * sizeof(float);
-  static cudaError_t attr = allow_smem(k_tf_zpass<N, NK>, smem);
+  const cudaError_t attr = allow_smem(k_tf_zpass<N, NK>, smem);
   if (attr != cudaSuccess) return attr;
   dim3 grid((unsigned)((a.x_cols + G::B - 1) / G::B), (unsigned)a.Y, (unsigned)a.n_tiles);
   WO_LAUNCH("tf_zpass", s, (k_tf_zpass<N, NK><<<grid, G::NT, smem, s>>>(a)));

@@ -42,6 +42,9 @@ __global__ void __launch_bounds__(256)
     const int y = mirror_idx(ty * core - halo + u, Yf);
     const int xs = tx * core - halo + v0;
     const float* row = src + (long long)y * Xf;
+    if (!WO_IN(tz * (long long)E * E + (long long)u * E + min(v0 + 3, E - 1), (long long)gridDim.y * E * E, 4) ||
+        !WO_IN(z * (long long)Yf * Xf + (long long)y * Xf, (long long)Z * Yf * Xf, 4))
+      continue;
     if (vec && xs >= 0 && xs + 3 < Xf && v0 + 3 < E) {
       *reinterpret_cast<float4*>(dst + (long long)u * E + v0) = __ldg(reinterpret_cast<const float4*>(row + xs));
     } else {
@@ -84,6 +87,8 @@ __global__ void __launch_bounds__(256)
       if (v < 0 || v >= E) continue;  // vec: v..v+3 lie in the same tile
       for (int a = 0; a < ny; ++a) {
         const long long t = (long long)tys[a] * tiles_x + c;
+        if (!WO_IN(((t * Z + z) * E + us[a]) * (long long)E + v + lanes - 1, (long long)tiles_y * tiles_x * Z * E * E, 4))
+          continue;
         const float* src = tiles + ((t * Z + z) * E + us[a]) * (long long)E + v;
         float val[4];
         if (vec) {
@@ -100,6 +105,7 @@ __global__ void __launch_bounds__(256)
       }
     }
     float* dst = field + zy * (long long)Xf + x0;
+    if (!WO_IN(zy * (long long)Xf + x0 + lanes - 1, (long long)gridDim.x * Xf, 4)) continue;
     if (vec) {
       *reinterpret_cast<float4*>(dst) =
           make_float4(acc[0] / wsum[0], acc[1] / wsum[1], acc[2] / wsum[2], acc[3] / wsum[3]);

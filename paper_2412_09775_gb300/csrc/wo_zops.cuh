@@ -129,6 +129,16 @@ __global__ void __launch_bounds__(ZGeom<N, (NI > NO ? NI : NO)>::NT, ZGeom<N, (N
   const long long col = (long long)y * Xh + x0;
   const int ntf = op.n_tf;
   const int tt = op.tf_shared ? 0 : t;  // the tile whose TFs and statistics apply
+#if defined(WO_CHECK) && WO_CHECK
+  {  // this strip's elements in the input, output and TF volumes
+    const long long span = (long long)(N - 1) * zs + w - 1;
+    const long long nt = gridDim.z, ntt = op.tf_shared ? 1 : nt;
+    if (!WO_IN((long long)t * NI * vol + (NI - 1) * vol + col + span, nt * NI * vol, 6) ||
+        !WO_IN((long long)t * NO * vol + (NO - 1) * vol + col + span, nt * NO * vol, 6) ||
+        !WO_IN((long long)tt * ntf * vol + (ntf - 1) * vol + col + span, ntt * ntf * vol, 6))
+      return;  // uniform across the CTA
+  }
+#endif
   if (outside_support(op.stats + (long long)tt * 8, y, Y, x0, 2 * (Xh - 1))) {
     // every TF is zero here, so is every operator's output
     zero_zcols<N, B, NT>(out + (long long)t * NO * vol + col, NO, vol, zs, w);
@@ -224,6 +234,16 @@ __global__ void __launch_bounds__(ZGeom<N, NI>::NT, ZGeom<N, NI>::MINB)
   const long long col = (long long)y * Xh + x0;
   const int L = op.lf_props;
   const int tt = op.tf_shared ? 0 : t;  // the tile whose TFs and statistics apply
+#if defined(WO_CHECK) && WO_CHECK
+  {  // this strip's elements in the input and TF volumes, and in the 2D output
+    const long long span = (long long)(N - 1) * zs + w - 1;
+    const long long nt = gridDim.z, ntt = op.tf_shared ? 1 : nt, np = L + op.has_fl;
+    if (!WO_IN((long long)t * NI * vol + (NI - 1) * vol + col + span, nt * NI * vol, 6) ||
+        !WO_IN((long long)tt * op.n_tf * vol + (op.n_tf - 1) * vol + col + span, ntt * op.n_tf * vol, 6) ||
+        !WO_IN(((long long)t * np + np - 1) * Y * Xh + col + w - 1, nt * np * Y * Xh, 6))
+      return;  // uniform across the CTA
+  }
+#endif
   if (outside_support(op.stats + (long long)tt * 8, y, Y, x0, 2 * (Xh - 1))) {
     if (threadIdx.x < w) {
       float2* o = out + (long long)t * (L + op.has_fl) * Y * Xh + col + threadIdx.x;
@@ -312,7 +332,7 @@ cudaError_t launch_z_fused(const float2* in, float2* out, const float2* tf, ZOp 
                            cudaStream_t s) {
   constexpr int NV = NI > NO ? NI : NO;
   using G = ZGeom<N, NV>;
-  static cudaError_t attr = allow_smem(k_z_fused<N, NI, NO>, G::SMEM_TF);
+  const cudaError_t attr = allow_smem(k_z_fused<N, NI, NO>, G::SMEM_TF);
   if (attr != cudaSuccess) return attr;
   dim3 grid((unsigned)((Xh + G::B - 1) / G::B), (unsigned)Y, (unsigned)n_tiles);
   WO_LAUNCH("z_fused", s, (k_z_fused<N, NI, NO><<<grid, G::NT, G::SMEM_TF, s>>>(in, out, tf, op, Y, Xh)));
@@ -324,7 +344,7 @@ cudaError_t launch_z_solve2d(const float2* in, float2* out, const float2* tf, ZO
                              cudaStream_t s) {
   using G = ZGeom<N, NI>;
   const size_t smem = G::SMEM + (size_t)G::NT * 11 * sizeof(float);
-  static cudaError_t attr = allow_smem(k_z_solve2d<N, NI>, smem);
+  const cudaError_t attr = allow_smem(k_z_solve2d<N, NI>, smem);
   if (attr != cudaSuccess) return attr;
   dim3 grid((unsigned)((Xh + G::B - 1) / G::B), (unsigned)Y, (unsigned)n_tiles);
   WO_LAUNCH("z_solve2d", s, (k_z_solve2d<N, NI><<<grid, G::NT, smem, s>>>(in, out, tf, op, Y, Xh)));

@@ -191,9 +191,9 @@ def test_schedule_table(B):
     assert lib.wo_schedule_get(3, 128) == -1
     # the reconstruction engine, keyed by Y: the tile pipeline at 64, 128 and 192 only
     for n in (64, 128, 192):
-        assert lib.wo_schedule_get(2, n) == 2                                     # default: the pipeline
-        assert lib.wo_schedule_set(2, n, 1) == 0 and lib.wo_schedule_get(2, n) == 1
-        assert lib.wo_schedule_set(2, n, 0) == 0 and lib.wo_schedule_get(2, n) == 2
+        assert lib.wo_schedule_get(2, n) == 1                                     # default: the five passes
+        assert lib.wo_schedule_set(2, n, 2) == 0 and lib.wo_schedule_get(2, n) == 2
+        assert lib.wo_schedule_set(2, n, 0) == 0 and lib.wo_schedule_get(2, n) == 1
     assert lib.wo_schedule_set(2, 512, 2) == 3 and lib.wo_schedule_get(2, 512) == 1
     for n in (96, 256, 512):  # the x passes
         assert lib.wo_schedule_set(1, n, 2) == 0 and lib.wo_schedule_get(1, n) == 2

@@ -103,7 +103,11 @@ def test_pipeline_with_shared_tf_and_derivative_bank(env):
     B.wo_build_tf([o, o], 2, Z, Y, X, kinds, tf, ws)
     din = torch.from_numpy(d[:2]).to(dev)
     out = torch.empty_like(din)
-    B.wo_reconstruct(tf, kinds, din, None, [1e-3], B.WO_ETA_RELATIVE, B.WO_MODE_3D, out, 2, Z, Y, X, ws)
+    engine(B, Y, B.WO_ENGINE_HYBRID)
+    try:
+        B.wo_reconstruct(tf, kinds, din, None, [1e-3], B.WO_ETA_RELATIVE, B.WO_MODE_3D, out, 2, Z, Y, X, ws)
+    finally:
+        engine(B, Y, B.WO_ENGINE_DEFAULT)
     assert B.wo_sync_status(ws)[0] == 0
     assert rel_l2(out.cpu().numpy(), got[:2]) <= 1e-5
 

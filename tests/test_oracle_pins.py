@@ -671,6 +671,32 @@ def test_estimator_backward_matches_finite_differences(monkeypatch):
             assert abs(g[i] - fd) <= 1e-6 * (abs(fd) + 1e-4), (k, i, g[i], fd)
 
 
+def test_estimator_backward_with_given_relu_decisions():
+    """Passing the forward pass's own ReLU decisions reproduces the default
+    gradient exactly; flipping the decision of one output that is exactly zero
+    before the ReLU changes only gradients of that layer and below."""
+    from oracle import estimator as E
+    rng = np.random.default_rng(4)
+    flat = rng.normal(size=E.n_params()) * 0.05
+    x = rng.normal(size=(2, 3, 16, 16))
+    t = rng.normal(size=(2, 4))
+    _, acts = E.forward(flat, x)
+    masks = [a > 0 for a in acts[1:5]]
+    L0, g0 = E.backward(flat, x, t)
+    L1, g1 = E.backward(flat, x, t, masks=masks)
+    assert L0 == L1 and np.array_equal(g0, g1)
+    # an inactive output of the last convolution layer switched on: its
+    # activation is 0 either way, so the forward pass and the head's
+    # gradients stay, while the layers below see one more path
+    m = [q.copy() for q in masks]
+    i = np.argwhere(~m[3])[0]
+    m[3][tuple(i)] = True
+    _, g2 = E.backward(flat, x, t, masks=m)
+    offs = np.cumsum([0] + [int(np.prod(sh)) for sh in E.param_shapes()])
+    assert np.array_equal(g2[offs[8]:], g0[offs[8]:])          # the linear head
+    assert not np.array_equal(g2[offs[6]:offs[7]], g0[offs[6]:offs[7]])  # the last conv's weights
+
+
 def test_estimator_features_properties():
     """Plane-to-plane drift shows in the cross channels with its sign and
     axis; reversing the plane order mirrors the rows and flips the drift;
