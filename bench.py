@@ -929,13 +929,16 @@ def field_e2e(args, B, step_on, field, o_list, n, Z, E, world, dev):
     ok = bool(torch.equal(lanes[0]["h_out"], lanes[-1]["h_out"]))
     del lanes
     torch.cuda.empty_cache()
-    return {"value": round(job_throughput(vox, world, piped), 1), "unit": "voxels/s", "ms_per_step": round(piped, 4),
-            "h2d_bytes_per_step": int(vox * 4), "d2h_bytes_per_step": int(vox * 4), "streams": args.e2e_streams,
-            "serial_ms_per_step": round(serial, 4), "serial_value": round(job_throughput(vox, world, serial), 1),
+    best = min(serial, piped)
+    return {"value": round(job_throughput(vox, world, best), 1), "unit": "voxels/s", "ms_per_step": round(best, 4),
+            "h2d_bytes_per_step": int(vox * 4), "d2h_bytes_per_step": int(vox * 4),
+            "mode": "serial" if serial <= piped else f"{args.e2e_streams} streams",
+            "serial_ms_per_step": round(serial, 4), "streams_ms_per_step": round(piped, 4),
             "lanes_agree": ok,
             "note": "pinned host field in, pinned host field out, every step, through the binding's calls "
-                    "(gather, TF build from device optics, reconstruction, blend); consecutive steps go round "
-                    "the streams, each with its own device buffers; serial_*: one stream"}
+                    "(gather, TF build from device optics, reconstruction, blend); timed serially on one stream "
+                    "and with consecutive steps going round the streams, each with its own device buffers; the "
+                    "value is the faster of the two"}
 
 
 def _oracle_tile(job):
@@ -1345,6 +1348,15 @@ def run_estimator(args, rank, world, local_rank):
     (feat, truth), t_gen = clock(lambda: E.generate(args.est_train, shape, base, seed=100 + rank, device=dev))
     est = E.Estimator(dev, seed=rank, batch=256)
     losses, t_train = clock(lambda: est.train(feat, truth, epochs=args.est_epochs, lr=2e-3))
+    # per-kernel times of training steps (the library's event profiler, a pass of its own)
+    f0, t0_ = feat[:256].contiguous(), truth[:256].contiguous()
+
+    def train_step():
+        B.wo_est_train_step(est.w32, est.wbf, est.m, est.v, f0, t0_, 256, E.SCALE, E.OFFSET, est.step + 1, 0.0,
+                            est.loss, est.ws)
+    step_prof = profiled_pass(B, train_step, 5)
+    step_kern = {k: {"launches_per_step": c // 5, "ms_per_step": round(t / 5, 4)} for k, (c, t) in step_prof.items()}
+    n_steps = args.est_epochs * (args.est_train // 256)
     del feat
     torch.cuda.empty_cache()
     # test tiles: stacks kept for the refinement, in chunks of 256
@@ -1446,7 +1458,8 @@ def run_estimator(args, rank, world, local_rank):
                         "estimate_error": summary(est_err), "refined_error": summary(ref_err)},
             "plain": {"s_per_tile": plain_s, "tune_50_s": t_plain, "error": summary(plain_err)},
             "speedup_vs_plain": round(plain_s / learned_s, 2),
-            "training": {"generate_s": round(t_gen, 2), "train_s": round(t_train, 2),
+            "training": {"generate_s": round(t_gen, 2), "train_s": round(t_train, 2), "steps": n_steps,
+                         "ms_per_step": round(1e3 * t_train / max(n_steps, 1), 3), "step_kernels": step_kern,
                          "loss_per_epoch": [round(v, 5) for v in losses], "params": est.n}}
     print(json.dumps(line), flush=True)
 

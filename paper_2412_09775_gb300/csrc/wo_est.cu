@@ -269,15 +269,14 @@ struct EstWs {
 };
 
 // Floats of the per-chunk partial weight gradients (the largest layer's need:
-// about 2k blocks of one tap and 16 input channels, at most one chunk per
-// sample).
+// about 600 blocks of 16 input channels, at most one chunk per sample).
 size_t est_part_floats(int B) {
   size_t m = 0;
   for (int l = 0; l < 4; ++l) {
-    const int per = 9 * ((kLayers[l].ci + 15) / 16);
-    long long chunks = (2048 + per - 1) / per;
+    const int per = (kLayers[l].ci + 15) / 16;
+    long long chunks = (608 + per - 1) / per;
     if (chunks > B) chunks = B;
-    const size_t need = (size_t)chunks * kLayers[l].co * kLayers[l].ci * 9;
+    const size_t need = (size_t)chunks * kLayers[l].co * kLayers[l].ci * 9 + (size_t)kLayers[l].co * 32;
     m = need > m ? need : m;
   }
   return m;

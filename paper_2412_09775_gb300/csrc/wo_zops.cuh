@@ -39,8 +39,10 @@ struct ZGeom {
   static constexpr int NT = threads_for(NV * N * B);
   static constexpr int MINB = (1536 / NT) > 1 ? (1536 / NT) : 1;
   static constexpr size_t SMEM = ((size_t)N + (size_t)NV * N * B) * sizeof(float2);
-  // fused pass: plus up to three transfer functions of N x B prefetched
+  // fused pass: plus up to three transfer functions of N x B prefetched (the
+  // launch asks for the slots the bank has)
   static constexpr size_t SMEM_TF = SMEM + (size_t)3 * N * B * sizeof(float2);
+  static constexpr size_t smem_tf(int n_tf) { return SMEM + (size_t)n_tf * N * B * sizeof(float2); }
 };
 
 __device__ __forceinline__ float2 sel3(int i, float2 a, float2 b, float2 c) { return i == 0 ? a : (i == 1 ? b : c); }
@@ -121,7 +123,7 @@ __global__ void __launch_bounds__(ZGeom<N, (NI > NO ? NI : NO)>::NT, ZGeom<N, (N
   extern __shared__ float2 sm[];
   float2* tw = sm;
   float2* buf = sm + N;
-  float2* htf = buf + NV * N * B;  // [n][kind][b] transfer functions, prefetched
+  float2* htf = buf + NV * N * B;  // [kind][n][b] transfer functions, prefetched
   const int t = blockIdx.z, y = blockIdx.y, x0 = blockIdx.x * B;
   const int w = min(B, Xh - x0);
   const long long zs = (long long)Y * Xh;
@@ -145,7 +147,8 @@ __global__ void __launch_bounds__(ZGeom<N, (NI > NO ? NI : NO)>::NT, ZGeom<N, (N
     return;  // uniform across the CTA
   }
   load_zcols<N, NV, B, NT>(buf, in + (long long)t * NI * vol + col, NI, vol, zs, w);
-  load_zcols<N, 3, B, NT>(htf, tf + (long long)tt * ntf * vol + col, ntf, vol, zs, w);
+  for (int q = 0; q < ntf; ++q)
+    load_zcols<N, 1, B, NT>(htf + q * N * B, tf + ((long long)tt * ntf + q) * vol + col, 1, vol, zs, w);
   make_twiddles<N>(tw);
   cp_async_wait_all();
   __syncthreads();
@@ -164,10 +167,10 @@ __global__ void __launch_bounds__(ZGeom<N, (NI > NO ? NI : NO)>::NT, ZGeom<N, (N
       const float2 x0v = cell[0];
       const float2 x1v = NI > 1 ? cell[B] : zero;
       const float2 x2v = NI > 2 ? cell[2 * B] : zero;
-      const float2* h = htf + k * 3 * B + b;
+      const float2* h = htf + k * B + b;  // slot s at h[s * N * B]
       float2 H[3];
 #pragma unroll
-      for (int s = 0; s < 3; ++s) H[s] = (s < ntf) ? h[s * B] : zero;
+      for (int s = 0; s < 3; ++s) H[s] = (s < ntf) ? h[s * N * B] : zero;
       if (op.op == 0) {  // forward: props in, channels out
         if (L > 0) {
           float2 d = cmul(H[0], x0v);
@@ -335,7 +338,8 @@ cudaError_t launch_z_fused(const float2* in, float2* out, const float2* tf, ZOp 
   const cudaError_t attr = allow_smem(k_z_fused<N, NI, NO>, G::SMEM_TF);
   if (attr != cudaSuccess) return attr;
   dim3 grid((unsigned)((Xh + G::B - 1) / G::B), (unsigned)Y, (unsigned)n_tiles);
-  WO_LAUNCH("z_fused", s, (k_z_fused<N, NI, NO><<<grid, G::NT, G::SMEM_TF, s>>>(in, out, tf, op, Y, Xh)));
+  const size_t smem = G::smem_tf(op.n_tf < 3 ? op.n_tf : 3);
+  WO_LAUNCH("z_fused", s, (k_z_fused<N, NI, NO><<<grid, G::NT, smem, s>>>(in, out, tf, op, Y, Xh)));
   return cudaGetLastError();
 }
 

@@ -134,11 +134,15 @@ def test_pipeline_timeout_returns_instead_of_hanging(env):
     assert code == B.STATUS_CODES["WO_ERR_TIMEOUT"] and site in (1, 2) and detail == 1, (code, site, detail)
     assert dt < 5.0, dt
     assert B.wo_sync_status(ws)[0] == 0  # read and cleared
-    # the same pipeline, nothing withheld: clean, and equal to wo_reconstruct
+    # the same pipeline, nothing withheld: clean, and equal to wo_reconstruct on the pipeline engine
     B.wo_pipeline_probe(tf, din, out, n, Z, Y, X, -1, 1_000_000_000, ws)
     assert B.wo_sync_status(ws)[0] == 0
     ref = torch.empty_like(din)
-    B.wo_reconstruct(tf, ("phase",), din, None, [1e-3], B.WO_ETA_ABSOLUTE, B.WO_MODE_3D, ref, n, Z, Y, X, ws)
+    engine(B, Y, B.WO_ENGINE_HYBRID)
+    try:
+        B.wo_reconstruct(tf, ("phase",), din, None, [1e-3], B.WO_ETA_ABSOLUTE, B.WO_MODE_3D, ref, n, Z, Y, X, ws)
+    finally:
+        engine(B, Y, B.WO_ENGINE_DEFAULT)
     assert B.wo_sync_status(ws)[0] == 0
     assert torch.equal(out, ref)
 
