@@ -98,6 +98,10 @@ struct ZOp {
 // Spectra laid out [tile][vol][Z][Y][Xh].
 cudaError_t z_fused(int Z, const float2* in, float2* out, const float2* tf, ZOp op, int n_tiles,
                     int Y, int Xh, cudaStream_t s);
+// The one-volume, one-TF case with register-resident z transforms (wo_zreg.cu).
+bool z_reg_supported(int Z, const ZOp& op);
+cudaError_t z_fused_reg(int Z, const float2* in, float2* out, const float2* tf, ZOp op, int n_tiles, int Y, int Xh,
+                        cudaStream_t s);
 // 2D reconstruction: FFT_z, per-transverse-frequency solve summed over k_z.
 // out: [tile][P][Y][Xh].
 cudaError_t z_solve2d(int Z, const float2* in, float2* out, const float2* tf, ZOp op, int n_tiles,
@@ -178,6 +182,9 @@ struct TfArgs {
 cudaError_t tf_pupil_record(const TfArgs& a, cudaStream_t s);
 int record_rows(int Y, int n_tiles);  // rows per pupil-record block
 cudaError_t tf_arms(const TfArgs& a, cudaStream_t s);
+// Arm pass with register-resident y transforms (wo_armsreg.cu): banks without derivatives, Y <= 192.
+bool arms_reg_supported(int Y, const TfArgs& a);
+cudaError_t tf_arms_reg(const TfArgs& a, cudaStream_t s);
 cudaError_t tf_psf_rows(const TfArgs& a, cudaStream_t s);
 // Hybrid column engine (wo_colhyb.cu) and the schedule table (wo_sched.cu).
 bool cols_hyb_supported(int N);

@@ -36,6 +36,7 @@
 
 #include "wo_fft.cuh"
 #include "wo_internal.h"
+#include "wo_zops.cuh"
 
 namespace wo {
 
@@ -238,6 +239,8 @@ __device__ __forceinline__ void item_B(const PipeArgs& a, const PipeSmem& m, int
     const int kz = e / Xh, x = e - kz * Xh;
     float2 d = D[e];
     if (a.zero_dc && kz == 0 && y == 0 && x == 0) d = make_float2(0.f, 0.f);
+    // columns outside the support disk hold only the TFs' rounding noise: zero out
+    if (outside_support(st, y, Y, x, 2 * H)) d = make_float2(0.f, 0.f);
     const float2 h = Hb[e];
     const float den = lam + cabs2(h);
     D[e] = cscale(cmulc(h, d), den > 0.f ? 1.0f / den : 0.f);  // zero TF and eta: minimum norm

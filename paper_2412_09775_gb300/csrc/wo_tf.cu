@@ -663,6 +663,7 @@ static cudaError_t launch_arms(const TfArgs& a, cudaStream_t s) {
 }
 
 cudaError_t tf_arms(const TfArgs& a, cudaStream_t s) {
+  if (arms_reg_supported(a.Y, a)) return tf_arms_reg(a, s);
   switch (a.Y) {
 #define WO_CASE(n) \
   case n:          \

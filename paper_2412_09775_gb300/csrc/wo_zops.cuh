@@ -103,10 +103,12 @@ __device__ __forceinline__ void zero_zcols(float2* __restrict__ dst, int nv, lon
   }
 }
 
-// True when the strip of columns k_x >= x0 of row y lies outside the tile's
-// TF support disk (k_y/Y)^2 + (k_x/X)^2 <= r^2 (r: statistics word 5, cycles
-// per pixel).  The nearest column of the strip is x0 (k_x >= 0 in the half
-// spectrum), so the whole strip is outside when x0 is.
+// True when column k_x = x0 of row y lies outside the tile's TF support disk
+// (k_y/Y)^2 + (k_x/X)^2 <= r^2 (r: statistics word 5, cycles per pixel);
+// there the TFs hold only the rounding noise of the PSF-row transforms, and
+// every operator's output is set to zero.  The nearest column of a strip
+// k_x >= x0 is x0 (k_x >= 0 in the half spectrum), so the whole strip is
+// outside when x0 is.
 __device__ __forceinline__ bool outside_support(const float* stats, int y, int Y, int x0, int X) {
   const float r = stats[5];
   const float fy = (float)(y < (Y + 1) / 2 ? y : y - Y) / (float)Y, fx = (float)x0 / (float)X;
@@ -163,7 +165,8 @@ __global__ void __launch_bounds__(ZGeom<N, (NI > NO ? NI : NO)>::NT, ZGeom<N, (N
     const int k = e / B, b = e % B;  // B is a power of two: shifts
     float2* cell = buf + k * NV * B + b;  // slot v at cell[v * B]
     float2 y0 = zero, y1 = zero, y2 = zero;
-    if (b < w) {
+    // columns outside the support disk hold only the TFs' rounding noise: zero out
+    if (b < w && !outside_support(st, y, Y, x0 + b, 2 * (Xh - 1))) {
       const float2 x0v = cell[0];
       const float2 x1v = NI > 1 ? cell[B] : zero;
       const float2 x2v = NI > 2 ? cell[2 * B] : zero;
@@ -264,7 +267,8 @@ __global__ void __launch_bounds__(ZGeom<N, NI>::NT, ZGeom<N, NI>::MINB)
   float acc[NACC];
 #pragma unroll
   for (int i = 0; i < NACC; ++i) acc[i] = 0.f;
-  if (b < w) {
+  // columns outside the support disk hold only the TFs' rounding noise: zero out
+  if (b < w && !outside_support(op.stats + (long long)tt * 8, y, Y, x0 + b, 2 * (Xh - 1))) {
     for (int k = kk; k < N; k += KK) {
       const float2* cell = buf + k * NI * B + b;
       const bool dc = op.zero_dc && k == 0 && y == 0 && (x0 + b) == 0;

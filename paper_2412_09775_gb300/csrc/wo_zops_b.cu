@@ -12,6 +12,7 @@ cudaError_t z_fused_grow(int ni, int no, int Z, const float2* in, float2* out, c
 
 cudaError_t z_fused(int Z, const float2* in, float2* out, const float2* tf, ZOp op, int nt, int Y, int Xh,
                     cudaStream_t s) {
+  if (z_reg_supported(Z, op)) return z_fused_reg(Z, in, out, tf, op, nt, Y, Xh, s);
   if (op.n_in == 2 && op.n_out == 1) {
     switch (Z) {
       WO_FOR_EACH_SIZE(WO_Z_CASE_21)
