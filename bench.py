@@ -56,20 +56,25 @@ WORKLOAD = "widefield 96x512x512: TF build (phase+absorption+fluorescence) + 3D 
 CPU_SAMPLE = (96, 256, 256)
 
 # Last ncu capture of DRAM traffic per launch (bytes) of a workload's dominant
-# kernel, keyed by (workload, kernel family), with the digest of the kernel's
-# sources at capture time (reported as null once a source changes).
-# field / tf_arms: 18.9 MB read + 844.6 MB written per launch on 64 tiles of
-# 48x192x192 (an 8x8-tile field; the full 256-tile workload is too large for a
-# full capture), scaled by 4 to the 256 tiles of a launch of the bench's field.
-NCU_TRAFFIC = {("field", "tf_arms"): {"bytes": 4 * (18939136 + 844591616), "digest": "f6f532e1fad69ba6"}}
+# kernels, keyed by (workload, kernel family), with the digest of the kernel's
+# sources at capture time (reported as null once a source changes).  Field
+# entries: read + written bytes per launch on 64 tiles of 48x192x192 (an
+# 8x8-tile field; the full 256-tile workload is too large for a full
+# capture), scaled by 4 to the 256 tiles of a launch of the bench's field
+# (the traffic grows with the tiles).
+NCU_TRAFFIC = {
+    ("field", "tf_arms"): {"bytes": 4 * (54647552 + 773743616), "digest": "e402c4e07b584d20"},
+    ("field", "tf_psf_rows"): {"bytes": 4 * (906212608 + 425125632), "digest": "4c82bab03e05b259"},
+}
 
 
 def kernel_digest(name: str) -> str:
     """Digest of the sources a kernel family is built from."""
     tf = ["wo_tf.cu", "wo_tf.cuh"]
-    src = {"z_fused": ["wo_zops.cuh", "wo_zops_a.cu", "wo_zops_b.cu"],
+    src = {"z_fused": ["wo_zops.cuh", "wo_zops_a.cu", "wo_zops_b.cu", "wo_zreg.cu", "wo_regfft.cuh"],
            "z_solve2d": ["wo_zops.cuh", "wo_zops_a.cu"], "rows_r2c": ["wo_rows.cu"], "rows_c2r": ["wo_rows.cu"],
-           "y_fwd": ["wo_cols.cu"], "y_inv": ["wo_cols.cu"], "tf_ypass": ["wo_cols.cu"], "tf_arms": tf,
+           "xy_fwd": ["wo_xy.cu", "wo_rowsplit.cuh", "wo_regfft.cuh"], "xy_inv": ["wo_xy.cu", "wo_rowsplit.cuh", "wo_regfft.cuh"],
+           "y_fwd": ["wo_cols.cu"], "y_inv": ["wo_cols.cu"], "tf_ypass": ["wo_cols.cu"], "tf_arms": tf + ["wo_armsreg.cu", "wo_regfft.cuh"],
            # the register-resident row kernel (rows of 32..512 points; wo_tf.cu holds only the
            # shared-memory fallback for other lengths)
            "tf_psf_rows": ["wo_psf.cu", "wo_regfft.cuh", "wo_tf.cuh", "wo_internal.h"],
@@ -148,6 +153,8 @@ def algorithmic_bytes(shape, kinds, o):
         "tf_zpass": 2 * nk * tf_cols,
         "rows_r2c": C * (real + half),
         "y_fwd": 2 * C * half,
+        "xy_fwd": C * (real + half),  # the fused x-y kernels (square planes)
+        "xy_inv": P * (half + real),
         "z_fused": (C + nk) * inside + P * half,
         "y_inv": 2 * P * half,
         "rows_c2r": P * (half + real),
@@ -157,6 +164,11 @@ def algorithmic_bytes(shape, kinds, o):
 def engines_recon(Y):
     from paper_2412_09775_gb300 import binding as B
     return {1: "five passes", 2: "tile pipeline"}.get(B.wo_schedule_get(B.WO_PASS_RECON, Y), "?")
+
+
+def engines_xy(n):
+    from paper_2412_09775_gb300 import binding as B
+    return {1: "x and y passes", 2: "fused x-y kernels"}.get(B.wo_schedule_get(B.WO_PASS_XY, n), "?")
 
 
 def pin_rows_engine(args, B, n):
@@ -700,7 +712,7 @@ def field_algorithmic_bytes(o_list, Z, E, field_vox):
     Xh = E // 2 + 1
     real, half = Z * E * E * 4, Z * E * Xh * 8
     out = {k: 0 for k in ("tf_pupil_record", "tf_arms", "tf_psf_rows", "tf_ypass", "tf_zpass", "rows_r2c", "y_fwd",
-                          "z_fused", "y_inv", "rows_c2r")}
+                          "xy_fwd", "z_fused", "y_inv", "rows_c2r", "xy_inv")}
     for o in o_list:
         arms = 2 * Z * E * band_columns(o, E) * 8
         inside = Z * support_columns(o, ("phase",), E, E) * 8
@@ -711,9 +723,11 @@ def field_algorithmic_bytes(o_list, Z, E, field_vox):
         out["tf_zpass"] += 2 * half
         out["rows_r2c"] += real + half
         out["y_fwd"] += 2 * half
+        out["xy_fwd"] += real + half
         out["z_fused"] += 2 * inside + half
         out["y_inv"] += 2 * half
         out["rows_c2r"] += half + real
+        out["xy_inv"] += half + real
     tiles = len(o_list) * Z * E * E * 4
     # the tile pipeline: every tile's data in, its phase TF in, its result out
     # (the spectra between its items stay in L2)
@@ -831,26 +845,34 @@ def field_leg(args, rank, world, local_rank):
     # per-kernel times from eager profiled steps (the events do not enter a graph)
     with torch.cuda.stream(s):
         prof = profiled_pass(B, step, args.steps)
-    # the same step with the reconstruction on the persistent tile pipeline
-    # instead of the five passes (context for the engine choice)
-    B.wo_schedule_set(B.WO_PASS_RECON, E, B.WO_ENGINE_HYBRID)
-    g5 = torch.cuda.CUDAGraph()
-    with torch.cuda.stream(s):
-        step()
-    torch.cuda.synchronize()
-    with torch.cuda.graph(g5, stream=s):
-        step()
-    B.wo_schedule_set(B.WO_PASS_RECON, E, B.WO_ENGINE_DEFAULT)
-    for _ in range(args.warmup):
-        g5.replay()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
-        g5.replay()
-    e1.record()
-    torch.cuda.synchronize()
-    passes_ms = e0.elapsed_time(e1) / args.steps
-    del g5
+    def alt_step_ms(pass_, engine):
+        """The step timed the same way with one schedule entry pinned (context
+        for the engine choices); the entry is restored afterwards."""
+        saved = B.wo_schedule_get(pass_, E)
+        B.wo_schedule_set(pass_, E, engine)
+        g5 = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            step()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g5, stream=s):
+            step()
+        B.wo_schedule_set(pass_, E, saved)
+        for _ in range(args.warmup):
+            g5.replay()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            g5.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        del g5
+        return e0.elapsed_time(e1) / args.steps
+
+    # the reconstruction on the persistent tile pipeline instead of the five
+    # passes, and the x-y transforms as separate passes instead of fused
+    pipe_ms = alt_step_ms(B.WO_PASS_RECON, B.WO_ENGINE_HYBRID)
+    other_xy = B.WO_ENGINE_SMEM if B.wo_schedule_get(B.WO_PASS_XY, E) == B.WO_ENGINE_HYBRID else B.WO_ENGINE_HYBRID
+    xy_ms = alt_step_ms(B.WO_PASS_XY, other_xy)
     code = B.wo_sync_status(ws)
     vox = float(field.numel())
     kern = kernel_table(prof, field_algorithmic_bytes(o_list, Z, E, vox), "launches")
@@ -871,7 +893,8 @@ def field_leg(args, rank, world, local_rank):
         "roofline": roofline_of(kern, prof, "field" if (ty, tx) == (16, 16) else None), "kernels": kern,
         "gpu_launches": int(per_step_launches * args.steps), "clocks": clk,
         "e2e": e2e,
-        "recon_engine": {"engine": engines_recon(E), "step_ms_with_tile_pipeline": round(passes_ms, 4),
+        "recon_engine": {"engine": engines_recon(E), "step_ms_with_tile_pipeline": round(pipe_ms, 4),
+                         "xy": engines_xy(E), "step_ms_with_other_xy_engine": round(xy_ms, 4),
                          "device_status": list(code)},
     }
     if not args.no_cpu_baseline:
@@ -1070,7 +1093,8 @@ def small_stack_leg(args, rank, world, local_rank):
     real = Z * Y * X * 4
     algo = {"tile_pipeline": nb * 2 * real + half,
             "rows_r2c": nb * (real + half), "y_fwd": 2 * nb * half, "z_fused": nb * (inside + half),
-            "y_inv": 2 * nb * half, "rows_c2r": nb * (half + real)}
+            "y_inv": 2 * nb * half, "rows_c2r": nb * (half + real), "xy_fwd": nb * (real + half),
+            "xy_inv": nb * (half + real)}
     kern = kernel_table(prof, algo, "launches")
     peak, _ = peaks()
     compulsory = 8.0 * vox

@@ -537,6 +537,18 @@ enum { WO_PASS_ROWS = 1 };
  * WO_ERR_TIMEOUT in the workspace's status block (wo_sync_status) and stops.
  * Results agree with the passes to float32 rounding. */
 enum { WO_PASS_RECON = 2 };
+/* WO_PASS_XY: the x and y transforms of a plane (the first two and last two
+ * passes of every operator, and of wo_spectrum and the gradient), keyed by
+ * n = Y for square planes X = Y: WO_ENGINE_SMEM (the x pass and the y pass,
+ * each a kernel over the batch) or WO_ENGINE_HYBRID (one kernel per
+ * direction: a cluster of two CTAs per plane transforms its rows along x,
+ * exchanges the bins through distributed shared memory and transforms its
+ * columns along y, so the intermediate spectrum never goes to memory;
+ * n = 64, 128, 192).  The default is WO_ENGINE_SMEM: the fused kernels hold
+ * a plane tile of about 109 KB per CTA (192 x 192), two CTAs per SM, and
+ * measured slower on the 256-tile field; wo_autotune picks them where they
+ * are faster.  Results agree to float32 rounding. */
+enum { WO_PASS_XY = 3 };
 enum { WO_ENGINE_DEFAULT = 0, WO_ENGINE_SMEM = 1, WO_ENGINE_HYBRID = 2 };
 wo_status wo_schedule_set(int pass, int n, int engine);
 int wo_schedule_get(int pass, int n);

@@ -25,7 +25,7 @@ WO_TF_PHASE_GRAD = 64
 WO_MODE_3D, WO_MODE_2D = 0, 1
 WO_ETA_RELATIVE, WO_ETA_ABSOLUTE = 0, 1
 WO_LOSS_DATA, WO_LOSS_MIDBAND = 0, 1
-WO_PASS_COLS, WO_PASS_ROWS, WO_PASS_RECON = 0, 1, 2
+WO_PASS_COLS, WO_PASS_ROWS, WO_PASS_RECON, WO_PASS_XY = 0, 1, 2, 3
 WO_ENGINE_DEFAULT, WO_ENGINE_SMEM, WO_ENGINE_HYBRID = 0, 1, 2
 WO_MAX_ZERNIKE = 36
 WO_PAD_ZERO, WO_PAD_MIRROR, WO_PAD_EDGE = 0, 1, 2

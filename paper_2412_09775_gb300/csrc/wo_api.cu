@@ -557,22 +557,19 @@ static wo_status run_op(int op, const void* d_tf, unsigned kinds, const float* d
     return cuda_status(tile_pipeline(p, cs));
   }
   const long long in_rows = (long long)n_tiles * n_in * Z * Y;
-  WO_TRY(rows_r2c(H, d_in, specA, in_rows, bg_in, cs));
-  WO_TRY(cols_c2c(Y, false, specA, Xh, (long long)Y * Xh, Xh, (long long)n_tiles * n_in * Z, cs, "y_fwd"));
+  WO_TRY(plane_xy_fwd(X, Y, d_in, specA, in_rows / Y, bg_in, cs));
   if (op == 2 && mode == WO_MODE_2D) {
     WO_TRY(z_solve2d(Z, specA, specB, tf, zo, n_tiles, Y, Xh, cs));
-    WO_TRY(cols_c2c(Y, true, specB, Xh, (long long)Y * Xh, Xh, (long long)n_tiles * s.P, cs, "y_inv"));
     const float scale = 2.0f / ((float)X * (float)Y);
     RowBg none{};
     none.rows_per_block = Y;
     none.nchan = 1;
-    WO_TRY(rows_c2r(H, specB, d_out, (long long)n_tiles * s.P * Y, scale, none, cs));
+    WO_TRY(plane_xy_inv(X, Y, specB, d_out, (long long)n_tiles * s.P, scale, none, cs));
     return WO_OK;
   }
   WO_TRY(z_fused(Z, specA, specB, tf, zo, n_tiles, Y, Xh, cs));
-  WO_TRY(cols_c2c(Y, true, specB, Xh, (long long)Y * Xh, Xh, (long long)n_tiles * n_out * Z, cs, "y_inv"));
   const float scale = (float)(2.0 / ((double)X * (double)Y * (double)Z));
-  WO_TRY(rows_c2r(H, specB, d_out, (long long)n_tiles * n_out * Z * Y, scale, bg_out, cs));
+  WO_TRY(plane_xy_inv(X, Y, specB, d_out, (long long)n_tiles * n_out * Z, scale, bg_out, cs));
   return WO_OK;
 }
 
@@ -681,8 +678,7 @@ wo_status wo_spectrum(const float* d_data, const float* h_background, int mode, 
   } else {
     bg.mode = 2;  // a constant per stack only moves the DC bins, fixed below
   }
-  WO_TRY(rows_r2c(H, d_data, spec, (long long)n_tiles * Z * Y, bg, cs));
-  WO_TRY(cols_c2c(Y, false, spec, Xh, plane, Xh, (long long)n_tiles * Z, cs, "y_fwd"));
+  WO_TRY(plane_xy_fwd(X, Y, d_data, spec, (long long)n_tiles * Z, bg, cs));
   if (mode == WO_MODE_3D) {
     WO_TRY(cols_c2c(Z, false, spec, plane, (long long)Z * plane, (int)plane, n_tiles, cs, "z_fwd"));
     if (!h_background) WO_TRY(zero_dc(spec, n_tiles, (long long)Z * plane, cs));
@@ -737,8 +733,7 @@ wo_status wo_reconstruct_vjp(const void* d_tf, unsigned kinds, const void* d_spe
   RowBg none{};
   none.rows_per_block = (long long)gz * Y;
   none.nchan = 1;
-  WO_TRY(rows_r2c(H, d_gout, G, (long long)n_tiles * gz * Y, none, cs));
-  WO_TRY(cols_c2c(Y, false, G, Xh, plane, Xh, (long long)n_tiles * gz, cs, "y_fwd"));
+  WO_TRY(plane_xy_fwd(X, Y, d_gout, G, (long long)n_tiles * gz, none, cs));
   if (mode == WO_MODE_3D) WO_TRY(cols_c2c(Z, false, G, plane, (long long)Z * plane, (int)plane, n_tiles, cs, "z_fwd"));
   return cuda_status(vjp_reduce((const float2*)d_tf, (const float2*)d_spec, G, n_tiles, Z, Y, X, eta,
                                 mode == WO_MODE_3D ? 1 : 0, np, partials, d_grad, cs));
@@ -803,20 +798,17 @@ wo_status wo_reconstruct_fused(const void* d_tf, int n_channels, const float* d_
   if (h_background)
     for (int c = 0; c < C; ++c) op.bg_dc[c] = (float)(nvox * (double)h_background[c]);
   const long long plane = (long long)Y * Xh;
-  WO_TRY(rows_r2c(H, d_data, A, (long long)n_tiles * C * Z * Y, bg, cs));
-  WO_TRY(cols_c2c(Y, false, A, Xh, plane, Xh, (long long)n_tiles * C * Z, cs, "y_fwd"));
+  WO_TRY(plane_xy_fwd(X, Y, d_data, A, (long long)n_tiles * C * Z, bg, cs));
   if (op.eta_relative) WO_TRY(fuse_stats((const float2*)d_tf, n_tiles, C, Z, Y, Xh, stats, cs));
   WO_TRY(z_fuse(Z, A, Bv, (const float2*)d_tf, op, n_tiles, Y, Xh, cs));
   RowBg none{};
   none.nchan = 1;
   if (mode == WO_MODE_3D) {
-    WO_TRY(cols_c2c(Y, true, Bv, Xh, plane, Xh, (long long)n_tiles * Z, cs, "y_inv"));
     none.rows_per_block = (long long)Z * Y;
-    WO_TRY(rows_c2r(H, Bv, d_f, (long long)n_tiles * Z * Y, (float)(2.0 / nvox), none, cs));
+    WO_TRY(plane_xy_inv(X, Y, Bv, d_f, (long long)n_tiles * Z, (float)(2.0 / nvox), none, cs));
   } else {
-    WO_TRY(cols_c2c(Y, true, Bv, Xh, plane, Xh, (long long)n_tiles, cs, "y_inv"));
     none.rows_per_block = Y;
-    WO_TRY(rows_c2r(H, Bv, d_f, (long long)n_tiles * Y, 2.0f / ((float)X * (float)Y), none, cs));
+    WO_TRY(plane_xy_inv(X, Y, Bv, d_f, (long long)n_tiles, 2.0f / ((float)X * (float)Y), none, cs));
   }
   return WO_OK;
 }

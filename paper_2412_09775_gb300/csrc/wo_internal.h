@@ -192,6 +192,16 @@ cudaError_t cols_c2c_hyb(int N, bool inverse, float2* data, long long col_stride
                          long long nplanes, cudaStream_t s, const char* name, long long groups,
                          long long group_stride);
 int cols_engine(int n);  // WO_ENGINE_SMEM or WO_ENGINE_HYBRID
+// The x and y transforms of a plane in one kernel per direction (wo_xy.cu),
+// and the helpers that pick it or the two passes by the schedule table.
+bool xy_supported(int X, int Y);
+int xy_engine(int X, int Y);  // WO_ENGINE_HYBRID: the fused kernels
+cudaError_t xy_fwd(int X, int Y, const float* in, float2* out, long long nplanes, RowBg bg, cudaStream_t s);
+cudaError_t xy_inv(int X, int Y, const float2* in, float* out, long long nplanes, float scale, RowBg bg,
+                   cudaStream_t s);
+cudaError_t plane_xy_fwd(int X, int Y, const float* in, float2* out, long long nplanes, RowBg bg, cudaStream_t s);
+cudaError_t plane_xy_inv(int X, int Y, float2* in, float* out, long long nplanes, float scale, RowBg bg,
+                         cudaStream_t s);
 int rows_engine(int n);  // engine of the x passes for n complex points (wo_rowsreg.cu: HYBRID)
 bool rows_reg_supported(int N);
 cudaError_t rows_r2c_reg(int N, const float* in, float2* out, long long nrows, RowBg bg, cudaStream_t s);

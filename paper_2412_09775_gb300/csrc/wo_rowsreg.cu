@@ -17,6 +17,7 @@
 #include "wo_fft.cuh"
 #include "wo_internal.h"
 #include "wo_regfft.cuh"
+#include "wo_rowsplit.cuh"
 
 namespace wo {
 
@@ -31,23 +32,6 @@ struct RowRegGeom {
   static constexpr size_t SMEM = ((size_t)P::TW + 2 * (size_t)N + (size_t)RPC * P::SLICE) * sizeof(float2);
 };
 
-// Background constant of a row (see RowBg): mode 1 the channel's value, mode 2
-// the first sample of the row's (tile, channel) block.
-__device__ __forceinline__ float row_constant(const float* in, long long row, long long n2, const RowBg& bg) {
-  const long long grow = bg.row_offset + row;
-  if (bg.mode == 1) return bg.v[(grow / bg.rows_per_block) % bg.nchan];
-  if (bg.mode == 2) return __ldg(in + ((grow / bg.rows_per_block) * bg.rows_per_block - bg.row_offset) * n2);
-  return 0.f;
-}
-
-// Lane layout shared by both kernels: the partner lane owns N - k, and the
-// register it sends for our register m is mirror(m) (lane 0: point T m pairs
-// with T ((E - m) mod E); lane t > 0: t + T m pairs with (T - t) + T (E-1-m)).
-template <int E>
-__device__ __forceinline__ float2 mirror_reg(const float2 (&v)[E], int m, bool lane0) {
-  return lane0 ? v[(E - m) % E] : v[E - 1 - m];
-}
-
 template <class P>
 __global__ void __launch_bounds__(kRowThreads) k_rows_r2c_reg(const float* __restrict__ in, float2* __restrict__ out,
                                                                long long nrows, RowBg bg) {
@@ -57,8 +41,6 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_r2c_reg(const float* __res
   float2* tw = sm;                  // P's twiddles
   float2* tw2 = sm + P::TW;         // exp(-2 pi i m / 2N)
   const int t = threadIdx.x % T, r = threadIdx.x / T;
-  const int lane = threadIdx.x & 31;
-  const int partner = (lane - t) + (T - t) % T;
   float2* S = sm + P::TW + 2 * N + r * P::SLICE;
   const long long row = (long long)blockIdx.x * RPC + r;
   const bool live0 = row < nrows;
@@ -79,16 +61,9 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_r2c_reg(const float* __res
   for (int m = 0; m < E; ++m) v[m] = make_float2(v[m].x - c, v[m].y - c);
   P::template fft<false>(v, tw, S, t);
   float2* o = out + rr * (N + 1);
-#pragma unroll
-  for (int m = 0; m < E; ++m) {
-    const float2 mv = mirror_reg<E>(v, m, t == 0);
-    const float2 zc = make_float2(__shfl_sync(0xffffffffu, mv.x, partner), -__shfl_sync(0xffffffffu, mv.y, partner));
-    const int k = t + T * m;
-    const float2 s = cadd(v[m], zc);
-    const float2 u = cmul(tw2[k], csub(v[m], zc));
-    if (live) o[k] = make_float2(0.5f * (s.x + u.y), 0.5f * (s.y - u.x));
-  }
-  if (live && t == 0) o[N] = make_float2(v[0].x - v[0].y, 0.f);
+  r2c_split<N, T, E>(v, tw2, t, [&](int k, float2 val) {
+    if (live) o[k] = val;
+  });
 }
 
 template <class P>
@@ -100,8 +75,6 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_c2r_reg(const float2* __re
   float2* tw = sm;
   float2* tw2 = sm + P::TW;
   const int t = threadIdx.x % T, r = threadIdx.x / T;
-  const int lane = threadIdx.x & 31;
-  const int partner = (lane - t) + (T - t) % T;
   float2* S = sm + P::TW + 2 * N + r * P::SLICE;
   const long long row = (long long)blockIdx.x * RPC + r;
   const bool live0 = row < nrows;
@@ -118,16 +91,7 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_c2r_reg(const float2* __re
   make_twiddles<2 * N>(tw2);
   __syncthreads();
   float2 v[E];
-#pragma unroll
-  for (int m = 0; m < E; ++m) {
-    const float2 mv = mirror_reg<E>(x, m, t == 0);
-    float2 xc = make_float2(__shfl_sync(0xffffffffu, mv.x, partner), -__shfl_sync(0xffffffffu, mv.y, partner));
-    if (t == 0 && m == 0) xc = make_float2(xn.x, -xn.y);
-    const int k = t + T * m;
-    const float2 a = make_float2(0.5f * (x[m].x + xc.x), 0.5f * (x[m].y + xc.y));
-    const float2 b = cmul(make_float2(0.5f * (x[m].x - xc.x), 0.5f * (x[m].y - xc.y)), cconj(tw2[k]));
-    v[m] = make_float2(a.x - b.y, a.y + b.x);
-  }
+  c2r_merge<T, E>(x, xn, tw2, t, v);
   P::template fft<true>(v, tw, S, t);
   if (!live) return;
   const float cst = bg.mode == 1 ? bg.v[((bg.row_offset + rr) / bg.rows_per_block) % bg.nchan] : 0.f;

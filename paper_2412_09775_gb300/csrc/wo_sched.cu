@@ -24,7 +24,21 @@ constexpr int kMaxLen = 2048;
 std::atomic<int> g_cols_engine[kMaxLen + 1];  // 0: default
 std::atomic<int> g_rows_engine[kMaxLen + 1];  // 0: default
 std::atomic<int> g_recon_engine[kMaxLen + 1];  // 0: default, keyed by Y
+std::atomic<int> g_xy_engine[kMaxLen + 1];     // 0: default, keyed by Y (X == Y)
 }  // namespace
+
+int xy_engine(int X, int Y) {
+  if (!xy_supported(X, Y)) return WO_ENGINE_SMEM;
+  const int e = g_xy_engine[Y].load(std::memory_order_relaxed);
+  if (e == WO_ENGINE_SMEM || e == WO_ENGINE_HYBRID) return e;
+  // default: the separate x and y passes.  The fused kernels hold a 109 KB
+  // plane tile per CTA, so an SM runs two CTAs of four warps and overlaps
+  // little of one CTA's copies with the other's transforms: 11.87 against
+  // 10.99 ms per step of the 256-tile field (k_xy_fwd 410 us and k_xy_inv
+  // 614 us per 64 tiles under ncu, 8 warps per SM); the autotuner keeps
+  // them where they measure faster
+  return WO_ENGINE_SMEM;
+}
 
 int recon_engine(int Z, int Y, int X) {
   if (!pipe_supported(Z, Y, X)) return WO_ENGINE_SMEM;
@@ -121,6 +135,19 @@ static int tune_cols(int n, int ncols, long long planes, float2* scratch, cudaSt
   });
 }
 
+// The x and y transforms of `planes` planes of Y x X (X == Y): the fused
+// kernels against the separate passes, forward and inverse per run.
+static int tune_xy(int X, long long planes, float2* scratch, cudaStream_t s) {
+  float* real = reinterpret_cast<float*>(scratch);
+  float2* half = scratch + (size_t)planes * X * X / 2;  // after the real planes
+  const RowBg none{};
+  return tune_entry(g_xy_engine[X], WO_ENGINE_SMEM, true, s, [&](int) {
+    cudaError_t e = plane_xy_fwd(X, X, real, half, planes, none, s);
+    if (e != cudaSuccess) return e;
+    return plane_xy_inv(X, X, half, real, planes, 1.0f, none, s);
+  });
+}
+
 // x passes of n complex points over `rows` rows: a real-to-half-spectrum
 // pass and its inverse per run, on two disjoint parts of the scratch buffer.
 static int tune_rows(int n, long long rows, float2* scratch, cudaStream_t s) {
@@ -141,12 +168,17 @@ using namespace wo;
 extern "C" {
 
 wo_status wo_schedule_set(int pass, int n, int engine) {
-  if (pass != WO_PASS_COLS && pass != WO_PASS_ROWS && pass != WO_PASS_RECON) return WO_ERR_ARG;
+  if (pass != WO_PASS_COLS && pass != WO_PASS_ROWS && pass != WO_PASS_RECON && pass != WO_PASS_XY) return WO_ERR_ARG;
   if (n < 1 || n > kMaxLen) return WO_ERR_ARG;
   if (engine != WO_ENGINE_DEFAULT && engine != WO_ENGINE_SMEM && engine != WO_ENGINE_HYBRID) return WO_ERR_ARG;
   if (pass == WO_PASS_RECON) {
     if (engine == WO_ENGINE_HYBRID && !recon_pipe_length(n)) return WO_ERR_UNSUPPORTED_SIZE;
     g_recon_engine[n].store(engine, std::memory_order_relaxed);
+    return WO_OK;
+  }
+  if (pass == WO_PASS_XY) {
+    if (engine == WO_ENGINE_HYBRID && !xy_supported(n, n)) return WO_ERR_UNSUPPORTED_SIZE;
+    g_xy_engine[n].store(engine, std::memory_order_relaxed);
     return WO_OK;
   }
   const bool hyb_ok = pass == WO_PASS_COLS ? cols_hyb_supported(n) : rows_reg_supported(n);
@@ -159,6 +191,7 @@ int wo_schedule_get(int pass, int n) {
   if (n < 1 || n > kMaxLen) return -1;
   if (pass == WO_PASS_COLS) return cols_engine(n);
   if (pass == WO_PASS_ROWS) return rows_engine(n);
+  if (pass == WO_PASS_XY) return xy_engine(n, n);
   if (pass == WO_PASS_RECON) {
     if (!recon_pipe_length(n)) return WO_ENGINE_SMEM;
     const int e = g_recon_engine[n].load(std::memory_order_relaxed);
@@ -191,6 +224,8 @@ wo_status wo_autotune(int n_tiles, int Z, int Y, int X, unsigned kinds, void* d_
   // x passes: the rows of the same volumes (2n real samples in, n+1 bins out
   // per row fit the volumes' half spectra twice over)
   if (rows_reg_supported(X / 2) && tune_rows(X / 2, vols * Z * Y, scratch, s) < 0) return WO_ERR_CUDA;
+  // fused x-y planes (the same volumes' planes, real and half spectrum side by side)
+  if (xy_supported(X, Y) && tune_xy(X, vols * Z, scratch, s) < 0) return WO_ERR_CUDA;
   return cudaStreamSynchronize(s) == cudaSuccess ? WO_OK : WO_ERR_CUDA;
 }
 

@@ -186,9 +186,15 @@ def test_tuning_validation(B):
 
 def test_schedule_table(B):
     lib = B._lib
-    assert lib.wo_schedule_set(3, 128, 1) == 1        # unknown pass
+    assert lib.wo_schedule_set(4, 128, 1) == 1        # unknown pass
     assert lib.wo_schedule_set(1, 1024, 2) == 3       # no register row engine for 1024 points
-    assert lib.wo_schedule_get(3, 128) == -1
+    assert lib.wo_schedule_get(4, 128) == -1
+    # the fused x-y kernels, keyed by Y for square planes: 64, 128 and 192 only
+    for n in (64, 128, 192):
+        assert lib.wo_schedule_get(3, n) == 1                                     # default: two passes
+        assert lib.wo_schedule_set(3, n, 2) == 0 and lib.wo_schedule_get(3, n) == 2
+        assert lib.wo_schedule_set(3, n, 0) == 0 and lib.wo_schedule_get(3, n) == 1
+    assert lib.wo_schedule_set(3, 512, 2) == 3 and lib.wo_schedule_get(3, 512) == 1
     # the reconstruction engine, keyed by Y: the tile pipeline at 64, 128 and 192 only
     for n in (64, 128, 192):
         assert lib.wo_schedule_get(2, n) == 1                                     # default: the five passes
