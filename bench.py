@@ -18,7 +18,10 @@ The same line carries the metric's other parts as legs:
 * "widefield": the 96 x 512 x 512 widefield step (phase + absorption +
   fluorescence TF build and 3D reconstruction);
 * "small_stacks": one 16 x 64 x 64 reconstruction call (latency) and a batch
-  of 4096 such stacks sharing one TF bank.
+  of 4096 such stacks sharing one TF bank;
+* "estimator": the learned optics estimator (training on 10^5 synthetic tiles
+  of 48 x 128 x 128, then a network start plus 10 refinement steps against
+  50 plain tuning steps on 4096 test tiles, errors against the true optics).
 ``--workload tiles|widefield|autotune|estimator`` prints one of them alone.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
@@ -63,10 +66,9 @@ CPU_SAMPLE = (96, 256, 256)
 # capture), scaled by 4 to the 256 tiles of a launch of the bench's field
 # (the traffic grows with the tiles).
 NCU_TRAFFIC = {
-    ("field", "tf_arms"): {"bytes": 4 * (54647552 + 773743616), "digest": "e402c4e07b584d20"},
-    ("field", "tf_psf_rows"): {"bytes": 4 * (906212608 + 425125632), "digest": "4c82bab03e05b259"},
+    ("field", "tf_arms"): {"bytes": 4 * (54615552 + 773050368), "digest": "e402c4e07b584d20"},
+    ("field", "tf_psf_rows"): {"bytes": 4 * (906471424 + 421568768), "digest": "c585ff1478e64ba4"},
 }
-
 
 def kernel_digest(name: str) -> str:
     """Digest of the sources a kernel family is built from."""
@@ -392,7 +394,8 @@ def widefield_leg(args, rank, world, local_rank, with_tune=False):
     Z, Y, X = SHAPE
     o, f = make_inputs(SHAPE, seed=2 + rank)
     tf, ws = B.alloc(1, Z, Y, X, KINDS, dev)
-    B.wo_autotune(1, Z, Y, X, KINDS, ws)  # engine per column-transform length, timed on these shapes
+    if not args.default_engines:
+        B.wo_autotune(1, Z, Y, X, KINDS, ws)  # engine per column-transform length, timed on these shapes
     pin_rows_engine(args, B, X // 2)
     # synthetic data: forward model of the phantom (on the GPU) + seeded noise
     f_d = torch.from_numpy(f).to(dev)
@@ -767,18 +770,24 @@ def roofline_of(kern, prof, workload=None):
 
 def run_tiles(args, rank, world, local_rank):
     """The shift-variant field as the headline line, with the auto-tuning,
-    widefield and small-stack legs unless --field-only."""
+    widefield, small-stack and learned-estimator legs unless --field-only."""
     import torch
     line = field_leg(args, rank, world, local_rank)
     if not args.field_only:
         tune = None if args.no_autotune else autotune_leg(args, rank, world, local_rank)
         wide = widefield_leg(args, rank, world, local_rank)
         small = small_stack_leg(args, rank, world, local_rank)
+        est = None if args.no_estimator else estimator_leg(args, rank, world, local_rank)
         if rank == 0:
             if tune is not None:
                 line["autotune"] = tune  # the metric's second half: auto-tuned tiles/s at fixed error
             line["widefield"] = wide
             line["small_stacks"] = small
+            if est is not None:  # learned start + 10 refinement steps against 50 plain steps
+                line["estimator"] = {k: est[k] for k in ("value", "unit", "ms_per_step", "config", "learned",
+                                                         "plain", "speedup_vs_plain",
+                                                         "learned_with_training_s_per_tile", "break_even_tiles",
+                                                         "training")}
     if rank == 0:
         print(json.dumps(line), flush=True)
     torch.cuda.synchronize()
@@ -803,7 +812,8 @@ def field_leg(args, rank, world, local_rank):
     rec = torch.empty_like(tiles)
     out = torch.empty_like(field)
     tf, ws = B.alloc(n, Z, E, E, ("phase",), dev)
-    B.wo_autotune(n, Z, E, E, ("phase",), ws)
+    if not args.default_engines:
+        B.wo_autotune(n, Z, E, E, ("phase",), ws)
     pin_rows_engine(args, B, E // 2)
 
     def step_on(fld, dst, tl, rc, tfb, wsb, opt):
@@ -1227,7 +1237,8 @@ def autotune_leg(args, rank, world, local_rank, with_cpu=True):
         start = [dict(o, defocus_um=0.0) for o in truth]
     data = make_tune_data(truth, dev, seed=5 + rank, smooth=four)
     pb = A.TuningProblem(data, start, TUNE_ETA, params=args.tune_params)
-    B.wo_autotune(n, Z, Y, X, pb.kinds, pb.ws)  # the workspace is scratch between calls
+    if not args.default_engines:
+        B.wo_autotune(n, Z, Y, X, pb.kinds, pb.ws)  # the workspace is scratch between calls
     sched = A.default_schedule4(truth[0]) if four else A.default_schedule(truth[0])
     n_adam = sum(p.steps for p in sched)
     # per-kernel times of one eager Adam step on the full loss
@@ -1350,7 +1361,7 @@ EST_WORKLOAD = ("learned optics estimator: conv net (4 conv 3x3 + pool + linear,
                 "50-step schedule), against 50-step auto-tuning from nominal on the same tiles")
 
 
-def run_estimator(args, rank, world, local_rank):
+def estimator_leg(args, rank, world, local_rank):
     import torch
     import phantom as ph
     from paper_2412_09775_gb300.build import build
@@ -1401,7 +1412,8 @@ def run_estimator(args, rank, world, local_rank):
 
     def new_problem(data, start):
         q = A.TuningProblem(data, start, TUNE_ETA, params="all")
-        B.wo_autotune(q.n, Z, Y, X, q.kinds, q.ws)
+        if not args.default_engines:
+            B.wo_autotune(q.n, Z, Y, X, q.kinds, q.ws)
         for sch in (refine, plain):  # capture both graphs outside the timed regions
             q.run(sch, graph=True)
             q.reset()
@@ -1461,7 +1473,7 @@ def run_estimator(args, rank, world, local_rank):
             ref_err[c][i] = np.abs(res[k] - truths[c][i])
     est_err, ref_err, plain_err = (np.concatenate(e) for e in (est_err, ref_err, plain_err))
     if rank != 0:
-        return
+        return None
 
     def summary(err):
         return {"defocus_max_um": round(float(err[:, 0].max()), 4),
@@ -1482,10 +1494,21 @@ def run_estimator(args, rank, world, local_rank):
                         "estimate_error": summary(est_err), "refined_error": summary(ref_err)},
             "plain": {"s_per_tile": plain_s, "tune_50_s": t_plain, "error": summary(plain_err)},
             "speedup_vs_plain": round(plain_s / learned_s, 2),
+            # the one-off cost of training, spread over the test tiles, and the
+            # number of tiles after which it has paid for itself
+            "learned_with_training_s_per_tile": (t_gen + t_train) / n_test + learned_s,
+            "break_even_tiles": (round((t_gen + t_train) / (plain_s - learned_s)) if plain_s > learned_s
+                                 else None),
             "training": {"generate_s": round(t_gen, 2), "train_s": round(t_train, 2), "steps": n_steps,
                          "ms_per_step": round(1e3 * t_train / max(n_steps, 1), 3), "step_kernels": step_kern,
                          "loss_per_epoch": [round(v, 5) for v in losses], "params": est.n}}
-    print(json.dumps(line), flush=True)
+    return line
+
+
+def run_estimator(args, rank, world, local_rank):
+    line = estimator_leg(args, rank, world, local_rank)
+    if line is not None:
+        print(json.dumps(line), flush=True)
 
 
 def _oracle_field_tile(job):
@@ -1556,6 +1579,10 @@ def main():
                     help="field (default): the shift-variant field as the headline with the auto-tuning, widefield "
                          "and small-stack legs; tiles: the field line alone")
     ap.add_argument("--field-only", action="store_true", help="field workload without the other legs")
+    ap.add_argument("--no-estimator", action="store_true", help="default run without the learned-estimator leg")
+    ap.add_argument("--default-engines", action="store_true",
+                    help="skip the engine autotuner (built-in engine choices; for runs under a profiler, whose "
+                         "serialised launches would mislead the autotuner's timings)")
     ap.add_argument("--est-train", type=int, default=EST_TRAIN, help="estimator training tiles")
     ap.add_argument("--est-epochs", type=int, default=12, help="estimator training epochs")
     ap.add_argument("--est-test", type=int, default=EST_TEST, help="estimator test tiles")

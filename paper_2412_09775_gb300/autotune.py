@@ -103,7 +103,10 @@ class TuningProblem:
         """Checkpoint of the tuning state as host arrays: the current and the
         starting optics (float64 [n, 9], wo_optics field order) and the Adam
         state (float64 [n, n_params, 3]: m, v and the step count per
-        parameter)."""
+        parameter).  Take it between calls of ``run``: a schedule runs to its
+        end within one call (one graph replay), so a checkpoint holds the
+        state after whole schedules; split a long schedule into its phases to
+        checkpoint between them."""
         return {"optics": self.optics.cpu().numpy().copy(), "optics0": self.optics0.cpu().numpy().copy(),
                 "adam": self.state.cpu().numpy().copy()}
 

@@ -161,12 +161,16 @@ __global__ void __launch_bounds__(ZGeom<N, (NI > NO ? NI : NO)>::NT, ZGeom<N, (N
   const float lam_fl = op.eta_absolute ? op.eta_fl : op.eta_fl * st[2];
   const int L = op.lf_props;
   const float2 zero = make_float2(0.f, 0.f);
+  // a thread keeps one column b (NT is a multiple of B); columns outside the
+  // support disk hold only the TFs' rounding noise: zero out
+  static_assert(NT % B == 0, "one column per thread");
+  const int bt = threadIdx.x % B;
+  const bool col_in = bt < w && !outside_support(st, y, Y, x0 + bt, 2 * (Xh - 1));
   for (int e = threadIdx.x; e < N * B; e += NT) {
     const int k = e / B, b = e % B;  // B is a power of two: shifts
     float2* cell = buf + k * NV * B + b;  // slot v at cell[v * B]
     float2 y0 = zero, y1 = zero, y2 = zero;
-    // columns outside the support disk hold only the TFs' rounding noise: zero out
-    if (b < w && !outside_support(st, y, Y, x0 + b, 2 * (Xh - 1))) {
+    if (col_in) {
       const float2 x0v = cell[0];
       const float2 x1v = NI > 1 ? cell[B] : zero;
       const float2 x2v = NI > 2 ? cell[2 * B] : zero;

@@ -325,6 +325,31 @@ def test_four_parameter_adam_from_nominal_under_a_cuda_graph(env, shape):
     assert np.all(err[:, 0] <= 0.05) and np.all(err[:, 1:] <= 0.01), err
 
 
+def test_checkpoint_between_runs_resumes_exactly(env):
+    """A run split by a checkpoint (state_dict after the first phase, a fresh
+    problem over the same tiles loading it, the second phase there) ends on
+    the same optics as the run in one problem, bit for bit; the first phase
+    and the second each run as their own captured graph in both."""
+    B, A, torch, dev = env
+    shape = (16, 64, 64)
+    ol = smooth_tiles(4, 31)
+    d = np.stack([thin_stack(o, shape, 90 + 5 * t) for t, o in enumerate(ol)])
+    data = torch.tensor(d, dtype=torch.float32, device=dev)
+    start = [dict(o, defocus_um=0.0, tilt_x=0.0, tilt_y=0.0, na_ill=0.825) for o in ol]
+    first, second = A.default_schedule4(ol[0])
+    whole = A.TuningProblem(data, start, 1e-3, params="all")
+    whole.run((first,), graph=True)
+    whole.run((second,), graph=True)
+    part = A.TuningProblem(data, start, 1e-3, params="all")
+    part.run((first,), graph=True)
+    sd = part.state_dict()
+    resumed = A.TuningProblem(data, start, 1e-3, params="all")
+    resumed.load_state_dict(sd)
+    resumed.run((second,), graph=True)
+    assert np.array_equal(resumed.params().cpu().numpy(), whole.params().cpu().numpy())
+    assert np.array_equal(resumed.state_dict()["adam"], whole.state_dict()["adam"])
+
+
 @pytest.mark.parametrize("shape", [SHAPE, SHAPE192])
 def test_four_parameter_gradient_full_batch(env, shape):
     """The auto-tuning workload's launch configuration: 256 tiles of
