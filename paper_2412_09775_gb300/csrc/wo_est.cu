@@ -264,7 +264,7 @@ __global__ void k_standardise(const float* __restrict__ phys, const float* __res
 
 // Workspace layout for a batch.
 struct EstWs {
-  size_t act[5], out, pooled, gpool, gA, gB, grad, target, scale, part, total;
+  size_t act[5], out, pooled, gpool, gA, gB, grad, target, scale, part, wt, total;
   size_t part_floats;  // partial weight gradients of the tensor-core kernels
 };
 
@@ -276,7 +276,7 @@ size_t est_part_floats(int B) {
     const int per = (kLayers[l].ci + 15) / 16;
     long long chunks = (608 + per - 1) / per;
     if (chunks > B) chunks = B;
-    const size_t need = (size_t)chunks * kLayers[l].co * kLayers[l].ci * 9 + (size_t)kLayers[l].co * 32;
+    const size_t need = (size_t)chunks * kLayers[l].co * ((size_t)kLayers[l].ci * 9 + 1);  // weights, bias
     m = need > m ? need : m;
   }
   return m;
@@ -302,6 +302,7 @@ EstWs est_ws(int B) {
   L.scale = o; o += al(2 * kOut * sizeof(float));
   L.part_floats = est_part_floats(B);
   L.part = o; o += al(L.part_floats * sizeof(float));
+  L.wt = o; o += al(est_conv_prep_elems() * 2);  // bfloat16
   L.total = o;
   return L;
 }
@@ -309,9 +310,12 @@ EstWs est_ws(int B) {
 cudaError_t net_forward(const __nv_bfloat16* wb, const float* w32, const float* feat, int B, char* ws, const EstWs& L,
                         cudaStream_t s, const float* scale, const float* offset, float* phys) {
   const float* x = feat;
+  void* wt = ws + L.wt;
+  cudaError_t e = est_conv_prep(wb, kMap.w, wt, s);
+  if (e != cudaSuccess) return e;
   for (int l = 0; l < 4; ++l) {
     float* y = (float*)(ws + L.act[l + 1]);
-    cudaError_t e = est_conv_fwd_mma(l, x, wb, w32, kMap.w[l], kMap.b[l], B, y, s);
+    e = est_conv_fwd_mma(l, x, wb, wt, w32, kMap.w[l], kMap.b[l], B, y, s);
     if (e != cudaSuccess) return e;
     x = y;
   }
@@ -342,7 +346,7 @@ cudaError_t net_backward(const __nv_bfloat16* wb, const float* w32, const float*
     const float* xin = l == 0 ? feat : (const float*)(ws + L.act[l]);
     // weight and bias gradients, then (below the first layer) the gradient at
     // the layer's input, masked by the ReLU that produced it
-    e = est_conv_bwd_mma(l, g, xin, wb, kMap.w[l], kMap.b[l], B, l == 0 ? nullptr : gnext, (float*)(ws + L.part),
+    e = est_conv_bwd_mma(l, g, xin, ws + L.wt, kMap.w[l], kMap.b[l], B, l == 0 ? nullptr : gnext, (float*)(ws + L.part),
                          L.part_floats, grad, s);
     if (e != cudaSuccess) return e;
     if (l == 0) break;

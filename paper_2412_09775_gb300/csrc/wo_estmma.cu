@@ -81,56 +81,140 @@ constexpr int kPitch32 = 40;
 
 __host__ __device__ constexpr int ceil16(int v) { return (v + 15) / 16 * 16; }
 
+// ------------------------------------------------------------------ weights for the staging copies
+// The layers' bfloat16 weights w[co][ci][tap] re-laid once per pass so that a
+// stage's B tile is a run of whole rows: wtf[tap][co][ci] (forward: k = ci)
+// and wtb[tap][ci][co] (data gradient: k = co), layer l at conv_off(l).
+__host__ __device__ constexpr int conv_ci(int l) { return l == 0 ? 3 : (l == 1 ? 32 : (l == 2 ? 64 : 96)); }
+__host__ __device__ constexpr int conv_co(int l) { return l == 0 ? 32 : (l == 1 ? 64 : (l == 2 ? 96 : 128)); }
+__host__ __device__ constexpr long long conv_off(int l) {
+  return l == 0 ? 0 : (l == 1 ? 864 : (l == 2 ? 864 + 18432 : 864 + 18432 + 55296));
+}
+constexpr long long kConvTotal = 864 + 18432 + 55296 + 110592;
+
+struct ConvOffsets {
+  long long w[4];  // each layer's weights in the flat parameter array
+};
+
+__global__ void k_conv_prep(const __nv_bfloat16* __restrict__ wb, ConvOffsets o, __nv_bfloat16* __restrict__ wtf,
+                            __nv_bfloat16* __restrict__ wtb) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kConvTotal) return;
+  const int l = i < conv_off(1) ? 0 : (i < conv_off(2) ? 1 : (i < conv_off(3) ? 2 : 3));
+  const int CI = conv_ci(l), CO = conv_co(l);
+  const long long off = conv_off(l);
+  const long long r = i - off;  // [co][ci][tap]
+  const int tap = (int)(r % 9), ci = (int)((r / 9) % CI), co = (int)(r / (9LL * CI));
+  const __nv_bfloat16 v = wb[o.w[l] + r];
+  wtf[off + ((long long)tap * CO + co) * CI + ci] = v;
+  wtb[off + ((long long)tap * CI + ci) * CO + co] = v;
+}
+
+// Lane map of the A staging copies: a warp covers 8 pixels x 4 channel pairs,
+// so the 32-bit (two-channel) shared-memory stores of a warp fall in
+// distinct banks for row pitches of 12 or 20 words (like the fragment loads),
+// and its global loads are 32-byte runs of 8 pixels per channel.
+struct StageLane {
+  int m_lo, p_lo;  // pixel within the group of 8, pair within the group of 4
+  __device__ StageLane() : m_lo((threadIdx.x & 31) >> 2), p_lo(threadIdx.x & 3) {}
+};
+
 // ------------------------------------------------------------------ forward
-// Block: 64 output pixels of one sample (four warps of 16) x all CO.
+// Block: 64 output pixels of one sample (four warps of 16) x all CO.  Stages
+// run over (tap, 16-channel chunk); each stage's A (64 pixels x 16 channels,
+// split in three parts) and B (CO x 16 weights, whole rows of wtf) are
+// loaded into registers during the previous stage's products and written to
+// the other of two shared-memory buffers: one barrier per stage.
 template <int CI, int CO, int H, int S>
 __global__ void __launch_bounds__(kMmaThreads) k_conv_fwd_mma(const float* __restrict__ x,
-                                                              const __nv_bfloat16* __restrict__ wb,
-                                                              const float* __restrict__ w32, long long woff,
-                                                              long long boff, float* __restrict__ y) {
-  constexpr int HO = (H + S - 1) / S, NPIX = HO * HO, CIP = ceil16(CI), NT = CO / 8;
-  __shared__ __align__(16) __nv_bfloat16 ahi[64 * kPitch], amid[64 * kPitch], alo[64 * kPitch], bs[CO * kPitch];
+                                                              const __nv_bfloat16* __restrict__ wtf,
+                                                              const float* __restrict__ w32, long long boff,
+                                                              float* __restrict__ y) {
+  constexpr int HO = (H + S - 1) / S, NPIX = HO * HO, NT = CO / 8, NC = CI / 16, NSTAGE = 9 * NC;
+  constexpr int BV = CO * 4 / kMmaThreads;  // 8-byte weight copies per thread per stage
+  static_assert(CI % 16 == 0 && (CO * 4) % kMmaThreads == 0, "channel counts of the staged forward");
+  __shared__ __align__(16) __nv_bfloat16 ahi[2][64 * kPitch], amid[2][64 * kPitch], alo[2][64 * kPitch];
+  __shared__ __align__(16) __nv_bfloat16 bs[2][CO * kPitch];
   const int b = blockIdx.y, p0 = blockIdx.x * 64;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const StageLane sl;
+  // this thread's two pixels (groups 2 warp, 2 warp + 1) and two pairs (p_lo, p_lo + 4)
+  int oh[2], ow[2];
+  bool pv[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int p = p0 + (2 * warp + h) * 8 + sl.m_lo;
+    pv[h] = p < NPIX;
+    oh[h] = p / HO;
+    ow[h] = p - (p / HO) * HO;
+  }
+  const float* xb = x + (long long)b * CI * H * H;
+  float av[2][2][2];  // [pixel][pair][channel of the pair]
+  uint2 bv[BV];
+  auto load = [&](int st) {
+    const int tap = st / NC, c0 = (st - (st / NC) * NC) * 16;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int ih = oh[h] * S + tap / 3 - 1, iw = ow[h] * S + tap % 3 - 1;
+      const bool ok = pv[h] && ih >= 0 && ih < H && iw >= 0 && iw < H;
+      const float* src = xb + ((long long)(c0 + 2 * sl.p_lo) * H + (ok ? ih : 0)) * H + (ok ? iw : 0);
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) av[h][q][c] = ok ? __ldg(src + (long long)(8 * q + c) * H * H) : 0.f;
+    }
+    const uint2* wsrc = reinterpret_cast<const uint2*>(wtf + (long long)tap * CO * CI + c0);
+#pragma unroll
+    for (int j = 0; j < BV; ++j) {
+      const int e = threadIdx.x + j * kMmaThreads, co = e >> 2, q = e & 3;
+      bv[j] = __ldg(wsrc + co * (CI / 4) + q);
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int m = (2 * warp + h) * 8 + sl.m_lo;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        __nv_bfloat16 h0, m0, l0, h1, m1, l1;
+        split_bf16(av[h][q][0], h0, m0, l0);
+        split_bf16(av[h][q][1], h1, m1, l1);
+        const int o = m * kPitch + 2 * (sl.p_lo + 4 * q);
+        *reinterpret_cast<__nv_bfloat162*>(&ahi[buf][o]) = __halves2bfloat162(h0, h1);
+        *reinterpret_cast<__nv_bfloat162*>(&amid[buf][o]) = __halves2bfloat162(m0, m1);
+        *reinterpret_cast<__nv_bfloat162*>(&alo[buf][o]) = __halves2bfloat162(l0, l1);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < BV; ++j) {
+      const int e = threadIdx.x + j * kMmaThreads, co = e >> 2, q = e & 3;
+      *reinterpret_cast<uint2*>(&bs[buf][co * kPitch + 4 * q]) = bv[j];
+    }
+  };
   float acc[NT][4];
 #pragma unroll
   for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-  const float* xb = x + (long long)b * CI * H * H;
-  for (int tap = 0; tap < 9; ++tap) {
-    const int kh = tap / 3, kw = tap % 3;
-    for (int c0 = 0; c0 < CIP; c0 += 16) {
-      // A: 64 pixels x 16 channels, split into three bfloat16 parts
-      for (int e = threadIdx.x; e < 64 * 16; e += kMmaThreads) {
-        const int c = e >> 6, m = e & 63;
-        const int p = p0 + m, ci = c0 + c;
-        float v = 0.f;
-        if (p < NPIX && ci < CI) {
-          const int oh = p / HO, ow = p - (p / HO) * HO;
-          const int ih = oh * S + kh - 1, iw = ow * S + kw - 1;
-          if (ih >= 0 && ih < H && iw >= 0 && iw < H) v = __ldg(xb + ((long long)ci * H + ih) * H + iw);
-        }
-        split_bf16(v, ahi[m * kPitch + c], amid[m * kPitch + c], alo[m * kPitch + c]);
-      }
-      // B: 16 channels x CO weights w[co][ci][tap]
-      for (int e = threadIdx.x; e < CO * 16; e += kMmaThreads) {
-        const int co = e >> 4, c = e & 15, ci = c0 + c;
-        bs[co * kPitch + c] = ci < CI ? wb[woff + ((long long)co * CI + ci) * 9 + tap] : __float2bfloat16_rn(0.f);
-      }
-      __syncthreads();
-      uint32_t fh[4], fm[4], fl[4];
-      frag_a(fh, ahi + warp * 16 * kPitch, lane);
-      frag_a(fm, amid + warp * 16 * kPitch, lane);
-      frag_a(fl, alo + warp * 16 * kPitch, lane);
+  load(0);
+  store(0);
+  __syncthreads();
+  for (int st = 0; st < NSTAGE; ++st) {
+    const int buf = st & 1;
+    if (st + 1 < NSTAGE) load(st + 1);  // in flight during this stage's products
+    uint32_t fh[4], fm[4], fl[4];
+    frag_a(fh, ahi[buf] + warp * 16 * kPitch, lane);
+    frag_a(fm, amid[buf] + warp * 16 * kPitch, lane);
+    frag_a(fl, alo[buf] + warp * 16 * kPitch, lane);
 #pragma unroll
-      for (int n = 0; n < NT; ++n) {
-        uint32_t b0, b1;
-        frag_b(b0, b1, bs + n * 8 * kPitch, lane);
-        mma16816(acc[n], fl, b0, b1);
-        mma16816(acc[n], fm, b0, b1);
-        mma16816(acc[n], fh, b0, b1);
-      }
-      __syncthreads();
+    for (int n = 0; n < NT; ++n) {
+      uint32_t b0, b1;
+      frag_b(b0, b1, bs[buf] + n * 8 * kPitch, lane);
+      mma16816(acc[n], fl, b0, b1);
+      mma16816(acc[n], fm, b0, b1);
+      mma16816(acc[n], fh, b0, b1);
     }
+    // the other buffer was last read before the previous barrier
+    if (st + 1 < NSTAGE) store(buf ^ 1);
+    __syncthreads();
   }
   const int g = lane >> 2, t = lane & 3;
   float* yb = y + (long long)b * CO * NPIX;
@@ -158,17 +242,33 @@ __global__ void __launch_bounds__(kMmaThreads) k_conv_fwd_mma_k32(const float* _
   const int b = blockIdx.y, p0 = blockIdx.x * 64;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float* xb = x + (long long)b * CI * H * H;
-  for (int e = threadIdx.x; e < 64 * 32; e += kMmaThreads) {
-    const int k = e >> 6, m = e & 63;
-    const int p = p0 + m;
-    float v = 0.f;
-    if (p < NPIX && k < KV) {
-      const int ci = k / 9, tap = k - 9 * (k / 9);
+  {  // A: 64 pixels x 16 k-pairs; a warp covers 8 pixels x 4 pairs (conflict-free 32-bit stores)
+    const StageLane sl;
+#pragma unroll
+    for (int it = 0; it < 8; ++it) {
+      const int combo = warp + 4 * it;  // 32 combos = 8 pixel groups x 4 pair groups
+      const int m = (combo & 7) * 8 + sl.m_lo, kp = (combo >> 3) * 4 + sl.p_lo;
+      const int p = p0 + m;
       const int oh = p / HO, ow = p - (p / HO) * HO;
-      const int ih = oh * S + tap / 3 - 1, iw = ow * S + tap % 3 - 1;
-      if (ih >= 0 && ih < H && iw >= 0 && iw < H) v = __ldg(xb + ((long long)ci * H + ih) * H + iw);
+      float v[2];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int k = 2 * kp + c;
+        v[c] = 0.f;
+        if (p < NPIX && k < KV) {
+          const int ci = k / 9, tap = k - 9 * (k / 9);
+          const int ih = oh * S + tap / 3 - 1, iw = ow * S + tap % 3 - 1;
+          if (ih >= 0 && ih < H && iw >= 0 && iw < H) v[c] = __ldg(xb + ((long long)ci * H + ih) * H + iw);
+        }
+      }
+      __nv_bfloat16 h0, m0, l0, h1, m1, l1;
+      split_bf16(v[0], h0, m0, l0);
+      split_bf16(v[1], h1, m1, l1);
+      const int o = m * P + 2 * kp;
+      *reinterpret_cast<__nv_bfloat162*>(&ahi[o]) = __halves2bfloat162(h0, h1);
+      *reinterpret_cast<__nv_bfloat162*>(&amid[o]) = __halves2bfloat162(m0, m1);
+      *reinterpret_cast<__nv_bfloat162*>(&alo[o]) = __halves2bfloat162(l0, l1);
     }
-    split_bf16(v, ahi[m * P + k], amid[m * P + k], alo[m * P + k]);
   }
   // w[co][ci][tap] sits at woff + co KV + k
   for (int e = threadIdx.x; e < CO * 32; e += kMmaThreads) {
@@ -221,57 +321,106 @@ __global__ void __launch_bounds__(kMmaThreads) k_conv_fwd_mma_k32(const float* _
 // is split in two (two MMAs: the data gradient decides no mask either).
 template <int CI, int CO, int H, int S>
 __global__ void __launch_bounds__(kMmaThreads) k_conv_bwd_data_mma(const float* __restrict__ gy,
-                                                                   const __nv_bfloat16* __restrict__ wb,
-                                                                   long long woff, const float* __restrict__ xin,
+                                                                   const __nv_bfloat16* __restrict__ wtb,
+                                                                   const float* __restrict__ xin,
                                                                    float* __restrict__ gx) {
   constexpr int HO = H / 2, W2 = H / 2, NCLS = W2 * W2, BPC = (NCLS + 63) / 64, NT = CI / 8, P = kPitch32;
+  constexpr int BV = CI * 4 / kMmaThreads;  // 16-byte weight copies per thread per stage
   static_assert(S == 2 && H % 2 == 0, "the data gradient by parity classes is for stride 2");
-  static_assert(CI % 8 == 0 && CO % 32 == 0, "channel counts of the data gradient");
-  __shared__ __align__(16) __nv_bfloat16 ahi[64 * P], alo[64 * P], bs[CI * P];
+  static_assert(CI % 8 == 0 && CO % 32 == 0 && (CI * 4) % kMmaThreads == 0, "channel counts of the data gradient");
+  __shared__ __align__(16) __nv_bfloat16 ahi[2][64 * P], alo[2][64 * P], bs[2][CI * P];
   const int b = blockIdx.y, cls = blockIdx.x / BPC, r0 = (blockIdx.x - cls * BPC) * 64;
   const int ph = cls >> 1, pw = cls & 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const StageLane sl;
+  // this thread's two class pixels (groups 2 warp, 2 warp + 1) and four pairs (p_lo + 4 q)
+  int ci_[2], cj_[2];
+  bool rv[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int r = r0 + (2 * warp + h) * 8 + sl.m_lo;
+    rv[h] = r < NCLS;
+    ci_[h] = r / W2;
+    cj_[h] = r - (r / W2) * W2;
+  }
+  const float* gb = gy + (long long)b * CO * HO * HO;
+  // the class's taps, (kh, kw) with ih + 1 - kh and iw + 1 - kw even; stages (tap, 32-channel chunk)
+  const int nkw = 1 + pw, NCH = CO / 32, nstage = (1 + ph) * nkw * NCH;
+  float av[2][4][2];  // [pixel][pair group][channel of the pair]
+  uint4 bv[BV];
+  auto tap_of = [&](int st, int& kh, int& kw, int& c0) {
+    const int tp = st / NCH;
+    c0 = (st - tp * NCH) * 32;
+    const int a = tp / nkw, c = tp - a * nkw;
+    kh = ph ? 2 * a : 1;
+    kw = pw ? 2 * c : 1;
+  };
+  auto load = [&](int st) {
+    int kh, kw, c0;
+    tap_of(st, kh, kw, c0);
+    const int dh = (ph + 1 - kh) >> 1, dw = (pw + 1 - kw) >> 1;  // output row i + dh, column j + dw
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int oh = ci_[h] + dh, ow = cj_[h] + dw;
+      const bool ok = rv[h] && oh < HO && ow < HO;
+      const float* src = gb + ((long long)(c0 + 2 * sl.p_lo) * HO + (ok ? oh : 0)) * HO + (ok ? ow : 0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) av[h][q][c] = ok ? __ldg(src + (long long)(8 * q + c) * HO * HO) : 0.f;
+    }
+    const uint4* wsrc = reinterpret_cast<const uint4*>(wtb + (long long)(kh * 3 + kw) * CI * CO + c0);
+#pragma unroll
+    for (int j = 0; j < BV; ++j) {
+      const int e = threadIdx.x + j * kMmaThreads, ci = e >> 2, q = e & 3;
+      bv[j] = __ldg(wsrc + ci * (CO / 8) + q);
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int m = (2 * warp + h) * 8 + sl.m_lo;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float v0 = av[h][q][0], v1 = av[h][q][1];
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(v0), h1 = __float2bfloat16_rn(v1);
+        const __nv_bfloat16 l0 = __float2bfloat16_rn(v0 - __bfloat162float(h0));
+        const __nv_bfloat16 l1 = __float2bfloat16_rn(v1 - __bfloat162float(h1));
+        const int o = m * P + 2 * (sl.p_lo + 4 * q);
+        *reinterpret_cast<__nv_bfloat162*>(&ahi[buf][o]) = __halves2bfloat162(h0, h1);
+        *reinterpret_cast<__nv_bfloat162*>(&alo[buf][o]) = __halves2bfloat162(l0, l1);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < BV; ++j) {
+      const int e = threadIdx.x + j * kMmaThreads, ci = e >> 2, q = e & 3;
+      *reinterpret_cast<uint4*>(&bs[buf][ci * P + 8 * q]) = bv[j];
+    }
+  };
   float acc[NT][4];
 #pragma unroll
   for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-  const float* gb = gy + (long long)b * CO * HO * HO;
-  for (int a = 0; a <= ph; ++a) {
-    for (int c = 0; c <= pw; ++c) {
-      const int kh = ph ? 2 * a : 1, kw = pw ? 2 * c : 1;
-      const int dh = (ph + 1 - kh) >> 1, dw = (pw + 1 - kw) >> 1;  // output row i + dh, column j + dw
-      for (int c0 = 0; c0 < CO; c0 += 32) {
-        for (int e = threadIdx.x; e < 64 * 32; e += kMmaThreads) {
-          const int m = e & 63, cc = e >> 6;
-          const int r = r0 + m;
-          const int i = r / W2, j = r - (r / W2) * W2;
-          const int oh = i + dh, ow = j + dw;
-          float v = 0.f;
-          if (r < NCLS && oh < HO && ow < HO) v = __ldg(gb + ((long long)(c0 + cc) * HO + oh) * HO + ow);
-          const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-          ahi[m * P + cc] = hi;
-          alo[m * P + cc] = __float2bfloat16_rn(v - __bfloat162float(hi));
-        }
-        for (int e = threadIdx.x; e < CI * 32; e += kMmaThreads) {
-          const int cc = e & 31, ci = e >> 5;
-          bs[ci * P + cc] = wb[woff + ((long long)(c0 + cc) * CI + ci) * 9 + kh * 3 + kw];
-        }
-        __syncthreads();
+  load(0);
+  store(0);
+  __syncthreads();
+  for (int st = 0; st < nstage; ++st) {
+    const int buf = st & 1;
+    if (st + 1 < nstage) load(st + 1);  // in flight during this stage's products
 #pragma unroll
-        for (int ks = 0; ks < 2; ++ks) {
-          uint32_t fh[4], fl[4];
-          frag_a<P>(fh, ahi + warp * 16 * P + ks * 16, lane);
-          frag_a<P>(fl, alo + warp * 16 * P + ks * 16, lane);
+    for (int ks = 0; ks < 2; ++ks) {
+      uint32_t fh[4], fl[4];
+      frag_a<P>(fh, ahi[buf] + warp * 16 * P + ks * 16, lane);
+      frag_a<P>(fl, alo[buf] + warp * 16 * P + ks * 16, lane);
 #pragma unroll
-          for (int n = 0; n < NT; ++n) {
-            uint32_t b0, b1;
-            frag_b<P>(b0, b1, bs + n * 8 * P + ks * 16, lane);
-            mma16816(acc[n], fl, b0, b1);
-            mma16816(acc[n], fh, b0, b1);
-          }
-        }
-        __syncthreads();
+      for (int n = 0; n < NT; ++n) {
+        uint32_t b0, b1;
+        frag_b<P>(b0, b1, bs[buf] + n * 8 * P + ks * 16, lane);
+        mma16816(acc[n], fl, b0, b1);
+        mma16816(acc[n], fh, b0, b1);
       }
     }
+    if (st + 1 < nstage) store(buf ^ 1);  // the other buffer was last read before the previous barrier
+    __syncthreads();
   }
   const int g = lane >> 2, t = lane & 3;
 #pragma unroll
@@ -290,185 +439,286 @@ __global__ void __launch_bounds__(kMmaThreads) k_conv_bwd_data_mma(const float* 
 }
 
 // ------------------------------------------------------------------ weight gradient
-// Block (eight warps): 16 input channels, every output channel (warp w takes
-// rows 16w .. 16w+15) and all nine taps, over the output pixels of samples
-// [s0, s0 + chunk), 32 pixels (in raster order) per stage: g for those pixels
-// and the nine taps' input samples for them are staged once and every tap's
-// products run from the same g fragments.  The weight gradient feeds only the
-// weight update, so g and x are split in two parts (three MMAs: hi hi, hi lo,
-// lo hi; 2^-16 of each product left out), unlike the forward pass, whose
-// sums decide the ReLU masks.
-constexpr int kWgThreads = 256;
+// Block: 16 input channels, every output channel and all nine taps, over the
+// output pixels of samples [s0, s0 + chunk), 32 pixels (in raster order) per
+// stage.  Warps: CO/16 row groups (16 output channels each) x 2 tap groups
+// (taps 0-4, 5-8), so every warp has products to do and 40 accumulators.
+// A stage's g (CO x 32) and the nine taps' input samples for its pixels
+// (9 x 16 x 32) are loaded into registers during the previous stage's
+// products and written to the other of two shared-memory buffers: one
+// barrier per stage.  The weight gradient feeds only the weight update, so g
+// and x are split in two parts (three MMAs: hi hi, hi lo, lo hi; 2^-16 of
+// each product left out), unlike the forward pass, whose sums decide the
+// ReLU masks.  The bias gradient (the sum of g over samples and pixels) is
+// accumulated from the same staged values in float32: per thread over its
+// stages, then over the warp's lanes in a fixed order; blocks of the first
+// channel group write it per sample chunk.
+constexpr int kWgThreads = 256;  // the first layer's kernel
 constexpr int kWgPix = 32;     // output pixels per stage
 constexpr int kWgPitch = 40;   // bfloat16 per staged row (32 used)
 
+template <int CO>
+struct WgGeom {
+  static constexpr int MT = CO / 16, NW = 2 * MT, NT = 32 * NW;
+  static constexpr int GV = CO * kWgPix / NT, XV = 9 * 16 * kWgPix / NT;
+  static constexpr int MINB = NT <= 384 ? 2 : 1;  // blocks per SM the register budget is cut for
+  static constexpr size_t SMEM = 2 * (2 * (size_t)CO + 2 * 9 * 16) * kWgPitch * sizeof(__nv_bfloat16);
+  static_assert(CO % 16 == 0 && (9 * 16 * kWgPix) % NT == 0, "output channels of the weight gradient");
+};
+
 template <int CI, int CO, int H, int S>
-__global__ void __launch_bounds__(kWgThreads) k_conv_bwd_weight_mma(const float* __restrict__ gy,
-                                                                    const float* __restrict__ x, int B, int chunk,
-                                                                    float* __restrict__ part) {
-  constexpr int HO = (H + S - 1) / S, NPIX = HO * HO, MT = CO / 16;
-  static_assert(CO % 16 == 0 && MT <= 8, "output channels of the weight gradient");
-  // g: [co][pixel] hi / lo; x: [tap][ci][pixel] hi / lo (pixel contiguous: the k index)
-  __shared__ __align__(16) __nv_bfloat16 ghi[CO * kWgPitch], glo[CO * kWgPitch];
-  __shared__ __align__(16) __nv_bfloat16 xhi[9 * 16 * kWgPitch], xlo[9 * 16 * kWgPitch];
+__global__ void __launch_bounds__(WgGeom<CO>::NT, WgGeom<CO>::MINB) k_conv_bwd_weight_mma(const float* __restrict__ gy,
+                                                                        const float* __restrict__ x, int B,
+                                                                        int chunk, float* __restrict__ part,
+                                                                        float* __restrict__ partb) {
+  using G = WgGeom<CO>;
+  constexpr int HO = (H + S - 1) / S, NPIX = HO * HO, PS = (NPIX + kWgPix - 1) / kWgPix;
+  constexpr int MT = G::MT, NW = G::NW, NT = G::NT, GV = G::GV, XV = G::XV, P = kWgPitch;
+  extern __shared__ __align__(16) unsigned char wg_raw[];
+  __nv_bfloat16* ghi = reinterpret_cast<__nv_bfloat16*>(wg_raw);  // [2][CO][P]
+  __nv_bfloat16* glo = ghi + 2 * CO * P;                           // [2][CO][P]
+  __nv_bfloat16* xhi = glo + 2 * CO * P;                           // [2][9 * 16][P]
+  __nv_bfloat16* xlo = xhi + 2 * 144 * P;                          // [2][9 * 16][P]
   const int c0 = blockIdx.x * 16, ck = blockIdx.y;
   const int s0 = ck * chunk, s1 = min(B, s0 + chunk);
+  const int nst = (s1 > s0 ? s1 - s0 : 0) * PS;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
-  float acc[9][2][4];
+  const int mt = warp % MT, tg = warp / MT, tap0 = tg * 5;  // taps tap0 .. min(tap0 + 5, 9) - 1
+  float acc[5][2][4];
 #pragma unroll
-  for (int q = 0; q < 9; ++q)
+  for (int q = 0; q < 5; ++q)
 #pragma unroll
     for (int n = 0; n < 2; ++n) acc[q][n][0] = acc[q][n][1] = acc[q][n][2] = acc[q][n][3] = 0.f;
-  for (int sb = s0; sb < s1; ++sb) {
-    const float* gb = gy + (long long)sb * CO * NPIX;
-    const float* xb = x + (long long)sb * CI * H * H;
-    for (int p0 = 0; p0 < NPIX; p0 += kWgPix) {
-      for (int e = threadIdx.x; e < CO * kWgPix; e += kWgThreads) {
-        const int co = e / kWgPix, k = e - co * kWgPix, p = p0 + k;
-        const float v = p < NPIX ? __ldg(gb + (long long)co * NPIX + p) : 0.f;
-        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-        ghi[co * kWgPitch + k] = hi;
-        glo[co * kWgPitch + k] = __float2bfloat16_rn(v - __bfloat162float(hi));
-      }
-      for (int e = threadIdx.x; e < 9 * 16 * kWgPix; e += kWgThreads) {
-        const int k = e % kWgPix, rest = e / kWgPix, c = rest % 16, tap = rest / 16;
-        const int p = p0 + k, ci = c0 + c;
-        float v = 0.f;
-        if (p < NPIX && ci < CI) {
-          const int oh = p / HO, ow = p - (p / HO) * HO;
-          const int ih = oh * S + tap / 3 - 1, iw = ow * S + tap % 3 - 1;
-          if (ih >= 0 && ih < H && iw >= 0 && iw < H) v = __ldg(xb + ((long long)ci * H + ih) * H + iw);
-        }
-        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-        xhi[(tap * 16 + c) * kWgPitch + k] = hi;
-        xlo[(tap * 16 + c) * kWgPitch + k] = __float2bfloat16_rn(v - __bfloat162float(hi));
-      }
-      __syncthreads();
-      if (warp < MT) {
+  // a thread stages pixel k = lane of every stage: output channels warp + NW i
+  // of g, and (tap, channel) pairs (warp + NW i) of x
+  float gv[GV], xv[XV], bacc[GV];
 #pragma unroll
-        for (int ks = 0; ks < kWgPix / 16; ++ks) {
-          // A (16 output channels x 16 pixels) of this warp's rows, shared by every tap
-          const __nv_bfloat16* ah = ghi + warp * 16 * kWgPitch + ks * 16;
-          const __nv_bfloat16* al = glo + warp * 16 * kWgPitch + ks * 16;
-          uint32_t fh[4], fl[4];
-          fh[0] = ld32(ah + g * kWgPitch + 2 * t);
-          fh[1] = ld32(ah + (g + 8) * kWgPitch + 2 * t);
-          fh[2] = ld32(ah + g * kWgPitch + 2 * t + 8);
-          fh[3] = ld32(ah + (g + 8) * kWgPitch + 2 * t + 8);
-          fl[0] = ld32(al + g * kWgPitch + 2 * t);
-          fl[1] = ld32(al + (g + 8) * kWgPitch + 2 * t);
-          fl[2] = ld32(al + g * kWgPitch + 2 * t + 8);
-          fl[3] = ld32(al + (g + 8) * kWgPitch + 2 * t + 8);
+  for (int i = 0; i < GV; ++i) bacc[i] = 0.f;
+  auto load = [&](int st) {
+    const int sb = s0 + st / PS, p = (st - (st / PS) * PS) * kWgPix + lane;
+    const bool pv = p < NPIX;
+    const float* gb = gy + (long long)sb * CO * NPIX + (pv ? p : 0);
 #pragma unroll
-          for (int tap = 0; tap < 9; ++tap) {
+    for (int i = 0; i < GV; ++i) gv[i] = pv ? __ldg(gb + (long long)(warp + NW * i) * NPIX) : 0.f;
+    const int oh = p / HO, ow = p - (p / HO) * HO;
+    const float* xb = x + ((long long)sb * CI + c0) * H * H;
 #pragma unroll
-            for (int n = 0; n < 2; ++n) {
-              const __nv_bfloat16* bh = xhi + (tap * 16 + n * 8 + g) * kWgPitch + ks * 16 + 2 * t;
-              const __nv_bfloat16* bl = xlo + (tap * 16 + n * 8 + g) * kWgPitch + ks * 16 + 2 * t;
-              const uint32_t bh0 = ld32(bh), bh1 = ld32(bh + 8), bl0 = ld32(bl), bl1 = ld32(bl + 8);
-              mma16816(acc[tap][n], fh, bl0, bl1);
-              mma16816(acc[tap][n], fl, bh0, bh1);
-              mma16816(acc[tap][n], fh, bh0, bh1);
-            }
-          }
-        }
-      }
-      __syncthreads();
+    for (int i = 0; i < XV; ++i) {
+      const int r = warp + NW * i, c = r & 15, tap = r >> 4;
+      const int ih = oh * S + tap / 3 - 1, iw = ow * S + tap % 3 - 1;
+      const bool ok = pv && c0 + c < CI && ih >= 0 && ih < H && iw >= 0 && iw < H;
+      xv[i] = ok ? __ldg(xb + ((long long)c * H + ih) * H + iw) : 0.f;
     }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int i = 0; i < GV; ++i) {
+      const int o = (buf * CO + warp + NW * i) * P + lane;
+      const __nv_bfloat16 h = __float2bfloat16_rn(gv[i]);
+      ghi[o] = h;
+      glo[o] = __float2bfloat16_rn(gv[i] - __bfloat162float(h));
+      bacc[i] += gv[i];
+    }
+#pragma unroll
+    for (int i = 0; i < XV; ++i) {
+      const int o = (buf * 144 + warp + NW * i) * P + lane;  // row tap * 16 + c
+      const __nv_bfloat16 h = __float2bfloat16_rn(xv[i]);
+      xhi[o] = h;
+      xlo[o] = __float2bfloat16_rn(xv[i] - __bfloat162float(h));
+    }
+  };
+  if (nst > 0) {
+    load(0);
+    store(0);
   }
-  if (warp >= MT) return;
+  __syncthreads();
+  for (int st = 0; st < nst; ++st) {
+    const int buf = st & 1;
+    if (st + 1 < nst) load(st + 1);  // in flight during this stage's products
+    const __nv_bfloat16* gh = ghi + (buf * CO + mt * 16) * P;
+    const __nv_bfloat16* gl = glo + (buf * CO + mt * 16) * P;
+#pragma unroll
+    for (int ks = 0; ks < kWgPix / 16; ++ks) {
+      uint32_t fh[4], fl[4];
+      frag_a<P>(fh, gh + ks * 16, lane);
+      frag_a<P>(fl, gl + ks * 16, lane);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        const int tap = tap0 + q;
+        if (tap >= 9) break;
+#pragma unroll
+        for (int n = 0; n < 2; ++n) {
+          uint32_t bh0, bh1, bl0, bl1;
+          frag_b<P>(bh0, bh1, xhi + (buf * 144 + tap * 16 + n * 8) * P + ks * 16, lane);
+          frag_b<P>(bl0, bl1, xlo + (buf * 144 + tap * 16 + n * 8) * P + ks * 16, lane);
+          mma16816(acc[q][n], fh, bl0, bl1);
+          mma16816(acc[q][n], fl, bh0, bh1);
+          mma16816(acc[q][n], fh, bh0, bh1);
+        }
+      }
+    }
+    if (st + 1 < nst) store(buf ^ 1);  // the other buffer was last read before the previous barrier
+    __syncthreads();
+  }
   float* pc = part + (long long)ck * CO * CI * 9;
 #pragma unroll
-  for (int tap = 0; tap < 9; ++tap) {
+  for (int q = 0; q < 5; ++q) {
+    const int tap = tap0 + q;
+    if (tap >= 9) break;
 #pragma unroll
     for (int n = 0; n < 2; ++n) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int co = warp * 16 + g + (q >= 2 ? 8 : 0), ci = c0 + n * 8 + 2 * t + (q & 1);
-        if (ci < CI) pc[((long long)co * CI + ci) * 9 + tap] = acc[tap][n][q];
+      for (int r = 0; r < 4; ++r) {
+        const int co = mt * 16 + g + (r >= 2 ? 8 : 0), ci = c0 + n * 8 + 2 * t + (r & 1);
+        if (ci < CI) pc[((long long)co * CI + ci) * 9 + tap] = acc[q][n][r];
       }
     }
+  }
+  if (blockIdx.x != 0) return;  // every channel group stages the same g: one writes the bias sums
+#pragma unroll
+  for (int i = 0; i < GV; ++i) {
+    float v = bacc[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) partb[(long long)ck * CO + warp + NW * i] = v;
   }
 }
 
 // Weight gradient of a layer with 9 CI <= 32 (the first layer): N is
 // (ci, tap), n = 9 ci + tap, one 32-wide tile (rows 9 CI .. 31 zero), instead
 // of nine taps each padded to 16 channels.  The eight warps are CO / 16 row
-// groups x 8 / (CO / 16) pixel slices over 128 output pixels per stage; the
-// slices' sums are added in slice order at the end.
-constexpr int kWgPixN = 128;
-constexpr int kWgPitchN = 136;  // 68 words: fragment rows g start in banks 4 g
+// groups x 8 / (CO / 16) pixel slices over 64 output pixels per stage; the
+// slices' sums are added in slice order at the end.  As in the other weight
+// gradients, a stage's g and x are loaded into registers during the previous
+// stage's products and written to the other of two buffers.
+constexpr int kWgPixN = 64;
+constexpr int kWgPitchN = 72;  // 36 words: fragment rows g start in banks 4 g
 
 template <int CI, int CO, int H, int S>
 __global__ void __launch_bounds__(kWgThreads, 2) k_conv_bwd_weight_mma_n32(const float* __restrict__ gy,
                                                                         const float* __restrict__ x, int B,
-                                                                        int chunk, float* __restrict__ part) {
+                                                                        int chunk, float* __restrict__ part,
+                                                                        float* __restrict__ partb) {
   constexpr int HO = (H + S - 1) / S, NPIX = HO * HO, MT = CO / 16, SL = 8 / MT, PX = kWgPixN / SL;
-  constexpr int KV = CI * 9, P = kWgPitchN;
-  static_assert(KV <= 32 && CO % 16 == 0 && 8 % MT == 0 && PX % 16 == 0, "first-layer weight gradient");
-  constexpr int STAGE_BYTES = (2 * CO + 2 * 32) * P * 2, RED_BYTES = (SL - 1) * MT * 512 * 4;
+  constexpr int KV = CI * 9, P = kWgPitchN, PS = (NPIX + kWgPixN - 1) / kWgPixN;
+  constexpr int GB = CO * kWgPixN / kWgThreads, CS = kWgThreads / kWgPixN;  // g per thread, channel sets
+  constexpr int XV = (KV * kWgPixN + kWgThreads - 1) / kWgThreads;
+  static_assert(KV <= 32 && CO % 16 == 0 && 8 % MT == 0 && PX % 16 == 0 && (CO * kWgPixN) % kWgThreads == 0,
+                "first-layer weight gradient");
+  constexpr int BUF = (2 * CO + 2 * 32) * P;  // bfloat16 per buffer: g hi, g lo, x hi, x lo
+  constexpr int STAGE_BYTES = 2 * BUF * 2, RED_BYTES = (SL - 1) * MT * 512 * 4;
   __shared__ __align__(16) unsigned char raw[STAGE_BYTES > RED_BYTES ? STAGE_BYTES : RED_BYTES];
-  __nv_bfloat16* ghi = reinterpret_cast<__nv_bfloat16*>(raw);
-  __nv_bfloat16* glo = ghi + CO * P;
-  __nv_bfloat16* xhi = glo + CO * P;
-  __nv_bfloat16* xlo = xhi + 32 * P;
+  __nv_bfloat16* base = reinterpret_cast<__nv_bfloat16*>(raw);
   const int ck = blockIdx.y;
   const int s0 = ck * chunk, s1 = min(B, s0 + chunk);
+  const int nst = (s1 > s0 ? s1 - s0 : 0) * PS;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int mt = warp % MT, sl = warp / MT;
   const int g = lane >> 2, t = lane & 3;
-  for (int e = threadIdx.x; e < (32 - KV) * kWgPixN; e += kWgThreads) {  // the zero rows, once
-    const int n = KV + e / kWgPixN, k = e % kWgPixN;
-    xhi[n * P + k] = xlo[n * P + k] = __float2bfloat16_rn(0.f);
+  for (int e = threadIdx.x; e < 2 * (32 - KV) * kWgPixN; e += kWgThreads) {  // the zero rows of both buffers, once
+    const int bb = e / ((32 - KV) * kWgPixN), r = e % ((32 - KV) * kWgPixN);
+    const int n = KV + r / kWgPixN, k = r % kWgPixN;
+    __nv_bfloat16* xb = base + bb * BUF + 2 * CO * P;
+    xb[n * P + k] = xb[32 * P + n * P + k] = __float2bfloat16_rn(0.f);
   }
   float acc[4][4];
 #pragma unroll
   for (int n = 0; n < 4; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-  for (int sb = s0; sb < s1; ++sb) {
-    const float* gb = gy + (long long)sb * CO * NPIX;
+  // thread tid stages pixel k = tid % kWgPixN of output channels tid / kWgPixN + CS i,
+  // and the bias gradient from those values
+  float gv[GB], xv[XV], bacc[GB];
+#pragma unroll
+  for (int i = 0; i < GB; ++i) bacc[i] = 0.f;
+  const int kk = threadIdx.x % kWgPixN;
+  auto load = [&](int st) {
+    const int sb = s0 + st / PS, p = (st - (st / PS) * PS) * kWgPixN + kk;
+    const bool pv = p < NPIX;
+    const float* gb = gy + (long long)sb * CO * NPIX + (pv ? p : 0);
+#pragma unroll
+    for (int i = 0; i < GB; ++i) gv[i] = pv ? __ldg(gb + (long long)(threadIdx.x / kWgPixN + CS * i) * NPIX) : 0.f;
+    const int oh = p / HO, ow = p - (p / HO) * HO;
     const float* xb = x + (long long)sb * CI * H * H;
-    for (int p0 = 0; p0 < NPIX; p0 += kWgPixN) {
-      for (int e = threadIdx.x; e < CO * kWgPixN; e += kWgThreads) {
-        const int co = e / kWgPixN, k = e % kWgPixN, p = p0 + k;
-        const float v = p < NPIX ? __ldg(gb + (long long)co * NPIX + p) : 0.f;
-        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-        ghi[co * P + k] = hi;
-        glo[co * P + k] = __float2bfloat16_rn(v - __bfloat162float(hi));
-      }
-      for (int e = threadIdx.x; e < KV * kWgPixN; e += kWgThreads) {
-        const int n = e / kWgPixN, k = e % kWgPixN, p = p0 + k;
-        const int ci = n / 9, tap = n - 9 * (n / 9);
-        float v = 0.f;
-        if (p < NPIX) {
-          const int oh = p / HO, ow = p - (p / HO) * HO;
-          const int ih = oh * S + tap / 3 - 1, iw = ow * S + tap % 3 - 1;
-          if (ih >= 0 && ih < H && iw >= 0 && iw < H) v = __ldg(xb + ((long long)ci * H + ih) * H + iw);
-        }
-        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-        xhi[n * P + k] = hi;
-        xlo[n * P + k] = __float2bfloat16_rn(v - __bfloat162float(hi));
-      }
-      __syncthreads();
 #pragma unroll
-      for (int ks = 0; ks < PX / 16; ++ks) {
-        const int k0 = sl * PX + ks * 16;
-        uint32_t fh[4], fl[4];
-        frag_a<P>(fh, ghi + mt * 16 * P + k0, lane);
-        frag_a<P>(fl, glo + mt * 16 * P + k0, lane);
-#pragma unroll
-        for (int n = 0; n < 4; ++n) {
-          uint32_t bh0, bh1, bl0, bl1;
-          frag_b<P>(bh0, bh1, xhi + n * 8 * P + k0, lane);
-          frag_b<P>(bl0, bl1, xlo + n * 8 * P + k0, lane);
-          mma16816(acc[n], fh, bl0, bl1);
-          mma16816(acc[n], fl, bh0, bh1);
-          mma16816(acc[n], fh, bh0, bh1);
-        }
-      }
-      __syncthreads();
+    for (int i = 0; i < XV; ++i) {
+      const int n = (threadIdx.x + kWgThreads * i) / kWgPixN;
+      const int ci = n / 9, tap = n - 9 * (n / 9);
+      const int ih = oh * S + tap / 3 - 1, iw = ow * S + tap % 3 - 1;
+      const bool ok = pv && n < KV && ih >= 0 && ih < H && iw >= 0 && iw < H;
+      xv[i] = ok ? __ldg(xb + ((long long)ci * H + ih) * H + iw) : 0.f;
     }
+  };
+  auto store = [&](int buf) {
+    __nv_bfloat16* gh = base + buf * BUF;
+#pragma unroll
+    for (int i = 0; i < GB; ++i) {
+      const int o = (threadIdx.x / kWgPixN + CS * i) * P + kk;
+      const __nv_bfloat16 h = __float2bfloat16_rn(gv[i]);
+      gh[o] = h;
+      gh[CO * P + o] = __float2bfloat16_rn(gv[i] - __bfloat162float(h));
+      bacc[i] += gv[i];
+    }
+    __nv_bfloat16* xh = gh + 2 * CO * P;
+#pragma unroll
+    for (int i = 0; i < XV; ++i) {
+      const int n = (threadIdx.x + kWgThreads * i) / kWgPixN;
+      if (n >= KV) continue;
+      const __nv_bfloat16 h = __float2bfloat16_rn(xv[i]);
+      xh[n * P + kk] = h;
+      xh[32 * P + n * P + kk] = __float2bfloat16_rn(xv[i] - __bfloat162float(h));
+    }
+  };
+  if (nst > 0) {
+    load(0);
+    store(0);
   }
+  __syncthreads();
+  for (int st = 0; st < nst; ++st) {
+    const int buf = st & 1;
+    if (st + 1 < nst) load(st + 1);  // in flight during this stage's products
+    const __nv_bfloat16* ghi = base + buf * BUF;
+    const __nv_bfloat16* glo = ghi + CO * P;
+    const __nv_bfloat16* xhi = glo + CO * P;
+    const __nv_bfloat16* xlo = xhi + 32 * P;
+#pragma unroll
+    for (int ks = 0; ks < PX / 16; ++ks) {
+      const int k0 = sl * PX + ks * 16;
+      uint32_t fh[4], fl[4];
+      frag_a<P>(fh, ghi + mt * 16 * P + k0, lane);
+      frag_a<P>(fl, glo + mt * 16 * P + k0, lane);
+#pragma unroll
+      for (int n = 0; n < 4; ++n) {
+        uint32_t bh0, bh1, bl0, bl1;
+        frag_b<P>(bh0, bh1, xhi + n * 8 * P + k0, lane);
+        frag_b<P>(bl0, bl1, xlo + n * 8 * P + k0, lane);
+        mma16816(acc[n], fh, bl0, bl1);
+        mma16816(acc[n], fl, bh0, bh1);
+        mma16816(acc[n], fh, bh0, bh1);
+      }
+    }
+    if (st + 1 < nst) store(buf ^ 1);  // the other buffer was last read before the previous barrier
+    __syncthreads();
+  }
+  // bias: each warp's sums over its lanes, then, in warp order, those of the
+  // warps that staged the same channels (the staging buffers are free: the
+  // loop ended on a barrier)
+  float* rb = reinterpret_cast<float*>(raw);  // [warp][GB]
+#pragma unroll
+  for (int i = 0; i < GB; ++i) {
+    float v = bacc[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) rb[warp * GB + i] = v;
+  }
+  __syncthreads();
+  constexpr int WPC = kWgPixN / 32;  // warps per channel set
+  if (threadIdx.x < CO) {
+    const int co = threadIdx.x, set = co % CS, i = co / CS;
+    float v = 0.f;
+    for (int w = 0; w < WPC; ++w) v += rb[(set * WPC + w) * GB + i];
+    partb[(long long)ck * CO + co] = v;
+  }
+  __syncthreads();  // rb read before the slices reuse the buffer
   // slices 1 .. SL-1 hand their sums to slice 0 (the staging buffers are free: the loop ended on a barrier)
   float* red = reinterpret_cast<float*>(raw);
   if (sl > 0) {
@@ -497,47 +747,32 @@ __global__ void __launch_bounds__(kWgThreads, 2) k_conv_bwd_weight_mma_n32(const
   }
 }
 
-// grad[woff + i] = sum over chunks of part[chunk][i], in chunk order.
-__global__ void k_reduce_chunks(const float* __restrict__ part, int chunks, long long n, long long woff,
-                                float* __restrict__ grad) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+// grad[woff + i] = sum over chunks of part[chunk][i] (i < n, the weights),
+// grad[boff + j] = sum over chunks of partb[chunk][j] (j < nb, the biases).
+// A block takes 32 consecutive entries (one per lane, coalesced loads); its
+// eight warps sum the chunks c = warp (mod 8) in chunk order, and lane e of
+// warp 0 adds the eight warp sums in warp order: a fixed order throughout.
+__global__ void __launch_bounds__(256) k_reduce_chunks(const float* __restrict__ part, int chunks, long long n,
+                                                       long long woff, const float* __restrict__ partb, int nb,
+                                                       long long boff, float* __restrict__ grad) {
+  __shared__ float red[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long i = (long long)blockIdx.x * 32 + lane;
+  const bool live = i < n + nb, w = i < n;
+  const float* src = w ? part + i : partb + (i - n);
+  const long long stride = w ? n : nb;
   float s = 0.f;
-  for (int c = 0; c < chunks; ++c) s += part[(long long)c * n + i];
-  grad[woff + i] = s;
-}
-
-// Bias gradient: db[co] = sum over samples and pixels of g[b][co][p], in two
-// fixed-order passes: blocks (co, sample chunk) reduce their samples' pixels
-// with a fixed tree into part[co][chunk], then one thread per co adds its
-// chunks in order.
-constexpr int kBiasChunks = 32;
-__global__ void __launch_bounds__(256) k_bias_part(const float* __restrict__ gy, int B, int CO, int NPIX,
-                                                   float* __restrict__ part) {
-  __shared__ float red[256];
-  const int co = blockIdx.x, ck = blockIdx.y;
-  const int per = (B + kBiasChunks - 1) / kBiasChunks;
-  const int b0 = ck * per, b1 = min(B, b0 + per);
-  float s = 0.f;
-  for (int b = b0; b < b1; ++b) {
-    const float* gc = gy + ((long long)b * CO + co) * NPIX;
-    for (int p = threadIdx.x; p < NPIX; p += blockDim.x) s += gc[p];
+  if (live) {
+#pragma unroll 4
+    for (int c = warp; c < chunks; c += 8) s += __ldg(src + (long long)c * stride);
   }
-  red[threadIdx.x] = s;
+  red[warp][lane] = s;
   __syncthreads();
-  for (int h = 128; h > 0; h >>= 1) {
-    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) part[(long long)co * kBiasChunks + ck] = red[0];
-}
-
-__global__ void k_bias_final(const float* __restrict__ part, int CO, long long boff, float* __restrict__ grad) {
-  const int co = blockIdx.x * blockDim.x + threadIdx.x;
-  if (co >= CO) return;
-  float s = 0.f;
-  for (int c = 0; c < kBiasChunks; ++c) s += part[(long long)co * kBiasChunks + c];
-  grad[boff + co] = s;
+  if (warp != 0 || !live) return;
+  float t = 0.f;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) t += red[q][lane];
+  grad[w ? woff + i : boff + (i - n)] = t;
 }
 
 // Profiler labels per layer.
@@ -551,62 +786,60 @@ __host__ __device__ constexpr int layer_of() {
 }
 
 template <int CI, int CO, int H, int S>
-cudaError_t fwd_layer(const float* x, const __nv_bfloat16* wb, const float* w32, long long woff, long long boff, int B,
-                      float* y, cudaStream_t s) {
+cudaError_t fwd_layer(const float* x, const __nv_bfloat16* wb, const __nv_bfloat16* wt, const float* w32,
+                      long long woff, long long boff, int B, float* y, cudaStream_t s) {
   constexpr int HO = (H + S - 1) / S;
+  constexpr int l = layer_of<CI, CO, H, S>();
   dim3 grid((unsigned)((HO * HO + 63) / 64), (unsigned)B);
-  const char* name = kFwdName[layer_of<CI, CO, H, S>()];
+  const char* name = kFwdName[l];
   if constexpr (CI * 9 <= 32) {
     WO_LAUNCH(name, s, (k_conv_fwd_mma_k32<CI, CO, H, S><<<grid, kMmaThreads, 0, s>>>(x, wb, w32, woff, boff, y)));
   } else {
-    WO_LAUNCH(name, s, (k_conv_fwd_mma<CI, CO, H, S><<<grid, kMmaThreads, 0, s>>>(x, wb, w32, woff, boff, y)));
+    WO_LAUNCH(name, s, (k_conv_fwd_mma<CI, CO, H, S><<<grid, kMmaThreads, 0, s>>>(x, wt + conv_off(l), w32, boff,
+                                                                                 y)));
   }
   return cudaGetLastError();
 }
 
 template <int CI, int CO, int H, int S>
-cudaError_t bwd_layer(const float* gy, const float* xin, const __nv_bfloat16* wb, long long woff, long long boff,
+cudaError_t bwd_layer(const float* gy, const float* xin, const __nv_bfloat16* wt, long long woff, long long boff,
                       int B, float* gx, float* part, size_t part_floats, float* grad, cudaStream_t s) {
   constexpr int HO = (H + S - 1) / S;
   // weight gradient: blocks (16-channel group, sample chunk); chunks so that
-  // the grid has about 600 blocks and the partials fit their buffer
+  // the grid has about 600 blocks and the partials fit their buffer (weight
+  // partials [chunk][CO][CI][9], then bias partials [chunk][CO])
   const int per = (CI + 15) / 16;
   int chunks = (608 + per - 1) / per;
   const long long wsz = (long long)CO * CI * 9;
-  const long long room = (long long)part_floats - (long long)CO * kBiasChunks;  // bias partials follow
-  if ((long long)chunks * wsz > room) chunks = (int)(room / wsz);
+  if ((long long)chunks * (wsz + CO) > (long long)part_floats) chunks = (int)(part_floats / (wsz + CO));
   if (chunks > B) chunks = B;
   if (chunks < 1) return cudaErrorInvalidValue;
   const int chunk = (B + chunks - 1) / chunks;
   chunks = (B + chunk - 1) / chunk;
+  float* bpart = part + (long long)chunks * wsz;
   dim3 gw((unsigned)((CI + 15) / 16), (unsigned)chunks);
   const char* wname = kWgName[layer_of<CI, CO, H, S>()];
   if constexpr (CI * 9 <= 32) {
     WO_LAUNCH(wname, s, (k_conv_bwd_weight_mma_n32<CI, CO, H, S><<<gw, kWgThreads, 0, s>>>(gy, xin, B, chunk,
-                                                                                          part)));
+                                                                                          part, bpart)));
   } else {
-    WO_LAUNCH(wname, s, (k_conv_bwd_weight_mma<CI, CO, H, S><<<gw, kWgThreads, 0, s>>>(gy, xin, B, chunk, part)));
+    using G = WgGeom<CO>;
+    const cudaError_t attr = allow_smem(k_conv_bwd_weight_mma<CI, CO, H, S>, G::SMEM);
+    if (attr != cudaSuccess) return attr;
+    WO_LAUNCH(wname, s, (k_conv_bwd_weight_mma<CI, CO, H, S><<<gw, G::NT, G::SMEM, s>>>(gy, xin, B, chunk, part,
+                                                                                      bpart)));
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  WO_LAUNCH("est_wgrad_reduce", s, (k_reduce_chunks<<<(unsigned)((wsz + 255) / 256), 256, 0, s>>>(part, chunks, wsz,
-                                                                                                  woff, grad)));
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  // the bias partials sit after the weight partials in the scratch
-  float* bpart = part + (long long)chunks * wsz;
-  if ((long long)chunks * wsz + (long long)CO * kBiasChunks > (long long)part_floats) return cudaErrorInvalidValue;
-  WO_LAUNCH("est_bias_grad", s, (k_bias_part<<<dim3((unsigned)CO, (unsigned)kBiasChunks), 256, 0, s>>>(gy, B, CO,
-                                                                                                     HO * HO, bpart)));
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  WO_LAUNCH("est_bias_grad", s, (k_bias_final<<<1, 128, 0, s>>>(bpart, CO, boff, grad)));
+  WO_LAUNCH("est_wgrad_reduce", s, (k_reduce_chunks<<<(unsigned)((wsz + CO + 31) / 32), 256, 0, s>>>(
+                                       part, chunks, wsz, woff, bpart, CO, boff, grad)));
   e = cudaGetLastError();
   if (e != cudaSuccess || gx == nullptr) return e;
   if constexpr (CI % 8 == 0 && S == 2) {
     dim3 gd((unsigned)(4 * ((H / 2 * (H / 2) + 63) / 64)), (unsigned)B);
     const char* dname = kDgName[layer_of<CI, CO, H, S>()];
-    WO_LAUNCH(dname, s, (k_conv_bwd_data_mma<CI, CO, H, S><<<gd, kMmaThreads, 0, s>>>(gy, wb, woff, xin, gx)));
+    WO_LAUNCH(dname, s, (k_conv_bwd_data_mma<CI, CO, H, S><<<gd, kMmaThreads, 0, s>>>(
+                            gy, wt + kConvTotal + conv_off(layer_of<CI, CO, H, S>()), xin, gx)));
     return cudaGetLastError();
   }
   return cudaErrorInvalidValue;
@@ -614,29 +847,43 @@ cudaError_t bwd_layer(const float* gy, const float* xin, const __nv_bfloat16* wb
 
 }  // namespace
 
+// The layers' weights re-laid for the staging copies (wt: 2 x 185184
+// bfloat16, forward layout then data-gradient layout).
+size_t est_conv_prep_elems() { return 2 * (size_t)kConvTotal; }
+
+cudaError_t est_conv_prep(const void* wb, const long long* woff, void* wt, cudaStream_t s) {
+  ConvOffsets o{};
+  for (int l = 0; l < 4; ++l) o.w[l] = woff[l];
+  __nv_bfloat16* f = (__nv_bfloat16*)wt;
+  WO_LAUNCH("est_conv_prep", s, (k_conv_prep<<<(unsigned)((kConvTotal + 255) / 256), 256, 0, s>>>(
+                                    (const __nv_bfloat16*)wb, o, f, f + kConvTotal)));
+  return cudaGetLastError();
+}
+
 // The four layers of the estimator (3->32 stride 1 at 64 x 64, 32->64,
 // 64->96, 96->128 stride 2).
-cudaError_t est_conv_fwd_mma(int layer, const float* x, const void* wb, const float* w32, long long woff,
-                             long long boff, int B, float* y, cudaStream_t s) {
+cudaError_t est_conv_fwd_mma(int layer, const float* x, const void* wb, const void* wt, const float* w32,
+                             long long woff, long long boff, int B, float* y, cudaStream_t s) {
   const __nv_bfloat16* w = (const __nv_bfloat16*)wb;
+  const __nv_bfloat16* t = (const __nv_bfloat16*)wt;
   switch (layer) {
-    case 0: return fwd_layer<3, 32, 64, 1>(x, w, w32, woff, boff, B, y, s);
-    case 1: return fwd_layer<32, 64, 64, 2>(x, w, w32, woff, boff, B, y, s);
-    case 2: return fwd_layer<64, 96, 32, 2>(x, w, w32, woff, boff, B, y, s);
-    case 3: return fwd_layer<96, 128, 16, 2>(x, w, w32, woff, boff, B, y, s);
+    case 0: return fwd_layer<3, 32, 64, 1>(x, w, t, w32, woff, boff, B, y, s);
+    case 1: return fwd_layer<32, 64, 64, 2>(x, w, t, w32, woff, boff, B, y, s);
+    case 2: return fwd_layer<64, 96, 32, 2>(x, w, t, w32, woff, boff, B, y, s);
+    case 3: return fwd_layer<96, 128, 16, 2>(x, w, t, w32, woff, boff, B, y, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t est_conv_bwd_mma(int layer, const float* gy, const float* xin, const void* wb, long long woff,
+cudaError_t est_conv_bwd_mma(int layer, const float* gy, const float* xin, const void* wt, long long woff,
                              long long boff, int B, float* gx, float* part, size_t part_floats, float* grad,
                              cudaStream_t s) {
-  const __nv_bfloat16* w = (const __nv_bfloat16*)wb;
+  const __nv_bfloat16* t = (const __nv_bfloat16*)wt;
   switch (layer) {
-    case 0: return bwd_layer<3, 32, 64, 1>(gy, xin, w, woff, boff, B, nullptr, part, part_floats, grad, s);
-    case 1: return bwd_layer<32, 64, 64, 2>(gy, xin, w, woff, boff, B, gx, part, part_floats, grad, s);
-    case 2: return bwd_layer<64, 96, 32, 2>(gy, xin, w, woff, boff, B, gx, part, part_floats, grad, s);
-    case 3: return bwd_layer<96, 128, 16, 2>(gy, xin, w, woff, boff, B, gx, part, part_floats, grad, s);
+    case 0: return bwd_layer<3, 32, 64, 1>(gy, xin, t, woff, boff, B, nullptr, part, part_floats, grad, s);
+    case 1: return bwd_layer<32, 64, 64, 2>(gy, xin, t, woff, boff, B, gx, part, part_floats, grad, s);
+    case 2: return bwd_layer<64, 96, 32, 2>(gy, xin, t, woff, boff, B, gx, part, part_floats, grad, s);
+    case 3: return bwd_layer<96, 128, 16, 2>(gy, xin, t, woff, boff, B, gx, part, part_floats, grad, s);
     default: return cudaErrorInvalidValue;
   }
 }

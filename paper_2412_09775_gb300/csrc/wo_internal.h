@@ -260,11 +260,15 @@ float* est_grad_buffer(void* ws, int B);
 // parameter array), float32 activations [B][C][H][H].  Backward: weight and
 // bias gradients of the layer into grad, and (gx != NULL) the gradient at its
 // input masked by xin > 0; part holds part_floats floats of scratch.
-cudaError_t est_conv_fwd_mma(int layer, const float* x, const void* wb, const float* w32, long long woff,
-                             long long boff, int B, float* y, cudaStream_t s);
-cudaError_t est_conv_bwd_mma(int layer, const float* gy, const float* xin, const void* wb, long long woff,
+cudaError_t est_conv_fwd_mma(int layer, const float* x, const void* wb, const void* wt, const float* w32,
+                             long long woff, long long boff, int B, float* y, cudaStream_t s);
+cudaError_t est_conv_bwd_mma(int layer, const float* gy, const float* xin, const void* wt, long long woff,
                              long long boff, int B, float* gx, float* part, size_t part_floats, float* grad,
                              cudaStream_t s);
+// wt: the layers' weights re-laid for the staging copies (est_conv_prep_elems()
+// bfloat16), made from wb by est_conv_prep before a forward or backward pass.
+size_t est_conv_prep_elems();
+cudaError_t est_conv_prep(const void* wb, const long long* woff, void* wt, cudaStream_t s);
 
 // Tiles.
 cudaError_t tiles_gather(const float* field, int Z, int ty, int tx, int core, int halo,
