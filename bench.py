@@ -66,9 +66,11 @@ CPU_SAMPLE = (96, 256, 256)
 # capture), scaled by 4 to the 256 tiles of a launch of the bench's field
 # (the traffic grows with the tiles).
 NCU_TRAFFIC = {
-    ("field", "tf_arms"): {"bytes": 4 * (54615552 + 773050368), "digest": "e402c4e07b584d20"},
-    ("field", "tf_psf_rows"): {"bytes": 4 * (906471424 + 421568768), "digest": "c585ff1478e64ba4"},
+    ("field", "tf_arms"): {"bytes": 4 * (54658560 + 772668416), "digest": "e402c4e07b584d20"},
+    ("field", "tf_psf_rows"): {"bytes": 4 * (906146048 + 424841472), "digest": "02f47ebe8b5595f1"},
+    ("field", "z_fused"): {"bytes": 4 * (584182784 + 417137152), "digest": "028d622b29b0f22f"},
 }
+
 
 def kernel_digest(name: str) -> str:
     """Digest of the sources a kernel family is built from."""
@@ -79,7 +81,7 @@ def kernel_digest(name: str) -> str:
            "y_fwd": ["wo_cols.cu"], "y_inv": ["wo_cols.cu"], "tf_ypass": ["wo_cols.cu"], "tf_arms": tf + ["wo_armsreg.cu", "wo_regfft.cuh"],
            # the register-resident row kernel (rows of 32..512 points; wo_tf.cu holds only the
            # shared-memory fallback for other lengths)
-           "tf_psf_rows": ["wo_psf.cu", "wo_regfft.cuh", "wo_tf.cuh", "wo_internal.h"],
+           "tf_psf_rows": ["wo_psf.cu", "wo_regfft.cuh", "wo_tf.cuh"],
            "tf_zpass": tf + ["wo_zops.cuh"],
            "tf_pupil_record": tf, "tune_cols": ["wo_tune.cu"]}.get(name)
     if src is None:
@@ -1045,6 +1047,37 @@ SMALL_WORKLOAD = ("small stacks 16x64x64 (20 spheres, phase-only, relative eta 1
                   "(wo_reconstruct_shared_tf)")
 
 
+def small_cpu_baseline(o, d):
+    """The oracle on one host core: the phase TF of a 16x64x64 stack and its
+    3D reconstruction (relative eta 1e-3), as for the GPU's single call, and
+    the reconstruction alone with the TF built once (as the GPU batch shares
+    one bank), each timed over 1 s or more."""
+    from oracle import model as OM, optics as OO
+    Z, Y, X = SMALL_SHAPE
+    d64 = d.astype(np.float64)
+
+    def per_call(fn):
+        n, t0 = 0, time.perf_counter()
+        while True:
+            fn()
+            n += 1
+            dt = time.perf_counter() - t0
+            if dt >= 1.0:
+                return dt / n
+
+    def build_and_solve():
+        modes, _, _ = OM.widefield_system(OO.transfer_functions(o, SMALL_SHAPE, ("phase",)), ("phase",))
+        OM.reconstruct(modes, d64, 1e-3, relative=True)
+    t_call = per_call(build_and_solve)
+    modes, _, _ = OM.widefield_system(OO.transfer_functions(o, SMALL_SHAPE, ("phase",)), ("phase",))
+    t_solve = per_call(lambda: OM.reconstruct(modes, d64, 1e-3, relative=True))
+    vox = Z * Y * X
+    return {"value": round(vox / t_solve, 1), "unit": "voxels/s", "cores": 1, "kind": "oracle",
+            "sample": f"numpy float64 oracle on one core: reconstruction of one 16x64x64 stack with a prebuilt TF "
+                      f"({1e3 * t_solve:.1f} ms per stack, the batch's per-stack work); with the TF build "
+                      f"{1e3 * t_call:.1f} ms per call ({vox / t_call:.0f} voxels/s)"}
+
+
 def small_stack_leg(args, rank, world, local_rank):
     """Config of the 16x64x64 stack: the latency of one reconstruction call
     (its 0.8 MB sit in L2) and the throughput of 4096 stacks sharing one TF
@@ -1116,6 +1149,8 @@ def small_stack_leg(args, rank, world, local_rank):
            "compulsory_frac": round(compulsory / (ms * 1e-3) / 1e9 / peak, 4),
            "roofline": roofline_of(kern, prof), "kernels": kern,
            "l2": "batch data 268 MB in, 268 MB out (> L2); the shared TF bank 0.27 MB stays in L2"}
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = small_cpu_baseline(o, d1[0].cpu().numpy())
     del data, outb, wsb
     torch.cuda.empty_cache()
     return out if rank == 0 else None

@@ -400,6 +400,28 @@ __global__ void __launch_bounds__(kMmaThreads) k_conv_bwd_data_mma(const float* 
   float acc[NT][4];
 #pragma unroll
   for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+  // the input ReLU's values at this thread's outputs, loaded now so that their
+  // latency hides under the stages (for the narrower layers, where the
+  // registers allow)
+  const int g = lane >> 2, t = lane & 3;
+  constexpr bool kEarly = NT <= 8;
+  float xm[kEarly ? 4 : 1][kEarly ? NT : 1];
+  // the input pixel of this thread's output rows (-1 past the class grid)
+  auto out_pixel = [&](int q4) -> int {
+    const int r = r0 + warp * 16 + g + (q4 >= 2 ? 8 : 0);
+    const int i = r / W2, j = r - (r / W2) * W2;
+    return r < NCLS ? (2 * i + ph) * H + 2 * j + pw : -1;
+  };
+  if constexpr (kEarly) {
+    int xidx[4];
+#pragma unroll
+    for (int q4 = 0; q4 < 4; ++q4) xidx[q4] = out_pixel(q4);
+#pragma unroll
+    for (int q4 = 0; q4 < 4; ++q4)
+#pragma unroll
+      for (int n = 0; n < NT; ++n)
+        xm[q4][n] = xidx[q4] >= 0 ? __ldg(xin + ((long long)b * CI + n * 8 + 2 * t + (q4 & 1)) * H * H + xidx[q4]) : 0.f;
+  }
   load(0);
   store(0);
   __syncthreads();
@@ -422,18 +444,18 @@ __global__ void __launch_bounds__(kMmaThreads) k_conv_bwd_data_mma(const float* 
     if (st + 1 < nstage) store(buf ^ 1);  // the other buffer was last read before the previous barrier
     __syncthreads();
   }
-  const int g = lane >> 2, t = lane & 3;
 #pragma unroll
   for (int q4 = 0; q4 < 4; ++q4) {
-    const int r = r0 + warp * 16 + g + (q4 >= 2 ? 8 : 0);
-    if (r >= NCLS) continue;
-    const int i = r / W2, j = r - (r / W2) * W2;
-    const long long pix = (long long)(2 * i + ph) * H + 2 * j + pw;
+    const int pix = out_pixel(q4);
+    if (pix < 0) continue;
 #pragma unroll
     for (int n = 0; n < NT; ++n) {
       const int ci = n * 8 + 2 * t + (q4 & 1);
       const long long idx = ((long long)b * CI + ci) * H * H + pix;
-      gx[idx] = xin[idx] > 0.f ? acc[n][q4] : 0.f;
+      float xv;
+      if constexpr (kEarly) xv = xm[q4][n];
+      else xv = __ldg(xin + idx);
+      gx[idx] = xv > 0.f ? acc[n][q4] : 0.f;
     }
   }
 }

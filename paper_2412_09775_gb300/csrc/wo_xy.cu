@@ -132,20 +132,28 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kXyThreads)
   const bool ok = plane < nplanes && WO_IN(plane, nplanes, 10);  // else: barriers only
   const uint32_t tile0 = cluster_addr(smem_addr(tile), 0), tile1 = cluster_addr(smem_addr(tile), 1);
   __syncthreads();  // the twiddles
-  // x: this CTA's rows; bin k of row y goes to tile (k < K0 ? 0 : 1) at [y][k - k0]
+  // x: this CTA's rows; bin k of row y goes to tile (k < K0 ? 0 : 1) at [y][k - k0].
+  // A round's row loads are issued during the previous round's transform.
   const int t = threadIdx.x % TX, rr = threadIdx.x / TX;
-  for (int r0 = 0; r0 < Y / 2; r0 += RX) {
+  float2 nxt[EX];
+  float cn = 0.f;
+  auto load_row = [&](int r0) {
     const int y = (int)rank * (Y / 2) + r0 + rr;
     const bool rv = ok && r0 + rr < Y / 2;
     const long long row = plane * Y + (rv ? y : 0);
-    const float c = rv ? row_constant(in, row, X, bg) : 0.f;
+    cn = rv ? row_constant(in, row, X, bg) : 0.f;
     const float2* src = reinterpret_cast<const float2*>(in + row * X) + t;
+#pragma unroll
+    for (int m = 0; m < EX; ++m) nxt[m] = rv ? __ldg(src + TX * m) : make_float2(0.f, 0.f);
+  };
+  load_row(0);
+  for (int r0 = 0; r0 < Y / 2; r0 += RX) {
+    const int y = (int)rank * (Y / 2) + r0 + rr;
+    const bool rv = ok && r0 + rr < Y / 2;
     float2 v[EX];
 #pragma unroll
-    for (int m = 0; m < EX; ++m) {
-      const float2 z = rv ? __ldg(src + TX * m) : make_float2(0.f, 0.f);
-      v[m] = make_float2(z.x - c, z.y - c);
-    }
+    for (int m = 0; m < EX; ++m) v[m] = make_float2(nxt[m].x - cn, nxt[m].y - cn);
+    if (r0 + RX < Y / 2) load_row(r0 + RX);
     PX::template fft<false>(v, twx, scr + rr * PX::SLICE, t);
     r2c_split<H, TX, EX>(v, tw2, t, [&](int k, float2 val) {
       if (rv) st_cluster((k < K0 ? tile0 + (uint32_t)(y * PITCH + k) * 8u
@@ -156,12 +164,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kXyThreads)
   const int ncols = rank == 0 ? K0 : XH - K0, k0 = rank == 0 ? 0 : K0;
   xy_columns<PX, PY, false>(tile, twy, scr, ncols);
   __syncthreads();
-  if (ok) {
+  if (ok) {  // whole row segments: warp w takes rows w, w + NT/32, ...
     float2* o = out + plane * (long long)Y * XH + k0;
-    for (int e = threadIdx.x; e < Y * ncols; e += G::NT) {
-      const int y = e / ncols, c = e - (e / ncols) * ncols;
-      o[(long long)y * XH + c] = tile[y * PITCH + c];
-    }
+    const int lane = threadIdx.x & 31;
+    for (int y = threadIdx.x >> 5; y < Y; y += G::NT / 32)
+      for (int c = lane; c < ncols; c += 32) o[(long long)y * XH + c] = tile[y * PITCH + c];
   }
 }
 
@@ -179,32 +186,39 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kXyThreads)
   const long long plane = plane0 + blockIdx.y + (long long)gridDim.y * blockIdx.z;
   const bool ok = plane < nplanes && WO_IN(plane, nplanes, 10);  // else: barriers only
   const int ncols = rank == 0 ? K0 : XH - K0, k0 = rank == 0 ? 0 : K0;
-  {  // this CTA's columns, in whole row segments
+  {  // this CTA's columns, in whole row segments (warp w: rows w, w + NT/32, ...), copied
+     // asynchronously so that every copy of the tile is in flight at once
     const float2* src = in + plane * (long long)Y * XH + k0;
-    for (int e = threadIdx.x; e < Y * ncols; e += G::NT) {
-      const int y = e / ncols, c = e - (e / ncols) * ncols;
-      tile[y * PITCH + c] = ok ? __ldg(src + (long long)y * XH + c) : make_float2(0.f, 0.f);
-    }
+    const int lane = threadIdx.x & 31;
+    for (int y = threadIdx.x >> 5; y < Y; y += G::NT / 32)
+      for (int c = lane; c < ncols; c += 32) cp_async8(tile + y * PITCH + c, ok ? src + (long long)y * XH + c : src, ok);
+    cp_async_wait_all();
   }
   __syncthreads();  // the tile and the twiddles
   xy_columns<PX, PY, true>(tile, twy, scr, ncols);
   const uint32_t tile0 = cluster_addr(smem_addr(tile), 0), tile1 = cluster_addr(smem_addr(tile), 1);
   cluster_sync();  // both tiles transformed
-  // x: this CTA's rows, each row's bins read from both tiles
+  // x: this CTA's rows, each row's bins read from both tiles; a round's bins
+  // are read during the previous round's transform
   const int t = threadIdx.x % TX, rr = threadIdx.x / TX;
-  for (int r0 = 0; r0 < Y / 2; r0 += RX) {
-    const int y = (int)rank * (Y / 2) + r0 + rr;
+  float2 x[EX], xn;
+  auto read_row = [&](int r0) {
     const bool rv = ok && r0 + rr < Y / 2;
-    const int ys = rv ? y : 0;
-    float2 x[EX];
+    const int ys = rv ? (int)rank * (Y / 2) + r0 + rr : 0;
 #pragma unroll
     for (int m = 0; m < EX; ++m) {
       const int k = t + TX * m;
       x[m] = ld_cluster(k < K0 ? tile0 + (uint32_t)(ys * PITCH + k) * 8u : tile1 + (uint32_t)(ys * PITCH + k - K0) * 8u);
     }
-    const float2 xn = t == 0 ? ld_cluster(tile1 + (uint32_t)(ys * PITCH + H - K0) * 8u) : make_float2(0.f, 0.f);
+    xn = t == 0 ? ld_cluster(tile1 + (uint32_t)(ys * PITCH + H - K0) * 8u) : make_float2(0.f, 0.f);
+  };
+  read_row(0);
+  for (int r0 = 0; r0 < Y / 2; r0 += RX) {
+    const int y = (int)rank * (Y / 2) + r0 + rr;
+    const bool rv = ok && r0 + rr < Y / 2;
     float2 v[EX];
     c2r_merge<TX, EX>(x, xn, tw2, t, v);
+    if (r0 + RX < Y / 2) read_row(r0 + RX);
     PX::template fft<true>(v, twx, scr + rr * PX::SLICE, t);
     if (rv) {
       const long long row = plane * Y + y;
