@@ -186,6 +186,10 @@ cudaError_t tf_arms(const TfArgs& a, cudaStream_t s);
 bool arms_reg_supported(int Y, const TfArgs& a);
 cudaError_t tf_arms_reg(const TfArgs& a, cudaStream_t s);
 cudaError_t tf_psf_rows(const TfArgs& a, cudaStream_t s);
+// The TF build's z pass for one-kind banks with register-resident z
+// transforms (wo_zreg.cu).
+bool tf_zpass_reg_supported(const TfArgs& a);
+cudaError_t tf_zpass_reg(const TfArgs& a, cudaStream_t s);
 // Hybrid column engine (wo_colhyb.cu) and the schedule table (wo_sched.cu).
 bool cols_hyb_supported(int N);
 cudaError_t cols_c2c_hyb(int N, bool inverse, float2* data, long long col_stride, long long plane_stride, int ncols,

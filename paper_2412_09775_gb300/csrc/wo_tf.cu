@@ -724,6 +724,7 @@ static cudaError_t launch_zpass(const TfArgs& a, cudaStream_t s) {
 #define WO_ZP_CASE_3(n) case n: return launch_zpass<n, 3>(a, s);
 
 cudaError_t tf_zpass(const TfArgs& a, cudaStream_t s) {
+  if (tf_zpass_reg_supported(a)) return tf_zpass_reg(a, s);
   if (a.n_kinds == 1) {
     switch (a.Z) { WO_FOR_EACH_SIZE(WO_ZP_CASE_1) default: return cudaErrorInvalidValue; }
   }

@@ -117,7 +117,106 @@ cudaError_t launch_z_reg(const float2* in, float2* out, const float2* tf, ZOp op
   return cudaGetLastError();
 }
 
+// The TF build's z pass for one-kind banks (the same scheme): forward
+// transform along z of every TF column in place, and the per-tile maxima the
+// relative regulariser uses — max over (k, column) of |H|^2 and max over
+// columns of sum_k |H|^2 (statistics words 0, 1 for a label-free kind, 2, 3
+// for fluorescence), as in k_tf_zpass.  Columns k_x >= x_cols (outside every
+// tile's support, rounding noise only) are left as they are.
+template <class P>
+__global__ void __launch_bounds__(ZRegGeom<P>::NT) k_tf_zpass_reg(TfArgs a) {
+  using G = ZRegGeom<P>;
+  constexpr int N = G::N, T = G::T, E = G::E, CPC = G::CPC, NT = G::NT;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* slices = sm + P::TW;  // [CPC][SLICE]
+  __shared__ float red[2 * (NT / 32)];
+  const int Y = a.Y, Xh = a.X / 2 + 1;
+  const int t = blockIdx.z, y = blockIdx.y, x0 = blockIdx.x * CPC;
+  const int w = min(CPC, a.x_cols - x0);
+  const long long zs = (long long)Y * Xh;
+  const long long vol = (long long)N * zs;
+#if defined(WO_CHECK) && WO_CHECK
+  {  // this strip's elements of the tile's TF slot
+    const long long span = (long long)(N - 1) * zs + (long long)y * Xh + x0 + w - 1;
+    if (!WO_IN((long long)t * vol + span, (long long)gridDim.z * vol, 6)) return;  // uniform across the CTA
+  }
+#endif
+  const int l = threadIdx.x % T, cl = threadIdx.x / T;
+  const bool live = cl < w;
+  float2* col = a.tf + (long long)t * vol + (long long)y * Xh + x0 + (live ? cl : 0);
+  float2 v[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) v[m] = live ? col[(long long)(l + T * m) * zs] : make_float2(0.f, 0.f);
+  P::twiddles(tw);  // while the loads are in flight
+  __syncthreads();
+  P::template fft<false>(v, tw, slices + cl * P::SLICE, l);
+  float m3 = 0.f, cs = 0.f;
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const float q = cabs2(v[m]);
+    m3 = fmaxf(m3, q);
+    cs += q;
+  }
+  if (live) {
+#pragma unroll
+    for (int m = 0; m < E; ++m) col[(long long)(l + T * m) * zs] = v[m];
+  }
+  // the column's sum over its T lanes (a fixed order), then block maxima
+  // (values >= 0: integer order equals float order) and one atomic per statistic
+#pragma unroll
+  for (int o = 1; o < T; o <<= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
+  float m2 = live ? cs : 0.f;
+  if (!live) m3 = 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    m3 = fmaxf(m3, __shfl_down_sync(0xffffffffu, m3, o));
+    m2 = fmaxf(m2, __shfl_down_sync(0xffffffffu, m2, o));
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[2 * warp] = m3;
+    red[2 * warp + 1] = m2;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    float mx = 0.f;
+    for (int q = 0; q < NT / 32; ++q) mx = fmaxf(mx, red[2 * q + threadIdx.x]);
+    const int slot = (a.lf_props > 0 ? 0 : 2) + threadIdx.x;
+    if (mx > 0.f) atomicMax(reinterpret_cast<int*>(a.stats + (long long)t * 8) + slot, __float_as_int(mx));
+  }
+}
+
+template <class P>
+cudaError_t launch_tf_zpass_reg(const TfArgs& a, cudaStream_t s) {
+  using G = ZRegGeom<P>;
+  const cudaError_t attr = allow_smem(k_tf_zpass_reg<P>, G::SMEM);
+  if (attr != cudaSuccess) return attr;
+  if (a.x_cols <= 0) return cudaSuccess;
+  dim3 grid((unsigned)((a.x_cols + G::CPC - 1) / G::CPC), (unsigned)a.Y, (unsigned)a.n_tiles);
+  WO_LAUNCH("tf_zpass", s, (k_tf_zpass_reg<P><<<grid, G::NT, G::SMEM, s>>>(a)));
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+bool tf_zpass_reg_supported(const TfArgs& a) {
+  if (a.n_kinds != 1) return false;
+  const int Z = a.Z;
+  return Z == 32 || Z == 48 || Z == 64 || Z == 96 || Z == 128 || Z == 192;
+}
+
+cudaError_t tf_zpass_reg(const TfArgs& a, cudaStream_t s) {
+  switch (a.Z) {
+    case 32: return launch_tf_zpass_reg<Row2<32, 8>>(a, s);
+    case 48: return launch_tf_zpass_reg<Row2<48, 12>>(a, s);
+    case 64: return launch_tf_zpass_reg<Row2<64, 8>>(a, s);
+    case 96: return launch_tf_zpass_reg<Row2<96, 24>>(a, s);
+    case 128: return launch_tf_zpass_reg<Row2<128, 16>>(a, s);
+    case 192: return launch_tf_zpass_reg<Row2<192, 24>>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 bool z_reg_supported(int Z, const ZOp& op) {
   if (op.n_in != 1 || op.n_out != 1 || op.n_tf != 1 || op.lf_props + op.has_fl != 1) return false;
