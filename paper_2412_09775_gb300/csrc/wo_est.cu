@@ -186,10 +186,37 @@ __global__ void __launch_bounds__(128) k_head_fwd(const float* __restrict__ y4, 
 
 // Loss and the head's gradients.  One block: g_out = 2 (out - t) / (B * 4),
 // d fc W = g_out^T pooled, d fc b = sum g_out; g_pooled = g_out fc W.
+// Head backward, spread over blocks: blocks [0, kOut C / 8) give the linear
+// weights' gradients (one warp per weight, lanes over samples, a fixed
+// shuffle order), the next B C / 256 blocks the pooled features' gradients
+// (one thread each), and the last block the loss and the linear biases'
+// gradients (a fixed tree).
+constexpr int kHeadWBlocks(int C) { return kOut * C / 8; }
 __global__ void __launch_bounds__(256) k_head_bwd(const float* __restrict__ out, const float* __restrict__ target,
                                                   const float* __restrict__ pooled, const __nv_bfloat16* __restrict__ wb,
                                                   int B, int C, float* __restrict__ grad, float* __restrict__ gpool,
                                                   float* __restrict__ loss) {
+  const float gs = 2.f / (float)(B * kOut);
+  const int nwb = kHeadWBlocks(C), npb = (B * C + 255) / 256;
+  if (blockIdx.x < nwb) {
+    const int i = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;  // weight [k][c]
+    const int k = i / C, c = i - (i / C) * C;
+    float s = 0.f;
+    for (int b = lane; b < B; b += 32) s += gs * (out[b * kOut + k] - target[b * kOut + k]) * pooled[(long long)b * C + c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) grad[kMap.fw + i] = s;
+    return;
+  }
+  if (blockIdx.x < nwb + npb) {
+    const int i = (blockIdx.x - nwb) * 256 + threadIdx.x;
+    if (i >= B * C) return;
+    const int b = i / C, c = i - (i / C) * C;
+    float s = 0.f;
+    for (int k = 0; k < kOut; ++k) s += gs * (out[b * kOut + k] - target[b * kOut + k]) * bf(wb, kMap.fw + (long long)k * C + c);
+    gpool[i] = s;
+    return;
+  }
   __shared__ float red[256];
   float l = 0.f;
   for (int i = threadIdx.x; i < B * kOut; i += blockDim.x) {
@@ -203,23 +230,10 @@ __global__ void __launch_bounds__(256) k_head_bwd(const float* __restrict__ out,
     __syncthreads();
   }
   if (threadIdx.x == 0 && loss) *loss = red[0] / (float)(B * kOut);
-  const float gs = 2.f / (float)(B * kOut);
-  for (int i = threadIdx.x; i < kOut * C; i += blockDim.x) {
-    const int k = i / C, c = i - (i / C) * C;
-    float s = 0.f;
-    for (int b = 0; b < B; ++b) s += gs * (out[b * kOut + k] - target[b * kOut + k]) * pooled[(long long)b * C + c];
-    grad[kMap.fw + i] = s;
-  }
   if (threadIdx.x < kOut) {
     float s = 0.f;
     for (int b = 0; b < B; ++b) s += gs * (out[b * kOut + threadIdx.x] - target[b * kOut + threadIdx.x]);
     grad[kMap.fb + threadIdx.x] = s;
-  }
-  for (int i = threadIdx.x; i < B * C; i += blockDim.x) {
-    const int b = i / C, c = i - (i / C) * C;
-    float s = 0.f;
-    for (int k = 0; k < kOut; ++k) s += gs * (out[b * kOut + k] - target[b * kOut + k]) * bf(wb, kMap.fw + (long long)k * C + c);
-    gpool[i] = s;
   }
 }
 
@@ -330,8 +344,10 @@ cudaError_t net_backward(const __nv_bfloat16* wb, const float* w32, const float*
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(grad, 0, (size_t)kMap.total * sizeof(float), s);
   if (e != cudaSuccess) return e;
-  WO_LAUNCH("est_head_bwd", s, (k_head_bwd<<<1, 256, 0, s>>>((float*)(ws + L.out), target, (float*)(ws + L.pooled), wb,
-                                                             B, 128, grad, (float*)(ws + L.gpool), loss)));
+  const unsigned head_blocks = (unsigned)(kHeadWBlocks(128) + (B * 128 + 255) / 256 + 1);
+  WO_LAUNCH("est_head_bwd", s, (k_head_bwd<<<head_blocks, 256, 0, s>>>((float*)(ws + L.out), target,
+                                                                       (float*)(ws + L.pooled), wb, B, 128, grad,
+                                                                       (float*)(ws + L.gpool), loss)));
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   float* g = (float*)(ws + L.gA);
