@@ -295,7 +295,12 @@ long long wo_launch_count(void) { return g_launches.load(); }
 namespace wo {
 namespace {
 std::mutex g_attr_mu;
-std::vector<std::pair<const void*, int>> g_attr_set;  // (kernel, device) with the shared-memory attribute set
+struct SmemGrant {
+  const void* kernel;
+  int device;
+  size_t bytes;  // dynamic shared memory the kernel may take on the device
+};
+std::vector<SmemGrant> g_attr_set;
 }  // namespace
 
 #if defined(WO_CHECK) && WO_CHECK
@@ -330,16 +335,21 @@ int check_take_all(int* info) {
 }
 #endif
 
-bool smem_attr_done(const void* kernel, int device) {
+size_t smem_attr_granted(const void* kernel, int device) {
   std::lock_guard<std::mutex> lk(g_attr_mu);
   for (const auto& e : g_attr_set)
-    if (e.first == kernel && e.second == device) return true;
-  return false;
+    if (e.kernel == kernel && e.device == device) return e.bytes;
+  return 0;
 }
 
-void smem_attr_mark(const void* kernel, int device) {
+void smem_attr_mark(const void* kernel, int device, size_t bytes) {
   std::lock_guard<std::mutex> lk(g_attr_mu);
-  g_attr_set.emplace_back(kernel, device);
+  for (auto& e : g_attr_set)
+    if (e.kernel == kernel && e.device == device) {
+      if (bytes > e.bytes) e.bytes = bytes;
+      return;
+    }
+  g_attr_set.push_back({kernel, device, bytes});
 }
 }  // namespace wo
 

@@ -280,20 +280,25 @@ cudaError_t tiles_gather(const float* field, int Z, int ty, int tx, int core, in
 cudaError_t tiles_blend(const float* tiles, int Z, int ty, int tx, int core, int halo,
                         float* field, cudaStream_t s);
 
-// Opt a kernel into more than 48 KB of dynamic shared memory, once per kernel
-// and device (the attribute belongs to the device's context): a registry of
-// the (kernel, device) pairs already set, kept by wo_api.cu.
-bool smem_attr_done(const void* kernel, int device);
-void smem_attr_mark(const void* kernel, int device);
+// Let a kernel take `bytes` of dynamic shared memory: the opt-in attribute is
+// needed once its static plus dynamic shared memory passes 48 KB, and is set
+// once per (kernel, device) for the largest size asked (the attribute belongs
+// to the device's context): a registry of the granted sizes, kept by wo_api.cu.
+size_t smem_attr_granted(const void* kernel, int device);
+void smem_attr_mark(const void* kernel, int device, size_t bytes);
 template <class K>
 inline cudaError_t allow_smem(K kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
+  if (bytes == 0) return cudaSuccess;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (smem_attr_done((const void*)kernel, dev)) return cudaSuccess;
-  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess) smem_attr_mark((const void*)kernel, dev);
+  if (smem_attr_granted((const void*)kernel, dev) >= bytes) return cudaSuccess;
+  cudaFuncAttributes fa{};
+  e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  if (fa.sharedSizeBytes + bytes > 48 * 1024)
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) smem_attr_mark((const void*)kernel, dev, bytes);
   return e;
 }
 
