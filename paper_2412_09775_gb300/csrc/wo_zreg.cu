@@ -221,12 +221,13 @@ cudaError_t tf_zpass_reg(const TfArgs& a, cudaStream_t s) {
 bool z_reg_supported(int Z, const ZOp& op) {
   if (op.n_in != 1 || op.n_out != 1 || op.n_tf != 1 || op.lf_props + op.has_fl != 1) return false;
   if (op.lf_props > 0 ? op.lf_chan != 0 : op.fl_chan != 0) return false;
-  return Z == 32 || Z == 48 || Z == 64 || Z == 96 || Z == 128 || Z == 192;
+  return Z == 16 || Z == 32 || Z == 48 || Z == 64 || Z == 96 || Z == 128 || Z == 192;
 }
 
 cudaError_t z_fused_reg(int Z, const float2* in, float2* out, const float2* tf, ZOp op, int n_tiles, int Y, int Xh,
                         cudaStream_t s) {
   switch (Z) {
+    case 16: return launch_z_reg<Row2<16, 4>>(in, out, tf, op, n_tiles, Y, Xh, s);
     case 32: return launch_z_reg<Row2<32, 8>>(in, out, tf, op, n_tiles, Y, Xh, s);
     case 48: return launch_z_reg<Row2<48, 12>>(in, out, tf, op, n_tiles, Y, Xh, s);
     case 64: return launch_z_reg<Row2<64, 8>>(in, out, tf, op, n_tiles, Y, Xh, s);
