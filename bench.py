@@ -1123,6 +1123,8 @@ def small_stack_leg(args, rank, world, local_rank):
     data += 1e-3 * torch.randn(data.shape, generator=g, device=dev)  # every stack its own noise
     outb = torch.empty_like(data)
     wsb = torch.empty(B.wo_workspace_bytes(nb, Z, Y, X, ("phase",)), dtype=torch.uint8, device=dev)
+    if not args.default_engines:
+        B.wo_autotune(nb, Z, Y, X, ("phase",), wsb)  # engines timed on these shapes (the batch's workspace)
 
     def batch():
         B.wo_reconstruct_shared_tf(tf1, ("phase",), data, None, [1e-3], B.WO_ETA_RELATIVE, B.WO_MODE_3D, outb, nb, Z,
@@ -1148,6 +1150,7 @@ def small_stack_leg(args, rank, world, local_rank):
            "compulsory_gbs": round(compulsory / (ms * 1e-3) / 1e9, 1),
            "compulsory_frac": round(compulsory / (ms * 1e-3) / 1e9 / peak, 4),
            "roofline": roofline_of(kern, prof), "kernels": kern,
+           "schedule": dict(engines(Y, Z, rows=X // 2), xy=engines_xy(Y)),
            "l2": "batch data 268 MB in, 268 MB out (> L2); the shared TF bank 0.27 MB stays in L2"}
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = small_cpu_baseline(o, d1[0].cpu().numpy())
