@@ -679,7 +679,8 @@ TILE_GRID = (16, 16)
 TILE_CORE, TILE_HALO = 128, 32
 FIELD_Z = 48
 TILES_WORKLOAD = ("shift-variant field 48x2048x2048: 16x16 tiles of 48x192x192 (128-px cores, 32-px halos), "
-                  "per-tile optics; gather + TF build (phase) + 3D Tikhonov + blend, one CUDA graph")
+                  "per-tile optics; TF build (phase) + 3D Tikhonov of the tiles read in place from the field "
+                  "+ blend, one CUDA graph")
 
 
 def make_field(o_list, dev, seed=4):
@@ -810,8 +811,8 @@ def field_leg(args, rank, world, local_rank):
     o_list = ph.tile_optics(np.random.default_rng(3 + rank), n)
     field = make_field(o_list, dev, seed=4 + rank)
     optics = B.optics_tensor(o_list, dev)
-    tiles = torch.empty((n, Z, E, E), dtype=torch.float32, device=dev)
-    rec = torch.empty_like(tiles)
+    tiles = None  # the step reads the tiles from the field in place
+    rec = torch.empty((n, Z, E, E), dtype=torch.float32, device=dev)
     out = torch.empty_like(field)
     tf, ws = B.alloc(n, Z, E, E, ("phase",), dev)
     if not args.default_engines:
@@ -819,9 +820,11 @@ def field_leg(args, rank, world, local_rank):
     pin_rows_engine(args, B, E // 2)
 
     def step_on(fld, dst, tl, rc, tfb, wsb, opt):
-        B.wo_tile_gather(fld, Z, ty, tx, TILE_CORE, TILE_HALO, tl)
+        # the reconstruction's first pass reads each tile's rows from the field
+        # (wo_reconstruct_field_tiles: the same tiles wo_tile_gather would copy)
         B.wo_build_tf_device(opt, n, Z, E, E, ("phase",), tfb, wsb)
-        B.wo_reconstruct(tfb, ("phase",), tl, None, [1e-3], B.WO_ETA_RELATIVE, B.WO_MODE_3D, rc, n, Z, E, E, wsb)
+        B.wo_reconstruct_field_tiles(tfb, ("phase",), fld, Z, ty, tx, TILE_CORE, TILE_HALO, None, [1e-3],
+                                     B.WO_ETA_RELATIVE, B.WO_MODE_3D, rc, wsb)
         B.wo_tile_blend(rc, Z, ty, tx, TILE_CORE, TILE_HALO, dst)
 
     def step():
@@ -918,7 +921,8 @@ def field_leg(args, rank, world, local_rank):
 
 def field_e2e(args, B, step_on, field, o_list, n, Z, E, world, dev):
     """The field step through the public API from pinned host memory: the
-    48x2048x2048 field copied in, gather + TF build + reconstruction + blend,
+    48x2048x2048 field copied in, TF build + reconstruction of the tiles read
+    in place from the field + blend,
     the restored field copied out, every step.  Consecutive steps go round
     ``args.e2e_streams`` streams, each with its own device buffers, so one
     step's copies overlap the others' kernels; also timed serially."""
@@ -931,7 +935,7 @@ def field_e2e(args, B, step_on, field, o_list, n, Z, E, world, dev):
     for i in range(max(1, args.e2e_streams)):
         tfb, wsb = B.alloc(n, Z, E, E, ("phase",), dev)
         lanes.append(dict(s=torch.cuda.Stream(device=dev), d_in=torch.empty_like(field), d_out=torch.empty_like(field),
-                          tl=torch.empty((n, Z, E, E), dtype=torch.float32, device=dev),
+                          tl=None,
                           rc=torch.empty((n, Z, E, E), dtype=torch.float32, device=dev), tf=tfb, ws=wsb,
                           opt=B.optics_tensor(o_list, dev),
                           h_out=torch.empty(field.shape, dtype=torch.float32, pin_memory=True)))

@@ -304,6 +304,26 @@ wo_status wo_reconstruct_fused(const void *d_tf, int n_channels, const float *d_
 wo_status wo_tile_gather(const float *d_field, int Z, int tiles_y, int tiles_x,
                          int core, int halo, float *d_tiles, wo_stream stream);
 
+/* Rows a8 + a7: wo_reconstruct of the tiles of a field without gathering
+ * them first.  The result (d_f [tiles_y*tiles_x][P][Z][E][E], E = core +
+ * 2 halo) equals, bit for bit, wo_tile_gather of d_field [Z][tiles_y*core]
+ * [tiles_x*core] followed by wo_reconstruct on the tiles with the same
+ * arguments: the reconstruction's first pass reads each tile's rows from the
+ * field in place (mirror-padded at the field's edges), so the gathered
+ * copy never goes to memory.  The TF bank holds one bank per tile (in tile
+ * order ty*tiles_x + tx); kinds must describe one data channel (phase and/or
+ * absorption, or fluorescence alone: else WO_ERR_ARG); E/2 must be one of
+ * the register row lengths (32, 48, 64, 96, 128, 192, 256, 512: else
+ * WO_ERR_UNSUPPORTED_SIZE); 0 <= halo, 2*halo <= core, tiles_y*tiles_x <=
+ * 65535 (else WO_ERR_ARG).  The workspace is wo_workspace_bytes(tiles_y *
+ * tiles_x, Z, E, E, kinds); h_background, h_eta, eta_flag and mode as for
+ * wo_reconstruct (NULL background: each tile's mean). */
+wo_status wo_reconstruct_field_tiles(const void *d_tf, unsigned kinds, const float *d_field, int Z,
+                                     int tiles_y, int tiles_x, int core, int halo,
+                                     const float *h_background, const float *h_eta, int eta_flag,
+                                     int mode, float *d_f, void *d_ws, size_t ws_bytes,
+                                     wo_stream stream);
+
 /* Row a8 (blend).  Stitch tiles back: field = sum_t w_t tile_t / sum_t w_t
  * with separable linear-ramp weights w(u) = min(1, (u+1/2)/(2 halo),
  * (E-u-1/2)/(2 halo)) per axis (linearly weighted distance-to-edge blending). */

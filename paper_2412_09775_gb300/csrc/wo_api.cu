@@ -488,12 +488,16 @@ static PipeLaunch pipe_launch(const Layout& L, const Sys& s, const void* d_tf, c
 }
 
 // tf_shared: d_tf holds one tile's bank, used for every tile of the batch.
+// field: the input stacks are the tiles of a field, read in place by the
+// first pass (d_in unused; one data channel).
 static wo_status run_op(int op, const void* d_tf, unsigned kinds, const float* d_in, const float* h_bg,
                         const float* h_eta, int eta_flag, int mode, float* d_out, int n_tiles, int Z,
-                        int Y, int X, void* d_ws, size_t ws_bytes, wo_stream stream, int tf_shared = 0) {
+                        int Y, int X, void* d_ws, size_t ws_bytes, wo_stream stream, int tf_shared = 0,
+                        const FieldSrc* field = nullptr) {
   wo_status st = check_shape(n_tiles, Z, Y, X, kinds);
   if (st != WO_OK) return st;
   if (kinds & WO_TF_PLANES) return WO_ERR_ARG;  // the operators need the 3D TFs
+  if (field) d_in = field->field;
   if (!aligned16(d_tf) || !aligned16(d_in) || !aligned16(d_out) || !aligned16(d_ws)) return WO_ERR_ARG;
   const Sys s = system_of(kinds);
   if (op == 2) {
@@ -560,14 +564,19 @@ static wo_status run_op(int op, const void* d_tf, unsigned kinds, const float* d
 
   // The phase-only 3D reconstruction of tile-sized planes runs as one
   // persistent pipeline (wo_pipe.cu) unless the schedule table says otherwise.
-  if (op == 2 && mode == WO_MODE_3D && pipe_system(s) && pipe_supported(Z, Y, X) &&
+  if (op == 2 && mode == WO_MODE_3D && !field && pipe_system(s) && pipe_supported(Z, Y, X) &&
       recon_engine(Z, Y, X) == WO_ENGINE_HYBRID) {
     PipeLaunch p = pipe_launch(L, s, d_tf, d_in, d_out, n_tiles, Z, Y, X, ws, tf_shared, zo.eta_lf,
                                zo.eta_absolute, h_bg);
     return cuda_status(tile_pipeline(p, cs));
   }
   const long long in_rows = (long long)n_tiles * n_in * Z * Y;
-  WO_TRY(plane_xy_fwd(X, Y, d_in, specA, in_rows / Y, bg_in, cs));
+  if (field) {  // the x pass reads the tiles from the field, then the y pass
+    WO_TRY(rows_r2c_field(H, *field, specA, in_rows, bg_in, cs));
+    WO_TRY(cols_c2c(Y, false, specA, Xh, (long long)Y * Xh, Xh, in_rows / Y, cs, "y_fwd"));
+  } else {
+    WO_TRY(plane_xy_fwd(X, Y, d_in, specA, in_rows / Y, bg_in, cs));
+  }
   if (op == 2 && mode == WO_MODE_2D) {
     WO_TRY(z_solve2d(Z, specA, specB, tf, zo, n_tiles, Y, Xh, cs));
     const float scale = 2.0f / ((float)X * (float)Y);
@@ -602,6 +611,22 @@ wo_status wo_reconstruct(const void* d_tf, unsigned kinds, const float* d_data, 
                          int X, void* d_ws, size_t ws_bytes, wo_stream stream) {
   return run_op(2, d_tf, kinds, d_data, h_background, h_eta, eta_flag, mode, d_f, n_tiles, Z, Y, X, d_ws,
                 ws_bytes, stream);
+}
+
+wo_status wo_reconstruct_field_tiles(const void* d_tf, unsigned kinds, const float* d_field, int Z, int tiles_y,
+                                     int tiles_x, int core, int halo, const float* h_background, const float* h_eta,
+                                     int eta_flag, int mode, float* d_f, void* d_ws, size_t ws_bytes,
+                                     wo_stream stream) {
+  if (tiles_y < 1 || tiles_x < 1 || core < 1 || halo < 0 || 2 * halo > core || Z < 1) return WO_ERR_ARG;
+  if ((long long)tiles_y * tiles_x > 65535) return WO_ERR_ARG;
+  if (!d_field) return WO_ERR_ARG;
+  const Sys s = system_of(kinds);
+  if (s.C != 1) return WO_ERR_ARG;  // a field is one channel
+  const int E = core + 2 * halo;
+  if (E % 2 || !rows_reg_supported(E / 2)) return WO_ERR_UNSUPPORTED_SIZE;
+  const FieldSrc f{d_field, Z, tiles_y, tiles_x, core, halo};
+  return run_op(2, d_tf, kinds, nullptr, h_background, h_eta, eta_flag, mode, d_f, tiles_y * tiles_x, Z, E, E, d_ws,
+                ws_bytes, stream, 0, &f);
 }
 
 wo_status wo_reconstruct_shared_tf(const void* d_tf, unsigned kinds, const float* d_data,

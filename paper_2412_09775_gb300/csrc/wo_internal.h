@@ -209,6 +209,17 @@ cudaError_t plane_xy_inv(int X, int Y, float2* in, float* out, long long nplanes
 int rows_engine(int n);  // engine of the x passes for n complex points (wo_rowsreg.cu: HYBRID)
 bool rows_reg_supported(int N);
 cudaError_t rows_r2c_reg(int N, const float* in, float2* out, long long nrows, RowBg bg, cudaStream_t s);
+// The tiles of a field as the rows' source (wo_rowsreg.cu): tile t = (ty, tx)
+// of a tiles_y x tiles_x grid covers field rows ty*core - halo .. and
+// columns tx*core - halo .., mirror-padded outside the field [Z][Yf][Xf]
+// (Yf = tiles_y core, Xf = tiles_x core); tile rows in [tile][z][row] order,
+// 2N = core + 2 halo samples each.  The same values wo_tile_gather would
+// write, read in place.
+struct FieldSrc {
+  const float* field;
+  int Z, tiles_y, tiles_x, core, halo;
+};
+cudaError_t rows_r2c_field(int N, const FieldSrc& f, float2* out, long long nrows, RowBg bg, cudaStream_t s);
 cudaError_t rows_c2r_reg(int N, const float2* in, float* out, long long nrows, float scale, RowBg bg,
                          cudaStream_t s);
 // Register-resident variant of the PSF-row pass for short rows (wo_psf.cu).

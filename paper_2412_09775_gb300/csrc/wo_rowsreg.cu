@@ -100,6 +100,77 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_c2r_reg(const float2* __re
   for (int m = 0; m < E; ++m) o[T * m] = make_float2(v[m].x * scale + cst, v[m].y * scale + cst);
 }
 
+__device__ __forceinline__ int mirror_px(int i, int n) {
+  i = i < 0 ? -i : i;
+  return i >= n ? 2 * (n - 1) - i : i;
+}
+
+// k_rows_r2c_reg with the rows read from the tiles of a field (FieldSrc):
+// tile row (t, z, u) is field row mirror(ty core - halo + u) of plane z,
+// samples mirror(tx core - halo + x); a tile whose columns lie inside the
+// field reads them as pairs, a border tile one mirrored sample at a time.
+// The mode-2 background is the tile's first sample, as for a gathered tile.
+template <class P>
+__global__ void __launch_bounds__(kRowThreads) k_rows_r2c_field(FieldSrc f, float2* __restrict__ out, long long nrows,
+                                                                 RowBg bg) {
+  using G = RowRegGeom<P>;
+  constexpr int N = G::N, T = G::T, E = G::E, RPC = G::RPC, W = 2 * N;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* tw2 = sm + P::TW;
+  const int t = threadIdx.x % T, r = threadIdx.x / T;
+  float2* S = sm + P::TW + 2 * N + r * P::SLICE;
+  const long long row = (long long)blockIdx.x * RPC + r;
+  const bool live0 = row < nrows;
+  long long rr = live0 ? row : nrows - 1;
+  const bool inside = WO_IN(rr, nrows, 7);
+  if (!inside) rr = 0;
+  const bool live = live0 && inside;
+  const int Yf = f.tiles_y * f.core, Xf = f.tiles_x * f.core;
+  const long long per_tile = (long long)f.Z * W;
+  const long long tile = rr / per_tile, rem = rr - tile * per_tile;
+  const int z = (int)(rem / W), u = (int)(rem - (long long)(rem / W) * W);
+  const int ty = (int)(tile / f.tiles_x), tx = (int)(tile - (tile / f.tiles_x) * f.tiles_x);
+  const int y0 = ty * f.core - f.halo, xs0 = tx * f.core - f.halo;
+  const float* frow = f.field + ((long long)z * Yf + mirror_px(y0 + u, Yf)) * Xf;
+  float c = 0.f;
+  if (bg.mode == 1) c = bg.v[((bg.row_offset + rr) / bg.rows_per_block) % bg.nchan];
+  if (bg.mode == 2) c = __ldg(f.field + (long long)mirror_px(y0, Yf) * Xf + mirror_px(xs0, Xf));
+  const bool pairs = xs0 >= 0 && xs0 + W <= Xf && ((xs0 | Xf) & 1) == 0;  // uniform per tile
+  float2 v[E];
+  if (pairs) {
+    const float2* src = reinterpret_cast<const float2*>(frow + xs0) + t;
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = __ldg(src + T * m);
+  } else {
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const int x = xs0 + 2 * (t + T * m);
+      v[m] = make_float2(__ldg(frow + mirror_px(x, Xf)), __ldg(frow + mirror_px(x + 1, Xf)));
+    }
+  }
+  P::twiddles(tw);  // while the row's loads are in flight
+  make_twiddles<2 * N>(tw2);
+  __syncthreads();
+#pragma unroll
+  for (int m = 0; m < E; ++m) v[m] = make_float2(v[m].x - c, v[m].y - c);
+  P::template fft<false>(v, tw, S, t);
+  float2* o = out + rr * (N + 1);
+  r2c_split<N, T, E>(v, tw2, t, [&](int k, float2 val) {
+    if (live) o[k] = val;
+  });
+}
+
+template <class P>
+cudaError_t launch_r2c_field(const FieldSrc& f, float2* out, long long nrows, RowBg bg, cudaStream_t s) {
+  using G = RowRegGeom<P>;
+  const cudaError_t attr = allow_smem(k_rows_r2c_field<P>, G::SMEM);
+  if (attr != cudaSuccess) return attr;
+  const long long blocks = (nrows + G::RPC - 1) / G::RPC;
+  WO_LAUNCH("rows_r2c", s, (k_rows_r2c_field<P><<<(unsigned)blocks, kRowThreads, G::SMEM, s>>>(f, out, nrows, bg)));
+  return cudaGetLastError();
+}
+
 template <class P>
 cudaError_t launch_r2c_reg(const float* in, float2* out, long long nrows, RowBg bg, cudaStream_t s) {
   using G = RowRegGeom<P>;
@@ -137,6 +208,21 @@ cudaError_t rows_r2c_reg(int N, const float* in, float2* out, long long nrows, R
     case 192: return launch_r2c_reg<Row2<192, 24>>(in, out, nrows, bg, s);
     case 256: return launch_r2c_reg<Row2<256, 16>>(in, out, nrows, bg, s);
     case 512: return launch_r2c_reg<Row512>(in, out, nrows, bg, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t rows_r2c_field(int N, const FieldSrc& f, float2* out, long long nrows, RowBg bg, cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  switch (N) {
+    case 32: return launch_r2c_field<Row2<32, 8>>(f, out, nrows, bg, s);
+    case 48: return launch_r2c_field<Row2<48, 12>>(f, out, nrows, bg, s);
+    case 64: return launch_r2c_field<Row2<64, 8>>(f, out, nrows, bg, s);
+    case 96: return launch_r2c_field<Row2<96, 24>>(f, out, nrows, bg, s);
+    case 128: return launch_r2c_field<Row2<128, 16>>(f, out, nrows, bg, s);
+    case 192: return launch_r2c_field<Row2<192, 24>>(f, out, nrows, bg, s);
+    case 256: return launch_r2c_field<Row2<256, 16>>(f, out, nrows, bg, s);
+    case 512: return launch_r2c_field<Row512>(f, out, nrows, bg, s);
     default: return cudaErrorInvalidValue;
   }
 }

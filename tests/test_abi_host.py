@@ -369,3 +369,19 @@ def test_launch_counter_is_host_side(B):
     n0 = B._lib.wo_launch_count()
     assert B._lib.wo_forward(1 << 20, 7, (1 << 20) + 8, None, 1 << 20, 1, 16, 64, 64, 1 << 20, 1 << 40, None) == 1
     assert B._lib.wo_launch_count() == n0
+
+
+def test_field_tiles_validation(B):
+    # the in-place field-tile reconstruction rejects what it cannot do before launching
+    lib = B._lib
+    fake = 1 << 20
+    big = 1 << 40
+    eta = B._floats([1e-3, 1e-3])
+
+    def call(kinds, Z, ty, tx, core, halo):
+        return lib.wo_reconstruct_field_tiles(fake, kinds, fake, Z, ty, tx, core, halo, None, eta[0], 0, 0, fake,
+                                              fake, big, None)
+    assert call(1 | 4, 16, 2, 2, 48, 8) == 1      # two data channels
+    assert call(1, 16, 2, 2, 48, 25) == 1         # 2 halo > core
+    assert call(1, 16, 0, 2, 48, 8) == 1          # no tiles
+    assert call(1, 16, 2, 2, 52, 4) == 3          # E = 60: no 30-point register rows

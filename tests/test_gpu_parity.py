@@ -640,6 +640,12 @@ def test_shift_variant_field_full_size(env):
     B.wo_build_tf_device(optics, n, Z, E, E, ("phase",), tf, ws)
     B.wo_reconstruct(tf, ("phase",), tiles, None, [1e-3], B.WO_ETA_RELATIVE, B.WO_MODE_3D, rec, n, Z, E, E, ws)
     B.wo_tile_blend(rec, Z, ty, tx, core, halo, out)
+    # the in-place reconstruction the bench's step runs gives the same tiles, bit for bit
+    rec2 = torch.empty_like(rec)
+    B.wo_reconstruct_field_tiles(tf, ("phase",), field, Z, ty, tx, core, halo, None, [1e-3], B.WO_ETA_RELATIVE,
+                                 B.WO_MODE_3D, rec2, ws)
+    assert torch.equal(rec2, rec)
+    del rec2
     torch.cuda.synchronize()
     for t in (0, 17, 255):  # a corner, an interior tile, the opposite corner
         y0, x0 = OT.tile_origin(t // tx, t % tx, core, halo)
