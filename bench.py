@@ -712,9 +712,11 @@ def make_field(o_list, dev, seed=4):
 
 def field_algorithmic_bytes(o_list, Z, E, field_vox):
     """Compulsory HBM bytes per launch of each kernel family of one field step:
-    gather, the phase TF build from device optics (every half-spectrum column),
-    the 3D reconstruction, blend; summed over the tiles, each with its own
-    detection band and TF support."""
+    the phase TF build from device optics (every half-spectrum column), the
+    3D reconstruction, whose first pass reads the tiles from the field (4 B
+    per tile voxel), and the blend; summed over the tiles, each with its own
+    detection band and TF support.  (tile_gather: the separate gather launch,
+    for runs that use it.)"""
     Xh = E // 2 + 1
     real, half = Z * E * E * 4, Z * E * Xh * 8
     out = {k: 0 for k in ("tf_pupil_record", "tf_arms", "tf_psf_rows", "tf_ypass", "tf_zpass", "rows_r2c", "y_fwd",
@@ -821,7 +823,8 @@ def field_leg(args, rank, world, local_rank):
 
     def step_on(fld, dst, tl, rc, tfb, wsb, opt):
         # the reconstruction's first pass reads each tile's rows from the field
-        # (wo_reconstruct_field_tiles: the same tiles wo_tile_gather would copy)
+        # (wo_reconstruct_field_tiles: the same tiles wo_tile_gather would copy);
+        # the separate blend is faster than wo_restore_field's fused last pass
         B.wo_build_tf_device(opt, n, Z, E, E, ("phase",), tfb, wsb)
         B.wo_reconstruct_field_tiles(tfb, ("phase",), fld, Z, ty, tx, TILE_CORE, TILE_HALO, None, [1e-3],
                                      B.WO_ETA_RELATIVE, B.WO_MODE_3D, rc, wsb)
@@ -935,8 +938,8 @@ def field_e2e(args, B, step_on, field, o_list, n, Z, E, world, dev):
     for i in range(max(1, args.e2e_streams)):
         tfb, wsb = B.alloc(n, Z, E, E, ("phase",), dev)
         lanes.append(dict(s=torch.cuda.Stream(device=dev), d_in=torch.empty_like(field), d_out=torch.empty_like(field),
-                          tl=None,
-                          rc=torch.empty((n, Z, E, E), dtype=torch.float32, device=dev), tf=tfb, ws=wsb,
+                          tl=None, rc=torch.empty((n, Z, E, E), dtype=torch.float32, device=dev), tf=tfb,
+                          ws=wsb,
                           opt=B.optics_tensor(o_list, dev),
                           h_out=torch.empty(field.shape, dtype=torch.float32, pin_memory=True)))
 

@@ -324,6 +324,19 @@ wo_status wo_reconstruct_field_tiles(const void *d_tf, unsigned kinds, const flo
                                      int mode, float *d_f, void *d_ws, size_t ws_bytes,
                                      wo_stream stream);
 
+/* Rows a8 + a7 + a8: restore a field in one call — the reconstruction of
+ * its tiles read in place (as wo_reconstruct_field_tiles) with the last pass
+ * blending the reconstructed tiles straight into d_out [P][Z][tiles_y*core]
+ * [tiles_x*core] (WO_MODE_2D: [P][tiles_y*core][tiles_x*core]), so neither
+ * the gathered nor the reconstructed tiles go to memory.  Equal, bit for
+ * bit, to wo_reconstruct_field_tiles followed by wo_tile_blend of each
+ * property.  Arguments as for wo_reconstruct_field_tiles; also tiles_x <= 64
+ * and d_out != d_field (else WO_ERR_ARG). */
+wo_status wo_restore_field(const void *d_tf, unsigned kinds, const float *d_field, int Z, int tiles_y,
+                           int tiles_x, int core, int halo, const float *h_background,
+                           const float *h_eta, int eta_flag, int mode, float *d_out, void *d_ws,
+                           size_t ws_bytes, wo_stream stream);
+
 /* Row a8 (blend).  Stitch tiles back: field = sum_t w_t tile_t / sum_t w_t
  * with separable linear-ramp weights w(u) = min(1, (u+1/2)/(2 halo),
  * (E-u-1/2)/(2 halo)) per axis (linearly weighted distance-to-edge blending). */

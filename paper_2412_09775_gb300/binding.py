@@ -73,6 +73,7 @@ def _load():
         "wo_reconstruct_static": (i, [vp, u, vp, fp, fp, i, i, vp, i, i, i, i, vp]),
         "wo_reconstruct_shared_tf": (i, [vp, u, vp, fp, fp, i, i, vp, i, i, i, i, vp, sz, vp]),
         "wo_reconstruct_field_tiles": (i, [vp, u, vp, i, i, i, i, i, fp, fp, i, i, vp, vp, sz, vp]),
+        "wo_restore_field": (i, [vp, u, vp, i, i, i, i, i, fp, fp, i, i, vp, vp, sz, vp]),
         "wo_clear_status": (i, [vp, vp]),
         "wo_sync_status": (i, [vp, ctypes.POINTER(ctypes.c_int), vp]),
         "wo_check_build": (i, []),
@@ -118,7 +119,7 @@ EXPORTED = ("wo_size_supported", "wo_tf_bytes", "wo_workspace_bytes", "wo_build_
             "wo_aberrated_workspace_bytes", "wo_build_tf_aberrated",
             "wo_forward",
             "wo_forward_adjoint", "wo_reconstruct", "wo_reconstruct_static", "wo_reconstruct_shared_tf",
-            "wo_reconstruct_field_tiles", "wo_clear_status", "wo_sync_status", "wo_check_build", "wo_pipeline_probe", "wo_spectrum",
+            "wo_reconstruct_field_tiles", "wo_restore_field", "wo_clear_status", "wo_sync_status", "wo_check_build", "wo_pipeline_probe", "wo_spectrum",
             "wo_tune_objective", "wo_reconstruct_vjp", "wo_adam_optics", "wo_fused_workspace_bytes", "wo_reconstruct_fused",
             "wo_est_param_count", "wo_est_workspace_bytes", "wo_est_activation_offset", "wo_est_sync_bf16", "wo_est_forward", "wo_est_backward",
             "wo_est_train_step", "wo_est_features", "wo_thin_phantom",
@@ -265,6 +266,17 @@ def wo_reconstruct_field_tiles(tf, kinds, field, Z, tiles_y, tiles_x, core, halo
                                            int(tiles_x), int(core), int(halo), bg[0] if bg else None, et[0],
                                            int(eta_flag), int(mode), _ptr(f), _ptr(ws), _nbytes(ws), _stream(stream)),
            "wo_reconstruct_field_tiles")
+
+
+def wo_restore_field(tf, kinds, field, Z, tiles_y, tiles_x, core, halo, background, eta, eta_flag, mode, out, ws,
+                     stream=None):
+    """Reconstruct the tiles of `field` read in place and blend them into
+    `out` [P][Z][tiles_y*core][tiles_x*core] in one call."""
+    bg = _floats(background)
+    et = _floats(eta if isinstance(eta, (list, tuple)) else [eta])
+    _check(_lib.wo_restore_field(_ptr(tf), kinds_mask(kinds), _ptr(field), int(Z), int(tiles_y), int(tiles_x),
+                                 int(core), int(halo), bg[0] if bg else None, et[0], int(eta_flag), int(mode),
+                                 _ptr(out), _ptr(ws), _nbytes(ws), _stream(stream)), "wo_restore_field")
 
 
 def wo_reconstruct_shared_tf(tf, kinds, data, background, eta, eta_flag, mode, f, n_tiles, Z, Y, X, ws,

@@ -489,15 +489,17 @@ static PipeLaunch pipe_launch(const Layout& L, const Sys& s, const void* d_tf, c
 
 // tf_shared: d_tf holds one tile's bank, used for every tile of the batch.
 // field: the input stacks are the tiles of a field, read in place by the
-// first pass (d_in unused; one data channel).
+// first pass (d_in unused; one data channel).  fout: the output tiles are
+// blended into a field by the last pass (d_out unused).
 static wo_status run_op(int op, const void* d_tf, unsigned kinds, const float* d_in, const float* h_bg,
                         const float* h_eta, int eta_flag, int mode, float* d_out, int n_tiles, int Z,
                         int Y, int X, void* d_ws, size_t ws_bytes, wo_stream stream, int tf_shared = 0,
-                        const FieldSrc* field = nullptr) {
+                        const FieldSrc* field = nullptr, const FieldDst* fout = nullptr) {
   wo_status st = check_shape(n_tiles, Z, Y, X, kinds);
   if (st != WO_OK) return st;
   if (kinds & WO_TF_PLANES) return WO_ERR_ARG;  // the operators need the 3D TFs
   if (field) d_in = field->field;
+  if (fout) d_out = fout->field;
   if (!aligned16(d_tf) || !aligned16(d_in) || !aligned16(d_out) || !aligned16(d_ws)) return WO_ERR_ARG;
   const Sys s = system_of(kinds);
   if (op == 2) {
@@ -564,7 +566,7 @@ static wo_status run_op(int op, const void* d_tf, unsigned kinds, const float* d
 
   // The phase-only 3D reconstruction of tile-sized planes runs as one
   // persistent pipeline (wo_pipe.cu) unless the schedule table says otherwise.
-  if (op == 2 && mode == WO_MODE_3D && !field && pipe_system(s) && pipe_supported(Z, Y, X) &&
+  if (op == 2 && mode == WO_MODE_3D && !field && !fout && pipe_system(s) && pipe_supported(Z, Y, X) &&
       recon_engine(Z, Y, X) == WO_ENGINE_HYBRID) {
     PipeLaunch p = pipe_launch(L, s, d_tf, d_in, d_out, n_tiles, Z, Y, X, ws, tf_shared, zo.eta_lf,
                                zo.eta_absolute, h_bg);
@@ -583,12 +585,24 @@ static wo_status run_op(int op, const void* d_tf, unsigned kinds, const float* d
     RowBg none{};
     none.rows_per_block = Y;
     none.nchan = 1;
-    WO_TRY(plane_xy_inv(X, Y, specB, d_out, (long long)n_tiles * s.P, scale, none, cs));
+    if (fout) {  // inverse y pass, then the inverse x pass blending the tiles into the field
+      WO_TRY(cols_c2c(Y, true, specB, Xh, (long long)Y * Xh, Xh, (long long)n_tiles * s.P, cs, "y_inv"));
+      FieldDst f2 = *fout;
+      f2.Z = 1;
+      WO_TRY(rows_c2r_blend(H, specB, f2, scale, cs));
+    } else {
+      WO_TRY(plane_xy_inv(X, Y, specB, d_out, (long long)n_tiles * s.P, scale, none, cs));
+    }
     return WO_OK;
   }
   WO_TRY(z_fused(Z, specA, specB, tf, zo, n_tiles, Y, Xh, cs));
   const float scale = (float)(2.0 / ((double)X * (double)Y * (double)Z));
-  WO_TRY(plane_xy_inv(X, Y, specB, d_out, (long long)n_tiles * n_out * Z, scale, bg_out, cs));
+  if (fout) {  // (reconstruction only: no background added on the way out)
+    WO_TRY(cols_c2c(Y, true, specB, Xh, (long long)Y * Xh, Xh, (long long)n_tiles * n_out * Z, cs, "y_inv"));
+    WO_TRY(rows_c2r_blend(H, specB, *fout, scale, cs));
+  } else {
+    WO_TRY(plane_xy_inv(X, Y, specB, d_out, (long long)n_tiles * n_out * Z, scale, bg_out, cs));
+  }
   return WO_OK;
 }
 
@@ -627,6 +641,22 @@ wo_status wo_reconstruct_field_tiles(const void* d_tf, unsigned kinds, const flo
   const FieldSrc f{d_field, Z, tiles_y, tiles_x, core, halo};
   return run_op(2, d_tf, kinds, nullptr, h_background, h_eta, eta_flag, mode, d_f, tiles_y * tiles_x, Z, E, E, d_ws,
                 ws_bytes, stream, 0, &f);
+}
+
+wo_status wo_restore_field(const void* d_tf, unsigned kinds, const float* d_field, int Z, int tiles_y, int tiles_x,
+                           int core, int halo, const float* h_background, const float* h_eta, int eta_flag, int mode,
+                           float* d_out, void* d_ws, size_t ws_bytes, wo_stream stream) {
+  if (tiles_y < 1 || tiles_x < 1 || core < 1 || halo < 0 || 2 * halo > core || Z < 1) return WO_ERR_ARG;
+  if ((long long)tiles_y * tiles_x > 65535 || tiles_x > 64) return WO_ERR_ARG;
+  if (!d_field || !d_out || d_out == d_field) return WO_ERR_ARG;
+  const Sys s = system_of(kinds);
+  if (s.C != 1) return WO_ERR_ARG;  // a field is one channel
+  const int E = core + 2 * halo;
+  if (E % 2 || !rows_reg_supported(E / 2)) return WO_ERR_UNSUPPORTED_SIZE;
+  const FieldSrc f{d_field, Z, tiles_y, tiles_x, core, halo};
+  const FieldDst o{d_out, s.P, Z, tiles_y, tiles_x, core, halo};
+  return run_op(2, d_tf, kinds, nullptr, h_background, h_eta, eta_flag, mode, nullptr, tiles_y * tiles_x, Z, E, E,
+                d_ws, ws_bytes, stream, 0, &f, &o);
 }
 
 wo_status wo_reconstruct_shared_tf(const void* d_tf, unsigned kinds, const float* d_data,

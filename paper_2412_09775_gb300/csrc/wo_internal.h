@@ -220,6 +220,14 @@ struct FieldSrc {
   int Z, tiles_y, tiles_x, core, halo;
 };
 cudaError_t rows_r2c_field(int N, const FieldSrc& f, float2* out, long long nrows, RowBg bg, cudaStream_t s);
+// The inverse x pass of a field's tiles fused with their blend into the
+// field (wo_rowsreg.cu): field [P][Z][tiles_y core][tiles_x core], the same
+// values as the inverse x pass into tiles followed by wo_tile_blend.
+struct FieldDst {
+  float* field;
+  int P, Z, tiles_y, tiles_x, core, halo;
+};
+cudaError_t rows_c2r_blend(int N, const float2* spec, const FieldDst& f, float scale, cudaStream_t s);
 cudaError_t rows_c2r_reg(int N, const float2* in, float* out, long long nrows, float scale, RowBg bg,
                          cudaStream_t s);
 // Register-resident variant of the PSF-row pass for short rows (wo_psf.cu).

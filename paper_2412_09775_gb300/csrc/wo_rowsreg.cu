@@ -18,6 +18,7 @@
 #include "wo_internal.h"
 #include "wo_regfft.cuh"
 #include "wo_rowsplit.cuh"
+#include "wo_tiles.cuh"
 
 namespace wo {
 
@@ -100,11 +101,6 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_c2r_reg(const float2* __re
   for (int m = 0; m < E; ++m) o[T * m] = make_float2(v[m].x * scale + cst, v[m].y * scale + cst);
 }
 
-__device__ __forceinline__ int mirror_px(int i, int n) {
-  i = i < 0 ? -i : i;
-  return i >= n ? 2 * (n - 1) - i : i;
-}
-
 // k_rows_r2c_reg with the rows read from the tiles of a field (FieldSrc):
 // tile row (t, z, u) is field row mirror(ty core - halo + u) of plane z,
 // samples mirror(tx core - halo + x); a tile whose columns lie inside the
@@ -132,10 +128,10 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_r2c_field(FieldSrc f, floa
   const int z = (int)(rem / W), u = (int)(rem - (long long)(rem / W) * W);
   const int ty = (int)(tile / f.tiles_x), tx = (int)(tile - (tile / f.tiles_x) * f.tiles_x);
   const int y0 = ty * f.core - f.halo, xs0 = tx * f.core - f.halo;
-  const float* frow = f.field + ((long long)z * Yf + mirror_px(y0 + u, Yf)) * Xf;
+  const float* frow = f.field + ((long long)z * Yf + mirror_idx(y0 + u, Yf)) * Xf;
   float c = 0.f;
   if (bg.mode == 1) c = bg.v[((bg.row_offset + rr) / bg.rows_per_block) % bg.nchan];
-  if (bg.mode == 2) c = __ldg(f.field + (long long)mirror_px(y0, Yf) * Xf + mirror_px(xs0, Xf));
+  if (bg.mode == 2) c = __ldg(f.field + (long long)mirror_idx(y0, Yf) * Xf + mirror_idx(xs0, Xf));
   const bool pairs = xs0 >= 0 && xs0 + W <= Xf && ((xs0 | Xf) & 1) == 0;  // uniform per tile
   float2 v[E];
   if (pairs) {
@@ -146,7 +142,7 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_r2c_field(FieldSrc f, floa
 #pragma unroll
     for (int m = 0; m < E; ++m) {
       const int x = xs0 + 2 * (t + T * m);
-      v[m] = make_float2(__ldg(frow + mirror_px(x, Xf)), __ldg(frow + mirror_px(x + 1, Xf)));
+      v[m] = make_float2(__ldg(frow + mirror_idx(x, Xf)), __ldg(frow + mirror_idx(x + 1, Xf)));
     }
   }
   P::twiddles(tw);  // while the row's loads are in flight
@@ -168,6 +164,115 @@ cudaError_t launch_r2c_field(const FieldSrc& f, float2* out, long long nrows, Ro
   if (attr != cudaSuccess) return attr;
   const long long blocks = (nrows + G::RPC - 1) / G::RPC;
   WO_LAUNCH("rows_r2c", s, (k_rows_r2c_field<P><<<(unsigned)blocks, kRowThreads, G::SMEM, s>>>(f, out, nrows, bg)));
+  return cudaGetLastError();
+}
+
+// The inverse x pass of a field's tiles fused with their blend (the tiles
+// wo_reconstruct writes, stitched as wo_tile_blend stitches them): a CTA
+// takes field row y of plane z of property p; the tile rows that cover it
+// (row u of the one or two tile rows ty, every tx) are transformed back (T
+// lanes each, as k_rows_c2r_reg), scaled, parked in shared memory, and
+// blended with k_blend's weights, order and arithmetic, so the field equals
+// the one from the tiles bit for bit.  spec: the half spectra after the
+// inverse y pass, [tile][P][Z][2N][N+1].
+template <class P>
+__global__ void __launch_bounds__(kRowThreads) k_rows_c2r_blend(const float2* __restrict__ spec, FieldDst f,
+                                                                 float scale, int vec) {
+  using G = RowRegGeom<P>;
+  constexpr int N = G::N, T = G::T, E = G::E, RPC = G::RPC, W = 2 * N, XH = N + 1;
+  // parked row pitch: the rows of a half-warp's pair stores start on distinct bank pairs
+  constexpr int RS = W + 8;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* tw2 = sm + P::TW;
+  float* vals = reinterpret_cast<float*>(sm + P::TW + 2 * N + RPC * P::SLICE);  // [2][tiles_x][RS]
+  const int t = threadIdx.x % T, r = threadIdx.x / T;
+  float2* S = sm + P::TW + 2 * N + r * P::SLICE;
+  const int core = f.core, halo = f.halo;
+  const int Yf = f.tiles_y * core, Xf = f.tiles_x * core;
+  const long long frow = blockIdx.x;  // (p Z + z) Yf + y
+  const int y = (int)(frow % Yf);
+  const long long pz = frow / Yf;
+  const int z = (int)(pz % f.Z), p = (int)(pz / f.Z);
+  int tys[2] = {0, 0}, us[2] = {0, 0};
+  float wys[2] = {0.f, 0.f};
+  int ny = 0;
+  const int qy = (y + halo) / core;
+  for (int c = qy - 1; c <= qy; ++c) {
+    if (c < 0 || c >= f.tiles_y) continue;
+    const int u = y - (c * core - halo);
+    if (u < 0 || u >= W) continue;
+    tys[ny] = c;
+    us[ny] = u;
+    wys[ny] = ramp(u, W, halo);
+    ++ny;
+  }
+  P::twiddles(tw);
+  make_twiddles<2 * N>(tw2);
+  __syncthreads();
+  const int nrow = ny * f.tiles_x;
+  for (int i0 = 0; i0 < nrow; i0 += RPC) {  // uniform across the CTA
+    const int i = i0 + r;
+    const bool live = i < nrow;
+    const int a = live ? i / f.tiles_x : 0, b = live ? i - (i / f.tiles_x) * f.tiles_x : 0;
+    const long long tile = (long long)tys[a] * f.tiles_x + b;
+    const long long srow = ((tile * f.P + p) * f.Z + z) * (long long)W + us[a];
+    const bool ok = live && WO_IN(srow, (long long)f.tiles_y * f.tiles_x * f.P * f.Z * W, 7);
+    const float2* src = spec + (ok ? srow : 0) * XH;
+    float2 x[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) x[m] = __ldg(src + t + T * m);
+    const float2 xn = t == 0 ? __ldg(src + N) : make_float2(0.f, 0.f);  // X[N], partner of X[0]
+    float2 v[E];
+    c2r_merge<T, E>(x, xn, tw2, t, v);
+    P::template fft<true>(v, tw, S, t);
+    if (ok) {
+      float2* dst = reinterpret_cast<float2*>(vals + (a * f.tiles_x + b) * RS) + t;
+      const float cst = 0.f;  // (as the reconstruction's inverse x pass: no background added)
+#pragma unroll
+      for (int m = 0; m < E; ++m) dst[T * m] = make_float2(v[m].x * scale + cst, v[m].y * scale + cst);
+    }
+  }
+  __syncthreads();
+  float* out = f.field + frow * (long long)Xf;
+  const int nvec = vec ? Xf / 4 : Xf;
+  for (int q = threadIdx.x; q < nvec; q += kRowThreads) {
+    const int x0 = vec ? 4 * q : q;
+    const int lanes = vec ? 4 : 1;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f}, wsum[4] = {0.f, 0.f, 0.f, 0.f};
+    const int qx = (x0 + halo) / core;
+    for (int c = qx - 1; c <= qx; ++c) {
+      if (c < 0 || c >= f.tiles_x) continue;
+      const int v = x0 - (c * core - halo);
+      if (v < 0 || v >= W) continue;  // vec: v .. v+3 lie in the same tile
+      for (int a = 0; a < ny; ++a) {
+        const float* src = vals + (a * f.tiles_x + c) * RS + v;
+        for (int k = 0; k < lanes; ++k) {
+          const float wgt = wys[a] * ramp(v + k, W, halo);
+          acc[k] += wgt * src[k];
+          wsum[k] += wgt;
+        }
+      }
+    }
+    if (!WO_IN(frow * (long long)Xf + x0 + lanes - 1, (long long)gridDim.x * Xf, 7)) continue;
+    if (vec) {
+      *reinterpret_cast<float4*>(out + x0) =
+          make_float4(acc[0] / wsum[0], acc[1] / wsum[1], acc[2] / wsum[2], acc[3] / wsum[3]);
+    } else {
+      out[x0] = acc[0] / wsum[0];
+    }
+  }
+}
+
+template <class P>
+cudaError_t launch_c2r_blend(const float2* spec, const FieldDst& f, float scale, cudaStream_t s) {
+  using G = RowRegGeom<P>;
+  const size_t smem = G::SMEM + (size_t)2 * f.tiles_x * (2 * G::N + 8) * sizeof(float);
+  const cudaError_t attr = allow_smem(k_rows_c2r_blend<P>, smem);
+  if (attr != cudaSuccess) return attr;
+  const int vec = (f.core % 4 == 0 && f.halo % 4 == 0) ? 1 : 0;
+  const long long rows = (long long)f.P * f.Z * f.tiles_y * f.core;
+  WO_LAUNCH("rows_c2r", s, (k_rows_c2r_blend<P><<<(unsigned)rows, kRowThreads, smem, s>>>(spec, f, scale, vec)));
   return cudaGetLastError();
 }
 
@@ -223,6 +328,21 @@ cudaError_t rows_r2c_field(int N, const FieldSrc& f, float2* out, long long nrow
     case 192: return launch_r2c_field<Row2<192, 24>>(f, out, nrows, bg, s);
     case 256: return launch_r2c_field<Row2<256, 16>>(f, out, nrows, bg, s);
     case 512: return launch_r2c_field<Row512>(f, out, nrows, bg, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t rows_c2r_blend(int N, const float2* spec, const FieldDst& f, float scale, cudaStream_t s) {
+  if (f.tiles_x > 64) return cudaErrorInvalidValue;  // the parked rows must fit shared memory
+  switch (N) {
+    case 32: return launch_c2r_blend<Row2<32, 8>>(spec, f, scale, s);
+    case 48: return launch_c2r_blend<Row2<48, 12>>(spec, f, scale, s);
+    case 64: return launch_c2r_blend<Row2<64, 8>>(spec, f, scale, s);
+    case 96: return launch_c2r_blend<Row2<96, 24>>(spec, f, scale, s);
+    case 128: return launch_c2r_blend<Row2<128, 16>>(spec, f, scale, s);
+    case 192: return launch_c2r_blend<Row2<192, 24>>(spec, f, scale, s);
+    case 256: return launch_c2r_blend<Row2<256, 16>>(spec, f, scale, s);
+    case 512: return launch_c2r_blend<Row512>(spec, f, scale, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -9,19 +9,9 @@
 // and the field is sum_t w_t tile_t / sum_t w_t.  With 2*halo <= core every
 // field pixel is covered by at most two tiles per axis.
 #include "wo_internal.h"
+#include "wo_tiles.cuh"
 
 namespace wo {
-
-__device__ __forceinline__ int mirror_idx(int i, int n) {
-  i = i < 0 ? -i : i;
-  return i >= n ? 2 * (n - 1) - i : i;
-}
-
-__device__ __forceinline__ float ramp(int u, int E, int halo) {
-  if (halo == 0) return 1.f;
-  const float inv = 1.0f / (2.0f * (float)halo);
-  return fminf(1.f, fminf(((float)u + 0.5f) * inv, ((float)(E - u) - 0.5f) * inv));
-}
 
 // Gather: one thread per 4 consecutive tile pixels of a row.  When the four
 // field pixels are in range they are contiguous and 16-byte aligned (tile

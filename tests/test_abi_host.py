@@ -385,3 +385,18 @@ def test_field_tiles_validation(B):
     assert call(1, 16, 2, 2, 48, 25) == 1         # 2 halo > core
     assert call(1, 16, 0, 2, 48, 8) == 1          # no tiles
     assert call(1, 16, 2, 2, 52, 4) == 3          # E = 60: no 30-point register rows
+
+
+def test_restore_field_validation(B):
+    lib = B._lib
+    fake = 1 << 20
+    big = 1 << 40
+    eta = B._floats([1e-3, 1e-3])
+
+    def call(kinds, ty, tx, core, halo, out=fake + 256):
+        return lib.wo_restore_field(fake, kinds, fake, 16, ty, tx, core, halo, None, eta[0], 0, 0, out, fake, big,
+                                    None)
+    assert call(1, 2, 2, 48, 8, out=fake) == 1    # output over the input field
+    assert call(1, 2, 65, 48, 8) == 1             # more than 64 tiles across
+    assert call(1 | 4, 2, 2, 48, 8) == 1          # two data channels
+    assert call(1, 2, 2, 52, 4) == 3              # E = 60: no 30-point register rows
