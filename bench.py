@@ -83,7 +83,9 @@ def kernel_digest(name: str) -> str:
            # shared-memory fallback for other lengths)
            "tf_psf_rows": ["wo_psf.cu", "wo_regfft.cuh", "wo_tf.cuh"],
            "tf_zpass": tf + ["wo_zops.cuh"],
-           "tf_pupil_record": tf, "tune_cols": ["wo_tune.cu"]}.get(name)
+           "tf_pupil_record": tf, "tune_cols": ["wo_tune.cu"],
+           "tf_yz": ["wo_plane.cu", "wo_bulk.cuh", "wo_regfft.cuh", "wo_zops.cuh"],
+           "yz_op": ["wo_plane.cu", "wo_bulk.cuh", "wo_regfft.cuh", "wo_zops.cuh"]}.get(name)
     if src is None:
         return ""
     h = hashlib.sha256()
@@ -120,6 +122,22 @@ def support_columns(o, kinds, Y, X):
     ky = np.where(np.arange(Y) < (Y + 1) // 2, np.arange(Y), np.arange(Y) - Y) / Y
     kx = np.arange(X // 2 + 1) / X
     return int(np.sum(ky[:, None] ** 2 + kx[None, :] ** 2 <= r * r))
+
+
+def support_planes(o, kinds, X):
+    """Half-spectrum columns k_x whose (k_x, k_y = 0) lies inside the TFs'
+    support disk (the planes the plane engine reads; the others are written
+    as zeros without being read)."""
+    lam = o["lambda_um"]
+    tilt = float(np.hypot(o["tilt_x"], o["tilt_y"]))
+    R = 0.0
+    if {"phase", "absorption"} & set(kinds):
+        R = o["na_det"] + min(o["na_det"], o["na_ill"] + tilt)
+    if "fluor" in kinds:
+        R = max(R, 2 * o["na_det"])
+    r = R / lam * o["pixel_um"] + 2.0 / X
+    kx = np.arange(X // 2 + 1) / X
+    return int(np.sum(kx ** 2 <= r * r))
 
 
 def support_xcols(o, kinds, X):
@@ -719,16 +737,21 @@ def field_algorithmic_bytes(o_list, Z, E, field_vox):
     for runs that use it.)"""
     Xh = E // 2 + 1
     real, half = Z * E * E * 4, Z * E * Xh * 8
-    out = {k: 0 for k in ("tf_pupil_record", "tf_arms", "tf_psf_rows", "tf_ypass", "tf_zpass", "rows_r2c", "y_fwd",
-                          "xy_fwd", "z_fused", "y_inv", "rows_c2r", "xy_inv")}
+    out = {k: 0 for k in ("tf_pupil_record", "tf_arms", "tf_psf_rows", "tf_ypass", "tf_zpass", "tf_yz", "rows_r2c",
+                          "y_fwd", "xy_fwd", "z_fused", "yz_op", "y_inv", "rows_c2r", "xy_inv")}
     for o in o_list:
         arms = 2 * Z * E * band_columns(o, E) * 8
         inside = Z * support_columns(o, ("phase",), E, E) * 8
+        planes_in = support_planes(o, ("phase",), E)
         out["tf_pupil_record"] += E * E * 16
         out["tf_arms"] += arms
         out["tf_psf_rows"] += arms + half
         out["tf_ypass"] += 2 * half
         out["tf_zpass"] += 2 * half
+        out["tf_yz"] += 2 * half  # the plane engine: every TF plane in and out once
+        # the plane engine's operator pass: the data planes inside the support
+        # disk in, the TF columns inside it in, every plane out
+        out["yz_op"] += planes_in * Z * E * 8 + inside + half
         out["rows_r2c"] += real + half
         out["y_fwd"] += 2 * half
         out["xy_fwd"] += real + half
@@ -820,15 +843,26 @@ def field_leg(args, rank, world, local_rank):
     if not args.default_engines:
         B.wo_autotune(n, Z, E, E, ("phase",), ws)
     pin_rows_engine(args, B, E // 2)
+    # planes: a kx-major phase bank (WO_TF_KX_MAJOR), whose build and
+    # reconstruction run their y and z transforms (and the operator between
+    # them) one (tile, k_x) plane per CTA; passes: the standard bank and the
+    # separate y pass, z pass and inverse y pass
+    field_kinds = {"planes": B.WO_TF_PHASE | B.WO_TF_KX_MAJOR, "passes": B.WO_TF_PHASE}
 
-    def step_on(fld, dst, tl, rc, tfb, wsb, opt):
-        # the reconstruction's first pass reads each tile's rows from the field
-        # (wo_reconstruct_field_tiles: the same tiles wo_tile_gather would copy);
-        # the separate blend is faster than wo_restore_field's fused last pass
-        B.wo_build_tf_device(opt, n, Z, E, E, ("phase",), tfb, wsb)
-        B.wo_reconstruct_field_tiles(tfb, ("phase",), fld, Z, ty, tx, TILE_CORE, TILE_HALO, None, [1e-3],
-                                     B.WO_ETA_RELATIVE, B.WO_MODE_3D, rc, wsb)
-        B.wo_tile_blend(rc, Z, ty, tx, TILE_CORE, TILE_HALO, dst)
+    def make_step_on(kinds):
+        def step_on(fld, dst, tl, rc, tfb, wsb, opt):
+            # the reconstruction's first pass reads each tile's rows from the field
+            # (wo_reconstruct_field_tiles: the same tiles wo_tile_gather would copy);
+            # the separate blend is faster than wo_restore_field's fused last pass
+            B.wo_build_tf_device(opt, n, Z, E, E, kinds, tfb, wsb)
+            B.wo_reconstruct_field_tiles(tfb, kinds, fld, Z, ty, tx, TILE_CORE, TILE_HALO, None, [1e-3],
+                                         B.WO_ETA_RELATIVE, B.WO_MODE_3D, rc, wsb)
+            B.wo_tile_blend(rc, Z, ty, tx, TILE_CORE, TILE_HALO, dst)
+        return step_on
+
+    step_on = make_step_on(field_kinds[args.field_engine])
+    other_engine = "passes" if args.field_engine == "planes" else "planes"
+    other_step_on = make_step_on(field_kinds[other_engine])
 
     def step():
         step_on(field, out, tiles, rec, tf, ws, optics)
@@ -863,17 +897,17 @@ def field_leg(args, rank, world, local_rank):
     # per-kernel times from eager profiled steps (the events do not enter a graph)
     with torch.cuda.stream(s):
         prof = profiled_pass(B, step, args.steps)
-    def alt_step_ms(pass_, engine):
+    def alt_step_ms(pass_, engine, step_fn=step):
         """The step timed the same way with one schedule entry pinned (context
         for the engine choices); the entry is restored afterwards."""
         saved = B.wo_schedule_get(pass_, E)
         B.wo_schedule_set(pass_, E, engine)
         g5 = torch.cuda.CUDAGraph()
         with torch.cuda.stream(s):
-            step()
+            step_fn()
         torch.cuda.synchronize()
         with torch.cuda.graph(g5, stream=s):
-            step()
+            step_fn()
         B.wo_schedule_set(pass_, E, saved)
         for _ in range(args.warmup):
             g5.replay()
@@ -888,9 +922,16 @@ def field_leg(args, rank, world, local_rank):
 
     # the reconstruction on the persistent tile pipeline instead of the five
     # passes, and the x-y transforms as separate passes instead of fused
-    pipe_ms = alt_step_ms(B.WO_PASS_RECON, B.WO_ENGINE_HYBRID)
+    # (the other field engine; with the passes, also the persistent tile
+    # pipeline instead of the five passes and the other x-y engine)
+    def other_step():
+        other_step_on(field, out, tiles, rec, tf, ws, optics)
+
+    passes_step = step if args.field_engine == "passes" else other_step
+    other_ms = alt_step_ms(B.WO_PASS_RECON, B.wo_schedule_get(B.WO_PASS_RECON, E), other_step)
+    pipe_ms = alt_step_ms(B.WO_PASS_RECON, B.WO_ENGINE_HYBRID, passes_step)
     other_xy = B.WO_ENGINE_SMEM if B.wo_schedule_get(B.WO_PASS_XY, E) == B.WO_ENGINE_HYBRID else B.WO_ENGINE_HYBRID
-    xy_ms = alt_step_ms(B.WO_PASS_XY, other_xy)
+    xy_ms = alt_step_ms(B.WO_PASS_XY, other_xy, passes_step)
     code = B.wo_sync_status(ws)
     vox = float(field.numel())
     kern = kernel_table(prof, field_algorithmic_bytes(o_list, Z, E, vox), "launches")
@@ -911,8 +952,10 @@ def field_leg(args, rank, world, local_rank):
         "roofline": roofline_of(kern, prof, "field" if (ty, tx) == (16, 16) else None), "kernels": kern,
         "gpu_launches": int(per_step_launches * args.steps), "clocks": clk,
         "e2e": e2e,
-        "recon_engine": {"engine": engines_recon(E), "step_ms_with_tile_pipeline": round(pipe_ms, 4),
-                         "xy": engines_xy(E), "step_ms_with_other_xy_engine": round(xy_ms, 4),
+        "recon_engine": {"field_engine": args.field_engine,
+                         f"step_ms_with_{other_engine}": round(other_ms, 4),
+                         "passes": {"engine": engines_recon(E), "step_ms_with_tile_pipeline": round(pipe_ms, 4),
+                                    "xy": engines_xy(E), "step_ms_with_other_xy_engine": round(xy_ms, 4)},
                          "device_status": list(code)},
     }
     if not args.no_cpu_baseline:
@@ -1628,6 +1671,9 @@ def main():
     ap.add_argument("--default-engines", action="store_true",
                     help="skip the engine autotuner (built-in engine choices; for runs under a profiler, whose "
                          "serialised launches would mislead the autotuner's timings)")
+    ap.add_argument("--field-engine", choices=["planes", "passes"], default="planes",
+                    help="field step: kx-major TF bank and one y-z pass per (tile, k_x) plane (planes), or the "
+                         "standard bank and separate y, z and inverse y passes (passes); the other is timed as context")
     ap.add_argument("--est-train", type=int, default=EST_TRAIN, help="estimator training tiles")
     ap.add_argument("--est-epochs", type=int, default=12, help="estimator training epochs")
     ap.add_argument("--est-test", type=int, default=EST_TEST, help="estimator test tiles")

@@ -109,6 +109,22 @@ enum { WO_TF_SMOOTH_SOURCE = 32 };
  * A_theta = (dS/dtheta) P e^{...}, D_theta = sum (dS/dtheta) P^2, through
  * Table 1 unchanged.  X must be 32, 48, 64, 96, 128, 192 or 256. */
 enum { WO_TF_PHASE_GRAD = 64 };
+/* Or-ed with exactly one of WO_TF_PHASE, WO_TF_ABSORPTION, WO_TF_FLUOR (and
+ * optionally WO_TF_SMOOTH_SOURCE): the bank's half spectra are stored
+ * kx-major, [n_tiles][1][X/2+1][Z][Y] complex64 (the Z x Y plane of every
+ * half-spectrum column k_x contiguous; same size, same statistics block).
+ * The build then runs its y and z transforms, and a reconstruction with such
+ * a bank its y and z transforms and the Tikhonov inverse between them, as one
+ * pass per (tile, k_x) plane on the chip (TMA bulk copies of the plane into
+ * shared memory; one trip through HBM instead of three), and the x passes
+ * transpose on the way in and out.  Supported for Z = 32 or 48, Y = 64, 128
+ * or 192 and X = 64, 128 or 192 (else WO_ERR_UNSUPPORTED_SIZE).  Accepted by
+ * wo_build_tf, wo_build_tf_device and, in WO_MODE_3D, by
+ * wo_reconstruct_field_tiles (the tiles must be square, E = Y = X); every
+ * other operator rejects such a bank (WO_ERR_ARG).  The plane kernels wait
+ * for their copies with a bound; a wait that runs out records WO_ERR_TIMEOUT
+ * in the workspace's status block (wo_sync_status). */
+enum { WO_TF_KX_MAJOR = 128 };
 enum { WO_MODE_3D = 0, WO_MODE_2D = 1 };
 enum { WO_ETA_RELATIVE = 0, WO_ETA_ABSOLUTE = 1 };
 

@@ -22,6 +22,7 @@ WO_TF_PHASE_DZ = 8
 WO_TF_PLANES = 16
 WO_TF_SMOOTH_SOURCE = 32
 WO_TF_PHASE_GRAD = 64
+WO_TF_KX_MAJOR = 128
 WO_MODE_3D, WO_MODE_2D = 0, 1
 WO_ETA_RELATIVE, WO_ETA_ABSOLUTE = 0, 1
 WO_LOSS_DATA, WO_LOSS_MIDBAND = 0, 1
@@ -31,7 +32,7 @@ WO_MAX_ZERNIKE = 36
 WO_PAD_ZERO, WO_PAD_MIRROR, WO_PAD_EDGE = 0, 1, 2
 KIND_BITS = {"phase": WO_TF_PHASE, "absorption": WO_TF_ABSORPTION, "fluor": WO_TF_FLUOR,
              "phase_dz": WO_TF_PHASE_DZ, "planes": WO_TF_PLANES, "smooth_source": WO_TF_SMOOTH_SOURCE,
-             "phase_grad": WO_TF_PHASE_GRAD}
+             "phase_grad": WO_TF_PHASE_GRAD, "kx_major": WO_TF_KX_MAJOR}
 STATUS = {0: "WO_OK", 1: "WO_ERR_ARG", 2: "WO_ERR_SHAPE", 3: "WO_ERR_UNSUPPORTED_SIZE",
           4: "WO_ERR_UNDERSAMPLED", 5: "WO_ERR_CUDA", 6: "WO_ERR_TIMEOUT", 7: "WO_ERR_OPTICS",
           8: "WO_ERR_WORKSPACE", 9: "WO_ERR_BOUNDS"}
@@ -467,15 +468,20 @@ def wo_launch_count() -> int:
 
 # ------------------------------------------------------------- views
 def tf_views(tf, n_tiles, Z, Y, X, kinds):
-    """(spectra, stats) views of a TF bank tensor: complex64 [n][k][Z][Y][X/2+1], float32 [n][8]."""
+    """(spectra, stats) views of a TF bank tensor: complex64 [n][k][Z][Y][X/2+1], float32 [n][8].
+    A kx-major bank's spectra are stored [n][k][X/2+1][Z][Y]; the view is
+    permuted back to [n][k][Z][Y][X/2+1] (not contiguous)."""
     import torch
     m = kinds_mask(kinds)
-    core = m & ~(WO_TF_PLANES | WO_TF_SMOOTH_SOURCE)
+    core = m & ~(WO_TF_PLANES | WO_TF_SMOOTH_SOURCE | WO_TF_KX_MAJOR)
     nk = 2 if core == WO_TF_PHASE_DZ else (5 if core == WO_TF_PHASE_GRAD else bin(core).count("1"))
     Xh = X // 2 + 1
     n_spec = n_tiles * nk * Z * Y * Xh
     raw = tf.view(torch.uint8)
-    spec = raw[: n_spec * 8].view(torch.complex64).view(n_tiles, nk, Z, Y, Xh)
+    if m & WO_TF_KX_MAJOR:
+        spec = raw[: n_spec * 8].view(torch.complex64).view(n_tiles, nk, Xh, Z, Y).permute(0, 1, 3, 4, 2)
+    else:
+        spec = raw[: n_spec * 8].view(torch.complex64).view(n_tiles, nk, Z, Y, Xh)
     off = ((n_spec * 8 + 255) // 256) * 256
     stats = raw[off: off + n_tiles * 32].view(torch.float32).view(n_tiles, 8)
     return spec, stats

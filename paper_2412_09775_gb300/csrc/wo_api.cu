@@ -65,6 +65,7 @@ static bool size_ok(int n) {
 struct Sys {
   int n_kinds, lf_props, has_fl, C, P, n_arms;
   int want_phase, want_abs, want_dz, planes, want_grad, smooth;
+  int kxm;    // kx-major bank (WO_TF_KX_MAJOR)
   int aberr;  // aberrated detection pupil (wo_build_tf_aberrated): set by the caller, not by kinds
 };
 
@@ -79,7 +80,8 @@ static Sys system_of(unsigned kinds) {
   s.P = s.n_kinds;
   s.n_arms = (s.lf_props ? 2 : 0) + s.has_fl;
   s.smooth = (kinds & WO_TF_SMOOTH_SOURCE) ? 1 : 0;
-  const unsigned core = kinds & ~(unsigned)(WO_TF_PLANES | WO_TF_SMOOTH_SOURCE);
+  s.kxm = (kinds & WO_TF_KX_MAJOR) ? 1 : 0;
+  const unsigned core = kinds & ~(unsigned)(WO_TF_PLANES | WO_TF_SMOOTH_SOURCE | WO_TF_KX_MAJOR);
   if (core == WO_TF_PHASE_GRAD) {  // phase TF and d/d(z0, tilt_x, tilt_y, NA_ill): five slots, seven arms
     s.want_phase = 1;
     s.want_dz = 1;
@@ -165,8 +167,12 @@ static size_t zpass_smem(int Z) {
 
 static wo_status check_shape(int n_tiles, int Z, int Y, int X, unsigned kinds) {
   if (n_tiles < 1 || n_tiles > 65535) return WO_ERR_ARG;
-  if (kinds & ~127u) return WO_ERR_ARG;
-  const unsigned base = kinds & ~(unsigned)(WO_TF_PLANES | WO_TF_SMOOTH_SOURCE);
+  if (kinds & ~255u) return WO_ERR_ARG;
+  const bool kxm = (kinds & WO_TF_KX_MAJOR) != 0;
+  const unsigned base = kinds & ~(unsigned)(WO_TF_PLANES | WO_TF_SMOOTH_SOURCE | WO_TF_KX_MAJOR);
+  // kx-major banks: one kind, 3D TFs
+  if (kxm && ((kinds & WO_TF_PLANES) || (base != WO_TF_PHASE && base != WO_TF_ABSORPTION && base != WO_TF_FLUOR)))
+    return WO_ERR_ARG;
   if (base == 0) return WO_ERR_ARG;
   if ((base & WO_TF_PHASE_DZ) && base != WO_TF_PHASE_DZ) return WO_ERR_ARG;
   if ((base & WO_TF_PHASE_GRAD) && base != WO_TF_PHASE_GRAD) return WO_ERR_ARG;
@@ -181,6 +187,9 @@ static wo_status check_shape(int n_tiles, int Z, int Y, int X, unsigned kinds) {
   if (base == WO_TF_PHASE_DZ && X > 768) return WO_ERR_UNSUPPORTED_SIZE;
   // the seven arms of the gradient bank need the register-resident row pass
   if (base == WO_TF_PHASE_GRAD && !(X == 32 || X == 48 || X == 64 || X == 96 || X == 128 || X == 192 || X == 256))
+    return WO_ERR_UNSUPPORTED_SIZE;
+  // the plane engine's shapes, and PSF-row and x-pass CTAs whose rows stay inside a plane
+  if (kxm && !(plane_supported(Z, Y) && psf_kxm_supported(X, Y) && rows_kxm_supported(X / 2, Y)))
     return WO_ERR_UNSUPPORTED_SIZE;
   return WO_OK;
 }
@@ -400,6 +409,7 @@ static wo_status build_tf_impl(const wo_optics* optics, bool on_host, int n_tile
   a.norm_part = (float*)(ws + L.norm_part);
   a.norms = (float*)(ws + L.norms);
   a.rec_blocks = (Y + record_rows(Y, n_tiles) - 1) / record_rows(Y, n_tiles);
+  a.kxm = s.kxm;
   // Columns k_x beyond the largest TF support radius of the batch hold only
   // the PSF rows' rounding noise: the y and z passes leave them out.  The
   // radius: H1(q) needs nu in S and P and nu + q in P; the fluorescence TF and
@@ -430,6 +440,7 @@ static wo_status build_tf_impl(const wo_optics* optics, bool on_host, int n_tile
   a.row_begin = 0;
   a.row_end = (long long)n_tiles * Z * Y;
   WO_TRY(tf_psf_rows(a, cs));
+  if (s.kxm) return cuda_status(tf_plane_yz(a, (int*)(ws + L.status), cs));  // y and z transforms, plane by plane
   const int Xh = X / 2 + 1;
   WO_TRY(cols_c2c(Y, false, a.tf, Xh, (long long)Y * Xh, a.x_cols, (long long)n_tiles * s.n_kinds * Z, cs,
                   "tf_ypass"));
@@ -502,6 +513,8 @@ static wo_status run_op(int op, const void* d_tf, unsigned kinds, const float* d
   if (fout) d_out = fout->field;
   if (!aligned16(d_tf) || !aligned16(d_in) || !aligned16(d_out) || !aligned16(d_ws)) return WO_ERR_ARG;
   const Sys s = system_of(kinds);
+  // a kx-major bank serves the 3D reconstruction of a field's square tiles only
+  if (s.kxm && (op != 2 || mode != WO_MODE_3D || !field || fout || X != Y)) return WO_ERR_ARG;
   if (op == 2) {
     if (!h_eta) return WO_ERR_ARG;
     if (eta_flag != WO_ETA_RELATIVE && eta_flag != WO_ETA_ABSOLUTE) return WO_ERR_ARG;
@@ -573,6 +586,18 @@ static wo_status run_op(int op, const void* d_tf, unsigned kinds, const float* d
     return cuda_status(tile_pipeline(p, cs));
   }
   const long long in_rows = (long long)n_tiles * n_in * Z * Y;
+  if (s.kxm) {
+    // kx-major bank: the field's tiles through the plane engine; the
+    // spectrum stays in specA throughout
+    WO_TRY(rows_r2c_field_kxm(H, *field, specA, in_rows, bg_in, cs));
+    WO_TRY(plane_yz_op(Z, Y, specA, tf, zo, n_tiles, Xh, (int*)(ws + L.status), cs));
+    RowBg none{};
+    none.rows_per_block = (long long)Z * Y;
+    none.nchan = 1;
+    const float scale = (float)(2.0 / ((double)X * (double)Y * (double)Z));
+    WO_TRY(rows_c2r_kxm(H, specA, d_out, in_rows, Z, Y, scale, none, cs));
+    return WO_OK;
+  }
   if (field) {  // the x pass reads the tiles from the field, then the y pass
     WO_TRY(rows_r2c_field(H, *field, specA, in_rows, bg_in, cs));
     WO_TRY(cols_c2c(Y, false, specA, Xh, (long long)Y * Xh, Xh, in_rows / Y, cs, "y_fwd"));

@@ -106,6 +106,10 @@ cudaError_t z_fused_reg(int Z, const float2* in, float2* out, const float2* tf, 
 // out: [tile][P][Y][Xh].
 cudaError_t z_solve2d(int Z, const float2* in, float2* out, const float2* tf, ZOp op, int n_tiles,
                       int Y, int Xh, cudaStream_t s);
+// The plane engine (wo_plane.cu) on a kx-major spectrum, in place: one
+// volume in and out, one TF slot (kx-major bank).
+cudaError_t plane_yz_op(int Z, int Y, float2* spec, const float2* tf, const ZOp& op, int n_tiles, int Xh,
+                        int* status, cudaStream_t s);
 
 // The device status block at the start of every workspace: int32 code (a
 // wo_status, 0 while nothing went wrong), site, detail; the rest reserved.
@@ -178,6 +182,7 @@ struct TfArgs {
   float* norms;             // [n_tiles][4]: sum S P, then sum dS/dtheta P (smooth source)
   int rec_blocks;           // record blocks per tile
   long long row_begin, row_end;  // PSF-row pass: rows (t*Z + j)*Y + y in [begin, end)
+  int kxm;                  // the bank is kx-major, [n_tiles][n_kinds][Xh][Z][Y] (WO_TF_KX_MAJOR)
 };
 cudaError_t tf_pupil_record(const TfArgs& a, cudaStream_t s);
 int record_rows(int Y, int n_tiles);  // rows per pupil-record block
@@ -190,6 +195,16 @@ cudaError_t tf_psf_rows(const TfArgs& a, cudaStream_t s);
 // transforms (wo_zreg.cu).
 bool tf_zpass_reg_supported(const TfArgs& a);
 cudaError_t tf_zpass_reg(const TfArgs& a, cudaStream_t s);
+// kx-major banks and spectra (WO_TF_KX_MAJOR; [block][Xh][Z][Y] complex):
+// PSF rows of length X whose pair kernel writes them (a lane's row pair
+// inside a plane of Y rows) (wo_psf.cu); the plane engine's shapes and
+// kernels (wo_plane.cu): the TF build's y and z transforms with the
+// regulariser maxima, and the y and z transforms with a one-volume operator
+// between them, in place; status: the workspace's status block (bounded
+// waits on the planes' bulk copies).
+bool psf_kxm_supported(int X, int Y);
+bool plane_supported(int Z, int Y);
+cudaError_t tf_plane_yz(const TfArgs& a, int* status, cudaStream_t s);
 // Hybrid column engine (wo_colhyb.cu) and the schedule table (wo_sched.cu).
 bool cols_hyb_supported(int N);
 cudaError_t cols_c2c_hyb(int N, bool inverse, float2* data, long long col_stride, long long plane_stride, int ncols,
@@ -220,6 +235,14 @@ struct FieldSrc {
   int Z, tiles_y, tiles_x, core, halo;
 };
 cudaError_t rows_r2c_field(int N, const FieldSrc& f, float2* out, long long nrows, RowBg bg, cudaStream_t s);
+// kx-major x passes (wo_rowsreg.cu): real rows of 2N points, Y rows per plane;
+// supported for N = 32, 64, 96 when a warp's rows (32 / T) divide Y.  The
+// forward pass reads the tiles of a field (out: [tile][N+1][Z][2N]); the
+// inverse writes real rows [block][Z][Y][2N] from [block][N+1][Z][Y].
+bool rows_kxm_supported(int N, int Y);
+cudaError_t rows_r2c_field_kxm(int N, const FieldSrc& f, float2* out, long long nrows, RowBg bg, cudaStream_t s);
+cudaError_t rows_c2r_kxm(int N, const float2* in, float* out, long long nrows, int Z, int Y, float scale, RowBg bg,
+                         cudaStream_t s);
 // The inverse x pass of a field's tiles fused with their blend into the
 // field (wo_rowsreg.cu): field [P][Z][tiles_y core][tiles_x core], the same
 // values as the inverse x pass into tiles followed by wo_tile_blend.

@@ -48,6 +48,7 @@ template <int N1>
 __device__ __forceinline__ float2 mirror_value(const float2 (&v)[N1], int m, bool lane0) {
   return lane0 ? v[(N1 - m) % N1] : v[N1 - 1 - m];
 }
+
 }  // namespace
 
 // P: the row transform (Row2 or Row512 of wo_regfft.cuh).  MODE 0: any mix
@@ -226,7 +227,13 @@ __global__ void __launch_bounds__(kPsfThreads, (P::E > 16 && MODE == 2) ? 2 : 4)
 // row waits in shared memory (each lane reads back only what it wrote) while
 // the second is formed.  The two rows may belong to different tiles when Z*Y
 // is odd; everything per row is formed per row.
-template <class P, int LF>  // LF: label-free kinds wanted (0, 1 or 2)
+//
+// KXM: the bank is kx-major, [tile][kind][k][j][y] (the plane engine's
+// layout, wo_plane.cu): a lane stores bin k of its two rows (y, y + 1 of one
+// plane, y even) as one 16-byte pair straight from registers; the lane
+// groups of a warp hold consecutive row pairs, so a warp store fills a run
+// of 2 * 32/T points of each of T bins (whole 32-byte sectors).
+template <class P, int LF, bool KXM>  // LF: label-free kinds wanted (0, 1 or 2)
 __global__ void __launch_bounds__(kPsfThreads, P::E > 16 ? 3 : 4) k_psf_rows_pair(TfArgs a) {
   constexpr int N = P::N, N1 = P::E, T = P::T, RP = P::SLICE, RPC = kPsfThreads / T;
   // held-row pitch = T mod 32: the rows of one warp start on distinct banks
@@ -296,6 +303,23 @@ __global__ void __launch_bounds__(kPsfThreads, P::E > 16 ? 3 : 4) k_psf_rows_pai
   // one forward transform of w = h0 + i h1 into TF slot `slot` of both rows
   auto store_pair = [&](int slot) {
     P::template fft<false>(w, tw, S, lt);
+    if constexpr (KXM) {
+      // rows r0, r0 + 1: one plane (Y even), bin k of both at dk + k Z Y
+      float2* dk = a.tf + ((t0 * a.n_kinds + slot) * Xh * a.Z) * (long long)a.Y + rem0;
+      const long long kz = (long long)a.Z * a.Y;
+#pragma unroll
+      for (int m = 0; m < N1; ++m) {
+        const float2 mv = mirror_value<N1>(w, m, lane0);
+        float2 c;  // conj(W(N - k))
+        c.x = __shfl_sync(0xffffffffu, mv.x, partner);
+        c.y = -__shfl_sync(0xffffffffu, mv.y, partner);
+        const int k = lt + T * m;
+        if (k > N / 2 || !live1) continue;
+        *reinterpret_cast<float4*>(dk + k * kz) = make_float4(0.5f * (w[m].x + c.x), 0.5f * (w[m].y + c.y),
+                                                              0.5f * (w[m].y - c.y), -0.5f * (w[m].x - c.x));
+      }
+      return;
+    }
 #pragma unroll
     for (int m = 0; m < N1; ++m) {
       const float2 mv = mirror_value<N1>(w, m, lane0);
@@ -367,13 +391,26 @@ static cudaError_t launch_psf_pair(const TfArgs& a, cudaStream_t s) {
   constexpr int RPC = kPsfThreads / P::T;
   const long long pairs = (a.row_end - a.row_begin + 1) / 2;
   const unsigned grid = (unsigned)((pairs + RPC - 1) / RPC);
+  if (a.kxm) {  // one kind, Y even (checked by the caller)
+    if constexpr (P::N == 64 || P::N == 128 || P::N == 192) {
+      if (a.lf_props == 0) WO_LAUNCH("tf_psf_rows", s, (k_psf_rows_pair<P, 0, true><<<grid, kPsfThreads, 0, s>>>(a)));
+      else WO_LAUNCH("tf_psf_rows", s, (k_psf_rows_pair<P, 1, true><<<grid, kPsfThreads, 0, s>>>(a)));
+      return cudaGetLastError();
+    }
+    return cudaErrorInvalidValue;
+  }
   switch (a.lf_props) {
-    case 0: WO_LAUNCH("tf_psf_rows", s, (k_psf_rows_pair<P, 0><<<grid, kPsfThreads, 0, s>>>(a))); break;
-    case 1: WO_LAUNCH("tf_psf_rows", s, (k_psf_rows_pair<P, 1><<<grid, kPsfThreads, 0, s>>>(a))); break;
-    default: WO_LAUNCH("tf_psf_rows", s, (k_psf_rows_pair<P, 2><<<grid, kPsfThreads, 0, s>>>(a))); break;
+    case 0: WO_LAUNCH("tf_psf_rows", s, (k_psf_rows_pair<P, 0, false><<<grid, kPsfThreads, 0, s>>>(a))); break;
+    case 1: WO_LAUNCH("tf_psf_rows", s, (k_psf_rows_pair<P, 1, false><<<grid, kPsfThreads, 0, s>>>(a))); break;
+    default: WO_LAUNCH("tf_psf_rows", s, (k_psf_rows_pair<P, 2, false><<<grid, kPsfThreads, 0, s>>>(a))); break;
   }
   return cudaGetLastError();
 }
+
+// Row lengths X whose PSF-row pair kernel writes kx-major banks (the
+// instantiated ones), and whether a lane's row pair stays inside a plane of
+// Y rows (Y even).
+bool psf_kxm_supported(int X, int Y) { return (X == 64 || X == 128 || X == 192) && Y % 2 == 0; }
 
 template <class P, int MODE>
 static cudaError_t launch_psf_reg(const TfArgs& a, cudaStream_t s) {

@@ -106,7 +106,13 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_c2r_reg(const float2* __re
 // samples mirror(tx core - halo + x); a tile whose columns lie inside the
 // field reads them as pairs, a border tile one mirrored sample at a time.
 // The mode-2 background is the tile's first sample, as for a gathered tile.
-template <class P>
+//
+// KXM: the output is kx-major, [tile][k][z][u] (the plane engine's layout,
+// wo_plane.cu): each lane stores its row's bins straight from registers; the
+// 32/T rows of a warp are consecutive rows u of one plane, so a warp store
+// of one register fills a run of 32/T points of each of T bins (whole
+// 32-byte sectors).
+template <class P, bool KXM>
 __global__ void __launch_bounds__(kRowThreads) k_rows_r2c_field(FieldSrc f, float2* __restrict__ out, long long nrows,
                                                                  RowBg bg) {
   using G = RowRegGeom<P>;
@@ -151,19 +157,83 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_r2c_field(FieldSrc f, floa
 #pragma unroll
   for (int m = 0; m < E; ++m) v[m] = make_float2(v[m].x - c, v[m].y - c);
   P::template fft<false>(v, tw, S, t);
-  float2* o = out + rr * (N + 1);
-  r2c_split<N, T, E>(v, tw2, t, [&](int k, float2 val) {
-    if (live) o[k] = val;
-  });
+  if constexpr (KXM) {
+    float2* o = out + (tile * (N + 1) * f.Z + z) * (long long)W + u;  // bin k at o + k Z W
+    const long long kstep = (long long)f.Z * W;
+    r2c_split<N, T, E>(v, tw2, t, [&](int k, float2 val) {
+      if (live) o[k * kstep] = val;
+    });
+  } else {
+    float2* o = out + rr * (N + 1);
+    r2c_split<N, T, E>(v, tw2, t, [&](int k, float2 val) {
+      if (live) o[k] = val;
+    });
+  }
+}
+
+template <class P, bool KXM>
+cudaError_t launch_r2c_field(const FieldSrc& f, float2* out, long long nrows, RowBg bg, cudaStream_t s) {
+  using G = RowRegGeom<P>;
+  const cudaError_t attr = allow_smem(k_rows_r2c_field<P, KXM>, G::SMEM);
+  if (attr != cudaSuccess) return attr;
+  const long long blocks = (nrows + G::RPC - 1) / G::RPC;
+  WO_LAUNCH("rows_r2c", s,
+            (k_rows_r2c_field<P, KXM><<<(unsigned)blocks, kRowThreads, G::SMEM, s>>>(f, out, nrows, bg)));
+  return cudaGetLastError();
+}
+
+// The inverse x pass from a kx-major half spectrum [block][k][z][y] (the
+// plane engine's layout) to real rows [block][z][y][2N], as
+// k_rows_c2r_reg: each lane loads its row's bins straight into registers;
+// the 32/T rows of a warp are consecutive rows y of one plane (32/T divides
+// Y), so a warp load of one register reads a run of 32/T points of each of
+// T bins (whole 32-byte sectors).
+template <class P>
+__global__ void __launch_bounds__(kRowThreads) k_rows_c2r_kxm(const float2* __restrict__ in, float* __restrict__ out,
+                                                               long long nrows, int Z, int Y, float scale, RowBg bg) {
+  using G = RowRegGeom<P>;
+  constexpr int N = G::N, T = G::T, E = G::E, RPC = G::RPC;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* tw2 = sm + P::TW;
+  const int t = threadIdx.x % T, r = threadIdx.x / T;
+  float2* S = sm + P::TW + 2 * N + r * P::SLICE;
+  const long long row = (long long)blockIdx.x * RPC + r;
+  const bool live0 = row < nrows;
+  long long rr = live0 ? row : nrows - 1;
+  const bool inside = WO_IN(rr, nrows, 7);
+  if (!inside) rr = 0;
+  const bool live = live0 && inside;
+  const long long plane_rows = (long long)Z * Y;
+  const long long blk = rr / plane_rows, rem = rr - blk * plane_rows;  // rem = z Y + y
+  const long long kstep = plane_rows;                                     // bin k of the row at src + k Z Y
+  const float2* src = in + blk * (N + 1) * plane_rows + rem;
+  float2 x[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) x[m] = __ldg(src + (t + T * m) * kstep);
+  const float2 xn = t == 0 ? __ldg(src + N * kstep) : make_float2(0.f, 0.f);  // X[N], partner of X[0]
+  P::twiddles(tw);  // while the row's loads are in flight
+  make_twiddles<2 * N>(tw2);
+  __syncthreads();
+  float2 v[E];
+  c2r_merge<T, E>(x, xn, tw2, t, v);
+  P::template fft<true>(v, tw, S, t);
+  if (!live) return;
+  const float cst = bg.mode == 1 ? bg.v[((bg.row_offset + rr) / bg.rows_per_block) % bg.nchan] : 0.f;
+  float2* o = reinterpret_cast<float2*>(out + rr * (2LL * N)) + t;
+#pragma unroll
+  for (int m = 0; m < E; ++m) o[T * m] = make_float2(v[m].x * scale + cst, v[m].y * scale + cst);
 }
 
 template <class P>
-cudaError_t launch_r2c_field(const FieldSrc& f, float2* out, long long nrows, RowBg bg, cudaStream_t s) {
+cudaError_t launch_c2r_kxm(const float2* in, float* out, long long nrows, int Z, int Y, float scale, RowBg bg,
+                           cudaStream_t s) {
   using G = RowRegGeom<P>;
-  const cudaError_t attr = allow_smem(k_rows_r2c_field<P>, G::SMEM);
+  const cudaError_t attr = allow_smem(k_rows_c2r_kxm<P>, G::SMEM);
   if (attr != cudaSuccess) return attr;
   const long long blocks = (nrows + G::RPC - 1) / G::RPC;
-  WO_LAUNCH("rows_r2c", s, (k_rows_r2c_field<P><<<(unsigned)blocks, kRowThreads, G::SMEM, s>>>(f, out, nrows, bg)));
+  WO_LAUNCH("rows_c2r", s,
+            (k_rows_c2r_kxm<P><<<(unsigned)blocks, kRowThreads, G::SMEM, s>>>(in, out, nrows, Z, Y, scale, bg)));
   return cudaGetLastError();
 }
 
@@ -320,14 +390,42 @@ cudaError_t rows_r2c_reg(int N, const float* in, float2* out, long long nrows, R
 cudaError_t rows_r2c_field(int N, const FieldSrc& f, float2* out, long long nrows, RowBg bg, cudaStream_t s) {
   if (nrows <= 0) return cudaSuccess;
   switch (N) {
-    case 32: return launch_r2c_field<Row2<32, 8>>(f, out, nrows, bg, s);
-    case 48: return launch_r2c_field<Row2<48, 12>>(f, out, nrows, bg, s);
-    case 64: return launch_r2c_field<Row2<64, 8>>(f, out, nrows, bg, s);
-    case 96: return launch_r2c_field<Row2<96, 24>>(f, out, nrows, bg, s);
-    case 128: return launch_r2c_field<Row2<128, 16>>(f, out, nrows, bg, s);
-    case 192: return launch_r2c_field<Row2<192, 24>>(f, out, nrows, bg, s);
-    case 256: return launch_r2c_field<Row2<256, 16>>(f, out, nrows, bg, s);
-    case 512: return launch_r2c_field<Row512>(f, out, nrows, bg, s);
+    case 32: return launch_r2c_field<Row2<32, 8>, false>(f, out, nrows, bg, s);
+    case 48: return launch_r2c_field<Row2<48, 12>, false>(f, out, nrows, bg, s);
+    case 64: return launch_r2c_field<Row2<64, 8>, false>(f, out, nrows, bg, s);
+    case 96: return launch_r2c_field<Row2<96, 24>, false>(f, out, nrows, bg, s);
+    case 128: return launch_r2c_field<Row2<128, 16>, false>(f, out, nrows, bg, s);
+    case 192: return launch_r2c_field<Row2<192, 24>, false>(f, out, nrows, bg, s);
+    case 256: return launch_r2c_field<Row2<256, 16>, false>(f, out, nrows, bg, s);
+    case 512: return launch_r2c_field<Row512, false>(f, out, nrows, bg, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+bool rows_kxm_supported(int N, int Y) {
+  const int rpw = N == 64 ? 32 / 8 : 32 / 4;  // rows per warp of the N-point row transform (8 or 4 lanes per row)
+  return (N == 32 || N == 64 || N == 96) && Y % rpw == 0;
+}
+
+cudaError_t rows_r2c_field_kxm(int N, const FieldSrc& f, float2* out, long long nrows, RowBg bg, cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  if (!rows_kxm_supported(N, 2 * N)) return cudaErrorInvalidValue;
+  switch (N) {
+    case 32: return launch_r2c_field<Row2<32, 8>, true>(f, out, nrows, bg, s);
+    case 64: return launch_r2c_field<Row2<64, 8>, true>(f, out, nrows, bg, s);
+    case 96: return launch_r2c_field<Row2<96, 24>, true>(f, out, nrows, bg, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t rows_c2r_kxm(int N, const float2* in, float* out, long long nrows, int Z, int Y, float scale, RowBg bg,
+                         cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  if (!rows_kxm_supported(N, Y) || nrows % ((long long)Z * Y)) return cudaErrorInvalidValue;  // whole planes
+  switch (N) {
+    case 32: return launch_c2r_kxm<Row2<32, 8>>(in, out, nrows, Z, Y, scale, bg, s);
+    case 64: return launch_c2r_kxm<Row2<64, 8>>(in, out, nrows, Z, Y, scale, bg, s);
+    case 96: return launch_c2r_kxm<Row2<96, 24>>(in, out, nrows, Z, Y, scale, bg, s);
     default: return cudaErrorInvalidValue;
   }
 }

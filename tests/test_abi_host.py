@@ -400,3 +400,40 @@ def test_restore_field_validation(B):
     assert call(1, 2, 65, 48, 8) == 1             # more than 64 tiles across
     assert call(1 | 4, 2, 2, 48, 8) == 1          # two data channels
     assert call(1, 2, 2, 52, 4) == 3              # E = 60: no 30-point register rows
+
+
+def test_kx_major_validation(B):
+    """WO_TF_KX_MAJOR: one kind, 3D TFs, the plane engine's shapes; same bank
+    size as the standard layout; the operators other than the field-tile 3D
+    reconstruction refuse it before launching anything."""
+    K = B.WO_TF_KX_MAJOR
+    for Z, E in ((48, 192), (48, 128), (48, 64), (32, 192), (32, 128), (32, 64)):
+        for kind in (1, 2, 4):
+            assert B.wo_tf_bytes(3, Z, E, E, kind | K) == B.wo_tf_bytes(3, Z, E, E, kind) > 0
+    assert B.wo_tf_bytes(1, 48, 192, 192, 1 | 32 | K) > 0          # smooth source
+    assert B.wo_tf_bytes(1, 48, 192, 192, 1 | 2 | K) == 0          # two kinds
+    assert B.wo_tf_bytes(1, 48, 192, 192, 8 | K) == 0              # derivative banks
+    assert B.wo_tf_bytes(1, 48, 192, 192, 8 | 16 | K) == 0
+    assert B.wo_tf_bytes(1, 48, 192, 192, K) == 0                  # no kind
+    assert B.wo_tf_bytes(1, 16, 64, 64, 1 | K) == 0                # Z outside the plane engine
+    assert B.wo_tf_bytes(1, 96, 192, 192, 1 | K) == 0
+    assert B.wo_tf_bytes(1, 48, 256, 256, 1 | K) == 0              # Y outside the plane engine
+    assert B.wo_tf_bytes(1, 48, 96, 96, 1 | K) == 0
+    assert B.wo_tf_bytes(1, 48, 192, 256, 1 | K) == 0              # 256-point PSF rows
+    assert B.wo_tf_bytes(1, 48, 192, 192, 1 | 256) == 0            # unknown bit
+    lib = B._lib
+    fake = 1 << 20
+    big = 1 << 40
+    eta = B._floats([1e-3, 1e-3])
+    n0 = lib.wo_launch_count()
+    m = 1 | K
+    assert lib.wo_reconstruct(fake, m, fake, None, eta[0], 0, 0, fake, 4, 32, 64, 64, fake, big, None) == 1
+    assert lib.wo_forward(fake, m, fake, None, fake, 4, 32, 64, 64, fake, big, None) == 1
+    assert lib.wo_forward_adjoint(fake, m, fake, None, fake, 4, 32, 64, 64, fake, big, None) == 1
+    assert lib.wo_reconstruct_field_tiles(fake, m, fake, 32, 2, 2, 48, 8, None, eta[0], 0, 1, fake, fake, big,
+                                          None) == 1               # 2D mode
+    assert lib.wo_restore_field(fake, m, fake, 32, 2, 2, 48, 8, None, eta[0], 0, 0, fake + 256, fake, big,
+                                None) == 1
+    assert lib.wo_reconstruct_field_tiles(fake, m, fake, 16, 2, 2, 48, 8, None, eta[0], 0, 0, fake, fake, big,
+                                          None) == 3               # Z = 16: no plane engine
+    assert lib.wo_launch_count() == n0
