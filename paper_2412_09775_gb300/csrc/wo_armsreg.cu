@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(ArmGeom<P>::NT) k_arms_reg(TfArgs a) {
     for (int i = 0; i < CH; ++i) {
       const int m = m0 + i;
       float s = 0.f, c = 0.f;
-      if (q[i].z != 0.f || q[i].w != 0.f) sincospif(2.0f * (phase_frac(q[i].x, q[i].y, zh, zl) + wv[i]), &s, &c);
+      if (q[i].z != 0.f || q[i].w != 0.f) unit_phasor(phase_frac(q[i].x, q[i].y, zh, zl) + wv[i], &s, &c);
       const float S = q[i].w, ie = q[i].z, in = ie != 0.f ? 1.f : 0.f;
       if (lf) {
         v[m] = make_float2(S * c, S * s);

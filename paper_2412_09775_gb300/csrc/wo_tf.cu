@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(ColGeom<N>::NT, (1024 / ColGeom<N>::NT) > 1 ? 
     const int e = threadIdx.x + i * NT;
     float ph = phase_frac(r[i].x, r[i].y, zh, zl);
     if (wrec && e < N * B && (e % B) < w) ph += __ldg(wrec + 4 * ((long long)(e / B) * X + e % B));
-    sincospif(2.0f * ph, &s_[i], &c_[i]);
+    unit_phasor(ph, &s_[i], &c_[i]);
   }
   // arms, in slot order: A, B (label-free), P (fluorescence), or
   // A, B, A' = i 2 pi eta A, B' = i 2 pi eta B (phase TF and its defocus

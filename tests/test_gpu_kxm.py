@@ -21,11 +21,18 @@ pytestmark = pytest.mark.gpu
 
 TOL = 1e-4      # against the float64 oracle (the parity bound of every GPU path)
 ENGINE = 2e-6   # between the two float32 engines (transform order only), relative eta 1e-3
-# With the absolute eta 1e-3 against max |H|^2 of order 1e2 the inverse is
-# about ten times worse conditioned (1 / (2 sqrt(eta / max |H|^2)) instead of
-# 1 / (2 sqrt(1e-3))), so the two banks' rounding differences (the TF build's
-# y and z transforms run in different orders) grow by about that much.
-ENGINE_ABS = 3e-5
+
+
+def engine_tol(flag, m3):
+    """Bound between the engines' reconstructions.  The Tikhonov inverse
+    multiplies a TF error by up to 1 / (2 sqrt(eta)) (times max |H|): with the
+    relative eta (eta = 1e-3 max |H|^2) that is 1 / (2 sqrt(1e-3)) whatever
+    the TF's scale, with the absolute eta 1e-3 it is max |H| = sqrt(m3) times
+    larger, so the two banks' rounding differences (their y and z transforms
+    run in different orders) grow by about that factor; twice the bound per
+    unit of gain, since the weakly regularised inverse brings a band of
+    frequencies near its peak gain, not one."""
+    return ENGINE if flag == 0 else 2.0 * ENGINE * max(1.0, float(np.sqrt(m3)))
 
 SHAPES = [(48, 192), (48, 128), (48, 64), (32, 192), (32, 128), (32, 64)]
 
@@ -103,13 +110,16 @@ def field_case(env, Z, ty, tx, core, halo, kinds, bg, flag, seed, device_optics)
     base = B.kinds_mask(kinds)
     eta = [1e-3]
     out = []
+    m3 = 0.0
     for m in (base, base | B.WO_TF_KX_MAJOR):
         tf, ws = build_bank(env, ol, Z, E, m, device_optics)
+        st = B.tf_views(tf, n, Z, E, E, m)[1].cpu().numpy()
+        m3 = max(m3, float(st[:, 2 if kinds == ("fluor",) else 0].max()))
         rec = torch.full((n, 1, Z, E, E), float("nan"), dtype=torch.float32, device=dev)
         B.wo_reconstruct_field_tiles(tf, m, field, Z, ty, tx, core, halo, bg, eta, flag, B.WO_MODE_3D, rec, ws)
         assert B.wo_sync_status(ws)[0] == 0
         out.append(rec.cpu().numpy()[:, 0])
-    return field_np, ol, out[0], out[1]
+    return field_np, ol, out[0], out[1], m3
 
 
 @pytest.mark.parametrize("geom", [(48, 2, 2, 128, 32), (48, 2, 3, 96, 16), (32, 3, 2, 48, 8), (32, 2, 2, 160, 16)])
@@ -120,10 +130,11 @@ def test_field_tiles_plane_engine(env, geom, bg, flag):
     B, torch, dev = env
     Z, ty, tx, core, halo = geom
     E = core + 2 * halo
-    field_np, ol, want, got = field_case(env, Z, ty, tx, core, halo, ("phase",), bg, flag, 11 + core, core % 3 == 0)
+    field_np, ol, want, got, m3 = field_case(env, Z, ty, tx, core, halo, ("phase",), bg, flag, 11 + core,
+                                             core % 3 == 0)
     assert np.all(np.isfinite(got))
     for t in range(ty * tx):
-        assert rel_l2(got[t], want[t]) <= (ENGINE if flag == 0 else ENGINE_ABS), t
+        assert rel_l2(got[t], want[t]) <= engine_tol(flag, m3), (t, m3)
     tiles = OT.gather(field_np.astype(np.float64), ty, tx, core, halo)
     for t in (0, ty * tx - 1):
         modes, _, _ = OM.widefield_system(OO.transfer_functions(ol[t], (Z, E, E), ("phase",)), ("phase",))
@@ -136,7 +147,7 @@ def test_field_tiles_plane_engine_other_kinds(env, kinds):
     B, torch, dev = env
     Z, ty, tx, core, halo = 32, 2, 2, 48, 8
     E = core + 2 * halo
-    field_np, ol, want, got = field_case(env, Z, ty, tx, core, halo, kinds, None, 0, 5, False)
+    field_np, ol, want, got, _ = field_case(env, Z, ty, tx, core, halo, kinds, None, 0, 5, False)
     tiles = OT.gather(field_np.astype(np.float64), ty, tx, core, halo)
     for t in range(ty * tx):
         assert rel_l2(got[t], want[t]) <= ENGINE, t
@@ -152,7 +163,7 @@ def test_field_workload_tiles_plane_engine(env):
     B, torch, dev = env
     Z, ty, tx, core, halo = 48, 4, 4, 128, 32
     E = core + 2 * halo
-    field_np, ol, want, got = field_case(env, Z, ty, tx, core, halo, ("phase",), None, 0, 3, True)
+    field_np, ol, want, got, _ = field_case(env, Z, ty, tx, core, halo, ("phase",), None, 0, 3, True)
     for t in range(ty * tx):
         assert rel_l2(got[t], want[t]) <= ENGINE, t
     tiles = OT.gather(field_np.astype(np.float64), ty, tx, core, halo)
