@@ -66,9 +66,10 @@ CPU_SAMPLE = (96, 256, 256)
 # capture), scaled by 4 to the 256 tiles of a launch of the bench's field
 # (the traffic grows with the tiles).
 NCU_TRAFFIC = {
-    ("field", "tf_arms"): {"bytes": 4 * (54658560 + 772668416), "digest": "e402c4e07b584d20"},
-    ("field", "tf_psf_rows"): {"bytes": 4 * (906146048 + 424841472), "digest": "02f47ebe8b5595f1"},
-    ("field", "z_fused"): {"bytes": 4 * (584182784 + 417137152), "digest": "028d622b29b0f22f"},
+    ("field", "tf_arms"): {"bytes": 4 * (54528000 + 772520960), "digest": "451b42818bf0103a"},
+    ("field", "tf_psf_rows"): {"bytes": 4 * (906495744 + 427798784), "digest": "78476baeceeec7ac"},
+    ("field", "yz_op"): {"bytes": 4 * (739290624 + 408136448), "digest": "12f8fcdcdf11184d"},
+    ("field", "tf_yz"): {"bytes": 4 * (457787648 + 400893184), "digest": "12f8fcdcdf11184d"},
 }
 
 
