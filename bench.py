@@ -67,7 +67,7 @@ CPU_SAMPLE = (96, 256, 256)
 # (the traffic grows with the tiles).
 NCU_TRAFFIC = {
     ("field", "tf_arms"): {"bytes": 4 * (54528000 + 772520960), "digest": "451b42818bf0103a"},
-    ("field", "tf_psf_rows"): {"bytes": 4 * (906495744 + 427798784), "digest": "78476baeceeec7ac"},
+    ("field", "tf_psf_rows"): {"bytes": 4 * (906186240 + 424698880), "digest": "5666e82979f1a29a"},
     ("field", "yz_op"): {"bytes": 4 * (739290624 + 408136448), "digest": "12f8fcdcdf11184d"},
     ("field", "tf_yz"): {"bytes": 4 * (457787648 + 400893184), "digest": "12f8fcdcdf11184d"},
 }

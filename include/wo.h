@@ -117,8 +117,8 @@ enum { WO_TF_PHASE_GRAD = 64 };
  * a bank its y and z transforms and the Tikhonov inverse between them, as one
  * pass per (tile, k_x) plane on the chip (TMA bulk copies of the plane into
  * shared memory; one trip through HBM instead of three), and the x passes
- * transpose on the way in and out.  Supported for Z = 32 or 48, Y = 64, 128
- * or 192 and X = 64, 128 or 192 (else WO_ERR_UNSUPPORTED_SIZE).  Accepted by
+ * transpose on the way in and out.  Supported for Z = 32 or 48 and square
+ * planes Y = X = 64, 128 or 192 (else WO_ERR_UNSUPPORTED_SIZE).  Accepted by
  * wo_build_tf, wo_build_tf_device and, in WO_MODE_3D, by
  * wo_reconstruct_field_tiles (the tiles must be square, E = Y = X); every
  * other operator rejects such a bank (WO_ERR_ARG).  The plane kernels wait

@@ -189,7 +189,7 @@ static wo_status check_shape(int n_tiles, int Z, int Y, int X, unsigned kinds) {
   if (base == WO_TF_PHASE_GRAD && !(X == 32 || X == 48 || X == 64 || X == 96 || X == 128 || X == 192 || X == 256))
     return WO_ERR_UNSUPPORTED_SIZE;
   // the plane engine's shapes, and PSF-row and x-pass CTAs whose rows stay inside a plane
-  if (kxm && !(plane_supported(Z, Y) && psf_kxm_supported(X, Y) && rows_kxm_supported(X / 2, Y)))
+  if (kxm && !(plane_supported(Z, Y) && psf_kxm_supported(X, Y, Z) && rows_kxm_supported(X / 2, Y)))
     return WO_ERR_UNSUPPORTED_SIZE;
   return WO_OK;
 }

@@ -196,13 +196,13 @@ cudaError_t tf_psf_rows(const TfArgs& a, cudaStream_t s);
 bool tf_zpass_reg_supported(const TfArgs& a);
 cudaError_t tf_zpass_reg(const TfArgs& a, cudaStream_t s);
 // kx-major banks and spectra (WO_TF_KX_MAJOR; [block][Xh][Z][Y] complex):
-// PSF rows of length X whose pair kernel writes them (a lane's row pair
-// inside a plane of Y rows) (wo_psf.cu); the plane engine's shapes and
+// PSF rows of length X whose pair kernel writes them (square planes, Y = X,
+// of Z = 32 or 48 planes) (wo_psf.cu); the plane engine's shapes and
 // kernels (wo_plane.cu): the TF build's y and z transforms with the
 // regulariser maxima, and the y and z transforms with a one-volume operator
 // between them, in place; status: the workspace's status block (bounded
 // waits on the planes' bulk copies).
-bool psf_kxm_supported(int X, int Y);
+bool psf_kxm_supported(int X, int Y, int Z);
 bool plane_supported(int Z, int Y);
 cudaError_t tf_plane_yz(const TfArgs& a, int* status, cudaStream_t s);
 // Hybrid column engine (wo_colhyb.cu) and the schedule table (wo_sched.cu).

@@ -19,6 +19,8 @@
 // Single real rows (fluorescence, or one label-free kind) pair up across two
 // rows of the bank instead (k_psf_rows_pair).
 // W*(-k) lives in the lane that owns N - k; it is fetched with a shuffle.
+#include <type_traits>
+
 #include "wo_fft.cuh"
 #include "wo_internal.h"
 #include "wo_regfft.cuh"
@@ -228,12 +230,14 @@ __global__ void __launch_bounds__(kPsfThreads, (P::E > 16 && MODE == 2) ? 2 : 4)
 // the second is formed.  The two rows may belong to different tiles when Z*Y
 // is odd; everything per row is formed per row.
 //
-// KXM: the bank is kx-major, [tile][kind][k][j][y] (the plane engine's
-// layout, wo_plane.cu): a lane stores bin k of its two rows (y, y + 1 of one
-// plane, y even) as one 16-byte pair straight from registers; the lane
-// groups of a warp hold consecutive row pairs, so a warp store fills a run
-// of 2 * 32/T points of each of T bins (whole 32-byte sectors).
-template <class P, int LF, bool KXM>  // LF: label-free kinds wanted (0, 1 or 2)
+// ZK > 0: the bank is kx-major, [tile][kind][k][j][y] (the plane engine's
+// layout, wo_plane.cu) with ZK planes of N rows: a lane stores bin k of its
+// two rows (y, y + 1 of one plane, y even) as one 16-byte pair straight from
+// registers; the lane groups of a warp hold consecutive row pairs, so a warp
+// store fills a run of 2 * 32/T points of each of T bins (whole 32-byte
+// sectors).  The bins' stride ZK N is a constant, so their offsets from the
+// lane's first bin are immediates.
+template <class P, int LF, int ZK>  // LF: label-free kinds wanted (0, 1 or 2)
 __global__ void __launch_bounds__(kPsfThreads, P::E > 16 ? 3 : 4) k_psf_rows_pair(TfArgs a) {
   constexpr int N = P::N, N1 = P::E, T = P::T, RP = P::SLICE, RPC = kPsfThreads / T;
   // held-row pitch = T mod 32: the rows of one warp start on distinct banks
@@ -303,10 +307,10 @@ __global__ void __launch_bounds__(kPsfThreads, P::E > 16 ? 3 : 4) k_psf_rows_pai
   // one forward transform of w = h0 + i h1 into TF slot `slot` of both rows
   auto store_pair = [&](int slot) {
     P::template fft<false>(w, tw, S, lt);
-    if constexpr (KXM) {
-      // rows r0, r0 + 1: one plane (Y even), bin k of both at dk + k Z Y
-      float2* dk = a.tf + ((t0 * a.n_kinds + slot) * Xh * a.Z) * (long long)a.Y + rem0;
-      const long long kz = (long long)a.Z * a.Y;
+    if constexpr (ZK > 0) {
+      // rows r0, r0 + 1: one plane (Y = N even), bin k of both at dk + k ZK N
+      float2* dk = a.tf + ((t0 * a.n_kinds + slot) * Xh * ZK) * (long long)N + rem0;
+      constexpr int kz = ZK * N;
 #pragma unroll
       for (int m = 0; m < N1; ++m) {
         const float2 mv = mirror_value<N1>(w, m, lane0);
@@ -391,26 +395,31 @@ static cudaError_t launch_psf_pair(const TfArgs& a, cudaStream_t s) {
   constexpr int RPC = kPsfThreads / P::T;
   const long long pairs = (a.row_end - a.row_begin + 1) / 2;
   const unsigned grid = (unsigned)((pairs + RPC - 1) / RPC);
-  if (a.kxm) {  // one kind, Y even (checked by the caller)
+  if (a.kxm) {  // one kind, Y = X, Z 32 or 48 (checked by the caller)
     if constexpr (P::N == 64 || P::N == 128 || P::N == 192) {
-      if (a.lf_props == 0) WO_LAUNCH("tf_psf_rows", s, (k_psf_rows_pair<P, 0, true><<<grid, kPsfThreads, 0, s>>>(a)));
-      else WO_LAUNCH("tf_psf_rows", s, (k_psf_rows_pair<P, 1, true><<<grid, kPsfThreads, 0, s>>>(a)));
-      return cudaGetLastError();
+      if (a.Y != P::N) return cudaErrorInvalidValue;
+      auto go = [&](auto zk) {
+        constexpr int ZK = decltype(zk)::value;
+        if (a.lf_props == 0) WO_LAUNCH("tf_psf_rows", s, (k_psf_rows_pair<P, 0, ZK><<<grid, kPsfThreads, 0, s>>>(a)));
+        else WO_LAUNCH("tf_psf_rows", s, (k_psf_rows_pair<P, 1, ZK><<<grid, kPsfThreads, 0, s>>>(a)));
+        return cudaGetLastError();
+      };
+      if (a.Z == 48) return go(std::integral_constant<int, 48>{});
+      if (a.Z == 32) return go(std::integral_constant<int, 32>{});
     }
     return cudaErrorInvalidValue;
   }
   switch (a.lf_props) {
-    case 0: WO_LAUNCH("tf_psf_rows", s, (k_psf_rows_pair<P, 0, false><<<grid, kPsfThreads, 0, s>>>(a))); break;
-    case 1: WO_LAUNCH("tf_psf_rows", s, (k_psf_rows_pair<P, 1, false><<<grid, kPsfThreads, 0, s>>>(a))); break;
-    default: WO_LAUNCH("tf_psf_rows", s, (k_psf_rows_pair<P, 2, false><<<grid, kPsfThreads, 0, s>>>(a))); break;
+    case 0: WO_LAUNCH("tf_psf_rows", s, (k_psf_rows_pair<P, 0, 0><<<grid, kPsfThreads, 0, s>>>(a))); break;
+    case 1: WO_LAUNCH("tf_psf_rows", s, (k_psf_rows_pair<P, 1, 0><<<grid, kPsfThreads, 0, s>>>(a))); break;
+    default: WO_LAUNCH("tf_psf_rows", s, (k_psf_rows_pair<P, 2, 0><<<grid, kPsfThreads, 0, s>>>(a))); break;
   }
   return cudaGetLastError();
 }
 
 // Row lengths X whose PSF-row pair kernel writes kx-major banks (the
-// instantiated ones), and whether a lane's row pair stays inside a plane of
-// Y rows (Y even).
-bool psf_kxm_supported(int X, int Y) { return (X == 64 || X == 128 || X == 192) && Y % 2 == 0; }
+// instantiated ones: square planes, Y = X, of 32 or 48 planes).
+bool psf_kxm_supported(int X, int Y, int Z) { return (X == 64 || X == 128 || X == 192) && Y == X && (Z == 32 || Z == 48); }
 
 template <class P, int MODE>
 static cudaError_t launch_psf_reg(const TfArgs& a, cudaStream_t s) {

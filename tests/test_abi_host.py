@@ -420,6 +420,7 @@ def test_kx_major_validation(B):
     assert B.wo_tf_bytes(1, 48, 256, 256, 1 | K) == 0              # Y outside the plane engine
     assert B.wo_tf_bytes(1, 48, 96, 96, 1 | K) == 0
     assert B.wo_tf_bytes(1, 48, 192, 256, 1 | K) == 0              # 256-point PSF rows
+    assert B.wo_tf_bytes(1, 48, 128, 192, 1 | K) == 0              # planes not square
     assert B.wo_tf_bytes(1, 48, 192, 192, 1 | 256) == 0            # unknown bit
     lib = B._lib
     fake = 1 << 20
