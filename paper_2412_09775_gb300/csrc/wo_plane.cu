@@ -102,6 +102,7 @@ struct PlaneGeom {
   static_assert(32 % PY::T == 0 && 32 % PZ::T == 0, "a row's or column's lanes sit in one warp");
   static_assert(Z % 2 == 0 && Y % 16 == 0 && Y > kRot, "row pairs; 16-byte rows; the odd-row rotation");
   static_assert(MINB >= 1, "the plane must fit shared memory");
+  static_assert(Z <= NT, "a thread issues each row's copies");
 };
 
 // Cell of point s of row z (odd rows rotated).
@@ -111,15 +112,15 @@ __device__ __forceinline__ int row_cell(int z, int s) {
   return q >= Y ? q - Y : q;
 }
 
-// Warp 0: copy plane `src` (Z rows of Y points) into P, odd rows rotated,
-// row z completing on bars[z] (lane l initialises and arms the barriers of
-// rows l, l + 32, ... and issues their copies).  The caller synchronises the
-// CTA before any thread waits on a barrier.
+// Threads 0 .. Z-1: copy plane `src` (Z rows of Y points) into P, odd rows
+// rotated, row z completing on bars[z] (thread z initialises and arms the
+// barrier of row z and issues its copies, so the rows' copies go out
+// together).  The caller synchronises the CTA before any thread waits on a
+// barrier.
 template <int Z, int Y>
 __device__ __forceinline__ void plane_copy_in(float2* P, const float2* src, uint64_t* bars) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll 1
-  for (int z = lane; z < Z; z += 32) {
+  const int z = threadIdx.x;
+  if (z < Z) {
     mbar_init(bars + z, 1);
     mbar_init_fence();
     mbar_expect_tx(bars + z, (unsigned)(Y * sizeof(float2)));
@@ -211,7 +212,7 @@ __global__ void __launch_bounds__(NT, PlaneGeom<PY, PZ, NT>::MINB) k_tf_yz(float
 #if defined(WO_CHECK) && WO_CHECK
   if (!WO_IN((pidx + 1) * G::PLANE - 1, (long long)gridDim.y * Xh * G::PLANE, 12)) return;  // uniform
 #endif
-  if (threadIdx.x < 32) plane_copy_in<Z, Y>(P, plane, bars);
+  plane_copy_in<Z, Y>(P, plane, bars);
   cell_twiddles<PY>(twy);
   cell_twiddles<PZ>(twz);
   __syncthreads();
@@ -293,11 +294,9 @@ __global__ void __launch_bounds__(NT, PlaneGeom<PY, PZ, NT>::MINB) k_yz_op(const
     for (int e = threadIdx.x; e < G::PLANE / 2; e += NT) d4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
     return;  // uniform
   }
-  if (threadIdx.x < 32) {
-    plane_copy_in<Z, Y>(P, src, bars);
-    // the TF plane is read in the z step: on its way to L2 meanwhile
-    for (int z = threadIdx.x; z < Z; z += 32) bulk_prefetch_l2(h + (long long)z * Y, (unsigned)(Y * sizeof(float2)));
-  }
+  plane_copy_in<Z, Y>(P, src, bars);
+  // the TF plane is read in the z step: on its way to L2 meanwhile
+  if (threadIdx.x < Z) bulk_prefetch_l2(h + (long long)threadIdx.x * Y, (unsigned)(Y * sizeof(float2)));
   const bool lf = op.lf_props > 0;
   const float eta = lf ? op.eta_lf : op.eta_fl;
   const float lam = op.eta_absolute ? eta : eta * st[lf ? 0 : 2];
