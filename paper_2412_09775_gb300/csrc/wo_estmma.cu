@@ -46,8 +46,6 @@ __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bflo
   lo = __float2bfloat16_rn(r - __bfloat162float(mid));
 }
 
-__device__ __forceinline__ uint32_t ld32(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
-
 // c += a b for one m16n8k16 tile.
 __device__ __forceinline__ void mma16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
   asm volatile(
@@ -57,22 +55,52 @@ __device__ __forceinline__ void mma16816(float (&c)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// A fragment of the 16 x 16 tile whose row 0 is at `s` (rows P bfloat16 apart).
-template <int P = kPitch>
-__device__ __forceinline__ void frag_a(uint32_t (&a)[4], const __nv_bfloat16* s, int lane) {
-  const int g = lane >> 2, t = lane & 3;
-  a[0] = ld32(s + g * P + 2 * t);
-  a[1] = ld32(s + (g + 8) * P + 2 * t);
-  a[2] = ld32(s + g * P + 2 * t + 8);
-  a[3] = ld32(s + (g + 8) * P + 2 * t + 8);
+// Fragments by ldmatrix: each of the 8-row by 8-column bfloat16 matrices it
+// reads is given by the 16-byte row addresses of eight lanes (lanes 8 i ..
+// 8 i + 7 for matrix i), and lane l receives elements (l / 4, 2 (l mod 4) ..
+// + 1) of every matrix: the m16n8k16 operand layout (g = l / 4, t = l mod 4).
+// Every staging pitch here is a multiple of 8 bfloat16, so the rows are
+// 16-byte aligned, and its eight rows fall on distinct 16-byte bank groups.
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const __nv_bfloat16* p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a)
+               : "memory");
 }
 
-// B fragment of the 8 columns whose column 0 (k contiguous) is at `s`.
+__device__ __forceinline__ void ldsm_x2(uint32_t& r0, uint32_t& r1, const __nv_bfloat16* p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(a) : "memory");
+}
+
+// A fragment of the 16 x 16 tile whose row 0 is at `s` (rows P bfloat16
+// apart): matrices rows 0-7 / 8-15 by k 0-7 / 8-15, in the order a0..a3.
+template <int P = kPitch>
+__device__ __forceinline__ void frag_a(uint32_t (&a)[4], const __nv_bfloat16* s, int lane) {
+  static_assert(P % 8 == 0, "16-byte aligned fragment rows");
+  const int mi = lane >> 3, r = lane & 7;
+  ldsm_x4(a, s + (r + ((mi & 1) << 3)) * P + ((mi & 2) << 2));
+}
+
+// B fragment of the 8 columns whose column 0 (k contiguous) is at `s`:
+// matrices k 0-7 and 8-15 of the 8 columns (lanes 16-31 repeat the addresses
+// of lanes 0-15; ldmatrix .x2 reads those of lanes 0-15).
 template <int P = kPitch>
 __device__ __forceinline__ void frag_b(uint32_t& b0, uint32_t& b1, const __nv_bfloat16* s, int lane) {
-  const int g = lane >> 2, t = lane & 3;
-  b0 = ld32(s + g * P + 2 * t);
-  b1 = ld32(s + g * P + 2 * t + 8);
+  static_assert(P % 8 == 0, "16-byte aligned fragment rows");
+  const int r = lane & 7, c = (lane >> 3) & 1;
+  ldsm_x2(b0, b1, s + r * P + 8 * c);
+}
+
+// B fragments of two adjacent 8-column tiles (columns 0-7 at `s`, 8-15 at
+// s + 8 P) by one ldmatrix .x4: b[0], b[1] of the first, b[2], b[3] of the
+// second.
+template <int P = kPitch>
+__device__ __forceinline__ void frag_b2(uint32_t (&b)[4], const __nv_bfloat16* s, int lane) {
+  static_assert(P % 8 == 0, "16-byte aligned fragment rows");
+  const int mi = lane >> 3, r = lane & 7;
+  ldsm_x4(b, s + (r + ((mi >> 1) << 3)) * P + 8 * (mi & 1));
 }
 
 // Tiles with 32 k per row: pitch 40 bfloat16 (20 words), so that the eight
@@ -204,13 +232,17 @@ __global__ void __launch_bounds__(kMmaThreads) k_conv_fwd_mma(const float* __res
     frag_a(fh, ahi[buf] + warp * 16 * kPitch, lane);
     frag_a(fm, amid[buf] + warp * 16 * kPitch, lane);
     frag_a(fl, alo[buf] + warp * 16 * kPitch, lane);
+    static_assert(NT % 2 == 0, "B tiles in pairs");
 #pragma unroll
-    for (int n = 0; n < NT; ++n) {
-      uint32_t b0, b1;
-      frag_b(b0, b1, bs[buf] + n * 8 * kPitch, lane);
-      mma16816(acc[n], fl, b0, b1);
-      mma16816(acc[n], fm, b0, b1);
-      mma16816(acc[n], fh, b0, b1);
+    for (int n = 0; n < NT; n += 2) {
+      uint32_t bb[4];
+      frag_b2(bb, bs[buf] + n * 8 * kPitch, lane);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        mma16816(acc[n + h], fl, bb[2 * h], bb[2 * h + 1]);
+        mma16816(acc[n + h], fm, bb[2 * h], bb[2 * h + 1]);
+        mma16816(acc[n + h], fh, bb[2 * h], bb[2 * h + 1]);
+      }
     }
     // the other buffer was last read before the previous barrier
     if (st + 1 < NSTAGE) store(buf ^ 1);
@@ -285,13 +317,17 @@ __global__ void __launch_bounds__(kMmaThreads) k_conv_fwd_mma_k32(const float* _
     frag_a<P>(fh, ahi + warp * 16 * P + ks * 16, lane);
     frag_a<P>(fm, amid + warp * 16 * P + ks * 16, lane);
     frag_a<P>(fl, alo + warp * 16 * P + ks * 16, lane);
+    static_assert(NT % 2 == 0, "B tiles in pairs");
 #pragma unroll
-    for (int n = 0; n < NT; ++n) {
-      uint32_t b0, b1;
-      frag_b<P>(b0, b1, bs + n * 8 * P + ks * 16, lane);
-      mma16816(acc[n], fl, b0, b1);
-      mma16816(acc[n], fm, b0, b1);
-      mma16816(acc[n], fh, b0, b1);
+    for (int n = 0; n < NT; n += 2) {
+      uint32_t bb[4];
+      frag_b2<P>(bb, bs + n * 8 * P + ks * 16, lane);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        mma16816(acc[n + h], fl, bb[2 * h], bb[2 * h + 1]);
+        mma16816(acc[n + h], fm, bb[2 * h], bb[2 * h + 1]);
+        mma16816(acc[n + h], fh, bb[2 * h], bb[2 * h + 1]);
+      }
     }
   }
   const int g = lane >> 2, t = lane & 3;
@@ -433,12 +469,16 @@ __global__ void __launch_bounds__(kMmaThreads) k_conv_bwd_data_mma(const float* 
       uint32_t fh[4], fl[4];
       frag_a<P>(fh, ahi[buf] + warp * 16 * P + ks * 16, lane);
       frag_a<P>(fl, alo[buf] + warp * 16 * P + ks * 16, lane);
+      static_assert(NT % 2 == 0, "B tiles in pairs");
 #pragma unroll
-      for (int n = 0; n < NT; ++n) {
-        uint32_t b0, b1;
-        frag_b<P>(b0, b1, bs[buf] + n * 8 * P + ks * 16, lane);
-        mma16816(acc[n], fl, b0, b1);
-        mma16816(acc[n], fh, b0, b1);
+      for (int n = 0; n < NT; n += 2) {
+        uint32_t bb[4];
+        frag_b2<P>(bb, bs[buf] + n * 8 * P + ks * 16, lane);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          mma16816(acc[n + h], fl, bb[2 * h], bb[2 * h + 1]);
+          mma16816(acc[n + h], fh, bb[2 * h], bb[2 * h + 1]);
+        }
       }
     }
     if (st + 1 < nstage) store(buf ^ 1);  // the other buffer was last read before the previous barrier
@@ -569,14 +609,25 @@ __global__ void __launch_bounds__(WgGeom<CO>::NT, WgGeom<CO>::MINB) k_conv_bwd_w
       for (int q = 0; q < 5; ++q) {
         const int tap = tap0 + q;
         if (tap >= 9) break;
+        // the tap's two 8-column tiles: by one ldmatrix .x4 each, unless the
+        // register budget is that of 384 threads at two blocks per SM (85 per
+        // thread), where the four fragment registers more spill
+        uint32_t bh[4], bl[4];
+        if constexpr (NT * G::MINB > 512) {
+#pragma unroll
+          for (int n = 0; n < 2; ++n) {
+            frag_b<P>(bh[2 * n], bh[2 * n + 1], xhi + (buf * 144 + tap * 16 + n * 8) * P + ks * 16, lane);
+            frag_b<P>(bl[2 * n], bl[2 * n + 1], xlo + (buf * 144 + tap * 16 + n * 8) * P + ks * 16, lane);
+          }
+        } else {
+          frag_b2<P>(bh, xhi + (buf * 144 + tap * 16) * P + ks * 16, lane);
+          frag_b2<P>(bl, xlo + (buf * 144 + tap * 16) * P + ks * 16, lane);
+        }
 #pragma unroll
         for (int n = 0; n < 2; ++n) {
-          uint32_t bh0, bh1, bl0, bl1;
-          frag_b<P>(bh0, bh1, xhi + (buf * 144 + tap * 16 + n * 8) * P + ks * 16, lane);
-          frag_b<P>(bl0, bl1, xlo + (buf * 144 + tap * 16 + n * 8) * P + ks * 16, lane);
-          mma16816(acc[q][n], fh, bl0, bl1);
-          mma16816(acc[q][n], fl, bh0, bh1);
-          mma16816(acc[q][n], fh, bh0, bh1);
+          mma16816(acc[q][n], fh, bl[2 * n], bl[2 * n + 1]);
+          mma16816(acc[q][n], fl, bh[2 * n], bh[2 * n + 1]);
+          mma16816(acc[q][n], fh, bh[2 * n], bh[2 * n + 1]);
         }
       }
     }
@@ -709,13 +760,16 @@ __global__ void __launch_bounds__(kWgThreads, 2) k_conv_bwd_weight_mma_n32(const
       frag_a<P>(fh, ghi + mt * 16 * P + k0, lane);
       frag_a<P>(fl, glo + mt * 16 * P + k0, lane);
 #pragma unroll
-      for (int n = 0; n < 4; ++n) {
-        uint32_t bh0, bh1, bl0, bl1;
-        frag_b<P>(bh0, bh1, xhi + n * 8 * P + k0, lane);
-        frag_b<P>(bl0, bl1, xlo + n * 8 * P + k0, lane);
-        mma16816(acc[n], fh, bl0, bl1);
-        mma16816(acc[n], fl, bh0, bh1);
-        mma16816(acc[n], fh, bh0, bh1);
+      for (int n = 0; n < 4; n += 2) {
+        uint32_t bh[4], bl[4];
+        frag_b2<P>(bh, xhi + n * 8 * P + k0, lane);
+        frag_b2<P>(bl, xlo + n * 8 * P + k0, lane);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          mma16816(acc[n + h], fh, bl[2 * h], bl[2 * h + 1]);
+          mma16816(acc[n + h], fl, bh[2 * h], bh[2 * h + 1]);
+          mma16816(acc[n + h], fh, bh[2 * h], bh[2 * h + 1]);
+        }
       }
     }
     if (st + 1 < nst) store(buf ^ 1);  // the other buffer was last read before the previous barrier
