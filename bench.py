@@ -749,7 +749,7 @@ def field_algorithmic_bytes(o_list, Z, E, field_vox):
         out["tf_psf_rows"] += arms + half
         out["tf_ypass"] += 2 * half
         out["tf_zpass"] += 2 * half
-        out["tf_yz"] += 2 * half  # the plane engine: every TF plane in and out once
+        out["tf_yz"] += 2 * planes_in * Z * E * 8  # the plane engine: the TF planes inside the support in and out
         # the plane engine's operator pass: the data planes inside the support
         # disk in, the TF columns inside it in, every plane out
         out["yz_op"] += planes_in * Z * E * 8 + inside + half

@@ -121,7 +121,10 @@ enum { WO_TF_PHASE_GRAD = 64 };
  * planes Y = X = 64, 128 or 192 (else WO_ERR_UNSUPPORTED_SIZE).  Accepted by
  * wo_build_tf, wo_build_tf_device and, in WO_MODE_3D, by
  * wo_reconstruct_field_tiles (the tiles must be square, E = Y = X); every
- * other operator rejects such a bank (WO_ERR_ARG).  The plane kernels wait
+ * other operator rejects such a bank (WO_ERR_ARG).  The planes of k_x outside
+ * a tile's own TF support disk hold the PSF rows' rounding noise (of the
+ * order of 1e-7 of the largest TF value) instead of transformed noise: the
+ * reconstruction writes zeros there without reading them.  The plane kernels wait
  * for their copies with a bound; a wait that runs out records WO_ERR_TIMEOUT
  * in the workspace's status block (wo_sync_status). */
 enum { WO_TF_KX_MAJOR = 128 };

@@ -193,7 +193,10 @@ __device__ __forceinline__ bool plane_rows_fwd(float2* P, const float2* twy, uin
 }
 
 // TF build: forward y and z transforms of TF plane (tile, k_x) in place and
-// the tile's regulariser maxima.  Planes k_x >= x_cols are not launched.
+// the tile's regulariser maxima.  Planes k_x >= x_cols are not launched;
+// planes outside the tile's own support disk (every TF of the tile vanishes
+// there: only the PSF rows' rounding noise) are left as they are, as the
+// operators never read them (k_yz_op writes zeros there).
 template <class PY, class PZ, int NT>
 __global__ void __launch_bounds__(NT, PlaneGeom<PY, PZ, NT>::MINB) k_tf_yz(float2* __restrict__ tf,
                                                                           float* __restrict__ stats, int Xh, int lf,
@@ -212,6 +215,7 @@ __global__ void __launch_bounds__(NT, PlaneGeom<PY, PZ, NT>::MINB) k_tf_yz(float
 #if defined(WO_CHECK) && WO_CHECK
   if (!WO_IN((pidx + 1) * G::PLANE - 1, (long long)gridDim.y * Xh * G::PLANE, 12)) return;  // uniform
 #endif
+  if (outside_support(stats + (long long)tile * 8, 0, Y, kx, 2 * (Xh - 1))) return;  // uniform
   plane_copy_in<Z, Y>(P, plane, bars);
   cell_twiddles<PY>(twy);
   cell_twiddles<PZ>(twz);
