@@ -103,11 +103,9 @@ __device__ __forceinline__ void frag_b2(uint32_t (&b)[4], const __nv_bfloat16* s
   ldsm_x4(b, s + (r + ((mi >> 1) << 3)) * P + 8 * (mi & 1));
 }
 
-// Tiles with 32 k per row: pitch 40 bfloat16 (20 words), so that the eight
-// rows g of a fragment load start in banks 20 g mod 32, all different.
+// Tiles with 32 k per row: pitch 40 bfloat16 (80 bytes), so that the eight
+// 16-byte rows of an ldmatrix phase fall on distinct bank groups.
 constexpr int kPitch32 = 40;
-
-__host__ __device__ constexpr int ceil16(int v) { return (v + 15) / 16 * 16; }
 
 // ------------------------------------------------------------------ weights for the staging copies
 // The layers' bfloat16 weights w[co][ci][tap] re-laid once per pass so that a
@@ -666,7 +664,7 @@ __global__ void __launch_bounds__(WgGeom<CO>::NT, WgGeom<CO>::MINB) k_conv_bwd_w
 // gradients, a stage's g and x are loaded into registers during the previous
 // stage's products and written to the other of two buffers.
 constexpr int kWgPixN = 64;
-constexpr int kWgPitchN = 72;  // 36 words: fragment rows g start in banks 4 g
+constexpr int kWgPitchN = 72;  // 144 bytes: the eight 16-byte rows of an ldmatrix phase on distinct bank groups
 
 template <int CI, int CO, int H, int S>
 __global__ void __launch_bounds__(kWgThreads, 2) k_conv_bwd_weight_mma_n32(const float* __restrict__ gy,
@@ -880,7 +878,6 @@ cudaError_t fwd_layer(const float* x, const __nv_bfloat16* wb, const __nv_bfloat
 template <int CI, int CO, int H, int S>
 cudaError_t bwd_layer(const float* gy, const float* xin, const __nv_bfloat16* wt, long long woff, long long boff,
                       int B, float* gx, float* part, size_t part_floats, float* grad, cudaStream_t s) {
-  constexpr int HO = (H + S - 1) / S;
   // weight gradient: blocks (16-channel group, sample chunk); chunks so that
   // the grid has about 600 blocks and the partials fit their buffer (weight
   // partials [chunk][CO][CI][9], then bias partials [chunk][CO])
