@@ -113,18 +113,21 @@ enum { WO_TF_PHASE_GRAD = 64 };
  * optionally WO_TF_SMOOTH_SOURCE): the bank's half spectra are stored
  * kx-major, [n_tiles][1][X/2+1][Z][Y] complex64 (the Z x Y plane of every
  * half-spectrum column k_x contiguous; same size, same statistics block).
- * The build then runs its y and z transforms, and a reconstruction with such
- * a bank its y and z transforms and the Tikhonov inverse between them, as one
- * pass per (tile, k_x) plane on the chip (TMA bulk copies of the plane into
- * shared memory; one trip through HBM instead of three), and the x passes
- * transpose on the way in and out.  Supported for Z = 32 or 48 and square
- * planes Y = X = 64, 128 or 192 (else WO_ERR_UNSUPPORTED_SIZE).  Accepted by
- * wo_build_tf, wo_build_tf_device and, in WO_MODE_3D, by
- * wo_reconstruct_field_tiles (the tiles must be square, E = Y = X); every
- * other operator rejects such a bank (WO_ERR_ARG).  The planes of k_x outside
- * a tile's own TF support disk hold the PSF rows' rounding noise (of the
- * order of 1e-7 of the largest TF value) instead of transformed noise: the
- * reconstruction writes zeros there without reading them.  The plane kernels wait
+ * The build then runs its y and z transforms, and an operator with such a
+ * bank its y and z transforms and the per-frequency operator between them, as
+ * one pass per (tile, k_x) plane on the chip (TMA bulk copies of the plane
+ * into shared memory; one trip through HBM instead of three), and the x
+ * passes transpose on the way in and out.  Supported for Z = 32 or 48 and
+ * square planes Y = X = 64, 128 or 192, and for Z = 16 with Y = X = 64 (else
+ * WO_ERR_UNSUPPORTED_SIZE).  Accepted by wo_build_tf, wo_build_tf_device, and
+ * with the same kinds value by wo_forward, wo_forward_adjoint, and in
+ * WO_MODE_3D by wo_reconstruct, wo_reconstruct_shared_tf and
+ * wo_reconstruct_field_tiles (square tiles, E = Y = X); the 2D solve,
+ * wo_restore_field and the tuning calls reject such a bank (WO_ERR_ARG).  The
+ * planes of k_x outside a tile's own TF support disk hold the PSF rows'
+ * rounding noise (of the order of 1e-7 of the largest TF value) instead of
+ * transformed noise: the operators write zeros there without reading them.
+ * The plane kernels wait
  * for their copies with a bound; a wait that runs out records WO_ERR_TIMEOUT
  * in the workspace's status block (wo_sync_status). */
 enum { WO_TF_KX_MAJOR = 128 };

@@ -513,8 +513,9 @@ static wo_status run_op(int op, const void* d_tf, unsigned kinds, const float* d
   if (fout) d_out = fout->field;
   if (!aligned16(d_tf) || !aligned16(d_in) || !aligned16(d_out) || !aligned16(d_ws)) return WO_ERR_ARG;
   const Sys s = system_of(kinds);
-  // a kx-major bank serves the 3D reconstruction of a field's square tiles only
-  if (s.kxm && (op != 2 || mode != WO_MODE_3D || !field || fout || X != Y)) return WO_ERR_ARG;
+  // a kx-major bank serves the 3D operators on square planes (not the 2D
+  // solve, not the fused blend)
+  if (s.kxm && (mode != WO_MODE_3D || fout || X != Y)) return WO_ERR_ARG;
   if (op == 2) {
     if (!h_eta) return WO_ERR_ARG;
     if (eta_flag != WO_ETA_RELATIVE && eta_flag != WO_ETA_ABSOLUTE) return WO_ERR_ARG;
@@ -579,7 +580,7 @@ static wo_status run_op(int op, const void* d_tf, unsigned kinds, const float* d
 
   // The phase-only 3D reconstruction of tile-sized planes runs as one
   // persistent pipeline (wo_pipe.cu) unless the schedule table says otherwise.
-  if (op == 2 && mode == WO_MODE_3D && !field && !fout && pipe_system(s) && pipe_supported(Z, Y, X) &&
+  if (op == 2 && mode == WO_MODE_3D && !field && !fout && !s.kxm && pipe_system(s) && pipe_supported(Z, Y, X) &&
       recon_engine(Z, Y, X) == WO_ENGINE_HYBRID) {
     PipeLaunch p = pipe_launch(L, s, d_tf, d_in, d_out, n_tiles, Z, Y, X, ws, tf_shared, zo.eta_lf,
                                zo.eta_absolute, h_bg);
@@ -587,15 +588,15 @@ static wo_status run_op(int op, const void* d_tf, unsigned kinds, const float* d
   }
   const long long in_rows = (long long)n_tiles * n_in * Z * Y;
   if (s.kxm) {
-    // kx-major bank: the field's tiles through the plane engine; the
-    // spectrum stays in specA throughout
-    WO_TRY(rows_r2c_field_kxm(H, *field, specA, in_rows, bg_in, cs));
+    // kx-major bank (one kind: one volume in, one out): the x pass into the
+    // kx-major spectrum (from the tiles, or from the field's tiles in place),
+    // the plane engine, the x pass back (the forward model adds its
+    // background there); the spectrum stays in specA throughout
+    if (field) WO_TRY(rows_r2c_field_kxm(H, *field, specA, in_rows, bg_in, cs));
+    else WO_TRY(rows_r2c_kxm(H, d_in, specA, in_rows, Z, Y, bg_in, cs));
     WO_TRY(plane_yz_op(Z, Y, specA, tf, zo, n_tiles, Xh, (int*)(ws + L.status), cs));
-    RowBg none{};
-    none.rows_per_block = (long long)Z * Y;
-    none.nchan = 1;
     const float scale = (float)(2.0 / ((double)X * (double)Y * (double)Z));
-    WO_TRY(rows_c2r_kxm(H, specA, d_out, in_rows, Z, Y, scale, none, cs));
+    WO_TRY(rows_c2r_kxm(H, specA, d_out, (long long)n_tiles * n_out * Z * Y, Z, Y, scale, bg_out, cs));
     return WO_OK;
   }
   if (field) {  // the x pass reads the tiles from the field, then the y pass

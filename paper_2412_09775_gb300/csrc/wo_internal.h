@@ -243,6 +243,10 @@ bool rows_kxm_supported(int N, int Y);
 cudaError_t rows_r2c_field_kxm(int N, const FieldSrc& f, float2* out, long long nrows, RowBg bg, cudaStream_t s);
 cudaError_t rows_c2r_kxm(int N, const float2* in, float* out, long long nrows, int Z, int Y, float scale, RowBg bg,
                          cudaStream_t s);
+// The forward pass from volumes [block][Z][Y][2N] (square planes, Y = 2N)
+// into [block][N+1][Z][Y].
+cudaError_t rows_r2c_kxm(int N, const float* in, float2* out, long long nrows, int Z, int Y, RowBg bg,
+                         cudaStream_t s);
 // The inverse x pass of a field's tiles fused with their blend into the
 // field (wo_rowsreg.cu): field [P][Z][tiles_y core][tiles_x core], the same
 // values as the inverse x pass into tiles followed by wo_tile_blend.

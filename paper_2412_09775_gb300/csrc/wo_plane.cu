@@ -389,9 +389,11 @@ cudaError_t launch_yz_op(float2* spec, const float2* tf, const ZOp& op, int n_ti
   return cudaGetLastError();
 }
 
-// The instantiated (Z, Y) shapes: Z 32 or 48, Y 64, 128 or 192.
+// The instantiated (Z, Y) shapes: Z 32 or 48 with Y 64, 128 or 192, and
+// 16 x 64 (small stacks).
 template <class F>
 cudaError_t plane_dispatch(int Z, int Y, F f) {
+  if (Z == 16 && Y == 64) return f(Row2<64, 8>{}, Row2<16, 4>{}, std::integral_constant<int, 128>{});
   if (Z == 48 && Y == 192) return f(Row2<192, 24>{}, Row2<48, 12>{}, std::integral_constant<int, 192>{});
   if (Z == 48 && Y == 128) return f(Row2<128, 16>{}, Row2<48, 12>{}, std::integral_constant<int, 128>{});
   if (Z == 48 && Y == 64) return f(Row2<64, 8>{}, Row2<48, 12>{}, std::integral_constant<int, 128>{});
@@ -403,7 +405,9 @@ cudaError_t plane_dispatch(int Z, int Y, F f) {
 
 }  // namespace
 
-bool plane_supported(int Z, int Y) { return (Z == 32 || Z == 48) && (Y == 64 || Y == 128 || Y == 192); }
+bool plane_supported(int Z, int Y) {
+  return ((Z == 32 || Z == 48) && (Y == 64 || Y == 128 || Y == 192)) || (Z == 16 && Y == 64);
+}
 
 cudaError_t tf_plane_yz(const TfArgs& a, int* status, cudaStream_t s) {
   if (a.n_kinds != 1) return cudaErrorInvalidValue;

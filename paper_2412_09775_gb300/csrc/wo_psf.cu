@@ -395,7 +395,7 @@ static cudaError_t launch_psf_pair(const TfArgs& a, cudaStream_t s) {
   constexpr int RPC = kPsfThreads / P::T;
   const long long pairs = (a.row_end - a.row_begin + 1) / 2;
   const unsigned grid = (unsigned)((pairs + RPC - 1) / RPC);
-  if (a.kxm) {  // one kind, Y = X, Z 32 or 48 (checked by the caller)
+  if (a.kxm) {  // one kind, Y = X, Z 32 or 48 (16 with X = 64) (checked by the caller)
     if constexpr (P::N == 64 || P::N == 128 || P::N == 192) {
       if (a.Y != P::N) return cudaErrorInvalidValue;
       auto go = [&](auto zk) {
@@ -406,6 +406,9 @@ static cudaError_t launch_psf_pair(const TfArgs& a, cudaStream_t s) {
       };
       if (a.Z == 48) return go(std::integral_constant<int, 48>{});
       if (a.Z == 32) return go(std::integral_constant<int, 32>{});
+      if constexpr (P::N == 64) {
+        if (a.Z == 16) return go(std::integral_constant<int, 16>{});
+      }
     }
     return cudaErrorInvalidValue;
   }
@@ -418,8 +421,11 @@ static cudaError_t launch_psf_pair(const TfArgs& a, cudaStream_t s) {
 }
 
 // Row lengths X whose PSF-row pair kernel writes kx-major banks (the
-// instantiated ones: square planes, Y = X, of 32 or 48 planes).
-bool psf_kxm_supported(int X, int Y, int Z) { return (X == 64 || X == 128 || X == 192) && Y == X && (Z == 32 || Z == 48); }
+// instantiated ones: square planes, Y = X, of 32 or 48 planes, or 16 planes
+// of 64 points).
+bool psf_kxm_supported(int X, int Y, int Z) {
+  return (X == 64 || X == 128 || X == 192) && Y == X && (Z == 32 || Z == 48 || (Z == 16 && X == 64));
+}
 
 template <class P, int MODE>
 static cudaError_t launch_psf_reg(const TfArgs& a, cudaStream_t s) {

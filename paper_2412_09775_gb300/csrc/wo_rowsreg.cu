@@ -33,9 +33,12 @@ struct RowRegGeom {
   static constexpr size_t SMEM = ((size_t)P::TW + 2 * (size_t)N + (size_t)RPC * P::SLICE) * sizeof(float2);
 };
 
-template <class P>
+// PY > 0: the output is kx-major, [block][N+1][Z][PY] (the plane engine's
+// layout; a row's bins at o + k Z PY, the 32/T rows of a warp consecutive
+// rows of one plane: whole 32-byte sectors per bin), Z the planes per block.
+template <class P, int PY = 0>
 __global__ void __launch_bounds__(kRowThreads) k_rows_r2c_reg(const float* __restrict__ in, float2* __restrict__ out,
-                                                               long long nrows, RowBg bg) {
+                                                               long long nrows, RowBg bg, int Z) {
   using G = RowRegGeom<P>;
   constexpr int N = G::N, T = G::T, E = G::E, RPC = G::RPC;
   extern __shared__ float2 sm[];
@@ -61,10 +64,30 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_r2c_reg(const float* __res
 #pragma unroll
   for (int m = 0; m < E; ++m) v[m] = make_float2(v[m].x - c, v[m].y - c);
   P::template fft<false>(v, tw, S, t);
-  float2* o = out + rr * (N + 1);
-  r2c_split<N, T, E>(v, tw2, t, [&](int k, float2 val) {
-    if (live) o[k] = val;
-  });
+  if constexpr (PY > 0) {
+    const long long plane_rows = (long long)Z * PY;
+    const long long blk = rr / plane_rows, rem = rr - blk * plane_rows;  // rem = z PY + y
+    float2* o = out + blk * (N + 1) * plane_rows + rem;
+    r2c_split<N, T, E>(v, tw2, t, [&](int k, float2 val) {
+      if (live) o[k * plane_rows] = val;
+    });
+  } else {
+    float2* o = out + rr * (N + 1);
+    r2c_split<N, T, E>(v, tw2, t, [&](int k, float2 val) {
+      if (live) o[k] = val;
+    });
+  }
+}
+
+template <class P, int PY>
+cudaError_t launch_r2c_kxm(const float* in, float2* out, long long nrows, int Z, RowBg bg, cudaStream_t s) {
+  using G = RowRegGeom<P>;
+  const cudaError_t attr = allow_smem(k_rows_r2c_reg<P, PY>, G::SMEM);
+  if (attr != cudaSuccess) return attr;
+  const long long blocks = (nrows + G::RPC - 1) / G::RPC;
+  WO_LAUNCH("rows_r2c", s,
+            (k_rows_r2c_reg<P, PY><<<(unsigned)blocks, kRowThreads, G::SMEM, s>>>(in, out, nrows, bg, Z)));
+  return cudaGetLastError();
 }
 
 template <class P>
@@ -352,7 +375,7 @@ cudaError_t launch_r2c_reg(const float* in, float2* out, long long nrows, RowBg 
   const cudaError_t attr = allow_smem(k_rows_r2c_reg<P>, G::SMEM);
   if (attr != cudaSuccess) return attr;
   const long long blocks = (nrows + G::RPC - 1) / G::RPC;
-  WO_LAUNCH("rows_r2c", s, (k_rows_r2c_reg<P><<<(unsigned)blocks, kRowThreads, G::SMEM, s>>>(in, out, nrows, bg)));
+  WO_LAUNCH("rows_r2c", s, (k_rows_r2c_reg<P><<<(unsigned)blocks, kRowThreads, G::SMEM, s>>>(in, out, nrows, bg, 1)));
   return cudaGetLastError();
 }
 
@@ -414,6 +437,18 @@ cudaError_t rows_r2c_field_kxm(int N, const FieldSrc& f, float2* out, long long 
     case 32: return launch_r2c_field<Row2<32, 8>, true>(f, out, nrows, bg, s);
     case 64: return launch_r2c_field<Row2<64, 8>, true>(f, out, nrows, bg, s);
     case 96: return launch_r2c_field<Row2<96, 24>, true>(f, out, nrows, bg, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t rows_r2c_kxm(int N, const float* in, float2* out, long long nrows, int Z, int Y, RowBg bg,
+                         cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  if (!rows_kxm_supported(N, Y) || Y != 2 * N || nrows % ((long long)Z * Y)) return cudaErrorInvalidValue;
+  switch (N) {  // square planes: Y = 2N
+    case 32: return launch_r2c_kxm<Row2<32, 8>, 64>(in, out, nrows, Z, bg, s);
+    case 64: return launch_r2c_kxm<Row2<64, 8>, 128>(in, out, nrows, Z, bg, s);
+    case 96: return launch_r2c_kxm<Row2<96, 24>, 192>(in, out, nrows, Z, bg, s);
     default: return cudaErrorInvalidValue;
   }
 }

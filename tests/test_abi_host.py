@@ -404,10 +404,10 @@ def test_restore_field_validation(B):
 
 def test_kx_major_validation(B):
     """WO_TF_KX_MAJOR: one kind, 3D TFs, the plane engine's shapes; same bank
-    size as the standard layout; the operators other than the field-tile 3D
-    reconstruction refuse it before launching anything."""
+    size as the standard layout; the 2D solve and the fused blend refuse it
+    before launching anything."""
     K = B.WO_TF_KX_MAJOR
-    for Z, E in ((48, 192), (48, 128), (48, 64), (32, 192), (32, 128), (32, 64)):
+    for Z, E in ((48, 192), (48, 128), (48, 64), (32, 192), (32, 128), (32, 64), (16, 64)):
         for kind in (1, 2, 4):
             assert B.wo_tf_bytes(3, Z, E, E, kind | K) == B.wo_tf_bytes(3, Z, E, E, kind) > 0
     assert B.wo_tf_bytes(1, 48, 192, 192, 1 | 32 | K) > 0          # smooth source
@@ -415,7 +415,7 @@ def test_kx_major_validation(B):
     assert B.wo_tf_bytes(1, 48, 192, 192, 8 | K) == 0              # derivative banks
     assert B.wo_tf_bytes(1, 48, 192, 192, 8 | 16 | K) == 0
     assert B.wo_tf_bytes(1, 48, 192, 192, K) == 0                  # no kind
-    assert B.wo_tf_bytes(1, 16, 64, 64, 1 | K) == 0                # Z outside the plane engine
+    assert B.wo_tf_bytes(1, 16, 128, 128, 1 | K) == 0              # 16 planes: 64-point planes only
     assert B.wo_tf_bytes(1, 96, 192, 192, 1 | K) == 0
     assert B.wo_tf_bytes(1, 48, 256, 256, 1 | K) == 0              # Y outside the plane engine
     assert B.wo_tf_bytes(1, 48, 96, 96, 1 | K) == 0
@@ -428,13 +428,12 @@ def test_kx_major_validation(B):
     eta = B._floats([1e-3, 1e-3])
     n0 = lib.wo_launch_count()
     m = 1 | K
-    assert lib.wo_reconstruct(fake, m, fake, None, eta[0], 0, 0, fake, 4, 32, 64, 64, fake, big, None) == 1
-    assert lib.wo_forward(fake, m, fake, None, fake, 4, 32, 64, 64, fake, big, None) == 1
-    assert lib.wo_forward_adjoint(fake, m, fake, None, fake, 4, 32, 64, 64, fake, big, None) == 1
+    assert lib.wo_reconstruct(fake, m, fake, None, eta[0], 0, 1, fake, 4, 32, 64, 64, fake, big, None) == 1  # 2D
+    assert lib.wo_forward(fake, m, fake, None, fake, 4, 32, 64, 128, fake, big, None) == 3  # not square
     assert lib.wo_reconstruct_field_tiles(fake, m, fake, 32, 2, 2, 48, 8, None, eta[0], 0, 1, fake, fake, big,
                                           None) == 1               # 2D mode
     assert lib.wo_restore_field(fake, m, fake, 32, 2, 2, 48, 8, None, eta[0], 0, 0, fake + 256, fake, big,
                                 None) == 1
-    assert lib.wo_reconstruct_field_tiles(fake, m, fake, 16, 2, 2, 48, 8, None, eta[0], 0, 0, fake, fake, big,
-                                          None) == 3               # Z = 16: no plane engine
+    assert lib.wo_reconstruct_field_tiles(fake, m, fake, 64, 2, 2, 48, 8, None, eta[0], 0, 0, fake, fake, big,
+                                          None) == 3               # Z = 64: no plane engine
     assert lib.wo_launch_count() == n0

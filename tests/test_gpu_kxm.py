@@ -8,7 +8,11 @@
   into the kx-major spectrum, one y-z-operator pass per plane, x pass
   transposing back) against the five-pass path with the standard bank and
   against the oracle, on border and interior tiles, both background rules.
-* Every other use of such a bank is refused with WO_ERR_ARG.
+* The forward model, its adjoint and the 3D reconstruction of plain tiles
+  (a bank per tile, and one bank shared by a batch) on the plane engine
+  against the same calls with the standard bank and against the oracle.
+* The uses such a bank does not serve (the 2D solve, the fused blend) are
+  refused with WO_ERR_ARG.
 """
 import numpy as np
 import pytest
@@ -34,7 +38,7 @@ def engine_tol(flag, m3):
     frequencies near its peak gain, not one."""
     return ENGINE if flag == 0 else 2.0 * ENGINE * max(1.0, float(np.sqrt(m3)))
 
-SHAPES = [(48, 192), (48, 128), (48, 64), (32, 192), (32, 128), (32, 64)]
+SHAPES = [(48, 192), (48, 128), (48, 64), (32, 192), (32, 128), (32, 64), (16, 64)]
 
 
 @pytest.fixture(scope="module")
@@ -173,6 +177,83 @@ def test_field_workload_tiles_plane_engine(env):
     assert rel_l2(got[t], ref) <= TOL
 
 
+@pytest.mark.parametrize("Z,E,n", [(16, 64, 5), (32, 128, 2), (48, 192, 3)])
+def test_operators_on_tiles_plane_engine(env, Z, E, n):
+    """wo_forward (with a background), wo_forward_adjoint, wo_reconstruct
+    (relative and absolute eta) and wo_reconstruct_shared_tf on plain tiles
+    with a kx-major bank: against the standard bank (every tile) and the
+    oracle (the first tile)."""
+    B, torch, dev = env
+    ol = ph.tile_optics(np.random.default_rng(Z + n), n)
+    base = B.WO_TF_PHASE
+    kx = base | B.WO_TF_KX_MAJOR
+    tfs, wss = build_bank(env, ol, Z, E, base, False)
+    tfk, wsk = build_bank(env, ol, Z, E, kx, False)
+    m3 = float(B.tf_views(tfs, n, Z, E, E, base)[1][:, 0].max())
+    f = torch.from_numpy(ph.uniform_volume(3, (n, 1, Z, E, E), -0.02, 0.02).astype(np.float32)).to(dev)
+    d = torch.from_numpy((1.0 + ph.uniform_volume(4, (n, Z, E, E), -0.02, 0.02)).astype(np.float32)).to(dev)
+
+    def both(fn):
+        outs = []
+        for tf, ws, m in ((tfs, wss, base), (tfk, wsk, kx)):
+            outs.append(fn(tf, ws, m))
+            assert B.wo_sync_status(ws)[0] == 0
+        return outs[0].cpu().numpy(), outs[1].cpu().numpy()
+
+    def fwd(tf, ws, m):
+        out = torch.full((n, Z, E, E), float("nan"), device=dev)
+        B.wo_forward(tf, m, f, [1.0], out, n, Z, E, E, ws)
+        return out
+
+    def adj(tf, ws, m):
+        out = torch.full((n, 1, Z, E, E), float("nan"), device=dev)
+        B.wo_forward_adjoint(tf, m, d, [1.0], out, n, Z, E, E, ws)
+        return out
+
+    def rec(flag, bg):
+        def run(tf, ws, m):
+            out = torch.full((n, 1, Z, E, E), float("nan"), device=dev)
+            B.wo_reconstruct(tf, m, d, bg, [1e-3], flag, B.WO_MODE_3D, out, n, Z, E, E, ws)
+            return out
+        return run
+
+    modes, _, _ = OM.widefield_system(OO.transfer_functions(ol[0], (Z, E, E), ("phase",)), ("phase",))
+    want, got = both(fwd)
+    for t in range(n):
+        assert rel_l2(got[t] - 1.0, want[t] - 1.0) <= ENGINE, ("forward", t)
+    ref = OM.forward(modes, f[0].cpu().numpy().astype(np.float64), [1.0])[0]
+    assert rel_l2(got[0] - 1.0, ref - 1.0) <= TOL
+    want, got = both(adj)
+    for t in range(n):
+        assert rel_l2(got[t], want[t]) <= ENGINE, ("adjoint", t)
+    ref = OM.adjoint(modes, d[0:1].cpu().numpy().astype(np.float64), [1.0])[0]
+    assert rel_l2(got[0, 0], ref) <= TOL
+    for flag, bg in ((0, None), (1, [1.0])):
+        want, got = both(rec(flag, bg))
+        # white-noise data: unlike the phantoms above, every frequency near the
+        # inverse's peak gain carries signal, so twice the phantoms' bound
+        for t in range(n):
+            assert rel_l2(got[t], want[t]) <= 2.0 * engine_tol(flag, m3), ("reconstruct", flag, t)
+        ref = OM.reconstruct(modes, d[0:1].cpu().numpy().astype(np.float64), 1e-3, background=bg,
+                             relative=(flag == 0))[0]
+        assert rel_l2(got[0, 0], ref) <= TOL, ("reconstruct", flag)
+    # one bank (tile 0's) shared by the whole batch
+    tf1s, ws1s = build_bank(env, ol[:1], Z, E, base, False)
+    tf1k, ws1k = build_bank(env, ol[:1], Z, E, kx, False)
+    outs = []
+    for tf, m in ((tf1s, base), (tf1k, kx)):
+        ws = torch.empty(B.wo_workspace_bytes(n, Z, E, E, m), dtype=torch.uint8, device=dev)
+        ws[:256].zero_()
+        out = torch.full((n, 1, Z, E, E), float("nan"), device=dev)
+        B.wo_reconstruct_shared_tf(tf, m, d, None, [1e-3], 0, B.WO_MODE_3D, out, n, Z, E, E, ws)
+        assert B.wo_sync_status(ws)[0] == 0
+        outs.append(out.cpu().numpy())
+    for t in range(n):
+        assert rel_l2(outs[1][t], outs[0][t]) <= 2.0 * ENGINE, ("shared", t)  # white-noise data, as above
+    ref = OM.reconstruct(modes, d[n - 1:n].cpu().numpy().astype(np.float64), 1e-3)[0]
+    assert rel_l2(outs[1][n - 1, 0], ref) <= TOL
+
+
 def test_kx_major_bank_refused_elsewhere(env):
     B, torch, dev = env
     Z, ty, tx, core, halo = 32, 2, 2, 48, 8
@@ -185,9 +266,8 @@ def test_kx_major_bank_refused_elsewhere(env):
     tiles = torch.ones((n, Z, E, E), dtype=torch.float32, device=dev)
     out = torch.empty((n, 1, Z, E, E), dtype=torch.float32, device=dev)
     calls = [
-        lambda: B.wo_reconstruct(tf, m, tiles, None, [1e-3], 0, B.WO_MODE_3D, out, n, Z, E, E, ws),
-        lambda: B.wo_forward(tf, m, out, [1.0], tiles, n, Z, E, E, ws),
-        lambda: B.wo_forward_adjoint(tf, m, tiles, None, out, n, Z, E, E, ws),
+        lambda: B.wo_reconstruct(tf, m, tiles, None, [1e-3], 0, B.WO_MODE_2D, out[:, :, 0].contiguous(), n, Z, E,
+                                 E, ws),
         lambda: B.wo_reconstruct_field_tiles(tf, m, field, Z, ty, tx, core, halo, None, [1e-3], 0, B.WO_MODE_2D,
                                              out[:, :, 0].contiguous(), ws),
         lambda: B.wo_restore_field(tf, m, field, Z, ty, tx, core, halo, None, [1e-3], 0, B.WO_MODE_3D,
