@@ -309,7 +309,8 @@ __global__ void __launch_bounds__(kPsfThreads, P::E > 16 ? 3 : 4) k_psf_rows_pai
     P::template fft<false>(w, tw, S, lt);
     if constexpr (ZK > 0) {
       // rows r0, r0 + 1: one plane (Y = N even), bin k of both at dk + k ZK N
-      float2* dk = a.tf + ((t0 * a.n_kinds + slot) * Xh * ZK) * (long long)N + rem0;
+      const long long db = ((t0 * a.n_kinds + slot) * Xh * ZK) * (long long)N + rem0;
+      float2* dk = a.tf + db;
       constexpr int kz = ZK * N;
 #pragma unroll
       for (int m = 0; m < N1; ++m) {
@@ -318,7 +319,7 @@ __global__ void __launch_bounds__(kPsfThreads, P::E > 16 ? 3 : 4) k_psf_rows_pai
         c.x = __shfl_sync(0xffffffffu, mv.x, partner);
         c.y = -__shfl_sync(0xffffffffu, mv.y, partner);
         const int k = lt + T * m;
-        if (k > N / 2 || !live1) continue;
+        if (k > N / 2 || !live1 || !WO_IN(db + k * kz + 1, (long long)a.n_tiles * a.n_kinds * kz * Xh, 9)) continue;
         *reinterpret_cast<float4*>(dk + k * kz) = make_float4(0.5f * (w[m].x + c.x), 0.5f * (w[m].y + c.y),
                                                               0.5f * (w[m].y - c.y), -0.5f * (w[m].x - c.x));
       }

@@ -67,9 +67,10 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_r2c_reg(const float* __res
   if constexpr (PY > 0) {
     const long long plane_rows = (long long)Z * PY;
     const long long blk = rr / plane_rows, rem = rr - blk * plane_rows;  // rem = z PY + y
-    float2* o = out + blk * (N + 1) * plane_rows + rem;
+    const long long ob = blk * (N + 1) * plane_rows + rem;
+    float2* o = out + ob;
     r2c_split<N, T, E>(v, tw2, t, [&](int k, float2 val) {
-      if (live) o[k * plane_rows] = val;
+      if (live && WO_IN(ob + k * plane_rows, nrows * (N + 1), 7)) o[k * plane_rows] = val;
     });
   } else {
     float2* o = out + rr * (N + 1);
@@ -181,10 +182,11 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_r2c_field(FieldSrc f, floa
   for (int m = 0; m < E; ++m) v[m] = make_float2(v[m].x - c, v[m].y - c);
   P::template fft<false>(v, tw, S, t);
   if constexpr (KXM) {
-    float2* o = out + (tile * (N + 1) * f.Z + z) * (long long)W + u;  // bin k at o + k Z W
+    const long long ob = (tile * (N + 1) * f.Z + z) * (long long)W + u;  // bin k at ob + k Z W
+    float2* o = out + ob;
     const long long kstep = (long long)f.Z * W;
     r2c_split<N, T, E>(v, tw2, t, [&](int k, float2 val) {
-      if (live) o[k * kstep] = val;
+      if (live && WO_IN(ob + k * kstep, nrows * (N + 1), 7)) o[k * kstep] = val;
     });
   } else {
     float2* o = out + rr * (N + 1);
@@ -230,11 +232,15 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_c2r_kxm(const float2* __re
   const long long plane_rows = (long long)Z * Y;
   const long long blk = rr / plane_rows, rem = rr - blk * plane_rows;  // rem = z Y + y
   const long long kstep = plane_rows;                                     // bin k of the row at src + k Z Y
-  const float2* src = in + blk * (N + 1) * plane_rows + rem;
+  const long long sb = blk * (N + 1) * plane_rows + rem;
+  const float2* src = in + sb;
   float2 x[E];
 #pragma unroll
-  for (int m = 0; m < E; ++m) x[m] = __ldg(src + (t + T * m) * kstep);
-  const float2 xn = t == 0 ? __ldg(src + N * kstep) : make_float2(0.f, 0.f);  // X[N], partner of X[0]
+  for (int m = 0; m < E; ++m)
+    x[m] = WO_IN(sb + (t + T * m) * kstep, nrows * (N + 1), 7) ? __ldg(src + (t + T * m) * kstep)
+                                                                : make_float2(0.f, 0.f);
+  const float2 xn = (t == 0 && WO_IN(sb + N * kstep, nrows * (N + 1), 7)) ? __ldg(src + N * kstep)
+                                                                           : make_float2(0.f, 0.f);  // X[N]
   P::twiddles(tw);  // while the row's loads are in flight
   make_twiddles<2 * N>(tw2);
   __syncthreads();

@@ -56,4 +56,26 @@ def run(B, torch, dev):
     B.wo_pipeline_probe(tf, d, r, 3, Z, Y, X, -1, 10 ** 9, ws)
     sync("pipeline", ws)
     out["pipeline"] = r.cpu().numpy()
+    # the plane engine: a kx-major bank (16 x 64 x 64), the operators on
+    # tiles, and a 2 x 2 field's tiles read in place (core 48, halo 8)
+    kx = B.WO_TF_PHASE | B.WO_TF_KX_MAJOR
+    tfk, wsk = B.alloc(3, Z, Y, X, kx, dev)
+    B.wo_build_tf(ol, 3, Z, Y, X, kx, tfk, wsk)
+    sync("kx-major build", wsk)
+    fk = torch.from_numpy(ph.uniform_volume(6, (3, 1, Z, Y, X), -0.02, 0.02).astype(np.float32)).to(dev)
+    dk = torch.empty((3, Z, Y, X), dtype=torch.float32, device=dev)
+    B.wo_forward(tfk, kx, fk, [1.0], dk, 3, Z, Y, X, wsk)
+    ak = torch.empty_like(fk)
+    B.wo_forward_adjoint(tfk, kx, d, [1.0], ak, 3, Z, Y, X, wsk)
+    rk = torch.empty_like(fk)
+    B.wo_reconstruct(tfk, kx, d, None, [1e-3], B.WO_ETA_RELATIVE, B.WO_MODE_3D, rk, 3, Z, Y, X, wsk)
+    sync("kx-major operators", wsk)
+    fld = torch.from_numpy(ph.uniform_volume(7, (Z, 96, 96), 0.9, 1.1).astype(np.float32)).to(dev)
+    tf4, ws4 = B.alloc(4, Z, Y, X, kx, dev)
+    B.wo_build_tf(ph.tile_optics(np.random.default_rng(3), 4), 4, Z, Y, X, kx, tf4, ws4)
+    rf = torch.empty((4, 1, Z, Y, X), dtype=torch.float32, device=dev)
+    B.wo_reconstruct_field_tiles(tf4, kx, fld, Z, 2, 2, 48, 8, None, [1e-3], B.WO_ETA_RELATIVE, B.WO_MODE_3D, rf, ws4)
+    sync("kx-major field tiles", ws4)
+    for k, v in (("kx tf", tfk), ("kx forward", dk), ("kx adjoint", ak), ("kx reconstruct", rk), ("kx field", rf)):
+        out[k] = v.cpu().numpy()
     return out, codes
