@@ -278,3 +278,47 @@ def test_kx_major_bank_refused_elsewhere(env):
             c()
         assert e.value.status == B.STATUS_CODES["WO_ERR_ARG"]
     assert B.wo_sync_status(ws)[0] == 0
+
+
+def test_tf_outside_support_is_never_read(env):
+    """The plane engine reads no TF value outside a tile's support disk:
+    filling every such entry of a kx-major bank (whole planes k_x outside the
+    disk, and the z columns (k_y, k_x) outside it in the planes inside) with
+    NaN leaves the field tiles' reconstruction bit for bit the same.  The
+    disk is the library's own test, (k_y / Y)^2 + (k_x / X)^2 > r^2 in
+    float32 with r from the bank's statistics (word 5); entries within 1e-6
+    of the circle are left as they are."""
+    B, torch, dev = env
+    Z, ty, tx, core, halo = 48, 2, 2, 128, 32
+    E = core + 2 * halo
+    n = ty * tx
+    m = B.WO_TF_PHASE | B.WO_TF_KX_MAJOR
+    ol = ph.tile_optics(np.random.default_rng(8), n)
+    tf, ws = build_bank(env, ol, Z, E, m, True)
+    field = torch.from_numpy((1.0 + ph.sphere_phantom(9, (Z, ty * core, tx * core), n_spheres=30))
+                             .astype(np.float32)).to(dev)
+
+    def recon():
+        rec = torch.empty((n, 1, Z, E, E), dtype=torch.float32, device=dev)
+        B.wo_reconstruct_field_tiles(tf, m, field, Z, ty, tx, core, halo, None, [1e-3], B.WO_ETA_RELATIVE,
+                                     B.WO_MODE_3D, rec, ws)
+        assert B.wo_sync_status(ws)[0] == 0
+        return rec.clone()
+
+    want = recon()
+    spec, stats = B.tf_views(tf, n, Z, E, E, m)  # spec: a permuted view of the kx-major storage
+    r = stats[:, 5].cpu().numpy().astype(np.float32)
+    ky = np.arange(E)
+    fy = (np.where(ky < (E + 1) // 2, ky, ky - E).astype(np.float32) / np.float32(E)).astype(np.float32)
+    fx = (np.arange(E // 2 + 1).astype(np.float32) / np.float32(E)).astype(np.float32)
+    planted = 0
+    for t in range(n):
+        # outside by a margin (the device may fuse the sum into an FMA, so entries
+        # within an ulp of the circle are left alone)
+        out = (fy[:, None] * fy[:, None] + fx[None, :] * fx[None, :]) > r[t] * r[t] * np.float32(1 + 1e-6)
+        mask = torch.from_numpy(np.broadcast_to(out, (Z,) + out.shape).copy()).to(dev)
+        spec[t, 0][mask] = complex(float("nan"), float("nan"))
+        planted += int(out.sum())
+    assert planted > 0
+    got = recon()
+    assert torch.equal(got, want)
