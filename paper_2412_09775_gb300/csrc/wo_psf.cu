@@ -146,7 +146,6 @@ __global__ void __launch_bounds__(kPsfThreads, (P::E > 16 && MODE == 2) ? 2 : 4)
     P::template fft<false>(w, tw, S, lt);
 #pragma unroll
     for (int m = 0; m < N1; ++m) {
-      if (T * m > N / 2) continue;  // no lane stores a bin of this register
       const float2 mv = mirror_value<N1>(w, m, lane0);
       float2 c;  // conj(W(N - k))
       c.x = __shfl_sync(0xffffffffu, mv.x, partner);
@@ -183,7 +182,6 @@ __global__ void __launch_bounds__(kPsfThreads, (P::E > 16 && MODE == 2) ? 2 : 4)
     P::template fft<false>(w, tw, S, lt);
 #pragma unroll
     for (int m = 0; m < N1; ++m) {
-      if (T * m > N / 2) continue;  // no lane stores a bin of this register
       const float2 mv = mirror_value<N1>(w, m, lane0);
       float2 c;  // conj(W(N - k))
       c.x = __shfl_sync(0xffffffffu, mv.x, partner);

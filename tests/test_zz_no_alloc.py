@@ -9,8 +9,11 @@ larger problem, then calls the entry point through the C ABI twice in a row
 on different inputs (three kinds through the five passes, and the phase-only
 case through the tile pipeline) and checks each result against the float64
 oracle and against wo_reconstruct with a caller-allocated workspace; the
-device's free memory must not change across those calls.  It lives in its
-own file, collected last, and passes alone or after the rest.
+device's free memory must not change across those calls.  One more call is
+captured in a CUDA graph in global capture mode, which rejects any device
+allocation or release made while the capture is open, and replayed: it must
+give the first call's result bit for bit.  It lives in its own file,
+collected last, and passes alone or after the rest.
 """
 import numpy as np
 import pytest
@@ -79,6 +82,16 @@ def test_static_workspace_matches_reconstruct_twice():
         assert rel_l2(g, ref.cpu().numpy()) <= TOL, call
         want = oracle_recon(o, (Z, Y, X), kinds, d_np[0], bg, eta)
         assert rel_l2(g[0], want) <= TOL, call
+    # the first case once more, captured and replayed: an allocation on this
+    # path would make the capture fail
+    kinds, d_np, d, bg, eta, tf, ref, got = prepared[0]
+    replayed = torch.full_like(ref, float("nan"))
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, capture_error_mode="global"):
+        B.wo_reconstruct_static(tf, kinds, d, bg, eta, B.WO_ETA_RELATIVE, B.WO_MODE_3D, replayed, 1, Z, Y, X)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(replayed, got)
 
 
 def test_static_workspace_rejects_problems_beyond_its_size():
