@@ -408,6 +408,27 @@ def test_relative_eta_definition():
     assert np.abs(a - b).max() <= 1e-14 * np.abs(a).max()
 
 
+def test_relative_eta_is_eta_times_the_forward_operators_squared_norm():
+    # Reading (v) without the per-frequency formula: the relative eta scales
+    # eta by the largest squared singular value of the forward model as a map
+    # of real volumes, taken here from its dense matrix (the real-space forward
+    # model applied to every unit voxel of every property) by an SVD
+    o = ph.optics(na_ill=0.5, tilt_x=0.1, defocus_um=0.2)
+    shape = (4, 8, 8)
+    kinds = ("phase", "absorption")
+    tfs = O.transfer_functions(o, shape, kinds)
+    modes, props, _ = model.widefield_system(tfs, kinds)
+    n, P = int(np.prod(shape)), len(props)
+    A = np.empty((n, P * n))
+    for col in range(P * n):
+        f = np.zeros((P,) + shape)
+        f.flat[col] = 1.0
+        A[:, col] = model.forward(modes, f, [0.0])[0].ravel()
+    smax2 = np.linalg.norm(A, 2) ** 2
+    got = model.eta_absolute(modes[0]["H"], 1e-3, True)
+    assert abs(got - 1e-3 * smax2) <= 1e-10 * 1e-3 * smax2
+
+
 def test_relative_eta_2d_is_the_3d_plane_sum_by_parseval():
     # 2D mode: eta_abs = eta * max over nu_perp of sum_j |H_j|^2 over the
     # planes; by Parseval over z that is (1/Z) sum over k_z of the 3D TF's
