@@ -43,18 +43,24 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// Blend: one thread per 4 consecutive field pixels of a row; the covering
-// tiles (at most two per axis) are the same for the four, only the x weights
-// differ.
-__global__ void __launch_bounds__(256)
+// Blend: one thread per L consecutive field pixels of a row (L = 4 when
+// core and halo are multiples of 4, else 1); the covering tiles (at most two
+// per axis) are the same for the L pixels, only the x weights differ.  The
+// kernel is bound by instruction issue, so the weights' reciprocal is formed
+// once per thread and each covering tile column's x weights once per group,
+// with the values and summation order of the plain per-tile form; eight
+// CTAs per SM (32 registers) keep every warp slot filled.
+template <int L>
+__global__ void __launch_bounds__(256, 8)
     k_blend(const float* __restrict__ tiles, int Z, int tiles_y, int tiles_x, int core, int halo,
-            float* __restrict__ field, int vec) {
+            float* __restrict__ field) {
   const int E = core + 2 * halo;
   const int Yf = tiles_y * core, Xf = tiles_x * core;
-  const int X4 = Xf / 4;  // Xf is a multiple of 4 when vec != 0
   const long long zy = blockIdx.x;  // z * Yf + y
   const long long z = zy / Yf;
   const int y = (int)(zy - z * Yf);
+  const float inv = halo > 0 ? 1.0f / (2.0f * (float)halo) : 0.f;
+  auto weight = [&](int u) { return halo > 0 ? ramp_inv(u, E, inv) : 1.f; };
   int tys[2], us[2];
   float wys[2];
   int ny = 0;
@@ -63,40 +69,45 @@ __global__ void __launch_bounds__(256)
     if (c < 0 || c >= tiles_y) continue;
     const int u = y - (c * core - halo);
     if (u < 0 || u >= E) continue;
-    tys[ny] = c; us[ny] = u; wys[ny] = ramp(u, E, halo); ++ny;
+    tys[ny] = c; us[ny] = u; wys[ny] = weight(u); ++ny;
   }
-  const int nvec = vec ? X4 : Xf;
+  const int nvec = Xf / L;  // Xf is a multiple of L
   for (int i = threadIdx.x; i < nvec; i += 256) {
-    const int x0 = vec ? 4 * i : i;
-    const int lanes = vec ? 4 : 1;
-    float acc[4] = {0.f, 0.f, 0.f, 0.f}, wsum[4] = {0.f, 0.f, 0.f, 0.f};
+    const int x0 = L * i;
+    float acc[L], wsum[L];
+#pragma unroll
+    for (int k = 0; k < L; ++k) acc[k] = wsum[k] = 0.f;
     const int qx = (x0 + halo) / core;
     for (int c = qx - 1; c <= qx; ++c) {
       if (c < 0 || c >= tiles_x) continue;
       const int v = x0 - (c * core - halo);
-      if (v < 0 || v >= E) continue;  // vec: v..v+3 lie in the same tile
+      if (v < 0 || v >= E) continue;  // L = 4: v..v+3 lie in the same tile
+      float wx[L];
+#pragma unroll
+      for (int k = 0; k < L; ++k) wx[k] = weight(v + k);
       for (int a = 0; a < ny; ++a) {
         const long long t = (long long)tys[a] * tiles_x + c;
-        if (!WO_IN(((t * Z + z) * E + us[a]) * (long long)E + v + lanes - 1, (long long)tiles_y * tiles_x * Z * E * E, 4))
+        if (!WO_IN(((t * Z + z) * E + us[a]) * (long long)E + v + L - 1, (long long)tiles_y * tiles_x * Z * E * E, 4))
           continue;
         const float* src = tiles + ((t * Z + z) * E + us[a]) * (long long)E + v;
-        float val[4];
-        if (vec) {
+        float val[L];
+        if constexpr (L == 4) {
           const float4 q = __ldg(reinterpret_cast<const float4*>(src));
           val[0] = q.x; val[1] = q.y; val[2] = q.z; val[3] = q.w;
         } else {
           val[0] = __ldg(src);
         }
-        for (int k = 0; k < lanes; ++k) {
-          const float wgt = wys[a] * ramp(v + k, E, halo);
+#pragma unroll
+        for (int k = 0; k < L; ++k) {
+          const float wgt = wys[a] * wx[k];
           acc[k] += wgt * val[k];
           wsum[k] += wgt;
         }
       }
     }
     float* dst = field + zy * (long long)Xf + x0;
-    if (!WO_IN(zy * (long long)Xf + x0 + lanes - 1, (long long)gridDim.x * Xf, 4)) continue;
-    if (vec) {
+    if (!WO_IN(zy * (long long)Xf + x0 + L - 1, (long long)gridDim.x * Xf, 4)) continue;
+    if constexpr (L == 4) {
       *reinterpret_cast<float4*>(dst) =
           make_float4(acc[0] / wsum[0], acc[1] / wsum[1], acc[2] / wsum[2], acc[3] / wsum[3]);
     } else {
@@ -119,7 +130,8 @@ cudaError_t tiles_blend(const float* tiles, int Z, int ty, int tx, int core, int
                         cudaStream_t s) {
   const int vec = (core % 4 == 0 && halo % 4 == 0) ? 1 : 0;
   dim3 grid((unsigned)((long long)ty * core * Z));
-  WO_LAUNCH("tile_blend", s, (k_blend<<<grid, 256, 0, s>>>(tiles, Z, ty, tx, core, halo, field, vec)));
+  if (vec) WO_LAUNCH("tile_blend", s, (k_blend<4><<<grid, 256, 0, s>>>(tiles, Z, ty, tx, core, halo, field)));
+  else WO_LAUNCH("tile_blend", s, (k_blend<1><<<grid, 256, 0, s>>>(tiles, Z, ty, tx, core, halo, field)));
   return cudaGetLastError();
 }
 

@@ -14,10 +14,14 @@ __device__ __forceinline__ int mirror_idx(int i, int n) {
   return i >= n ? 2 * (n - 1) - i : i;
 }
 
+// The ramp for halo > 0 with inv = 1 / (2 halo) formed by the caller.
+__device__ __forceinline__ float ramp_inv(int u, int E, float inv) {
+  return fminf(1.f, fminf(((float)u + 0.5f) * inv, ((float)(E - u) - 0.5f) * inv));
+}
+
 __device__ __forceinline__ float ramp(int u, int E, int halo) {
   if (halo == 0) return 1.f;
-  const float inv = 1.0f / (2.0f * (float)halo);
-  return fminf(1.f, fminf(((float)u + 0.5f) * inv, ((float)(E - u) - 0.5f) * inv));
+  return ramp_inv(u, E, 1.0f / (2.0f * (float)halo));
 }
 
 }  // namespace wo
