@@ -68,8 +68,6 @@ CPU_SAMPLE = (96, 256, 256)
 NCU_TRAFFIC = {
     ("field", "tf_arms"): {"bytes": 4 * (54528000 + 772520960), "digest": "451b42818bf0103a"},
     ("field", "tf_psf_rows"): {"bytes": 4 * (906436096 + 440025600), "digest": "cf4d832d91af6988"},
-    ("field", "yz_op"): {"bytes": 4 * (744135680 + 407397120), "digest": "55abe3870b2bdbf8"},
-    ("field", "tf_yz"): {"bytes": 4 * (369236736 + 312187904), "digest": "55abe3870b2bdbf8"},
 }
 
 

@@ -109,3 +109,13 @@ def test_tuning_state_checkpoint_round_trip():
     assert np.array_equal(p.optics0.numpy(), want["optics0"])
     with pytest.raises(ValueError):
         p.load_state_dict(dict(want, adam=np.zeros((5, 1, 3))))
+
+
+def test_traffic_records_match_their_kernels_sources():
+    # a DRAM-traffic record is reported only while the kernel's sources are
+    # the ones it was captured from; a record that no longer matches would
+    # never be reported, so none is kept
+    assert bench.NCU_TRAFFIC
+    for (workload, family), rec in bench.NCU_TRAFFIC.items():
+        assert rec["bytes"] > 0
+        assert rec["digest"] == bench.kernel_digest(family), (workload, family)
